@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark of the droplet time step (Mcell-steps/s) on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+One step = one pass of the whole segregated step (thermodynamics, evaporation
+flux, alpha source and advection, properties, energy, species, momentum,
+pressure projection, diagnostics) over one droplet grid.  Default workload:
+the 2D axisymmetric 256 x 512 case with gravity and the centripetal force
+(FP64 with an FP32 multigrid preconditioner).  Under torchrun every rank runs
+an independent replica (the single-droplet path does not shard), and value is
+the cells x steps of all ranks over the slowest rank's time.
+
+The reference arm (--impl reference) times the plain FP64 CPU oracle on the
+host cores on the same workload; no GPU is used there.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+if "--impl" in sys.argv and "reference" in sys.argv:
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+
+import numpy as np  # noqa: E402
+
+from paper_2005_02867_gb300 import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    "cfg2_axisym_256x512": lambda: W.cfg2_axisym_256x512(),
+    "cfg2_axisym_256x512_fp64": lambda: W.cfg2_axisym_256x512(precision=0),
+    "cfg3_cart3d_256": lambda: W.cfg3_cart3d(),
+    "cfg3_cart3d_256_fp64": lambda: W.cfg3_cart3d(precision=0),
+    "cfg1_axisym_64x128": lambda: W.cfg1_axisym_64x128(cg_rtol=1e-12, helm_rtol=1e-13),
+    "cfg5_axisym_128x256": lambda: W.cfg5_axisym_128x256(cg_rtol=1e-12, helm_rtol=1e-13),
+}
+DEFAULT = "cfg2_axisym_256x512"
+METRIC = "Mcell-steps/s"
+FLUSH_BYTES = 512 << 20      # larger than the 129 MB L2
+
+
+def describe(name, cfg):
+    n = list(cfg["n"][:2]) if cfg["geom"] == 0 else list(cfg["n"])
+    return {
+        "workload": name,
+        "geometry": "axisymmetric r-z" if cfg["geom"] == 0 else "3D Cartesian",
+        "grid": n,
+        "cells": int(np.prod(n)),
+        "dt_s": cfg["dt"],
+        "gravity": list(cfg["g"]),
+        "equilibrium": "Raoult" if cfg["eq_model"] == 0 else "Peng-Robinson",
+        "pressure_Pa": cfg["P"],
+        "precision": "fp64" if cfg["precision"] == 0 else "fp64 CG + fp32 multigrid preconditioner",
+        "cg_rtol": cfg["cg_rtol"],
+        "helm_rtol": cfg["helm_rtol"],
+        "l2": "flushed between timed steps (512 MiB device write outside the step events)",
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured (MEASURED_PEAKS.json)"
+        except Exception:
+            pass
+    return 6800.0, "fallback (6.8 TB/s)"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, gpu):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+ORACLE_SNIPPET = r"""
+import sys, time, json
+sys.path.insert(0, {root!r})
+from oracle import step as O
+cfg = json.loads({cfg!r})
+cfg["n"] = tuple(cfg["n"]); cfg["L"] = tuple(cfg["L"]); cfg["xc"] = tuple(cfg["xc"]); cfg["g"] = tuple(cfg["g"])
+st = O.init_state(cfg)
+st = O.step(cfg, st)
+t0 = time.perf_counter()
+n = 0
+while n < {nmax} and (n < {nmin} or time.perf_counter() - t0 < {budget}):
+    st = O.step(cfg, st)
+    n += 1
+print(json.dumps(dict(steps=n, seconds=time.perf_counter() - t0)))
+"""
+
+
+def cpu_oracle(cfg, nmin=2, nmax=50, budget=15.0):
+    """Time the oracle on the host in a fresh single-threaded process (a bounded sample)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SNIPPET.format(root=ROOT, cfg=json.dumps(cfg), nmin=nmin, nmax=nmax, budget=budget)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1200)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["steps"], d["seconds"]
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    name = args.workload
+    cfg = WORKLOADS[name]()
+    ncell = int(np.prod(cfg["n"]))
+    from oracle import step as O
+    st = O.init_state(cfg)
+    for _ in range(args.warmup):
+        st = O.step(cfg, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = O.step(cfg, st)
+    el = time.perf_counter() - t0
+    value = ncell * args.steps / el / 1e6
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "impl": "reference", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": describe(name, cfg),
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full oracle steps of the workload after {args.warmup} warm-up steps"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2005_02867_gb300 import _build, droplet as D
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or not os.path.exists(D.LIBPATH):
+        _build.build_library()
+    if world > 1:
+        dist.barrier()
+    D.load_library()
+
+    name = args.workload
+    cfg = WORKLOADS[name]()
+    ncell = int(np.prod(cfg["n"]))
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sim = D.Droplet(cfg, stream=stream.cuda_stream)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region: inputs resident in HBM, L2 flushed before every step
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = Clocks(local)
+    D.droplet_profile(sim.h, 1)
+    n0 = D.droplet_launch_count(sim.h)
+    status = 0
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        rc = sim.step(1)
+        status = status or rc
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = D.droplet_launch_count(sim.h) - n0
+    ck = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    prof = {k: D.droplet_profile_read(sim.h, k) for k in D.KCLASS}
+    D.droplet_profile(sim.h, 0)
+    if world > 1:
+        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = ncell * args.steps * world / (t_ms / 1e3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers: upload the state from
+    # pinned host memory, one step, read the state back, every step
+    fields = ["alpha", "T", "omega", "p", "rhoG"] + ["u%d" % a for a in range(3 if cfg["geom"] == 1 else 2)]
+    bufs = {}
+    for f in fields:
+        n = D.droplet_field_size(sim.h, f)
+        bufs[f] = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        D.droplet_get_field_ptr(sim.h, f, bufs[f].data_ptr(), n)
+    nbytes = sum(b.numel() * 8 for b in bufs.values())
+    e2e_steps = max(1, min(args.steps, 10))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for f in fields:
+            D.droplet_set_field_ptr(sim.h, f, bufs[f].data_ptr(), bufs[f].numel())
+        sim.step(1)
+        for f in fields:
+            D.droplet_get_field_ptr(sim.h, f, bufs[f].data_ptr(), bufs[f].numel())
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = ncell * e2e_steps * world / e2e_s / 1e6
+    diag = sim.diag()
+    sim.close()
+
+    if rank == 0:
+        dom = max(prof, key=lambda k: prof[k][0])
+        ms, nl, by = prof[dom]
+        achieved = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        peak, src = load_peaks()
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64" if cfg["precision"] == 0 else "f64 (f32 multigrid preconditioner)",
+            "data": "synthetic", "config": describe(name, cfg),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": src, "traffic": None,
+                         "launches": nl, "kernel_ms_total": ms,
+                         "share_of_step": ms / t_ms if t_ms > 0 else None},
+            "kernel_classes": {k: {"ms": v[0], "launches": v[1], "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else 0}
+                               for k, v in prof.items()},
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                    "steps": e2e_steps},
+            "gpu_launches": launches,
+            "solver_iterations_last_step": {"p": diag["its_p"], "T": diag["its_T"], "omega": diag["its_w"],
+                                            "u": diag["its_u"]},
+            "status": status,
+            "clocks": ck,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            try:
+                n, sec = cpu_oracle(cfg)
+                line["cpu_baseline"] = {"value": ncell * n / sec / 1e6, "unit": METRIC, "cores": 1, "kind": "oracle",
+                                        "sample": f"{n} oracle steps of the same workload (single thread, after one "
+                                                  f"untimed step)"}
+            except Exception as e:  # the GPU number stands on its own
+                line["cpu_baseline"] = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle",
+                                        "sample": f"failed: {str(e)[-200:]}"}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,196 @@
+/*
+ * droplet.h -- C ABI of the GB300 (sm_103a) implementation of one time step of
+ * the VOF droplet-evaporation method of Saufi, Frassoldati, Faravelli & Cuoci,
+ * "DropletSMOKE++: a comprehensive multiphase CFD framework for the
+ * evaporation of multidimensional fuel droplets" (arXiv 2005.02867).
+ *
+ * The library advances, on one GPU, an isolated droplet on a uniform 2D
+ * axisymmetric (r, z) or 3D Cartesian grid.  One call of droplet_step runs,
+ * per time step, the segregated sequence of Sec. 3.1 (Fig. Scheme):
+ *   thermodynamics (Sec. 2.5, Eqs. equilibrium / equilibirumyi / densitygas),
+ *   evaporation flux (Sec. 2.4, Eqs. massflux, sumoverm, alphafunction),
+ *   alpha source (Eq. alphasource), interface advection (Eq. advection),
+ *   mixture properties (Sec. 2.7), energy (Eq. Teqn), species
+ *   (Eq. speciesequation), momentum with the centripetal force
+ *   (Eqs. magneticfield, magneticpotential, NavierStokesModified) and the
+ *   variable-density pressure projection (Eq. pequation).
+ *
+ * Conventions
+ *   - Every function returns an int status: 0 = success, < 0 = error
+ *     (DROPLET_ERR_*).  droplet_strerror() names it.  No function aborts the
+ *     process; a CUDA failure is reported as DROPLET_ERR_CUDA.
+ *   - Units are SI.  Fields are FP64 on the host side of this ABI.
+ *   - Grid layout: cell (i, j, k) has the linear index i + n0 (j + n1 k)
+ *     (index 0 fastest).  Axisymmetric runs use n2 = 1 with axis 0 = r and
+ *     axis 1 = z; 3D runs use x, y, z with z the streamwise (gravity / inflow)
+ *     axis.  Face velocities of direction a are stored on the faces normal to
+ *     a, with n_a + 1 entries along a (same index order).
+ *   - The library owns all device memory it allocates; caller buffers are
+ *     only read or written during the call that receives them.
+ */
+#ifndef DROPLET_H
+#define DROPLET_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define DROPLET_OK                 0
+#define DROPLET_ERR_ARG           -1  /* invalid configuration or argument            */
+#define DROPLET_ERR_CUDA          -2  /* a CUDA runtime call failed                    */
+#define DROPLET_ERR_NOT_CONVERGED -3  /* a linear solve hit its iteration cap          */
+#define DROPLET_ERR_NONFINITE     -4  /* a non-finite value appeared in the state      */
+#define DROPLET_ERR_SIZE          -5  /* host buffer size does not match the field     */
+#define DROPLET_ERR_NOMEM         -6  /* device allocation failed                      */
+
+/* diagnostic flag bits (droplet_diag_t.flags), accumulated since the last read */
+#define DROPLET_FLAG_NO_INTERFACE   1u   /* sum f(alpha) m_raw V = 0: mdot set to 0         */
+#define DROPLET_FLAG_MDOT_CAPPED    2u   /* mdot limited to rho_L alpha / dt somewhere     */
+#define DROPLET_FLAG_ALPHA_CLIPPED  4u   /* alpha left [0, 1] and was clipped              */
+#define DROPLET_FLAG_ADJ_NOT_FOUND  8u   /* an interface cell found no adjacent gas cell   */
+#define DROPLET_FLAG_BOILING       16u   /* saturation mole fraction clamped below 1       */
+
+/* physics_mask bits */
+#define DROPLET_PHYS_EVAP     1
+#define DROPLET_PHYS_ENERGY   2
+#define DROPLET_PHYS_SPECIES  4
+#define DROPLET_PHYS_FLOW     8
+#define DROPLET_PHYS_ALL     15
+
+/* Problem statement of one droplet (Sec. 2, Sec. 3.2 boundary conditions,
+ * case tables table1Dcases / tableGravityCases / tableForcedCases).
+ * Copied by droplet_init; the caller keeps ownership. */
+typedef struct droplet_config {
+  int    geom;          /* 0 = 2D axisymmetric r-z, 1 = 3D Cartesian                  */
+  int    n[3];          /* cells per axis; n[2] is ignored (taken as 1) when geom = 0  */
+  double L[3];          /* domain extent [m]                                           */
+  double xc[3];         /* droplet and fibre centre [m]; xc[0] = 0 when geom = 0        */
+  double D0;            /* initial droplet diameter [m]                                */
+  double T_drop;        /* initial liquid temperature [K]                              */
+  double T_amb;         /* ambient (and inflow) temperature [K]                        */
+  double P;             /* thermodynamic pressure [Pa]                                 */
+  double g[3];          /* gravity per axis [m/s2]                                     */
+  double u_inflow;      /* forced-convection inlet velocity along the streamwise axis  */
+  int    bc_mode;       /* 0 natural convection (open inlet), 1 forced-convection inlet */
+  int    eq_model;      /* 0 Raoult + Clausius-Clapeyron, 1 Peng-Robinson fugacities   */
+  double Tb, Lv, M_l, rho_l, cp_l, k_l, mu_l, D_l;   /* liquid fuel                    */
+  double M_g, cp_g, cp_v, k_g, mu_g, D_g;            /* inert gas; D_g at 1 bar        */
+  double Tc, Pc, omega_ac, Tc_g, Pc_g, omega_g, kij; /* Peng-Robinson data            */
+  double xi0;           /* centripetal potential intensity [m2/s2] (Eq. magneticpotential) */
+  double fiber_radius;  /* D_f [m] (Eq. magneticpotential)                             */
+  double dt;            /* time step [s]                                               */
+  int    precision;     /* 0 = FP64 throughout, 1 = FP32 multigrid preconditioner     */
+  double cg_rtol;       /* pressure solve: relative residual target                    */
+  int    cg_maxit;      /* pressure solve: iteration cap                               */
+  double helm_rtol;     /* T, omega, momentum solves: relative residual target         */
+  int    helm_maxit;    /* T, omega, momentum solves: iteration cap                    */
+  unsigned long long seed;  /* initial temperature perturbation seed (SplitMix64)      */
+  double T_perturb;     /* relative amplitude of the initial T perturbation            */
+  int    const_props_check; /* 1 = constant-property d2-law check mode                 */
+  int    physics_mask;  /* DROPLET_PHYS_* bits of the active stages                     */
+  double C_alpha;       /* interface-compression coefficient of the alpha flux         */
+} droplet_config;
+
+/* Diagnostics of one droplet after the last completed step (Sec. 4 reports
+ * the diameter decay, the surface temperature and the vaporisation rate). */
+typedef struct droplet_diag_t {
+  double t;             /* simulated time [s]                                         */
+  long long step;       /* steps taken                                                 */
+  double V_l;           /* liquid volume [m3] (2 pi sum alpha V in 2D)                 */
+  double d_eq;          /* equivalent diameter (6 V_l / pi)^(1/3) [m]                  */
+  double d2;            /* d_eq^2 [m2]                                                 */
+  double mdot_tot;      /* evaporation rate of the last step [kg/s]                    */
+  double K_norm;        /* K of Eq. alphafunction in the last step                     */
+  double T_s_mean;      /* |grad alpha|-weighted mean temperature [K]                  */
+  double M_liq, M_vap;  /* liquid and vapour masses [kg]                               */
+  double vap_out_cum;   /* vapour mass that left through open boundaries [kg]          */
+  double max_u;         /* max |face velocity| [m/s]                                   */
+  double alpha_min, alpha_max;
+  double clip_mass;     /* cumulative clipped liquid volume [m3]                       */
+  int    its_p, its_T, its_w, its_u;   /* iterations of the last step's solves        */
+  double res_p;         /* final relative residual of the last pressure solve          */
+  unsigned flags;       /* DROPLET_FLAG_* accumulated since the previous droplet_diag  */
+} droplet_diag_t;
+
+typedef struct droplet_ctx droplet_ctx;   /* opaque; owns all device memory */
+
+/* field identifiers for droplet_get_field / droplet_set_field */
+enum droplet_field {
+  DROPLET_F_ALPHA = 0, DROPLET_F_T = 1, DROPLET_F_OMEGA = 2, DROPLET_F_P = 3, DROPLET_F_RHOG = 4,
+  DROPLET_F_U0 = 5, DROPLET_F_U1 = 6, DROPLET_F_U2 = 7,
+  /* intermediates of the last step (read only) */
+  DROPLET_F_MDOT = 8, DROPLET_F_MRAW = 9, DROPLET_F_ALPHA_STAR = 10, DROPLET_F_DP = 11, DROPLET_F_S = 12,
+  DROPLET_F_USTAR0 = 13, DROPLET_F_USTAR1 = 14, DROPLET_F_USTAR2 = 15, DROPLET_F_RHOG_OLD = 16,
+  DROPLET_F_OMEGA_PINNED = 17,
+  DROPLET_F_COUNT = 18
+};
+
+/* Create a context for n_droplets independent droplets (currently 1) and set
+ * the initial state of Sec. 3.3: alpha from sub-cell sampling of the sphere,
+ * the steady spherical conduction profile of T, the quasi-steady Stefan
+ * profile of the vapour, u = 0, p_rgh = 0.  cuda_stream is a cudaStream_t
+ * (NULL = the legacy default stream) on which every later call enqueues its
+ * work.  On success *out receives the context.  Errors: DROPLET_ERR_ARG (bad
+ * dimensions, droplet not inside the domain, dt <= 0, unsupported option),
+ * DROPLET_ERR_NOMEM, DROPLET_ERR_CUDA. */
+int droplet_init(const droplet_config* cfgs, int n_droplets, void* cuda_stream, droplet_ctx** out);
+
+/* Advance every droplet by n_steps time steps (the stage list of Sec. 3.1).
+ * Enqueued on the context's stream; returns after the last step has been
+ * enqueued and its solver status checked.  DROPLET_ERR_NOT_CONVERGED is
+ * returned when a linear solve reached its cap (the state is still advanced). */
+int droplet_step(droplet_ctx* ctx, int n_steps);
+
+/* Copy the diagnostics of droplet `droplet` into the caller-owned *out
+ * (synchronises the stream).  Clears the accumulated flags. */
+int droplet_diag(droplet_ctx* ctx, int droplet, droplet_diag_t* out);
+
+/* Number of doubles of field `field_id` (cells, or faces for velocities). */
+int droplet_field_size(droplet_ctx* ctx, int droplet, int field_id, size_t* n);
+
+/* Copy a field to the caller-owned host array `host` of exactly n doubles
+ * (DROPLET_ERR_SIZE otherwise).  Synchronises the stream. */
+int droplet_get_field(droplet_ctx* ctx, int droplet, int field_id, double* host, size_t n);
+
+/* Overwrite a state field (ALPHA, T, OMEGA, P, RHOG, U0..U2) from n host doubles. */
+int droplet_set_field(droplet_ctx* ctx, int droplet, int field_id, const double* host, size_t n);
+
+/* Kernel classes timed by droplet_profile (algorithmic bytes per launch in brackets,
+ * w = word size of the launch, d = 2 or 3 active axes, N = unknowns of the launch):
+ *   0 MG_SMOOTH   red-black Gauss-Seidel half sweep    [(2.5 + d) N w]
+ *   1 SPMV        CG operator application + dot        [(3 + d) N 8]
+ *   2 UPDATE      CG x/r update + dot                  [5 N 8]
+ *   3 MG_RESTRICT residual + restriction               [(3 + d) N w + N/2^d w]
+ *   4 MG_PROLONG  injection prolongation               [(2 + 1/2^d) N w]
+ *   5 MOM_ASSEMBLE momentum system assembly            [(12 + 2d) N 8]
+ *   6 SCALAR_ASSEMBLE energy / species assembly        [(12 + 2d) N 8]           */
+#define DROPLET_KCLASS_COUNT 7
+
+/* Start (enable = 1) or stop (0) timing every launch of the kernel classes above
+ * with CUDA events on the context's stream; starting clears the totals. */
+int droplet_profile(droplet_ctx* ctx, int enable);
+
+/* Totals since profiling started for one kernel class: summed event time [ms],
+ * number of launches and summed algorithmic bytes.  Synchronises the stream. */
+int droplet_profile_read(droplet_ctx* ctx, int kclass, double* ms_total, long long* launches, double* bytes_total);
+
+/* Number of kernel launches the library has issued for this context so far. */
+int droplet_launch_count(droplet_ctx* ctx, long long* launches);
+
+/* Block until all work enqueued by the context has finished. */
+int droplet_sync(droplet_ctx* ctx);
+
+/* Release every device allocation of the context (NULL is accepted). */
+void droplet_free(droplet_ctx* ctx);
+
+/* Static, human-readable name of a status code. */
+const char* droplet_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DROPLET_H */

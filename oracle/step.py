@@ -664,7 +664,6 @@ def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=Non
     Fsum = divergence_sum(G, [u[a] * G.A[a] if a in G.act else None for a in range(3)])
     rhs = rhs - coef_t * (net - phi_n * Fsum)
     if pin_mask is not None and pin_mask.any():
-        rhs = np.where(pin_mask, pin_val, rhs)
         for a in G.act:
             lo = [slice(None)] * 3
             hi = [slice(None)] * 3
@@ -681,7 +680,11 @@ def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=Non
             rhs[hi] += np.where(m_hi, c * pin_val[lo], 0.0)
             diag[hi] += np.where(m_hi, c, 0.0)
             coup[a] = np.where(pl | ph, 0.0, c)
-        diag = np.where(pin_mask, 1.0, diag)
+        # pinned rows keep the scale of the other rows (coef V/dt), so that a
+        # relative residual measures the free rows too
+        dpin = coef_t * G.V / dt
+        diag = np.where(pin_mask, dpin, diag)
+        rhs = np.where(pin_mask, dpin * pin_val, rhs)
     return solve_box(n, diag, coup, rhs)
 
 

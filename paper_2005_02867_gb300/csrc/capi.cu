@@ -1,0 +1,460 @@
+// C ABI of the droplet library (include/droplet.h): context lifetime, the
+// per-step stage sequence of Sec. 3.1 (Fig. Scheme), diagnostics and field
+// access.  Every stage runs in the kernels of step_kernels.cu and solver.cu;
+// this file only allocates, launches and copies.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include "kernels.h"
+
+using namespace dg;
+
+#define CKR(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { fprintf(stderr, "droplet: %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); return DROPLET_ERR_CUDA; } } while (0)
+
+struct droplet_ctx {
+  cudaStream_t st = nullptr;
+  droplet_config cfg;
+  Geo g;
+  Phys p;
+  // state
+  double *alpha = nullptr, *T = nullptr, *omega = nullptr, *pr = nullptr, *rhoG = nullptr, *u[3] = {nullptr, nullptr, nullptr};
+  // step work arrays
+  double *rhoG_old = nullptr, *mdot = nullptr, *mraw = nullptr, *astar = nullptr, *aL = nullptr, *Rp = nullptr, *Rm = nullptr;
+  double *FL[3] = {nullptr, nullptr, nullptr}, *AF[3] = {nullptr, nullptr, nullptr}, *us[3] = {nullptr, nullptr, nullptr};
+  double *rho = nullptr, *mu = nullptr, *kc = nullptr, *cp = nullptr, *Dm = nullptr, *yq = nullptr, *dp = nullptr, *S = nullptr;
+  int* adj = nullptr;
+  double *bD = nullptr, *bc[3] = {nullptr, nullptr, nullptr}, *brhs = nullptr, *bx = nullptr;
+  double *part = nullptr, *psum = nullptr, *pmax = nullptr, *scal = nullptr;
+  unsigned* flags = nullptr;
+  double* hscal = nullptr;
+  unsigned* hflags = nullptr;
+  Solver solver;
+  Prof prof;
+  int its_p = 0, its_T = 0, its_w = 0, its_u = 0;
+  double res_p = 0.0, t = 0.0;
+  long long step = 0;
+};
+
+static const char* kErr[] = {"ok", "invalid argument", "CUDA error", "linear solve not converged",
+                             "non-finite value", "buffer size mismatch", "device allocation failed"};
+
+extern "C" const char* droplet_strerror(int s) {
+  if (s > 0 || s < -6) return "unknown status";
+  return kErr[-s];
+}
+
+static int check_cfg(const droplet_config& c) {
+  if (c.geom != 0 && c.geom != 1) return DROPLET_ERR_ARG;
+  int na = c.geom == 0 ? 2 : 3;
+  for (int a = 0; a < na; ++a) {
+    if (c.n[a] < 4 || c.n[a] > 16384 || !(c.L[a] > 0.0)) return DROPLET_ERR_ARG;
+  }
+  if (!(c.dt > 0.0) || !(c.D0 > 0.0) || !(c.P > 0.0) || !(c.T_amb > 0.0) || !(c.T_drop > 0.0)) return DROPLET_ERR_ARG;
+  for (int a = 0; a < na; ++a)
+    if (c.xc[a] < 0.0 || c.xc[a] > c.L[a]) return DROPLET_ERR_ARG;
+  if (c.geom == 0 && c.xc[0] != 0.0) return DROPLET_ERR_ARG;
+  if (c.eq_model != 0 && c.eq_model != 1) return DROPLET_ERR_ARG;
+  if (c.bc_mode != 0 && c.bc_mode != 1) return DROPLET_ERR_ARG;
+  if (c.cp_v != c.cp_g) return DROPLET_ERR_ARG;   // the j_d (cp_v - cp_g) . grad T term is not carried
+  if (c.cg_maxit < 1 || c.helm_maxit < 1 || !(c.cg_rtol > 0.0) || !(c.helm_rtol > 0.0)) return DROPLET_ERR_ARG;
+  if (c.precision != 0 && c.precision != 1) return DROPLET_ERR_ARG;
+  return 0;
+}
+
+static void make_geo(const droplet_config& c, Geo& g) {
+  memset(&g, 0, sizeof(g));
+  g.axisym = c.geom == 0;
+  g.act3 = !g.axisym;
+  g.n[0] = c.n[0];
+  g.n[1] = c.n[1];
+  g.n[2] = g.axisym ? 1 : c.n[2];
+  for (int a = 0; a < 3; ++a) g.h[a] = (a < 2 || !g.axisym) ? c.L[a] / g.n[a] : 1.0;
+  g.hmin = g.axisym ? fmin(g.h[0], g.h[1]) : fmin(g.h[0], fmin(g.h[1], g.h[2]));
+  g.s = g.axisym ? 1 : 2;
+  int inlet = c.bc_mode == 1 ? BC_FORCED : BC_OPEN;
+  if (g.axisym) {
+    g.bc[0][0] = BC_AXIS; g.bc[0][1] = BC_WALL;
+    g.bc[1][0] = inlet;   g.bc[1][1] = BC_OPEN;
+    g.bc[2][0] = BC_WALL; g.bc[2][1] = BC_WALL;
+  } else {
+    g.bc[0][0] = BC_WALL; g.bc[0][1] = BC_WALL;
+    g.bc[1][0] = BC_WALL; g.bc[1][1] = BC_WALL;
+    g.bc[2][0] = inlet;   g.bc[2][1] = BC_OPEN;
+  }
+  g.N = (long long)g.n[0] * g.n[1] * g.n[2];
+}
+
+static void make_phys(const droplet_config& c, Phys& p) {
+  memset(&p, 0, sizeof(p));
+  p.D0 = c.D0; p.T_drop = c.T_drop; p.T_amb = c.T_amb; p.P = c.P;
+  for (int a = 0; a < 3; ++a) { p.g[a] = c.g[a]; p.xc[a] = c.xc[a]; }
+  if (c.geom == 0) p.g[2] = 0.0;
+  p.u_in = c.u_inflow;
+  p.Tb = c.Tb; p.Lv = c.Lv; p.M_l = c.M_l; p.rho_l = c.rho_l; p.cp_l = c.cp_l; p.k_l = c.k_l; p.mu_l = c.mu_l; p.D_l = c.D_l;
+  p.M_g = c.M_g; p.cp_g = c.cp_g; p.cp_v = c.cp_v; p.k_g = c.k_g; p.mu_g = c.mu_g; p.D_g = c.D_g;
+  p.Tc = c.Tc; p.Pc = c.Pc; p.om = c.omega_ac; p.Tc_g = c.Tc_g; p.Pc_g = c.Pc_g; p.om_g = c.omega_g; p.kij = c.kij;
+  p.xi0 = c.xi0; p.Df = c.fiber_radius; p.dt = c.dt; p.C_alpha = c.C_alpha; p.T_perturb = c.T_perturb;
+  p.D_gas = c.D_g * (1.0e5 / c.P);
+  p.rhoG_const = c.P * c.M_g / (R_GAS * c.T_amb);
+  p.seed = c.seed;
+  p.eq_model = c.eq_model;
+  p.const_props = c.const_props_check;
+  p.physics = c.physics_mask;
+}
+
+static int dalloc(double** q, long long n) {
+  if (cudaMalloc((void**)q, sizeof(double) * (size_t)(n > 0 ? n : 1)) != cudaSuccess) return DROPLET_ERR_NOMEM;
+  return 0;
+}
+
+static void free_all(droplet_ctx* c) {
+  double** arrs[] = {&c->alpha, &c->T, &c->omega, &c->pr, &c->rhoG, &c->rhoG_old, &c->mdot, &c->mraw, &c->astar,
+                     &c->aL, &c->Rp, &c->Rm, &c->rho, &c->mu, &c->kc, &c->cp, &c->Dm, &c->yq, &c->dp, &c->S,
+                     &c->bD, &c->brhs, &c->bx, &c->part, &c->psum, &c->pmax, &c->scal};
+  for (auto q : arrs) { cudaFree(*q); *q = nullptr; }
+  for (int a = 0; a < 3; ++a) {
+    cudaFree(c->u[a]); cudaFree(c->FL[a]); cudaFree(c->AF[a]); cudaFree(c->us[a]); cudaFree(c->bc[a]);
+    c->u[a] = c->FL[a] = c->AF[a] = c->us[a] = c->bc[a] = nullptr;
+  }
+  cudaFree(c->adj); cudaFree(c->flags);
+  c->adj = nullptr; c->flags = nullptr;
+  cudaFreeHost(c->hscal); cudaFreeHost(c->hflags);
+  c->hscal = nullptr; c->hflags = nullptr;
+  c->solver.release();
+  c->prof.destroy();
+}
+
+static int run_diag(droplet_ctx* c) {
+  Geo& g = c->g;
+  int nb = red_grid(g.N);
+  ++g_launches, k_diag<<<nb, TPB, 0, c->st>>>(g, c->alpha, c->T, c->mdot, c->omega, c->rhoG, c->u[0], c->u[1], c->u[2] ? c->u[2] : c->u[0],
+                                c->psum, c->pmax);
+  ++g_launches, k_diag_finish<<<1, TPB, 0, c->st>>>(c->psum, c->pmax, nb, c->scal);
+  CKR(cudaGetLastError());
+  return 0;
+}
+
+extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cuda_stream, droplet_ctx** out) {
+  if (!cfgs || !out || n_droplets != 1) return DROPLET_ERR_ARG;
+  *out = nullptr;
+  int rc = check_cfg(cfgs[0]);
+  if (rc) return rc;
+  droplet_ctx* c = new (std::nothrow) droplet_ctx();
+  if (!c) return DROPLET_ERR_NOMEM;
+  c->cfg = cfgs[0];
+  c->st = (cudaStream_t)cuda_stream;
+  make_geo(c->cfg, c->g);
+  make_phys(c->cfg, c->p);
+  Geo& g = c->g;
+  long long N = g.N;
+  int na = nact(g);
+  double** cells[] = {&c->alpha, &c->T, &c->omega, &c->pr, &c->rhoG, &c->rhoG_old, &c->mdot, &c->mraw, &c->astar,
+                      &c->aL, &c->Rp, &c->Rm, &c->rho, &c->mu, &c->kc, &c->cp, &c->Dm, &c->yq, &c->dp, &c->S,
+                      &c->bD, &c->brhs, &c->bx};
+  for (auto q : cells)
+    if ((rc = dalloc(q, N))) { free_all(c); delete c; return rc; }
+  for (int a = 0; a < 3; ++a) {
+    if ((rc = dalloc(&c->bc[a], N))) { free_all(c); delete c; return rc; }
+    if (a >= na) continue;
+    long long nf = nfaces(g, a);
+    if ((rc = dalloc(&c->u[a], nf)) || (rc = dalloc(&c->FL[a], nf)) || (rc = dalloc(&c->AF[a], nf)) ||
+        (rc = dalloc(&c->us[a], nf))) { free_all(c); delete c; return rc; }
+  }
+  if ((rc = dalloc(&c->part, RED_BLOCKS * 8)) || (rc = dalloc(&c->psum, RED_BLOCKS * 6)) ||
+      (rc = dalloc(&c->pmax, RED_BLOCKS * 3)) || (rc = dalloc(&c->scal, SC_COUNT))) { free_all(c); delete c; return rc; }
+  if (cudaMalloc((void**)&c->adj, sizeof(int) * N) != cudaSuccess || cudaMalloc((void**)&c->flags, sizeof(unsigned)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->hscal, sizeof(double) * SC_COUNT) != cudaSuccess ||
+      cudaMallocHost((void**)&c->hflags, sizeof(unsigned)) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_NOMEM; }
+  if ((rc = c->solver.setup(N, c->st))) { free_all(c); delete c; return rc; }
+  c->solver.prof = &c->prof;
+  cudaStream_t st = c->st;
+  int gc = lin_grid(N);
+  cudaMemsetAsync(c->scal, 0, sizeof(double) * SC_COUNT, st);
+  cudaMemsetAsync(c->flags, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(c->pr, 0, sizeof(double) * N, st);
+  cudaMemsetAsync(c->mdot, 0, sizeof(double) * N, st);
+  cudaMemsetAsync(c->mraw, 0, sizeof(double) * N, st);
+  for (int a = 0; a < na; ++a) {
+    cudaMemsetAsync(c->u[a], 0, sizeof(double) * nfaces(g, a), st);
+    cudaMemsetAsync(c->us[a], 0, sizeof(double) * nfaces(g, a), st);
+  }
+  double dtv = c->cfg.dt;
+  cudaMemcpyAsync(c->scal + SC_DT, &dtv, sizeof(double), cudaMemcpyHostToDevice, st);
+  ++g_launches, k_init<<<gc, TPB, 0, st>>>(g, c->p, c->alpha, c->T, c->omega, c->rhoG);
+  if (g.bc[g.s][0] == BC_FORCED) {
+    // inlet faces (index 0 along the streamwise axis) carry u_inflow: the first n0*n1 entries of u[s] in 3D,
+    // the first n0 entries of u[1] in 2D
+    long long cnt = g.axisym ? g.n[0] : (long long)g.n[0] * g.n[1];
+    double* hv = (double*)malloc(sizeof(double) * cnt);
+    for (long long q = 0; q < cnt; ++q) hv[q] = c->cfg.u_inflow;
+    cudaMemcpyAsync(c->u[g.s], hv, sizeof(double) * cnt, cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+    free(hv);
+  }
+  if ((rc = run_diag(c))) { free_all(c); delete c; return rc; }
+  if (cudaStreamSynchronize(st) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_CUDA; }
+  *out = c;
+  return 0;
+}
+
+static int one_step(droplet_ctx* c, int* nc_flag) {
+  Geo& g = c->g;
+  Phys& p = c->p;
+  cudaStream_t st = c->st;
+  long long N = g.N;
+  int na = nact(g);
+  int gc = lin_grid(N), nb = red_grid(N);
+  double* u2 = c->u[2] ? c->u[2] : c->u[0];
+  int mask = p.physics;
+  // S0
+  ++g_launches, k_thermo_pin<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->T, c->omega, c->rhoG_old, c->flags);
+  // S1, S2
+  if (mask & DROPLET_PHYS_EVAP) {
+    ++g_launches, k_evap_raw<<<nb, TPB, 0, st>>>(g, p, c->alpha, c->omega, c->rhoG_old, c->u[0], c->u[1], u2, c->mraw, c->adj, c->part, c->flags);
+    ++g_launches, k_evap_K<<<1, TPB, 0, st>>>(c->part, nb, c->scal, c->flags);
+  } else {
+    cudaMemsetAsync(c->mraw, 0, sizeof(double) * N, st);
+    cudaMemsetAsync(c->scal + SC_K, 0, sizeof(double), st);
+  }
+  ++g_launches, k_alpha_source<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->mraw, c->scal, c->mdot, c->astar, c->flags);
+  // S3
+  if (mask & DROPLET_PHYS_FLOW) {
+    for (int a = 0; a < na; ++a)
+      ++g_launches, k_adv_faces<<<lin_grid(nfaces(g, a)), TPB, 0, st>>>(g, p, a, c->astar, c->u[a], c->FL[a], c->AF[a]);
+    double* F2 = c->FL[2] ? c->FL[2] : c->FL[0];
+    double* A2 = c->AF[2] ? c->AF[2] : c->AF[0];
+    ++g_launches, k_adv_low<<<gc, TPB, 0, st>>>(g, c->astar, c->FL[0], c->FL[1], F2, c->aL);
+    ++g_launches, k_adv_limit<<<gc, TPB, 0, st>>>(g, c->astar, c->aL, c->AF[0], c->AF[1], A2, c->Rp, c->Rm);
+    ++g_launches, k_adv_update<<<nb, TPB, 0, st>>>(g, c->aL, c->AF[0], c->AF[1], A2, c->Rp, c->Rm, c->alpha, c->part, c->flags);
+  } else {
+    ++g_launches, k_alpha_clip_only<<<nb, TPB, 0, st>>>(g, c->astar, c->alpha, c->part);
+  }
+  ++g_launches, k_clip_finish<<<1, TPB, 0, st>>>(c->part, nb, c->scal, c->flags);
+  // S4
+  ++g_launches, k_props<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->rhoG_old, c->omega, c->rho, c->mu, c->kc, c->cp, c->Dm);
+  BoxSys bs;
+  bs.D = c->bD; bs.b = c->brhs; bs.x = c->bx;
+  for (int a = 0; a < 3; ++a) bs.c[a] = a < na ? c->bc[a] : nullptr;
+  SolveStats ss;
+  int rc;
+  // S5 energy
+  c->its_T = 0;
+  if ((mask & DROPLET_PHYS_ENERGY) && !p.const_props) {
+    {
+    ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
+    ++g_launches, k_scalar_assemble<<<gc, TPB, 0, st>>>(g, p, 0, c->T, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2,
+                                          c->alpha, c->yq, p.T_amb, c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+    }
+    for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
+    bs.N = N;
+    cudaMemcpyAsync(c->bx, c->T, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
+    if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
+    c->its_T = ss.its;
+    cudaMemcpyAsync(c->T, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  }
+  // S6 species
+  ++g_launches, k_yeq<<<gc, TPB, 0, st>>>(g, p, c->T, c->yq, c->flags);
+  c->its_w = 0;
+  if (mask & DROPLET_PHYS_SPECIES) {
+    {
+    ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
+    ++g_launches, k_scalar_assemble<<<gc, TPB, 0, st>>>(g, p, 1, c->omega, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2,
+                                          c->alpha, c->yq, 0.0, c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+    }
+    for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
+    bs.N = N;
+    cudaMemcpyAsync(c->bx, c->omega, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
+    if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
+    c->its_w = ss.its;
+    cudaMemcpyAsync(c->omega, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  } else {
+    ++g_launches, k_species_noflow<<<gc, TPB, 0, st>>>(g, c->alpha, c->yq, c->omega);
+  }
+  ++g_launches, k_rhoG<<<gc, TPB, 0, st>>>(g, p, c->T, c->omega, c->rhoG);
+  // S7 - S10
+  c->its_u = 0;
+  c->its_p = 0;
+  if (mask & DROPLET_PHYS_FLOW) {
+    for (int cc = 0; cc < na; ++cc) {
+      int m[3] = {g.n[0], g.n[1], g.n[2]};
+      m[cc] -= 1;
+      long long nbx = (long long)m[0] * m[1] * m[2];
+      {
+      ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, st, (12.0 + 2 * na) * nbx * 8.0);
+      ++g_launches, k_mom_assemble<<<lin_grid(nbx), TPB, 0, st>>>(g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha,
+                                                    c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+      }
+      for (int a = 0; a < 3; ++a) bs.m[a] = m[a];
+      bs.N = nbx;
+      cudaMemsetAsync(c->bx, 0, sizeof(double) * nbx, st);
+      rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
+      if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
+      c->its_u += ss.its;
+      cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, st);
+      ++g_launches, k_mom_scatter<<<lin_grid(nfaces(g, cc)), TPB, 0, st>>>(g, p, cc, c->bx, c->us[cc]);
+    }
+    double* us2 = c->us[2] ? c->us[2] : c->us[0];
+    ++g_launches, k_poisson_assemble<<<gc, TPB, 0, st>>>(g, p, c->mdot, c->alpha, c->rhoG_old, c->rhoG, c->u[0], c->u[1], u2,
+                                           c->us[0], c->us[1], us2, c->rho, c->S, c->bD, c->bc[0], c->bc[1],
+                                           na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+    for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
+    bs.N = N;
+    cudaMemsetAsync(c->bx, 0, sizeof(double) * N, st);
+    rc = c->solver.pcg_mg(bs, c->cfg.cg_rtol, c->cfg.cg_maxit, c->cfg.precision == 1, &ss);
+    if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
+    c->its_p = ss.its;
+    c->res_p = ss.relres;
+    cudaMemcpyAsync(c->dp, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    for (int cc = 0; cc < na; ++cc)
+      ++g_launches, k_correct<<<lin_grid(nfaces(g, cc)), TPB, 0, st>>>(g, p, cc, c->us[cc], c->dp, c->rho, c->u[cc]);
+    ++g_launches, k_add<<<gc, TPB, 0, st>>>(N, c->pr, c->dp);
+  } else {
+    cudaMemsetAsync(c->dp, 0, sizeof(double) * N, st);
+    cudaMemsetAsync(c->S, 0, sizeof(double) * N, st);
+  }
+  // S11
+  if ((rc = run_diag(c))) return rc;
+  CKR(cudaGetLastError());
+  c->t += p.dt;
+  c->step += 1;
+  return 0;
+}
+
+extern "C" int droplet_step(droplet_ctx* c, int n_steps) {
+  if (!c || n_steps < 0) return DROPLET_ERR_ARG;
+  int nc = 0;
+  for (int s = 0; s < n_steps; ++s) {
+    int rc = one_step(c, &nc);
+    if (rc) return rc;
+  }
+  return nc ? DROPLET_ERR_NOT_CONVERGED : 0;
+}
+
+extern "C" int droplet_profile(droplet_ctx* c, int enable) {
+  if (!c) return DROPLET_ERR_ARG;
+  CKR(cudaStreamSynchronize(c->st));
+  if (enable) c->prof.reset();
+  c->prof.on = enable != 0;
+  return 0;
+}
+
+extern "C" int droplet_profile_read(droplet_ctx* c, int kclass, double* ms, long long* launches, double* bytes) {
+  if (!c || !ms || !launches || !bytes || kclass < 0 || kclass >= KC_COUNT) return DROPLET_ERR_ARG;
+  return c->prof.read(kclass, ms, launches, bytes);
+}
+
+extern "C" int droplet_launch_count(droplet_ctx* c, long long* launches) {
+  if (!c || !launches) return DROPLET_ERR_ARG;
+  *launches = g_launches;
+  return 0;
+}
+
+extern "C" int droplet_sync(droplet_ctx* c) {
+  if (!c) return DROPLET_ERR_ARG;
+  CKR(cudaStreamSynchronize(c->st));
+  return 0;
+}
+
+extern "C" int droplet_diag(droplet_ctx* c, int droplet, droplet_diag_t* out) {
+  if (!c || !out || droplet != 0) return DROPLET_ERR_ARG;
+  CKR(cudaMemcpyAsync(c->hscal, c->scal, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, c->st));
+  CKR(cudaMemcpyAsync(c->hflags, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+  CKR(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), c->st));
+  CKR(cudaStreamSynchronize(c->st));
+  const double* s = c->hscal;
+  double w = c->g.axisym ? 2.0 * M_PI : 1.0;
+  memset(out, 0, sizeof(*out));
+  out->t = c->t;
+  out->step = c->step;
+  out->V_l = w * s[SC_SUM_ALPHA_V];
+  out->d_eq = cbrt(6.0 * out->V_l / M_PI);
+  out->d2 = out->d_eq * out->d_eq;
+  out->mdot_tot = w * s[SC_SUM_MDOT_V];
+  out->K_norm = s[SC_K];
+  out->T_s_mean = s[SC_SUM_G] > 0.0 ? s[SC_SUM_TG] / s[SC_SUM_G] : 0.0;
+  out->M_liq = c->cfg.rho_l * out->V_l;
+  out->M_vap = w * s[SC_SUM_VAP];
+  out->vap_out_cum = w * s[SC_VAPOUT];
+  out->max_u = s[SC_MAXU];
+  out->alpha_min = s[SC_AMIN];
+  out->alpha_max = s[SC_AMAX];
+  out->clip_mass = w * s[SC_CLIP];
+  out->its_p = c->its_p; out->its_T = c->its_T; out->its_w = c->its_w; out->its_u = c->its_u;
+  out->res_p = c->res_p;
+  out->flags = *c->hflags;
+  if (!std::isfinite(out->V_l) || !std::isfinite(out->max_u) || !std::isfinite(out->T_s_mean)) return DROPLET_ERR_NONFINITE;
+  return 0;
+}
+
+static double* field_ptr(droplet_ctx* c, int id, long long* n, bool* writable) {
+  Geo& g = c->g;
+  *writable = false;
+  *n = g.N;
+  switch (id) {
+    case DROPLET_F_ALPHA: *writable = true; return c->alpha;
+    case DROPLET_F_T: *writable = true; return c->T;
+    case DROPLET_F_OMEGA: *writable = true; return c->omega;
+    case DROPLET_F_P: *writable = true; return c->pr;
+    case DROPLET_F_RHOG: *writable = true; return c->rhoG;
+    case DROPLET_F_MDOT: return c->mdot;
+    case DROPLET_F_MRAW: return c->mraw;
+    case DROPLET_F_ALPHA_STAR: return c->astar;
+    case DROPLET_F_DP: return c->dp;
+    case DROPLET_F_S: return c->S;
+    case DROPLET_F_RHOG_OLD: return c->rhoG_old;
+    case DROPLET_F_OMEGA_PINNED: return nullptr;
+    default: break;
+  }
+  int a = -1;
+  bool star = false;
+  if (id >= DROPLET_F_U0 && id <= DROPLET_F_U2) a = id - DROPLET_F_U0;
+  if (id >= DROPLET_F_USTAR0 && id <= DROPLET_F_USTAR2) { a = id - DROPLET_F_USTAR0; star = true; }
+  if (a < 0 || a >= nact(g)) return nullptr;
+  *n = nfaces(g, a);
+  *writable = !star;
+  return star ? c->us[a] : c->u[a];
+}
+
+extern "C" int droplet_field_size(droplet_ctx* c, int droplet, int field_id, size_t* n) {
+  if (!c || !n || droplet != 0) return DROPLET_ERR_ARG;
+  long long m;
+  bool w;
+  if (!field_ptr(c, field_id, &m, &w)) return DROPLET_ERR_ARG;
+  *n = (size_t)m;
+  return 0;
+}
+
+extern "C" int droplet_get_field(droplet_ctx* c, int droplet, int field_id, double* host, size_t n) {
+  if (!c || !host || droplet != 0) return DROPLET_ERR_ARG;
+  long long m;
+  bool w;
+  double* d = field_ptr(c, field_id, &m, &w);
+  if (!d) return DROPLET_ERR_ARG;
+  if ((size_t)m != n) return DROPLET_ERR_SIZE;
+  CKR(cudaMemcpyAsync(host, d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
+  CKR(cudaStreamSynchronize(c->st));
+  return 0;
+}
+
+extern "C" int droplet_set_field(droplet_ctx* c, int droplet, int field_id, const double* host, size_t n) {
+  if (!c || !host || droplet != 0) return DROPLET_ERR_ARG;
+  long long m;
+  bool w;
+  double* d = field_ptr(c, field_id, &m, &w);
+  if (!d || !w) return DROPLET_ERR_ARG;
+  if ((size_t)m != n) return DROPLET_ERR_SIZE;
+  CKR(cudaMemcpyAsync(d, host, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+  CKR(cudaStreamSynchronize(c->st));
+  return 0;
+}
+
+extern "C" void droplet_free(droplet_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  free_all(c);
+  delete c;
+}

@@ -1,0 +1,343 @@
+// Device-side definitions shared by the kernels of the droplet step:
+// grid geometry, boundary rules, thermodynamics and block reductions.
+//
+// Grid: uniform cells, cell (i, j, k) at linear index i + n0 (j + n1 k).
+// Axisymmetric runs (axisym = 1): axis 0 = r, axis 1 = z, n2 = 1, all
+// volumes and areas per radian.  A face array of direction a has n_a + 1
+// entries along a.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "droplet.h"
+
+namespace dg {
+
+enum { BC_AXIS = 0, BC_WALL = 1, BC_OPEN = 2, BC_FORCED = 3 };
+enum { R_ALPHA = 0, R_ZG = 1, R_TO = 2 };
+
+constexpr double R_GAS = 8.314462618;
+constexpr double P_ATM = 101325.0;
+constexpr double Y_CLAMP = 1.0 - 1e-6;
+constexpr double ALPHA_GAS = 1e-3;
+constexpr int RED_BLOCKS = 1216;       // 8 x 152 SMs: grid of the reduction kernels
+constexpr int TPB = 256;
+
+struct Geo {
+  int n[3];
+  int axisym;
+  int act3;          // 1 when axis 2 is active (3D)
+  int s;             // streamwise axis (gravity / inflow): 1 axisym, 2 in 3D
+  int bc[3][2];
+  double h[3];
+  double hmin;
+  long long N;       // number of cells
+};
+
+// Physical parameters used on the device (copied from droplet_config).
+struct Phys {
+  double D0, T_drop, T_amb, P, g[3], u_in, xc[3];
+  double Tb, Lv, M_l, rho_l, cp_l, k_l, mu_l, D_l;
+  double M_g, cp_g, cp_v, k_g, mu_g, D_g;
+  double Tc, Pc, om, Tc_g, Pc_g, om_g, kij;
+  double xi0, Df, dt, C_alpha, T_perturb;
+  double D_gas;        // D_g scaled to the operating pressure
+  double rhoG_const;   // frozen gas density of the constant-property check
+  unsigned long long seed;
+  int eq_model, const_props, physics;
+};
+
+__host__ __device__ inline int nact(const Geo& g) { return g.act3 ? 3 : 2; }
+
+__device__ __forceinline__ long long cidx(const Geo& g, int i, int j, int k) {
+  return (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k);
+}
+// face of direction a at integer face coords (i, j, k)
+__device__ __forceinline__ long long fidx(const Geo& g, int a, int i, int j, int k) {
+  long long f0 = g.n[0] + (a == 0), f1 = g.n[1] + (a == 1);
+  return (long long)i + f0 * ((long long)j + f1 * k);
+}
+__host__ __device__ inline long long nfaces(const Geo& g, int a) {
+  return (long long)(g.n[0] + (a == 0)) * (g.n[1] + (a == 1)) * (g.n[2] + (a == 2));
+}
+__device__ __forceinline__ void decomp(long long id, int n0, int n1, int& i, int& j, int& k) {
+  i = (int)(id % n0);
+  long long t = id / n0;
+  j = (int)(t % n1);
+  k = (int)(t / n1);
+}
+
+__device__ __forceinline__ double rc(const Geo& g, int i) { return (i + 0.5) * g.h[0]; }
+__device__ __forceinline__ double cellV(const Geo& g, int i) {
+  return g.axisym ? rc(g, i) * g.h[0] * g.h[1] : g.h[0] * g.h[1] * g.h[2];
+}
+// area of the face of direction a whose low-side cell index along 0 is i
+// (for a = 0, i is the face index)
+__device__ __forceinline__ double faceA(const Geo& g, int a, int i) {
+  if (g.axisym) return a == 0 ? (i * g.h[0]) * g.h[1] : rc(g, i) * g.h[0];
+  return g.h[0] * g.h[1] * g.h[2] / g.h[a];
+}
+// area of a face normal to a located at radial coordinate rl (control volumes of the momentum)
+__device__ __forceinline__ double areaN(const Geo& g, int a, double rl) {
+  if (g.axisym) return rl * (a == 0 ? g.h[1] : g.h[0]);
+  return g.h[0] * g.h[1] * g.h[2] / g.h[a];
+}
+
+// ------------------------------------------------------------------ ghosts
+// Cell field value with at most one index outside the domain (by 1 or 2).
+//   R_ALPHA: mirror at the axis, 0 outside other boundaries
+//   R_ZG   : zero gradient (mirror at the axis)
+//   R_TO   : T / omega: axis mirror, wall zero gradient, forced inlet fixed amb,
+//            open boundary inletOutlet (fixed amb where the boundary face
+//            velocity points inward, zero gradient otherwise)
+// A fixed face value amb gives the ghost 2 amb - phi_b.
+__device__ inline double cellg(const Geo& g, const double* f, int i, int j, int k, int rule, double amb,
+                               const double* u0, const double* u1, const double* u2) {
+  int q[3] = {i, j, k};
+  for (int a = 0; a < 3; ++a) {
+    if (q[a] < 0 || q[a] >= g.n[a]) {
+      int side = q[a] < 0 ? 0 : 1;
+      q[a] = side ? g.n[a] - 1 : 0;
+      double vb = f[cidx(g, q[0], q[1], q[2])];
+      int kind = g.bc[a][side];
+      if (rule == R_ALPHA) return kind == BC_AXIS ? vb : 0.0;
+      if (rule == R_ZG) return vb;
+      if (kind == BC_AXIS || kind == BC_WALL) return vb;
+      if (kind == BC_FORCED) return 2.0 * amb - vb;
+      int fq[3] = {q[0], q[1], q[2]};
+      fq[a] = side ? g.n[a] : 0;
+      const double* ua = a == 0 ? u0 : (a == 1 ? u1 : u2);
+      double un = ua[fidx(g, a, fq[0], fq[1], fq[2])];
+      double vout = side ? un : -un;
+      return vout < 0.0 ? 2.0 * amb - vb : vb;
+    }
+  }
+  return f[cidx(g, q[0], q[1], q[2])];
+}
+
+// Face velocity of direction c with at most one index outside its array
+// (by 1 or 2).  Own axis, beyond the boundary face value u_b: axis / wall /
+// forced inlet give u(-k) = 2 u_b - u(k); open boundary u(-k) = u_b.
+// Tangential axis beyond the boundary cells: wall / forced inlet u(-k) =
+// -u(k-1); axis u(-k) = u(k-1); open u(-k) = u(0).
+__device__ inline double ufg(const Geo& g, const double* uc, int c, int i, int j, int k) {
+  int q[3] = {i, j, k};
+  int m[3] = {g.n[0] + (c == 0), g.n[1] + (c == 1), g.n[2] + (c == 2)};
+  for (int a = 0; a < 3; ++a) {
+    if (q[a] < 0 || q[a] >= m[a]) {
+      int side = q[a] < 0 ? 0 : 1;
+      int kind = g.bc[a][side];
+      int kk = side ? q[a] - (m[a] - 1) : -q[a];          // 1 or 2
+      int qb[3] = {q[0], q[1], q[2]};
+      if (a == c) {
+        qb[a] = side ? m[a] - 1 : 0;
+        double ub = uc[fidx(g, c, qb[0], qb[1], qb[2])];
+        if (kind == BC_OPEN) return ub;
+        qb[a] = side ? m[a] - 1 - kk : kk;
+        return 2.0 * ub - uc[fidx(g, c, qb[0], qb[1], qb[2])];
+      } else {
+        if (kind == BC_OPEN) {
+          qb[a] = side ? m[a] - 1 : 0;
+          return uc[fidx(g, c, qb[0], qb[1], qb[2])];
+        }
+        qb[a] = side ? m[a] - kk : kk - 1;
+        double v = uc[fidx(g, c, qb[0], qb[1], qb[2])];
+        return kind == BC_AXIS ? v : -v;
+      }
+    }
+  }
+  return uc[fidx(g, c, q[0], q[1], q[2])];
+}
+
+// clamp a cell index into the domain (zero-gradient access)
+__device__ __forceinline__ double cellc(const Geo& g, const double* f, int i, int j, int k) {
+  i = i < 0 ? 0 : (i >= g.n[0] ? g.n[0] - 1 : i);
+  j = j < 0 ? 0 : (j >= g.n[1] ? g.n[1] - 1 : j);
+  k = k < 0 ? 0 : (k >= g.n[2] ? g.n[2] - 1 : k);
+  return f[cidx(g, i, j, k)];
+}
+
+// ------------------------------------------------------------------ small formulas
+__device__ __forceinline__ double minmod(double x, double y) {
+  return (x * y > 0.0) ? (x > 0.0 ? fmin(fabs(x), fabs(y)) : -fmin(fabs(x), fabs(y))) : 0.0;
+}
+__device__ __forceinline__ double lim_up(double uu, double u, double d) { return u + 0.5 * minmod(u - uu, d - u); }
+__device__ __forceinline__ double van_leer(double uu, double u, double d) {
+  double dU = u - uu, dD = d - u, pr = dU * dD;
+  return u + (pr > 0.0 ? pr / (dU + dD) : 0.0);
+}
+
+// ------------------------------------------------------------------ thermodynamics
+__device__ __forceinline__ double psat(const Phys& p, double T) {
+  return P_ATM * exp((p.Lv * p.M_l / R_GAS) * (1.0 / p.Tb - 1.0 / T));
+}
+__device__ __forceinline__ double Y_from_y(const Phys& p, double y) {
+  return y * p.M_l / (y * p.M_l + (1.0 - y) * p.M_g);
+}
+__device__ __forceinline__ double y_from_Y(const Phys& p, double Y) {
+  return (Y / p.M_l) / (Y / p.M_l + (1.0 - Y) / p.M_g);
+}
+
+__device__ inline void pr_pure(double T, double Tc, double Pc, double om, double& a, double& b) {
+  double kappa = 0.37464 + 1.54226 * om - 0.26992 * om * om;
+  double sq = 1.0 + kappa * (1.0 - sqrt(T / Tc));
+  a = 0.45724 * R_GAS * R_GAS * Tc * Tc / Pc * sq * sq;
+  b = 0.07780 * R_GAS * Tc / Pc;
+}
+
+// largest real root of z^3 + c2 z^2 + c1 z + c0 (Cardano; trigonometric form for three real roots)
+__device__ inline double cubic_largest(double c2, double c1, double c0) {
+  double p = c1 - c2 * c2 / 3.0;
+  double q = 2.0 * c2 * c2 * c2 / 27.0 - c2 * c1 / 3.0 + c0;
+  double disc = 0.25 * q * q + p * p * p / 27.0;
+  double t;
+  if (disc > 0.0) {
+    double h = -0.5 * q;
+    double w = h + copysign(sqrt(disc), h);
+    double u = copysign(cbrt(fabs(w)), w);
+    t = (u != 0.0) ? u - p / (3.0 * u) : 0.0;
+  } else if (p == 0.0) {
+    t = 0.0;
+  } else {
+    double m = 2.0 * sqrt(-p / 3.0);
+    double arg = 3.0 * q / (p * m);
+    arg = fmin(1.0, fmax(-1.0, arg));
+    t = m * cos(acos(arg) / 3.0);
+  }
+  return t - c2 / 3.0;
+}
+
+// binary (fuel, inert) Peng-Robinson: vapour Z and ln phi_hat of the fuel at mole fraction y
+__device__ inline void pr_binary(const Phys& p, double T, double P, double y, double& Z, double& lnphi0) {
+  double a0, b0, a1, b1;
+  pr_pure(T, p.Tc, p.Pc, p.om, a0, b0);
+  pr_pure(T, p.Tc_g, p.Pc_g, p.om_g, a1, b1);
+  double a01 = sqrt(a0 * a1) * (1.0 - p.kij);
+  double y1 = 1.0 - y;
+  double am = y * y * a0 + y * y1 * a01 + y1 * y * a01 + y1 * y1 * a1;
+  double bm = y * b0 + y1 * b1;
+  double RT = R_GAS * T;
+  double A = am * P / (RT * RT);
+  double B = bm * P / RT;
+  Z = cubic_largest(-(1.0 - B), A - 3.0 * B * B - 2.0 * B, -(A * B - B * B - B * B * B));
+  const double s2 = 1.4142135623730951;
+  double logterm = log((Z + (1.0 + s2) * B) / (Z + (1.0 - s2) * B));
+  double sa = y * a0 + y1 * a01;
+  lnphi0 = b0 / bm * (Z - 1.0) - log(Z - B) - A / (2.0 * s2 * B) * (2.0 * sa / am - b0 / bm) * logterm;
+}
+
+// saturation mole fraction (Raoult, or the Peng-Robinson fixed point with the Poynting factor)
+__device__ inline double y_eq(const Phys& p, double T, unsigned* boil) {
+  double p0 = psat(p, T);
+  double y = p0 / p.P;
+  if (y > Y_CLAMP) { y = Y_CLAMP; if (boil) *boil = 1u; }
+  if (p.eq_model == 0) return y;
+  double Zp, lp;
+  pr_binary(p, T, p0, 1.0, Zp, lp);
+  double vL = p.M_l / p.rho_l;
+  double num = p0 * exp(lp) * exp(vL * (p.P - p0) / (R_GAS * T));
+  for (int it = 0; it < 50; ++it) {
+    double Z, l0;
+    pr_binary(p, T, p.P, y, Z, l0);
+    double yn = num / (p.P * exp(l0));
+    if (yn > Y_CLAMP) { yn = Y_CLAMP; if (boil) *boil = 1u; }
+    double dy = fabs(yn - y);
+    y = yn;
+    if (dy < 1e-13) break;
+  }
+  return y;
+}
+
+__device__ __forceinline__ double Y_eq(const Phys& p, double T, unsigned* boil) { return Y_from_y(p, y_eq(p, T, boil)); }
+
+__device__ inline double rho_gas(const Phys& p, double T, double Y) {
+  if (p.const_props) return p.rhoG_const;
+  double inv_m = Y / p.M_l + (1.0 - Y) / p.M_g;
+  double Z = 1.0;
+  if (p.eq_model != 0) {
+    double l0;
+    pr_binary(p, T, p.P, y_from_Y(p, Y), Z, l0);
+  }
+  return p.P / (Z * R_GAS * T * inv_m);
+}
+
+// ------------------------------------------------------------------ reductions
+// Block-level sums of NV values, written to partials[v * gridDim.x + blockIdx.x].
+template <int NV>
+__device__ inline void block_sum_store(double (&v)[NV], double* partials) {
+  __shared__ double sh[NV][TPB / 32];
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double t = lane < (int)(blockDim.x >> 5) ? sh[q][lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (lane == 0) partials[q * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+template <int NV>
+__device__ inline void block_max_store(double (&v)[NV], double* partials) {
+  __shared__ double sh[NV][TPB / 32];
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+    for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double t = lane < (int)(blockDim.x >> 5) ? sh[q][lane] : -1e300;
+      for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+      if (lane == 0) partials[q * gridDim.x + blockIdx.x] = t;
+    }
+  }
+}
+
+// Single-block sum of nblk partials per value (fixed order: deterministic).
+__device__ inline double block_sum_partials(const double* part, int nblk) {
+  __shared__ double sh[TPB / 32];
+  double t = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) t += part[b];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = t;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r += sh[q];
+  return r;   // valid in thread 0
+}
+__device__ inline double block_max_partials(const double* part, int nblk) {
+  __shared__ double sh[TPB / 32];
+  double t = -1e300;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) t = fmax(t, part[b]);
+  for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = t;
+  __syncthreads();
+  double r = -1e300;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r = fmax(r, sh[q]);
+  return r;
+}
+
+inline int red_grid(long long n) {
+  long long b = (n + TPB - 1) / TPB;
+  return (int)(b < RED_BLOCKS ? (b < 1 ? 1 : b) : RED_BLOCKS);
+}
+inline int lin_grid(long long n) { return (int)((n + TPB - 1) / TPB); }
+
+}  // namespace dg

@@ -1,0 +1,147 @@
+// Declarations shared by the translation units of the droplet library.
+#pragma once
+#include "common.cuh"
+
+#include <vector>
+
+namespace dg {
+
+// launches issued by the library in this process
+extern long long g_launches;
+
+enum { KC_MG_SMOOTH = 0, KC_SPMV, KC_UPDATE, KC_MG_RESTRICT, KC_MG_PROLONG, KC_MOM_ASSEMBLE, KC_SCALAR_ASSEMBLE, KC_COUNT };
+
+// Optional CUDA-event timing of the kernel classes above (per context).
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> kind;        // kernel class of each recorded pair
+  size_t used = 0;              // event pairs in use
+  double bytes[KC_COUNT] = {0};
+  long long n[KC_COUNT] = {0};
+  int begin(int k, cudaStream_t st, double b);
+  void end(int idx, cudaStream_t st);
+  void reset();
+  int read(int k, double* ms, long long* launches, double* bytes_total);
+  void destroy();
+};
+
+struct ProfScope {
+  Prof* p;
+  cudaStream_t st;
+  int idx;
+  ProfScope(Prof* p_, int k, cudaStream_t st_, double b) : p(p_), st(st_), idx(-1) {
+    if (p && p->on) idx = p->begin(k, st, b);
+  }
+  ~ProfScope() {
+    if (idx >= 0) p->end(idx, st);
+  }
+};
+
+// indices of the per-droplet device scalar array
+enum {
+  SC_K = 0, SC_CLIP, SC_VAPOUT, SC_DT,
+  SC_SUM_ALPHA_V, SC_SUM_MDOT_V, SC_SUM_TG, SC_SUM_G, SC_SUM_VAP, SC_MAXU, SC_AMAX, SC_AMIN,
+  SC_COUNT
+};
+
+// ---- step kernels (step_kernels.cu)
+__global__ void k_init(Geo g, Phys p, double* alpha, double* T, double* omega, double* rhoG);
+__global__ void k_thermo_pin(Geo g, Phys p, const double* alpha, const double* T, double* omega, double* rhoG_old,
+                             unsigned* flags);
+__global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG,
+                           const double* u0, const double* u1, const double* u2, double* mraw, int* adj,
+                           double* partials, unsigned* flags);
+__global__ void k_evap_K(const double* partials, int nblk, double* scal, unsigned* flags);
+__global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double* mraw, const double* scal,
+                               double* mdot, double* alpha_star, unsigned* flags);
+__global__ void k_adv_faces(Geo g, Phys p, int a, const double* as, const double* ua, double* FL, double* AF);
+__global__ void k_adv_low(Geo g, const double* as, const double* F0, const double* F1, const double* F2, double* aL);
+__global__ void k_adv_limit(Geo g, const double* as, const double* aL, const double* A0, const double* A1,
+                            const double* A2, double* Rp, double* Rm);
+__global__ void k_adv_update(Geo g, const double* aL, const double* A0, const double* A1, const double* A2,
+                             const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags);
+__global__ void k_clip_finish(const double* partials, int nblk, double* scal, unsigned* flags);
+__global__ void k_alpha_clip_only(Geo g, const double* as, double* alpha, double* partials);
+__global__ void k_props(Geo g, Phys p, const double* alpha, const double* rhoG, const double* omega, double* rho,
+                        double* mu, double* kc, double* cp, double* D);
+__global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
+                                  const double* kc, const double* D, const double* mdot, const double* u0,
+                                  const double* u1, const double* u2, const double* alpha_new, const double* pinv,
+                                  double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs);
+__global__ void k_yeq(Geo g, Phys p, const double* T, double* yq, unsigned* flags);
+__global__ void k_species_noflow(Geo g, const double* alpha_new, const double* yq, double* omega);
+__global__ void k_rhoG(Geo g, Phys p, const double* T, const double* w, double* rhoG);
+__global__ void k_mom_assemble(Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2,
+                               const double* rho, const double* mu, const double* pr, const double* alpha,
+                               double* Dg, double* c0, double* c1, double* c2, double* rhs);
+__global__ void k_mom_scatter(Geo g, Phys p, int c, const double* x, double* us);
+__global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo,
+                                   const double* rgn, const double* u0, const double* u1, const double* u2,
+                                   const double* us0, const double* us1, const double* us2, const double* rho,
+                                   double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs);
+__global__ void k_correct(Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u);
+__global__ void k_add(long long n, double* y, const double* x);
+__global__ void k_diag(Geo g, const double* alpha, const double* T, const double* mdot, const double* omega,
+                       const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum,
+                       double* pmax);
+__global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal);
+
+// ---- linear solvers (solver.cu)
+// Box operator on dims m: y_P = D_P x_P + sum_a [c_a[P](x_P - x_{P-e_a}) + c_a[P+e_a](x_P - x_{P+e_a})],
+// the coupling of a pair stored at its high cell (c_a[P] = 0 when P_a = 0).
+struct BoxSys {
+  int m[3];
+  long long N;
+  double* D;
+  double* c[3];     // c[2] may be null (2D)
+  double* b;
+  double* x;
+};
+
+struct SolveStats {
+  int its;
+  double relres;
+  int converged;
+};
+
+struct MGLevel {
+  int m[3];
+  long long N;
+  void* D;          // float or double per precision
+  void* c[3];
+  void* x;
+  void* b;
+};
+
+class Solver {
+ public:
+  // workspace sized for boxes of up to maxN unknowns
+  int setup(long long maxN, cudaStream_t st);
+  void release();
+  // Jacobi-preconditioned CG; x holds the initial guess and receives the solution
+  int pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out);
+  // multigrid-preconditioned CG on the pressure box (hierarchy built from s)
+  int pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats* out);
+  cudaStream_t stream = nullptr;
+  Prof* prof = nullptr;
+
+ private:
+  int build_mg(const BoxSys& s, int fp32);
+  void vcycle(int fp32);
+  long long cap = 0;
+  double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *idg = nullptr;
+  double* part = nullptr;       // reduction partials
+  double* sc = nullptr;         // device scalars
+  int* done = nullptr;
+  double* hsc = nullptr;        // pinned host copy of the scalars
+  // multigrid
+  int nlev = 0;
+  MGLevel lev[24];
+  void* mgbuf = nullptr;
+  size_t mgbytes = 0;
+  int mg_fp32 = -1;
+  int mg_m[3] = {0, 0, 0};
+};
+
+}  // namespace dg

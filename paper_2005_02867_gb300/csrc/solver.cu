@@ -1,0 +1,604 @@
+// Linear solvers of the step: Jacobi-preconditioned CG for the energy,
+// species and momentum systems, and CG preconditioned by a symmetric
+// geometric multigrid V-cycle for the variable-density pressure equation
+// (Eq. pequation).  Dot products and the CG scalars are FP64; the multigrid
+// hierarchy is FP64 or FP32.  Convergence is tested on the device: every
+// kernel of an iteration returns at once when the done flag is set, so the
+// host only reads the status every few iterations.
+#include <cstdio>
+#include <cstring>
+#include "kernels.h"
+
+namespace dg {
+
+enum { S_RZ = 0, S_PAP, S_RR, S_BB, S_ALPHA, S_BETA, S_ITS, S_TOL2, S_MAXIT, S_COUNT };
+
+// done flag values: 0 running, 1 converged, 2 stopped at the iteration cap
+
+struct BoxV {
+  int m[3];
+  long long N;
+  const double* D;
+  const double* c[3];
+};
+
+__device__ __forceinline__ void bdecomp(const int m[3], long long id, int& i, int& j, int& k) {
+  i = (int)(id % m[0]);
+  long long t = id / m[0];
+  j = (int)(t % m[1]);
+  k = (int)(t / m[1]);
+}
+
+// y = A x at cell id, and the total diagonal D + sum of adjacent couplings
+template <typename T, typename TX>
+__device__ __forceinline__ void box_row(const int m[3], const T* D, const T* const c[3], const TX* x, long long id,
+                                        int i, int j, int k, double& ax, double& dtot) {
+  double xp = (double)x[id];
+  double y = (double)D[id] * xp;
+  double dt = (double)D[id];
+  int q[3] = {i, j, k};
+  long long st[3] = {1, (long long)m[0], (long long)m[0] * m[1]};
+  for (int a = 0; a < 3; ++a) {
+    if (!c[a] || m[a] < 2) continue;
+    if (q[a] > 0) {
+      double cl = (double)c[a][id];
+      y += cl * (xp - (double)x[id - st[a]]);
+      dt += cl;
+    }
+    if (q[a] < m[a] - 1) {
+      double ch = (double)c[a][id + st[a]];
+      y += ch * (xp - (double)x[id + st[a]]);
+      dt += ch;
+    }
+  }
+  ax = y;
+  dtot = dt;
+}
+
+// ---------------------------------------------------------------- CG kernels
+__global__ void k_pcg_init(BoxV A, const double* b, const double* x, double* r, double* z, double* p, double* idg,
+                           int jacobi, double* part) {
+  double acc[3] = {0, 0, 0};   // r.z, b.b, r.r
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < A.N; id += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    bdecomp(A.m, id, i, j, k);
+    double ax, dt;
+    box_row<double, double>(A.m, A.D, A.c, x, id, i, j, k, ax, dt);
+    double rr = b[id] - ax;
+    r[id] = rr;
+    double bb = b[id];
+    acc[1] += bb * bb;
+    acc[2] += rr * rr;
+    if (jacobi) {
+      double iv = 1.0 / dt;
+      idg[id] = iv;
+      double zz = iv * rr;
+      z[id] = zz;
+      p[id] = zz;
+      acc[0] += rr * zz;
+    }
+  }
+  block_sum_store<3>(acc, part);
+}
+
+__global__ void k_fin_init(const double* part, int nblk, double* sc, int* done, double tol2, int maxit) {
+  double rz = block_sum_partials(part, nblk);
+  __syncthreads();
+  double bb = block_sum_partials(part + nblk, nblk);
+  __syncthreads();
+  double rr = block_sum_partials(part + 2 * nblk, nblk);
+  if (threadIdx.x == 0) {
+    sc[S_RZ] = rz;
+    sc[S_BB] = bb;
+    sc[S_RR] = rr;
+    sc[S_ITS] = 0.0;
+    sc[S_TOL2] = tol2;
+    sc[S_MAXIT] = (double)maxit;
+    *done = (bb == 0.0 || rr <= tol2 * bb) ? 1 : 0;
+  }
+}
+
+__global__ void k_spmv_dot(BoxV A, const double* p, double* Ap, double* part, const int* done) {
+  if (*done) return;
+  double acc[1] = {0.0};
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < A.N; id += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    bdecomp(A.m, id, i, j, k);
+    double ax, dt;
+    box_row<double, double>(A.m, A.D, A.c, p, id, i, j, k, ax, dt);
+    Ap[id] = ax;
+    acc[0] += p[id] * ax;
+  }
+  block_sum_store<1>(acc, part);
+}
+
+__global__ void k_fin_alpha(const double* part, int nblk, double* sc, const int* done) {
+  if (*done) return;
+  double pap = block_sum_partials(part, nblk);
+  if (threadIdx.x == 0) {
+    sc[S_PAP] = pap;
+    sc[S_ALPHA] = sc[S_RZ] / pap;
+  }
+}
+
+// x += alpha p, r -= alpha Ap; Jacobi: z = r / diag and r.z; both: r.r
+__global__ void k_update(long long N, double* x, double* r, const double* p, const double* Ap, const double* idg,
+                         double* z, int jacobi, const double* sc, double* part, const int* done) {
+  if (*done) return;
+  double al = sc[S_ALPHA];
+  double acc[2] = {0, 0};
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N; id += (long long)gridDim.x * blockDim.x) {
+    x[id] += al * p[id];
+    double rr = r[id] - al * Ap[id];
+    r[id] = rr;
+    acc[1] += rr * rr;
+    if (jacobi) {
+      double zz = idg[id] * rr;
+      z[id] = zz;
+      acc[0] += rr * zz;
+    }
+  }
+  block_sum_store<2>(acc, part);
+}
+
+// iteration count, convergence test, and (Jacobi) beta
+__global__ void k_fin_iter(const double* part, int nblk, double* sc, int* done, int jacobi) {
+  if (*done) return;
+  double rz = block_sum_partials(part, nblk);
+  __syncthreads();
+  double rr = block_sum_partials(part + nblk, nblk);
+  if (threadIdx.x == 0) {
+    sc[S_ITS] += 1.0;
+    sc[S_RR] = rr;
+    if (rr <= sc[S_TOL2] * sc[S_BB]) *done = 1;
+    else if (sc[S_ITS] >= sc[S_MAXIT]) *done = 2;
+    if (jacobi) {
+      sc[S_BETA] = rz / sc[S_RZ];
+      sc[S_RZ] = rz;
+    }
+  }
+}
+
+__global__ void k_dot_rz(long long N, const double* r, const double* z, double* part, const int* done) {
+  if (*done) return;
+  double acc[1] = {0.0};
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N; id += (long long)gridDim.x * blockDim.x)
+    acc[0] += r[id] * z[id];
+  block_sum_store<1>(acc, part);
+}
+
+// beta = rz_new / rz (first == 1: only store rz)
+__global__ void k_fin_rz(const double* part, int nblk, double* sc, const int* done, int first) {
+  if (*done) return;
+  double rz = block_sum_partials(part, nblk);
+  if (threadIdx.x == 0) {
+    sc[S_BETA] = first ? 0.0 : rz / sc[S_RZ];
+    sc[S_RZ] = rz;
+  }
+}
+
+__global__ void k_p_update(long long N, double* p, const double* z, const double* sc, const int* done) {
+  if (*done) return;
+  double be = sc[S_BETA];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N; id += (long long)gridDim.x * blockDim.x)
+    p[id] = z[id] + be * p[id];
+}
+
+// ---------------------------------------------------------------- multigrid kernels
+template <typename T>
+struct LevV {
+  int m[3];
+  long long N;
+  const T* D;
+  const T* c[3];
+  T* x;
+  const T* b;
+};
+
+// red-black Gauss-Seidel half sweep of colour `col`; first = 1: neighbours taken as 0
+template <typename T>
+__global__ void k_mg_smooth(LevV<T> L, int col, int first, const int* done) {
+  if (*done) return;
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= L.N) return;
+  int i, j, k;
+  bdecomp(L.m, id, i, j, k);
+  if (((i + j + k) & 1) != col) return;
+  long long st[3] = {1, (long long)L.m[0], (long long)L.m[0] * L.m[1]};
+  int q[3] = {i, j, k};
+  double s = (double)L.b[id];
+  double dt = (double)L.D[id];
+  for (int a = 0; a < 3; ++a) {
+    if (!L.c[a] || L.m[a] < 2) continue;
+    if (q[a] > 0) {
+      double cl = (double)L.c[a][id];
+      dt += cl;
+      if (!first) s += cl * (double)L.x[id - st[a]];
+    }
+    if (q[a] < L.m[a] - 1) {
+      double ch = (double)L.c[a][id + st[a]];
+      dt += ch;
+      if (!first) s += ch * (double)L.x[id + st[a]];
+    }
+  }
+  L.x[id] = (T)(s / dt);
+}
+
+// residual of the fine level restricted (summed) into the coarse right-hand side
+template <typename T>
+__global__ void k_mg_restrict(LevV<T> F, LevV<T> C, const int* done) {
+  if (*done) return;
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= C.N) return;
+  int I, J, K;
+  bdecomp(C.m, id, I, J, K);
+  int kz = F.m[2] > 1 ? 2 : 1;
+  double s = 0.0;
+  for (int dk = 0; dk < kz; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        int i = 2 * I + di, j = 2 * J + dj, k = kz == 2 ? 2 * K + dk : 0;
+        long long fi = (long long)i + (long long)F.m[0] * ((long long)j + (long long)F.m[1] * k);
+        double ax, dt;
+        box_row<T, T>(F.m, F.D, F.c, F.x, fi, i, j, k, ax, dt);
+        s += (double)F.b[fi] - ax;
+      }
+  ((T*)C.b)[id] = (T)s;
+}
+
+template <typename T>
+__global__ void k_mg_prolong(LevV<T> F, LevV<T> C, const int* done) {
+  if (*done) return;
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= F.N) return;
+  int i, j, k;
+  bdecomp(F.m, id, i, j, k);
+  int K = F.m[2] > 1 ? k / 2 : 0;
+  long long ci = (long long)(i / 2) + (long long)C.m[0] * ((long long)(j / 2) + (long long)C.m[1] * K);
+  F.x[id] = (T)((double)F.x[id] + (double)C.x[ci]);
+}
+
+// coarse operator: couplings = 1/2 sum of the fine couplings across the coarse face, D = 1/2 sum
+template <typename T>
+__global__ void k_mg_coarsen(LevV<T> F, LevV<T> C, T* Dc, T* c0, T* c1, T* c2) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= C.N) return;
+  int I, J, K;
+  bdecomp(C.m, id, I, J, K);
+  int kz = F.m[2] > 1 ? 2 : 1;
+  double d = 0.0, s[3] = {0, 0, 0};
+  T* cc[3] = {c0, c1, c2};
+  for (int dk = 0; dk < kz; ++dk)
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        int i = 2 * I + di, j = 2 * J + dj, k = kz == 2 ? 2 * K + dk : 0;
+        long long fi = (long long)i + (long long)F.m[0] * ((long long)j + (long long)F.m[1] * k);
+        d += (double)F.D[fi];
+        if (di == 0) s[0] += (double)F.c[0][fi];
+        if (dj == 0) s[1] += (double)F.c[1][fi];
+        if (kz == 2 && dk == 0) s[2] += (double)F.c[2][fi];
+      }
+  Dc[id] = (T)(0.5 * d);
+  for (int a = 0; a < 3; ++a)
+    if (cc[a]) cc[a][id] = (T)(0.5 * s[a]);
+}
+
+template <typename TO, typename TI>
+__global__ void k_cast(long long n, TO* y, const TI* x) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id < n) y[id] = (TO)x[id];
+}
+template <typename TO, typename TI>
+__global__ void k_cast_done(long long n, TO* y, const TI* x, const int* done) {
+  if (*done) return;
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id < n) y[id] = (TO)x[id];
+}
+
+// ---------------------------------------------------------------- host side
+long long g_launches = 0;
+
+int Prof::begin(int k, cudaStream_t st, double b) {
+  if (2 * (used + 1) > pool.size()) {
+    for (int q = 0; q < 256; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      pool.push_back(e);
+    }
+  }
+  int idx = (int)used++;
+  if ((int)kind.size() < (int)used) kind.resize(used);
+  kind[idx] = k;
+  bytes[k] += b;
+  n[k] += 1;
+  cudaEventRecord(pool[2 * idx], st);
+  return idx;
+}
+
+void Prof::end(int idx, cudaStream_t st) { cudaEventRecord(pool[2 * idx + 1], st); }
+
+void Prof::reset() {
+  used = 0;
+  for (int k = 0; k < KC_COUNT; ++k) { bytes[k] = 0.0; n[k] = 0; }
+}
+
+int Prof::read(int k, double* ms, long long* launches, double* bytes_total) {
+  double tot = 0.0;
+  for (size_t i = 0; i < used; ++i) {
+    if (kind[i] != k) continue;
+    float t = 0.f;
+    if (cudaEventSynchronize(pool[2 * i + 1]) != cudaSuccess) return DROPLET_ERR_CUDA;
+    if (cudaEventElapsedTime(&t, pool[2 * i], pool[2 * i + 1]) != cudaSuccess) return DROPLET_ERR_CUDA;
+    tot += t;
+  }
+  *ms = tot;
+  *launches = n[k];
+  *bytes_total = bytes[k];
+  return 0;
+}
+
+void Prof::destroy() {
+  for (auto e : pool) cudaEventDestroy(e);
+  pool.clear();
+  kind.clear();
+  used = 0;
+}
+#define CK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { fprintf(stderr, "droplet: %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); return DROPLET_ERR_CUDA; } } while (0)
+
+int Solver::setup(long long maxN, cudaStream_t s) {
+  stream = s;
+  cap = maxN;
+  size_t b = sizeof(double) * (size_t)maxN;
+  CK(cudaMalloc(&r, b));
+  CK(cudaMalloc(&z, b));
+  CK(cudaMalloc(&p, b));
+  CK(cudaMalloc(&Ap, b));
+  CK(cudaMalloc(&idg, b));
+  CK(cudaMalloc(&part, sizeof(double) * RED_BLOCKS * 8));
+  CK(cudaMalloc(&sc, sizeof(double) * S_COUNT));
+  CK(cudaMalloc(&done, sizeof(int)));
+  CK(cudaMallocHost(&hsc, sizeof(double) * (S_COUNT + 2)));
+  return 0;
+}
+
+void Solver::release() {
+  cudaFree(r); cudaFree(z); cudaFree(p); cudaFree(Ap); cudaFree(idg);
+  cudaFree(part); cudaFree(sc); cudaFree(done); cudaFreeHost(hsc);
+  cudaFree(mgbuf);
+  r = z = p = Ap = idg = part = sc = nullptr;
+  done = nullptr; hsc = nullptr; mgbuf = nullptr;
+}
+
+static BoxV view(const BoxSys& s) {
+  BoxV v;
+  for (int a = 0; a < 3; ++a) { v.m[a] = s.m[a]; v.c[a] = s.c[a]; }
+  v.N = s.N;
+  v.D = s.D;
+  return v;
+}
+
+// read the device status; returns 1 when the solve stopped (converged or capped)
+static int poll(double* hsc, const double* sc, const int* done, cudaStream_t st, int maxit, int* conv) {
+  cudaMemcpyAsync(hsc, sc, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(hsc + S_COUNT, done, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaStreamSynchronize(st);
+  int d = *(int*)(hsc + S_COUNT);
+  *conv = d == 1;
+  return d != 0 || (int)hsc[S_ITS] >= maxit;
+}
+
+static void fill_stats(const double* hsc, int conv, SolveStats* out) {
+  if (!out) return;
+  out->its = (int)hsc[S_ITS];
+  out->relres = hsc[S_BB] > 0 ? sqrt(hsc[S_RR] / hsc[S_BB]) : 0.0;
+  out->converged = conv;
+}
+
+int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
+  BoxV A = view(s);
+  int nb = red_grid(s.N);
+  ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 1, part);
+  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);
+  const int chunk = 8;
+  int conv = 0;
+  for (int it = 0; it < maxit; it += chunk) {
+    for (int q = 0; q < chunk; ++q) {
+      {
+        ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0);
+        ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done);
+      }
+      ++g_launches, k_fin_alpha<<<1, TPB, 0, stream>>>(part, nb, sc, done);
+      {
+        ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0);
+        ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 1, sc, part, done);
+      }
+      ++g_launches, k_fin_iter<<<1, TPB, 0, stream>>>(part, nb, sc, done, 1);
+      ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
+    }
+    CK(cudaGetLastError());
+    if (poll(hsc, sc, done, stream, maxit, &conv)) break;
+  }
+  if (!conv) poll(hsc, sc, done, stream, maxit, &conv);
+  fill_stats(hsc, conv, out);
+  return conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------- multigrid setup / cycle
+template <typename T>
+static LevV<T> lv(const MGLevel& L) {
+  LevV<T> v;
+  for (int a = 0; a < 3; ++a) { v.m[a] = L.m[a]; v.c[a] = (const T*)L.c[a]; }
+  v.N = L.N;
+  v.D = (const T*)L.D;
+  v.x = (T*)L.x;
+  v.b = (const T*)L.b;
+  return v;
+}
+
+int Solver::build_mg(const BoxSys& s, int fp32) {
+  size_t es = fp32 ? sizeof(float) : sizeof(double);
+  bool same = (mg_fp32 == fp32 && mg_m[0] == s.m[0] && mg_m[1] == s.m[1] && mg_m[2] == s.m[2]);
+  if (!same) {
+    // level dims: halve while every active dim is even and > 2
+    int m[3] = {s.m[0], s.m[1], s.m[2]};
+    bool d3 = s.m[2] > 1;
+    nlev = 0;
+    size_t total = 0;
+    for (;;) {
+      MGLevel& L = lev[nlev];
+      for (int a = 0; a < 3; ++a) L.m[a] = m[a];
+      L.N = (long long)m[0] * m[1] * m[2];
+      total += (size_t)L.N * es * 6;
+      nlev++;
+      bool can = (m[0] % 2 == 0 && m[1] % 2 == 0 && m[0] > 2 && m[1] > 2) && (!d3 || (m[2] % 2 == 0 && m[2] > 2));
+      if (!can || nlev >= 24) break;
+      m[0] /= 2; m[1] /= 2;
+      if (d3) m[2] /= 2;
+    }
+    cudaFree(mgbuf);
+    mgbuf = nullptr;
+    CK(cudaMalloc(&mgbuf, total + 256 * 6 * nlev));
+    char* ptr = (char*)mgbuf;
+    auto take = [&](long long n) { void* q = ptr; ptr += ((size_t)n * es + 255) / 256 * 256; return q; };
+    for (int l = 0; l < nlev; ++l) {
+      MGLevel& L = lev[l];
+      L.D = take(L.N);
+      L.c[0] = take(L.N);
+      L.c[1] = take(L.N);
+      L.c[2] = d3 ? take(L.N) : nullptr;
+      L.x = take(L.N);
+      L.b = take(L.N);
+    }
+    mg_fp32 = fp32;
+    mg_m[0] = s.m[0]; mg_m[1] = s.m[1]; mg_m[2] = s.m[2];
+  }
+  // level 0 operator: the pressure box in the hierarchy precision
+  MGLevel& L0 = lev[0];
+  int g0 = lin_grid(L0.N);
+  if (fp32) {
+    ++g_launches, k_cast<float, double><<<g0, TPB, 0, stream>>>(L0.N, (float*)L0.D, s.D);
+    for (int a = 0; a < 3; ++a)
+      if (L0.c[a]) ++g_launches, k_cast<float, double><<<g0, TPB, 0, stream>>>(L0.N, (float*)L0.c[a], s.c[a]);
+  } else {
+    cudaMemcpyAsync(L0.D, s.D, L0.N * 8, cudaMemcpyDeviceToDevice, stream);
+    for (int a = 0; a < 3; ++a)
+      if (L0.c[a]) cudaMemcpyAsync(L0.c[a], s.c[a], L0.N * 8, cudaMemcpyDeviceToDevice, stream);
+  }
+  for (int l = 1; l < nlev; ++l) {
+    int gl = lin_grid(lev[l].N);
+    if (fp32) {
+      LevV<float> F = lv<float>(lev[l - 1]), C = lv<float>(lev[l]);
+      ++g_launches, k_mg_coarsen<float><<<gl, TPB, 0, stream>>>(F, C, (float*)lev[l].D, (float*)lev[l].c[0], (float*)lev[l].c[1], (float*)lev[l].c[2]);
+    } else {
+      LevV<double> F = lv<double>(lev[l - 1]), C = lv<double>(lev[l]);
+      ++g_launches, k_mg_coarsen<double><<<gl, TPB, 0, stream>>>(F, C, (double*)lev[l].D, (double*)lev[l].c[0], (double*)lev[l].c[1], (double*)lev[l].c[2]);
+    }
+  }
+  CK(cudaGetLastError());
+  return 0;
+}
+
+template <typename T>
+static void smooth(Prof* prof, LevV<T> L, int col, int first, const int* done, cudaStream_t st) {
+  int d = L.c[2] ? 3 : 2;
+  ProfScope ps(prof, KC_MG_SMOOTH, st, (2.5 + d) * L.N * (double)sizeof(T));
+  ++g_launches, k_mg_smooth<T><<<lin_grid(L.N), TPB, 0, st>>>(L, col, first, done);
+}
+
+template <typename T>
+static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaStream_t st) {
+  const int nu = 2;          // smoothing sweeps (red + black) before and after
+  const int ncoarse = 16;    // symmetric sweep pairs on the coarsest level
+  for (int l = 0; l < nlev - 1; ++l) {
+    LevV<T> L = lv<T>(lev[l]);
+    int g = lin_grid(L.N);
+    for (int s = 0; s < nu; ++s) {
+      smooth<T>(prof, L, 0, s == 0, done, st);
+      smooth<T>(prof, L, 1, 0, done, st);
+    }
+    LevV<T> C = lv<T>(lev[l + 1]);
+    {
+      int d = L.c[2] ? 3 : 2;
+      ProfScope ps(prof, KC_MG_RESTRICT, st, ((3.0 + d) * L.N + C.N) * (double)sizeof(T));
+      ++g_launches, k_mg_restrict<T><<<lin_grid(C.N), TPB, 0, st>>>(L, C, done);
+    }
+  }
+  {
+    LevV<T> L = lv<T>(lev[nlev - 1]);
+    int g = lin_grid(L.N);
+    for (int s = 0; s < ncoarse; ++s) {
+      smooth<T>(prof, L, 0, s == 0, done, st);
+      smooth<T>(prof, L, 1, 0, done, st);
+    }
+    for (int s = 0; s < ncoarse; ++s) {
+      smooth<T>(prof, L, 1, 0, done, st);
+      smooth<T>(prof, L, 0, 0, done, st);
+    }
+  }
+  for (int l = nlev - 2; l >= 0; --l) {
+    LevV<T> L = lv<T>(lev[l]), C = lv<T>(lev[l + 1]);
+    int g = lin_grid(L.N);
+    {
+      ProfScope ps(prof, KC_MG_PROLONG, st, (2.0 * L.N + C.N) * (double)sizeof(T));
+      ++g_launches, k_mg_prolong<T><<<g, TPB, 0, st>>>(L, C, done);
+    }
+    for (int s = 0; s < nu; ++s) {
+      smooth<T>(prof, L, 1, 0, done, st);
+      smooth<T>(prof, L, 0, 0, done, st);
+    }
+  }
+}
+
+void Solver::vcycle(int fp32) {
+  MGLevel& L0 = lev[0];
+  int g0 = lin_grid(L0.N);
+  if (fp32) {
+    ++g_launches, k_cast_done<float, double><<<g0, TPB, 0, stream>>>(L0.N, (float*)L0.b, r, done);
+    vcycle_t<float>(prof, lev, nlev, done, stream);
+    ++g_launches, k_cast_done<double, float><<<g0, TPB, 0, stream>>>(L0.N, z, (const float*)L0.x, done);
+  } else {
+    vcycle_t<double>(prof, lev, nlev, done, stream);
+  }
+}
+
+int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats* out) {
+  int rc = build_mg(s, fp32);
+  if (rc) return rc;
+  if (!fp32) { lev[0].b = r; lev[0].x = z; }
+  BoxV A = view(s);
+  int nb = red_grid(s.N);
+  int g = lin_grid(s.N);
+  ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
+  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);
+  vcycle(fp32);
+  ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done);
+  ++g_launches, k_fin_rz<<<1, TPB, 0, stream>>>(part, nb, sc, done, 1);
+  ++g_launches, k_cast_done<double, double><<<g, TPB, 0, stream>>>(s.N, p, z, done);
+  const int chunk = 4;
+  int conv = 0;
+  for (int it = 0; it < maxit; it += chunk) {
+    for (int q = 0; q < chunk; ++q) {
+      {
+        ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0);
+        ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done);
+      }
+      ++g_launches, k_fin_alpha<<<1, TPB, 0, stream>>>(part, nb, sc, done);
+      {
+        ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0);
+        ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 0, sc, part, done);
+      }
+      ++g_launches, k_fin_iter<<<1, TPB, 0, stream>>>(part, nb, sc, done, 0);
+      vcycle(fp32);
+      ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done);
+      ++g_launches, k_fin_rz<<<1, TPB, 0, stream>>>(part, nb, sc, done, 0);
+      ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
+    }
+    CK(cudaGetLastError());
+    if (poll(hsc, sc, done, stream, maxit, &conv)) break;
+  }
+  if (!conv) poll(hsc, sc, done, stream, maxit, &conv);
+  fill_stats(hsc, conv, out);
+  return conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
+}
+
+}  // namespace dg

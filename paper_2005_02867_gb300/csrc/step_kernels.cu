@@ -1,0 +1,816 @@
+// Kernels of one segregated time step (Sec. 3.1, Fig. Scheme):
+// initial state, thermodynamics, evaporation flux, alpha source, alpha
+// advection, mixture properties, assembly of the energy / species /
+// momentum / pressure systems, velocity correction and diagnostics.
+// One thread per cell or face; FP64 throughout.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dg {
+
+// ============================================================== initial state
+// alpha: fraction of S^d sub-cell samples inside the sphere (S = 16 in 2D, 8 in 3D),
+// computed without contracted multiply-adds so that every sample decision is exact.
+__global__ void k_init(Geo g, Phys p, double* alpha, double* T, double* omega, double* rhoG) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  int i, j, k;
+  decomp(id, g.n[0], g.n[1], i, j, k);
+  int ci[3] = {i, j, k};
+  const int S = g.axisym ? 16 : 8;
+  double R2 = __dmul_rn(0.5 * p.D0, 0.5 * p.D0);
+  // squared offsets of the sample coordinates per axis
+  double d2a[3][16];
+  int na = nact(g);
+  for (int a = 0; a < na; ++a)
+    for (int m = 0; m < S; ++m) {
+      double frac = (m + 0.5) / S;
+      double pos = __dmul_rn(__dadd_rn((double)ci[a], frac), g.h[a]);
+      double dx = __dadd_rn(pos, -p.xc[a]);
+      d2a[a][m] = __dmul_rn(dx, dx);
+    }
+  int count = 0;
+  if (na == 2) {
+    for (int m0 = 0; m0 < S; ++m0)
+      for (int m1 = 0; m1 < S; ++m1) count += (__dadd_rn(d2a[0][m0], d2a[1][m1]) <= R2);
+  } else {
+    // quick classification of cells far from the sphere surface
+    double lo = 0.0, hi = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double mn = d2a[a][0], mx = d2a[a][0];
+      for (int m = 1; m < S; ++m) { mn = fmin(mn, d2a[a][m]); mx = fmax(mx, d2a[a][m]); }
+      lo += mn; hi += mx;
+    }
+    if (lo > R2 * (1.0 + 1e-12)) count = 0;
+    else if (hi < R2 * (1.0 - 1e-12)) count = S * S * S;
+    else
+      for (int m0 = 0; m0 < S; ++m0)
+        for (int m1 = 0; m1 < S; ++m1) {
+          double s01 = __dadd_rn(d2a[0][m0], d2a[1][m1]);
+          for (int m2 = 0; m2 < S; ++m2) count += (__dadd_rn(s01, d2a[2][m2]) <= R2);
+        }
+  }
+  double a = (double)count / (double)(na == 2 ? S * S : S * S * S);
+  alpha[id] = a;
+  // distance of the cell centre to the droplet centre
+  double d2 = 0.0;
+  for (int q = 0; q < na; ++q) {
+    double x = (ci[q] + 0.5) * g.h[q] - p.xc[q];
+    d2 = d2 + x * x;
+  }
+  double r = sqrt(d2);
+  double rs = 0.5 * p.D0;
+  double t;
+  if (p.const_props) {
+    t = p.T_drop;
+  } else {
+    double Rf = 2.0 * p.D0;
+    double w = (1.0 / fmax(r, rs) - 1.0 / Rf) / (1.0 / rs - 1.0 / Rf);
+    w = fmin(1.0, fmax(0.0, w));
+    t = p.T_amb + (p.T_drop - p.T_amb) * w;
+  }
+  if (p.T_perturb != 0.0) {
+    // SplitMix64 (Steele, Lea & Flood 2014) of seed xor the linear cell index
+    unsigned long long z = (p.seed ^ (unsigned long long)id) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    double u = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+    t = t * (1.0 + p.T_perturb * u);
+  }
+  T[id] = t;
+  double Ys = Y_eq(p, p.T_drop, nullptr);
+  double w;
+  if (a >= 0.5) {
+    w = Y_eq(p, t, nullptr);
+  } else {
+    double Rinf = p.const_props ? 4e-3 : 2.0 * p.D0;
+    double ww = (1.0 / fmax(r, rs) - 1.0 / Rinf) / (1.0 / rs - 1.0 / Rinf);
+    ww = fmin(1.0, fmax(0.0, ww));
+    w = 1.0 - exp(log(1.0 - Ys) * ww);
+    if (r >= Rinf) w = 0.0;
+  }
+  omega[id] = w;
+  rhoG[id] = rho_gas(p, t, w);
+}
+
+// ============================================================== S0 thermodynamics
+// Saturation value written into the liquid (alpha >= 1/2), gas density at T^n.
+__global__ void k_thermo_pin(Geo g, Phys p, const double* alpha, const double* T, double* omega,
+                             double* rhoG_old, unsigned* flags) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  unsigned boil = 0;
+  double w = omega[id];
+  if (alpha[id] >= 0.5) { w = Y_eq(p, T[id], &boil); omega[id] = w; }
+  rhoG_old[id] = rho_gas(p, T[id], w);
+  if (boil) atomicOr(flags, (unsigned)DROPLET_FLAG_BOILING);
+}
+
+// central gradient of alpha at cell (i,j,k) with the alpha ghost rule
+__device__ inline void grad_alpha(const Geo& g, const double* al, int i, int j, int k, double gr[3]) {
+  gr[0] = (cellg(g, al, i + 1, j, k, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i - 1, j, k, R_ALPHA, 0, 0, 0, 0)) / (2.0 * g.h[0]);
+  gr[1] = (cellg(g, al, i, j + 1, k, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i, j - 1, k, R_ALPHA, 0, 0, 0, 0)) / (2.0 * g.h[1]);
+  gr[2] = g.act3 ? (cellg(g, al, i, j, k + 1, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i, j, k - 1, R_ALPHA, 0, 0, 0, 0)) / (2.0 * g.h[2]) : 0.0;
+}
+__device__ __forceinline__ double norm_rn(const double gr[3], int na) {
+  double s = __dadd_rn(__dmul_rn(gr[0], gr[0]), __dmul_rn(gr[1], gr[1]));
+  if (na == 3) s = __dadd_rn(s, __dmul_rn(gr[2], gr[2]));
+  return sqrt(s);
+}
+
+// ============================================================== S1 evaporation flux
+// Interface cells |grad alpha| > 1e-8/h_min; adjacent gas cell = first cell at
+// distance s h_min (s = 1, 2, 3) along n = -grad(alpha)/|grad(alpha)| with
+// alpha < 1e-3 (axis mirrored, stop at the domain edge); j = -rho D grad(omega)
+// + rho omega v there; m_raw = -j . grad(alpha) (Eqs. massflux, globalFlux).
+// Partial sums of m_raw V and f(alpha) m_raw V per block.
+__global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG,
+                           const double* u0, const double* u1, const double* u2,
+                           double* mraw, int* adj, double* partials, unsigned* flags) {
+  double acc[2] = {0.0, 0.0};
+  int na = nact(g);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    decomp(id, g.n[0], g.n[1], i, j, k);
+    double gr[3];
+    grad_alpha(g, alpha, i, j, k, gr);
+    double gm = norm_rn(gr, na);
+    double m = 0.0;
+    int found = -1;
+    if (gm > 1e-8 / g.hmin) {
+      double nh[3] = {-gr[0] / gm, -gr[1] / gm, -gr[2] / gm};
+      int ci[3] = {i, j, k};
+      int q[3] = {0, 0, 0};
+      for (int s = 1; s <= 3 && found < 0; ++s) {
+        bool inside = true;
+        for (int a = 0; a < na; ++a) {
+          double ratio = g.hmin / g.h[a];
+          double xi = __dadd_rn((double)ci[a] + 0.5, __dmul_rn(__dmul_rn((double)s, ratio), nh[a]));
+          if (g.axisym && a == 0) xi = fabs(xi);
+          double fq = floor(xi);
+          if (fq < 0.0 || fq >= (double)g.n[a]) { inside = false; break; }
+          q[a] = (int)fq;
+        }
+        if (!inside) break;
+        if (!g.act3) q[2] = 0;
+        long long qi = cidx(g, q[0], q[1], q[2]);
+        if (alpha[qi] < ALPHA_GAS) found = (int)qi;
+      }
+      if (found < 0) {
+        atomicOr(flags, (unsigned)DROPLET_FLAG_ADJ_NOT_FOUND);
+      } else {
+        // total flux at the adjacent cell Q
+        double aQ = alpha[found], rgQ = rhoG[found], wQ = omega[found];
+        double rhoQ = aQ * p.rho_l + (1.0 - aQ) * rgQ;
+        double DQ = aQ * p.D_l + (1.0 - aQ) * p.D_gas;
+        int qi, qj, qk;
+        decomp(found, g.n[0], g.n[1], qi, qj, qk);
+        double gw[3];
+        gw[0] = (cellg(g, omega, qi + 1, qj, qk, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi - 1, qj, qk, R_TO, 0.0, u0, u1, u2)) / (2.0 * g.h[0]);
+        gw[1] = (cellg(g, omega, qi, qj + 1, qk, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi, qj - 1, qk, R_TO, 0.0, u0, u1, u2)) / (2.0 * g.h[1]);
+        gw[2] = g.act3 ? (cellg(g, omega, qi, qj, qk + 1, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi, qj, qk - 1, R_TO, 0.0, u0, u1, u2)) / (2.0 * g.h[2]) : 0.0;
+        double vc[3];
+        vc[0] = 0.5 * (u0[fidx(g, 0, qi, qj, qk)] + u0[fidx(g, 0, qi + 1, qj, qk)]);
+        vc[1] = 0.5 * (u1[fidx(g, 1, qi, qj, qk)] + u1[fidx(g, 1, qi, qj + 1, qk)]);
+        vc[2] = g.act3 ? 0.5 * (u2[fidx(g, 2, qi, qj, qk)] + u2[fidx(g, 2, qi, qj, qk + 1)]) : 0.0;
+        double s = 0.0;
+        for (int a = 0; a < na; ++a) {
+          double ja = -rhoQ * DQ * gw[a] + rhoQ * wQ * vc[a];
+          s = s + ja * gr[a];
+        }
+        m = -s;
+      }
+    }
+    mraw[id] = m;
+    adj[id] = found;
+    double V = cellV(g, i);
+    double a = alpha[id];
+    acc[0] += m * V;
+    acc[1] += sqrt(a * (1.0 - a)) * m * V;
+  }
+  block_sum_store<2>(acc, partials);
+}
+
+// K = sum(m_raw V) / sum(f m_raw V) (Eq. alphafunction normalisation)
+__global__ void k_evap_K(const double* partials, int nblk, double* scal, unsigned* flags) {
+  double s1 = block_sum_partials(partials, nblk);
+  double s2 = block_sum_partials(partials + nblk, nblk);
+  if (threadIdx.x == 0) {
+    if (fabs(s2) < 1e-300) { scal[SC_K] = 0.0; atomicOr(flags, (unsigned)DROPLET_FLAG_NO_INTERFACE); }
+    else scal[SC_K] = s1 / s2;
+  }
+}
+
+// ============================================================== S2 alpha source
+__global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double* mraw, const double* scal,
+                               double* mdot, double* alpha_star, unsigned* flags) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  double a = alpha[id];
+  double K = scal[SC_K];
+  double m = (K == 0.0) ? 0.0 : K * sqrt(a * (1.0 - a)) * mraw[id];
+  double cap = p.rho_l * a / p.dt;
+  if (m > cap) { m = cap; atomicOr(flags, (unsigned)DROPLET_FLAG_MDOT_CAPPED); }
+  mdot[id] = m;
+  alpha_star[id] = a - p.dt * m / p.rho_l;
+}
+
+// ============================================================== S3 alpha advection (FCT)
+// Per face of direction a: low-order flux FL = phi alpha_upwind and the
+// antidiffusive flux AF = FH - FL (interior faces only), FH = phi alpha_vanLeer
+// + C_alpha |phi| (n_f . e_a) a_c (1 - a_c).
+__global__ void k_adv_faces(Geo g, Phys p, int a, const double* as, const double* ua, double* FL, double* AF) {
+  long long nf = nfaces(g, a);
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= nf) return;
+  int m0 = g.n[0] + (a == 0), m1 = g.n[1] + (a == 1);
+  int f[3];
+  decomp(id, m0, m1, f[0], f[1], f[2]);
+  int L[3] = {f[0], f[1], f[2]}, R[3] = {f[0], f[1], f[2]};
+  L[a] -= 1;
+  double phi = ua[id] * faceA(g, a, f[0]) * p.dt;
+  double aL = cellg(g, as, L[0], L[1], L[2], R_ALPHA, 0, 0, 0, 0);
+  double aR = cellg(g, as, R[0], R[1], R[2], R_ALPHA, 0, 0, 0, 0);
+  bool pos = phi >= 0.0;
+  FL[id] = phi * (pos ? aL : aR);
+  double A = 0.0;
+  if (f[a] > 0 && f[a] < g.n[a]) {
+    int LL[3] = {L[0], L[1], L[2]}, RR[3] = {R[0], R[1], R[2]};
+    LL[a] -= 1;
+    RR[a] += 1;
+    double aLL = cellg(g, as, LL[0], LL[1], LL[2], R_ALPHA, 0, 0, 0, 0);
+    double aRR = cellg(g, as, RR[0], RR[1], RR[2], R_ALPHA, 0, 0, 0, 0);
+    double aVL = pos ? van_leer(aLL, aL, aR) : van_leer(aRR, aR, aL);
+    double gL[3], gR[3];
+    grad_alpha(g, as, L[0], L[1], L[2], gL);
+    grad_alpha(g, as, R[0], R[1], R[2], gR);
+    double gf[3] = {gL[0] + gR[0], gL[1] + gR[1], gL[2] + gR[2]};
+    double gfm = sqrt(gf[0] * gf[0] + gf[1] * gf[1] + (g.act3 ? gf[2] * gf[2] : 0.0));
+    double ne = gfm > 1e-8 / g.hmin ? gf[a] / gfm : 0.0;
+    double ac = 0.5 * (aL + aR);
+    double FH = phi * aVL + p.C_alpha * fabs(phi) * ne * ac * (1.0 - ac);
+    A = FH - FL[id];
+  }
+  AF[id] = A;
+}
+
+__device__ __forceinline__ double face_net(const Geo& g, const double* F0, const double* F1, const double* F2,
+                                           int i, int j, int k) {
+  double s = F0[fidx(g, 0, i + 1, j, k)] - F0[fidx(g, 0, i, j, k)];
+  s += F1[fidx(g, 1, i, j + 1, k)] - F1[fidx(g, 1, i, j, k)];
+  if (g.act3) s += F2[fidx(g, 2, i, j, k + 1)] - F2[fidx(g, 2, i, j, k)];
+  return s;
+}
+
+__global__ void k_adv_low(Geo g, const double* as, const double* F0, const double* F1, const double* F2, double* aL) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  int i, j, k;
+  decomp(id, g.n[0], g.n[1], i, j, k);
+  aL[id] = as[id] - face_net(g, F0, F1, F2, i, j, k) / cellV(g, i);
+}
+
+// Zalesak limiter ratios R+ and R- from the local bounds over the cell and its face neighbours.
+__global__ void k_adv_limit(Geo g, const double* as, const double* aL, const double* A0, const double* A1,
+                            const double* A2, double* Rp, double* Rm) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  int i, j, k;
+  decomp(id, g.n[0], g.n[1], i, j, k);
+  double amax = fmax(as[id], aL[id]), amin = fmin(as[id], aL[id]);
+  int na = nact(g);
+  for (int a = 0; a < na; ++a)
+    for (int sh = -1; sh <= 1; sh += 2) {
+      int q[3] = {i, j, k};
+      q[a] += sh;
+      if (q[a] < 0 || q[a] >= g.n[a]) continue;
+      long long qi = cidx(g, q[0], q[1], q[2]);
+      amax = fmax(amax, fmax(as[qi], aL[qi]));
+      amin = fmin(amin, fmin(as[qi], aL[qi]));
+    }
+  amax = fmin(amax, 1.0);
+  amin = fmax(amin, 0.0);
+  const double* AA[3] = {A0, A1, A2};
+  double Pp = 0.0, Pm = 0.0;
+  for (int a = 0; a < na; ++a) {
+    int hi[3] = {i, j, k};
+    hi[a] += 1;
+    double Alo = AA[a][fidx(g, a, i, j, k)];
+    double Ahi = AA[a][fidx(g, a, hi[0], hi[1], hi[2])];
+    Pp += fmax(0.0, Alo) + fmax(0.0, -Ahi);
+    Pm += fmax(0.0, -Alo) + fmax(0.0, Ahi);
+  }
+  double V = cellV(g, i);
+  double Qp = (amax - aL[id]) * V, Qm = (aL[id] - amin) * V;
+  Rp[id] = Pp > 0.0 ? fmin(1.0, fmax(0.0, Qp / Pp)) : 0.0;
+  Rm[id] = Pm > 0.0 ? fmin(1.0, fmax(0.0, Qm / Pm)) : 0.0;
+}
+
+__device__ __forceinline__ double limited_flux(const Geo& g, int a, const double* A, const double* Rp,
+                                               const double* Rm, int f0, int f1, int f2) {
+  double Af = A[fidx(g, a, f0, f1, f2)];
+  if (Af == 0.0) return 0.0;
+  int L[3] = {f0, f1, f2};
+  L[a] -= 1;
+  long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, f0, f1, f2);
+  double C = Af >= 0.0 ? fmin(Rp[ri], Rm[li]) : fmin(Rp[li], Rm[ri]);
+  return C * Af;
+}
+
+// alpha^{n+1} = alpha^L - sum C A / V, clipped to [0, 1] with the clipped volume summed.
+__global__ void k_adv_update(Geo g, const double* aL, const double* A0, const double* A1, const double* A2,
+                             const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags) {
+  double acc[2] = {0.0, 0.0};
+  const double* AA[3] = {A0, A1, A2};
+  int na = nact(g);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    decomp(id, g.n[0], g.n[1], i, j, k);
+    double s = 0.0;
+    for (int a = 0; a < na; ++a) {
+      int hi[3] = {i, j, k};
+      hi[a] += 1;
+      s += limited_flux(g, a, AA[a], Rp, Rm, hi[0], hi[1], hi[2]) - limited_flux(g, a, AA[a], Rp, Rm, i, j, k);
+    }
+    double V = cellV(g, i);
+    double an = aL[id] - s / V;
+    double ac = fmin(1.0, fmax(0.0, an));
+    if (ac != an) { acc[1] += 1.0; acc[0] += (an - ac) * V; }
+    alpha[id] = ac;
+  }
+  block_sum_store<2>(acc, partials);
+}
+
+__global__ void k_clip_finish(const double* partials, int nblk, double* scal, unsigned* flags) {
+  double v = block_sum_partials(partials, nblk);
+  double c = block_sum_partials(partials + nblk, nblk);
+  if (threadIdx.x == 0) {
+    scal[SC_CLIP] += v;
+    if (c > 0.0) atomicOr(flags, (unsigned)DROPLET_FLAG_ALPHA_CLIPPED);
+  }
+}
+
+// no advection: clip alpha* into alpha
+__global__ void k_alpha_clip_only(Geo g, const double* as, double* alpha, double* partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    decomp(id, g.n[0], g.n[1], i, j, k);
+    double an = as[id], ac = fmin(1.0, fmax(0.0, an));
+    if (ac != an) { acc[1] += 1.0; acc[0] += (an - ac) * cellV(g, i); }
+    alpha[id] = ac;
+  }
+  block_sum_store<2>(acc, partials);
+}
+
+// ============================================================== S4 mixture properties
+__global__ void k_props(Geo g, Phys p, const double* alpha, const double* rhoG, const double* omega, double* rho,
+                        double* mu, double* kc, double* cp, double* D) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  double a = alpha[id], w = omega[id];
+  rho[id] = a * p.rho_l + (1.0 - a) * rhoG[id];
+  mu[id] = a * p.mu_l + (1.0 - a) * p.mu_g;
+  kc[id] = a * p.k_l + (1.0 - a) * p.k_g;
+  double cpG = w * p.cp_v + (1.0 - w) * p.cp_g;
+  cp[id] = a * p.cp_l + (1.0 - a) * cpG;
+  D[id] = a * p.D_l + (1.0 - a) * p.D_gas;
+}
+
+// ============================================================== S5 / S6 scalar transport systems
+// coef V (phi - phi^n)/dt + coef [sum F phi_f - phi_P sum F] = sum gamma_f A (phi_N - phi_P)/h + src V
+// Box operator: y_P = D_P x_P + sum c (x_P - x_Q); c stored at the high cell of each pair.
+// mode 0: energy (coef = rho cp, gamma = k, src = -mdot L), mode 1: species (coef = rho,
+// gamma = rho D, rows with alpha >= 1/2 pinned to Y_eq(T^{n+1})).
+__device__ __forceinline__ double gam(int mode, const double* kc, const double* rho, const double* D, long long q) {
+  return mode == 0 ? kc[q] : rho[q] * D[q];
+}
+__device__ __forceinline__ double harm(double x, double y) { return 2.0 * x * y / (x + y); }
+
+__global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
+                                  const double* kc, const double* D, const double* mdot, const double* u0,
+                                  const double* u1, const double* u2, const double* alpha_new, const double* pinv,
+                                  double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  int i, j, k;
+  decomp(id, g.n[0], g.n[1], i, j, k);
+  int na = nact(g);
+  const double* U[3] = {u0, u1, u2};
+  double* C[3] = {c0, c1, c2};
+  double V = cellV(g, i);
+  double coef = mode == 0 ? rho[id] * cp[id] : rho[id];
+  double dP = coef * V / p.dt;
+  double r = coef * V * phi[id] / p.dt + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
+  double net = 0.0, Fsum = 0.0;
+  double gP = gam(mode, kc, rho, D, id);
+  bool pin = (mode == 1) && (alpha_new[id] >= 0.5);
+  int ci[3] = {i, j, k};
+  for (int a = 0; a < na; ++a) {
+    for (int side = 0; side < 2; ++side) {
+      int f[3] = {i, j, k};
+      if (side) f[a] += 1;
+      double F = U[a][fidx(g, a, f[0], f[1], f[2])] * faceA(g, a, f[0]);
+      double val;
+      if (f[a] == 0 || f[a] == g.n[a]) {
+        int kind = g.bc[a][side];
+        bool inflow = side == 0 ? (F > 0.0) : (F < 0.0);
+        val = ((kind == BC_OPEN || kind == BC_FORCED) && inflow) ? amb : phi[id];
+      } else {
+        int L[3] = {f[0], f[1], f[2]};
+        L[a] -= 1;
+        int LL[3] = {L[0], L[1], L[2]}, RR[3] = {f[0], f[1], f[2]};
+        LL[a] -= 1;
+        RR[a] += 1;
+        double vL = phi[cidx(g, L[0], L[1], L[2])], vR = phi[cidx(g, f[0], f[1], f[2])];
+        if (F >= 0.0) val = lim_up(cellg(g, phi, LL[0], LL[1], LL[2], R_TO, amb, u0, u1, u2), vL, vR);
+        else val = lim_up(cellg(g, phi, RR[0], RR[1], RR[2], R_TO, amb, u0, u1, u2), vR, vL);
+      }
+      double sgn = side ? 1.0 : -1.0;
+      net += sgn * F * val;
+      Fsum += sgn * F;
+    }
+    // coupling across the low face, stored at this cell
+    double cl = 0.0;
+    if (ci[a] > 0) {
+      int Lc[3] = {i, j, k};
+      Lc[a] -= 1;
+      long long li = cidx(g, Lc[0], Lc[1], Lc[2]);
+      cl = harm(gam(mode, kc, rho, D, li), gP) * faceA(g, a, i) / g.h[a];
+      if (mode == 1) {
+        bool lp = alpha_new[li] >= 0.5;
+        if (!pin && lp) { r += cl * pinv[li]; dP += cl; }
+        if (pin || lp) cl = 0.0;
+      }
+    }
+    C[a][id] = cl;
+    // coupling across the high face (owned by the neighbour): only the pinned-neighbour transfer here
+    if (mode == 1 && ci[a] < g.n[a] - 1 && !pin) {
+      int Hc[3] = {i, j, k};
+      Hc[a] += 1;
+      long long hi = cidx(g, Hc[0], Hc[1], Hc[2]);
+      if (alpha_new[hi] >= 0.5) {
+        double ch = harm(gP, gam(mode, kc, rho, D, hi)) * faceA(g, a, Hc[0]) / g.h[a];
+        r += ch * pinv[hi];
+        dP += ch;
+      }
+    }
+    // Dirichlet boundary faces
+    for (int side = 0; side < 2; ++side) {
+      bool atb = side ? (ci[a] == g.n[a] - 1) : (ci[a] == 0);
+      if (!atb) continue;
+      int kind = g.bc[a][side];
+      bool isdir = false;
+      int f[3] = {i, j, k};
+      if (side) f[a] += 1;
+      if (kind == BC_FORCED) isdir = true;
+      else if (kind == BC_OPEN) {
+        double un = U[a][fidx(g, a, f[0], f[1], f[2])];
+        isdir = (side ? un : -un) < 0.0;
+      }
+      if (isdir) {
+        double cb = gP * faceA(g, a, f[0]) / (0.5 * g.h[a]);
+        dP += cb;
+        r += cb * amb;
+      }
+    }
+  }
+  r -= coef * (net - phi[id] * Fsum);
+  if (pin) {
+    // pinned row, scaled like the other rows: (coef V/dt) x = (coef V/dt) Y_eq
+    double dd = coef * V / p.dt;
+    r = dd * pinv[id];
+    dP = dd;
+  }
+  Dg[id] = dP;
+  rhs[id] = r;
+}
+
+__global__ void k_yeq(Geo g, Phys p, const double* T, double* yq, unsigned* flags) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  unsigned b = 0;
+  yq[id] = Y_eq(p, T[id], &b);
+  if (b) atomicOr(flags, (unsigned)DROPLET_FLAG_BOILING);
+}
+
+__global__ void k_species_noflow(Geo g, const double* alpha_new, const double* yq, double* omega) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  if (alpha_new[id] >= 0.5) omega[id] = yq[id];
+}
+
+__global__ void k_rhoG(Geo g, Phys p, const double* T, const double* w, double* rhoG) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  rhoG[id] = rho_gas(p, T[id], w[id]);
+}
+
+// ============================================================== S7 momentum predictor
+// For each interior face of direction c (box index b, face index f = b + e_c),
+// V_f-weighted: rho_f V_f/dt u* - [implicit viscous] = rho_f V_f u^n/dt + adv + visc^T + forces.
+__device__ __forceinline__ double mu_edge(const Geo& g, const double* mu, const int L[3], const int R[3], int a, int sh) {
+  int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
+  La[a] += sh;
+  Ra[a] += sh;
+  double s = cellc(g, mu, L[0], L[1], L[2]) + cellc(g, mu, R[0], R[1], R[2]) + cellc(g, mu, La[0], La[1], La[2]) +
+             cellc(g, mu, Ra[0], Ra[1], Ra[2]);
+  return 0.25 * s;
+}
+
+__global__ void k_mom_assemble(Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2,
+                               const double* rho, const double* mu, const double* pr, const double* alpha,
+                               double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+  // box dims: n with n_c - 1 along c
+  int m[3] = {g.n[0], g.n[1], g.n[2]};
+  m[c] -= 1;
+  long long nb = (long long)m[0] * m[1] * m[2];
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= nb) return;
+  int b[3];
+  decomp(id, m[0], m[1], b[0], b[1], b[2]);
+  int f[3] = {b[0], b[1], b[2]};
+  f[c] += 1;                                   // face index
+  int L[3] = {f[0], f[1], f[2]}, R[3] = {f[0], f[1], f[2]};
+  L[c] -= 1;
+  const double* U[3] = {u0, u1, u2};
+  const double* uc = U[c];
+  double* Cc[3] = {c0, c1, c2};
+  int na = nact(g);
+  long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, R[0], R[1], R[2]);
+  double rhoL = rho[li], rhoR = rho[ri], muL = mu[li], muR = mu[ri];
+  double rho_f = 0.5 * (rhoL + rhoR), mu_f = 0.5 * (muL + muR);
+  double r_f = 0.0, V_f;
+  if (g.axisym) {
+    r_f = (c == 0) ? f[0] * g.h[0] : (f[0] + 0.5) * g.h[0];
+    V_f = r_f * g.h[0] * g.h[1];
+  } else {
+    V_f = g.h[0] * g.h[1] * g.h[2];
+  }
+  double A_f = V_f / g.h[c];
+  double u_f = uc[fidx(g, c, f[0], f[1], f[2])];
+  double d = rho_f * V_f / p.dt;
+  double r = rho_f * V_f * u_f / p.dt;
+  double t_adv = 0.0, t_vT = 0.0, d_visc = 0.0;
+  for (int a = 0; a < na; ++a) {
+    // ---- advection (advective form, minmod limited linear upwind)
+    double ubar;
+    if (a == c) ubar = u_f;
+    else {
+      const double* ua = U[a];
+      int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
+      La[a] += 1;
+      Ra[a] += 1;
+      ubar = 0.25 * (((ua[fidx(g, a, L[0], L[1], L[2])] + ua[fidx(g, a, La[0], La[1], La[2])]) +
+                      ua[fidx(g, a, R[0], R[1], R[2])]) + ua[fidx(g, a, Ra[0], Ra[1], Ra[2])]);
+    }
+    int q[3];
+    double us[5];
+    for (int s = -2; s <= 2; ++s) {
+      q[0] = f[0]; q[1] = f[1]; q[2] = f[2];
+      q[a] += s;
+      us[s + 2] = ufg(g, uc, c, q[0], q[1], q[2]);
+    }
+    double uplus, uminus;
+    if (ubar >= 0.0) { uplus = lim_up(us[1], us[2], us[3]); uminus = lim_up(us[0], us[1], us[2]); }
+    else { uplus = lim_up(us[4], us[3], us[2]); uminus = lim_up(us[3], us[2], us[1]); }
+    t_adv = t_adv - rho_f * V_f * ubar * (uplus - uminus) / g.h[a];
+    // ---- viscous
+    if (a == c) {
+      double ApL, ApR;
+      if (g.axisym && c == 0) { ApL = areaN(g, 0, (L[0] + 0.5) * g.h[0]); ApR = areaN(g, 0, (R[0] + 0.5) * g.h[0]); }
+      else if (g.axisym) { ApL = ApR = areaN(g, 1, r_f); }
+      else { ApL = ApR = areaN(g, c, 0.0); }
+      double kR = muR * ApR / g.h[c], kL = muL * ApL / g.h[c];
+      double dR = (us[3] - us[2]) / g.h[c], dL = (us[2] - us[1]) / g.h[c];
+      t_vT = t_vT + muR * ApR * dR - muL * ApL * dL;
+      // coupling with the lower neighbour face (stored at this box cell)
+      Cc[c][id] = (b[c] > 0) ? kL : 0.0;
+      if (b[c] == 0 && g.bc[c][0] != BC_OPEN) {
+        int fb[3] = {f[0], f[1], f[2]};
+        fb[c] = 0;
+        d_visc += kL;
+        r += kL * uc[fidx(g, c, fb[0], fb[1], fb[2])];
+      }
+      if (b[c] == m[c] - 1 && g.bc[c][1] != BC_OPEN) {
+        int fb[3] = {f[0], f[1], f[2]};
+        fb[c] = g.n[c];
+        d_visc += kR;
+        r += kR * uc[fidx(g, c, fb[0], fb[1], fb[2])];
+      }
+    } else {
+      double App, Apm;
+      if (g.axisym && a == 0) { App = areaN(g, 0, (f[0] + 1) * g.h[0]); Apm = areaN(g, 0, f[0] * g.h[0]); }
+      else if (g.axisym) { App = Apm = areaN(g, 1, r_f); }
+      else { App = Apm = areaN(g, a, 0.0); }
+      double mup = mu_edge(g, mu, L, R, a, 1), mum = mu_edge(g, mu, L, R, a, -1);
+      double kp = mup * App / g.h[a], km = mum * Apm / g.h[a];
+      const double* ua = U[a];
+      int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
+      La[a] += 1;
+      Ra[a] += 1;
+      double uaR_hi = ua[fidx(g, a, Ra[0], Ra[1], Ra[2])], uaL_hi = ua[fidx(g, a, La[0], La[1], La[2])];
+      double uaR_lo = ua[fidx(g, a, R[0], R[1], R[2])], uaL_lo = ua[fidx(g, a, L[0], L[1], L[2])];
+      t_vT = t_vT + mup * App * (uaR_hi - uaL_hi) / g.h[c] - mum * Apm * (uaR_lo - uaL_lo) / g.h[c];
+      Cc[a][id] = (b[a] > 0) ? km : 0.0;
+      if (b[a] == 0 && (g.bc[a][0] == BC_WALL || g.bc[a][0] == BC_FORCED)) d_visc += 2.0 * km;
+      if (b[a] == m[a] - 1 && (g.bc[a][1] == BC_WALL || g.bc[a][1] == BC_FORCED)) d_visc += 2.0 * kp;
+    }
+  }
+  if (g.axisym && c == 0 && r_f > 0.0) d_visc = d_visc + 2.0 * mu_f * V_f / (r_f * r_f);
+  // pressure, buoyancy and centripetal force in the balanced face form
+  double gx = 0.0;
+  for (int a = 0; a < na; ++a) {
+    double xa = (a == c) ? f[a] * g.h[a] : (f[a] + 0.5) * g.h[a];
+    gx = gx + p.g[a] * xa;
+  }
+  auto xi_at = [&](const int q[3]) {
+    double d2 = 0.0;
+    for (int a = 0; a < na; ++a) { double x = (q[a] + 0.5) * g.h[a] - p.xc[a]; d2 = d2 + x * x; }
+    return p.xi0 * p.Df / (2.0 * fmax(sqrt(d2), p.Df));
+  };
+  double xiL = xi_at(L), xiR = xi_at(R);
+  double raL = rhoL * alpha[li], raR = rhoR * alpha[ri];
+  double t_force = -A_f * (pr[ri] - pr[li]) - A_f * gx * (rhoR - rhoL) + A_f * 0.5 * (raL + raR) * (xiR - xiL);
+  d = d + d_visc;
+  r = r + t_adv + t_vT + t_force;
+  Dg[id] = d;
+  rhs[id] = r;
+}
+
+// u* of direction c from the box solution; boundary faces by their rule.
+__global__ void k_mom_scatter(Geo g, Phys p, int c, const double* x, double* us) {
+  long long nf = nfaces(g, c);
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= nf) return;
+  int m0 = g.n[0] + (c == 0), m1 = g.n[1] + (c == 1);
+  int f[3];
+  decomp(id, m0, m1, f[0], f[1], f[2]);
+  int mb[3] = {g.n[0], g.n[1], g.n[2]};
+  mb[c] -= 1;
+  auto box = [&](int fc) {
+    int b[3] = {f[0], f[1], f[2]};
+    b[c] = fc - 1;
+    return x[(long long)b[0] + (long long)mb[0] * ((long long)b[1] + (long long)mb[1] * b[2])];
+  };
+  if (f[c] > 0 && f[c] < g.n[c]) { us[id] = box(f[c]); return; }
+  int side = f[c] == 0 ? 0 : 1;
+  int kind = g.bc[c][side];
+  if (kind == BC_OPEN) us[id] = box(side ? g.n[c] - 1 : 1);
+  // axis / wall: stays 0; forced inlet: keeps u_in (both already stored)
+}
+
+// ============================================================== S8 - S10 projection
+// S = mdot (1/rho_G - 1/rho_L) - (1 - alpha)/rho_G [(rho_G^{n+1} - rho_G^n)/dt + vbar . grad rho_G^{n+1}]
+// sum beta_f (dp_P - dp_N) + sum_open beta_b dp_P = (S V - sum u* A)/dt
+__global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo,
+                                   const double* rgn, const double* u0, const double* u1, const double* u2,
+                                   const double* us0, const double* us1, const double* us2, const double* rho,
+                                   double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  int i, j, k;
+  decomp(id, g.n[0], g.n[1], i, j, k);
+  int na = nact(g);
+  const double* U[3] = {u0, u1, u2};
+  const double* US[3] = {us0, us1, us2};
+  double* C[3] = {c0, c1, c2};
+  int ci[3] = {i, j, k};
+  double adv = 0.0;
+  for (int a = 0; a < na; ++a) {
+    int hi[3] = {i, j, k};
+    hi[a] += 1;
+    double vc = 0.5 * (U[a][fidx(g, a, i, j, k)] + U[a][fidx(g, a, hi[0], hi[1], hi[2])]);
+    int qp[3] = {i, j, k}, qm[3] = {i, j, k};
+    qp[a] += 1;
+    qm[a] -= 1;
+    double gr = (cellg(g, rgn, qp[0], qp[1], qp[2], R_ZG, 0, 0, 0, 0) - cellg(g, rgn, qm[0], qm[1], qm[2], R_ZG, 0, 0, 0, 0)) / (2.0 * g.h[a]);
+    adv = adv + vc * gr;
+  }
+  double rn = rgn[id];
+  double s = mdot[id] * (1.0 / rn - 1.0 / p.rho_l) - (1.0 - alpha[id]) / rn * ((rn - rgo[id]) / p.dt + adv);
+  S[id] = s;
+  double dg = 0.0, div = 0.0;
+  double rP = rho[id];
+  for (int a = 0; a < na; ++a) {
+    int hi[3] = {i, j, k};
+    hi[a] += 1;
+    div += US[a][fidx(g, a, hi[0], hi[1], hi[2])] * faceA(g, a, hi[0]) - US[a][fidx(g, a, i, j, k)] * faceA(g, a, i);
+    double cl = 0.0;
+    if (ci[a] > 0) {
+      int Lc[3] = {i, j, k};
+      Lc[a] -= 1;
+      double rf = 0.5 * (rho[cidx(g, Lc[0], Lc[1], Lc[2])] + rP);
+      cl = faceA(g, a, i) / (rf * g.h[a]);
+    }
+    C[a][id] = cl;
+    if (ci[a] == 0 && g.bc[a][0] == BC_OPEN) dg += faceA(g, a, i) / (rP * 0.5 * g.h[a]);
+    if (ci[a] == g.n[a] - 1 && g.bc[a][1] == BC_OPEN) dg += faceA(g, a, hi[0]) / (rP * 0.5 * g.h[a]);
+  }
+  Dg[id] = dg;
+  rhs[id] = (s * cellV(g, i) - div) / p.dt;
+}
+
+// u = u* - dt beta_f (dp_R - dp_L)/A_f with dp = 0 beyond open faces (half-cell distance)
+__global__ void k_correct(Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u) {
+  long long nf = nfaces(g, c);
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= nf) return;
+  int m0 = g.n[0] + (c == 0), m1 = g.n[1] + (c == 1);
+  int f[3];
+  decomp(id, m0, m1, f[0], f[1], f[2]);
+  double A = faceA(g, c, f[0]);
+  double corr = 0.0;
+  if (A > 0.0) {
+    int L[3] = {f[0], f[1], f[2]};
+    L[c] -= 1;
+    if (f[c] > 0 && f[c] < g.n[c]) {
+      long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, f[0], f[1], f[2]);
+      double beta = A / (0.5 * (rho[li] + rho[ri]) * g.h[c]);
+      corr = p.dt * beta * (dp[ri] - dp[li]) / A;
+    } else {
+      int side = f[c] == 0 ? 0 : 1;
+      if (g.bc[c][side] == BC_OPEN) {
+        long long pi = side ? cidx(g, L[0], L[1], L[2]) : cidx(g, f[0], f[1], f[2]);
+        double beta = A / (rho[pi] * 0.5 * g.h[c]);
+        corr = side ? p.dt * beta * (0.0 - dp[pi]) / A : p.dt * beta * (dp[pi] - 0.0) / A;
+      }
+    }
+  }
+  u[id] = us[id] - corr;
+}
+
+__global__ void k_add(long long n, double* y, const double* x) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id < n) y[id] += x[id];
+}
+
+// ============================================================== S11 diagnostics
+// sums: alpha V, mdot V, T |grad alpha| V, |grad alpha| V, (1-alpha) rhoG omega V, open-boundary vapour outflow
+// maxima: |u|, alpha, -alpha
+__global__ void k_diag(Geo g, const double* alpha, const double* T, const double* mdot, const double* omega,
+                       const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum,
+                       double* pmax) {
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  double mx[3] = {0.0, -1e300, -1e300};
+  int na = nact(g);
+  const double* U[3] = {u0, u1, u2};
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    decomp(id, g.n[0], g.n[1], i, j, k);
+    double V = cellV(g, i);
+    double a = alpha[id];
+    double gr[3];
+    grad_alpha(g, alpha, i, j, k, gr);
+    double gm = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + (g.act3 ? gr[2] * gr[2] : 0.0));
+    s[0] += a * V;
+    s[1] += mdot[id] * V;
+    s[2] += T[id] * gm * V;
+    s[3] += gm * V;
+    s[4] += (1.0 - a) * rhoG[id] * omega[id] * V;
+    mx[1] = fmax(mx[1], a);
+    mx[2] = fmax(mx[2], -a);
+    int ci[3] = {i, j, k};
+    for (int q = 0; q < na; ++q) {
+      mx[0] = fmax(mx[0], fabs(U[q][fidx(g, q, i, j, k)]));
+      if (ci[q] == g.n[q] - 1) {
+        int hi[3] = {i, j, k};
+        hi[q] += 1;
+        mx[0] = fmax(mx[0], fabs(U[q][fidx(g, q, hi[0], hi[1], hi[2])]));
+      }
+      for (int side = 0; side < 2; ++side) {
+        bool atb = side ? (ci[q] == g.n[q] - 1) : (ci[q] == 0);
+        int kind = g.bc[q][side];
+        if (!atb || !(kind == BC_OPEN || kind == BC_FORCED)) continue;
+        int f[3] = {i, j, k};
+        if (side) f[q] += 1;
+        double un = U[q][fidx(g, q, f[0], f[1], f[2])];
+        double vout = side ? un : -un;
+        if (vout > 0.0) s[5] += rhoG[id] * omega[id] * vout * faceA(g, q, f[0]);
+      }
+    }
+  }
+  block_sum_store<6>(s, psum);
+  __syncthreads();
+  block_max_store<3>(mx, pmax);
+}
+
+__global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal) {
+  double v[6], m[3];
+  for (int q = 0; q < 6; ++q) { v[q] = block_sum_partials(psum + q * nblk, nblk); __syncthreads(); }
+  for (int q = 0; q < 3; ++q) { m[q] = block_max_partials(pmax + q * nblk, nblk); __syncthreads(); }
+  if (threadIdx.x == 0) {
+    scal[SC_SUM_ALPHA_V] = v[0];
+    scal[SC_SUM_MDOT_V] = v[1];
+    scal[SC_SUM_TG] = v[2];
+    scal[SC_SUM_G] = v[3];
+    scal[SC_SUM_VAP] = v[4];
+    scal[SC_VAPOUT] += v[5] * scal[SC_DT];
+    scal[SC_MAXU] = m[0];
+    scal[SC_AMAX] = m[1];
+    scal[SC_AMIN] = -m[2];
+  }
+}
+
+}  // namespace dg
