@@ -158,6 +158,24 @@ int droplet_get_field(droplet_ctx* ctx, int droplet, int field_id, double* host,
 /* Overwrite a state field (ALPHA, T, OMEGA, P, RHOG, U0..U2) from n host doubles. */
 int droplet_set_field(droplet_ctx* ctx, int droplet, int field_id, const double* host, size_t n);
 
+/* Solve one symmetric positive-definite box system of the kind the step
+ * assembles for the energy, species and momentum equations (Sec. 3.1: implicit
+ * Euler with the orthogonal Laplacian), with the library's Jacobi-preconditioned
+ * conjugate gradient.  The unknowns sit on an m[0] x m[1] x m[2] box (index 0
+ * fastest); the operator is
+ *   y_P = D_P x_P + sum_a [ c_a[P] (x_P - x_{P-e_a}) + c_a[P+e_a] (x_P - x_{P+e_a}) ],
+ * i.e. the coupling of each pair of neighbours is stored at its high cell, and
+ * c_a[P] is ignored where P_a = 0.  D, c0, c1, b are device arrays of
+ * m0*m1*m2 doubles; c2 is NULL when m[2] = 1; x (device) holds the initial guess
+ * and receives the solution.  Stops at ||b - A x|| <= rtol ||b|| or after maxit
+ * iterations (DROPLET_ERR_NOT_CONVERGED).  Work is enqueued on cuda_stream and
+ * the call returns when the solve has finished; *its and *relres (host, may be
+ * NULL) receive the iteration count and the final relative residual.
+ * Allocates its workspace with cudaMalloc for the duration of the call. */
+int droplet_box_solve(const int m[3], const double* D, const double* c0, const double* c1, const double* c2,
+                      const double* b, double* x, double rtol, int maxit, void* cuda_stream, int* its,
+                      double* relres);
+
 /* Kernel classes timed by droplet_profile (algorithmic bytes per launch in brackets,
  * w = word size of the launch, d = 2 or 3 active axes, N = unknowns of the launch):
  *   0 MG_SMOOTH   red-black Gauss-Seidel half sweep    [(2.5 + d) N w]

@@ -458,3 +458,29 @@ extern "C" void droplet_free(droplet_ctx* c) {
   free_all(c);
   delete c;
 }
+
+extern "C" int droplet_box_solve(const int m[3], const double* D, const double* c0, const double* c1,
+                                 const double* c2, const double* b, double* x, double rtol, int maxit,
+                                 void* cuda_stream, int* its, double* relres) {
+  if (!m || !D || !c0 || !c1 || !b || !x || maxit < 1 || !(rtol > 0.0)) return DROPLET_ERR_ARG;
+  if (m[0] < 1 || m[1] < 1 || m[2] < 1 || (m[2] > 1 && !c2)) return DROPLET_ERR_ARG;
+  long long N = (long long)m[0] * m[1] * m[2];
+  Solver sv;
+  int rc = sv.setup(N, (cudaStream_t)cuda_stream);
+  if (rc) { sv.release(); return rc; }
+  BoxSys bs;
+  for (int a = 0; a < 3; ++a) bs.m[a] = m[a];
+  bs.N = N;
+  bs.D = (double*)D;
+  bs.c[0] = (double*)c0;
+  bs.c[1] = (double*)c1;
+  bs.c[2] = m[2] > 1 ? (double*)c2 : nullptr;
+  bs.b = (double*)b;
+  bs.x = x;
+  SolveStats ss;
+  rc = sv.pcg_jacobi(bs, rtol, maxit, &ss);
+  sv.release();
+  if (its) *its = ss.its;
+  if (relres) *relres = ss.relres;
+  return rc;
+}

@@ -52,7 +52,7 @@ FIELDS = dict(alpha=0, T=1, omega=2, p=3, rhoG=4, u0=5, u1=6, u2=7, mdot=8, mraw
 
 EXPORTS = ["droplet_init", "droplet_step", "droplet_diag", "droplet_field_size", "droplet_get_field",
            "droplet_set_field", "droplet_sync", "droplet_free", "droplet_strerror", "droplet_profile",
-           "droplet_profile_read", "droplet_launch_count"]
+           "droplet_profile_read", "droplet_launch_count", "droplet_box_solve"]
 
 # kernel classes timed by droplet_profile
 KCLASS = dict(mg_smooth=0, spmv=1, update=2, mg_restrict=3, mg_prolong=4, mom_assemble=5, scalar_assemble=6)
@@ -90,6 +90,8 @@ def load_library(path=LIBPATH):
     lib.droplet_profile_read.argtypes = [P, _c_int, ctypes.POINTER(_c_dbl), ctypes.POINTER(ctypes.c_longlong),
                                          ctypes.POINTER(_c_dbl)]
     lib.droplet_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
+    BOX = [ctypes.POINTER(_c_int), P, P, P, P, P, P, _c_dbl, _c_int, P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl)]
+    lib.droplet_box_solve.argtypes = BOX
     lib.droplet_strerror.argtypes = [_c_int]
     lib.droplet_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -214,6 +216,20 @@ def droplet_launch_count(h):
     if rc:
         raise DropletError(rc, "droplet_launch_count")
     return n.value
+
+
+def _box_call(fn, m, D, c0, c1, c2, b, x, rtol, maxit, stream):
+    mm = (_c_int * 3)(*[int(v) for v in m])
+    its, rel = _c_int(), _c_dbl()
+    rc = fn(mm, ctypes.c_void_p(D), ctypes.c_void_p(c0), ctypes.c_void_p(c1),
+            ctypes.c_void_p(c2) if c2 else None, ctypes.c_void_p(b), ctypes.c_void_p(x),
+            float(rtol), int(maxit), ctypes.c_void_p(stream), ctypes.byref(its), ctypes.byref(rel))
+    return rc, its.value, rel.value
+
+
+def droplet_box_solve(m, D, c0, c1, c2, b, x, rtol, maxit, stream):
+    """Device pointers (ints) of the box system; returns (status, iterations, relative residual)."""
+    return _box_call(load_library().droplet_box_solve, m, D, c0, c1, c2, b, x, rtol, maxit, stream)
 
 
 def droplet_sync(h):
