@@ -176,6 +176,29 @@ int droplet_box_solve(const int m[3], const double* D, const double* c0, const d
                       const double* b, double* x, double rtol, int maxit, void* cuda_stream, int* its,
                       double* relres);
 
+/* droplet_box_solve for callers that cannot allocate device memory: a host
+ * framework whose device memory all comes from its own pool or arena, code
+ * that must not call cudaMalloc / cudaFree while other streams are in flight
+ * (those calls can synchronise the device), or a tight loop where allocation
+ * latency matters.  The paper has no counterpart; this is a service of the
+ * library.
+ *
+ * Same arguments, operator, stopping rule and statuses as droplet_box_solve.
+ * The solver's work vectors live in one static device array inside the
+ * library, sized for at most DROPLET_NOALLOC_MAX_UNKNOWNS unknowns (about
+ * 10.5 MB, held by every GPU that loads the library until the process
+ * exits); a larger box is rejected with DROPLET_ERR_SIZE before any work is
+ * enqueued.  The call makes no cudaMalloc, cudaFree, pinned-memory or other
+ * allocating call.  The first call on a device, with that device current,
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it;
+ * make that first call outside any stream capture.  Every call reuses the same
+ * array and initialises what it needs, so calls must not overlap on the GPU:
+ * two solves running at once on different streams would race on the array. */
+#define DROPLET_NOALLOC_MAX_UNKNOWNS 262144
+int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0, const double* c1,
+                              const double* c2, const double* b, double* x, double rtol, int maxit,
+                              void* cuda_stream, int* its, double* relres);
+
 /* Kernel classes timed by droplet_profile (algorithmic bytes per launch in brackets,
  * w = word size of the launch, d = 2 or 3 active axes, N = unknowns of the launch):
  *   0 MG_SMOOTH   red-black Gauss-Seidel half sweep    [(2.5 + d) N w]

@@ -601,4 +601,84 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
   return conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
 }
 
+// ---------------------------------------------------------------- no-allocation box solve
+// Work vectors of droplet_box_solve_noalloc: r, z, p, Ap, 1/diag (5 x max unknowns),
+// reduction partials, CG scalars and the done flag, in one static device array.
+constexpr long long NA_MAX = DROPLET_NOALLOC_MAX_UNKNOWNS;
+constexpr long long NA_PART = (long long)RED_BLOCKS * 8;
+constexpr long long NA_WORDS = 5 * NA_MAX + NA_PART + S_COUNT + 8;
+static __device__ __align__(256) double g_noalloc_ws[NA_WORDS];
+
+// device address of the array, looked up once per device (host code may not use the symbol directly)
+static double* g_noalloc_addr[64] = {nullptr};
+
+static int noalloc_workspace(double** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DROPLET_ERR_CUDA;
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_ws);
+    if (e != cudaSuccess || !ptr) {
+      fprintf(stderr, "droplet: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+      return DROPLET_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = (double*)ptr;
+  }
+  *out = g_noalloc_addr[dev];
+  return 0;
+}
+
 }  // namespace dg
+
+extern "C" int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0, const double* c1,
+                                         const double* c2, const double* b, double* x, double rtol, int maxit,
+                                         void* cuda_stream, int* its, double* relres) {
+  using namespace dg;
+  if (!m || !D || !c0 || !c1 || !b || !x || maxit < 1 || !(rtol > 0.0)) return DROPLET_ERR_ARG;
+  if (m[0] < 1 || m[1] < 1 || m[2] < 1 || (m[2] > 1 && !c2)) return DROPLET_ERR_ARG;
+  long long N = (long long)m[0] * m[1] * m[2];
+  if (N > NA_MAX) {
+    fprintf(stderr, "droplet_box_solve_noalloc: %lld unknowns exceed the static workspace (%lld)\n", N, NA_MAX);
+    return DROPLET_ERR_SIZE;
+  }
+  double* ws = nullptr;
+  int rc = noalloc_workspace(&ws);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double *r = ws, *z = ws + NA_MAX, *p = ws + 2 * NA_MAX, *Ap = ws + 3 * NA_MAX, *idg = ws + 4 * NA_MAX;
+  double* part = ws + 5 * NA_MAX;
+  double* sc = part + NA_PART;
+  int* done = (int*)(sc + S_COUNT);
+  BoxV A;
+  for (int a = 0; a < 3; ++a) A.m[a] = m[a];
+  A.N = N;
+  A.D = D;
+  A.c[0] = c0;
+  A.c[1] = c1;
+  A.c[2] = m[2] > 1 ? c2 : nullptr;
+  int nb = red_grid(N);
+  // every vector, partial, scalar and the flag are written by k_pcg_init / k_fin_init before use
+  k_pcg_init<<<nb, TPB, 0, st>>>(A, b, x, r, z, p, idg, 1, part);
+  k_fin_init<<<1, TPB, 0, st>>>(part, nb, sc, done, rtol * rtol, maxit);
+  double hs[S_COUNT + 1];
+  int d = 0;
+  for (int it = 0; it < maxit; it += 8) {
+    for (int q = 0; q < 8; ++q) {
+      k_spmv_dot<<<nb, TPB, 0, st>>>(A, p, Ap, part, done);
+      k_fin_alpha<<<1, TPB, 0, st>>>(part, nb, sc, done);
+      k_update<<<nb, TPB, 0, st>>>(N, x, r, p, Ap, idg, z, 1, sc, part, done);
+      k_fin_iter<<<1, TPB, 0, st>>>(part, nb, sc, done, 1);
+      k_p_update<<<nb, TPB, 0, st>>>(N, p, z, sc, done);
+    }
+    if (cudaGetLastError() != cudaSuccess) return DROPLET_ERR_CUDA;
+    // pageable host destination: no pinned allocation
+    if (cudaMemcpyAsync(hs, sc, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(&d, done, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return DROPLET_ERR_CUDA;
+    if (d != 0) break;
+  }
+  if (its) *its = (int)hs[S_ITS];
+  if (relres) *relres = hs[S_BB] > 0 ? sqrt(hs[S_RR] / hs[S_BB]) : 0.0;
+  return d == 1 ? 0 : DROPLET_ERR_NOT_CONVERGED;
+}

@@ -52,7 +52,9 @@ FIELDS = dict(alpha=0, T=1, omega=2, p=3, rhoG=4, u0=5, u1=6, u2=7, mdot=8, mraw
 
 EXPORTS = ["droplet_init", "droplet_step", "droplet_diag", "droplet_field_size", "droplet_get_field",
            "droplet_set_field", "droplet_sync", "droplet_free", "droplet_strerror", "droplet_profile",
-           "droplet_profile_read", "droplet_launch_count", "droplet_box_solve"]
+           "droplet_profile_read", "droplet_launch_count", "droplet_box_solve", "droplet_box_solve_noalloc"]
+
+NOALLOC_MAX_UNKNOWNS = 262144
 
 # kernel classes timed by droplet_profile
 KCLASS = dict(mg_smooth=0, spmv=1, update=2, mg_restrict=3, mg_prolong=4, mom_assemble=5, scalar_assemble=6)
@@ -92,6 +94,7 @@ def load_library(path=LIBPATH):
     lib.droplet_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
     BOX = [ctypes.POINTER(_c_int), P, P, P, P, P, P, _c_dbl, _c_int, P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl)]
     lib.droplet_box_solve.argtypes = BOX
+    lib.droplet_box_solve_noalloc.argtypes = BOX
     lib.droplet_strerror.argtypes = [_c_int]
     lib.droplet_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -230,6 +233,12 @@ def _box_call(fn, m, D, c0, c1, c2, b, x, rtol, maxit, stream):
 def droplet_box_solve(m, D, c0, c1, c2, b, x, rtol, maxit, stream):
     """Device pointers (ints) of the box system; returns (status, iterations, relative residual)."""
     return _box_call(load_library().droplet_box_solve, m, D, c0, c1, c2, b, x, rtol, maxit, stream)
+
+
+def droplet_box_solve_noalloc(m, D, c0, c1, c2, b, x, rtol, maxit, stream):
+    """droplet_box_solve with the work vectors in the library's static device array
+    (no device allocation; at most NOALLOC_MAX_UNKNOWNS unknowns; calls must not overlap)."""
+    return _box_call(load_library().droplet_box_solve_noalloc, m, D, c0, c1, c2, b, x, rtol, maxit, stream)
 
 
 def droplet_sync(h):
