@@ -32,6 +32,9 @@ struct droplet_ctx {
   unsigned* hflags = nullptr;
   Solver solver;
   Prof prof;
+  cudaStream_t st2 = nullptr;        // capture stream of the solver loop bodies
+  cudaStream_t own = nullptr;        // internal stream when the caller passed the legacy default stream
+  cudaGraphExec_t exec = nullptr;    // the captured step
   int its_p = 0, its_T = 0, its_w = 0, its_u = 0;
   double res_p = 0.0, t = 0.0;
   long long step = 0;
@@ -124,6 +127,10 @@ static void free_all(droplet_ctx* c) {
   c->hscal = nullptr; c->hflags = nullptr;
   c->solver.release();
   c->prof.destroy();
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->st2) cudaStreamDestroy(c->st2);
+  if (c->own) cudaStreamDestroy(c->own);
+  c->exec = nullptr; c->st2 = nullptr; c->own = nullptr;
 }
 
 static int run_diag(droplet_ctx* c) {
@@ -145,6 +152,13 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
   if (!c) return DROPLET_ERR_NOMEM;
   c->cfg = cfgs[0];
   c->st = (cudaStream_t)cuda_stream;
+  if (!c->st) {
+    // the legacy default stream cannot be captured: work on an internal blocking stream,
+    // which the legacy default stream orders against all other work
+    if (cudaStreamCreate(&c->own) != cudaSuccess) { delete c; return DROPLET_ERR_CUDA; }
+    c->st = c->own;
+  }
+  if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_CUDA; }
   make_geo(c->cfg, c->g);
   make_phys(c->cfg, c->p);
   Geo& g = c->g;
@@ -169,6 +183,11 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
       cudaMallocHost((void**)&c->hflags, sizeof(unsigned)) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_NOMEM; }
   if ((rc = c->solver.setup(N, c->st))) { free_all(c); delete c; return rc; }
   c->solver.prof = &c->prof;
+  c->solver.stream2 = c->st2;
+  if (c->cfg.physics_mask & DROPLET_PHYS_FLOW) {
+    int mm[3] = {g.n[0], g.n[1], g.n[2]};
+    if ((rc = c->solver.prepare_mg(mm, c->cfg.precision == 1))) { free_all(c); delete c; return rc; }
+  }
   cudaStream_t st = c->st;
   int gc = lin_grid(N);
   cudaMemsetAsync(c->scal, 0, sizeof(double) * SC_COUNT, st);
@@ -208,6 +227,7 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
   int gc = lin_grid(N), nb = red_grid(N);
   double* u2 = c->u[2] ? c->u[2] : c->u[0];
   int mask = p.physics;
+  cudaMemsetAsync(c->scal + SC_ITS_P, 0, sizeof(double) * 5, st);
   // S0
   ++g_launches, k_thermo_pin<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->T, c->omega, c->rhoG_old, c->flags);
   // S1, S2
@@ -240,7 +260,6 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
   SolveStats ss;
   int rc;
   // S5 energy
-  c->its_T = 0;
   if ((mask & DROPLET_PHYS_ENERGY) && !p.const_props) {
     {
     ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
@@ -252,12 +271,11 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
     cudaMemcpyAsync(c->bx, c->T, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
     rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
     if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
-    c->its_T = ss.its;
+    c->solver.record(c->scal, SC_ITS_T, -1, 0);
     cudaMemcpyAsync(c->T, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
   }
   // S6 species
   ++g_launches, k_yeq<<<gc, TPB, 0, st>>>(g, p, c->T, c->yq, c->flags);
-  c->its_w = 0;
   if (mask & DROPLET_PHYS_SPECIES) {
     {
     ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
@@ -269,15 +287,13 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
     cudaMemcpyAsync(c->bx, c->omega, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
     rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
     if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
-    c->its_w = ss.its;
+    c->solver.record(c->scal, SC_ITS_W, -1, 0);
     cudaMemcpyAsync(c->omega, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
   } else {
     ++g_launches, k_species_noflow<<<gc, TPB, 0, st>>>(g, c->alpha, c->yq, c->omega);
   }
   ++g_launches, k_rhoG<<<gc, TPB, 0, st>>>(g, p, c->T, c->omega, c->rhoG);
   // S7 - S10
-  c->its_u = 0;
-  c->its_p = 0;
   if (mask & DROPLET_PHYS_FLOW) {
     for (int cc = 0; cc < na; ++cc) {
       int m[3] = {g.n[0], g.n[1], g.n[2]};
@@ -293,7 +309,7 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
       cudaMemsetAsync(c->bx, 0, sizeof(double) * nbx, st);
       rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
       if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
-      c->its_u += ss.its;
+      c->solver.record(c->scal, SC_ITS_U, -1, cc > 0);
       cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, st);
       ++g_launches, k_mom_scatter<<<lin_grid(nfaces(g, cc)), TPB, 0, st>>>(g, p, cc, c->bx, c->us[cc]);
     }
@@ -306,8 +322,7 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
     cudaMemsetAsync(c->bx, 0, sizeof(double) * N, st);
     rc = c->solver.pcg_mg(bs, c->cfg.cg_rtol, c->cfg.cg_maxit, c->cfg.precision == 1, &ss);
     if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
-    c->its_p = ss.its;
-    c->res_p = ss.relres;
+    c->solver.record(c->scal, SC_ITS_P, SC_RES_P, 0);
     cudaMemcpyAsync(c->dp, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
     for (int cc = 0; cc < na; ++cc)
       ++g_launches, k_correct<<<lin_grid(nfaces(g, cc)), TPB, 0, st>>>(g, p, cc, c->us[cc], c->dp, c->rho, c->u[cc]);
@@ -319,18 +334,52 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
   // S11
   if ((rc = run_diag(c))) return rc;
   CKR(cudaGetLastError());
-  c->t += p.dt;
-  c->step += 1;
+  return 0;
+}
+
+// Capture one step (every stage, every solver loop as a conditional WHILE node) into a graph.
+static int capture_step(droplet_ctx* c) {
+  cudaGraph_t graph = nullptr;
+  int nc = 0;
+  CKR(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeRelaxed));
+  c->solver.capturing = true;
+  int rc = one_step(c, &nc);
+  c->solver.capturing = false;
+  cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+  if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+  CKR(e);
+  e = cudaGraphInstantiate(&c->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CKR(e);
   return 0;
 }
 
 extern "C" int droplet_step(droplet_ctx* c, int n_steps) {
   if (!c || n_steps < 0) return DROPLET_ERR_ARG;
   int nc = 0;
-  for (int s = 0; s < n_steps; ++s) {
-    int rc = one_step(c, &nc);
-    if (rc) return rc;
+  CKR(cudaMemsetAsync(c->scal + SC_NC, 0, sizeof(double), c->st));
+  if (c->prof.on) {
+    // timed kernel classes need one event pair per launch: run the stages directly
+    for (int s = 0; s < n_steps; ++s) {
+      int rc = one_step(c, &nc);
+      if (rc) return rc;
+      c->t += c->p.dt;
+      c->step += 1;
+    }
+  } else {
+    if (!c->exec) {
+      int rc = capture_step(c);
+      if (rc) return rc;
+    }
+    for (int s = 0; s < n_steps; ++s) {
+      CKR(cudaGraphLaunch(c->exec, c->st));
+      c->t += c->p.dt;
+      c->step += 1;
+    }
   }
+  CKR(cudaMemcpyAsync(c->hscal + SC_NC, c->scal + SC_NC, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CKR(cudaStreamSynchronize(c->st));
+  if (c->hscal[SC_NC] != 0.0) nc = 1;
   return nc ? DROPLET_ERR_NOT_CONVERGED : 0;
 }
 
@@ -383,8 +432,9 @@ extern "C" int droplet_diag(droplet_ctx* c, int droplet, droplet_diag_t* out) {
   out->alpha_min = s[SC_AMIN];
   out->alpha_max = s[SC_AMAX];
   out->clip_mass = w * s[SC_CLIP];
-  out->its_p = c->its_p; out->its_T = c->its_T; out->its_w = c->its_w; out->its_u = c->its_u;
-  out->res_p = c->res_p;
+  out->its_p = (int)s[SC_ITS_P]; out->its_T = (int)s[SC_ITS_T]; out->its_w = (int)s[SC_ITS_W];
+  out->its_u = (int)s[SC_ITS_U];
+  out->res_p = s[SC_RES_P];
   out->flags = *c->hflags;
   if (!std::isfinite(out->V_l) || !std::isfinite(out->max_u) || !std::isfinite(out->T_s_mean)) return DROPLET_ERR_NONFINITE;
   return 0;

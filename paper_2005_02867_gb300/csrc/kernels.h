@@ -42,6 +42,7 @@ struct ProfScope {
 enum {
   SC_K = 0, SC_CLIP, SC_VAPOUT, SC_DT,
   SC_SUM_ALPHA_V, SC_SUM_MDOT_V, SC_SUM_TG, SC_SUM_G, SC_SUM_VAP, SC_MAXU, SC_AMAX, SC_AMIN,
+  SC_ITS_P, SC_ITS_T, SC_ITS_W, SC_ITS_U, SC_RES_P, SC_NC,
   SC_COUNT
 };
 
@@ -123,10 +124,19 @@ class Solver {
   int pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out);
   // multigrid-preconditioned CG on the pressure box (hierarchy built from s)
   int pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats* out);
+  // allocate the multigrid hierarchy for a box (outside any stream capture)
+  int prepare_mg(const int m[3], int fp32);
+  // store the last solve's iterations (slot_its, accumulated when accumulate = 1), relative
+  // residual (slot_res, may be null) and a not-converged mark (scal[SC_NC]) on the device
+  void record(double* scal, int slot_its, int slot_res, int accumulate);
   cudaStream_t stream = nullptr;
+  cudaStream_t stream2 = nullptr;   // captures the bodies of the device-driven solver loops
+  bool capturing = false;           // the step is being captured into a CUDA graph
   Prof* prof = nullptr;
 
  private:
+  template <typename F>
+  int device_loop(F body);
   int build_mg(const BoxSys& s, int fp32);
   void vcycle(int fp32);
   long long cap = 0;

@@ -184,6 +184,18 @@ __global__ void k_p_update(long long N, double* p, const double* z, const double
     p[id] = z[id] + be * p[id];
 }
 
+// condition of a solver WHILE node: run another iteration while not done
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const int* done) {
+  cudaGraphSetConditional(h, *done == 0 ? 1u : 0u);
+}
+
+__global__ void k_record(const double* sc, const int* done, double* scal, int slot_its, int slot_res, int accumulate) {
+  if (accumulate) scal[slot_its] += sc[S_ITS];
+  else scal[slot_its] = sc[S_ITS];
+  if (slot_res >= 0) scal[slot_res] = sc[S_BB] > 0.0 ? sqrt(sc[S_RR] / sc[S_BB]) : 0.0;
+  if (*done != 1) scal[SC_NC] = 1.0;
+}
+
 // ---------------------------------------------------------------- multigrid kernels
 template <typename T>
 struct LevV {
@@ -394,27 +406,71 @@ static void fill_stats(const double* hsc, int conv, SolveStats* out) {
   out->converged = conv;
 }
 
+void Solver::record(double* scal, int slot_its, int slot_res, int accumulate) {
+  ++g_launches, k_record<<<1, 1, 0, stream>>>(sc, done, scal, slot_its, slot_res, accumulate);
+}
+
+// Inside a stream capture: a conditional WHILE node whose body is one solver
+// iteration (captured from `body` on stream2) followed by the condition update.
+// The loop ends when the done flag is set: converged, or the iteration cap.
+template <typename F>
+int Solver::device_loop(F body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(stream, &cs, nullptr, &g, &deps, &ed, &nd));
+  if (cs != cudaStreamCaptureStatusActive) return DROPLET_ERR_CUDA;
+  cudaGraphConditionalHandle h;
+  CK(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+  ++g_launches, k_set_cond<<<1, 1, 0, stream>>>(h, done);
+  CK(cudaStreamGetCaptureInfo(stream, &cs, nullptr, &g, &deps, &ed, &nd));
+  // the parameter struct holds a union without a default constructor: zeroed raw storage
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(raw);
+  np->type = cudaGraphNodeTypeConditional;
+  np->conditional.handle = h;
+  np->conditional.type = cudaGraphCondTypeWhile;
+  np->conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, deps, ed, nd, np));
+  cudaGraph_t bodyg = np->conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(stream2, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  cudaStream_t saved = stream;
+  stream = stream2;
+  body();
+  ++g_launches, k_set_cond<<<1, 1, 0, stream>>>(h, done);
+  stream = saved;
+  CK(cudaStreamEndCapture(stream2, &bodyg));
+  CK(cudaStreamUpdateCaptureDependencies(stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+  return 0;
+}
+
 int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
   BoxV A = view(s);
   int nb = red_grid(s.N);
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 1, part);
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);
+  auto iteration = [&]() {
+    {
+      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0);
+      ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done);
+    }
+    ++g_launches, k_fin_alpha<<<1, TPB, 0, stream>>>(part, nb, sc, done);
+    {
+      ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0);
+      ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 1, sc, part, done);
+    }
+    ++g_launches, k_fin_iter<<<1, TPB, 0, stream>>>(part, nb, sc, done, 1);
+    ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
+  };
+  if (capturing) return device_loop(iteration);
   const int chunk = 8;
   int conv = 0;
   for (int it = 0; it < maxit; it += chunk) {
-    for (int q = 0; q < chunk; ++q) {
-      {
-        ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0);
-        ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done);
-      }
-      ++g_launches, k_fin_alpha<<<1, TPB, 0, stream>>>(part, nb, sc, done);
-      {
-        ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0);
-        ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 1, sc, part, done);
-      }
-      ++g_launches, k_fin_iter<<<1, TPB, 0, stream>>>(part, nb, sc, done, 1);
-      ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
-    }
+    for (int q = 0; q < chunk; ++q) iteration();
     CK(cudaGetLastError());
     if (poll(hsc, sc, done, stream, maxit, &conv)) break;
   }
@@ -435,43 +491,47 @@ static LevV<T> lv(const MGLevel& L) {
   return v;
 }
 
-int Solver::build_mg(const BoxSys& s, int fp32) {
+int Solver::prepare_mg(const int mm[3], int fp32) {
   size_t es = fp32 ? sizeof(float) : sizeof(double);
-  bool same = (mg_fp32 == fp32 && mg_m[0] == s.m[0] && mg_m[1] == s.m[1] && mg_m[2] == s.m[2]);
-  if (!same) {
-    // level dims: halve while every active dim is even and > 2
-    int m[3] = {s.m[0], s.m[1], s.m[2]};
-    bool d3 = s.m[2] > 1;
-    nlev = 0;
-    size_t total = 0;
-    for (;;) {
-      MGLevel& L = lev[nlev];
-      for (int a = 0; a < 3; ++a) L.m[a] = m[a];
-      L.N = (long long)m[0] * m[1] * m[2];
-      total += (size_t)L.N * es * 6;
-      nlev++;
-      bool can = (m[0] % 2 == 0 && m[1] % 2 == 0 && m[0] > 2 && m[1] > 2) && (!d3 || (m[2] % 2 == 0 && m[2] > 2));
-      if (!can || nlev >= 24) break;
-      m[0] /= 2; m[1] /= 2;
-      if (d3) m[2] /= 2;
-    }
-    cudaFree(mgbuf);
-    mgbuf = nullptr;
-    CK(cudaMalloc(&mgbuf, total + 256 * 6 * nlev));
-    char* ptr = (char*)mgbuf;
-    auto take = [&](long long n) { void* q = ptr; ptr += ((size_t)n * es + 255) / 256 * 256; return q; };
-    for (int l = 0; l < nlev; ++l) {
-      MGLevel& L = lev[l];
-      L.D = take(L.N);
-      L.c[0] = take(L.N);
-      L.c[1] = take(L.N);
-      L.c[2] = d3 ? take(L.N) : nullptr;
-      L.x = take(L.N);
-      L.b = take(L.N);
-    }
-    mg_fp32 = fp32;
-    mg_m[0] = s.m[0]; mg_m[1] = s.m[1]; mg_m[2] = s.m[2];
+  if (mg_fp32 == fp32 && mg_m[0] == mm[0] && mg_m[1] == mm[1] && mg_m[2] == mm[2]) return 0;
+  // level dims: halve while every active dim is even and > 2
+  int m[3] = {mm[0], mm[1], mm[2]};
+  bool d3 = mm[2] > 1;
+  nlev = 0;
+  size_t total = 0;
+  for (;;) {
+    MGLevel& L = lev[nlev];
+    for (int a = 0; a < 3; ++a) L.m[a] = m[a];
+    L.N = (long long)m[0] * m[1] * m[2];
+    total += (size_t)L.N * es * 6;
+    nlev++;
+    bool can = (m[0] % 2 == 0 && m[1] % 2 == 0 && m[0] > 2 && m[1] > 2) && (!d3 || (m[2] % 2 == 0 && m[2] > 2));
+    if (!can || nlev >= 24) break;
+    m[0] /= 2; m[1] /= 2;
+    if (d3) m[2] /= 2;
   }
+  cudaFree(mgbuf);
+  mgbuf = nullptr;
+  CK(cudaMalloc(&mgbuf, total + 256 * 6 * nlev));
+  char* ptr = (char*)mgbuf;
+  auto take = [&](long long n) { void* q = ptr; ptr += ((size_t)n * es + 255) / 256 * 256; return q; };
+  for (int l = 0; l < nlev; ++l) {
+    MGLevel& L = lev[l];
+    L.D = take(L.N);
+    L.c[0] = take(L.N);
+    L.c[1] = take(L.N);
+    L.c[2] = d3 ? take(L.N) : nullptr;
+    L.x = take(L.N);
+    L.b = take(L.N);
+  }
+  mg_fp32 = fp32;
+  mg_m[0] = mm[0]; mg_m[1] = mm[1]; mg_m[2] = mm[2];
+  return 0;
+}
+
+int Solver::build_mg(const BoxSys& s, int fp32) {
+  int rc = prepare_mg(s.m, fp32);
+  if (rc) return rc;
   // level 0 operator: the pressure box in the hierarchy precision
   MGLevel& L0 = lev[0];
   int g0 = lin_grid(L0.N);
@@ -480,9 +540,9 @@ int Solver::build_mg(const BoxSys& s, int fp32) {
     for (int a = 0; a < 3; ++a)
       if (L0.c[a]) ++g_launches, k_cast<float, double><<<g0, TPB, 0, stream>>>(L0.N, (float*)L0.c[a], s.c[a]);
   } else {
-    cudaMemcpyAsync(L0.D, s.D, L0.N * 8, cudaMemcpyDeviceToDevice, stream);
-    for (int a = 0; a < 3; ++a)
-      if (L0.c[a]) cudaMemcpyAsync(L0.c[a], s.c[a], L0.N * 8, cudaMemcpyDeviceToDevice, stream);
+    // FP64 hierarchy: level 0 is the pressure box itself
+    L0.D = s.D;
+    for (int a = 0; a < 3; ++a) L0.c[a] = s.c[a];
   }
   for (int l = 1; l < nlev; ++l) {
     int gl = lin_grid(lev[l].N);
@@ -574,25 +634,27 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
   ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done);
   ++g_launches, k_fin_rz<<<1, TPB, 0, stream>>>(part, nb, sc, done, 1);
   ++g_launches, k_cast_done<double, double><<<g, TPB, 0, stream>>>(s.N, p, z, done);
+  auto iteration = [&]() {
+    {
+      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0);
+      ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done);
+    }
+    ++g_launches, k_fin_alpha<<<1, TPB, 0, stream>>>(part, nb, sc, done);
+    {
+      ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0);
+      ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 0, sc, part, done);
+    }
+    ++g_launches, k_fin_iter<<<1, TPB, 0, stream>>>(part, nb, sc, done, 0);
+    vcycle(fp32);
+    ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done);
+    ++g_launches, k_fin_rz<<<1, TPB, 0, stream>>>(part, nb, sc, done, 0);
+    ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
+  };
+  if (capturing) return device_loop(iteration);
   const int chunk = 4;
   int conv = 0;
   for (int it = 0; it < maxit; it += chunk) {
-    for (int q = 0; q < chunk; ++q) {
-      {
-        ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0);
-        ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done);
-      }
-      ++g_launches, k_fin_alpha<<<1, TPB, 0, stream>>>(part, nb, sc, done);
-      {
-        ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0);
-        ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 0, sc, part, done);
-      }
-      ++g_launches, k_fin_iter<<<1, TPB, 0, stream>>>(part, nb, sc, done, 0);
-      vcycle(fp32);
-      ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done);
-      ++g_launches, k_fin_rz<<<1, TPB, 0, stream>>>(part, nb, sc, done, 0);
-      ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
-    }
+    for (int q = 0; q < chunk; ++q) iteration();
     CK(cudaGetLastError());
     if (poll(hsc, sc, done, stream, maxit, &conv)) break;
   }
