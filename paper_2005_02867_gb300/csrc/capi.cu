@@ -23,11 +23,13 @@ struct droplet_ctx {
   // step work arrays
   double *rhoG_old = nullptr, *mdot = nullptr, *mraw = nullptr, *astar = nullptr, *aL = nullptr, *Rp = nullptr, *Rm = nullptr;
   double *FL[3] = {nullptr, nullptr, nullptr}, *AF[3] = {nullptr, nullptr, nullptr}, *us[3] = {nullptr, nullptr, nullptr};
+  double *xi = nullptr;
   double *rho = nullptr, *mu = nullptr, *kc = nullptr, *cp = nullptr, *Dm = nullptr, *yq = nullptr, *dp = nullptr, *S = nullptr;
   int* adj = nullptr;
   double *bD = nullptr, *bc[3] = {nullptr, nullptr, nullptr}, *brhs = nullptr, *bx = nullptr;
   double *part = nullptr, *psum = nullptr, *pmax = nullptr, *scal = nullptr;
   unsigned* flags = nullptr;
+  int* dirty = nullptr;              // a state field was overwritten: S0 re-evaluates rho_G everywhere
   double* hscal = nullptr;
   unsigned* hflags = nullptr;
   Solver solver;
@@ -63,6 +65,8 @@ static int check_cfg(const droplet_config& c) {
   if (c.cp_v != c.cp_g) return DROPLET_ERR_ARG;   // the j_d (cp_v - cp_g) . grad T term is not carried
   if (c.cg_maxit < 1 || c.helm_maxit < 1 || !(c.cg_rtol > 0.0) || !(c.helm_rtol > 0.0)) return DROPLET_ERR_ARG;
   if (c.precision != 0 && c.precision != 1) return DROPLET_ERR_ARG;
+  long long nn = (long long)c.n[0] * c.n[1] * (c.geom == 0 ? 1 : c.n[2]);
+  if (nn + (long long)c.n[0] * c.n[1] >= (1LL << 31)) return DROPLET_ERR_ARG;   // 32-bit cell and face indices
   return 0;
 }
 
@@ -74,6 +78,7 @@ static void make_geo(const droplet_config& c, Geo& g) {
   g.n[1] = c.n[1];
   g.n[2] = g.axisym ? 1 : c.n[2];
   for (int a = 0; a < 3; ++a) g.h[a] = (a < 2 || !g.axisym) ? c.L[a] / g.n[a] : 1.0;
+  for (int a = 0; a < 3; ++a) g.ih[a] = 1.0 / g.h[a];
   g.hmin = g.axisym ? fmin(g.h[0], g.h[1]) : fmin(g.h[0], fmin(g.h[1], g.h[2]));
   g.s = g.axisym ? 1 : 2;
   int inlet = c.bc_mode == 1 ? BC_FORCED : BC_OPEN;
@@ -99,6 +104,7 @@ static void make_phys(const droplet_config& c, Phys& p) {
   p.M_g = c.M_g; p.cp_g = c.cp_g; p.cp_v = c.cp_v; p.k_g = c.k_g; p.mu_g = c.mu_g; p.D_g = c.D_g;
   p.Tc = c.Tc; p.Pc = c.Pc; p.om = c.omega_ac; p.Tc_g = c.Tc_g; p.Pc_g = c.Pc_g; p.om_g = c.omega_g; p.kij = c.kij;
   p.xi0 = c.xi0; p.Df = c.fiber_radius; p.dt = c.dt; p.C_alpha = c.C_alpha; p.T_perturb = c.T_perturb;
+  p.idt = 1.0 / c.dt;
   p.D_gas = c.D_g * (1.0e5 / c.P);
   p.rhoG_const = c.P * c.M_g / (R_GAS * c.T_amb);
   p.seed = c.seed;
@@ -115,14 +121,14 @@ static int dalloc(double** q, long long n) {
 static void free_all(droplet_ctx* c) {
   double** arrs[] = {&c->alpha, &c->T, &c->omega, &c->pr, &c->rhoG, &c->rhoG_old, &c->mdot, &c->mraw, &c->astar,
                      &c->aL, &c->Rp, &c->Rm, &c->rho, &c->mu, &c->kc, &c->cp, &c->Dm, &c->yq, &c->dp, &c->S,
-                     &c->bD, &c->brhs, &c->bx, &c->part, &c->psum, &c->pmax, &c->scal};
+                     &c->bD, &c->brhs, &c->bx, &c->part, &c->psum, &c->pmax, &c->scal, &c->xi};
   for (auto q : arrs) { cudaFree(*q); *q = nullptr; }
   for (int a = 0; a < 3; ++a) {
     cudaFree(c->u[a]); cudaFree(c->FL[a]); cudaFree(c->AF[a]); cudaFree(c->us[a]); cudaFree(c->bc[a]);
     c->u[a] = c->FL[a] = c->AF[a] = c->us[a] = c->bc[a] = nullptr;
   }
-  cudaFree(c->adj); cudaFree(c->flags);
-  c->adj = nullptr; c->flags = nullptr;
+  cudaFree(c->adj); cudaFree(c->flags); cudaFree(c->dirty);
+  c->adj = nullptr; c->flags = nullptr; c->dirty = nullptr;
   cudaFreeHost(c->hscal); cudaFreeHost(c->hflags);
   c->hscal = nullptr; c->hflags = nullptr;
   c->solver.release();
@@ -136,7 +142,7 @@ static void free_all(droplet_ctx* c) {
 static int run_diag(droplet_ctx* c) {
   Geo& g = c->g;
   int nb = red_grid(g.N);
-  ++g_launches, k_diag<<<nb, TPB, 0, c->st>>>(g, c->alpha, c->T, c->mdot, c->omega, c->rhoG, c->u[0], c->u[1], c->u[2] ? c->u[2] : c->u[0],
+  L_diag(c->st, nb, g, c->alpha, c->T, c->mdot, c->omega, c->rhoG, c->u[0], c->u[1], c->u[2] ? c->u[2] : c->u[0],
                                 c->psum, c->pmax);
   ++g_launches, k_diag_finish<<<1, TPB, 0, c->st>>>(c->psum, c->pmax, nb, c->scal);
   CKR(cudaGetLastError());
@@ -166,7 +172,7 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
   int na = nact(g);
   double** cells[] = {&c->alpha, &c->T, &c->omega, &c->pr, &c->rhoG, &c->rhoG_old, &c->mdot, &c->mraw, &c->astar,
                       &c->aL, &c->Rp, &c->Rm, &c->rho, &c->mu, &c->kc, &c->cp, &c->Dm, &c->yq, &c->dp, &c->S,
-                      &c->bD, &c->brhs, &c->bx};
+                      &c->bD, &c->brhs, &c->bx, &c->xi};
   for (auto q : cells)
     if ((rc = dalloc(q, N))) { free_all(c); delete c; return rc; }
   for (int a = 0; a < 3; ++a) {
@@ -179,6 +185,7 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
   if ((rc = dalloc(&c->part, RED_BLOCKS * 8)) || (rc = dalloc(&c->psum, RED_BLOCKS * 6)) ||
       (rc = dalloc(&c->pmax, RED_BLOCKS * 3)) || (rc = dalloc(&c->scal, SC_COUNT))) { free_all(c); delete c; return rc; }
   if (cudaMalloc((void**)&c->adj, sizeof(int) * N) != cudaSuccess || cudaMalloc((void**)&c->flags, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc((void**)&c->dirty, sizeof(int)) != cudaSuccess ||
       cudaMallocHost((void**)&c->hscal, sizeof(double) * SC_COUNT) != cudaSuccess ||
       cudaMallocHost((void**)&c->hflags, sizeof(unsigned)) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_NOMEM; }
   if ((rc = c->solver.setup(N, c->st))) { free_all(c); delete c; return rc; }
@@ -192,6 +199,7 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
   int gc = lin_grid(N);
   cudaMemsetAsync(c->scal, 0, sizeof(double) * SC_COUNT, st);
   cudaMemsetAsync(c->flags, 0, sizeof(unsigned), st);
+  cudaMemsetAsync(c->dirty, 0, sizeof(int), st);
   cudaMemsetAsync(c->pr, 0, sizeof(double) * N, st);
   cudaMemsetAsync(c->mdot, 0, sizeof(double) * N, st);
   cudaMemsetAsync(c->mraw, 0, sizeof(double) * N, st);
@@ -202,6 +210,7 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
   double dtv = c->cfg.dt;
   cudaMemcpyAsync(c->scal + SC_DT, &dtv, sizeof(double), cudaMemcpyHostToDevice, st);
   ++g_launches, k_init<<<gc, TPB, 0, st>>>(g, c->p, c->alpha, c->T, c->omega, c->rhoG);
+  ++g_launches, k_xi<<<gc, TPB, 0, st>>>(g, c->p, c->xi);
   if (g.bc[g.s][0] == BC_FORCED) {
     // inlet faces (index 0 along the streamwise axis) carry u_inflow: the first n0*n1 entries of u[s] in 3D,
     // the first n0 entries of u[1] in 2D
@@ -229,10 +238,11 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
   int mask = p.physics;
   cudaMemsetAsync(c->scal + SC_ITS_P, 0, sizeof(double) * 5, st);
   // S0
-  ++g_launches, k_thermo_pin<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->T, c->omega, c->rhoG_old, c->flags);
+  ++g_launches, k_thermo_pin<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->T, c->omega, c->rhoG, c->rhoG_old, c->flags, c->dirty);
+  cudaMemsetAsync(c->dirty, 0, sizeof(int), st);
   // S1, S2
   if (mask & DROPLET_PHYS_EVAP) {
-    ++g_launches, k_evap_raw<<<nb, TPB, 0, st>>>(g, p, c->alpha, c->omega, c->rhoG_old, c->u[0], c->u[1], u2, c->mraw, c->adj, c->part, c->flags);
+    L_evap_raw(st, nb, g, p, c->alpha, c->omega, c->rhoG_old, c->u[0], c->u[1], u2, c->mraw, c->adj, c->part, c->flags);
     ++g_launches, k_evap_K<<<1, TPB, 0, st>>>(c->part, nb, c->scal, c->flags);
   } else {
     cudaMemsetAsync(c->mraw, 0, sizeof(double) * N, st);
@@ -242,12 +252,12 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
   // S3
   if (mask & DROPLET_PHYS_FLOW) {
     for (int a = 0; a < na; ++a)
-      ++g_launches, k_adv_faces<<<lin_grid(nfaces(g, a)), TPB, 0, st>>>(g, p, a, c->astar, c->u[a], c->FL[a], c->AF[a]);
+      L_adv_faces(st, lin_grid(nfaces(g, a)), g, p, a, c->astar, c->u[a], c->FL[a], c->AF[a]);
     double* F2 = c->FL[2] ? c->FL[2] : c->FL[0];
     double* A2 = c->AF[2] ? c->AF[2] : c->AF[0];
     ++g_launches, k_adv_low<<<gc, TPB, 0, st>>>(g, c->astar, c->FL[0], c->FL[1], F2, c->aL);
-    ++g_launches, k_adv_limit<<<gc, TPB, 0, st>>>(g, c->astar, c->aL, c->AF[0], c->AF[1], A2, c->Rp, c->Rm);
-    ++g_launches, k_adv_update<<<nb, TPB, 0, st>>>(g, c->aL, c->AF[0], c->AF[1], A2, c->Rp, c->Rm, c->alpha, c->part, c->flags);
+    L_adv_limit(st, gc, g, c->astar, c->aL, c->AF[0], c->AF[1], A2, c->Rp, c->Rm);
+    L_adv_update(st, nb, g, c->aL, c->AF[0], c->AF[1], A2, c->Rp, c->Rm, c->alpha, c->part, c->flags);
   } else {
     ++g_launches, k_alpha_clip_only<<<nb, TPB, 0, st>>>(g, c->astar, c->alpha, c->part);
   }
@@ -263,7 +273,7 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
   if ((mask & DROPLET_PHYS_ENERGY) && !p.const_props) {
     {
     ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
-    ++g_launches, k_scalar_assemble<<<gc, TPB, 0, st>>>(g, p, 0, c->T, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2,
+    L_scalar_assemble(st, gc, g, p, 0, c->T, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2,
                                           c->alpha, c->yq, p.T_amb, c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
     }
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
@@ -275,11 +285,11 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
     cudaMemcpyAsync(c->T, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
   }
   // S6 species
-  ++g_launches, k_yeq<<<gc, TPB, 0, st>>>(g, p, c->T, c->yq, c->flags);
+  ++g_launches, k_yeq<<<gc, TPB, 0, st>>>(g, p, c->T, c->alpha, c->yq, c->flags);
   if (mask & DROPLET_PHYS_SPECIES) {
     {
     ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
-    ++g_launches, k_scalar_assemble<<<gc, TPB, 0, st>>>(g, p, 1, c->omega, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2,
+    L_scalar_assemble(st, gc, g, p, 1, c->omega, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2,
                                           c->alpha, c->yq, 0.0, c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
     }
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
@@ -301,20 +311,20 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
       long long nbx = (long long)m[0] * m[1] * m[2];
       {
       ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, st, (12.0 + 2 * na) * nbx * 8.0);
-      ++g_launches, k_mom_assemble<<<lin_grid(nbx), TPB, 0, st>>>(g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha,
+      L_mom_assemble(st, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi,
                                                     c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
       }
       for (int a = 0; a < 3; ++a) bs.m[a] = m[a];
       bs.N = nbx;
-      cudaMemsetAsync(c->bx, 0, sizeof(double) * nbx, st);
+      L_faces_to_box(st, lin_grid(nbx), g, cc, c->u[cc], c->bx);
       rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
       if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
       c->solver.record(c->scal, SC_ITS_U, -1, cc > 0);
       cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, st);
-      ++g_launches, k_mom_scatter<<<lin_grid(nfaces(g, cc)), TPB, 0, st>>>(g, p, cc, c->bx, c->us[cc]);
+      L_mom_scatter(st, lin_grid(nfaces(g, cc)), g, p, cc, c->bx, c->us[cc]);
     }
     double* us2 = c->us[2] ? c->us[2] : c->us[0];
-    ++g_launches, k_poisson_assemble<<<gc, TPB, 0, st>>>(g, p, c->mdot, c->alpha, c->rhoG_old, c->rhoG, c->u[0], c->u[1], u2,
+    L_poisson_assemble(st, gc, g, p, c->mdot, c->alpha, c->rhoG_old, c->rhoG, c->u[0], c->u[1], u2,
                                            c->us[0], c->us[1], us2, c->rho, c->S, c->bD, c->bc[0], c->bc[1],
                                            na == 3 ? c->bc[2] : c->bc[0], c->brhs);
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
@@ -325,7 +335,7 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
     c->solver.record(c->scal, SC_ITS_P, SC_RES_P, 0);
     cudaMemcpyAsync(c->dp, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
     for (int cc = 0; cc < na; ++cc)
-      ++g_launches, k_correct<<<lin_grid(nfaces(g, cc)), TPB, 0, st>>>(g, p, cc, c->us[cc], c->dp, c->rho, c->u[cc]);
+      L_correct(st, lin_grid(nfaces(g, cc)), g, p, cc, c->us[cc], c->dp, c->rho, c->u[cc]);
     ++g_launches, k_add<<<gc, TPB, 0, st>>>(N, c->pr, c->dp);
   } else {
     cudaMemsetAsync(c->dp, 0, sizeof(double) * N, st);
@@ -498,6 +508,7 @@ extern "C" int droplet_set_field(droplet_ctx* c, int droplet, int field_id, cons
   if (!d || !w) return DROPLET_ERR_ARG;
   if ((size_t)m != n) return DROPLET_ERR_SIZE;
   CKR(cudaMemcpyAsync(d, host, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
+  CKR(cudaMemsetAsync(c->dirty, 0xff, sizeof(int), c->st));
   CKR(cudaStreamSynchronize(c->st));
   return 0;
 }

@@ -29,8 +29,9 @@ struct Geo {
   int s;             // streamwise axis (gravity / inflow): 1 axisym, 2 in 3D
   int bc[3][2];
   double h[3];
+  double ih[3];      // 1 / h
   double hmin;
-  long long N;       // number of cells
+  long long N;       // number of cells (< 2^31)
 };
 
 // Physical parameters used on the device (copied from droplet_config).
@@ -40,6 +41,7 @@ struct Phys {
   double M_g, cp_g, cp_v, k_g, mu_g, D_g;
   double Tc, Pc, om, Tc_g, Pc_g, om_g, kij;
   double xi0, Df, dt, C_alpha, T_perturb;
+  double idt;          // 1 / dt
   double D_gas;        // D_g scaled to the operating pressure
   double rhoG_const;   // frozen gas density of the constant-property check
   unsigned long long seed;
@@ -59,11 +61,14 @@ __device__ __forceinline__ long long fidx(const Geo& g, int a, int i, int j, int
 __host__ __device__ inline long long nfaces(const Geo& g, int a) {
   return (long long)(g.n[0] + (a == 0)) * (g.n[1] + (a == 1)) * (g.n[2] + (a == 2));
 }
+// linear index -> (i, j, k); 32-bit arithmetic (every array here has fewer than 2^31 entries)
 __device__ __forceinline__ void decomp(long long id, int n0, int n1, int& i, int& j, int& k) {
-  i = (int)(id % n0);
-  long long t = id / n0;
-  j = (int)(t % n1);
-  k = (int)(t / n1);
+  unsigned u = (unsigned)id;
+  unsigned t = u / (unsigned)n0;
+  i = (int)(u - t * (unsigned)n0);
+  unsigned t2 = t / (unsigned)n1;
+  j = (int)(t - t2 * (unsigned)n1);
+  k = (int)t2;
 }
 
 __device__ __forceinline__ double rc(const Geo& g, int i) { return (i + 0.5) * g.h[0]; }
@@ -74,12 +79,12 @@ __device__ __forceinline__ double cellV(const Geo& g, int i) {
 // (for a = 0, i is the face index)
 __device__ __forceinline__ double faceA(const Geo& g, int a, int i) {
   if (g.axisym) return a == 0 ? (i * g.h[0]) * g.h[1] : rc(g, i) * g.h[0];
-  return g.h[0] * g.h[1] * g.h[2] / g.h[a];
+  return g.h[0] * g.h[1] * g.h[2] * g.ih[a];
 }
 // area of a face normal to a located at radial coordinate rl (control volumes of the momentum)
 __device__ __forceinline__ double areaN(const Geo& g, int a, double rl) {
   if (g.axisym) return rl * (a == 0 ? g.h[1] : g.h[0]);
-  return g.h[0] * g.h[1] * g.h[2] / g.h[a];
+  return g.h[0] * g.h[1] * g.h[2] * g.ih[a];
 }
 
 // ------------------------------------------------------------------ ghosts
@@ -90,28 +95,39 @@ __device__ __forceinline__ double areaN(const Geo& g, int a, double rl) {
 //            open boundary inletOutlet (fixed amb where the boundary face
 //            velocity points inward, zero gradient otherwise)
 // A fixed face value amb gives the ghost 2 amb - phi_b.
-__device__ inline double cellg(const Geo& g, const double* f, int i, int j, int k, int rule, double amb,
-                               const double* u0, const double* u1, const double* u2) {
-  int q[3] = {i, j, k};
-  for (int a = 0; a < 3; ++a) {
-    if (q[a] < 0 || q[a] >= g.n[a]) {
-      int side = q[a] < 0 ? 0 : 1;
-      q[a] = side ? g.n[a] - 1 : 0;
-      double vb = f[cidx(g, q[0], q[1], q[2])];
-      int kind = g.bc[a][side];
-      if (rule == R_ALPHA) return kind == BC_AXIS ? vb : 0.0;
-      if (rule == R_ZG) return vb;
-      if (kind == BC_AXIS || kind == BC_WALL) return vb;
-      if (kind == BC_FORCED) return 2.0 * amb - vb;
-      int fq[3] = {q[0], q[1], q[2]};
-      fq[a] = side ? g.n[a] : 0;
-      const double* ua = a == 0 ? u0 : (a == 1 ? u1 : u2);
-      double un = ua[fidx(g, a, fq[0], fq[1], fq[2])];
-      double vout = side ? un : -un;
-      return vout < 0.0 ? 2.0 * amb - vb : vb;
-    }
+__device__ __forceinline__ int bc_of(const Geo& g, int a, int side) {
+  int lo = a == 0 ? g.bc[0][0] : (a == 1 ? g.bc[1][0] : g.bc[2][0]);
+  int hi = a == 0 ? g.bc[0][1] : (a == 1 ? g.bc[1][1] : g.bc[2][1]);
+  return side ? hi : lo;
+}
+
+__device__ __forceinline__ double cellg(const Geo& g, const double* f, int i, int j, int k, int rule, double amb,
+                                        const double* u0, const double* u1, const double* u2) {
+  int a, side;
+  if (i < 0) { a = 0; side = 0; i = 0; }
+  else if (i >= g.n[0]) { a = 0; side = 1; i = g.n[0] - 1; }
+  else if (j < 0) { a = 1; side = 0; j = 0; }
+  else if (j >= g.n[1]) { a = 1; side = 1; j = g.n[1] - 1; }
+  else if (k < 0) { a = 2; side = 0; k = 0; }
+  else if (k >= g.n[2]) { a = 2; side = 1; k = g.n[2] - 1; }
+  else return f[cidx(g, i, j, k)];
+  double vb = f[cidx(g, i, j, k)];
+  int kind = bc_of(g, a, side);
+  if (rule == R_ALPHA) return kind == BC_AXIS ? vb : 0.0;
+  if (rule == R_ZG) return vb;
+  if (kind == BC_AXIS || kind == BC_WALL) return vb;
+  if (kind == BC_FORCED) return 2.0 * amb - vb;
+  // open boundary: the boundary face of direction a next to the clamped cell
+  int fi = i, fj = j, fk = k;
+  if (side) {
+    if (a == 0) fi = g.n[0];
+    else if (a == 1) fj = g.n[1];
+    else fk = g.n[2];
   }
-  return f[cidx(g, q[0], q[1], q[2])];
+  const double* ua = a == 0 ? u0 : (a == 1 ? u1 : u2);
+  double un = ua[fidx(g, a, fi, fj, fk)];
+  double vout = side ? un : -un;
+  return vout < 0.0 ? 2.0 * amb - vb : vb;
 }
 
 // Face velocity of direction c with at most one index outside its array
@@ -119,33 +135,32 @@ __device__ inline double cellg(const Geo& g, const double* f, int i, int j, int 
 // forced inlet give u(-k) = 2 u_b - u(k); open boundary u(-k) = u_b.
 // Tangential axis beyond the boundary cells: wall / forced inlet u(-k) =
 // -u(k-1); axis u(-k) = u(k-1); open u(-k) = u(0).
-__device__ inline double ufg(const Geo& g, const double* uc, int c, int i, int j, int k) {
-  int q[3] = {i, j, k};
-  int m[3] = {g.n[0] + (c == 0), g.n[1] + (c == 1), g.n[2] + (c == 2)};
-  for (int a = 0; a < 3; ++a) {
-    if (q[a] < 0 || q[a] >= m[a]) {
-      int side = q[a] < 0 ? 0 : 1;
-      int kind = g.bc[a][side];
-      int kk = side ? q[a] - (m[a] - 1) : -q[a];          // 1 or 2
-      int qb[3] = {q[0], q[1], q[2]};
-      if (a == c) {
-        qb[a] = side ? m[a] - 1 : 0;
-        double ub = uc[fidx(g, c, qb[0], qb[1], qb[2])];
-        if (kind == BC_OPEN) return ub;
-        qb[a] = side ? m[a] - 1 - kk : kk;
-        return 2.0 * ub - uc[fidx(g, c, qb[0], qb[1], qb[2])];
-      } else {
-        if (kind == BC_OPEN) {
-          qb[a] = side ? m[a] - 1 : 0;
-          return uc[fidx(g, c, qb[0], qb[1], qb[2])];
-        }
-        qb[a] = side ? m[a] - kk : kk - 1;
-        double v = uc[fidx(g, c, qb[0], qb[1], qb[2])];
-        return kind == BC_AXIS ? v : -v;
-      }
-    }
+__device__ __forceinline__ double ufg(const Geo& g, const double* uc, int c, int i, int j, int k) {
+  int m0 = g.n[0] + (c == 0), m1 = g.n[1] + (c == 1), m2 = g.n[2] + (c == 2);
+  int a, side, q, m;
+  if (i < 0 || i >= m0) { a = 0; q = i; m = m0; }
+  else if (j < 0 || j >= m1) { a = 1; q = j; m = m1; }
+  else if (k < 0 || k >= m2) { a = 2; q = k; m = m2; }
+  else return uc[fidx(g, c, i, j, k)];
+  side = q < 0 ? 0 : 1;
+  int kind = bc_of(g, a, side);
+  int kk = side ? q - (m - 1) : -q;          // 1 or 2
+  int qb;
+  double sign = 1.0, base = 0.0;
+  if (a == c) {
+    int qe = side ? m - 1 : 0;
+    double ub = uc[fidx(g, c, a == 0 ? qe : i, a == 1 ? qe : j, a == 2 ? qe : k)];
+    if (kind == BC_OPEN) return ub;
+    qb = side ? m - 1 - kk : kk;
+    base = 2.0 * ub;
+    sign = -1.0;
+  } else {
+    if (kind == BC_OPEN) qb = side ? m - 1 : 0;
+    else qb = side ? m - kk : kk - 1;
+    sign = (kind == BC_OPEN || kind == BC_AXIS) ? 1.0 : -1.0;
   }
-  return uc[fidx(g, c, q[0], q[1], q[2])];
+  double v = uc[fidx(g, c, a == 0 ? qb : i, a == 1 ? qb : j, a == 2 ? qb : k)];
+  return base + sign * v;
 }
 
 // clamp a cell index into the domain (zero-gradient access)
@@ -308,7 +323,7 @@ __device__ inline void block_max_store(double (&v)[NV], double* partials) {
 __device__ inline double block_sum_partials(const double* part, int nblk) {
   __shared__ double sh[TPB / 32];
   double t = 0.0;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) t += part[b];
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) t += __ldcg(part + b);
   for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __syncthreads();
@@ -322,7 +337,7 @@ __device__ inline double block_sum_partials(const double* part, int nblk) {
 __device__ inline double block_max_partials(const double* part, int nblk) {
   __shared__ double sh[TPB / 32];
   double t = -1e300;
-  for (int b = threadIdx.x; b < nblk; b += blockDim.x) t = fmax(t, part[b]);
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) t = fmax(t, __ldcg(part + b));
   for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __syncthreads();
@@ -332,6 +347,18 @@ __device__ inline double block_max_partials(const double* part, int nblk) {
   if (threadIdx.x == 0)
     for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r = fmax(r, sh[q]);
   return r;
+}
+
+// True in the last block of the grid to reach this point (threadfence + atomic
+// ticket; no waiting).  The block that gets the last ticket sees every other
+// block's partials and resets the counter for the next launch.
+__device__ __forceinline__ bool last_block(unsigned* cnt) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) am_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
+  __syncthreads();
+  return am_last;
 }
 
 inline int red_grid(long long n) {

@@ -48,45 +48,42 @@ enum {
 
 // ---- step kernels (step_kernels.cu)
 __global__ void k_init(Geo g, Phys p, double* alpha, double* T, double* omega, double* rhoG);
-__global__ void k_thermo_pin(Geo g, Phys p, const double* alpha, const double* T, double* omega, double* rhoG_old,
-                             unsigned* flags);
-__global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG,
-                           const double* u0, const double* u1, const double* u2, double* mraw, int* adj,
-                           double* partials, unsigned* flags);
+__global__ void k_xi(Geo g, Phys p, double* xi);
+__global__ void k_thermo_pin(Geo g, Phys p, const double* alpha, const double* T, double* omega,
+                             const double* rhoG, double* rhoG_old, unsigned* flags, const int* dirty);
+
 __global__ void k_evap_K(const double* partials, int nblk, double* scal, unsigned* flags);
 __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double* mraw, const double* scal,
                                double* mdot, double* alpha_star, unsigned* flags);
-__global__ void k_adv_faces(Geo g, Phys p, int a, const double* as, const double* ua, double* FL, double* AF);
+
 __global__ void k_adv_low(Geo g, const double* as, const double* F0, const double* F1, const double* F2, double* aL);
-__global__ void k_adv_limit(Geo g, const double* as, const double* aL, const double* A0, const double* A1,
-                            const double* A2, double* Rp, double* Rm);
-__global__ void k_adv_update(Geo g, const double* aL, const double* A0, const double* A1, const double* A2,
-                             const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags);
+
 __global__ void k_clip_finish(const double* partials, int nblk, double* scal, unsigned* flags);
 __global__ void k_alpha_clip_only(Geo g, const double* as, double* alpha, double* partials);
 __global__ void k_props(Geo g, Phys p, const double* alpha, const double* rhoG, const double* omega, double* rho,
                         double* mu, double* kc, double* cp, double* D);
-__global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
-                                  const double* kc, const double* D, const double* mdot, const double* u0,
-                                  const double* u1, const double* u2, const double* alpha_new, const double* pinv,
-                                  double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs);
-__global__ void k_yeq(Geo g, Phys p, const double* T, double* yq, unsigned* flags);
+
+__global__ void k_yeq(Geo g, Phys p, const double* T, const double* alpha, double* yq, unsigned* flags);
 __global__ void k_species_noflow(Geo g, const double* alpha_new, const double* yq, double* omega);
 __global__ void k_rhoG(Geo g, Phys p, const double* T, const double* w, double* rhoG);
-__global__ void k_mom_assemble(Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2,
-                               const double* rho, const double* mu, const double* pr, const double* alpha,
-                               double* Dg, double* c0, double* c1, double* c2, double* rhs);
-__global__ void k_mom_scatter(Geo g, Phys p, int c, const double* x, double* us);
-__global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo,
-                                   const double* rgn, const double* u0, const double* u1, const double* u2,
-                                   const double* us0, const double* us1, const double* us2, const double* rho,
-                                   double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs);
-__global__ void k_correct(Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u);
+
 __global__ void k_add(long long n, double* y, const double* x);
-__global__ void k_diag(Geo g, const double* alpha, const double* T, const double* mdot, const double* omega,
-                       const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum,
-                       double* pmax);
+
 __global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal);
+
+// launch wrappers of the kernels templated on the active axes / face direction (step_kernels.cu)
+void L_evap_raw(cudaStream_t st, int grid, Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* mraw, int* adj, double* partials, unsigned* flags);
+void L_adv_faces(cudaStream_t st, int grid, Geo g, Phys p, int a, const double* as, const double* ua, double* FL, double* AF);
+void L_adv_limit(cudaStream_t st, int grid, Geo g, const double* as, const double* aL, const double* A0, const double* A1, const double* A2, double* Rp, double* Rm);
+void L_adv_update(cudaStream_t st, int grid, Geo g, const double* aL, const double* A0, const double* A1, const double* A2, const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags);
+void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs);
+void L_mom_assemble(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs);
+void L_mom_scatter(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* x, double* us);
+void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo, const double* rgn, const double* u0, const double* u1, const double* u2, const double* us0, const double* us1, const double* us2, const double* rho, double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs);
+void L_correct(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u);
+void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax);
+
+void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x);
 
 // ---- linear solvers (solver.cu)
 // Box operator on dims m: y_P = D_P x_P + sum_a [c_a[P](x_P - x_{P-e_a}) + c_a[P+e_a](x_P - x_{P+e_a})],
@@ -113,6 +110,7 @@ struct MGLevel {
   void* c[3];
   void* x;
   void* b;
+  void* idg;        // 1 / (D + sum of adjacent couplings), used by the smoother
 };
 
 class Solver {
@@ -144,6 +142,7 @@ class Solver {
   double* part = nullptr;       // reduction partials
   double* sc = nullptr;         // device scalars
   int* done = nullptr;
+  unsigned* cnt = nullptr;      // last-block ticket counter of the fused reductions
   double* hsc = nullptr;        // pinned host copy of the scalars
   // multigrid
   int nlev = 0;

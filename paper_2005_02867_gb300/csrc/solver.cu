@@ -23,14 +23,16 @@ struct BoxV {
 };
 
 __device__ __forceinline__ void bdecomp(const int m[3], long long id, int& i, int& j, int& k) {
-  i = (int)(id % m[0]);
-  long long t = id / m[0];
-  j = (int)(t % m[1]);
-  k = (int)(t / m[1]);
+  unsigned u = (unsigned)id;
+  unsigned t = u / (unsigned)m[0];
+  i = (int)(u - t * (unsigned)m[0]);
+  unsigned t2 = t / (unsigned)m[1];
+  j = (int)(t - t2 * (unsigned)m[1]);
+  k = (int)t2;
 }
 
 // y = A x at cell id, and the total diagonal D + sum of adjacent couplings
-template <typename T, typename TX>
+template <typename T, typename TX, bool DT = true>
 __device__ __forceinline__ void box_row(const int m[3], const T* D, const T* const c[3], const TX* x, long long id,
                                         int i, int j, int k, double& ax, double& dtot) {
   double xp = (double)x[id];
@@ -38,17 +40,18 @@ __device__ __forceinline__ void box_row(const int m[3], const T* D, const T* con
   double dt = (double)D[id];
   int q[3] = {i, j, k};
   long long st[3] = {1, (long long)m[0], (long long)m[0] * m[1]};
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     if (!c[a] || m[a] < 2) continue;
     if (q[a] > 0) {
       double cl = (double)c[a][id];
       y += cl * (xp - (double)x[id - st[a]]);
-      dt += cl;
+      if (DT) dt += cl;
     }
     if (q[a] < m[a] - 1) {
       double ch = (double)c[a][id + st[a]];
       y += ch * (xp - (double)x[id + st[a]]);
-      dt += ch;
+      if (DT) dt += ch;
     }
   }
   ax = y;
@@ -98,18 +101,28 @@ __global__ void k_fin_init(const double* part, int nblk, double* sc, int* done, 
   }
 }
 
-__global__ void k_spmv_dot(BoxV A, const double* p, double* Ap, double* part, const int* done) {
+// Ap = A p and p.Ap; with a counter (cnt != null) the last block also sets alpha = rz / pAp
+__global__ void k_spmv_dot(BoxV A, const double* p, double* Ap, double* part, const int* done, double* sc,
+                           unsigned* cnt) {
   if (*done) return;
   double acc[1] = {0.0};
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < A.N; id += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     bdecomp(A.m, id, i, j, k);
     double ax, dt;
-    box_row<double, double>(A.m, A.D, A.c, p, id, i, j, k, ax, dt);
+    box_row<double, double, false>(A.m, A.D, A.c, p, id, i, j, k, ax, dt);
     Ap[id] = ax;
     acc[0] += p[id] * ax;
   }
   block_sum_store<1>(acc, part);
+  if (cnt && last_block(cnt)) {
+    double pap = block_sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+      sc[S_PAP] = pap;
+      sc[S_ALPHA] = sc[S_RZ] / pap;
+      *cnt = 0u;
+    }
+  }
 }
 
 __global__ void k_fin_alpha(const double* part, int nblk, double* sc, const int* done) {
@@ -123,7 +136,7 @@ __global__ void k_fin_alpha(const double* part, int nblk, double* sc, const int*
 
 // x += alpha p, r -= alpha Ap; Jacobi: z = r / diag and r.z; both: r.r
 __global__ void k_update(long long N, double* x, double* r, const double* p, const double* Ap, const double* idg,
-                         double* z, int jacobi, const double* sc, double* part, const int* done) {
+                         double* z, int jacobi, double* sc, double* part, int* done, unsigned* cnt) {
   if (*done) return;
   double al = sc[S_ALPHA];
   double acc[2] = {0, 0};
@@ -139,6 +152,23 @@ __global__ void k_update(long long N, double* x, double* r, const double* p, con
     }
   }
   block_sum_store<2>(acc, part);
+  if (cnt && last_block(cnt)) {
+    // iteration count, convergence test, and (Jacobi) beta: the work of k_fin_iter
+    double rz = block_sum_partials(part, gridDim.x);
+    __syncthreads();
+    double rr = block_sum_partials(part + gridDim.x, gridDim.x);
+    if (threadIdx.x == 0) {
+      sc[S_ITS] += 1.0;
+      sc[S_RR] = rr;
+      if (rr <= sc[S_TOL2] * sc[S_BB]) *done = 1;
+      else if (sc[S_ITS] >= sc[S_MAXIT]) *done = 2;
+      if (jacobi) {
+        sc[S_BETA] = rz / sc[S_RZ];
+        sc[S_RZ] = rz;
+      }
+      *cnt = 0u;
+    }
+  }
 }
 
 // iteration count, convergence test, and (Jacobi) beta
@@ -159,12 +189,22 @@ __global__ void k_fin_iter(const double* part, int nblk, double* sc, int* done, 
   }
 }
 
-__global__ void k_dot_rz(long long N, const double* r, const double* z, double* part, const int* done) {
+// r.z; with a counter the last block also sets beta = rz_new / rz (first = 1: only rz)
+__global__ void k_dot_rz(long long N, const double* r, const double* z, double* part, const int* done, double* sc,
+                         unsigned* cnt, int first) {
   if (*done) return;
   double acc[1] = {0.0};
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N; id += (long long)gridDim.x * blockDim.x)
     acc[0] += r[id] * z[id];
   block_sum_store<1>(acc, part);
+  if (cnt && last_block(cnt)) {
+    double rz = block_sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+      sc[S_BETA] = first ? 0.0 : rz / sc[S_RZ];
+      sc[S_RZ] = rz;
+      *cnt = 0u;
+    }
+  }
 }
 
 // beta = rz_new / rz (first == 1: only store rz)
@@ -205,9 +245,28 @@ struct LevV {
   const T* c[3];
   T* x;
   const T* b;
+  const T* idg;
 };
 
-// red-black Gauss-Seidel half sweep of colour `col`; first = 1: neighbours taken as 0
+// one cell of a red-black Gauss-Seidel half sweep: x_P = (b_P + sum c x_nb) / diag_total
+// (first = 1: neighbours taken as 0).  Arithmetic in the hierarchy precision T.
+template <typename T>
+__device__ __forceinline__ void gs_cell(const LevV<T>& L, long long id, int i, int j, int k, int first) {
+  long long st1 = L.m[0], st2 = (long long)L.m[0] * L.m[1];
+  T s = L.b[id];
+  if (!first) {
+    if (i > 0) s += L.c[0][id] * L.x[id - 1];
+    if (i < L.m[0] - 1) s += L.c[0][id + 1] * L.x[id + 1];
+    if (j > 0) s += L.c[1][id] * L.x[id - st1];
+    if (j < L.m[1] - 1) s += L.c[1][id + st1] * L.x[id + st1];
+    if (L.c[2]) {
+      if (k > 0) s += L.c[2][id] * L.x[id - st2];
+      if (k < L.m[2] - 1) s += L.c[2][id + st2] * L.x[id + st2];
+    }
+  }
+  L.x[id] = s * L.idg[id];
+}
+
 template <typename T>
 __global__ void k_mg_smooth(LevV<T> L, int col, int first, const int* done) {
   if (*done) return;
@@ -216,24 +275,42 @@ __global__ void k_mg_smooth(LevV<T> L, int col, int first, const int* done) {
   int i, j, k;
   bdecomp(L.m, id, i, j, k);
   if (((i + j + k) & 1) != col) return;
+  gs_cell<T>(L, id, i, j, k, first);
+}
+
+// inverse total diagonal of a level
+template <typename T>
+__global__ void k_mg_idg(LevV<T> L, T* idg) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= L.N) return;
+  int i, j, k;
+  bdecomp(L.m, id, i, j, k);
   long long st[3] = {1, (long long)L.m[0], (long long)L.m[0] * L.m[1]};
   int q[3] = {i, j, k};
-  double s = (double)L.b[id];
   double dt = (double)L.D[id];
   for (int a = 0; a < 3; ++a) {
     if (!L.c[a] || L.m[a] < 2) continue;
-    if (q[a] > 0) {
-      double cl = (double)L.c[a][id];
-      dt += cl;
-      if (!first) s += cl * (double)L.x[id - st[a]];
-    }
-    if (q[a] < L.m[a] - 1) {
-      double ch = (double)L.c[a][id + st[a]];
-      dt += ch;
-      if (!first) s += ch * (double)L.x[id + st[a]];
-    }
+    if (q[a] > 0) dt += (double)L.c[a][id];
+    if (q[a] < L.m[a] - 1) dt += (double)L.c[a][id + st[a]];
   }
-  L.x[id] = (T)(s / dt);
+  idg[id] = (T)(1.0 / dt);
+}
+
+// residual b - A x of one cell in the hierarchy precision
+template <typename T>
+__device__ __forceinline__ T mg_resid(const LevV<T>& L, long long id, int i, int j, int k) {
+  long long st1 = L.m[0], st2 = (long long)L.m[0] * L.m[1];
+  T xp = L.x[id];
+  T y = L.D[id] * xp;
+  if (i > 0) y += L.c[0][id] * (xp - L.x[id - 1]);
+  if (i < L.m[0] - 1) y += L.c[0][id + 1] * (xp - L.x[id + 1]);
+  if (j > 0) y += L.c[1][id] * (xp - L.x[id - st1]);
+  if (j < L.m[1] - 1) y += L.c[1][id + st1] * (xp - L.x[id + st1]);
+  if (L.c[2]) {
+    if (k > 0) y += L.c[2][id] * (xp - L.x[id - st2]);
+    if (k < L.m[2] - 1) y += L.c[2][id + st2] * (xp - L.x[id + st2]);
+  }
+  return L.b[id] - y;
 }
 
 // residual of the fine level restricted (summed) into the coarse right-hand side
@@ -245,17 +322,15 @@ __global__ void k_mg_restrict(LevV<T> F, LevV<T> C, const int* done) {
   int I, J, K;
   bdecomp(C.m, id, I, J, K);
   int kz = F.m[2] > 1 ? 2 : 1;
-  double s = 0.0;
+  T s = 0;
   for (int dk = 0; dk < kz; ++dk)
     for (int dj = 0; dj < 2; ++dj)
       for (int di = 0; di < 2; ++di) {
         int i = 2 * I + di, j = 2 * J + dj, k = kz == 2 ? 2 * K + dk : 0;
         long long fi = (long long)i + (long long)F.m[0] * ((long long)j + (long long)F.m[1] * k);
-        double ax, dt;
-        box_row<T, T>(F.m, F.D, F.c, F.x, fi, i, j, k, ax, dt);
-        s += (double)F.b[fi] - ax;
+        s += mg_resid<T>(F, fi, i, j, k);
       }
-  ((T*)C.b)[id] = (T)s;
+  ((T*)C.b)[id] = s;
 }
 
 template <typename T>
@@ -267,7 +342,7 @@ __global__ void k_mg_prolong(LevV<T> F, LevV<T> C, const int* done) {
   bdecomp(F.m, id, i, j, k);
   int K = F.m[2] > 1 ? k / 2 : 0;
   long long ci = (long long)(i / 2) + (long long)C.m[0] * ((long long)(j / 2) + (long long)C.m[1] * K);
-  F.x[id] = (T)((double)F.x[id] + (double)C.x[ci]);
+  F.x[id] = F.x[id] + C.x[ci];
 }
 
 // coarse operator: couplings = 1/2 sum of the fine couplings across the coarse face, D = 1/2 sum
@@ -293,6 +368,81 @@ __global__ void k_mg_coarsen(LevV<T> F, LevV<T> C, T* Dc, T* c0, T* c1, T* c2) {
   Dc[id] = (T)(0.5 * d);
   for (int a = 0; a < 3; ++a)
     if (cc[a]) cc[a][id] = (T)(0.5 * s[a]);
+}
+
+// V-cycle of levels l0 .. nl-1 inside one thread block (small levels: one launch
+// instead of ten per level).  Same operations and order as the per-level kernels.
+constexpr int TAIL_MAX_CELLS = 8192;
+constexpr int TAIL_THREADS = 1024;
+template <typename T>
+struct TailLevels {
+  LevV<T> L[24];
+};
+
+template <typename T>
+__device__ void tail_smooth(const LevV<T>& L, int col, int first) {
+  for (long long id = threadIdx.x; id < L.N; id += blockDim.x) {
+    int i, j, k;
+    bdecomp(L.m, id, i, j, k);
+    if (((i + j + k) & 1) == col) gs_cell<T>(L, id, i, j, k, first);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels<T> TL, int l0, int nl, int nu, int ncoarse,
+                                                          const int* done) {
+  if (*done) return;
+  for (int l = l0; l < nl - 1; ++l) {
+    const LevV<T>& F = TL.L[l];
+    for (int s = 0; s < nu; ++s) {
+      tail_smooth<T>(F, 0, s == 0);
+      tail_smooth<T>(F, 1, 0);
+    }
+    const LevV<T>& C = TL.L[l + 1];
+    int kz = F.m[2] > 1 ? 2 : 1;
+    for (long long id = threadIdx.x; id < C.N; id += blockDim.x) {
+      int I, J, K;
+      bdecomp(C.m, id, I, J, K);
+      T s = 0;
+      for (int dk = 0; dk < kz; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+          for (int di = 0; di < 2; ++di) {
+            int i = 2 * I + di, j = 2 * J + dj, k = kz == 2 ? 2 * K + dk : 0;
+            long long fi = (long long)i + (long long)F.m[0] * ((long long)j + (long long)F.m[1] * k);
+            s += mg_resid<T>(F, fi, i, j, k);
+          }
+      ((T*)C.b)[id] = s;
+    }
+    __syncthreads();
+  }
+  {
+    const LevV<T>& L = TL.L[nl - 1];
+    for (int s = 0; s < ncoarse; ++s) {
+      tail_smooth<T>(L, 0, s == 0);
+      tail_smooth<T>(L, 1, 0);
+    }
+    for (int s = 0; s < ncoarse; ++s) {
+      tail_smooth<T>(L, 1, 0);
+      tail_smooth<T>(L, 0, 0);
+    }
+  }
+  for (int l = nl - 2; l >= l0; --l) {
+    const LevV<T>& F = TL.L[l];
+    const LevV<T>& C = TL.L[l + 1];
+    for (long long id = threadIdx.x; id < F.N; id += blockDim.x) {
+      int i, j, k;
+      bdecomp(F.m, id, i, j, k);
+      int K = F.m[2] > 1 ? k / 2 : 0;
+      long long ci = (long long)(i / 2) + (long long)C.m[0] * ((long long)(j / 2) + (long long)C.m[1] * K);
+      F.x[id] = F.x[id] + C.x[ci];
+    }
+    __syncthreads();
+    for (int s = 0; s < nu; ++s) {
+      tail_smooth<T>(F, 1, 0);
+      tail_smooth<T>(F, 0, 0);
+    }
+  }
 }
 
 template <typename TO, typename TI>
@@ -369,13 +519,16 @@ int Solver::setup(long long maxN, cudaStream_t s) {
   CK(cudaMalloc(&part, sizeof(double) * RED_BLOCKS * 8));
   CK(cudaMalloc(&sc, sizeof(double) * S_COUNT));
   CK(cudaMalloc(&done, sizeof(int)));
+  CK(cudaMalloc(&cnt, sizeof(unsigned)));
+  CK(cudaMemset(cnt, 0, sizeof(unsigned)));
   CK(cudaMallocHost(&hsc, sizeof(double) * (S_COUNT + 2)));
   return 0;
 }
 
 void Solver::release() {
   cudaFree(r); cudaFree(z); cudaFree(p); cudaFree(Ap); cudaFree(idg);
-  cudaFree(part); cudaFree(sc); cudaFree(done); cudaFreeHost(hsc);
+  cudaFree(part); cudaFree(sc); cudaFree(done); cudaFree(cnt); cudaFreeHost(hsc);
+  cnt = nullptr;
   cudaFree(mgbuf);
   r = z = p = Ap = idg = part = sc = nullptr;
   done = nullptr; hsc = nullptr; mgbuf = nullptr;
@@ -456,14 +609,12 @@ int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out)
   auto iteration = [&]() {
     {
       ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0);
-      ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done);
+      ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt);
     }
-    ++g_launches, k_fin_alpha<<<1, TPB, 0, stream>>>(part, nb, sc, done);
     {
       ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0);
-      ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 1, sc, part, done);
+      ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 1, sc, part, done, cnt);
     }
-    ++g_launches, k_fin_iter<<<1, TPB, 0, stream>>>(part, nb, sc, done, 1);
     ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
   };
   if (capturing) return device_loop(iteration);
@@ -488,6 +639,7 @@ static LevV<T> lv(const MGLevel& L) {
   v.D = (const T*)L.D;
   v.x = (T*)L.x;
   v.b = (const T*)L.b;
+  v.idg = (const T*)L.idg;
   return v;
 }
 
@@ -503,7 +655,7 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
     MGLevel& L = lev[nlev];
     for (int a = 0; a < 3; ++a) L.m[a] = m[a];
     L.N = (long long)m[0] * m[1] * m[2];
-    total += (size_t)L.N * es * 6;
+    total += (size_t)L.N * es * 7;
     nlev++;
     bool can = (m[0] % 2 == 0 && m[1] % 2 == 0 && m[0] > 2 && m[1] > 2) && (!d3 || (m[2] % 2 == 0 && m[2] > 2));
     if (!can || nlev >= 24) break;
@@ -512,7 +664,7 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
   }
   cudaFree(mgbuf);
   mgbuf = nullptr;
-  CK(cudaMalloc(&mgbuf, total + 256 * 6 * nlev));
+  CK(cudaMalloc(&mgbuf, total + 256 * 7 * nlev));
   char* ptr = (char*)mgbuf;
   auto take = [&](long long n) { void* q = ptr; ptr += ((size_t)n * es + 255) / 256 * 256; return q; };
   for (int l = 0; l < nlev; ++l) {
@@ -523,6 +675,7 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
     L.c[2] = d3 ? take(L.N) : nullptr;
     L.x = take(L.N);
     L.b = take(L.N);
+    L.idg = take(L.N);
   }
   mg_fp32 = fp32;
   mg_m[0] = mm[0]; mg_m[1] = mm[1]; mg_m[2] = mm[2];
@@ -554,6 +707,11 @@ int Solver::build_mg(const BoxSys& s, int fp32) {
       ++g_launches, k_mg_coarsen<double><<<gl, TPB, 0, stream>>>(F, C, (double*)lev[l].D, (double*)lev[l].c[0], (double*)lev[l].c[1], (double*)lev[l].c[2]);
     }
   }
+  for (int l = 0; l < nlev; ++l) {
+    int gl = lin_grid(lev[l].N);
+    if (fp32) ++g_launches, k_mg_idg<float><<<gl, TPB, 0, stream>>>(lv<float>(lev[l]), (float*)lev[l].idg);
+    else ++g_launches, k_mg_idg<double><<<gl, TPB, 0, stream>>>(lv<double>(lev[l]), (double*)lev[l].idg);
+  }
   CK(cudaGetLastError());
   return 0;
 }
@@ -569,9 +727,11 @@ template <typename T>
 static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaStream_t st) {
   const int nu = 2;          // smoothing sweeps (red + black) before and after
   const int ncoarse = 16;    // symmetric sweep pairs on the coarsest level
-  for (int l = 0; l < nlev - 1; ++l) {
+  // levels from `lt` on run inside one block (k_mg_tail)
+  int lt = nlev - 1;
+  while (lt > 0 && lev[lt - 1].N <= TAIL_MAX_CELLS) --lt;
+  for (int l = 0; l < lt; ++l) {
     LevV<T> L = lv<T>(lev[l]);
-    int g = lin_grid(L.N);
     for (int s = 0; s < nu; ++s) {
       smooth<T>(prof, L, 0, s == 0, done, st);
       smooth<T>(prof, L, 1, 0, done, st);
@@ -583,19 +743,10 @@ static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaSt
       ++g_launches, k_mg_restrict<T><<<lin_grid(C.N), TPB, 0, st>>>(L, C, done);
     }
   }
-  {
-    LevV<T> L = lv<T>(lev[nlev - 1]);
-    int g = lin_grid(L.N);
-    for (int s = 0; s < ncoarse; ++s) {
-      smooth<T>(prof, L, 0, s == 0, done, st);
-      smooth<T>(prof, L, 1, 0, done, st);
-    }
-    for (int s = 0; s < ncoarse; ++s) {
-      smooth<T>(prof, L, 1, 0, done, st);
-      smooth<T>(prof, L, 0, 0, done, st);
-    }
-  }
-  for (int l = nlev - 2; l >= 0; --l) {
+  TailLevels<T> TL;
+  for (int l = 0; l < nlev; ++l) TL.L[l] = lv<T>(lev[l]);
+  ++g_launches, k_mg_tail<T><<<1, TAIL_THREADS, 0, st>>>(TL, lt, nlev, nu, ncoarse, done);
+  for (int l = lt - 1; l >= 0; --l) {
     LevV<T> L = lv<T>(lev[l]), C = lv<T>(lev[l + 1]);
     int g = lin_grid(L.N);
     {
@@ -631,23 +782,19 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);
   vcycle(fp32);
-  ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done);
-  ++g_launches, k_fin_rz<<<1, TPB, 0, stream>>>(part, nb, sc, done, 1);
+  ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done, sc, cnt, 1);
   ++g_launches, k_cast_done<double, double><<<g, TPB, 0, stream>>>(s.N, p, z, done);
   auto iteration = [&]() {
     {
       ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0);
-      ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done);
+      ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt);
     }
-    ++g_launches, k_fin_alpha<<<1, TPB, 0, stream>>>(part, nb, sc, done);
     {
       ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0);
-      ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 0, sc, part, done);
+      ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 0, sc, part, done, cnt);
     }
-    ++g_launches, k_fin_iter<<<1, TPB, 0, stream>>>(part, nb, sc, done, 0);
     vcycle(fp32);
-    ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done);
-    ++g_launches, k_fin_rz<<<1, TPB, 0, stream>>>(part, nb, sc, done, 0);
+    ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done, sc, cnt, 0);
     ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
   };
   if (capturing) return device_loop(iteration);
@@ -726,9 +873,9 @@ extern "C" int droplet_box_solve_noalloc(const int m[3], const double* D, const 
   int d = 0;
   for (int it = 0; it < maxit; it += 8) {
     for (int q = 0; q < 8; ++q) {
-      k_spmv_dot<<<nb, TPB, 0, st>>>(A, p, Ap, part, done);
+      k_spmv_dot<<<nb, TPB, 0, st>>>(A, p, Ap, part, done, sc, nullptr);
       k_fin_alpha<<<1, TPB, 0, st>>>(part, nb, sc, done);
-      k_update<<<nb, TPB, 0, st>>>(N, x, r, p, Ap, idg, z, 1, sc, part, done);
+      k_update<<<nb, TPB, 0, st>>>(N, x, r, p, Ap, idg, z, 1, sc, part, done, nullptr);
       k_fin_iter<<<1, TPB, 0, st>>>(part, nb, sc, done, 1);
       k_p_update<<<nb, TPB, 0, st>>>(N, p, z, sc, done);
     }

@@ -94,24 +94,45 @@ __global__ void k_init(Geo g, Phys p, double* alpha, double* T, double* omega, d
   rhoG[id] = rho_gas(p, t, w);
 }
 
+// centripetal potential xi = xi0 D_f / (2 max(r, D_f)) at the cell centres (Eq. magneticpotential);
+// static, computed once
+__global__ void k_xi(Geo g, Phys p, double* xi) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  int q[3];
+  decomp(id, g.n[0], g.n[1], q[0], q[1], q[2]);
+  int na = nact(g);
+  double d2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    if (a >= na) break;
+    double x = (q[a] + 0.5) * g.h[a] - p.xc[a];
+    d2 = d2 + x * x;
+  }
+  xi[id] = p.xi0 * p.Df / (2.0 * fmax(sqrt(d2), p.Df));
+}
+
 // ============================================================== S0 thermodynamics
 // Saturation value written into the liquid (alpha >= 1/2), gas density at T^n.
+// The state rho_G left by the previous step is rho_gas(T, omega) of the same T and
+// omega (and the pinned values Y_eq(T) are unchanged), so only liquid cells are
+// re-evaluated, unless a field was overwritten since (*dirty != 0).
 __global__ void k_thermo_pin(Geo g, Phys p, const double* alpha, const double* T, double* omega,
-                             double* rhoG_old, unsigned* flags) {
+                             const double* rhoG, double* rhoG_old, unsigned* flags, const int* dirty) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
   unsigned boil = 0;
   double w = omega[id];
-  if (alpha[id] >= 0.5) { w = Y_eq(p, T[id], &boil); omega[id] = w; }
-  rhoG_old[id] = rho_gas(p, T[id], w);
+  bool liq = alpha[id] >= 0.5;
+  if (liq) { w = Y_eq(p, T[id], &boil); omega[id] = w; }
+  rhoG_old[id] = (liq || *dirty) ? rho_gas(p, T[id], w) : rhoG[id];
   if (boil) atomicOr(flags, (unsigned)DROPLET_FLAG_BOILING);
 }
 
 // central gradient of alpha at cell (i,j,k) with the alpha ghost rule
-__device__ inline void grad_alpha(const Geo& g, const double* al, int i, int j, int k, double gr[3]) {
-  gr[0] = (cellg(g, al, i + 1, j, k, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i - 1, j, k, R_ALPHA, 0, 0, 0, 0)) / (2.0 * g.h[0]);
-  gr[1] = (cellg(g, al, i, j + 1, k, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i, j - 1, k, R_ALPHA, 0, 0, 0, 0)) / (2.0 * g.h[1]);
-  gr[2] = g.act3 ? (cellg(g, al, i, j, k + 1, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i, j, k - 1, R_ALPHA, 0, 0, 0, 0)) / (2.0 * g.h[2]) : 0.0;
+__device__ __forceinline__ void grad_alpha(const Geo& g, const double* al, int i, int j, int k, double gr[3]) {
+  gr[0] = (cellg(g, al, i + 1, j, k, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i - 1, j, k, R_ALPHA, 0, 0, 0, 0)) * (0.5 * g.ih[0]);
+  gr[1] = (cellg(g, al, i, j + 1, k, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i, j - 1, k, R_ALPHA, 0, 0, 0, 0)) * (0.5 * g.ih[1]);
+  gr[2] = g.act3 ? (cellg(g, al, i, j, k + 1, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i, j, k - 1, R_ALPHA, 0, 0, 0, 0)) * (0.5 * g.ih[2]) : 0.0;
 }
 __device__ __forceinline__ double norm_rn(const double gr[3], int na) {
   double s = __dadd_rn(__dmul_rn(gr[0], gr[0]), __dmul_rn(gr[1], gr[1]));
@@ -125,11 +146,12 @@ __device__ __forceinline__ double norm_rn(const double gr[3], int na) {
 // alpha < 1e-3 (axis mirrored, stop at the domain edge); j = -rho D grad(omega)
 // + rho omega v there; m_raw = -j . grad(alpha) (Eqs. massflux, globalFlux).
 // Partial sums of m_raw V and f(alpha) m_raw V per block.
+template <int NA>
 __global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG,
                            const double* u0, const double* u1, const double* u2,
                            double* mraw, int* adj, double* partials, unsigned* flags) {
   double acc[2] = {0.0, 0.0};
-  int na = nact(g);
+  constexpr int na = NA;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     decomp(id, g.n[0], g.n[1], i, j, k);
@@ -144,8 +166,9 @@ __global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* ome
       int q[3] = {0, 0, 0};
       for (int s = 1; s <= 3 && found < 0; ++s) {
         bool inside = true;
+        #pragma unroll
         for (int a = 0; a < na; ++a) {
-          double ratio = g.hmin / g.h[a];
+          double ratio = g.hmin * g.ih[a];
           double xi = __dadd_rn((double)ci[a] + 0.5, __dmul_rn(__dmul_rn((double)s, ratio), nh[a]));
           if (g.axisym && a == 0) xi = fabs(xi);
           double fq = floor(xi);
@@ -167,14 +190,15 @@ __global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* ome
         int qi, qj, qk;
         decomp(found, g.n[0], g.n[1], qi, qj, qk);
         double gw[3];
-        gw[0] = (cellg(g, omega, qi + 1, qj, qk, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi - 1, qj, qk, R_TO, 0.0, u0, u1, u2)) / (2.0 * g.h[0]);
-        gw[1] = (cellg(g, omega, qi, qj + 1, qk, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi, qj - 1, qk, R_TO, 0.0, u0, u1, u2)) / (2.0 * g.h[1]);
-        gw[2] = g.act3 ? (cellg(g, omega, qi, qj, qk + 1, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi, qj, qk - 1, R_TO, 0.0, u0, u1, u2)) / (2.0 * g.h[2]) : 0.0;
+        gw[0] = (cellg(g, omega, qi + 1, qj, qk, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi - 1, qj, qk, R_TO, 0.0, u0, u1, u2)) * (0.5 * g.ih[0]);
+        gw[1] = (cellg(g, omega, qi, qj + 1, qk, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi, qj - 1, qk, R_TO, 0.0, u0, u1, u2)) * (0.5 * g.ih[1]);
+        gw[2] = g.act3 ? (cellg(g, omega, qi, qj, qk + 1, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi, qj, qk - 1, R_TO, 0.0, u0, u1, u2)) * (0.5 * g.ih[2]) : 0.0;
         double vc[3];
         vc[0] = 0.5 * (u0[fidx(g, 0, qi, qj, qk)] + u0[fidx(g, 0, qi + 1, qj, qk)]);
         vc[1] = 0.5 * (u1[fidx(g, 1, qi, qj, qk)] + u1[fidx(g, 1, qi, qj + 1, qk)]);
         vc[2] = g.act3 ? 0.5 * (u2[fidx(g, 2, qi, qj, qk)] + u2[fidx(g, 2, qi, qj, qk + 1)]) : 0.0;
         double s = 0.0;
+        #pragma unroll
         for (int a = 0; a < na; ++a) {
           double ja = -rhoQ * DQ * gw[a] + rhoQ * wQ * vc[a];
           s = s + ja * gr[a];
@@ -210,7 +234,7 @@ __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double*
   double a = alpha[id];
   double K = scal[SC_K];
   double m = (K == 0.0) ? 0.0 : K * sqrt(a * (1.0 - a)) * mraw[id];
-  double cap = p.rho_l * a / p.dt;
+  double cap = p.rho_l * a * p.idt;
   if (m > cap) { m = cap; atomicOr(flags, (unsigned)DROPLET_FLAG_MDOT_CAPPED); }
   mdot[id] = m;
   alpha_star[id] = a - p.dt * m / p.rho_l;
@@ -220,7 +244,9 @@ __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double*
 // Per face of direction a: low-order flux FL = phi alpha_upwind and the
 // antidiffusive flux AF = FH - FL (interior faces only), FH = phi alpha_vanLeer
 // + C_alpha |phi| (n_f . e_a) a_c (1 - a_c).
-__global__ void k_adv_faces(Geo g, Phys p, int a, const double* as, const double* ua, double* FL, double* AF) {
+template <int DIR, int NA>
+__global__ void k_adv_faces(Geo g, Phys p, const double* as, const double* ua, double* FL, double* AF) {
+  constexpr int a = DIR;
   long long nf = nfaces(g, a);
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= nf) return;
@@ -272,6 +298,7 @@ __global__ void k_adv_low(Geo g, const double* as, const double* F0, const doubl
 }
 
 // Zalesak limiter ratios R+ and R- from the local bounds over the cell and its face neighbours.
+template <int NA>
 __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const double* A0, const double* A1,
                             const double* A2, double* Rp, double* Rm) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -279,8 +306,10 @@ __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const dou
   int i, j, k;
   decomp(id, g.n[0], g.n[1], i, j, k);
   double amax = fmax(as[id], aL[id]), amin = fmin(as[id], aL[id]);
-  int na = nact(g);
+  constexpr int na = NA;
+  #pragma unroll
   for (int a = 0; a < na; ++a)
+    #pragma unroll
     for (int sh = -1; sh <= 1; sh += 2) {
       int q[3] = {i, j, k};
       q[a] += sh;
@@ -293,6 +322,7 @@ __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const dou
   amin = fmax(amin, 0.0);
   const double* AA[3] = {A0, A1, A2};
   double Pp = 0.0, Pm = 0.0;
+  #pragma unroll
   for (int a = 0; a < na; ++a) {
     int hi[3] = {i, j, k};
     hi[a] += 1;
@@ -319,15 +349,17 @@ __device__ __forceinline__ double limited_flux(const Geo& g, int a, const double
 }
 
 // alpha^{n+1} = alpha^L - sum C A / V, clipped to [0, 1] with the clipped volume summed.
+template <int NA>
 __global__ void k_adv_update(Geo g, const double* aL, const double* A0, const double* A1, const double* A2,
                              const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags) {
   double acc[2] = {0.0, 0.0};
   const double* AA[3] = {A0, A1, A2};
-  int na = nact(g);
+  constexpr int na = NA;
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     decomp(id, g.n[0], g.n[1], i, j, k);
     double s = 0.0;
+    #pragma unroll
     for (int a = 0; a < na; ++a) {
       int hi[3] = {i, j, k};
       hi[a] += 1;
@@ -388,6 +420,7 @@ __device__ __forceinline__ double gam(int mode, const double* kc, const double* 
 }
 __device__ __forceinline__ double harm(double x, double y) { return 2.0 * x * y / (x + y); }
 
+template <int NA>
 __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
                                   const double* kc, const double* D, const double* mdot, const double* u0,
                                   const double* u1, const double* u2, const double* alpha_new, const double* pinv,
@@ -396,25 +429,27 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
   if (id >= g.N) return;
   int i, j, k;
   decomp(id, g.n[0], g.n[1], i, j, k);
-  int na = nact(g);
+  constexpr int na = NA;
   const double* U[3] = {u0, u1, u2};
   double* C[3] = {c0, c1, c2};
   double V = cellV(g, i);
   double coef = mode == 0 ? rho[id] * cp[id] : rho[id];
-  double dP = coef * V / p.dt;
-  double r = coef * V * phi[id] / p.dt + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
+  double dP = coef * V * p.idt;
+  double r = coef * V * phi[id] * p.idt + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
   double net = 0.0, Fsum = 0.0;
   double gP = gam(mode, kc, rho, D, id);
   bool pin = (mode == 1) && (alpha_new[id] >= 0.5);
   int ci[3] = {i, j, k};
+  #pragma unroll
   for (int a = 0; a < na; ++a) {
+    #pragma unroll
     for (int side = 0; side < 2; ++side) {
       int f[3] = {i, j, k};
       if (side) f[a] += 1;
       double F = U[a][fidx(g, a, f[0], f[1], f[2])] * faceA(g, a, f[0]);
       double val;
       if (f[a] == 0 || f[a] == g.n[a]) {
-        int kind = g.bc[a][side];
+        int kind = (side ? g.bc[a][1] : g.bc[a][0]);
         bool inflow = side == 0 ? (F > 0.0) : (F < 0.0);
         val = ((kind == BC_OPEN || kind == BC_FORCED) && inflow) ? amb : phi[id];
       } else {
@@ -437,7 +472,7 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
       int Lc[3] = {i, j, k};
       Lc[a] -= 1;
       long long li = cidx(g, Lc[0], Lc[1], Lc[2]);
-      cl = harm(gam(mode, kc, rho, D, li), gP) * faceA(g, a, i) / g.h[a];
+      cl = harm(gam(mode, kc, rho, D, li), gP) * faceA(g, a, i) * g.ih[a];
       if (mode == 1) {
         bool lp = alpha_new[li] >= 0.5;
         if (!pin && lp) { r += cl * pinv[li]; dP += cl; }
@@ -451,16 +486,17 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
       Hc[a] += 1;
       long long hi = cidx(g, Hc[0], Hc[1], Hc[2]);
       if (alpha_new[hi] >= 0.5) {
-        double ch = harm(gP, gam(mode, kc, rho, D, hi)) * faceA(g, a, Hc[0]) / g.h[a];
+        double ch = harm(gP, gam(mode, kc, rho, D, hi)) * faceA(g, a, Hc[0]) * g.ih[a];
         r += ch * pinv[hi];
         dP += ch;
       }
     }
     // Dirichlet boundary faces
+    #pragma unroll
     for (int side = 0; side < 2; ++side) {
       bool atb = side ? (ci[a] == g.n[a] - 1) : (ci[a] == 0);
       if (!atb) continue;
-      int kind = g.bc[a][side];
+      int kind = (side ? g.bc[a][1] : g.bc[a][0]);
       bool isdir = false;
       int f[3] = {i, j, k};
       if (side) f[a] += 1;
@@ -470,7 +506,7 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
         isdir = (side ? un : -un) < 0.0;
       }
       if (isdir) {
-        double cb = gP * faceA(g, a, f[0]) / (0.5 * g.h[a]);
+        double cb = gP * faceA(g, a, f[0]) * (2.0 * g.ih[a]);
         dP += cb;
         r += cb * amb;
       }
@@ -479,7 +515,7 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
   r -= coef * (net - phi[id] * Fsum);
   if (pin) {
     // pinned row, scaled like the other rows: (coef V/dt) x = (coef V/dt) Y_eq
-    double dd = coef * V / p.dt;
+    double dd = coef * V * p.idt;
     r = dd * pinv[id];
     dP = dd;
   }
@@ -487,9 +523,11 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
   rhs[id] = r;
 }
 
-__global__ void k_yeq(Geo g, Phys p, const double* T, double* yq, unsigned* flags) {
+// saturation value for the rows pinned in the species solve (alpha >= 1/2); 0 elsewhere (unused)
+__global__ void k_yeq(Geo g, Phys p, const double* T, const double* alpha, double* yq, unsigned* flags) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
+  if (alpha[id] < 0.5) { yq[id] = 0.0; return; }
   unsigned b = 0;
   yq[id] = Y_eq(p, T[id], &b);
   if (b) atomicOr(flags, (unsigned)DROPLET_FLAG_BOILING);
@@ -519,9 +557,11 @@ __device__ __forceinline__ double mu_edge(const Geo& g, const double* mu, const 
   return 0.25 * s;
 }
 
-__global__ void k_mom_assemble(Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2,
+template <int C, int NA>
+__global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1, const double* u2,
                                const double* rho, const double* mu, const double* pr, const double* alpha,
-                               double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+                               const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+  constexpr int c = C;
   // box dims: n with n_c - 1 along c
   int m[3] = {g.n[0], g.n[1], g.n[2]};
   m[c] -= 1;
@@ -537,7 +577,7 @@ __global__ void k_mom_assemble(Geo g, Phys p, int c, const double* u0, const dou
   const double* U[3] = {u0, u1, u2};
   const double* uc = U[c];
   double* Cc[3] = {c0, c1, c2};
-  int na = nact(g);
+  constexpr int na = NA;
   long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, R[0], R[1], R[2]);
   double rhoL = rho[li], rhoR = rho[ri], muL = mu[li], muR = mu[ri];
   double rho_f = 0.5 * (rhoL + rhoR), mu_f = 0.5 * (muL + muR);
@@ -548,11 +588,12 @@ __global__ void k_mom_assemble(Geo g, Phys p, int c, const double* u0, const dou
   } else {
     V_f = g.h[0] * g.h[1] * g.h[2];
   }
-  double A_f = V_f / g.h[c];
+  double A_f = V_f * g.ih[c];
   double u_f = uc[fidx(g, c, f[0], f[1], f[2])];
-  double d = rho_f * V_f / p.dt;
-  double r = rho_f * V_f * u_f / p.dt;
+  double d = rho_f * V_f * p.idt;
+  double r = rho_f * V_f * u_f * p.idt;
   double t_adv = 0.0, t_vT = 0.0, d_visc = 0.0;
+  #pragma unroll
   for (int a = 0; a < na; ++a) {
     // ---- advection (advective form, minmod limited linear upwind)
     double ubar;
@@ -567,6 +608,7 @@ __global__ void k_mom_assemble(Geo g, Phys p, int c, const double* u0, const dou
     }
     int q[3];
     double us[5];
+    #pragma unroll
     for (int s = -2; s <= 2; ++s) {
       q[0] = f[0]; q[1] = f[1]; q[2] = f[2];
       q[a] += s;
@@ -575,15 +617,15 @@ __global__ void k_mom_assemble(Geo g, Phys p, int c, const double* u0, const dou
     double uplus, uminus;
     if (ubar >= 0.0) { uplus = lim_up(us[1], us[2], us[3]); uminus = lim_up(us[0], us[1], us[2]); }
     else { uplus = lim_up(us[4], us[3], us[2]); uminus = lim_up(us[3], us[2], us[1]); }
-    t_adv = t_adv - rho_f * V_f * ubar * (uplus - uminus) / g.h[a];
+    t_adv = t_adv - rho_f * V_f * ubar * (uplus - uminus) * g.ih[a];
     // ---- viscous
     if (a == c) {
       double ApL, ApR;
       if (g.axisym && c == 0) { ApL = areaN(g, 0, (L[0] + 0.5) * g.h[0]); ApR = areaN(g, 0, (R[0] + 0.5) * g.h[0]); }
       else if (g.axisym) { ApL = ApR = areaN(g, 1, r_f); }
       else { ApL = ApR = areaN(g, c, 0.0); }
-      double kR = muR * ApR / g.h[c], kL = muL * ApL / g.h[c];
-      double dR = (us[3] - us[2]) / g.h[c], dL = (us[2] - us[1]) / g.h[c];
+      double kR = muR * ApR * g.ih[c], kL = muL * ApL * g.ih[c];
+      double dR = (us[3] - us[2]) * g.ih[c], dL = (us[2] - us[1]) * g.ih[c];
       t_vT = t_vT + muR * ApR * dR - muL * ApL * dL;
       // coupling with the lower neighbour face (stored at this box cell)
       Cc[c][id] = (b[c] > 0) ? kL : 0.0;
@@ -605,14 +647,14 @@ __global__ void k_mom_assemble(Geo g, Phys p, int c, const double* u0, const dou
       else if (g.axisym) { App = Apm = areaN(g, 1, r_f); }
       else { App = Apm = areaN(g, a, 0.0); }
       double mup = mu_edge(g, mu, L, R, a, 1), mum = mu_edge(g, mu, L, R, a, -1);
-      double kp = mup * App / g.h[a], km = mum * Apm / g.h[a];
+      double kp = mup * App * g.ih[a], km = mum * Apm * g.ih[a];
       const double* ua = U[a];
       int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
       La[a] += 1;
       Ra[a] += 1;
       double uaR_hi = ua[fidx(g, a, Ra[0], Ra[1], Ra[2])], uaL_hi = ua[fidx(g, a, La[0], La[1], La[2])];
       double uaR_lo = ua[fidx(g, a, R[0], R[1], R[2])], uaL_lo = ua[fidx(g, a, L[0], L[1], L[2])];
-      t_vT = t_vT + mup * App * (uaR_hi - uaL_hi) / g.h[c] - mum * Apm * (uaR_lo - uaL_lo) / g.h[c];
+      t_vT = t_vT + mup * App * (uaR_hi - uaL_hi) * g.ih[c] - mum * Apm * (uaR_lo - uaL_lo) * g.ih[c];
       Cc[a][id] = (b[a] > 0) ? km : 0.0;
       if (b[a] == 0 && (g.bc[a][0] == BC_WALL || g.bc[a][0] == BC_FORCED)) d_visc += 2.0 * km;
       if (b[a] == m[a] - 1 && (g.bc[a][1] == BC_WALL || g.bc[a][1] == BC_FORCED)) d_visc += 2.0 * kp;
@@ -621,16 +663,12 @@ __global__ void k_mom_assemble(Geo g, Phys p, int c, const double* u0, const dou
   if (g.axisym && c == 0 && r_f > 0.0) d_visc = d_visc + 2.0 * mu_f * V_f / (r_f * r_f);
   // pressure, buoyancy and centripetal force in the balanced face form
   double gx = 0.0;
+  #pragma unroll
   for (int a = 0; a < na; ++a) {
     double xa = (a == c) ? f[a] * g.h[a] : (f[a] + 0.5) * g.h[a];
     gx = gx + p.g[a] * xa;
   }
-  auto xi_at = [&](const int q[3]) {
-    double d2 = 0.0;
-    for (int a = 0; a < na; ++a) { double x = (q[a] + 0.5) * g.h[a] - p.xc[a]; d2 = d2 + x * x; }
-    return p.xi0 * p.Df / (2.0 * fmax(sqrt(d2), p.Df));
-  };
-  double xiL = xi_at(L), xiR = xi_at(R);
+  double xiL = xi[li], xiR = xi[ri];
   double raL = rhoL * alpha[li], raR = rhoR * alpha[ri];
   double t_force = -A_f * (pr[ri] - pr[li]) - A_f * gx * (rhoR - rhoL) + A_f * 0.5 * (raL + raR) * (xiR - xiL);
   d = d + d_visc;
@@ -640,7 +678,9 @@ __global__ void k_mom_assemble(Geo g, Phys p, int c, const double* u0, const dou
 }
 
 // u* of direction c from the box solution; boundary faces by their rule.
-__global__ void k_mom_scatter(Geo g, Phys p, int c, const double* x, double* us) {
+template <int C>
+__global__ void k_mom_scatter(Geo g, Phys p, const double* x, double* us) {
+  constexpr int c = C;
   long long nf = nfaces(g, c);
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= nf) return;
@@ -656,14 +696,30 @@ __global__ void k_mom_scatter(Geo g, Phys p, int c, const double* x, double* us)
   };
   if (f[c] > 0 && f[c] < g.n[c]) { us[id] = box(f[c]); return; }
   int side = f[c] == 0 ? 0 : 1;
-  int kind = g.bc[c][side];
+  int kind = (side ? g.bc[c][1] : g.bc[c][0]);
   if (kind == BC_OPEN) us[id] = box(side ? g.n[c] - 1 : 1);
   // axis / wall: stays 0; forced inlet: keeps u_in (both already stored)
+}
+
+// initial guess of the momentum solve of direction c: u^n on the interior faces
+template <int C>
+__global__ void k_faces_to_box(Geo g, const double* u, double* x) {
+  constexpr int c = C;
+  int m[3] = {g.n[0], g.n[1], g.n[2]};
+  m[c] -= 1;
+  long long nb = (long long)m[0] * m[1] * m[2];
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= nb) return;
+  int b[3];
+  decomp(id, m[0], m[1], b[0], b[1], b[2]);
+  b[c] += 1;
+  x[id] = u[fidx(g, c, b[0], b[1], b[2])];
 }
 
 // ============================================================== S8 - S10 projection
 // S = mdot (1/rho_G - 1/rho_L) - (1 - alpha)/rho_G [(rho_G^{n+1} - rho_G^n)/dt + vbar . grad rho_G^{n+1}]
 // sum beta_f (dp_P - dp_N) + sum_open beta_b dp_P = (S V - sum u* A)/dt
+template <int NA>
 __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo,
                                    const double* rgn, const double* u0, const double* u1, const double* u2,
                                    const double* us0, const double* us1, const double* us2, const double* rho,
@@ -672,12 +728,13 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
   if (id >= g.N) return;
   int i, j, k;
   decomp(id, g.n[0], g.n[1], i, j, k);
-  int na = nact(g);
+  constexpr int na = NA;
   const double* U[3] = {u0, u1, u2};
   const double* US[3] = {us0, us1, us2};
   double* C[3] = {c0, c1, c2};
   int ci[3] = {i, j, k};
   double adv = 0.0;
+  #pragma unroll
   for (int a = 0; a < na; ++a) {
     int hi[3] = {i, j, k};
     hi[a] += 1;
@@ -685,14 +742,15 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
     int qp[3] = {i, j, k}, qm[3] = {i, j, k};
     qp[a] += 1;
     qm[a] -= 1;
-    double gr = (cellg(g, rgn, qp[0], qp[1], qp[2], R_ZG, 0, 0, 0, 0) - cellg(g, rgn, qm[0], qm[1], qm[2], R_ZG, 0, 0, 0, 0)) / (2.0 * g.h[a]);
+    double gr = (cellg(g, rgn, qp[0], qp[1], qp[2], R_ZG, 0, 0, 0, 0) - cellg(g, rgn, qm[0], qm[1], qm[2], R_ZG, 0, 0, 0, 0)) * (0.5 * g.ih[a]);
     adv = adv + vc * gr;
   }
   double rn = rgn[id];
-  double s = mdot[id] * (1.0 / rn - 1.0 / p.rho_l) - (1.0 - alpha[id]) / rn * ((rn - rgo[id]) / p.dt + adv);
+  double s = mdot[id] * (1.0 / rn - 1.0 / p.rho_l) - (1.0 - alpha[id]) / rn * ((rn - rgo[id]) * p.idt + adv);
   S[id] = s;
   double dg = 0.0, div = 0.0;
   double rP = rho[id];
+  #pragma unroll
   for (int a = 0; a < na; ++a) {
     int hi[3] = {i, j, k};
     hi[a] += 1;
@@ -702,18 +760,20 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
       int Lc[3] = {i, j, k};
       Lc[a] -= 1;
       double rf = 0.5 * (rho[cidx(g, Lc[0], Lc[1], Lc[2])] + rP);
-      cl = faceA(g, a, i) / (rf * g.h[a]);
+      cl = faceA(g, a, i) * g.ih[a] / rf;
     }
     C[a][id] = cl;
-    if (ci[a] == 0 && g.bc[a][0] == BC_OPEN) dg += faceA(g, a, i) / (rP * 0.5 * g.h[a]);
-    if (ci[a] == g.n[a] - 1 && g.bc[a][1] == BC_OPEN) dg += faceA(g, a, hi[0]) / (rP * 0.5 * g.h[a]);
+    if (ci[a] == 0 && g.bc[a][0] == BC_OPEN) dg += faceA(g, a, i) * (2.0 * g.ih[a]) / rP;
+    if (ci[a] == g.n[a] - 1 && g.bc[a][1] == BC_OPEN) dg += faceA(g, a, hi[0]) * (2.0 * g.ih[a]) / rP;
   }
   Dg[id] = dg;
-  rhs[id] = (s * cellV(g, i) - div) / p.dt;
+  rhs[id] = (s * cellV(g, i) - div) * p.idt;
 }
 
 // u = u* - dt beta_f (dp_R - dp_L)/A_f with dp = 0 beyond open faces (half-cell distance)
-__global__ void k_correct(Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u) {
+template <int C>
+__global__ void k_correct(Geo g, Phys p, const double* us, const double* dp, const double* rho, double* u) {
+  constexpr int c = C;
   long long nf = nfaces(g, c);
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= nf) return;
@@ -727,13 +787,13 @@ __global__ void k_correct(Geo g, Phys p, int c, const double* us, const double* 
     L[c] -= 1;
     if (f[c] > 0 && f[c] < g.n[c]) {
       long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, f[0], f[1], f[2]);
-      double beta = A / (0.5 * (rho[li] + rho[ri]) * g.h[c]);
+      double beta = A * g.ih[c] / (0.5 * (rho[li] + rho[ri]));
       corr = p.dt * beta * (dp[ri] - dp[li]) / A;
     } else {
       int side = f[c] == 0 ? 0 : 1;
-      if (g.bc[c][side] == BC_OPEN) {
+      if ((side ? g.bc[c][1] : g.bc[c][0]) == BC_OPEN) {
         long long pi = side ? cidx(g, L[0], L[1], L[2]) : cidx(g, f[0], f[1], f[2]);
-        double beta = A / (rho[pi] * 0.5 * g.h[c]);
+        double beta = A * (2.0 * g.ih[c]) / rho[pi];
         corr = side ? p.dt * beta * (0.0 - dp[pi]) / A : p.dt * beta * (dp[pi] - 0.0) / A;
       }
     }
@@ -749,12 +809,13 @@ __global__ void k_add(long long n, double* y, const double* x) {
 // ============================================================== S11 diagnostics
 // sums: alpha V, mdot V, T |grad alpha| V, |grad alpha| V, (1-alpha) rhoG omega V, open-boundary vapour outflow
 // maxima: |u|, alpha, -alpha
+template <int NA>
 __global__ void k_diag(Geo g, const double* alpha, const double* T, const double* mdot, const double* omega,
                        const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum,
                        double* pmax) {
   double s[6] = {0, 0, 0, 0, 0, 0};
   double mx[3] = {0.0, -1e300, -1e300};
-  int na = nact(g);
+  constexpr int na = NA;
   const double* U[3] = {u0, u1, u2};
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
@@ -772,6 +833,7 @@ __global__ void k_diag(Geo g, const double* alpha, const double* T, const double
     mx[1] = fmax(mx[1], a);
     mx[2] = fmax(mx[2], -a);
     int ci[3] = {i, j, k};
+    #pragma unroll
     for (int q = 0; q < na; ++q) {
       mx[0] = fmax(mx[0], fabs(U[q][fidx(g, q, i, j, k)]));
       if (ci[q] == g.n[q] - 1) {
@@ -779,9 +841,10 @@ __global__ void k_diag(Geo g, const double* alpha, const double* T, const double
         hi[q] += 1;
         mx[0] = fmax(mx[0], fabs(U[q][fidx(g, q, hi[0], hi[1], hi[2])]));
       }
+      #pragma unroll
       for (int side = 0; side < 2; ++side) {
         bool atb = side ? (ci[q] == g.n[q] - 1) : (ci[q] == 0);
-        int kind = g.bc[q][side];
+        int kind = (side ? g.bc[q][1] : g.bc[q][0]);
         if (!atb || !(kind == BC_OPEN || kind == BC_FORCED)) continue;
         int f[3] = {i, j, k};
         if (side) f[q] += 1;
@@ -811,6 +874,88 @@ __global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, 
     scal[SC_AMAX] = m[1];
     scal[SC_AMIN] = -m[2];
   }
+}
+
+// ============================================================== launch wrappers
+void L_evap_raw(cudaStream_t st, int grid, Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* mraw, int* adj, double* partials, unsigned* flags) {
+  ++g_launches;
+  if (nact(g) == 3) k_evap_raw<3><<<grid, TPB, 0, st>>>(g, p, alpha, omega, rhoG, u0, u1, u2, mraw, adj, partials, flags);
+  else k_evap_raw<2><<<grid, TPB, 0, st>>>(g, p, alpha, omega, rhoG, u0, u1, u2, mraw, adj, partials, flags);
+}
+
+void L_adv_faces(cudaStream_t st, int grid, Geo g, Phys p, int a, const double* as, const double* ua, double* FL, double* AF) {
+  ++g_launches;
+  if (nact(g) == 3) {
+    if (a == 0) k_adv_faces<0, 3><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
+    else if (a == 1) k_adv_faces<1, 3><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
+    else k_adv_faces<2, 3><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
+  } else {
+    if (a == 0) k_adv_faces<0, 2><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
+    else k_adv_faces<1, 2><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
+  }
+}
+
+void L_adv_limit(cudaStream_t st, int grid, Geo g, const double* as, const double* aL, const double* A0, const double* A1, const double* A2, double* Rp, double* Rm) {
+  ++g_launches;
+  if (nact(g) == 3) k_adv_limit<3><<<grid, TPB, 0, st>>>(g, as, aL, A0, A1, A2, Rp, Rm);
+  else k_adv_limit<2><<<grid, TPB, 0, st>>>(g, as, aL, A0, A1, A2, Rp, Rm);
+}
+
+void L_adv_update(cudaStream_t st, int grid, Geo g, const double* aL, const double* A0, const double* A1, const double* A2, const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags) {
+  ++g_launches;
+  if (nact(g) == 3) k_adv_update<3><<<grid, TPB, 0, st>>>(g, aL, A0, A1, A2, Rp, Rm, alpha, partials, flags);
+  else k_adv_update<2><<<grid, TPB, 0, st>>>(g, aL, A0, A1, A2, Rp, Rm, alpha, partials, flags);
+}
+
+void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+  ++g_launches;
+  if (nact(g) == 3) k_scalar_assemble<3><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, kc, D, mdot, u0, u1, u2, alpha_new, pinv, amb, Dg, c0, c1, c2, rhs);
+  else k_scalar_assemble<2><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, kc, D, mdot, u0, u1, u2, alpha_new, pinv, amb, Dg, c0, c1, c2, rhs);
+}
+
+void L_mom_assemble(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+  ++g_launches;
+  if (nact(g) == 3) {
+    if (c == 0) k_mom_assemble<0, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
+    else if (c == 1) k_mom_assemble<1, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
+    else k_mom_assemble<2, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
+  } else {
+    if (c == 0) k_mom_assemble<0, 2><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
+    else k_mom_assemble<1, 2><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
+  }
+}
+
+void L_mom_scatter(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* x, double* us) {
+  ++g_launches;
+  if (c == 0) k_mom_scatter<0><<<grid, TPB, 0, st>>>(g, p, x, us);
+  else if (c == 1) k_mom_scatter<1><<<grid, TPB, 0, st>>>(g, p, x, us);
+  else k_mom_scatter<2><<<grid, TPB, 0, st>>>(g, p, x, us);
+}
+
+void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo, const double* rgn, const double* u0, const double* u1, const double* u2, const double* us0, const double* us1, const double* us2, const double* rho, double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+  ++g_launches;
+  if (nact(g) == 3) k_poisson_assemble<3><<<grid, TPB, 0, st>>>(g, p, mdot, alpha, rgo, rgn, u0, u1, u2, us0, us1, us2, rho, S, Dg, c0, c1, c2, rhs);
+  else k_poisson_assemble<2><<<grid, TPB, 0, st>>>(g, p, mdot, alpha, rgo, rgn, u0, u1, u2, us0, us1, us2, rho, S, Dg, c0, c1, c2, rhs);
+}
+
+void L_correct(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u) {
+  ++g_launches;
+  if (c == 0) k_correct<0><<<grid, TPB, 0, st>>>(g, p, us, dp, rho, u);
+  else if (c == 1) k_correct<1><<<grid, TPB, 0, st>>>(g, p, us, dp, rho, u);
+  else k_correct<2><<<grid, TPB, 0, st>>>(g, p, us, dp, rho, u);
+}
+
+void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax) {
+  ++g_launches;
+  if (nact(g) == 3) k_diag<3><<<grid, TPB, 0, st>>>(g, alpha, T, mdot, omega, rhoG, u0, u1, u2, psum, pmax);
+  else k_diag<2><<<grid, TPB, 0, st>>>(g, alpha, T, mdot, omega, rhoG, u0, u1, u2, psum, pmax);
+}
+
+void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x) {
+  ++g_launches;
+  if (c == 0) k_faces_to_box<0><<<grid, TPB, 0, st>>>(g, u, x);
+  else if (c == 1) k_faces_to_box<1><<<grid, TPB, 0, st>>>(g, u, x);
+  else k_faces_to_box<2><<<grid, TPB, 0, st>>>(g, u, x);
 }
 
 }  // namespace dg
