@@ -39,6 +39,7 @@ WORKLOADS = {
     "cfg2_axisym_256x512_fp64": lambda: W.cfg2_axisym_256x512(precision=0),
     "cfg3_cart3d_256": lambda: W.cfg3_cart3d(),
     "cfg3_cart3d_256_fp64": lambda: W.cfg3_cart3d(precision=0),
+    "cfg3_cart3d_128_fp64": lambda: W.cfg3_cart3d(nc=128, precision=0),
     "cfg1_axisym_64x128": lambda: W.cfg1_axisym_64x128(cg_rtol=1e-12, helm_rtol=1e-13),
     "cfg5_axisym_128x256": lambda: W.cfg5_axisym_128x256(cg_rtol=1e-12, helm_rtol=1e-13),
 }

@@ -188,6 +188,7 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
       cudaMalloc((void**)&c->dirty, sizeof(int)) != cudaSuccess ||
       cudaMallocHost((void**)&c->hscal, sizeof(double) * SC_COUNT) != cudaSuccess ||
       cudaMallocHost((void**)&c->hflags, sizeof(unsigned)) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_NOMEM; }
+  c->solver.f32_helm = c->cfg.precision == 1;
   if ((rc = c->solver.setup(N, c->st))) { free_all(c); delete c; return rc; }
   c->solver.prof = &c->prof;
   c->solver.stream2 = c->st2;

@@ -130,11 +130,15 @@ class Solver {
   cudaStream_t stream = nullptr;
   cudaStream_t stream2 = nullptr;   // captures the bodies of the device-driven solver loops
   bool capturing = false;           // the step is being captured into a CUDA graph
+  bool f32_helm = false;            // Jacobi-PCG as FP32 defect correction (set before setup)
   Prof* prof = nullptr;
 
  private:
   template <typename F>
   int device_loop(F body);
+  int pcg_jacobi_f32(const BoxSys& s, double rtol, int maxit, SolveStats* out);
+  float *fD = nullptr, *fc[3] = {nullptr, nullptr, nullptr}, *fidg = nullptr, *fr = nullptr, *fz = nullptr,
+        *fp = nullptr, *fAp = nullptr, *fdx = nullptr;
   int build_mg(const BoxSys& s, int fp32);
   void vcycle(int fp32);
   long long cap = 0;

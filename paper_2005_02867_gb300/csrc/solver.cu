@@ -224,6 +224,137 @@ __global__ void k_p_update(long long N, double* p, const double* z, const double
     p[id] = z[id] + be * p[id];
 }
 
+// ---------------------------------------------------------------- FP32 defect-correction CG
+// Mixed precision for the Helmholtz systems: with the FP64 defect r0 = b - A x0,
+// solve A d = r0 by Jacobi-PCG in FP32 (operator, vectors, arithmetic), per-thread
+// FP32 partial sums reduced across threads and blocks in FP64, then x = x0 + d in FP64.
+struct BoxVf {
+  int m[3];
+  long long N;
+  const float* D;
+  const float* c[3];
+};
+
+__global__ void k_mx_setup(BoxV A, const double* r64, float* fD, float* fc0, float* fc1, float* fc2, float* fidg,
+                           float* fr, float* fz, float* fp, float* fdx, double* part, const int* done, double* sc,
+                           unsigned* cnt) {
+  if (*done) return;
+  float rz = 0.f;
+  float* fc[3] = {fc0, fc1, fc2};
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < A.N; id += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    bdecomp(A.m, id, i, j, k);
+    int q[3] = {i, j, k};
+    long long st[3] = {1, (long long)A.m[0], (long long)A.m[0] * A.m[1]};
+    float D = (float)A.D[id];
+    float dt = D;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (!A.c[a]) continue;
+      float cl = (float)A.c[a][id];
+      fc[a][id] = cl;
+      if (q[a] > 0) dt += cl;
+      if (q[a] < A.m[a] - 1) dt += (float)A.c[a][id + st[a]];
+    }
+    fD[id] = D;
+    float iv = 1.f / dt;
+    fidg[id] = iv;
+    float rr = (float)r64[id];
+    fr[id] = rr;
+    float zz = iv * rr;
+    fz[id] = zz;
+    fp[id] = zz;
+    fdx[id] = 0.f;
+    rz += rr * zz;
+  }
+  double acc[1] = {(double)rz};
+  block_sum_store<1>(acc, part);
+  if (last_block(cnt)) {
+    double t = block_sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+      sc[S_RZ] = t;
+      *cnt = 0u;
+    }
+  }
+}
+
+__global__ void k_spmv_f(BoxVf A, const float* p, float* Ap, double* part, const int* done, double* sc, unsigned* cnt) {
+  if (*done) return;
+  float acc_f = 0.f;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < A.N; id += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    bdecomp(A.m, id, i, j, k);
+    long long st1 = A.m[0], st2 = (long long)A.m[0] * A.m[1];
+    float xp = p[id];
+    float y = A.D[id] * xp;
+    if (i > 0) y += A.c[0][id] * (xp - p[id - 1]);
+    if (i < A.m[0] - 1) y += A.c[0][id + 1] * (xp - p[id + 1]);
+    if (j > 0) y += A.c[1][id] * (xp - p[id - st1]);
+    if (j < A.m[1] - 1) y += A.c[1][id + st1] * (xp - p[id + st1]);
+    if (A.c[2]) {
+      if (k > 0) y += A.c[2][id] * (xp - p[id - st2]);
+      if (k < A.m[2] - 1) y += A.c[2][id + st2] * (xp - p[id + st2]);
+    }
+    Ap[id] = y;
+    acc_f += xp * y;
+  }
+  double acc[1] = {(double)acc_f};
+  block_sum_store<1>(acc, part);
+  if (last_block(cnt)) {
+    double pap = block_sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+      sc[S_PAP] = pap;
+      sc[S_ALPHA] = sc[S_RZ] / pap;
+      *cnt = 0u;
+    }
+  }
+}
+
+__global__ void k_update_f(long long N, float* dx, float* r, const float* p, const float* Ap, const float* idg, float* z,
+                           double* sc, double* part, int* done, unsigned* cnt) {
+  if (*done) return;
+  float al = (float)sc[S_ALPHA];
+  float rz_f = 0.f, rr_f = 0.f;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N; id += (long long)gridDim.x * blockDim.x) {
+    dx[id] += al * p[id];
+    float rr = r[id] - al * Ap[id];
+    r[id] = rr;
+    float zz = idg[id] * rr;
+    z[id] = zz;
+    rz_f += rr * zz;
+    rr_f += rr * rr;
+  }
+  double acc[2] = {(double)rz_f, (double)rr_f};
+  block_sum_store<2>(acc, part);
+  if (last_block(cnt)) {
+    double rz = block_sum_partials(part, gridDim.x);
+    __syncthreads();
+    double rr = block_sum_partials(part + gridDim.x, gridDim.x);
+    if (threadIdx.x == 0) {
+      sc[S_ITS] += 1.0;
+      sc[S_RR] = rr;
+      if (rr <= sc[S_TOL2] * sc[S_BB]) *done = 1;
+      else if (sc[S_ITS] >= sc[S_MAXIT]) *done = 2;
+      sc[S_BETA] = rz / sc[S_RZ];
+      sc[S_RZ] = rz;
+      *cnt = 0u;
+    }
+  }
+}
+
+__global__ void k_p_update_f(long long N, float* p, const float* z, const double* sc, const int* done) {
+  if (*done) return;
+  float be = (float)sc[S_BETA];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N; id += (long long)gridDim.x * blockDim.x)
+    p[id] = z[id] + be * p[id];
+}
+
+// x = x0 + d (FP64)
+__global__ void k_mx_finish(long long N, double* x, const float* dx) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id < N) x[id] += (double)dx[id];
+}
+
 // condition of a solver WHILE node: run another iteration while not done
 __global__ void k_set_cond(cudaGraphConditionalHandle h, const int* done) {
   cudaGraphSetConditional(h, *done == 0 ? 1u : 0u);
@@ -522,12 +653,21 @@ int Solver::setup(long long maxN, cudaStream_t s) {
   CK(cudaMalloc(&cnt, sizeof(unsigned)));
   CK(cudaMemset(cnt, 0, sizeof(unsigned)));
   CK(cudaMallocHost(&hsc, sizeof(double) * (S_COUNT + 2)));
+  if (f32_helm) {
+    size_t bf = sizeof(float) * (size_t)maxN;
+    float** fa[] = {&fD, &fc[0], &fc[1], &fc[2], &fidg, &fr, &fz, &fp, &fAp, &fdx};
+    for (auto q : fa) CK(cudaMalloc((void**)q, bf));
+  }
   return 0;
 }
 
 void Solver::release() {
   cudaFree(r); cudaFree(z); cudaFree(p); cudaFree(Ap); cudaFree(idg);
   cudaFree(part); cudaFree(sc); cudaFree(done); cudaFree(cnt); cudaFreeHost(hsc);
+  {
+    float** fa[] = {&fD, &fc[0], &fc[1], &fc[2], &fidg, &fr, &fz, &fp, &fAp, &fdx};
+    for (auto q : fa) { cudaFree(*q); *q = nullptr; }
+  }
   cnt = nullptr;
   cudaFree(mgbuf);
   r = z = p = Ap = idg = part = sc = nullptr;
@@ -602,6 +742,7 @@ int Solver::device_loop(F body) {
 }
 
 int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
+  if (f32_helm) return pcg_jacobi_f32(s, rtol, maxit, out);
   BoxV A = view(s);
   int nb = red_grid(s.N);
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 1, part);
@@ -628,6 +769,47 @@ int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out)
   if (!conv) poll(hsc, sc, done, stream, maxit, &conv);
   fill_stats(hsc, conv, out);
   return conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
+}
+
+int Solver::pcg_jacobi_f32(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
+  BoxV A = view(s);
+  BoxVf Af;
+  for (int a = 0; a < 3; ++a) { Af.m[a] = s.m[a]; Af.c[a] = s.c[a] ? fc[a] : nullptr; }
+  Af.N = s.N;
+  Af.D = fD;
+  int nb = red_grid(s.N);
+  // FP64 defect of the initial guess, ||b||, ||r0||
+  ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
+  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);
+  ++g_launches, k_mx_setup<<<nb, TPB, 0, stream>>>(A, r, fD, fc[0], fc[1], s.c[2] ? fc[2] : fc[0], fidg, fr, fz, fp, fdx,
+                                                  part, done, sc, cnt);
+  auto iteration = [&]() {
+    {
+      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 4.0);
+      ++g_launches, k_spmv_f<<<nb, TPB, 0, stream>>>(Af, fp, fAp, part, done, sc, cnt);
+    }
+    {
+      ProfScope ps(prof, KC_UPDATE, stream, 8.0 * s.N * 4.0);
+      ++g_launches, k_update_f<<<nb, TPB, 0, stream>>>(s.N, fdx, fr, fp, fAp, fidg, fz, sc, part, done, cnt);
+    }
+    ++g_launches, k_p_update_f<<<nb, TPB, 0, stream>>>(s.N, fp, fz, sc, done);
+  };
+  int rc = 0;
+  if (capturing) {
+    rc = device_loop(iteration);
+  } else {
+    int conv = 0;
+    for (int it = 0; it < maxit; it += 8) {
+      for (int q = 0; q < 8; ++q) iteration();
+      CK(cudaGetLastError());
+      if (poll(hsc, sc, done, stream, maxit, &conv)) break;
+    }
+    if (!conv) poll(hsc, sc, done, stream, maxit, &conv);
+    fill_stats(hsc, conv, out);
+    rc = conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
+  }
+  ++g_launches, k_mx_finish<<<lin_grid(s.N), TPB, 0, stream>>>(s.N, s.x, fdx);
+  return rc;
 }
 
 // ---------------------------------------------------------------- multigrid setup / cycle

@@ -67,7 +67,7 @@ def cfg1_d2law(**over):
 def cfg2_axisym_256x512(**over):
     """2D axisymmetric 256x512 over 4 x 8 mm, normal gravity, droplet held by
     the centripetal force, natural convection, 773 K, 1 bar, dt 5e-6 s."""
-    base = dict(n=(256, 512, 1), g=(0.0, -9.81, 0.0), dt=5e-6, precision=1, cg_rtol=1e-8, helm_rtol=1e-10)
+    base = dict(n=(256, 512, 1), g=(0.0, -9.81, 0.0), dt=5e-6, precision=1, cg_rtol=1e-8, helm_rtol=1e-8)
     base.update(over)
     return make(**base)
 
@@ -78,7 +78,7 @@ def cfg3_cart3d(nc=256, **over):
     the initial temperature, dt 2e-6 s."""
     base = dict(geom=GEOM_CART3D, n=(nc, nc, nc), L=(4e-3, 4e-3, 4e-3), xc=(2e-3, 2e-3, 2e-3),
                 D0=0.8e-3, P=20e5, g=(0.0, 0.0, -9.81), u_inflow=1.0, bc_mode=1, eq_model=1,
-                dt=2e-6, T_perturb=0.01, precision=1, cg_rtol=1e-8, helm_rtol=1e-10)
+                dt=2e-6, T_perturb=0.01, precision=1, cg_rtol=1e-8, helm_rtol=1e-8)
     base.update(over)
     return make(**base)
 
@@ -119,7 +119,7 @@ def cfg4_batch(n_drop=64, seed=20050286, nr_choices=(64, 96, 128, 160, 192, 224,
         dx = L0 / nr
         out.append(make(n=(nr, 2 * nr, 1), L=(L0, L1, 0.0), xc=(0.0, 0.5 * L1, 0.0), D0=d0,
                         T_amb=tamb, P=p, g=(0.0, -9.81, 0.0), dt=1e-5 * dx / 62.5e-6,
-                        precision=1, cg_rtol=1e-8, helm_rtol=1e-10))
+                        precision=1, cg_rtol=1e-8, helm_rtol=1e-8))
     return out
 
 
