@@ -40,6 +40,8 @@ WORKLOADS = {
     "cfg3_cart3d_256": lambda: W.cfg3_cart3d(),
     "cfg3_cart3d_256_fp64": lambda: W.cfg3_cart3d(precision=0),
     "cfg3_cart3d_128_fp64": lambda: W.cfg3_cart3d(nc=128, precision=0),
+    "cfg4_batch64": lambda: W.cfg4_batch(),
+    "cfg4_batch64_fp64": lambda: [dict(c, precision=0) for c in W.cfg4_batch()],
     "cfg1_axisym_64x128": lambda: W.cfg1_axisym_64x128(cg_rtol=1e-12, helm_rtol=1e-13),
     "cfg5_axisym_128x256": lambda: W.cfg5_axisym_128x256(cg_rtol=1e-12, helm_rtol=1e-13),
 }
@@ -48,7 +50,23 @@ METRIC = "Mcell-steps/s"
 FLUSH_BYTES = 512 << 20      # larger than the 129 MB L2
 
 
+def cells_of(cfg):
+    if isinstance(cfg, list):
+        return sum(cells_of(c) for c in cfg)
+    return int(np.prod(cfg["n"][:2])) if cfg["geom"] == 0 else int(np.prod(cfg["n"]))
+
+
 def describe(name, cfg):
+    if isinstance(cfg, list):
+        c0 = cfg[0]
+        return {
+            "workload": name, "droplets": len(cfg), "cells": cells_of(cfg),
+            "grids": sorted({tuple(c["n"][:2]) for c in cfg}),
+            "precision": "fp64" if c0["precision"] == 0 else "fp64 CG + fp32 multigrid / fp32 Helmholtz defect correction",
+            "cg_rtol": c0["cg_rtol"], "helm_rtol": c0["helm_rtol"],
+            "execution": "one graph launch per step, one branch per droplet",
+            "l2": "flushed between timed steps (512 MiB device write outside the step events)",
+        }
     n = list(cfg["n"][:2]) if cfg["geom"] == 0 else list(cfg["n"])
     return {
         "workload": name,
@@ -59,7 +77,7 @@ def describe(name, cfg):
         "gravity": list(cfg["g"]),
         "equilibrium": "Raoult" if cfg["eq_model"] == 0 else "Peng-Robinson",
         "pressure_Pa": cfg["P"],
-        "precision": "fp64" if cfg["precision"] == 0 else "fp64 CG + fp32 multigrid preconditioner",
+        "precision": "fp64" if cfg["precision"] == 0 else "fp64 CG + fp32 multigrid / fp32 Helmholtz defect correction",
         "cg_rtol": cfg["cg_rtol"],
         "helm_rtol": cfg["helm_rtol"],
         "l2": "flushed between timed steps (512 MiB device write outside the step events)",
@@ -157,7 +175,9 @@ def run_reference(args):
         return 0
     name = args.workload
     cfg = WORKLOADS[name]()
-    ncell = int(np.prod(cfg["n"]))
+    if isinstance(cfg, list):
+        cfg = cfg[0]       # the oracle steps one droplet of the batch: cells counted for that droplet
+    ncell = cells_of(cfg)
     from oracle import step as O
     st = O.init_state(cfg)
     for _ in range(args.warmup):
@@ -199,7 +219,7 @@ def run_ours(args):
 
     name = args.workload
     cfg = WORKLOADS[name]()
-    ncell = int(np.prod(cfg["n"]))
+    ncell = cells_of(cfg)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     sim = D.Droplet(cfg, stream=stream.cuda_stream)
@@ -252,23 +272,25 @@ def run_ours(args):
 
     # ---- end to end through the C ABI with host buffers: upload the state from
     # pinned host memory, one step, read the state back, every step
-    fields = ["alpha", "T", "omega", "p", "rhoG"] + ["u%d" % a for a in range(3 if cfg["geom"] == 1 else 2)]
+    cl = cfg if isinstance(cfg, list) else [cfg]
     bufs = {}
-    for f in fields:
-        n = D.droplet_field_size(sim.h, f)
-        bufs[f] = torch.empty(n, dtype=torch.float64, pin_memory=True)
-        D.droplet_get_field_ptr(sim.h, f, bufs[f].data_ptr(), n)
+    for di, cd in enumerate(cl):
+        fields = ["alpha", "T", "omega", "p", "rhoG"] + ["u%d" % a for a in range(3 if cd["geom"] == 1 else 2)]
+        for f in fields:
+            n = D.droplet_field_size(sim.h, f, droplet=di)
+            bufs[(di, f)] = torch.empty(n, dtype=torch.float64, pin_memory=True)
+            D.droplet_get_field_ptr(sim.h, f, bufs[(di, f)].data_ptr(), n, droplet=di)
     nbytes = sum(b.numel() * 8 for b in bufs.values())
     e2e_steps = max(1, min(args.steps, 10))
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        for f in fields:
-            D.droplet_set_field_ptr(sim.h, f, bufs[f].data_ptr(), bufs[f].numel())
+        for (di, f), b in bufs.items():
+            D.droplet_set_field_ptr(sim.h, f, b.data_ptr(), b.numel(), droplet=di)
         sim.step(1)
-        for f in fields:
-            D.droplet_get_field_ptr(sim.h, f, bufs[f].data_ptr(), bufs[f].numel())
+        for (di, f), b in bufs.items():
+            D.droplet_get_field_ptr(sim.h, f, b.data_ptr(), b.numel(), droplet=di)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     if world > 1:
@@ -288,7 +310,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64" if cfg["precision"] == 0 else "f64 (f32 multigrid preconditioner)",
+            "dtype": "f64" if cl[0]["precision"] == 0 else "f64 state, f32 stencil solves (multigrid, Helmholtz increments)",
             "data": "synthetic", "config": describe(name, cfg),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": src, "traffic": None,
@@ -307,10 +329,13 @@ def run_ours(args):
         }
         if world == 1 and not args.no_cpu_baseline:
             try:
-                n, sec = cpu_oracle(cfg)
-                line["cpu_baseline"] = {"value": ncell * n / sec / 1e6, "unit": METRIC, "cores": 1, "kind": "oracle",
+                c0 = cl[0]
+                n, sec = cpu_oracle(c0)
+                line["cpu_baseline"] = {"value": cells_of(c0) * n / sec / 1e6, "unit": METRIC, "cores": 1,
+                                        "kind": "oracle",
                                         "sample": f"{n} oracle steps of the same workload (single thread, after one "
-                                                  f"untimed step)"}
+                                                  f"untimed step)" + ("" if len(cl) == 1 else
+                                                                      "; first droplet of the batch")}
             except Exception as e:  # the GPU number stands on its own
                 line["cpu_baseline"] = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle",
                                         "sample": f"failed: {str(e)[-200:]}"}

@@ -128,20 +128,27 @@ enum droplet_field {
   DROPLET_F_COUNT = 18
 };
 
-/* Create a context for n_droplets independent droplets (currently 1) and set
- * the initial state of Sec. 3.3: alpha from sub-cell sampling of the sphere,
- * the steady spherical conduction profile of T, the quasi-steady Stefan
- * profile of the vapour, u = 0, p_rgh = 0.  cuda_stream is a cudaStream_t
- * (NULL = the legacy default stream) on which every later call enqueues its
- * work.  On success *out receives the context.  Errors: DROPLET_ERR_ARG (bad
+/* Create a context for n_droplets independent droplets (cfgs[0..n-1], each
+ * with its own grid, conditions and precision) and set the initial state of
+ * Sec. 3.3: alpha from sub-cell sampling of the sphere, the steady spherical
+ * conduction profile of T, the quasi-steady Stefan profile of the vapour,
+ * u = 0, p_rgh = 0.  cuda_stream is a cudaStream_t (NULL = the legacy default
+ * stream, replaced by an internal blocking stream) on which every later call
+ * orders its work.  A batch (n_droplets > 1) steps all droplets in one CUDA
+ * graph per step, one branch per droplet on a stream of its own; at creation
+ * an autotuner times a few steps for each candidate block cap of the
+ * reduction kernels (the state is restored afterwards) and keeps the fastest.
+ * On success *out receives the context.  Errors: DROPLET_ERR_ARG (bad
  * dimensions, droplet not inside the domain, dt <= 0, unsupported option),
  * DROPLET_ERR_NOMEM, DROPLET_ERR_CUDA. */
 int droplet_init(const droplet_config* cfgs, int n_droplets, void* cuda_stream, droplet_ctx** out);
 
-/* Advance every droplet by n_steps time steps (the stage list of Sec. 3.1).
- * Enqueued on the context's stream; returns after the last step has been
- * enqueued and its solver status checked.  DROPLET_ERR_NOT_CONVERGED is
- * returned when a linear solve reached its cap (the state is still advanced). */
+/* Advance every droplet by n_steps time steps (the stage list of Sec. 3.1):
+ * one launch of the captured step graph per step (captured at the first call;
+ * while profiling, the kernels are launched one by one instead).  Returns when
+ * the steps have finished (one stream synchronisation per call).
+ * DROPLET_ERR_NOT_CONVERGED is returned when a linear solve of any droplet
+ * reached its cap (the state is still advanced). */
 int droplet_step(droplet_ctx* ctx, int n_steps);
 
 /* Copy the diagnostics of droplet `droplet` into the caller-owned *out

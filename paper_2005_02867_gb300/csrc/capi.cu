@@ -7,13 +7,14 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 #include "kernels.h"
 
 using namespace dg;
 
 #define CKR(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) { fprintf(stderr, "droplet: %s at %s:%d\n", cudaGetErrorString(e_), __FILE__, __LINE__); return DROPLET_ERR_CUDA; } } while (0)
 
-struct droplet_ctx {
+struct dctx {
   cudaStream_t st = nullptr;
   droplet_config cfg;
   Geo g;
@@ -35,8 +36,8 @@ struct droplet_ctx {
   Solver solver;
   Prof prof;
   cudaStream_t st2 = nullptr;        // capture stream of the solver loop bodies
-  cudaStream_t own = nullptr;        // internal stream when the caller passed the legacy default stream
-  cudaGraphExec_t exec = nullptr;    // the captured step
+  cudaStream_t own = nullptr;        // the droplet's own stream in a batch
+  int rb = RED_BLOCKS;               // block cap of the reduction kernels
   int its_p = 0, its_T = 0, its_w = 0, its_u = 0;
   double res_p = 0.0, t = 0.0;
   long long step = 0;
@@ -118,7 +119,7 @@ static int dalloc(double** q, long long n) {
   return 0;
 }
 
-static void free_all(droplet_ctx* c) {
+static void free_all(dctx* c) {
   double** arrs[] = {&c->alpha, &c->T, &c->omega, &c->pr, &c->rhoG, &c->rhoG_old, &c->mdot, &c->mraw, &c->astar,
                      &c->aL, &c->Rp, &c->Rm, &c->rho, &c->mu, &c->kc, &c->cp, &c->Dm, &c->yq, &c->dp, &c->S,
                      &c->bD, &c->brhs, &c->bx, &c->part, &c->psum, &c->pmax, &c->scal, &c->xi};
@@ -133,15 +134,14 @@ static void free_all(droplet_ctx* c) {
   c->hscal = nullptr; c->hflags = nullptr;
   c->solver.release();
   c->prof.destroy();
-  if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->st2) cudaStreamDestroy(c->st2);
   if (c->own) cudaStreamDestroy(c->own);
-  c->exec = nullptr; c->st2 = nullptr; c->own = nullptr;
+  c->st2 = nullptr; c->own = nullptr;
 }
 
-static int run_diag(droplet_ctx* c) {
+static int run_diag(dctx* c) {
   Geo& g = c->g;
-  int nb = red_grid(g.N);
+  int nb = red_grid_cap(g.N, c->rb);
   L_diag(c->st, nb, g, c->alpha, c->T, c->mdot, c->omega, c->rhoG, c->u[0], c->u[1], c->u[2] ? c->u[2] : c->u[0],
                                 c->psum, c->pmax);
   ++g_launches, k_diag_finish<<<1, TPB, 0, c->st>>>(c->psum, c->pmax, nb, c->scal);
@@ -149,19 +149,17 @@ static int run_diag(droplet_ctx* c) {
   return 0;
 }
 
-extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cuda_stream, droplet_ctx** out) {
-  if (!cfgs || !out || n_droplets != 1) return DROPLET_ERR_ARG;
+// One droplet's context: device memory, solver workspace and the initial state (Sec. 3.3).
+// own_stream: the droplet works on a stream of its own (a branch of the batch graph).
+static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_stream, dctx** out) {
   *out = nullptr;
-  int rc = check_cfg(cfgs[0]);
-  if (rc) return rc;
-  droplet_ctx* c = new (std::nothrow) droplet_ctx();
+  int rc;
+  dctx* c = new (std::nothrow) dctx();
   if (!c) return DROPLET_ERR_NOMEM;
-  c->cfg = cfgs[0];
-  c->st = (cudaStream_t)cuda_stream;
-  if (!c->st) {
-    // the legacy default stream cannot be captured: work on an internal blocking stream,
-    // which the legacy default stream orders against all other work
-    if (cudaStreamCreate(&c->own) != cudaSuccess) { delete c; return DROPLET_ERR_CUDA; }
+  c->cfg = cfg;
+  c->st = main_st;
+  if (own_stream) {
+    if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) { delete c; return DROPLET_ERR_CUDA; }
     c->st = c->own;
   }
   if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_CUDA; }
@@ -189,6 +187,7 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
       cudaMallocHost((void**)&c->hscal, sizeof(double) * SC_COUNT) != cudaSuccess ||
       cudaMallocHost((void**)&c->hflags, sizeof(unsigned)) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_NOMEM; }
   c->solver.f32_helm = c->cfg.precision == 1;
+  c->solver.rb = c->rb;
   if ((rc = c->solver.setup(N, c->st))) { free_all(c); delete c; return rc; }
   c->solver.prof = &c->prof;
   c->solver.stream2 = c->st2;
@@ -228,13 +227,13 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
   return 0;
 }
 
-static int one_step(droplet_ctx* c, int* nc_flag) {
+static int one_step(dctx* c, int* nc_flag) {
   Geo& g = c->g;
   Phys& p = c->p;
   cudaStream_t st = c->st;
   long long N = g.N;
   int na = nact(g);
-  int gc = lin_grid(N), nb = red_grid(N);
+  int gc = lin_grid(N), nb = red_grid_cap(N, c->rb);
   double* u2 = c->u[2] ? c->u[2] : c->u[0];
   int mask = p.physics;
   cudaMemsetAsync(c->scal + SC_ITS_P, 0, sizeof(double) * 5, st);
@@ -286,7 +285,7 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
     cudaMemcpyAsync(c->T, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
   }
   // S6 species
-  ++g_launches, k_yeq<<<gc, TPB, 0, st>>>(g, p, c->T, c->alpha, c->yq, c->flags);
+  ++g_launches, k_yeq<<<gc, TPB, 0, st>>>(g, p, c->T, c->alpha, c->omega, c->yq, c->flags);
   if (mask & DROPLET_PHYS_SPECIES) {
     {
     ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
@@ -348,14 +347,54 @@ static int one_step(droplet_ctx* c, int* nc_flag) {
   return 0;
 }
 
-// Capture one step (every stage, every solver loop as a conditional WHILE node) into a graph.
+// ---------------------------------------------------------------- the public context
+struct droplet_ctx {
+  cudaStream_t st = nullptr;         // the caller's stream (or own_main)
+  cudaStream_t own_main = nullptr;   // internal stream when the caller passed the legacy default stream
+  std::vector<dctx*> d;              // one context per droplet
+  std::vector<cudaEvent_t> ev;       // fork / join events of the batch graph
+  cudaGraphExec_t exec = nullptr;    // the captured step of every droplet
+  double* hnc = nullptr;             // pinned not-converged marks
+  bool prof_on = false;
+  int rb = RED_BLOCKS;               // reduction block cap in use
+};
+
+static void free_ctx(droplet_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (auto x : c->d) {
+    if (x->st) cudaStreamSynchronize(x->st);
+    free_all(x);
+    delete x;
+  }
+  c->d.clear();
+  for (auto e : c->ev) cudaEventDestroy(e);
+  c->ev.clear();
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->hnc) cudaFreeHost(c->hnc);
+  if (c->own_main) cudaStreamDestroy(c->own_main);
+  delete c;
+}
+
+// Capture one step of every droplet into one graph: each droplet is a branch forked from
+// the main stream (every stage, every solver loop as a conditional WHILE node) and joined back.
 static int capture_step(droplet_ctx* c) {
   cudaGraph_t graph = nullptr;
-  int nc = 0;
+  int nc = 0, rc = 0;
+  bool batch = c->d.size() > 1;
   CKR(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeRelaxed));
-  c->solver.capturing = true;
-  int rc = one_step(c, &nc);
-  c->solver.capturing = false;
+  if (batch) CKR(cudaEventRecord(c->ev[0], c->st));
+  for (size_t i = 0; i < c->d.size() && !rc; ++i) {
+    dctx* x = c->d[i];
+    if (batch) cudaStreamWaitEvent(x->st, c->ev[0], 0);
+    x->solver.capturing = true;
+    rc = one_step(x, &nc);
+    x->solver.capturing = false;
+    if (batch) {
+      cudaEventRecord(c->ev[1 + i], x->st);
+      cudaStreamWaitEvent(c->st, c->ev[1 + i], 0);
+    }
+  }
   cudaError_t e = cudaStreamEndCapture(c->st, &graph);
   if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
   CKR(e);
@@ -365,18 +404,125 @@ static int capture_step(droplet_ctx* c) {
   return 0;
 }
 
+static void set_rb(droplet_ctx* c, int rb) {
+  c->rb = rb;
+  for (auto x : c->d) { x->rb = rb; x->solver.rb = rb; }
+}
+
+// Autotuner of the batch: the reduction kernels of every droplet run with at most rb blocks,
+// so that the branches of the batch graph share the SMs.  Each candidate is captured and
+// timed over a few steps on copies of the state; the fastest is kept and the state restored.
+static int autotune(droplet_ctx* c) {
+  const int cand[] = {RED_BLOCKS, 304, 152, 76, 38};
+  // snapshot the state of every droplet
+  std::vector<std::vector<double*>> snap(c->d.size());
+  for (size_t i = 0; i < c->d.size(); ++i) {
+    dctx* x = c->d[i];
+    double* fs[8] = {x->alpha, x->T, x->omega, x->pr, x->rhoG, x->u[0], x->u[1], x->u[2]};
+    for (int f = 0; f < 8; ++f) {
+      if (!fs[f]) { snap[i].push_back(nullptr); continue; }
+      long long n = f < 5 ? x->g.N : nfaces(x->g, f - 5);
+      double* q = nullptr;
+      if (cudaMalloc(&q, sizeof(double) * n) != cudaSuccess) return DROPLET_ERR_NOMEM;
+      cudaMemcpyAsync(q, fs[f], sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st);
+      snap[i].push_back(q);
+    }
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_rb = RED_BLOCKS;
+  for (int rb : cand) {
+    set_rb(c, rb);
+    if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
+    int rc = capture_step(c);
+    if (rc) return rc;
+    CKR(cudaGraphLaunch(c->exec, c->st));   // warm-up
+    CKR(cudaEventRecord(e0, c->st));
+    for (int k = 0; k < 3; ++k) CKR(cudaGraphLaunch(c->exec, c->st));
+    CKR(cudaEventRecord(e1, c->st));
+    CKR(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_rb = rb; }
+    // restore the state
+    for (size_t i = 0; i < c->d.size(); ++i) {
+      dctx* x = c->d[i];
+      double* fs[8] = {x->alpha, x->T, x->omega, x->pr, x->rhoG, x->u[0], x->u[1], x->u[2]};
+      for (int f = 0; f < 8; ++f) {
+        if (!fs[f]) continue;
+        long long n = f < 5 ? x->g.N : nfaces(x->g, f - 5);
+        cudaMemcpyAsync(fs[f], snap[i][f], sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st);
+      }
+      cudaMemsetAsync(x->scal, 0, sizeof(double) * SC_COUNT, c->st);
+      double dtv = x->cfg.dt;
+      cudaMemcpyAsync(x->scal + SC_DT, &dtv, sizeof(double), cudaMemcpyHostToDevice, c->st);
+      cudaMemsetAsync(x->flags, 0, sizeof(unsigned), c->st);
+      cudaMemsetAsync(x->dirty, 0xff, sizeof(int), c->st);
+    }
+    CKR(cudaStreamSynchronize(c->st));
+  }
+  for (auto& v : snap) for (auto q : v) cudaFree(q);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  set_rb(c, best_rb);
+  if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
+  for (auto x : c->d) if (run_diag(x)) return DROPLET_ERR_CUDA;
+  CKR(cudaStreamSynchronize(c->st));
+  return 0;
+}
+
+extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cuda_stream, droplet_ctx** out) {
+  if (!cfgs || !out || n_droplets < 1 || n_droplets > 4096) return DROPLET_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n_droplets; ++i) {
+    int rc = check_cfg(cfgs[i]);
+    if (rc) return rc;
+  }
+  droplet_ctx* c = new (std::nothrow) droplet_ctx();
+  if (!c) return DROPLET_ERR_NOMEM;
+  c->st = (cudaStream_t)cuda_stream;
+  if (!c->st) {
+    // the legacy default stream cannot be captured: work on an internal blocking stream,
+    // which the legacy default stream orders against all other work
+    if (cudaStreamCreate(&c->own_main) != cudaSuccess) { delete c; return DROPLET_ERR_CUDA; }
+    c->st = c->own_main;
+  }
+  if (cudaMallocHost((void**)&c->hnc, sizeof(double) * n_droplets) != cudaSuccess) { free_ctx(c); return DROPLET_ERR_NOMEM; }
+  bool batch = n_droplets > 1;
+  for (int i = 0; i < n_droplets; ++i) {
+    dctx* x = nullptr;
+    int rc = init_one(cfgs[i], c->st, batch, &x);
+    if (rc) { free_ctx(c); return rc; }
+    c->d.push_back(x);
+  }
+  if (batch) {
+    c->ev.resize(n_droplets + 1);
+    for (auto& e : c->ev)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { free_ctx(c); return DROPLET_ERR_CUDA; }
+    int rc = autotune(c);
+    if (rc) { free_ctx(c); return rc; }
+  }
+  *out = c;
+  return 0;
+}
+
 extern "C" int droplet_step(droplet_ctx* c, int n_steps) {
   if (!c || n_steps < 0) return DROPLET_ERR_ARG;
   int nc = 0;
-  CKR(cudaMemsetAsync(c->scal + SC_NC, 0, sizeof(double), c->st));
-  if (c->prof.on) {
+  for (auto x : c->d) CKR(cudaMemsetAsync(x->scal + SC_NC, 0, sizeof(double), x->st));
+  for (auto x : c->d) if (x->st != c->st) CKR(cudaStreamSynchronize(x->st));
+  if (c->prof_on) {
     // timed kernel classes need one event pair per launch: run the stages directly
-    for (int s = 0; s < n_steps; ++s) {
-      int rc = one_step(c, &nc);
-      if (rc) return rc;
-      c->t += c->p.dt;
-      c->step += 1;
-    }
+    for (int s = 0; s < n_steps; ++s)
+      for (auto x : c->d) {
+        int rc = one_step(x, &nc);
+        if (rc) return rc;
+        x->t += x->p.dt;
+        x->step += 1;
+      }
+    for (auto x : c->d) if (x->st != c->st) CKR(cudaStreamSynchronize(x->st));
   } else {
     if (!c->exec) {
       int rc = capture_step(c);
@@ -384,27 +530,42 @@ extern "C" int droplet_step(droplet_ctx* c, int n_steps) {
     }
     for (int s = 0; s < n_steps; ++s) {
       CKR(cudaGraphLaunch(c->exec, c->st));
-      c->t += c->p.dt;
-      c->step += 1;
+      for (auto x : c->d) { x->t += x->p.dt; x->step += 1; }
     }
   }
-  CKR(cudaMemcpyAsync(c->hscal + SC_NC, c->scal + SC_NC, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  for (size_t i = 0; i < c->d.size(); ++i)
+    CKR(cudaMemcpyAsync(c->hnc + i, c->d[i]->scal + SC_NC, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CKR(cudaStreamSynchronize(c->st));
-  if (c->hscal[SC_NC] != 0.0) nc = 1;
+  for (size_t i = 0; i < c->d.size(); ++i)
+    if (c->hnc[i] != 0.0) nc = 1;
   return nc ? DROPLET_ERR_NOT_CONVERGED : 0;
 }
 
 extern "C" int droplet_profile(droplet_ctx* c, int enable) {
   if (!c) return DROPLET_ERR_ARG;
   CKR(cudaStreamSynchronize(c->st));
-  if (enable) c->prof.reset();
-  c->prof.on = enable != 0;
+  for (auto x : c->d) {
+    CKR(cudaStreamSynchronize(x->st));
+    if (enable) x->prof.reset();
+    x->prof.on = enable != 0;
+  }
+  c->prof_on = enable != 0;
   return 0;
 }
 
 extern "C" int droplet_profile_read(droplet_ctx* c, int kclass, double* ms, long long* launches, double* bytes) {
   if (!c || !ms || !launches || !bytes || kclass < 0 || kclass >= KC_COUNT) return DROPLET_ERR_ARG;
-  return c->prof.read(kclass, ms, launches, bytes);
+  double tm = 0.0, tb = 0.0;
+  long long tn = 0;
+  for (auto x : c->d) {
+    double m, b;
+    long long n;
+    int rc = x->prof.read(kclass, &m, &n, &b);
+    if (rc) return rc;
+    tm += m; tb += b; tn += n;
+  }
+  *ms = tm; *launches = tn; *bytes = tb;
+  return 0;
 }
 
 extern "C" int droplet_launch_count(droplet_ctx* c, long long* launches) {
@@ -416,11 +577,14 @@ extern "C" int droplet_launch_count(droplet_ctx* c, long long* launches) {
 extern "C" int droplet_sync(droplet_ctx* c) {
   if (!c) return DROPLET_ERR_ARG;
   CKR(cudaStreamSynchronize(c->st));
+  for (auto x : c->d) CKR(cudaStreamSynchronize(x->st));
   return 0;
 }
 
-extern "C" int droplet_diag(droplet_ctx* c, int droplet, droplet_diag_t* out) {
-  if (!c || !out || droplet != 0) return DROPLET_ERR_ARG;
+extern "C" int droplet_diag(droplet_ctx* cc, int droplet, droplet_diag_t* out) {
+  if (!cc || !out || droplet < 0 || droplet >= (int)cc->d.size()) return DROPLET_ERR_ARG;
+  dctx* c = cc->d[droplet];
+  CKR(cudaStreamSynchronize(cc->st));
   CKR(cudaMemcpyAsync(c->hscal, c->scal, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, c->st));
   CKR(cudaMemcpyAsync(c->hflags, c->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
   CKR(cudaMemsetAsync(c->flags, 0, sizeof(unsigned), c->st));
@@ -451,7 +615,7 @@ extern "C" int droplet_diag(droplet_ctx* c, int droplet, droplet_diag_t* out) {
   return 0;
 }
 
-static double* field_ptr(droplet_ctx* c, int id, long long* n, bool* writable) {
+static double* field_ptr(dctx* c, int id, long long* n, bool* writable) {
   Geo& g = c->g;
   *writable = false;
   *n = g.N;
@@ -480,46 +644,45 @@ static double* field_ptr(droplet_ctx* c, int id, long long* n, bool* writable) {
   return star ? c->us[a] : c->u[a];
 }
 
-extern "C" int droplet_field_size(droplet_ctx* c, int droplet, int field_id, size_t* n) {
-  if (!c || !n || droplet != 0) return DROPLET_ERR_ARG;
+extern "C" int droplet_field_size(droplet_ctx* cc, int droplet, int field_id, size_t* n) {
+  if (!cc || !n || droplet < 0 || droplet >= (int)cc->d.size()) return DROPLET_ERR_ARG;
   long long m;
   bool w;
-  if (!field_ptr(c, field_id, &m, &w)) return DROPLET_ERR_ARG;
+  if (!field_ptr(cc->d[droplet], field_id, &m, &w)) return DROPLET_ERR_ARG;
   *n = (size_t)m;
   return 0;
 }
 
-extern "C" int droplet_get_field(droplet_ctx* c, int droplet, int field_id, double* host, size_t n) {
-  if (!c || !host || droplet != 0) return DROPLET_ERR_ARG;
+extern "C" int droplet_get_field(droplet_ctx* cc, int droplet, int field_id, double* host, size_t n) {
+  if (!cc || !host || droplet < 0 || droplet >= (int)cc->d.size()) return DROPLET_ERR_ARG;
+  dctx* c = cc->d[droplet];
   long long m;
   bool w;
   double* d = field_ptr(c, field_id, &m, &w);
   if (!d) return DROPLET_ERR_ARG;
   if ((size_t)m != n) return DROPLET_ERR_SIZE;
+  CKR(cudaStreamSynchronize(cc->st));
   CKR(cudaMemcpyAsync(host, d, sizeof(double) * n, cudaMemcpyDeviceToHost, c->st));
   CKR(cudaStreamSynchronize(c->st));
   return 0;
 }
 
-extern "C" int droplet_set_field(droplet_ctx* c, int droplet, int field_id, const double* host, size_t n) {
-  if (!c || !host || droplet != 0) return DROPLET_ERR_ARG;
+extern "C" int droplet_set_field(droplet_ctx* cc, int droplet, int field_id, const double* host, size_t n) {
+  if (!cc || !host || droplet < 0 || droplet >= (int)cc->d.size()) return DROPLET_ERR_ARG;
+  dctx* c = cc->d[droplet];
   long long m;
   bool w;
   double* d = field_ptr(c, field_id, &m, &w);
   if (!d || !w) return DROPLET_ERR_ARG;
   if ((size_t)m != n) return DROPLET_ERR_SIZE;
+  CKR(cudaStreamSynchronize(cc->st));
   CKR(cudaMemcpyAsync(d, host, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
   CKR(cudaMemsetAsync(c->dirty, 0xff, sizeof(int), c->st));
   CKR(cudaStreamSynchronize(c->st));
   return 0;
 }
 
-extern "C" void droplet_free(droplet_ctx* c) {
-  if (!c) return;
-  cudaStreamSynchronize(c->st);
-  free_all(c);
-  delete c;
-}
+extern "C" void droplet_free(droplet_ctx* c) { free_ctx(c); }
 
 extern "C" int droplet_box_solve(const int m[3], const double* D, const double* c0, const double* c1,
                                  const double* c2, const double* b, double* x, double rtol, int maxit,

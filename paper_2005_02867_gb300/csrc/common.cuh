@@ -240,12 +240,16 @@ __device__ inline void pr_binary(const Phys& p, double T, double P, double y, do
   lnphi0 = b0 / bm * (Z - 1.0) - log(Z - B) - A / (2.0 * s2 * B) * (2.0 * sa / am - b0 / bm) * logterm;
 }
 
-// saturation mole fraction (Raoult, or the Peng-Robinson fixed point with the Poynting factor)
-__device__ inline double y_eq(const Phys& p, double T, unsigned* boil) {
+// saturation mole fraction (Raoult, or the Peng-Robinson fixed point with the Poynting factor).
+// y_start > 0 starts the fixed point there instead of at the Raoult value (a pinned cell's
+// previous saturation value: the iteration then stops after a few steps at the same
+// fixed point, within its 1e-13 tolerance).
+__device__ inline double y_eq(const Phys& p, double T, unsigned* boil, double y_start = -1.0) {
   double p0 = psat(p, T);
   double y = p0 / p.P;
   if (y > Y_CLAMP) { y = Y_CLAMP; if (boil) *boil = 1u; }
   if (p.eq_model == 0) return y;
+  if (y_start > 0.0 && y_start < Y_CLAMP) y = y_start;
   double Zp, lp;
   pr_binary(p, T, p0, 1.0, Zp, lp);
   double vL = p.M_l / p.rho_l;
@@ -262,7 +266,9 @@ __device__ inline double y_eq(const Phys& p, double T, unsigned* boil) {
   return y;
 }
 
-__device__ __forceinline__ double Y_eq(const Phys& p, double T, unsigned* boil) { return Y_from_y(p, y_eq(p, T, boil)); }
+__device__ __forceinline__ double Y_eq(const Phys& p, double T, unsigned* boil, double Y_start = -1.0) {
+  return Y_from_y(p, y_eq(p, T, boil, Y_start > 0.0 ? y_from_Y(p, Y_start) : -1.0));
+}
 
 __device__ inline double rho_gas(const Phys& p, double T, double Y) {
   if (p.const_props) return p.rhoG_const;
@@ -359,6 +365,13 @@ __device__ __forceinline__ bool last_block(unsigned* cnt) {
   if (threadIdx.x == 0) am_last = atomicAdd(cnt, 1u) == gridDim.x - 1;
   __syncthreads();
   return am_last;
+}
+
+// grid of a reduction kernel with at most cap blocks (cap <= RED_BLOCKS, the partial buffers' size)
+inline int red_grid_cap(long long n, int cap) {
+  long long b = (n + TPB - 1) / TPB;
+  if (cap < 1 || cap > RED_BLOCKS) cap = RED_BLOCKS;
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
 inline int red_grid(long long n) {

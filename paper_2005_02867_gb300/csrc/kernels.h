@@ -63,7 +63,8 @@ __global__ void k_alpha_clip_only(Geo g, const double* as, double* alpha, double
 __global__ void k_props(Geo g, Phys p, const double* alpha, const double* rhoG, const double* omega, double* rho,
                         double* mu, double* kc, double* cp, double* D);
 
-__global__ void k_yeq(Geo g, Phys p, const double* T, const double* alpha, double* yq, unsigned* flags);
+__global__ void k_yeq(Geo g, Phys p, const double* T, const double* alpha, const double* omega, double* yq,
+                      unsigned* flags);
 __global__ void k_species_noflow(Geo g, const double* alpha_new, const double* yq, double* omega);
 __global__ void k_rhoG(Geo g, Phys p, const double* T, const double* w, double* rhoG);
 
@@ -131,6 +132,7 @@ class Solver {
   cudaStream_t stream2 = nullptr;   // captures the bodies of the device-driven solver loops
   bool capturing = false;           // the step is being captured into a CUDA graph
   bool f32_helm = false;            // Jacobi-PCG as FP32 defect correction (set before setup)
+  int rb = RED_BLOCKS;              // block cap of the reduction kernels (tuned for batches)
   Prof* prof = nullptr;
 
  private:

@@ -744,7 +744,7 @@ int Solver::device_loop(F body) {
 int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
   if (f32_helm) return pcg_jacobi_f32(s, rtol, maxit, out);
   BoxV A = view(s);
-  int nb = red_grid(s.N);
+  int nb = red_grid_cap(s.N, rb);
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 1, part);
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);
   auto iteration = [&]() {
@@ -777,7 +777,7 @@ int Solver::pcg_jacobi_f32(const BoxSys& s, double rtol, int maxit, SolveStats* 
   for (int a = 0; a < 3; ++a) { Af.m[a] = s.m[a]; Af.c[a] = s.c[a] ? fc[a] : nullptr; }
   Af.N = s.N;
   Af.D = fD;
-  int nb = red_grid(s.N);
+  int nb = red_grid_cap(s.N, rb);
   // FP64 defect of the initial guess, ||b||, ||r0||
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);
@@ -908,7 +908,7 @@ static void smooth(Prof* prof, LevV<T> L, int col, int first, const int* done, c
 template <typename T>
 static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaStream_t st) {
   const int nu = 2;          // smoothing sweeps (red + black) before and after
-  const int ncoarse = 16;    // symmetric sweep pairs on the coarsest level
+  const int ncoarse = 4;     // symmetric sweep pairs on the coarsest level (at most 2^d x ... cells)
   // levels from `lt` on run inside one block (k_mg_tail)
   int lt = nlev - 1;
   while (lt > 0 && lev[lt - 1].N <= TAIL_MAX_CELLS) --lt;
@@ -959,7 +959,7 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
   if (rc) return rc;
   if (!fp32) { lev[0].b = r; lev[0].x = z; }
   BoxV A = view(s);
-  int nb = red_grid(s.N);
+  int nb = red_grid_cap(s.N, rb);
   int g = lin_grid(s.N);
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);

@@ -123,7 +123,7 @@ __global__ void k_thermo_pin(Geo g, Phys p, const double* alpha, const double* T
   unsigned boil = 0;
   double w = omega[id];
   bool liq = alpha[id] >= 0.5;
-  if (liq) { w = Y_eq(p, T[id], &boil); omega[id] = w; }
+  if (liq) { w = Y_eq(p, T[id], &boil, w); omega[id] = w; }
   rhoG_old[id] = (liq || *dirty) ? rho_gas(p, T[id], w) : rhoG[id];
   if (boil) atomicOr(flags, (unsigned)DROPLET_FLAG_BOILING);
 }
@@ -524,12 +524,13 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
 }
 
 // saturation value for the rows pinned in the species solve (alpha >= 1/2); 0 elsewhere (unused)
-__global__ void k_yeq(Geo g, Phys p, const double* T, const double* alpha, double* yq, unsigned* flags) {
+__global__ void k_yeq(Geo g, Phys p, const double* T, const double* alpha, const double* omega, double* yq,
+                      unsigned* flags) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
   if (alpha[id] < 0.5) { yq[id] = 0.0; return; }
   unsigned b = 0;
-  yq[id] = Y_eq(p, T[id], &b);
+  yq[id] = Y_eq(p, T[id], &b, omega[id]);
   if (b) atomicOr(flags, (unsigned)DROPLET_FLAG_BOILING);
 }
 

@@ -125,15 +125,17 @@ def make_config(cfg):
 # ------------------------------------------------------------ C-named wrappers
 
 def droplet_init(cfg, stream=None):
-    """Returns the context handle (int).  stream: a cudaStream_t as int, or None
-    for torch's current stream on the current device."""
+    """Returns the context handle (int).  cfg: one config dict, or a list of them
+    (a batch of independent droplets stepped together).  stream: a cudaStream_t
+    as int, or None for torch's current stream on the current device."""
     lib = load_library()
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
-    c = make_config(cfg)
+    cfgs = cfg if isinstance(cfg, (list, tuple)) else [cfg]
+    arr = (DropletConfig * len(cfgs))(*[make_config(x) for x in cfgs])
     h = ctypes.c_void_p()
-    rc = lib.droplet_init(ctypes.byref(c), 1, ctypes.c_void_p(stream), ctypes.byref(h))
+    rc = lib.droplet_init(arr, len(cfgs), ctypes.c_void_p(stream), ctypes.byref(h))
     if rc:
         raise DropletError(rc, "droplet_init")
     return h.value
@@ -252,10 +254,12 @@ def droplet_free(h):
 
 
 class Droplet:
-    """One droplet context on the current CUDA device."""
+    """A context of one droplet (cfg a dict) or of a batch (cfg a list of dicts)
+    on the current CUDA device."""
 
     def __init__(self, cfg, stream=None):
         self.cfg = cfg
+        self.n = len(cfg) if isinstance(cfg, (list, tuple)) else 1
         self.h = droplet_init(cfg, stream)
         self.last_status = 0
 
@@ -263,14 +267,14 @@ class Droplet:
         self.last_status = droplet_step(self.h, n)
         return self.last_status
 
-    def diag(self):
-        return droplet_diag(self.h)
+    def diag(self, droplet=0):
+        return droplet_diag(self.h, droplet)
 
-    def get(self, field):
-        return droplet_get_field(self.h, field)
+    def get(self, field, droplet=0):
+        return droplet_get_field(self.h, field, droplet=droplet)
 
-    def set(self, field, values):
-        droplet_set_field(self.h, field, values)
+    def set(self, field, values, droplet=0):
+        droplet_set_field(self.h, field, values, droplet=droplet)
 
     def sync(self):
         droplet_sync(self.h)
