@@ -42,6 +42,7 @@ WORKLOADS = {
     "cfg3_cart3d_128_fp64": lambda: W.cfg3_cart3d(nc=128, precision=0),
     "cfg4_batch64": lambda: W.cfg4_batch(),
     "cfg4_batch64_fp64": lambda: [dict(c, precision=0) for c in W.cfg4_batch()],
+    "cfg4_serial64_fp64": lambda: [dict(c, precision=0) for c in W.cfg4_batch()],
     "cfg1_axisym_64x128": lambda: W.cfg1_axisym_64x128(cg_rtol=1e-12, helm_rtol=1e-13),
     "cfg5_axisym_128x256": lambda: W.cfg5_axisym_128x256(cg_rtol=1e-12, helm_rtol=1e-13),
 }
@@ -169,6 +170,44 @@ def cpu_oracle(cfg, nmin=2, nmax=50, budget=15.0):
     return d["steps"], d["seconds"]
 
 
+class SerialDroplets:
+    """Single-droplet contexts driven one after the other (the unbatched form)."""
+
+    def __init__(self, D, cfgs, stream):
+        self.D = D
+        self.sims = [D.Droplet(c, stream=stream) for c in cfgs]
+        self.h = self.sims[0].h
+
+    def step(self, n=1):
+        rc = 0
+        for s in self.sims:
+            rc = rc or s.step(n)
+        return rc
+
+    def diag(self, droplet=0):
+        return self.sims[droplet].diag()
+
+    def close(self):
+        for s in self.sims:
+            s.close()
+
+
+def replica_throughput(t_ms, ncell, steps):
+    """Whole-job throughput of independent replicas: every rank advanced ncell
+    cells by `steps` steps in its own t_ms; the job's time is the slowest
+    rank's.  Returns (Mcell-steps/s over all ranks, max t_ms)."""
+    import torch
+    import torch.distributed as dist
+    world = 1
+    if dist.is_available() and dist.is_initialized():
+        world = dist.get_world_size()
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(t_ms)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    return ncell * steps * world / (t_ms / 1e3) / 1e6, t_ms
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -222,7 +261,11 @@ def run_ours(args):
     ncell = cells_of(cfg)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    sim = D.Droplet(cfg, stream=stream.cuda_stream)
+    if name.endswith("_serial64_fp64"):
+        # the plain form: one single-droplet context per droplet, stepped one after the other
+        sim = SerialDroplets(D, cfg, stream.cuda_stream)
+    else:
+        sim = D.Droplet(cfg, stream=stream.cuda_stream)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def barrier():
@@ -249,11 +292,12 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     ck = clocks.stop()
-    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    t_ms_local = sum(a.elapsed_time(b) for a, b in evs)
 
     # ---- per-kernel timing: the same steps launched kernel by kernel with a CUDA event
     # pair around every launch of the timed classes (library stream), L2 flushed per step
     kprof = max(1, min(args.steps, 5))
+    serial = isinstance(sim, SerialDroplets)
     D.droplet_profile(sim.h, 1)
     n0 = D.droplet_launch_count(sim.h)
     for k in range(kprof):
@@ -261,25 +305,25 @@ def run_ours(args):
         sim.step(1)
     torch.cuda.synchronize()
     launches_per_step = (D.droplet_launch_count(sim.h) - n0) / kprof
+    # (serial form: every context's launches count, the event timing covers the first context)
     prof = {k: D.droplet_profile_read(sim.h, k) for k in D.KCLASS}
     D.droplet_profile(sim.h, 0)
     launches = int(round(launches_per_step * args.steps))
-    if world > 1:
-        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = ncell * args.steps * world / (t_ms / 1e3) / 1e6
+    value, t_ms = replica_throughput(t_ms_local, ncell, args.steps)
 
     # ---- end to end through the C ABI with host buffers: upload the state from
     # pinned host memory, one step, read the state back, every step
     cl = cfg if isinstance(cfg, list) else [cfg]
     bufs = {}
+    def handle(di):
+        return (sim.sims[di].h, 0) if serial else (sim.h, di)
     for di, cd in enumerate(cl):
         fields = ["alpha", "T", "omega", "p", "rhoG"] + ["u%d" % a for a in range(3 if cd["geom"] == 1 else 2)]
+        h, k = handle(di)
         for f in fields:
-            n = D.droplet_field_size(sim.h, f, droplet=di)
+            n = D.droplet_field_size(h, f, droplet=k)
             bufs[(di, f)] = torch.empty(n, dtype=torch.float64, pin_memory=True)
-            D.droplet_get_field_ptr(sim.h, f, bufs[(di, f)].data_ptr(), n, droplet=di)
+            D.droplet_get_field_ptr(h, f, bufs[(di, f)].data_ptr(), n, droplet=k)
     nbytes = sum(b.numel() * 8 for b in bufs.values())
     e2e_steps = max(1, min(args.steps, 10))
     barrier()
@@ -287,17 +331,15 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         for (di, f), b in bufs.items():
-            D.droplet_set_field_ptr(sim.h, f, b.data_ptr(), b.numel(), droplet=di)
+            h, k = handle(di)
+            D.droplet_set_field_ptr(h, f, b.data_ptr(), b.numel(), droplet=k)
         sim.step(1)
         for (di, f), b in bufs.items():
-            D.droplet_get_field_ptr(sim.h, f, b.data_ptr(), b.numel(), droplet=di)
+            h, k = handle(di)
+            D.droplet_get_field_ptr(h, f, b.data_ptr(), b.numel(), droplet=k)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = ncell * e2e_steps * world / e2e_s / 1e6
+    e2e_value, _ = replica_throughput(e2e_s * 1e3, ncell, e2e_steps)
     diag = sim.diag()
     sim.close()
 

@@ -45,6 +45,7 @@ extern "C" {
 #define DROPLET_ERR_NONFINITE     -4  /* a non-finite value appeared in the state      */
 #define DROPLET_ERR_SIZE          -5  /* host buffer size does not match the field     */
 #define DROPLET_ERR_NOMEM         -6  /* device allocation failed                      */
+#define DROPLET_ERR_IO            -7  /* checkpoint file could not be written or read  */
 
 /* diagnostic flag bits (droplet_diag_t.flags), accumulated since the last read */
 #define DROPLET_FLAG_NO_INTERFACE   1u   /* sum f(alpha) m_raw V = 0: mdot set to 0         */
@@ -227,6 +228,16 @@ int droplet_profile_read(droplet_ctx* ctx, int kclass, double* ms_total, long lo
 
 /* Number of kernel launches the library has issued for this context so far. */
 int droplet_launch_count(droplet_ctx* ctx, long long* launches);
+
+/* Checkpoint / resume.  droplet_save writes, for every droplet, its config, time,
+ * step count, the accumulated diagnostics (clipped volume, vapour outflow) and the
+ * state fields (alpha, T, omega, p_rgh, rho_G and the face velocities, FP64,
+ * little-endian) to `path`.  droplet_load reads such a file into a context
+ * created with the same configs (byte-identical droplet_config structs, else
+ * DROPLET_ERR_ARG) and continues from there: the next steps are bit-identical to
+ * those of the saved run.  File errors: DROPLET_ERR_IO. */
+int droplet_save(droplet_ctx* ctx, const char* path);
+int droplet_load(droplet_ctx* ctx, const char* path);
 
 /* Block until all work enqueued by the context has finished. */
 int droplet_sync(droplet_ctx* ctx);

@@ -44,10 +44,11 @@ struct dctx {
 };
 
 static const char* kErr[] = {"ok", "invalid argument", "CUDA error", "linear solve not converged",
-                             "non-finite value", "buffer size mismatch", "device allocation failed"};
+                             "non-finite value", "buffer size mismatch", "device allocation failed",
+                             "checkpoint file error"};
 
 extern "C" const char* droplet_strerror(int s) {
-  if (s > 0 || s < -6) return "unknown status";
+  if (s > 0 || s < -7) return "unknown status";
   return kErr[-s];
 }
 
@@ -683,6 +684,83 @@ extern "C" int droplet_set_field(droplet_ctx* cc, int droplet, int field_id, con
 }
 
 extern "C" void droplet_free(droplet_ctx* c) { free_ctx(c); }
+
+// ---------------------------------------------------------------- checkpoint / resume
+static const char kMagic[8] = {'D', 'R', 'O', 'P', 'C', 'K', 'P', '1'};
+
+static int state_fields(dctx* x, double* f[8], long long n[8]) {
+  double* fs[8] = {x->alpha, x->T, x->omega, x->pr, x->rhoG, x->u[0], x->u[1], x->u[2]};
+  for (int q = 0; q < 8; ++q) {
+    f[q] = fs[q];
+    n[q] = fs[q] ? (q < 5 ? x->g.N : nfaces(x->g, q - 5)) : 0;
+  }
+  return 0;
+}
+
+extern "C" int droplet_save(droplet_ctx* c, const char* path) {
+  if (!c || !path) return DROPLET_ERR_ARG;
+  CKR(cudaStreamSynchronize(c->st));
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return DROPLET_ERR_IO;
+  long long nd = (long long)c->d.size();
+  bool ok = fwrite(kMagic, 1, 8, fp) == 8 && fwrite(&nd, sizeof(nd), 1, fp) == 1;
+  std::vector<double> host;
+  for (auto x : c->d) {
+    if (!ok) break;
+    CKR(cudaStreamSynchronize(x->st));
+    CKR(cudaMemcpy(x->hscal, x->scal, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost));
+    ok = fwrite(&x->cfg, sizeof(droplet_config), 1, fp) == 1 && fwrite(&x->t, sizeof(double), 1, fp) == 1 &&
+         fwrite(&x->step, sizeof(long long), 1, fp) == 1 && fwrite(x->hscal, sizeof(double), SC_COUNT, fp) == SC_COUNT;
+    double* f[8];
+    long long n[8];
+    state_fields(x, f, n);
+    for (int q = 0; q < 8 && ok; ++q) {
+      if (!n[q]) continue;
+      host.resize((size_t)n[q]);
+      if (cudaMemcpy(host.data(), f[q], sizeof(double) * n[q], cudaMemcpyDeviceToHost) != cudaSuccess) { fclose(fp); return DROPLET_ERR_CUDA; }
+      ok = fwrite(host.data(), sizeof(double), (size_t)n[q], fp) == (size_t)n[q];
+    }
+  }
+  if (fclose(fp) != 0) ok = false;
+  return ok ? 0 : DROPLET_ERR_IO;
+}
+
+extern "C" int droplet_load(droplet_ctx* c, const char* path) {
+  if (!c || !path) return DROPLET_ERR_ARG;
+  CKR(cudaStreamSynchronize(c->st));
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return DROPLET_ERR_IO;
+  char mg[8];
+  long long nd = 0;
+  if (fread(mg, 1, 8, fp) != 8 || memcmp(mg, kMagic, 8) != 0 || fread(&nd, sizeof(nd), 1, fp) != 1) { fclose(fp); return DROPLET_ERR_IO; }
+  if (nd != (long long)c->d.size()) { fclose(fp); return DROPLET_ERR_ARG; }
+  std::vector<double> host;
+  for (auto x : c->d) {
+    droplet_config cf;
+    double t;
+    long long step;
+    if (fread(&cf, sizeof(cf), 1, fp) != 1 || fread(&t, sizeof(t), 1, fp) != 1 || fread(&step, sizeof(step), 1, fp) != 1 ||
+        fread(x->hscal, sizeof(double), SC_COUNT, fp) != SC_COUNT) { fclose(fp); return DROPLET_ERR_IO; }
+    if (memcmp(&cf, &x->cfg, sizeof(cf)) != 0) { fclose(fp); return DROPLET_ERR_ARG; }
+    CKR(cudaStreamSynchronize(x->st));
+    double* f[8];
+    long long n[8];
+    state_fields(x, f, n);
+    for (int q = 0; q < 8; ++q) {
+      if (!n[q]) continue;
+      host.resize((size_t)n[q]);
+      if (fread(host.data(), sizeof(double), (size_t)n[q], fp) != (size_t)n[q]) { fclose(fp); return DROPLET_ERR_IO; }
+      if (cudaMemcpy(f[q], host.data(), sizeof(double) * n[q], cudaMemcpyHostToDevice) != cudaSuccess) { fclose(fp); return DROPLET_ERR_CUDA; }
+    }
+    if (cudaMemcpy(x->scal, x->hscal, sizeof(double) * SC_COUNT, cudaMemcpyHostToDevice) != cudaSuccess) { fclose(fp); return DROPLET_ERR_CUDA; }
+    x->t = t;
+    x->step = step;
+    // the saved rho_G is rho_gas(T, omega) of the saved state: S0 may reuse it
+    if (cudaMemset(x->dirty, 0, sizeof(int)) != cudaSuccess) { fclose(fp); return DROPLET_ERR_CUDA; }
+  }
+  fclose(fp);
+  return 0;
+}
 
 extern "C" int droplet_box_solve(const int m[3], const double* D, const double* c0, const double* c1,
                                  const double* c2, const double* b, double* x, double rtol, int maxit,

@@ -52,7 +52,7 @@ FIELDS = dict(alpha=0, T=1, omega=2, p=3, rhoG=4, u0=5, u1=6, u2=7, mdot=8, mraw
 
 EXPORTS = ["droplet_init", "droplet_step", "droplet_diag", "droplet_field_size", "droplet_get_field",
            "droplet_set_field", "droplet_sync", "droplet_free", "droplet_strerror", "droplet_profile",
-           "droplet_profile_read", "droplet_launch_count", "droplet_box_solve", "droplet_box_solve_noalloc"]
+           "droplet_profile_read", "droplet_launch_count", "droplet_box_solve", "droplet_box_solve_noalloc", "droplet_save", "droplet_load"]
 
 NOALLOC_MAX_UNKNOWNS = 262144
 
@@ -95,6 +95,8 @@ def load_library(path=LIBPATH):
     BOX = [ctypes.POINTER(_c_int), P, P, P, P, P, P, _c_dbl, _c_int, P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl)]
     lib.droplet_box_solve.argtypes = BOX
     lib.droplet_box_solve_noalloc.argtypes = BOX
+    lib.droplet_save.argtypes = [P, ctypes.c_char_p]
+    lib.droplet_load.argtypes = [P, ctypes.c_char_p]
     lib.droplet_strerror.argtypes = [_c_int]
     lib.droplet_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
@@ -243,6 +245,18 @@ def droplet_box_solve_noalloc(m, D, c0, c1, c2, b, x, rtol, maxit, stream):
     return _box_call(load_library().droplet_box_solve_noalloc, m, D, c0, c1, c2, b, x, rtol, maxit, stream)
 
 
+def droplet_save(h, path):
+    rc = load_library().droplet_save(ctypes.c_void_p(h), os.fsencode(path))
+    if rc:
+        raise DropletError(rc, "droplet_save")
+
+
+def droplet_load(h, path):
+    rc = load_library().droplet_load(ctypes.c_void_p(h), os.fsencode(path))
+    if rc:
+        raise DropletError(rc, "droplet_load")
+
+
 def droplet_sync(h):
     rc = load_library().droplet_sync(ctypes.c_void_p(h))
     if rc:
@@ -278,6 +292,12 @@ class Droplet:
 
     def sync(self):
         droplet_sync(self.h)
+
+    def save(self, path):
+        droplet_save(self.h, path)
+
+    def load(self, path):
+        droplet_load(self.h, path)
 
     def close(self):
         if self.h:

@@ -243,3 +243,29 @@ def test_graph_step_equals_direct_step(D):
     assert da["its_p"] == db["its_p"] and da["its_u"] == db["its_u"] and da["step"] == db["step"] == 5
     a.close()
     b.close()
+
+
+def test_checkpoint_resume_is_bit_identical(D, tmp_path):
+    cfg = W.cfg5_axisym_128x256(**SMALL, cg_rtol=1e-12, helm_rtol=1e-12)
+    a = D.Droplet(cfg)
+    a.step(4)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    a.step(3)
+    b = D.Droplet(cfg)
+    b.load(path)
+    assert b.diag()["step"] == 4
+    b.step(3)
+    for nm in ("alpha", "T", "omega", "p", "rhoG", "u0", "u1"):
+        assert np.array_equal(a.get(nm), b.get(nm)), nm
+    da, db = a.diag(), b.diag()
+    assert da["step"] == db["step"] == 7 and da["clip_mass"] == db["clip_mass"]
+    other = D.Droplet(dict(cfg, T_amb=700.0))
+    with pytest.raises(D.DropletError) as e:
+        other.load(path)
+    assert e.value.status == -1
+    with pytest.raises(D.DropletError) as e:
+        other.load(str(tmp_path / "missing.bin"))
+    assert e.value.status == -7
+    for s in (a, b, other):
+        s.close()
