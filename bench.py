@@ -345,20 +345,31 @@ def run_ours(args):
 
     if rank == 0:
         dom = max(prof, key=lambda k: prof[k][0])
-        ms, nl, by = prof[dom]
-        achieved = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        ms, nl, by, fl = prof[dom]
+        hbm_gbs = by / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        fp64_tfs = fl / (ms / 1e3) / 1e12 if ms > 0 else 0.0
         peak, src = load_peaks()
+        # GB300's FP64 pipe (1.25 TFLOP/s nominal, 1.2 measured with an FMA loop) is the
+        # tighter roof for FP64 stencils: report the bound with the larger fraction
+        fp64_peak = 1.25
+        if fp64_tfs / fp64_peak > hbm_gbs / peak:
+            roof = {"bound": "alu", "achieved": fp64_tfs, "peak": fp64_peak, "unit": "TFLOP/s (FP64)",
+                    "frac": fp64_tfs / fp64_peak, "peak_source": "nominal FP64 rate of the profiling recipe",
+                    "hbm_achieved_GBps": hbm_gbs, "hbm_frac": hbm_gbs / peak}
+        else:
+            roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": peak, "unit": "GB/s", "frac": hbm_gbs / peak,
+                    "peak_source": src, "fp64_achieved_TFs": fp64_tfs}
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": "f64" if cl[0]["precision"] == 0 else "f64 state, f32 stencil solves (multigrid, Helmholtz increments)",
             "data": "synthetic", "config": describe(name, cfg),
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": src, "traffic": None,
-                         "launches": nl, "kernel_ms_total": ms, "profiled_steps": kprof,
-                         "share_of_graph_step": (ms / kprof) / (t_ms / args.steps) if t_ms > 0 else None},
-            "kernel_classes": {k: {"ms": v[0], "launches": v[1], "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else 0}
+            "roofline": dict(roof, kernel=dom, traffic=None, launches=nl, kernel_ms_total=ms, profiled_steps=kprof,
+                             share_of_graph_step=(ms / kprof) / (t_ms / args.steps) if t_ms > 0 else None),
+            "kernel_classes": {k: {"ms": v[0], "launches": v[1],
+                                   "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else 0,
+                                   "fp64_TFs": (v[3] / (v[0] / 1e3) / 1e12) if v[0] > 0 else 0}
                                for k, v in prof.items()},
             "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                     "steps": e2e_steps},

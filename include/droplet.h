@@ -209,13 +209,14 @@ int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0,
 
 /* Kernel classes timed by droplet_profile (algorithmic bytes per launch in brackets,
  * w = word size of the launch, d = 2 or 3 active axes, N = unknowns of the launch):
- *   0 MG_SMOOTH   red-black Gauss-Seidel half sweep    [(2.5 + d) N w]
- *   1 SPMV        CG operator application + dot        [(3 + d) N 8]
- *   2 UPDATE      CG x/r update + dot                  [5 N 8]
- *   3 MG_RESTRICT residual + restriction               [(3 + d) N w + N/2^d w]
- *   4 MG_PROLONG  injection prolongation               [(2 + 1/2^d) N w]
+ *   0 MG_SMOOTH   red-black Gauss-Seidel half sweep    [(2.5 + d) N w; FP64: (4d + 1) N/2 flops]
+ *   1 SPMV        CG operator application + dot        [(3 + d) N w; FP64: (6d + 3) N flops]
+ *   2 UPDATE      CG x/r update + dot                  [5 N 8 or 8 N 4; FP64: 9 N (Jacobi), 6 N flops]
+ *   3 MG_RESTRICT residual + restriction               [(3 + d) N w + N/2^d w; FP64: (6d + 3) N flops]
+ *   4 MG_PROLONG  injection prolongation               [(2 + 1/2^d) N w; FP64: N flops]
  *   5 MOM_ASSEMBLE momentum system assembly            [(12 + 2d) N 8]
- *   6 SCALAR_ASSEMBLE energy / species assembly        [(12 + 2d) N 8]           */
+ *   6 SCALAR_ASSEMBLE energy / species assembly        [(12 + 2d) N 8]
+ * (w = 8 for FP64 launches, 4 for FP32 ones.)                                     */
 #define DROPLET_KCLASS_COUNT 7
 
 /* Start (enable = 1) or stop (0) timing every launch of the kernel classes above
@@ -223,11 +224,36 @@ int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0,
 int droplet_profile(droplet_ctx* ctx, int enable);
 
 /* Totals since profiling started for one kernel class: summed event time [ms],
- * number of launches and summed algorithmic bytes.  Synchronises the stream. */
-int droplet_profile_read(droplet_ctx* ctx, int kclass, double* ms_total, long long* launches, double* bytes_total);
+ * number of launches, summed algorithmic bytes and summed algorithmic FP64 flops
+ * (flops64 may be NULL; launches computing in FP32 add none).  Synchronises. */
+int droplet_profile_read(droplet_ctx* ctx, int kclass, double* ms_total, long long* launches, double* bytes_total,
+                         double* flops64);
 
 /* Number of kernel launches the library has issued for this context so far. */
 int droplet_launch_count(droplet_ctx* ctx, long long* launches);
+
+/* Hand-written discrete adjoint of the step without flow (physics_mask =
+ * EVAP | ENERGY | SPECIES: evaporation flux with the K normalisation of
+ * Eq. alphafunction, alpha source of Eq. alphasource, energy Eq. Teqn, species
+ * Eq. speciesequation with the liquid pinned to the Raoult saturation value,
+ * gas density Eq. densitygas; FP64, Raoult, natural boundaries, one droplet).
+ * Starting from the initial state of droplet_init (step 0) it runs n_steps
+ * forward, keeping the state every ckpt_every steps, and returns
+ *   *J = (1/n_steps) sum_n mdot_tot^n   (mean evaporation rate, kg/s)
+ * and, through a reverse sweep that recomputes each segment from its
+ * checkpoint, the derivatives of J with respect to T_amb (which enters through
+ * the initial temperature profile), D_g, and the initial temperature field
+ * (dJ_dT0, host array of nT0 = cell-count doubles).  Any gradient pointer may be
+ * NULL; with all three NULL only J is computed.  The branch decisions of the
+ * forward step (interface cells, adjacent cells, the mdot cap, clipping,
+ * pinned cells) are held fixed.  The context is left at the state after
+ * n_steps.  Errors: DROPLET_ERR_ARG (another physics mask, precision,
+ * equilibrium model or boundary mode, a batch, or step != 0), DROPLET_ERR_SIZE,
+ * DROPLET_ERR_NOMEM (work memory: 3 N doubles per checkpoint plus
+ * 3 N (ckpt_every + 18) doubles), DROPLET_ERR_NOT_CONVERGED (a solve reached its
+ * cap; results still returned). */
+int droplet_adjoint(droplet_ctx* ctx, int n_steps, int ckpt_every, double* J, double* dJ_dTamb, double* dJ_dDg,
+                    double* dJ_dT0, size_t nT0);
 
 /* Checkpoint / resume.  droplet_save writes, for every droplet, its config, time,
  * step count, the accumulated diagnostics (clipped volume, vapour outflow) and the

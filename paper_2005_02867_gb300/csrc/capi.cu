@@ -554,18 +554,20 @@ extern "C" int droplet_profile(droplet_ctx* c, int enable) {
   return 0;
 }
 
-extern "C" int droplet_profile_read(droplet_ctx* c, int kclass, double* ms, long long* launches, double* bytes) {
+extern "C" int droplet_profile_read(droplet_ctx* c, int kclass, double* ms, long long* launches, double* bytes,
+                                    double* flops64) {
   if (!c || !ms || !launches || !bytes || kclass < 0 || kclass >= KC_COUNT) return DROPLET_ERR_ARG;
-  double tm = 0.0, tb = 0.0;
+  double tm = 0.0, tb = 0.0, tf = 0.0;
   long long tn = 0;
   for (auto x : c->d) {
-    double m, b;
+    double m, b, f;
     long long n;
-    int rc = x->prof.read(kclass, &m, &n, &b);
+    int rc = x->prof.read(kclass, &m, &n, &b, &f);
     if (rc) return rc;
-    tm += m; tb += b; tn += n;
+    tm += m; tb += b; tn += n; tf += f;
   }
   *ms = tm; *launches = tn; *bytes = tb;
+  if (flops64) *flops64 = tf;
   return 0;
 }
 
@@ -684,6 +686,140 @@ extern "C" int droplet_set_field(droplet_ctx* cc, int droplet, int field_id, con
 }
 
 extern "C" void droplet_free(droplet_ctx* c) { free_ctx(c); }
+
+// ---------------------------------------------------------------- adjoint (no flow)
+extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, double* J, double* dJ_dTamb,
+                               double* dJ_dDg, double* dJ_dT0, size_t nT0) {
+  if (!cc || cc->d.size() != 1 || n_steps < 1 || ckpt_every < 1 || !J) return DROPLET_ERR_ARG;
+  dctx* x = cc->d[0];
+  const droplet_config& cf = x->cfg;
+  if (cf.physics_mask != (DROPLET_PHYS_EVAP | DROPLET_PHYS_ENERGY | DROPLET_PHYS_SPECIES) || cf.precision != 0 ||
+      cf.eq_model != 0 || cf.const_props_check != 0 || cf.bc_mode != 0 || x->step != 0)
+    return DROPLET_ERR_ARG;
+  Geo& g = x->g;
+  Phys& p = x->p;
+  long long N = g.N;
+  if (dJ_dT0 && nT0 != (size_t)N) return DROPLET_ERR_SIZE;
+  cudaStream_t st = x->st;
+  CKR(cudaStreamSynchronize(cc->st));
+  CKR(cudaStreamSynchronize(st));
+  int nseg = (n_steps + ckpt_every - 1) / ckpt_every;
+  size_t S3 = 3 * (size_t)N;
+  // device work memory
+  double *ck = nullptr, *seg = nullptr, *w = nullptr, *acc = nullptr, *part = nullptr, *fin = nullptr;
+  const int NW = 17;
+  auto cleanup = [&]() { cudaFree(ck); cudaFree(seg); cudaFree(w); cudaFree(acc); cudaFree(part); cudaFree(fin); };
+  if (cudaMalloc(&ck, sizeof(double) * S3 * nseg) != cudaSuccess || cudaMalloc(&seg, sizeof(double) * S3 * (ckpt_every + 1)) != cudaSuccess ||
+      cudaMalloc(&w, sizeof(double) * N * NW) != cudaSuccess || cudaMalloc(&acc, sizeof(double) * AC_COUNT) != cudaSuccess ||
+      cudaMalloc(&part, sizeof(double) * RED_BLOCKS * 4) != cudaSuccess || cudaMalloc(&fin, sizeof(double) * S3) != cudaSuccess) {
+    cleanup();
+    return DROPLET_ERR_NOMEM;
+  }
+  double* aA = w;           double* aT = w + N;       double* aW = w + 2 * N;
+  double* Tn1bar = w + 3 * N; double* wpbar = w + 4 * N; double* rhobar = w + 5 * N;
+  double* Dbar = w + 6 * N;  double* kbar = w + 7 * N;  double* cpbar = w + 8 * N;
+  double* mdbar = w + 9 * N; double* rgbar = w + 10 * N; double* mrbar = w + 11 * N;
+  double* aAn = w + 12 * N;  double* Tnbar = w + 13 * N; double* wp = w + 14 * N;
+  double* zero = w + 15 * N;
+  cudaMemsetAsync(acc, 0, sizeof(double) * AC_COUNT, st);
+  cudaMemsetAsync(zero, 0, sizeof(double) * N, st);
+  double wgt = g.axisym ? 2.0 * M_PI : 1.0;
+  double jweight = wgt / n_steps;
+  auto save_state = [&](double* dst) {
+    cudaMemcpyAsync(dst, x->alpha, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(dst + N, x->T, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(dst + 2 * N, x->omega, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  };
+  auto load_state = [&](const double* src) {
+    cudaMemcpyAsync(x->alpha, src, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(x->T, src + N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(x->omega, src + 2 * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    cudaMemsetAsync(x->dirty, 0xff, sizeof(int), st);   // rho_G from T and omega at S0
+  };
+  int nc = 0, rc = 0;
+  // forward with checkpoints every ckpt_every steps, J accumulated on the device
+  for (int n = 0; n < n_steps && !rc; ++n) {
+    if (n % ckpt_every == 0) save_state(ck + S3 * (n / ckpt_every));
+    rc = one_step(x, &nc);
+    L_acc_J(st, x->scal, jweight, acc);
+  }
+  save_state(fin);
+  CKR(cudaStreamSynchronize(st));
+  double host_acc[AC_COUNT];
+  CKR(cudaMemcpy(host_acc, acc, sizeof(double) * AC_COUNT, cudaMemcpyDeviceToHost));
+  *J = host_acc[AC_J];
+  bool want = dJ_dTamb || dJ_dDg || dJ_dT0;
+  if (!rc && want) {
+    cudaMemsetAsync(aA, 0, sizeof(double) * 3 * N, st);   // aA, aT, aW: J does not depend on the final state
+    BoxSys bs;
+    bs.D = x->bD; bs.b = x->brhs; bs.x = x->bx;
+    int na = nact(g);
+    for (int a = 0; a < 3; ++a) { bs.c[a] = a < na ? x->bc[a] : nullptr; bs.m[a] = g.n[a]; }
+    bs.N = N;
+    double* u2 = x->u[2] ? x->u[2] : x->u[0];
+    SolveStats ss;
+    for (int sgi = nseg - 1; sgi >= 0 && !rc; --sgi) {
+      int n0 = sgi * ckpt_every, n1 = n0 + ckpt_every < n_steps ? n0 + ckpt_every : n_steps;
+      // states n0 .. n1-1 of the segment
+      load_state(ck + S3 * sgi);
+      for (int n = n0; n < n1 && !rc; ++n) {
+        save_state(seg + S3 * (n - n0));
+        if (n + 1 < n1) rc = one_step(x, &nc);
+      }
+      for (int n = n1 - 1; n >= n0 && !rc; --n) {
+        const double* sA = seg + S3 * (n - n0);
+        const double* sT = sA + N;
+        const double* sW = sA + 2 * N;
+        load_state(sA);
+        rc = one_step(x, &nc);           // leaves step n's intermediates and state n+1
+        if (rc) break;
+        L_adj_pin(st, g, p, sA, sT, sW, wp);
+        // species: adjoint solve on the free rows, pinned rows and coefficients
+        L_scalar_assemble(st, lin_grid(N), g, p, 1, wp, x->rho, x->cp, x->kc, x->Dm, x->mdot, x->u[0], x->u[1], u2,
+                          x->alpha, x->yq, 0.0, x->bD, x->bc[0], x->bc[1], na == 3 ? x->bc[2] : x->bc[0], x->brhs);
+        L_adj_rhs(st, g, aW, x->alpha, 1, x->brhs, x->bx);
+        rc = x->solver.pcg_jacobi(bs, 1e-14, 4 * cf.helm_maxit, &ss);
+        if (rc == DROPLET_ERR_NOT_CONVERGED) { nc = 1; rc = 0; }
+        if (rc) break;
+        L_adj_species(st, g, p, x->bx, aW, aT, x->alpha, wp, x->omega, x->T, x->rho, x->Dm, Tn1bar, wpbar, rhobar, Dbar);
+        // energy
+        L_scalar_assemble(st, lin_grid(N), g, p, 0, sT, x->rho, x->cp, x->kc, x->Dm, x->mdot, x->u[0], x->u[1], u2,
+                          x->alpha, x->yq, p.T_amb, x->bD, x->bc[0], x->bc[1], na == 3 ? x->bc[2] : x->bc[0], x->brhs);
+        L_adj_rhs(st, g, Tn1bar, x->alpha, 0, x->brhs, x->bx);
+        rc = x->solver.pcg_jacobi(bs, 1e-14, 4 * cf.helm_maxit, &ss);
+        if (rc == DROPLET_ERR_NOT_CONVERGED) { nc = 1; rc = 0; }
+        if (rc) break;
+        L_adj_energy(st, g, p, x->bx, sT, x->T, x->rho, x->cp, x->kc, Tnbar, rhobar, kbar, cpbar, mdbar);
+        // properties, clipping, alpha source, J, cap, K and f(alpha)
+        L_adj_source(st, g, p, aA, sA, x->alpha, x->astar, x->rhoG_old, x->mraw, x->scal, rhobar, kbar, cpbar, Dbar,
+                     jweight, aAn, rgbar, mdbar, mrbar, part, acc);
+        // evaporation flux at the adjacent gas cells
+        L_adj_evap(st, g, p, sA, wp, x->rhoG_old, x->adj, mrbar, aAn, wpbar, rgbar, part, acc);
+        // gas density and the pinned liquid values of S0
+        L_adj_thermo(st, g, p, sA, sT, wp, x->rhoG_old, rgbar, wpbar, Tnbar, aW);
+        cudaMemcpyAsync(aA, aAn, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(aT, Tnbar, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+        CKR(cudaGetLastError());
+      }
+    }
+    if (!rc) {
+      L_adj_tamb(st, g, p, aT, part, acc);
+      CKR(cudaStreamSynchronize(st));
+      CKR(cudaMemcpy(host_acc, acc, sizeof(double) * AC_COUNT, cudaMemcpyDeviceToHost));
+      if (dJ_dDg) *dJ_dDg = host_acc[AC_DGAS] * (1.0e5 / cf.P);
+      if (dJ_dTamb) *dJ_dTamb = host_acc[AC_TAMB];
+      if (dJ_dT0) CKR(cudaMemcpy(dJ_dT0, aT, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    }
+  }
+  // leave the context at the state after n_steps
+  load_state(fin);
+  CKR(cudaStreamSynchronize(st));
+  cleanup();
+  x->t = n_steps * p.dt;
+  x->step = n_steps;
+  if (rc) return rc;
+  return nc ? DROPLET_ERR_NOT_CONVERGED : 0;
+}
 
 // ---------------------------------------------------------------- checkpoint / resume
 static const char kMagic[8] = {'D', 'R', 'O', 'P', 'C', 'K', 'P', '1'};

@@ -18,11 +18,12 @@ struct Prof {
   std::vector<int> kind;        // kernel class of each recorded pair
   size_t used = 0;              // event pairs in use
   double bytes[KC_COUNT] = {0};
+  double flops[KC_COUNT] = {0};   // algorithmic FP64 flops (0 for FP32 launches)
   long long n[KC_COUNT] = {0};
-  int begin(int k, cudaStream_t st, double b);
+  int begin(int k, cudaStream_t st, double b, double f64 = 0.0);
   void end(int idx, cudaStream_t st);
   void reset();
-  int read(int k, double* ms, long long* launches, double* bytes_total);
+  int read(int k, double* ms, long long* launches, double* bytes_total, double* flops_total = nullptr);
   void destroy();
 };
 
@@ -30,8 +31,8 @@ struct ProfScope {
   Prof* p;
   cudaStream_t st;
   int idx;
-  ProfScope(Prof* p_, int k, cudaStream_t st_, double b) : p(p_), st(st_), idx(-1) {
-    if (p && p->on) idx = p->begin(k, st, b);
+  ProfScope(Prof* p_, int k, cudaStream_t st_, double b, double f64 = 0.0) : p(p_), st(st_), idx(-1) {
+    if (p && p->on) idx = p->begin(k, st, b, f64);
   }
   ~ProfScope() {
     if (idx >= 0) p->end(idx, st);
@@ -85,6 +86,32 @@ void L_correct(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* us
 void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax);
 
 void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x);
+
+// ---- adjoint of the step without flow (adjoint.cu)
+enum { AC_DGAS = 0, AC_J, AC_TAMB, AC_COUNT };
+void L_adj_pin(cudaStream_t st, const Geo& g, const Phys& p, const double* alpha, const double* T,
+               const double* omega, double* wp);
+void L_adj_rhs(cudaStream_t st, const Geo& g, const double* abar, const double* alpha_new, int pinned_rows,
+               double* rhs, double* x);
+void L_adj_species(cudaStream_t st, const Geo& g, const Phys& p, const double* bW, const double* aW, const double* aT,
+                   const double* alpha_new, const double* wp, const double* wn1, const double* Tn1, const double* rho,
+                   const double* D, double* Tn1bar, double* wpbar, double* rhobar, double* Dbar);
+void L_adj_energy(cudaStream_t st, const Geo& g, const Phys& p, const double* bT, const double* Tn, const double* Tn1,
+                  const double* rho, const double* cp, const double* kc, double* Tnbar, double* rhobar, double* kbar,
+                  double* cpbar, double* mdbar);
+void L_adj_source(cudaStream_t st, const Geo& g, const Phys& p, const double* aA, const double* alpha_n,
+                  const double* alpha_new, const double* astar, const double* rgn, const double* mraw,
+                  const double* scal, const double* rhobar, const double* kbar, const double* cpbar,
+                  const double* Dbar, double jweight, double* aAn, double* rgbar, double* mdbar, double* mrbar,
+                  double* part, double* acc_out);
+void L_adj_evap(cudaStream_t st, const Geo& g, const Phys& p, const double* alpha_n, const double* wp,
+                const double* rgn, const int* adj, const double* mrbar, double* aAn, double* wpbar, double* rgbar,
+                double* part, double* acc_out);
+void L_adj_thermo(cudaStream_t st, const Geo& g, const Phys& p, const double* alpha_n, const double* Tn,
+                  const double* wp, const double* rgn, const double* rgbar, const double* wpbar, double* Tnbar,
+                  double* aW);
+void L_acc_J(cudaStream_t st, const double* scal, double weight, double* acc_out);
+void L_adj_tamb(cudaStream_t st, const Geo& g, const Phys& p, const double* T0bar, double* part, double* acc_out);
 
 // ---- linear solvers (solver.cu)
 // Box operator on dims m: y_P = D_P x_P + sum_a [c_a[P](x_P - x_{P-e_a}) + c_a[P+e_a](x_P - x_{P+e_a})],

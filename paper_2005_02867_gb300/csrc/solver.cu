@@ -591,7 +591,7 @@ __global__ void k_cast_done(long long n, TO* y, const TI* x, const int* done) {
 // ---------------------------------------------------------------- host side
 long long g_launches = 0;
 
-int Prof::begin(int k, cudaStream_t st, double b) {
+int Prof::begin(int k, cudaStream_t st, double b, double f64) {
   if (2 * (used + 1) > pool.size()) {
     for (int q = 0; q < 256; ++q) {
       cudaEvent_t e;
@@ -603,6 +603,7 @@ int Prof::begin(int k, cudaStream_t st, double b) {
   if ((int)kind.size() < (int)used) kind.resize(used);
   kind[idx] = k;
   bytes[k] += b;
+  flops[k] += f64;
   n[k] += 1;
   cudaEventRecord(pool[2 * idx], st);
   return idx;
@@ -612,10 +613,10 @@ void Prof::end(int idx, cudaStream_t st) { cudaEventRecord(pool[2 * idx + 1], st
 
 void Prof::reset() {
   used = 0;
-  for (int k = 0; k < KC_COUNT; ++k) { bytes[k] = 0.0; n[k] = 0; }
+  for (int k = 0; k < KC_COUNT; ++k) { bytes[k] = 0.0; flops[k] = 0.0; n[k] = 0; }
 }
 
-int Prof::read(int k, double* ms, long long* launches, double* bytes_total) {
+int Prof::read(int k, double* ms, long long* launches, double* bytes_total, double* flops_total) {
   double tot = 0.0;
   for (size_t i = 0; i < used; ++i) {
     if (kind[i] != k) continue;
@@ -627,6 +628,7 @@ int Prof::read(int k, double* ms, long long* launches, double* bytes_total) {
   *ms = tot;
   *launches = n[k];
   *bytes_total = bytes[k];
+  if (flops_total) *flops_total = flops[k];
   return 0;
 }
 
@@ -749,11 +751,11 @@ int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out)
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);
   auto iteration = [&]() {
     {
-      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0);
+      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0, (6.0 * (s.c[2] ? 3 : 2) + 3.0) * s.N);
       ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt);
     }
     {
-      ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0);
+      ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0, 9.0 * s.N);
       ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 1, sc, part, done, cnt);
     }
     ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
@@ -901,7 +903,8 @@ int Solver::build_mg(const BoxSys& s, int fp32) {
 template <typename T>
 static void smooth(Prof* prof, LevV<T> L, int col, int first, const int* done, cudaStream_t st) {
   int d = L.c[2] ? 3 : 2;
-  ProfScope ps(prof, KC_MG_SMOOTH, st, (2.5 + d) * L.N * (double)sizeof(T));
+  ProfScope ps(prof, KC_MG_SMOOTH, st, (2.5 + d) * L.N * (double)sizeof(T),
+               sizeof(T) == 8 ? (4.0 * d + 1.0) * 0.5 * L.N : 0.0);
   ++g_launches, k_mg_smooth<T><<<lin_grid(L.N), TPB, 0, st>>>(L, col, first, done);
 }
 
@@ -921,7 +924,8 @@ static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaSt
     LevV<T> C = lv<T>(lev[l + 1]);
     {
       int d = L.c[2] ? 3 : 2;
-      ProfScope ps(prof, KC_MG_RESTRICT, st, ((3.0 + d) * L.N + C.N) * (double)sizeof(T));
+      ProfScope ps(prof, KC_MG_RESTRICT, st, ((3.0 + d) * L.N + C.N) * (double)sizeof(T),
+                   sizeof(T) == 8 ? (6.0 * d + 3.0) * L.N : 0.0);
       ++g_launches, k_mg_restrict<T><<<lin_grid(C.N), TPB, 0, st>>>(L, C, done);
     }
   }
@@ -932,7 +936,7 @@ static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaSt
     LevV<T> L = lv<T>(lev[l]), C = lv<T>(lev[l + 1]);
     int g = lin_grid(L.N);
     {
-      ProfScope ps(prof, KC_MG_PROLONG, st, (2.0 * L.N + C.N) * (double)sizeof(T));
+      ProfScope ps(prof, KC_MG_PROLONG, st, (2.0 * L.N + C.N) * (double)sizeof(T), sizeof(T) == 8 ? 1.0 * L.N : 0.0);
       ++g_launches, k_mg_prolong<T><<<g, TPB, 0, st>>>(L, C, done);
     }
     for (int s = 0; s < nu; ++s) {
@@ -968,11 +972,11 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
   ++g_launches, k_cast_done<double, double><<<g, TPB, 0, stream>>>(s.N, p, z, done);
   auto iteration = [&]() {
     {
-      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0);
+      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0, (6.0 * (s.c[2] ? 3 : 2) + 3.0) * s.N);
       ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt);
     }
     {
-      ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0);
+      ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0, 6.0 * s.N);
       ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 0, sc, part, done, cnt);
     }
     vcycle(fp32);

@@ -52,7 +52,7 @@ FIELDS = dict(alpha=0, T=1, omega=2, p=3, rhoG=4, u0=5, u1=6, u2=7, mdot=8, mraw
 
 EXPORTS = ["droplet_init", "droplet_step", "droplet_diag", "droplet_field_size", "droplet_get_field",
            "droplet_set_field", "droplet_sync", "droplet_free", "droplet_strerror", "droplet_profile",
-           "droplet_profile_read", "droplet_launch_count", "droplet_box_solve", "droplet_box_solve_noalloc", "droplet_save", "droplet_load"]
+           "droplet_profile_read", "droplet_launch_count", "droplet_box_solve", "droplet_box_solve_noalloc", "droplet_save", "droplet_load", "droplet_adjoint"]
 
 NOALLOC_MAX_UNKNOWNS = 262144
 
@@ -90,11 +90,13 @@ def load_library(path=LIBPATH):
     lib.droplet_free.restype = None
     lib.droplet_profile.argtypes = [P, _c_int]
     lib.droplet_profile_read.argtypes = [P, _c_int, ctypes.POINTER(_c_dbl), ctypes.POINTER(ctypes.c_longlong),
-                                         ctypes.POINTER(_c_dbl)]
+                                         ctypes.POINTER(_c_dbl), ctypes.POINTER(_c_dbl)]
     lib.droplet_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_longlong)]
     BOX = [ctypes.POINTER(_c_int), P, P, P, P, P, P, _c_dbl, _c_int, P, ctypes.POINTER(_c_int), ctypes.POINTER(_c_dbl)]
     lib.droplet_box_solve.argtypes = BOX
     lib.droplet_box_solve_noalloc.argtypes = BOX
+    D = ctypes.POINTER(_c_dbl)
+    lib.droplet_adjoint.argtypes = [P, _c_int, _c_int, D, D, D, D, ctypes.c_size_t]
     lib.droplet_save.argtypes = [P, ctypes.c_char_p]
     lib.droplet_load.argtypes = [P, ctypes.c_char_p]
     lib.droplet_strerror.argtypes = [_c_int]
@@ -208,13 +210,15 @@ def droplet_profile(h, enable):
 
 
 def droplet_profile_read(h, kclass):
-    """(ms_total, launches, algorithmic_bytes_total) of a kernel class since droplet_profile(h, 1)."""
-    ms, n, b = _c_dbl(), ctypes.c_longlong(), _c_dbl()
+    """(ms_total, launches, algorithmic_bytes_total, algorithmic_fp64_flops_total) of a kernel
+    class since droplet_profile(h, 1)."""
+    ms, n, b, f = _c_dbl(), ctypes.c_longlong(), _c_dbl(), _c_dbl()
     k = KCLASS[kclass] if isinstance(kclass, str) else int(kclass)
-    rc = load_library().droplet_profile_read(ctypes.c_void_p(h), k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b))
+    rc = load_library().droplet_profile_read(ctypes.c_void_p(h), k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b),
+                                             ctypes.byref(f))
     if rc:
         raise DropletError(rc, "droplet_profile_read")
-    return ms.value, n.value, b.value
+    return ms.value, n.value, b.value, f.value
 
 
 def droplet_launch_count(h):
@@ -255,6 +259,27 @@ def droplet_load(h, path):
     rc = load_library().droplet_load(ctypes.c_void_p(h), os.fsencode(path))
     if rc:
         raise DropletError(rc, "droplet_load")
+
+
+def droplet_adjoint(h, n_steps, ckpt_every, gradients=True):
+    """J (mean evaporation rate) and, if gradients, (dJ/dT_amb, dJ/dD_g, dJ/dT0 as a
+    flat array).  The context must be at step 0 with physics_mask = EVAP|ENERGY|SPECIES."""
+    J = _c_dbl()
+    if not gradients:
+        rc = load_library().droplet_adjoint(ctypes.c_void_p(h), int(n_steps), int(ckpt_every), ctypes.byref(J),
+                                            None, None, None, 0)
+        if rc and rc != ERR_NOT_CONVERGED:
+            raise DropletError(rc, "droplet_adjoint")
+        return J.value
+    n = droplet_field_size(h, "T")
+    gT0 = np.empty(n, dtype=np.float64)
+    gTa, gDg = _c_dbl(), _c_dbl()
+    rc = load_library().droplet_adjoint(ctypes.c_void_p(h), int(n_steps), int(ckpt_every), ctypes.byref(J),
+                                        ctypes.byref(gTa), ctypes.byref(gDg),
+                                        gT0.ctypes.data_as(ctypes.POINTER(_c_dbl)), n)
+    if rc and rc != ERR_NOT_CONVERGED:
+        raise DropletError(rc, "droplet_adjoint")
+    return J.value, gTa.value, gDg.value, gT0
 
 
 def droplet_sync(h):
@@ -309,3 +334,32 @@ class Droplet:
             self.close()
         except Exception:
             pass
+
+
+def evaporation_rate_function():
+    """torch.autograd.Function J(T_amb, D_g, dT0): mean evaporation rate over
+    n_steps of the step without flow, from the initial state with T0 =
+    profile(T_amb) + dT0.  Backward returns the hand-written adjoint's gradient,
+    computed (with checkpointing) when the forward runs."""
+    import torch
+
+    class EvaporationRate(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, T_amb, D_g, dT0, cfg, n_steps, ckpt_every):
+            c = dict(cfg, T_amb=float(T_amb), D_g=float(D_g))
+            sim = Droplet(c)
+            if dT0 is not None:
+                T0 = sim.get("T") + dT0.detach().cpu().numpy().ravel()
+                sim.set("T", T0)
+            J, gTa, gDg, gT0 = droplet_adjoint(sim.h, n_steps, ckpt_every, gradients=True)
+            sim.close()
+            ctx.save_for_backward(torch.tensor(gTa, dtype=torch.float64), torch.tensor(gDg, dtype=torch.float64),
+                                  torch.from_numpy(gT0))
+            return torch.tensor(J, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gTa, gDg, gT0 = ctx.saved_tensors
+            return gJ * gTa, gJ * gDg, gJ * gT0, None, None, None
+
+    return EvaporationRate
