@@ -188,6 +188,8 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
       cudaMallocHost((void**)&c->hscal, sizeof(double) * SC_COUNT) != cudaSuccess ||
       cudaMallocHost((void**)&c->hflags, sizeof(unsigned)) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_NOMEM; }
   c->solver.f32_helm = c->cfg.precision == 1;
+  // one droplet of a latency-bound size: persistent solver; batches overlap their branches instead
+  c->solver.persistent = !own_stream && N <= Solver::PERSIST_MAX_CELLS;
   c->solver.rb = c->rb;
   if ((rc = c->solver.setup(N, c->st))) { free_all(c); delete c; return rc; }
   c->solver.prof = &c->prof;

@@ -159,6 +159,8 @@ class Solver {
   cudaStream_t stream2 = nullptr;   // captures the bodies of the device-driven solver loops
   bool capturing = false;           // the step is being captured into a CUDA graph
   bool f32_helm = false;            // Jacobi-PCG as FP32 defect correction (set before setup)
+  bool persistent = false;          // Jacobi-PCG in one cooperative launch (set before setup)
+  static constexpr long long PERSIST_MAX_CELLS = 1LL << 22;   // latency-bound sizes only
   int rb = RED_BLOCKS;              // block cap of the reduction kernels (tuned for batches)
   Prof* prof = nullptr;
 
@@ -166,8 +168,16 @@ class Solver {
   template <typename F>
   int device_loop(F body);
   int pcg_jacobi_f32(const BoxSys& s, double rtol, int maxit, SolveStats* out);
+  template <typename T>
+  int pcg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out);
+  int persist_blocks(bool f32);
   float *fD = nullptr, *fc[3] = {nullptr, nullptr, nullptr}, *fidg = nullptr, *fr = nullptr, *fz = nullptr,
         *fp = nullptr, *fAp = nullptr, *fdx = nullptr;
+  static constexpr int PERSIST_VECTORS = 13;
+  void* pw[PERSIST_VECTORS] = {};   // persistent-solve vectors
+  unsigned* bar = nullptr;      // grid barrier counter and generation
+  int* err = nullptr;           // set when a grid barrier wait ran out
+  int pb_f32 = 0, pb_f64 = 0;   // co-resident blocks of the persistent solver
   int build_mg(const BoxSys& s, int fp32);
   void vcycle(int fp32);
   long long cap = 0;

@@ -84,7 +84,13 @@ __global__ void k_pcg_init(BoxV A, const double* b, const double* x, double* r, 
   block_sum_store<3>(acc, part);
 }
 
-__global__ void k_fin_init(const double* part, int nblk, double* sc, int* done, double tol2, int maxit) {
+__global__ void k_fin_init(const double* part, int nblk, double* sc, int* done, double tol2, int maxit,
+                           unsigned* bar, int* err) {
+  if (bar && threadIdx.x == 0) {   // grid barrier of the persistent solver back to its idle state
+    bar[0] = 0u;
+    bar[1] = 0u;
+    *err = 0;
+  }
   double rz = block_sum_partials(part, nblk);
   __syncthreads();
   double bb = block_sum_partials(part + nblk, nblk);
@@ -353,6 +359,257 @@ __global__ void k_p_update_f(long long N, float* p, const float* z, const double
 __global__ void k_mx_finish(long long N, double* x, const float* dx) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id < N) x[id] += (double)dx[id];
+}
+
+// ---------------------------------------------------------------- persistent Jacobi-PCG
+// The whole Jacobi-preconditioned CG of a box system in one cooperative launch.
+//
+// Form.  Jacobi-PCG on A equals plain CG on the unit-diagonal system
+// A^ = S A S, S = diag(A)^(-1/2), with x = S x^ and r^ = S r.  The kernel solves the
+// defect equation A d = r0 that way, with r0 normalised to unit length
+// (r^0 = S r0 / |r0|), so every working quantity is O(1) and the FP32 variant can
+// keep its sums and scalars in FP32 without range trouble.  A^ is applied in matrix
+// form, y = x - sum_f c^_f x_nb(f), c^_f = c_f s_P s_nb.  The convergence test is
+// the caller's: |r|^2 = |r0|^2 sum_i diag_i r^_i^2 <= rtol^2 |b|^2.
+//
+// Iteration.  CG in the single-reduction form of Chronopoulos & Gear (1989): with
+// w = A^ r^ kept alongside r^, the inner products gamma = r^.r^, delta = w.r^ and the
+// weighted residual norm come from one grid-wide sum, after which
+//   beta = gamma / gamma_old,  alpha = gamma / (delta - beta gamma / alpha_old),
+//   p = r^ + beta p,  s = w + beta s (= A^ p),  x^ += alpha p,  r^ -= alpha s.
+// In exact arithmetic the iterates are those of the standard method.  w_new = A^ r^_new
+// needs r^_new at the neighbours, which each thread recomputes from the neighbours'
+// r^, s, w of the previous iteration; those three vectors are double buffered so no
+// cell is overwritten while a neighbour still reads it, and one grid barrier per
+// iteration suffices.
+//
+// Grid sum.  Each block stores its partial sums (buffers alternate with the phase)
+// and arrives on a monotone counter; every block waits for the counter to reach
+// (phase + 1) x blocks, then warp q adds partial q over all blocks in block order, so
+// every block obtains the same totals (deterministic).  One thread forms the scalars
+// and broadcasts them through shared memory: GB300 retires about two FP64 FMAs per SM
+// clock, so scalar work repeated by every thread is not free.  Waits are bounded:
+// past the limit the solve stops (done = 2) and *err is set, so a launch whose blocks
+// were not all resident cannot hang.
+constexpr long long BARRIER_SPIN_LIMIT = 1LL << 22;
+constexpr int PTPB = 512;   // threads per block of the persistent solver
+
+template <typename T>
+struct PersistArgs {
+  BoxV A;                   // FP64 operator (difference form)
+  const double* r64;        // FP64 defect r0 = b - A x0
+  double* x;                // FP64 solution, x += d at the end
+  T *ch[3];                 // c^ on the low face of each cell, per axis
+  T *dg, *sc;               // diag(A) and S = diag^(-1/2)
+  T *r[2], *s[2], *w[2];    // double-buffered r^, s = A^ p, w = A^ r^
+  T *p, *dx;                // search direction, x^
+  T* part;                  // 2 x 3 x blocks partial sums
+  double* stat;             // solver scalars (S_*)
+  int* done;
+  unsigned* bar;            // [0] arrivals (zero at launch)
+  int* err;
+};
+
+// grid-wide sums of 3 values (nv = 0: plain barrier); returns false when a wait ran out
+template <typename T>
+__device__ __forceinline__ bool grid_sum3(T (&v)[3], int nv, int phase, const PersistArgs<T>& a) {
+  __shared__ T sh[3][PTPB / 32];
+  __shared__ int ok;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, G = gridDim.x;
+  T* part = a.part + (phase & 1) * 3 * G;
+  for (int q = 0; q < nv; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    if (lane == 0) sh[q][wid] = v[q];
+  }
+  __syncthreads();
+  if (threadIdx.x < nv) {
+    T t = 0;
+#pragma unroll
+    for (int w = 0; w < PTPB / 32; ++w) t += sh[threadIdx.x][w];
+    part[threadIdx.x * G + blockIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(a.bar, 1u);
+    volatile unsigned* cnt = a.bar;
+    const unsigned target = (unsigned)(phase + 1) * (unsigned)G;
+    long long spins = 0;
+    int good = 1;
+    while (*cnt < target) {
+      if (++spins > BARRIER_SPIN_LIMIT) { atomicExch(a.err, 1); good = 0; break; }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  if (wid < nv) {
+    T t = 0;
+    for (int b = lane; b < G; b += 32) t += __ldcg(part + wid * G + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sh[wid][0] = t;
+  }
+  __syncthreads();
+  for (int q = 0; q < nv; ++q) v[q] = sh[q][0];
+  const bool r = ok != 0;
+  __syncthreads();
+  return r;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(PersistArgs<T> a) {
+  if (*a.done) return;                      // converged at the initial guess
+  __shared__ T bc[3];                       // broadcast: alpha, beta, state
+  const int m0 = a.A.m[0], m1 = a.A.m[1], m2 = a.A.m[2];
+  const int N = (int)a.A.N;                 // at most PERSIST_MAX_CELLS: 32-bit indices
+  const int st1 = m0, st2 = m0 * m1;
+  const bool has2 = a.A.c[2] != nullptr;
+  const int gs = gridDim.x * blockDim.x;
+  const int id0 = blockIdx.x * blockDim.x + threadIdx.x;
+  // per-solve scalars, formed once (FP64 work repeated by every thread is slow on GB300)
+  __shared__ double sd[3];
+  if (threadIdx.x == 0) {
+    const double rr0 = a.stat[S_RR];
+    sd[0] = sqrt(rr0);                                    // |r0| = 1 / nu
+    sd[1] = 1.0 / sd[0];                                  // nu
+    sd[2] = a.stat[S_TOL2] * a.stat[S_BB] / rr0;          // rtol^2 |b|^2 / |r0|^2
+  }
+  __syncthreads();
+  const double inv_nu = sd[0];
+  const T nu = (T)sd[1];
+  const T thr = (T)sd[2];
+  int phase = 0;
+  // setup 1: diag, S, r^0 = nu S r0; s = p = x^ = 0
+  for (int id = id0; id < N; id += gs) {
+    int i, j, k;
+    bdecomp(a.A.m, id, i, j, k);
+    double d = a.A.D[id];
+    if (i > 0) d += a.A.c[0][id];
+    if (i < m0 - 1) d += a.A.c[0][id + 1];
+    if (j > 0) d += a.A.c[1][id];
+    if (j < m1 - 1) d += a.A.c[1][id + st1];
+    if (has2) {
+      if (k > 0) d += a.A.c[2][id];
+      if (k < m2 - 1) d += a.A.c[2][id + st2];
+    }
+    const T dT = (T)d;
+    const T sP = (T)1 / sqrt(dT);
+    a.dg[id] = dT;
+    a.sc[id] = sP;
+    a.r[0][id] = nu * sP * (T)a.r64[id];
+    a.s[0][id] = 0;
+    a.p[id] = 0;
+    a.dx[id] = 0;
+  }
+  T v[3] = {0, 0, 0};
+  bool ok = grid_sum3<T>(v, 0, phase++, a);
+  // setup 2: c^ on the low faces, w = A^ r^0, gamma, delta, weighted |r^|^2
+  if (ok) {
+    const T* r = a.r[0];
+    T g = 0, dl = 0, q = 0;
+    for (int id = id0; id < N; id += gs) {
+      int i, j, k;
+      bdecomp(a.A.m, id, i, j, k);
+      const T sP = a.sc[id], rP = r[id];
+      T y = rP;
+      if (i > 0) {
+        const T c = (T)a.A.c[0][id] * sP * a.sc[id - 1];
+        a.ch[0][id] = c;
+        y -= c * r[id - 1];
+      } else {
+        a.ch[0][id] = 0;
+      }
+      if (i < m0 - 1) y -= (T)a.A.c[0][id + 1] * sP * a.sc[id + 1] * r[id + 1];
+      if (j > 0) {
+        const T c = (T)a.A.c[1][id] * sP * a.sc[id - st1];
+        a.ch[1][id] = c;
+        y -= c * r[id - st1];
+      } else {
+        a.ch[1][id] = 0;
+      }
+      if (j < m1 - 1) y -= (T)a.A.c[1][id + st1] * sP * a.sc[id + st1] * r[id + st1];
+      if (has2) {
+        if (k > 0) {
+          const T c = (T)a.A.c[2][id] * sP * a.sc[id - st2];
+          a.ch[2][id] = c;
+          y -= c * r[id - st2];
+        } else {
+          a.ch[2][id] = 0;
+        }
+        if (k < m2 - 1) y -= (T)a.A.c[2][id + st2] * sP * a.sc[id + st2] * r[id + st2];
+      }
+      a.w[0][id] = y;
+      g += rP * rP;
+      dl += y * rP;
+      q += a.dg[id] * rP * rP;
+    }
+    v[0] = g; v[1] = dl; v[2] = q;
+    ok = grid_sum3<T>(v, 3, phase++, a);
+  }
+  const int maxit = (int)a.stat[S_MAXIT];
+  T gamma = v[0], alpha = v[0] / v[1], beta = 0, rho = v[2];
+  int its = 0, result = ok ? 2 : 3;
+  for (int cur = 0; ok && its < maxit; cur ^= 1) {
+    const T al = alpha, bt = beta;
+    const T *r = a.r[cur], *s = a.s[cur], *w = a.w[cur];
+    T *rn = a.r[cur ^ 1], *sn = a.s[cur ^ 1], *wn = a.w[cur ^ 1];
+    T g = 0, dl = 0, q = 0;
+    for (int id = id0; id < N; id += gs) {
+      int i, j, k;
+      bdecomp(a.A.m, id, i, j, k);
+      const T rP = r[id];
+      const T pP = rP + bt * a.p[id];       // p = r^ + beta p
+      const T sP = w[id] + bt * s[id];      // s = w + beta s
+      a.p[id] = pP;
+      a.dx[id] += al * pP;                  // x^ += alpha p
+      const T rN = rP - al * sP;            // r^ -= alpha s
+      // neighbours: clamped indices and zero couplings at the box edges, so that all
+      // loads issue together; r^_new of a neighbour from its r^, s, w
+      const int iw = i > 0 ? id - 1 : id, ie = i < m0 - 1 ? id + 1 : id;
+      const int is = j > 0 ? id - st1 : id, in = j < m1 - 1 ? id + st1 : id;
+      const T cw = a.ch[0][id], ce = i < m0 - 1 ? a.ch[0][ie] : (T)0;
+      const T cs = a.ch[1][id], cn = j < m1 - 1 ? a.ch[1][in] : (T)0;
+#define UNB(o) (r[o] - al * (w[o] + bt * s[o]))
+      T y = rN - (cw * UNB(iw) + ce * UNB(ie) + cs * UNB(is) + cn * UNB(in));
+      if (has2) {
+        const int ib = k > 0 ? id - st2 : id, it = k < m2 - 1 ? id + st2 : id;
+        const T cb = a.ch[2][id], ct = k < m2 - 1 ? a.ch[2][it] : (T)0;
+        y -= cb * UNB(ib) + ct * UNB(it);
+      }
+#undef UNB
+      rn[id] = rN;
+      sn[id] = sP;
+      wn[id] = y;
+      g += rN * rN;
+      dl += y * rN;
+      q += a.dg[id] * rN * rN;
+    }
+    v[0] = g; v[1] = dl; v[2] = q;
+    ok = grid_sum3<T>(v, 3, phase++, a);
+    ++its;
+    if (!ok) { result = 3; break; }
+    if (threadIdx.x == 0) {
+      const T bn = v[0] / gamma;
+      bc[0] = v[0] / (v[1] - bn * v[0] / alpha);
+      bc[1] = bn;
+    }
+    rho = v[2];
+    if (v[2] <= thr) { result = 1; break; }
+    __syncthreads();
+    alpha = bc[0];
+    beta = bc[1];
+    gamma = v[0];
+    __syncthreads();
+  }
+  // x += S x^ / nu
+  for (int id = id0; id < N; id += gs) a.x[id] += (double)(a.sc[id] * a.dx[id]) * inv_nu;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.stat[S_ITS] = (double)its;
+    a.stat[S_RR] = (double)rho * inv_nu * inv_nu;
+    *a.done = result == 1 ? 1 : 2;
+  }
 }
 
 // condition of a solver WHILE node: run another iteration while not done
@@ -655,11 +912,17 @@ int Solver::setup(long long maxN, cudaStream_t s) {
   CK(cudaMalloc(&cnt, sizeof(unsigned)));
   CK(cudaMemset(cnt, 0, sizeof(unsigned)));
   CK(cudaMallocHost(&hsc, sizeof(double) * (S_COUNT + 2)));
+  CK(cudaMalloc(&bar, 2 * sizeof(unsigned)));
+  CK(cudaMemset(bar, 0, 2 * sizeof(unsigned)));
+  CK(cudaMalloc(&err, sizeof(int)));
+  CK(cudaMemset(err, 0, sizeof(int)));
   if (f32_helm) {
     size_t bf = sizeof(float) * (size_t)maxN;
     float** fa[] = {&fD, &fc[0], &fc[1], &fc[2], &fidg, &fr, &fz, &fp, &fAp, &fdx};
     for (auto q : fa) CK(cudaMalloc((void**)q, bf));
   }
+  if (persistent)
+    for (int q = 0; q < PERSIST_VECTORS; ++q) CK(cudaMalloc(&pw[q], (f32_helm ? sizeof(float) : sizeof(double)) * (size_t)maxN));
   return 0;
 }
 
@@ -669,6 +932,9 @@ void Solver::release() {
   {
     float** fa[] = {&fD, &fc[0], &fc[1], &fc[2], &fidg, &fr, &fz, &fp, &fAp, &fdx};
     for (auto q : fa) { cudaFree(*q); *q = nullptr; }
+    for (int q = 0; q < PERSIST_VECTORS; ++q) { cudaFree(pw[q]); pw[q] = nullptr; }
+    cudaFree(bar); cudaFree(err);
+    bar = nullptr; err = nullptr;
   }
   cnt = nullptr;
   cudaFree(mgbuf);
@@ -743,12 +1009,85 @@ int Solver::device_loop(F body) {
   return 0;
 }
 
+template <typename T>
+int Solver::pcg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
+  BoxV A = view(s);
+  int nb = red_grid_cap(s.N, rb);
+  ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
+  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, bar, err);
+  PersistArgs<T> a;
+  a.A = A;
+  a.r64 = r;
+  a.x = s.x;
+  constexpr bool f32 = sizeof(T) == 4;
+  for (int q = 0; q < 3; ++q) a.ch[q] = (T*)pw[q];
+  a.dg = (T*)pw[3];
+  a.sc = (T*)pw[4];
+  for (int q = 0; q < 2; ++q) {
+    a.r[q] = (T*)pw[5 + q];
+    a.s[q] = (T*)pw[7 + q];
+    a.w[q] = (T*)pw[9 + q];
+  }
+  a.p = (T*)pw[11];
+  a.dx = (T*)pw[12];
+  a.part = (T*)part;
+  a.stat = sc;
+  a.done = done;
+  a.bar = bar;
+  a.err = err;
+  int grid = (int)((s.N + PTPB - 1) / PTPB);
+  int cap = persist_blocks(f32);
+  if (grid > cap) grid = cap;
+  if (grid > RED_BLOCKS) grid = RED_BLOCKS;   // partials: 2 x 3 x grid values in part[0, 8 RED_BLOCKS)
+  if (grid < 1) grid = 1;
+  cudaLaunchConfig_t lc;
+  memset(&lc, 0, sizeof(lc));
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(PTPB);
+  lc.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  // algorithmic bytes: setup (FP64 operator read twice and defect in; diag, S, r^, s, p,
+  // x^, c^, w out), the final x += S x^ / nu, and per iteration r^, s, w, p, x^, diag
+  // and c^ in, r^, s, w, p, x^ out
+  const double na = s.c[2] ? 3.0 : 2.0, wb = (double)sizeof(T);
+  const double setup_b = ((2.0 + 2.0 * na) * 8.0 + (7.0 + na) * wb + 2.0 * wb + 16.0) * s.N;
+  const double iter_b = (11.0 + na) * wb * s.N;
+  ++g_launches;
+  {
+    ProfScope ps(prof, KC_SPMV, stream, setup_b);
+    CK(cudaLaunchKernelEx(&lc, k_pcg_persist<T>, a));
+  }
+  if (capturing) return 0;
+  int conv = 0;
+  poll(hsc, sc, done, stream, maxit, &conv);
+  if (prof && prof->on) prof->bytes[KC_SPMV] += hsc[S_ITS] * iter_b;
+  fill_stats(hsc, conv, out);
+  return conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
+}
+
+int Solver::persist_blocks(bool f32) {
+  int& cache = f32 ? pb_f32 : pb_f64;
+  if (cache > 0) return cache;
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (f32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persist<float>, PTPB, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persist<double>, PTPB, 0);
+  cache = per * nsm;
+  return cache;
+}
+
 int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
+  if (persistent) return f32_helm ? pcg_persist<float>(s, rtol, maxit, out) : pcg_persist<double>(s, rtol, maxit, out);
   if (f32_helm) return pcg_jacobi_f32(s, rtol, maxit, out);
   BoxV A = view(s);
   int nb = red_grid_cap(s.N, rb);
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 1, part);
-  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);
+  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, nullptr, nullptr);
   auto iteration = [&]() {
     {
       ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0, (6.0 * (s.c[2] ? 3 : 2) + 3.0) * s.N);
@@ -782,7 +1121,7 @@ int Solver::pcg_jacobi_f32(const BoxSys& s, double rtol, int maxit, SolveStats* 
   int nb = red_grid_cap(s.N, rb);
   // FP64 defect of the initial guess, ||b||, ||r0||
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
-  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);
+  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, nullptr, nullptr);
   ++g_launches, k_mx_setup<<<nb, TPB, 0, stream>>>(A, r, fD, fc[0], fc[1], s.c[2] ? fc[2] : fc[0], fidg, fr, fz, fp, fdx,
                                                   part, done, sc, cnt);
   auto iteration = [&]() {
@@ -966,7 +1305,7 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
   int nb = red_grid_cap(s.N, rb);
   int g = lin_grid(s.N);
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
-  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit);
+  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, nullptr, nullptr);
   vcycle(fp32);
   ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done, sc, cnt, 1);
   ++g_launches, k_cast_done<double, double><<<g, TPB, 0, stream>>>(s.N, p, z, done);
@@ -1054,7 +1393,7 @@ extern "C" int droplet_box_solve_noalloc(const int m[3], const double* D, const 
   int nb = red_grid(N);
   // every vector, partial, scalar and the flag are written by k_pcg_init / k_fin_init before use
   k_pcg_init<<<nb, TPB, 0, st>>>(A, b, x, r, z, p, idg, 1, part);
-  k_fin_init<<<1, TPB, 0, st>>>(part, nb, sc, done, rtol * rtol, maxit);
+  k_fin_init<<<1, TPB, 0, st>>>(part, nb, sc, done, rtol * rtol, maxit, nullptr, nullptr);
   double hs[S_COUNT + 1];
   int d = 0;
   for (int it = 0; it < maxit; it += 8) {
