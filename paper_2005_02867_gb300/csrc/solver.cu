@@ -760,35 +760,70 @@ __global__ void k_mg_coarsen(LevV<T> F, LevV<T> C, T* Dc, T* c0, T* c1, T* c2) {
 
 // V-cycle of levels l0 .. nl-1 inside one thread block (small levels: one launch
 // instead of ten per level).  Same operations and order as the per-level kernels.
+// The iterate x of every tail level and the right-hand side b of the levels the tail
+// restricts to live in shared memory (the sweeps would otherwise wait on L2 after
+// every half sweep); the operator and the first tail level's b are read through L1.
 constexpr int TAIL_MAX_CELLS = 8192;
 constexpr int TAIL_THREADS = 1024;
 template <typename T>
 struct TailLevels {
   LevV<T> L[24];
+  int xo[24], bo[24];   // shared-memory offsets (elements) of x and b per level
+  int total;            // shared-memory elements
 };
 
+// shared-memory elements of a tail over levels of sizes N[l0..nl-1]: x of every level,
+// b of every level but the first, each rounded up to 16 bytes
+static long long tail_layout(const MGLevel* lev, int l0, int nl, size_t es, int* xo, int* bo) {
+  const long long al = 16 / (long long)es;
+  long long off = 0;
+  for (int l = l0; l < nl; ++l) {
+    if (xo) xo[l] = (int)off;
+    off += (lev[l].N + al - 1) / al * al;
+  }
+  for (int l = l0 + 1; l < nl; ++l) {
+    if (bo) bo[l] = (int)off;
+    off += (lev[l].N + al - 1) / al * al;
+  }
+  return off;
+}
+
+// one red-black half sweep over the cells of colour `col` only (half rows)
 template <typename T>
 __device__ void tail_smooth(const LevV<T>& L, int col, int first) {
-  for (long long id = threadIdx.x; id < L.N; id += blockDim.x) {
-    int i, j, k;
-    bdecomp(L.m, id, i, j, k);
-    if (((i + j + k) & 1) == col) gs_cell<T>(L, id, i, j, k, first);
+  const int m0 = L.m[0], m1 = L.m[1], h = (m0 + 1) >> 1;
+  const int n = h * m1 * L.m[2];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int row = t / h, q = t - row * h;
+    const int k = row / m1, j = row - k * m1;
+    const int i = 2 * q + ((j + k + col) & 1);
+    if (i < m0) gs_cell<T>(L, (long long)i + (long long)m0 * row, i, j, k, first);
   }
   __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ LevV<T> tail_level(const TailLevels<T>& TL, T* sm, int l, int l0) {
+  LevV<T> L = TL.L[l];
+  L.x = sm + TL.xo[l];
+  if (l > l0) L.b = sm + TL.bo[l];
+  return L;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels<T> TL, int l0, int nl, int nu, int ncoarse,
                                                           const int* done) {
   if (*done) return;
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  T* sm = reinterpret_cast<T*>(tail_smem);
   for (int l = l0; l < nl - 1; ++l) {
-    const LevV<T>& F = TL.L[l];
+    const LevV<T> F = tail_level<T>(TL, sm, l, l0);
     for (int s = 0; s < nu; ++s) {
       tail_smooth<T>(F, 0, s == 0);
       tail_smooth<T>(F, 1, 0);
     }
-    const LevV<T>& C = TL.L[l + 1];
-    int kz = F.m[2] > 1 ? 2 : 1;
+    const LevV<T> C = tail_level<T>(TL, sm, l + 1, l0);
+    const int kz = F.m[2] > 1 ? 2 : 1;
     for (long long id = threadIdx.x; id < C.N; id += blockDim.x) {
       int I, J, K;
       bdecomp(C.m, id, I, J, K);
@@ -805,7 +840,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels<T> TL, int 
     __syncthreads();
   }
   {
-    const LevV<T>& L = TL.L[nl - 1];
+    const LevV<T> L = tail_level<T>(TL, sm, nl - 1, l0);
     for (int s = 0; s < ncoarse; ++s) {
       tail_smooth<T>(L, 0, s == 0);
       tail_smooth<T>(L, 1, 0);
@@ -816,8 +851,8 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels<T> TL, int 
     }
   }
   for (int l = nl - 2; l >= l0; --l) {
-    const LevV<T>& F = TL.L[l];
-    const LevV<T>& C = TL.L[l + 1];
+    const LevV<T> F = tail_level<T>(TL, sm, l, l0);
+    const LevV<T> C = tail_level<T>(TL, sm, l + 1, l0);
     for (long long id = threadIdx.x; id < F.N; id += blockDim.x) {
       int i, j, k;
       bdecomp(F.m, id, i, j, k);
@@ -831,6 +866,9 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels<T> TL, int 
       tail_smooth<T>(F, 0, 0);
     }
   }
+  // the first tail level's x goes back to global memory for the prolongation above
+  const T* xs = sm + TL.xo[l0];
+  for (long long id = threadIdx.x; id < TL.L[l0].N; id += blockDim.x) TL.L[l0].x[id] = xs[id];
 }
 
 template <typename TO, typename TI>
@@ -1200,6 +1238,18 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
     L.b = take(L.N);
     L.idg = take(L.N);
   }
+  // shared memory of the one-block tail of the V-cycle
+  int lt = nlev - 1;
+  while (lt > 0 && lev[lt - 1].N <= TAIL_MAX_CELLS) --lt;
+  // (the limit is raised to the device's opt-in maximum, not to this hierarchy's need,
+  // so that contexts with different hierarchies do not lower it for one another)
+  const size_t smem = (size_t)tail_layout(lev, lt, nlev, es, nullptr, nullptr) * es;
+  int dev = 0, optin = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > (size_t)optin) return DROPLET_ERR_SIZE;
+  if (fp32) CK(cudaFuncSetAttribute(k_mg_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  else CK(cudaFuncSetAttribute(k_mg_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   mg_fp32 = fp32;
   mg_m[0] = mm[0]; mg_m[1] = mm[1]; mg_m[2] = mm[2];
   return 0;
@@ -1270,7 +1320,16 @@ static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaSt
   }
   TailLevels<T> TL;
   for (int l = 0; l < nlev; ++l) TL.L[l] = lv<T>(lev[l]);
-  ++g_launches, k_mg_tail<T><<<1, TAIL_THREADS, 0, st>>>(TL, lt, nlev, nu, ncoarse, done);
+  TL.total = (int)tail_layout(lev, lt, nlev, sizeof(T), TL.xo, TL.bo);
+  const size_t smem = (size_t)TL.total * sizeof(T);
+  {
+    // algorithmic bytes: the tail levels' operators (D, couplings, 1/diag) and the first
+    // tail level's b in, its x out
+    double tb = 2.0 * lev[lt].N;
+    for (int l = lt; l < nlev; ++l) tb += (2.0 + (lev[l].c[2] ? 3 : 2)) * lev[l].N;
+    ProfScope ps(prof, KC_MG_SMOOTH, st, tb * sizeof(T));
+    ++g_launches, k_mg_tail<T><<<1, TAIL_THREADS, smem, st>>>(TL, lt, nlev, nu, ncoarse, done);
+  }
   for (int l = lt - 1; l >= 0; --l) {
     LevV<T> L = lv<T>(lev[l]), C = lv<T>(lev[l + 1]);
     int g = lin_grid(L.N);
