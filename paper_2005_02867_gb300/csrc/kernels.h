@@ -171,6 +171,9 @@ class Solver {
   template <typename T>
   int pcg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out);
   int persist_blocks(bool f32);
+  template <typename T>
+  int pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out);
+  int pmg_blocks = 0;           // co-resident blocks of the persistent MG-PCG
   float *fD = nullptr, *fc[3] = {nullptr, nullptr, nullptr}, *fidg = nullptr, *fr = nullptr, *fz = nullptr,
         *fp = nullptr, *fAp = nullptr, *fdx = nullptr;
   static constexpr int PERSIST_VECTORS = 13;

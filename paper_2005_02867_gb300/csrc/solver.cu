@@ -410,35 +410,55 @@ struct PersistArgs {
   int* err;
 };
 
-// grid-wide sums of 3 values (nv = 0: plain barrier); returns false when a wait ran out
+// Grid-wide sums of up to 3 values (nv = 0: a plain barrier) for a cooperative launch
+// of PTPB-thread blocks; `phase` counts the grid syncs of the launch (uniform), bar[0]
+// the arrivals (zero at launch), `part` holds 2 x 3 x blocks partials.  The totals are
+// returned to every thread; false when a wait ran out.  FP32 block sums use warp
+// shuffles; FP64 ones go through shared memory so that only three warps do FP64 adds.
 template <typename T>
-__device__ __forceinline__ bool grid_sum3(T (&v)[3], int nv, int phase, const PersistArgs<T>& a) {
+__device__ __forceinline__ bool grid_sum3(T (&v)[3], int nv, int phase, T* part_all, unsigned* bar, int* err) {
   __shared__ T sh[3][PTPB / 32];
   __shared__ int ok;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, G = gridDim.x;
-  T* part = a.part + (phase & 1) * 3 * G;
-  for (int q = 0; q < nv; ++q) {
+  T* part = part_all + (phase & 1) * 3 * G;
+  if (nv > 0) {
+    if constexpr (sizeof(T) == 8) {
+      __shared__ double red[3][PTPB];
+      for (int q = 0; q < nv; ++q) red[q][threadIdx.x] = v[q];
+      __syncthreads();
+      if (wid < nv) {
+        double t = 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
-    if (lane == 0) sh[q][wid] = v[q];
-  }
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    T t = 0;
+        for (int u = 0; u < PTPB / 32; ++u) t += red[wid][lane + 32 * u];
 #pragma unroll
-    for (int w = 0; w < PTPB / 32; ++w) t += sh[threadIdx.x][w];
-    part[threadIdx.x * G + blockIdx.x] = t;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) part[wid * G + blockIdx.x] = t;
+      }
+    } else {
+      for (int q = 0; q < nv; ++q) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+        if (lane == 0) sh[q][wid] = v[q];
+      }
+      __syncthreads();
+      if (threadIdx.x < nv) {
+        T t = 0;
+#pragma unroll
+        for (int w = 0; w < PTPB / 32; ++w) t += sh[threadIdx.x][w];
+        part[threadIdx.x * G + blockIdx.x] = t;
+      }
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
-    atomicAdd(a.bar, 1u);
-    volatile unsigned* cnt = a.bar;
+    atomicAdd(bar, 1u);
+    volatile unsigned* cnt = bar;
     const unsigned target = (unsigned)(phase + 1) * (unsigned)G;
     long long spins = 0;
     int good = 1;
     while (*cnt < target) {
-      if (++spins > BARRIER_SPIN_LIMIT) { atomicExch(a.err, 1); good = 0; break; }
+      if (++spins > BARRIER_SPIN_LIMIT) { atomicExch(err, 1); good = 0; break; }
     }
     __threadfence();
     ok = good;
@@ -504,7 +524,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
     a.dx[id] = 0;
   }
   T v[3] = {0, 0, 0};
-  bool ok = grid_sum3<T>(v, 0, phase++, a);
+  bool ok = grid_sum3<T>(v, 0, phase++, a.part, a.bar, a.err);
   // setup 2: c^ on the low faces, w = A^ r^0, gamma, delta, weighted |r^|^2
   if (ok) {
     const T* r = a.r[0];
@@ -546,7 +566,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
       q += a.dg[id] * rP * rP;
     }
     v[0] = g; v[1] = dl; v[2] = q;
-    ok = grid_sum3<T>(v, 3, phase++, a);
+    ok = grid_sum3<T>(v, 3, phase++, a.part, a.bar, a.err);
   }
   const int maxit = (int)a.stat[S_MAXIT];
   T gamma = v[0], alpha = v[0] / v[1], beta = 0, rho = v[2];
@@ -587,7 +607,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
       q += a.dg[id] * rN * rN;
     }
     v[0] = g; v[1] = dl; v[2] = q;
-    ok = grid_sum3<T>(v, 3, phase++, a);
+    ok = grid_sum3<T>(v, 3, phase++, a.part, a.bar, a.err);
     ++its;
     if (!ok) { result = 3; break; }
     if (threadIdx.x == 0) {
@@ -810,12 +830,11 @@ __device__ __forceinline__ LevV<T> tail_level(const TailLevels<T>& TL, T* sm, in
   return L;
 }
 
+// V-cycle of the tail levels l0 .. nl-1 by the calling block; x and the restricted b
+// in shared memory `sm` (layout TL.xo / TL.bo); level l0's b is read from global
+// memory and its x written back there at the end.
 template <typename T>
-__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels<T> TL, int l0, int nl, int nu, int ncoarse,
-                                                          const int* done) {
-  if (*done) return;
-  extern __shared__ __align__(16) unsigned char tail_smem[];
-  T* sm = reinterpret_cast<T*>(tail_smem);
+__device__ void tail_vcycle(const TailLevels<T>& TL, T* sm, int l0, int nl, int nu, int ncoarse) {
   for (int l = l0; l < nl - 1; ++l) {
     const LevV<T> F = tail_level<T>(TL, sm, l, l0);
     for (int s = 0; s < nu; ++s) {
@@ -869,6 +888,239 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels<T> TL, int 
   // the first tail level's x goes back to global memory for the prolongation above
   const T* xs = sm + TL.xo[l0];
   for (long long id = threadIdx.x; id < TL.L[l0].N; id += blockDim.x) TL.L[l0].x[id] = xs[id];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels<T> TL, int l0, int nl, int nu, int ncoarse,
+                                                          const int* done) {
+  if (*done) return;
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  tail_vcycle<T>(TL, reinterpret_cast<T*>(tail_smem), l0, nl, nu, ncoarse);
+}
+
+// ---------------------------------------------------------------- persistent MG-PCG
+// The whole multigrid-preconditioned CG of the pressure system in one cooperative
+// launch (single droplets of a latency-bound size).  The preconditioner is the V-cycle
+// of the launched path, operation for operation (same sweeps, order, transfer and
+// precision), so the iterates agree with it up to the order of the inner-product sums.
+//
+// Outer iteration: CG in the single-reduction form of Chronopoulos & Gear with the
+// preconditioner, in FP64: z = M r, w = A z, gamma = r.z and delta = w.z from one grid
+// sum, then beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old),
+// p = z + beta p, q = w + beta q (= A p), x += alpha p, r -= alpha q.  The update is
+// fused with the start of the next V-cycle (r cast into the level-0 right-hand side
+// and the first red half sweep, x = b / diag), and |r|^2 travels with that phase's
+// barrier, so the convergence test sees each new residual before any further work.
+//
+// V-cycle phases, each ended by a grid barrier: half sweeps over the cells of one
+// colour; the restriction fused with the coarse level's first red half sweep (which
+// needs only the cell's own b); the prolongation fused with the fine level's first
+// black half sweep, whose red neighbours take their corrected value x + x_coarse on
+// the fly (the red cells' own corrected values are read by nothing else: the next red
+// half sweep overwrites them from their black neighbours).  Levels of at most
+// PMG_TAIL_MAX_CELLS cells run in block 0 out of shared memory while the other blocks
+// wait at the barrier.
+constexpr int PMG_TAIL_MAX_CELLS = 2048;
+
+template <typename T>
+struct MgArgs {
+  BoxV A;                      // FP64 pressure operator
+  double *x, *r, *p, *q, *w;   // solution, residual, direction, q = A p, w = A z
+  TailLevels<T> TL;            // hierarchy views and the tail's shared-memory layout
+  int nlev, lt, nu, ncoarse;   // levels, first tail level, sweeps per side, coarsest sweeps
+  double* part;
+  double* stat;
+  int* done;
+  unsigned* bar;
+  int* err;
+};
+
+// half sweep of colour `col` over a whole level, grid-strided
+template <typename T>
+__device__ __forceinline__ void grid_half_sweep(const LevV<T>& L, int col, int first, int gid, int gs) {
+  const int m0 = L.m[0], m1 = L.m[1], h = (m0 + 1) >> 1;
+  const int n = h * m1 * L.m[2];
+  for (int t = gid; t < n; t += gs) {
+    const int row = t / h, q = t - row * h;
+    const int k = row / m1, j = row - k * m1;
+    const int i = 2 * q + ((j + k + col) & 1);
+    if (i < m0) gs_cell<T>(L, (long long)i + (long long)m0 * row, i, j, k, first);
+  }
+}
+
+// C.b = restricted residual of F; with `red`, also the first (red) half sweep on C
+template <typename T>
+__device__ __forceinline__ void grid_restrict(const LevV<T>& F, const LevV<T>& C, bool red, int gid, int gs) {
+  const int kz = F.m[2] > 1 ? 2 : 1;
+  for (long long id = gid; id < C.N; id += gs) {
+    int I, J, K;
+    bdecomp(C.m, id, I, J, K);
+    T s = 0;
+    for (int dk = 0; dk < kz; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+          int i = 2 * I + di, j = 2 * J + dj, k = kz == 2 ? 2 * K + dk : 0;
+          long long fi = (long long)i + (long long)F.m[0] * ((long long)j + (long long)F.m[1] * k);
+          s += mg_resid<T>(F, fi, i, j, k);
+        }
+    ((T*)C.b)[id] = s;
+    if (red && ((I + J + K) & 1) == 0) C.x[id] = s * C.idg[id];
+  }
+}
+
+// x of F at a cell plus its coarse-level correction
+template <typename T>
+__device__ __forceinline__ T prolonged(const LevV<T>& F, const LevV<T>& C, long long id, int i, int j, int k) {
+  const int K = F.m[2] > 1 ? k / 2 : 0;
+  const long long ci = (long long)(i / 2) + (long long)C.m[0] * ((long long)(j / 2) + (long long)C.m[1] * K);
+  return F.x[id] + C.x[ci];
+}
+
+// prolongation F.x += C.x fused with the black half sweep of F (same arithmetic as
+// the separate prolongation followed by gs_cell)
+template <typename T>
+__device__ __forceinline__ void grid_prolong_black(const LevV<T>& F, const LevV<T>& C, int gid, int gs) {
+  const int m0 = F.m[0], m1 = F.m[1], m2 = F.m[2], h = (m0 + 1) >> 1;
+  const int n = h * m1 * m2;
+  const long long st1 = m0, st2 = (long long)m0 * m1;
+  for (int t = gid; t < n; t += gs) {
+    const int row = t / h, q = t - row * h;
+    const int k = row / m1, j = row - k * m1;
+    const int i = 2 * q + ((j + k + 1) & 1);
+    if (i >= m0) continue;
+    const long long id = (long long)i + (long long)m0 * row;
+    T s = F.b[id];
+    if (i > 0) s += F.c[0][id] * prolonged<T>(F, C, id - 1, i - 1, j, k);
+    if (i < m0 - 1) s += F.c[0][id + 1] * prolonged<T>(F, C, id + 1, i + 1, j, k);
+    if (j > 0) s += F.c[1][id] * prolonged<T>(F, C, id - st1, i, j - 1, k);
+    if (j < m1 - 1) s += F.c[1][id + st1] * prolonged<T>(F, C, id + st1, i, j + 1, k);
+    if (F.c[2]) {
+      if (k > 0) s += F.c[2][id] * prolonged<T>(F, C, id - st2, i, j, k - 1);
+      if (k < m2 - 1) s += F.c[2][id + st2] * prolonged<T>(F, C, id + st2, i, j, k + 1);
+    }
+    F.x[id] = s * F.idg[id];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
+  if (*a.done) return;                      // converged at the initial guess
+  extern __shared__ __align__(16) unsigned char pmg_smem[];
+  T* sm = reinterpret_cast<T*>(pmg_smem);
+  __shared__ double bc[2];
+  const int gs = gridDim.x * blockDim.x;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const LevV<T>& L0 = a.TL.L[0];
+  const long long N = a.A.N;
+  const double thr = a.stat[S_TOL2] * a.stat[S_BB];
+  const int maxit = (int)a.stat[S_MAXIT], lt = a.lt, nu = a.nu;
+  const bool b_alias = (const void*)L0.b == (const void*)a.r;   // FP64 hierarchy: level-0 b is r
+  double alpha = 0.0, beta = 0.0, gamma = 1.0, rr_last = a.stat[S_RR];
+  int phase = 0, its = 0, result = 2;
+  for (;;) {
+    // phase A: CG update, level-0 right-hand side, first red half sweep of level 0
+    double rrl = 0.0;
+    for (long long id = gid; id < N; id += gs) {
+      double rP = a.r[id];
+      if (its > 0) {
+        const double zP = (double)L0.x[id];
+        const double pP = its > 1 ? zP + beta * a.p[id] : zP;         // p_old = 0 at the start
+        const double qP = its > 1 ? a.w[id] + beta * a.q[id] : a.w[id];
+        a.p[id] = pP;
+        a.q[id] = qP;
+        a.x[id] += alpha * pP;
+        rP -= alpha * qP;
+        a.r[id] = rP;
+        rrl += rP * rP;
+      }
+      const T bP = (T)rP;
+      if (!b_alias) ((T*)L0.b)[id] = bP;
+      if (lt > 0) {
+        int i, j, k;
+        bdecomp(L0.m, id, i, j, k);
+        if (((i + j + k) & 1) == 0) L0.x[id] = bP * L0.idg[id];
+      }
+    }
+    double v[3] = {rrl, 0.0, 0.0};
+    if (!grid_sum3<double>(v, its > 0 ? 1 : 0, phase++, a.part, a.bar, a.err)) { result = 3; break; }
+    if (its > 0) {
+      rr_last = v[0];
+      if (v[0] <= thr) { result = 1; break; }
+    }
+    if (its >= maxit) break;
+    // V-cycle: pre-smoothing and restriction on the grid levels (red half sweep of
+    // sweep 0 already done by the phase before)
+    bool ok = true;
+    for (int l = 0; l < lt && ok; ++l) {
+      const LevV<T>& F = a.TL.L[l];
+      for (int s = 0; s < nu && ok; ++s) {
+        if (s > 0) {
+          grid_half_sweep<T>(F, 0, 0, gid, gs);
+          ok = grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+        }
+        grid_half_sweep<T>(F, 1, 0, gid, gs);
+        ok = ok && grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+      }
+      if (!ok) break;
+      grid_restrict<T>(F, a.TL.L[l + 1], l + 1 < lt, gid, gs);
+      ok = grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+    }
+    if (!ok) { result = 3; break; }
+    // the tail levels in block 0, out of shared memory
+    if (blockIdx.x == 0) tail_vcycle<T>(a.TL, sm, lt, a.nlev, nu, a.ncoarse);
+    if (!grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err)) { result = 3; break; }
+    // prolongation and post-smoothing on the grid levels
+    for (int l = lt - 1; l >= 0 && ok; --l) {
+      const LevV<T>& F = a.TL.L[l];
+      grid_prolong_black<T>(F, a.TL.L[l + 1], gid, gs);
+      ok = grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+      grid_half_sweep<T>(F, 0, 0, gid, gs);
+      ok = ok && grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+      for (int s = 1; s < nu && ok; ++s) {
+        grid_half_sweep<T>(F, 1, 0, gid, gs);
+        ok = grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+        grid_half_sweep<T>(F, 0, 0, gid, gs);
+        ok = ok && grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+      }
+    }
+    if (!ok) { result = 3; break; }
+    // phase W: z = M r (level-0 x), w = A z, gamma = r.z, delta = w.z
+    double gl = 0.0, dl = 0.0;
+    for (long long id = gid; id < N; id += gs) {
+      int i, j, k;
+      bdecomp(a.A.m, id, i, j, k);
+      double wP, dtot;
+      box_row<double, T, false>(a.A.m, a.A.D, a.A.c, L0.x, id, i, j, k, wP, dtot);
+      const double zP = (double)L0.x[id];
+      a.w[id] = wP;
+      gl += a.r[id] * zP;
+      dl += wP * zP;
+    }
+    v[0] = gl;
+    v[1] = dl;
+    if (!grid_sum3<double>(v, 2, phase++, a.part, a.bar, a.err)) { result = 3; break; }
+    if (threadIdx.x == 0) {
+      if (its == 0) {
+        bc[0] = v[0] / v[1];
+        bc[1] = 0.0;
+      } else {
+        const double bn = v[0] / gamma;
+        bc[0] = v[0] / (v[1] - bn * v[0] / alpha);
+        bc[1] = bn;
+      }
+    }
+    __syncthreads();
+    alpha = bc[0];
+    beta = bc[1];
+    gamma = v[0];
+    __syncthreads();
+    ++its;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.stat[S_ITS] = (double)its;
+    a.stat[S_RR] = rr_last;
+    *a.done = result == 1 ? 1 : 2;
+  }
 }
 
 template <typename TO, typename TI>
@@ -1250,6 +1502,31 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
   if (smem > (size_t)optin) return DROPLET_ERR_SIZE;
   if (fp32) CK(cudaFuncSetAttribute(k_mg_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   else CK(cudaFuncSetAttribute(k_mg_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  if (persistent) {
+    // the persistent MG-PCG: its own (smaller) tail; co-resident blocks at that size
+    int ltp = nlev - 1;
+    while (ltp > 0 && lev[ltp - 1].N <= PMG_TAIL_MAX_CELLS) --ltp;
+    const size_t psm = (size_t)tail_layout(lev, ltp, nlev, es, nullptr, nullptr) * es;
+    int nsm = 0, per = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    // (dynamic limit: the opt-in maximum less the kernel's static shared memory)
+    cudaFuncAttributes fa;
+    if (fp32) {
+      CK(cudaFuncGetAttributes(&fa, k_mgpcg_persist<float>));
+      if (psm + fa.sharedSizeBytes > (size_t)optin) return DROPLET_ERR_SIZE;
+      CK(cudaFuncSetAttribute(k_mgpcg_persist<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes));
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mgpcg_persist<float>, PTPB, psm));
+    } else {
+      CK(cudaFuncGetAttributes(&fa, k_mgpcg_persist<double>));
+      if (psm + fa.sharedSizeBytes > (size_t)optin) return DROPLET_ERR_SIZE;
+      CK(cudaFuncSetAttribute(k_mgpcg_persist<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)fa.sharedSizeBytes));
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mgpcg_persist<double>, PTPB, psm));
+    }
+    pmg_blocks = per * nsm;
+    if (pmg_blocks < 1) return DROPLET_ERR_SIZE;
+  }
   mg_fp32 = fp32;
   mg_m[0] = mm[0]; mg_m[1] = mm[1]; mg_m[2] = mm[2];
   return 0;
@@ -1356,7 +1633,86 @@ void Solver::vcycle(int fp32) {
   }
 }
 
+template <typename T>
+int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
+  constexpr bool f32 = sizeof(T) == 4;
+  int rc = build_mg(s, f32);
+  if (rc) return rc;
+  if (!f32) { lev[0].b = r; lev[0].x = z; }
+  BoxV A = view(s);
+  int nb = red_grid_cap(s.N, rb);
+  ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
+  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, bar, err);
+  MgArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.A = A;
+  a.x = s.x;
+  a.r = r;
+  a.p = p;
+  a.q = Ap;
+  a.w = idg;
+  for (int l = 0; l < nlev; ++l) a.TL.L[l] = lv<T>(lev[l]);
+  int lt = nlev - 1;
+  while (lt > 0 && lev[lt - 1].N <= PMG_TAIL_MAX_CELLS) --lt;
+  a.nlev = nlev;
+  a.lt = lt;
+  a.nu = 2;
+  a.ncoarse = 4;
+  a.TL.total = (int)tail_layout(lev, lt, nlev, sizeof(T), a.TL.xo, a.TL.bo);
+  a.part = part;
+  a.stat = sc;
+  a.done = done;
+  a.bar = bar;
+  a.err = err;
+  const size_t smem = (size_t)a.TL.total * sizeof(T);
+  int grid = (int)((s.N + PTPB - 1) / PTPB);
+  if (grid > pmg_blocks) grid = pmg_blocks;
+  if (grid > RED_BLOCKS) grid = RED_BLOCKS;
+  if (grid < 1) grid = 1;
+  cudaLaunchConfig_t lc;
+  memset(&lc, 0, sizeof(lc));
+  lc.gridDim = dim3(grid);
+  lc.blockDim = dim3(PTPB);
+  lc.dynamicSmemBytes = smem;
+  lc.stream = stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  // algorithmic bytes per iteration: level-0 FP64 vectors (update: x, r, p, q, w in,
+  // x, r, p, q out; w = A z: operator in, w out), the level-0 b and z in the hierarchy
+  // precision, the grid levels' sweeps and transfers as counted for the launched
+  // kernels, and the tail; FP64 flops: the update and w = A z, plus the sweeps of an
+  // FP64 hierarchy
+  const double d = s.c[2] ? 3.0 : 2.0, es = (double)sizeof(T), N0 = (double)s.N;
+  double iter_b = (9.0 * 8.0 + 3.0 * es) * N0 + ((1.0 + d) * 8.0 + 16.0 + es) * N0;
+  double iter_f = (10.0 + 4.0 * d) * N0;
+  for (int l = 0; l < lt; ++l) {
+    const double Nl = (double)lev[l].N, Nc = (double)lev[l + 1].N;
+    iter_b += 4.0 * a.nu * (2.5 + d) * Nl * es + ((3.0 + d) * Nl + Nc) * es + (2.0 * Nl + Nc) * es;
+    if (!f32) iter_f += 4.0 * a.nu * (1.0 + 2.0 * d) * 0.5 * Nl;
+  }
+  iter_b += 2.0 * lev[lt].N * es;
+  for (int l = lt; l < nlev; ++l) iter_b += (2.0 + d) * lev[l].N * es;
+  ++g_launches;
+  {
+    ProfScope ps(prof, KC_MG_SMOOTH, stream, 0.0);
+    CK(cudaLaunchKernelEx(&lc, k_mgpcg_persist<T>, a));
+  }
+  if (capturing) return 0;
+  int conv = 0;
+  poll(hsc, sc, done, stream, maxit, &conv);
+  if (prof && prof->on) {
+    prof->bytes[KC_MG_SMOOTH] += hsc[S_ITS] * iter_b;
+    prof->flops[KC_MG_SMOOTH] += hsc[S_ITS] * iter_f;
+  }
+  fill_stats(hsc, conv, out);
+  return conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
+}
+
 int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats* out) {
+  if (persistent) return fp32 ? pcg_mg_persist<float>(s, rtol, maxit, out) : pcg_mg_persist<double>(s, rtol, maxit, out);
   int rc = build_mg(s, fp32);
   if (rc) return rc;
   if (!fp32) { lev[0].b = r; lev[0].x = z; }
