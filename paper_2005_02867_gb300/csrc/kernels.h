@@ -139,6 +139,7 @@ struct MGLevel {
   void* x;
   void* b;
   void* idg;        // 1 / (D + sum of adjacent couplings), used by the smoother
+  void* xp;         // post-smoothed iterate (tiled persistent V-cycle)
 };
 
 class Solver {
@@ -174,6 +175,7 @@ class Solver {
   template <typename T>
   int pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out);
   int pmg_blocks = 0;           // co-resident blocks of the persistent MG-PCG
+  double* mg_q2 = nullptr;      // second buffer of its q = A p
   float *fD = nullptr, *fc[3] = {nullptr, nullptr, nullptr}, *fidg = nullptr, *fr = nullptr, *fz = nullptr,
         *fp = nullptr, *fAp = nullptr, *fdx = nullptr;
   static constexpr int PERSIST_VECTORS = 13;

@@ -654,6 +654,7 @@ struct LevV {
   T* x;
   const T* b;
   const T* idg;
+  T* xp;        // post-smoothed iterate of the tiled persistent V-cycle
 };
 
 // one cell of a red-black Gauss-Seidel half sweep: x_P = (b_P + sum c x_nb) / diag_total
@@ -922,19 +923,6 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels<T> TL, int 
 // wait at the barrier.
 constexpr int PMG_TAIL_MAX_CELLS = 2048;
 
-template <typename T>
-struct MgArgs {
-  BoxV A;                      // FP64 pressure operator
-  double *x, *r, *p, *q, *w;   // solution, residual, direction, q = A p, w = A z
-  TailLevels<T> TL;            // hierarchy views and the tail's shared-memory layout
-  int nlev, lt, nu, ncoarse;   // levels, first tail level, sweeps per side, coarsest sweeps
-  double* part;
-  double* stat;
-  int* done;
-  unsigned* bar;
-  int* err;
-};
-
 // half sweep of colour `col` over a whole level, grid-strided
 template <typename T>
 __device__ __forceinline__ void grid_half_sweep(const LevV<T>& L, int col, int first, int gid, int gs) {
@@ -970,10 +958,11 @@ __device__ __forceinline__ void grid_restrict(const LevV<T>& F, const LevV<T>& C
 
 // x of F at a cell plus its coarse-level correction
 template <typename T>
-__device__ __forceinline__ T prolonged(const LevV<T>& F, const LevV<T>& C, long long id, int i, int j, int k) {
+__device__ __forceinline__ T prolonged(const LevV<T>& F, const LevV<T>& C, const T* cx, long long id, int i, int j,
+                                      int k) {
   const int K = F.m[2] > 1 ? k / 2 : 0;
   const long long ci = (long long)(i / 2) + (long long)C.m[0] * ((long long)(j / 2) + (long long)C.m[1] * K);
-  return F.x[id] + C.x[ci];
+  return F.x[id] + cx[ci];
 }
 
 // prolongation F.x += C.x fused with the black half sweep of F (same arithmetic as
@@ -990,16 +979,213 @@ __device__ __forceinline__ void grid_prolong_black(const LevV<T>& F, const LevV<
     if (i >= m0) continue;
     const long long id = (long long)i + (long long)m0 * row;
     T s = F.b[id];
-    if (i > 0) s += F.c[0][id] * prolonged<T>(F, C, id - 1, i - 1, j, k);
-    if (i < m0 - 1) s += F.c[0][id + 1] * prolonged<T>(F, C, id + 1, i + 1, j, k);
-    if (j > 0) s += F.c[1][id] * prolonged<T>(F, C, id - st1, i, j - 1, k);
-    if (j < m1 - 1) s += F.c[1][id + st1] * prolonged<T>(F, C, id + st1, i, j + 1, k);
+    if (i > 0) s += F.c[0][id] * prolonged<T>(F, C, C.x, id - 1, i - 1, j, k);
+    if (i < m0 - 1) s += F.c[0][id + 1] * prolonged<T>(F, C, C.x, id + 1, i + 1, j, k);
+    if (j > 0) s += F.c[1][id] * prolonged<T>(F, C, C.x, id - st1, i, j - 1, k);
+    if (j < m1 - 1) s += F.c[1][id + st1] * prolonged<T>(F, C, C.x, id + st1, i, j + 1, k);
     if (F.c[2]) {
-      if (k > 0) s += F.c[2][id] * prolonged<T>(F, C, id - st2, i, j, k - 1);
-      if (k < m2 - 1) s += F.c[2][id + st2] * prolonged<T>(F, C, id + st2, i, j, k + 1);
+      if (k > 0) s += F.c[2][id] * prolonged<T>(F, C, C.x, id - st2, i, j, k - 1);
+      if (k < m2 - 1) s += F.c[2][id + st2] * prolonged<T>(F, C, C.x, id + st2, i, j, k + 1);
     }
     F.x[id] = s * F.idg[id];
   }
+}
+
+// Temporal blocking of the smoothing on 2D levels: each block takes a TLX x TLY tile,
+// loads it with THALO rings into shared memory and runs all 2 nu half sweeps there.
+// Half sweep s updates the cells within THALO - s rings of the tile (clipped to the
+// level), which read only cells updated by half sweep s - 1, so the tile's cells end
+// with exactly the values of the level-wide sweeps (same arithmetic, same order) and a
+// whole pre- or post-smoothing costs one grid barrier instead of 2 nu.
+constexpr int MG_NU = 2;                       // red-black sweeps before and after
+constexpr int TLX = 32, TLY = 32;              // owned tile
+constexpr int THALO = 2 * MG_NU;               // rings: one per half sweep
+constexpr int TRX = TLX + 2 * THALO, TRY = TLY + 2 * THALO;
+constexpr int TREG = TRX * TRY;                // cells of a tile region
+
+// dynamic shared memory of the persistent MG-PCG: the tail, then five tile arrays
+static size_t pmg_smem_bytes(int tail_elems, size_t es) { return ((size_t)(tail_elems + 3) / 4 * 4 + 5 * (size_t)TREG) * es; }
+
+template <typename T>
+struct TileSmem {
+  T *x, *b, *idg, *c0, *c1;
+};
+
+struct TileBox {
+  int oi0, oi1, oj0, oj1;   // owned cells
+  int i0, j0, rx, ry;       // region origin and extent (owned + THALO rings, clipped)
+};
+
+__device__ __forceinline__ TileBox tile_box(int m0, int m1, int t) {
+  const int ntx = (m0 + TLX - 1) / TLX;
+  const int ty = t / ntx, tx = t - ty * ntx;
+  TileBox B;
+  B.oi0 = tx * TLX;
+  B.oi1 = min(B.oi0 + TLX, m0);
+  B.oj0 = ty * TLY;
+  B.oj1 = min(B.oj0 + TLY, m1);
+  B.i0 = max(B.oi0 - THALO, 0);
+  B.j0 = max(B.oj0 - THALO, 0);
+  B.rx = min(B.oi1 + THALO, m0) - B.i0;
+  B.ry = min(B.oj1 + THALO, m1) - B.j0;
+  return B;
+}
+
+__device__ __forceinline__ int tile_count(int m0, int m1) { return ((m0 + TLX - 1) / TLX) * ((m1 + TLY - 1) / TLY); }
+
+// the 2 nu half sweeps of a loaded tile; pre: red (from b alone), black, red, black;
+// post: black, red, black, red (gs_cell's arithmetic)
+template <typename T>
+__device__ void tile_sweeps(const TileSmem<T>& S, const TileBox& B, int m0, int m1, bool pre) {
+  for (int s = 1; s <= 2 * MG_NU; ++s) {
+    const int col = pre ? ((s - 1) & 1) : (s & 1);
+    const int ring = THALO - s;
+    const int a0 = max(B.oi0 - ring, 0), a1 = min(B.oi1 + ring, m0);
+    const int b0 = max(B.oj0 - ring, 0), b1 = min(B.oj1 + ring, m1);
+    const int w = a1 - a0, n = w * (b1 - b0);
+    const bool first = pre && s == 1;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const int jj = t / w;
+      const int i = a0 + (t - jj * w), j = b0 + jj;
+      if (((i + j) & 1) != col) continue;
+      const int c = (i - B.i0) + B.rx * (j - B.j0);
+      T v = S.b[c];
+      if (!first) {
+        if (i > 0) v += S.c0[c] * S.x[c - 1];
+        if (i < m0 - 1) v += S.c0[c + 1] * S.x[c + 1];
+        if (j > 0) v += S.c1[c] * S.x[c - B.rx];
+        if (j < m1 - 1) v += S.c1[c + B.rx] * S.x[c + B.rx];
+      }
+      S.x[c] = v * S.idg[c];
+    }
+    __syncthreads();
+  }
+}
+
+// operator of a tile region into shared memory
+template <typename T>
+__device__ __forceinline__ void tile_load_op(const TileSmem<T>& S, const TileBox& B, const LevV<T>& F, int c,
+                                             long long g) {
+  S.idg[c] = F.idg[g];
+  S.c0[c] = F.c[0][g];
+  S.c1[c] = F.c[1][g];
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_store_x(const TileSmem<T>& S, const TileBox& B, int m0, T* dst) {
+  const int w = B.oi1 - B.oi0, n = w * (B.oj1 - B.oj0);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int jj = t / w;
+    const int i = B.oi0 + (t - jj * w), j = B.oj0 + jj;
+    dst[(long long)i + (long long)m0 * j] = S.x[(i - B.i0) + B.rx * (j - B.j0)];
+  }
+}
+
+// pre-smoothing of a 2D level l >= 1 (b from the restriction), tile by tile
+template <typename T>
+__device__ void tiled_pre(const TileSmem<T>& S, const LevV<T>& F) {
+  const int m0 = F.m[0], m1 = F.m[1];
+  for (int t = blockIdx.x; t < tile_count(m0, m1); t += gridDim.x) {
+    const TileBox B = tile_box(m0, m1, t);
+    const int n = B.rx * B.ry;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const int lj = c / B.rx;
+      const long long g = (long long)(B.i0 + c - lj * B.rx) + (long long)m0 * (B.j0 + lj);
+      S.b[c] = F.b[g];
+      tile_load_op<T>(S, B, F, c, g);
+    }
+    __syncthreads();
+    tile_sweeps<T>(S, B, m0, m1, true);
+    tile_store_x<T>(S, B, m0, F.x);
+    __syncthreads();
+  }
+}
+
+// prolongation and post-smoothing of a 2D level, tile by tile: reads the pre-smoothed
+// F.x and the coarse level's final iterate cx, writes F.xp (tiles of other blocks
+// still read F.x in their halos during the phase)
+template <typename T>
+__device__ void tiled_post(const TileSmem<T>& S, const LevV<T>& F, const LevV<T>& C, const T* cx) {
+  const int m0 = F.m[0], m1 = F.m[1];
+  for (int t = blockIdx.x; t < tile_count(m0, m1); t += gridDim.x) {
+    const TileBox B = tile_box(m0, m1, t);
+    const int n = B.rx * B.ry;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const int lj = c / B.rx;
+      const int i = B.i0 + c - lj * B.rx, j = B.j0 + lj;
+      const long long g = (long long)i + (long long)m0 * j;
+      S.x[c] = prolonged<T>(F, C, cx, g, i, j, 0);
+      S.b[c] = F.b[g];
+      tile_load_op<T>(S, B, F, c, g);
+    }
+    __syncthreads();
+    tile_sweeps<T>(S, B, m0, m1, false);
+    tile_store_x<T>(S, B, m0, F.xp);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+struct MgArgs {
+  BoxV A;                      // FP64 pressure operator
+  double* x;                   // solution
+  double *r[2], *q[2];         // residual and q = A p, double buffered (tiles read neighbours')
+  double *p, *w;               // direction, w = A z
+  TailLevels<T> TL;            // hierarchy views and the tail's shared-memory layout
+  const T* z0;                 // level-0 iterate at the end of a V-cycle (z = M r)
+  int nlev, lt, ncoarse;       // levels, first tail level, coarsest-level sweeps
+  double* part;
+  double* stat;
+  int* done;
+  unsigned* bar;
+  int* err;
+};
+
+// Phase A on a 2D level 0: the CG update (x, p of the tile's cells; r and q of the
+// tile region into the other buffers, halo cells recomputed from the neighbours'
+// current values), b = r, and the whole pre-smoothing of the tile.  Returns the
+// block's share of |r_new|^2 over its owned cells.
+template <typename T>
+__device__ double tiled_phase_a(const TileSmem<T>& S, const MgArgs<T>& a, int cur, int its, double alpha,
+                                double beta) {
+  const LevV<T>& L0 = a.TL.L[0];
+  const int m0 = L0.m[0], m1 = L0.m[1];
+  const double *r = a.r[cur], *q = a.q[cur];
+  double *rn = a.r[cur ^ 1], *qn = a.q[cur ^ 1];
+  double rr = 0.0;
+  for (int t = blockIdx.x; t < tile_count(m0, m1); t += gridDim.x) {
+    const TileBox B = tile_box(m0, m1, t);
+    const int n = B.rx * B.ry;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const int lj = c / B.rx;
+      const int i = B.i0 + c - lj * B.rx, j = B.j0 + lj;
+      const long long g = (long long)i + (long long)m0 * j;
+      double rP = r[g];
+      const bool own = i >= B.oi0 && i < B.oi1 && j >= B.oj0 && j < B.oj1;
+      if (its > 0) {
+        const double qP = its > 1 ? a.w[g] + beta * q[g] : a.w[g];   // q_old = 0 at the start
+        rP -= alpha * qP;
+        if (own) {
+          const double zP = (double)a.z0[g];
+          const double pP = its > 1 ? zP + beta * a.p[g] : zP;
+          a.p[g] = pP;
+          a.x[g] += alpha * pP;
+          qn[g] = qP;
+          rn[g] = rP;
+          rr += rP * rP;
+        }
+      }
+      const T bP = (T)rP;
+      S.b[c] = bP;
+      if (own) ((T*)L0.b)[g] = bP;
+      tile_load_op<T>(S, B, L0, c, g);
+    }
+    __syncthreads();
+    tile_sweeps<T>(S, B, m0, m1, true);
+    tile_store_x<T>(S, B, m0, L0.x);
+    __syncthreads();
+  }
+  return rr;
 }
 
 template <typename T>
@@ -1007,98 +1193,129 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
   if (*a.done) return;                      // converged at the initial guess
   extern __shared__ __align__(16) unsigned char pmg_smem[];
   T* sm = reinterpret_cast<T*>(pmg_smem);
+  TileSmem<T> S;
+  {
+    T* tb = sm + (a.TL.total + 3) / 4 * 4;
+    S.x = tb;
+    S.b = tb + TREG;
+    S.idg = tb + 2 * TREG;
+    S.c0 = tb + 3 * TREG;
+    S.c1 = tb + 4 * TREG;
+  }
   __shared__ double bc[2];
   const int gs = gridDim.x * blockDim.x;
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const LevV<T>& L0 = a.TL.L[0];
   const long long N = a.A.N;
   const double thr = a.stat[S_TOL2] * a.stat[S_BB];
-  const int maxit = (int)a.stat[S_MAXIT], lt = a.lt, nu = a.nu;
-  const bool b_alias = (const void*)L0.b == (const void*)a.r;   // FP64 hierarchy: level-0 b is r
+  const int maxit = (int)a.stat[S_MAXIT], lt = a.lt;
   double alpha = 0.0, beta = 0.0, gamma = 1.0, rr_last = a.stat[S_RR];
-  int phase = 0, its = 0, result = 2;
+  int phase = 0, its = 0, result = 2, cur = 0;
+  auto sync = [&](double (&v)[3], int nv) { return grid_sum3<double>(v, nv, phase++, a.part, a.bar, a.err); };
   for (;;) {
-    // phase A: CG update, level-0 right-hand side, first red half sweep of level 0
-    double rrl = 0.0;
-    for (long long id = gid; id < N; id += gs) {
-      double rP = a.r[id];
-      if (its > 0) {
-        const double zP = (double)L0.x[id];
-        const double pP = its > 1 ? zP + beta * a.p[id] : zP;         // p_old = 0 at the start
-        const double qP = its > 1 ? a.w[id] + beta * a.q[id] : a.w[id];
-        a.p[id] = pP;
-        a.q[id] = qP;
-        a.x[id] += alpha * pP;
-        rP -= alpha * qP;
-        a.r[id] = rP;
-        rrl += rP * rP;
-      }
-      const T bP = (T)rP;
-      if (!b_alias) ((T*)L0.b)[id] = bP;
-      if (lt > 0) {
-        int i, j, k;
-        bdecomp(L0.m, id, i, j, k);
-        if (((i + j + k) & 1) == 0) L0.x[id] = bP * L0.idg[id];
+    double v[3] = {0.0, 0.0, 0.0};
+    const bool tiled0 = lt > 0 && L0.m[2] == 1;
+    // phase A: CG update, level-0 right-hand side and the start of the pre-smoothing
+    if (tiled0) {
+      v[0] = tiled_phase_a<T>(S, a, cur, its, alpha, beta);
+    } else {
+      const double *r = a.r[cur], *q = a.q[cur];
+      double *rn = a.r[cur ^ 1], *qn = a.q[cur ^ 1];
+      for (long long id = gid; id < N; id += gs) {
+        double rP = r[id];
+        if (its > 0) {
+          const double zP = (double)a.z0[id];
+          const double pP = its > 1 ? zP + beta * a.p[id] : zP;   // p_old = q_old = 0 at the start
+          const double qP = its > 1 ? a.w[id] + beta * q[id] : a.w[id];
+          a.p[id] = pP;
+          qn[id] = qP;
+          a.x[id] += alpha * pP;
+          rP -= alpha * qP;
+          rn[id] = rP;
+          v[0] += rP * rP;
+        }
+        const T bP = (T)rP;
+        ((T*)L0.b)[id] = bP;
+        if (lt > 0) {
+          int i, j, k;
+          bdecomp(L0.m, id, i, j, k);
+          if (((i + j + k) & 1) == 0) L0.x[id] = bP * L0.idg[id];
+        }
       }
     }
-    double v[3] = {rrl, 0.0, 0.0};
-    if (!grid_sum3<double>(v, its > 0 ? 1 : 0, phase++, a.part, a.bar, a.err)) { result = 3; break; }
+    if (!sync(v, its > 0 ? 1 : 0)) { result = 3; break; }
     if (its > 0) {
+      cur ^= 1;
       rr_last = v[0];
       if (v[0] <= thr) { result = 1; break; }
     }
     if (its >= maxit) break;
-    // V-cycle: pre-smoothing and restriction on the grid levels (red half sweep of
-    // sweep 0 already done by the phase before)
+    // V-cycle down: pre-smoothing and restriction on the grid levels
     bool ok = true;
     for (int l = 0; l < lt && ok; ++l) {
       const LevV<T>& F = a.TL.L[l];
-      for (int s = 0; s < nu && ok; ++s) {
-        if (s > 0) {
-          grid_half_sweep<T>(F, 0, 0, gid, gs);
-          ok = grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+      const bool tl = F.m[2] == 1;
+      if (!tl) {   // level-wide half sweeps (the red half sweep of sweep 0 came before)
+        for (int s = 0; s < MG_NU && ok; ++s) {
+          if (s > 0) {
+            grid_half_sweep<T>(F, 0, 0, gid, gs);
+            ok = sync(v, 0);
+          }
+          grid_half_sweep<T>(F, 1, 0, gid, gs);
+          ok = ok && sync(v, 0);
         }
-        grid_half_sweep<T>(F, 1, 0, gid, gs);
-        ok = ok && grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+        if (!ok) break;
       }
-      if (!ok) break;
-      grid_restrict<T>(F, a.TL.L[l + 1], l + 1 < lt, gid, gs);
-      ok = grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+      const LevV<T>& C = a.TL.L[l + 1];
+      const bool ctl = l + 1 < lt && C.m[2] == 1;
+      grid_restrict<T>(F, C, l + 1 < lt && !ctl, gid, gs);
+      ok = sync(v, 0);
+      if (ok && ctl) {
+        tiled_pre<T>(S, C);
+        ok = sync(v, 0);
+      }
     }
     if (!ok) { result = 3; break; }
     // the tail levels in block 0, out of shared memory
-    if (blockIdx.x == 0) tail_vcycle<T>(a.TL, sm, lt, a.nlev, nu, a.ncoarse);
-    if (!grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err)) { result = 3; break; }
-    // prolongation and post-smoothing on the grid levels
+    if (blockIdx.x == 0) tail_vcycle<T>(a.TL, sm, lt, a.nlev, MG_NU, a.ncoarse);
+    if (!sync(v, 0)) { result = 3; break; }
+    // V-cycle up: prolongation and post-smoothing on the grid levels
     for (int l = lt - 1; l >= 0 && ok; --l) {
       const LevV<T>& F = a.TL.L[l];
+      if (F.m[2] == 1) {
+        const LevV<T>& C = a.TL.L[l + 1];
+        tiled_post<T>(S, F, C, l + 1 < lt ? C.xp : C.x);
+        ok = sync(v, 0);
+        continue;
+      }
       grid_prolong_black<T>(F, a.TL.L[l + 1], gid, gs);
-      ok = grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+      ok = sync(v, 0);
       grid_half_sweep<T>(F, 0, 0, gid, gs);
-      ok = ok && grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
-      for (int s = 1; s < nu && ok; ++s) {
+      ok = ok && sync(v, 0);
+      for (int s = 1; s < MG_NU && ok; ++s) {
         grid_half_sweep<T>(F, 1, 0, gid, gs);
-        ok = grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+        ok = sync(v, 0);
         grid_half_sweep<T>(F, 0, 0, gid, gs);
-        ok = ok && grid_sum3<double>(v, 0, phase++, a.part, a.bar, a.err);
+        ok = ok && sync(v, 0);
       }
     }
     if (!ok) { result = 3; break; }
     // phase W: z = M r (level-0 x), w = A z, gamma = r.z, delta = w.z
-    double gl = 0.0, dl = 0.0;
-    for (long long id = gid; id < N; id += gs) {
-      int i, j, k;
-      bdecomp(a.A.m, id, i, j, k);
-      double wP, dtot;
-      box_row<double, T, false>(a.A.m, a.A.D, a.A.c, L0.x, id, i, j, k, wP, dtot);
-      const double zP = (double)L0.x[id];
-      a.w[id] = wP;
-      gl += a.r[id] * zP;
-      dl += wP * zP;
+    v[0] = v[1] = v[2] = 0.0;
+    {
+      const double* r = a.r[cur];
+      for (long long id = gid; id < N; id += gs) {
+        int i, j, k;
+        bdecomp(a.A.m, id, i, j, k);
+        double wP, dtot;
+        box_row<double, T, false>(a.A.m, a.A.D, a.A.c, a.z0, id, i, j, k, wP, dtot);
+        const double zP = (double)a.z0[id];
+        a.w[id] = wP;
+        v[0] += r[id] * zP;
+        v[1] += wP * zP;
+      }
     }
-    v[0] = gl;
-    v[1] = dl;
-    if (!grid_sum3<double>(v, 2, phase++, a.part, a.bar, a.err)) { result = 3; break; }
+    if (!sync(v, 2)) { result = 3; break; }
     if (threadIdx.x == 0) {
       if (its == 0) {
         bc[0] = v[0] / v[1];
@@ -1211,6 +1428,7 @@ int Solver::setup(long long maxN, cudaStream_t s) {
     float** fa[] = {&fD, &fc[0], &fc[1], &fc[2], &fidg, &fr, &fz, &fp, &fAp, &fdx};
     for (auto q : fa) CK(cudaMalloc((void**)q, bf));
   }
+  if (persistent) CK(cudaMalloc(&mg_q2, sizeof(double) * (size_t)maxN));
   if (persistent)
     for (int q = 0; q < PERSIST_VECTORS; ++q) CK(cudaMalloc(&pw[q], (f32_helm ? sizeof(float) : sizeof(double)) * (size_t)maxN));
   return 0;
@@ -1223,7 +1441,8 @@ void Solver::release() {
     float** fa[] = {&fD, &fc[0], &fc[1], &fc[2], &fidg, &fr, &fz, &fp, &fAp, &fdx};
     for (auto q : fa) { cudaFree(*q); *q = nullptr; }
     for (int q = 0; q < PERSIST_VECTORS; ++q) { cudaFree(pw[q]); pw[q] = nullptr; }
-    cudaFree(bar); cudaFree(err);
+    cudaFree(bar); cudaFree(err); cudaFree(mg_q2);
+    mg_q2 = nullptr;
     bar = nullptr; err = nullptr;
   }
   cnt = nullptr;
@@ -1453,6 +1672,7 @@ static LevV<T> lv(const MGLevel& L) {
   v.x = (T*)L.x;
   v.b = (const T*)L.b;
   v.idg = (const T*)L.idg;
+  v.xp = (T*)L.xp;
   return v;
 }
 
@@ -1468,7 +1688,7 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
     MGLevel& L = lev[nlev];
     for (int a = 0; a < 3; ++a) L.m[a] = m[a];
     L.N = (long long)m[0] * m[1] * m[2];
-    total += (size_t)L.N * es * 7;
+    total += (size_t)L.N * es * 8;
     nlev++;
     bool can = (m[0] % 2 == 0 && m[1] % 2 == 0 && m[0] > 2 && m[1] > 2) && (!d3 || (m[2] % 2 == 0 && m[2] > 2));
     if (!can || nlev >= 24) break;
@@ -1477,7 +1697,7 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
   }
   cudaFree(mgbuf);
   mgbuf = nullptr;
-  CK(cudaMalloc(&mgbuf, total + 256 * 7 * nlev));
+  CK(cudaMalloc(&mgbuf, total + 256 * 8 * nlev));
   char* ptr = (char*)mgbuf;
   auto take = [&](long long n) { void* q = ptr; ptr += ((size_t)n * es + 255) / 256 * 256; return q; };
   for (int l = 0; l < nlev; ++l) {
@@ -1489,6 +1709,7 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
     L.x = take(L.N);
     L.b = take(L.N);
     L.idg = take(L.N);
+    L.xp = take(L.N);
   }
   // shared memory of the one-block tail of the V-cycle
   int lt = nlev - 1;
@@ -1506,7 +1727,7 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
     // the persistent MG-PCG: its own (smaller) tail; co-resident blocks at that size
     int ltp = nlev - 1;
     while (ltp > 0 && lev[ltp - 1].N <= PMG_TAIL_MAX_CELLS) --ltp;
-    const size_t psm = (size_t)tail_layout(lev, ltp, nlev, es, nullptr, nullptr) * es;
+    const size_t psm = pmg_smem_bytes((int)tail_layout(lev, ltp, nlev, es, nullptr, nullptr), es);
     int nsm = 0, per = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     // (dynamic limit: the opt-in maximum less the kernel's static shared memory)
@@ -1638,7 +1859,6 @@ int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* 
   constexpr bool f32 = sizeof(T) == 4;
   int rc = build_mg(s, f32);
   if (rc) return rc;
-  if (!f32) { lev[0].b = r; lev[0].x = z; }
   BoxV A = view(s);
   int nb = red_grid_cap(s.N, rb);
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
@@ -1647,24 +1867,26 @@ int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* 
   memset(&a, 0, sizeof(a));
   a.A = A;
   a.x = s.x;
-  a.r = r;
+  a.r[0] = r;
+  a.r[1] = z;
+  a.q[0] = Ap;
+  a.q[1] = mg_q2;
   a.p = p;
-  a.q = Ap;
   a.w = idg;
   for (int l = 0; l < nlev; ++l) a.TL.L[l] = lv<T>(lev[l]);
   int lt = nlev - 1;
   while (lt > 0 && lev[lt - 1].N <= PMG_TAIL_MAX_CELLS) --lt;
   a.nlev = nlev;
   a.lt = lt;
-  a.nu = 2;
   a.ncoarse = 4;
+  a.z0 = (lt > 0 && lev[0].m[2] == 1) ? (const T*)lev[0].xp : (const T*)lev[0].x;
   a.TL.total = (int)tail_layout(lev, lt, nlev, sizeof(T), a.TL.xo, a.TL.bo);
   a.part = part;
   a.stat = sc;
   a.done = done;
   a.bar = bar;
   a.err = err;
-  const size_t smem = (size_t)a.TL.total * sizeof(T);
+  const size_t smem = pmg_smem_bytes(a.TL.total, sizeof(T));
   int grid = (int)((s.N + PTPB - 1) / PTPB);
   if (grid > pmg_blocks) grid = pmg_blocks;
   if (grid > RED_BLOCKS) grid = RED_BLOCKS;
@@ -1682,16 +1904,16 @@ int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* 
   lc.numAttrs = 1;
   // algorithmic bytes per iteration: level-0 FP64 vectors (update: x, r, p, q, w in,
   // x, r, p, q out; w = A z: operator in, w out), the level-0 b and z in the hierarchy
-  // precision, the grid levels' sweeps and transfers as counted for the launched
-  // kernels, and the tail; FP64 flops: the update and w = A z, plus the sweeps of an
+  // precision, each grid level's operator, b and x once per smoothing side and the
+  // transfers, and the tail; FP64 flops: the update and w = A z, plus the sweeps of an
   // FP64 hierarchy
   const double d = s.c[2] ? 3.0 : 2.0, es = (double)sizeof(T), N0 = (double)s.N;
   double iter_b = (9.0 * 8.0 + 3.0 * es) * N0 + ((1.0 + d) * 8.0 + 16.0 + es) * N0;
   double iter_f = (10.0 + 4.0 * d) * N0;
   for (int l = 0; l < lt; ++l) {
     const double Nl = (double)lev[l].N, Nc = (double)lev[l + 1].N;
-    iter_b += 4.0 * a.nu * (2.5 + d) * Nl * es + ((3.0 + d) * Nl + Nc) * es + (2.0 * Nl + Nc) * es;
-    if (!f32) iter_f += 4.0 * a.nu * (1.0 + 2.0 * d) * 0.5 * Nl;
+    iter_b += 2.0 * (3.0 + d) * Nl * es + ((3.0 + d) * Nl + Nc) * es + (2.0 * Nl + Nc) * es;
+    if (!f32) iter_f += 4.0 * MG_NU * (1.0 + 2.0 * d) * 0.5 * Nl;
   }
   iter_b += 2.0 * lev[lt].N * es;
   for (int l = lt; l < nlev; ++l) iter_b += (2.0 + d) * lev[l].N * es;
