@@ -281,11 +281,12 @@ static int one_step(dctx* c, int* nc_flag) {
     }
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
-    cudaMemcpyAsync(c->bx, c->T, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    bs.x = c->T;   // solved in place: T is the initial guess and receives the solution
+    c->solver.record_next(c->scal, SC_ITS_T, -1, 0);
     rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
     if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
     c->solver.record(c->scal, SC_ITS_T, -1, 0);
-    cudaMemcpyAsync(c->T, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    bs.x = c->bx;
   }
   // S6 species
   ++g_launches, k_yeq<<<gc, TPB, 0, st>>>(g, p, c->T, c->alpha, c->omega, c->yq, c->flags);
@@ -297,11 +298,12 @@ static int one_step(dctx* c, int* nc_flag) {
     }
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
-    cudaMemcpyAsync(c->bx, c->omega, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    bs.x = c->omega;   // in place
+    c->solver.record_next(c->scal, SC_ITS_W, -1, 0);
     rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
     if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
     c->solver.record(c->scal, SC_ITS_W, -1, 0);
-    cudaMemcpyAsync(c->omega, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    bs.x = c->bx;
   } else {
     ++g_launches, k_species_noflow<<<gc, TPB, 0, st>>>(g, c->alpha, c->yq, c->omega);
   }
@@ -320,6 +322,7 @@ static int one_step(dctx* c, int* nc_flag) {
       for (int a = 0; a < 3; ++a) bs.m[a] = m[a];
       bs.N = nbx;
       L_faces_to_box(st, lin_grid(nbx), g, cc, c->u[cc], c->bx);
+      c->solver.record_next(c->scal, SC_ITS_U, -1, cc > 0);
       rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
       if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
       c->solver.record(c->scal, SC_ITS_U, -1, cc > 0);
@@ -332,11 +335,13 @@ static int one_step(dctx* c, int* nc_flag) {
                                            na == 3 ? c->bc[2] : c->bc[0], c->brhs);
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
-    cudaMemsetAsync(c->bx, 0, sizeof(double) * N, st);
+    bs.x = c->dp;   // pressure increment from a zero initial guess, solved in place
+    cudaMemsetAsync(c->dp, 0, sizeof(double) * N, st);
+    c->solver.record_next(c->scal, SC_ITS_P, SC_RES_P, 0);
     rc = c->solver.pcg_mg(bs, c->cfg.cg_rtol, c->cfg.cg_maxit, c->cfg.precision == 1, &ss);
     if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
     c->solver.record(c->scal, SC_ITS_P, SC_RES_P, 0);
-    cudaMemcpyAsync(c->dp, c->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+    bs.x = c->bx;
     for (int cc = 0; cc < na; ++cc)
       L_correct(st, lin_grid(nfaces(g, cc)), g, p, cc, c->us[cc], c->dp, c->rho, c->u[cc]);
     ++g_launches, k_add<<<gc, TPB, 0, st>>>(N, c->pr, c->dp);

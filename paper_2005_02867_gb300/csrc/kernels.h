@@ -116,6 +116,13 @@ void L_adj_tamb(cudaStream_t st, const Geo& g, const Phys& p, const double* T0ba
 // ---- linear solvers (solver.cu)
 // Box operator on dims m: y_P = D_P x_P + sum_a [c_a[P](x_P - x_{P-e_a}) + c_a[P+e_a](x_P - x_{P+e_a})],
 // the coupling of a pair stored at its high cell (c_a[P] = 0 when P_a = 0).
+// where the step keeps a solve's statistics (iterations, relative residual, the
+// not-converged flag); scal == nullptr: nowhere
+struct RecordSpec {
+  double* scal;
+  int its, res, acc;
+};
+
 struct BoxSys {
   int m[3];
   long long N;
@@ -156,6 +163,11 @@ class Solver {
   // store the last solve's iterations (slot_its, accumulated when accumulate = 1), relative
   // residual (slot_res, may be null) and a not-converged mark (scal[SC_NC]) on the device
   void record(double* scal, int slot_its, int slot_res, int accumulate);
+  // statistics slots of the next solve (set before it; a persistent solve writes them
+  // itself and the record() after it then launches nothing)
+  void record_next(double* scal, int slot_its, int slot_res, int accumulate) {
+    rec_scal = scal; rec_its = slot_its; rec_res = slot_res; rec_acc = accumulate;
+  }
   cudaStream_t stream = nullptr;
   cudaStream_t stream2 = nullptr;   // captures the bodies of the device-driven solver loops
   bool capturing = false;           // the step is being captured into a CUDA graph
@@ -172,6 +184,10 @@ class Solver {
   template <typename T>
   int pcg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out);
   int persist_blocks(bool f32);
+  RecordSpec take_record();
+  double* rec_scal = nullptr;
+  int rec_its = 0, rec_res = -1, rec_acc = 0;
+  bool recorded = false;
   template <typename T>
   int pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out);
   int pmg_blocks = 0;           // co-resident blocks of the persistent MG-PCG

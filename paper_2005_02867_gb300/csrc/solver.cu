@@ -394,21 +394,7 @@ __global__ void k_mx_finish(long long N, double* x, const float* dx) {
 constexpr long long BARRIER_SPIN_LIMIT = 1LL << 22;
 constexpr int PTPB = 512;   // threads per block of the persistent solver
 
-template <typename T>
-struct PersistArgs {
-  BoxV A;                   // FP64 operator (difference form)
-  const double* r64;        // FP64 defect r0 = b - A x0
-  double* x;                // FP64 solution, x += d at the end
-  T *ch[3];                 // c^ on the low face of each cell, per axis
-  T *dg, *sc;               // diag(A) and S = diag^(-1/2)
-  T *r[2], *s[2], *w[2];    // double-buffered r^, s = A^ p, w = A^ r^
-  T *p, *dx;                // search direction, x^
-  T* part;                  // 2 x 3 x blocks partial sums
-  double* stat;             // solver scalars (S_*)
-  int* done;
-  unsigned* bar;            // [0] arrivals (zero at launch)
-  int* err;
-};
+
 
 // Grid-wide sums of up to 3 values (nv = 0: a plain barrier) for a cooperative launch
 // of PTPB-thread blocks; `phase` counts the grid syncs of the launch (uniform), bar[0]
@@ -478,159 +464,213 @@ __device__ __forceinline__ bool grid_sum3(T (&v)[3], int nv, int phase, T* part_
   return r;
 }
 
+
+// End of a persistent solve: statistics (block 0), then the last block to leave
+// returns the barrier counters to zero for the next launch (no block can still be
+// waiting on them once every block has counted itself out).
+__device__ __forceinline__ void persist_finish(double* stat, int* done, const RecordSpec& rec, int its, double rr,
+                                               double bb, int result, unsigned* bar, int* err) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    stat[S_ITS] = (double)its;
+    stat[S_RR] = rr;
+    stat[S_BB] = bb;
+    const int d = result == 1 ? 1 : 2;
+    *done = d;
+    if (rec.scal) {
+      if (rec.acc) rec.scal[rec.its] += (double)its;
+      else rec.scal[rec.its] = (double)its;
+      if (rec.res >= 0) rec.scal[rec.res] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+      if (d != 1) rec.scal[SC_NC] = 1.0;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned e = atomicAdd(bar + 1, 1u);
+    if (e == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      atomicExch(bar + 1, 0u);
+      atomicExch(err, 0);
+      __threadfence();
+    }
+  }
+}
+
+template <typename T>
+struct PersistArgs {
+  BoxV A;                   // FP64 operator (difference form)
+  const double* b;          // FP64 right-hand side
+  double* x;                // FP64 initial guess in, solution out
+  double* r64;              // FP64 defect r0 = b - A x0 (scratch)
+  T *ch[3];                 // c^ on the low face of each cell, per axis
+  T *dg, *sc;               // diag(A) and S = diag^(-1/2)
+  T *r[2], *s[2], *w[2];    // double-buffered r^, s = A^ p, w = A^ r^
+  T *p, *dx;                // search direction, x^
+  T* part;                  // 2 x 3 x blocks partial sums
+  double* part64;           // FP64 partials of the initial norms
+  double tol2;              // rtol^2
+  int maxit;
+  double* stat;             // solver scalars (S_*)
+  int* done;
+  unsigned* bar;            // [0] arrivals, [1] departures (zero at launch)
+  int* err;
+  RecordSpec rec;
+};
+
 template <typename T>
 __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(PersistArgs<T> a) {
-  if (*a.done) return;                      // converged at the initial guess
-  __shared__ T bc[3];                       // broadcast: alpha, beta, state
+  __shared__ T bc[3];                       // broadcast: alpha, beta
+  __shared__ double sd[3];
   const int m0 = a.A.m[0], m1 = a.A.m[1], m2 = a.A.m[2];
   const int N = (int)a.A.N;                 // at most PERSIST_MAX_CELLS: 32-bit indices
   const int st1 = m0, st2 = m0 * m1;
   const bool has2 = a.A.c[2] != nullptr;
   const int gs = gridDim.x * blockDim.x;
   const int id0 = blockIdx.x * blockDim.x + threadIdx.x;
-  // per-solve scalars, formed once (FP64 work repeated by every thread is slow on GB300)
-  __shared__ double sd[3];
-  if (threadIdx.x == 0) {
-    const double rr0 = a.stat[S_RR];
-    sd[0] = sqrt(rr0);                                    // |r0| = 1 / nu
-    sd[1] = 1.0 / sd[0];                                  // nu
-    sd[2] = a.stat[S_TOL2] * a.stat[S_BB] / rr0;          // rtol^2 |b|^2 / |r0|^2
-  }
-  __syncthreads();
-  const double inv_nu = sd[0];
-  const T nu = (T)sd[1];
-  const T thr = (T)sd[2];
   int phase = 0;
-  // setup 1: diag, S, r^0 = nu S r0; s = p = x^ = 0
+  // phase 0: r0 = b - A x0 in FP64, diag, S = diag^(-1/2); |b|^2 and |r0|^2
+  double q64[3] = {0.0, 0.0, 0.0};
   for (int id = id0; id < N; id += gs) {
     int i, j, k;
     bdecomp(a.A.m, id, i, j, k);
-    double d = a.A.D[id];
-    if (i > 0) d += a.A.c[0][id];
-    if (i < m0 - 1) d += a.A.c[0][id + 1];
-    if (j > 0) d += a.A.c[1][id];
-    if (j < m1 - 1) d += a.A.c[1][id + st1];
-    if (has2) {
-      if (k > 0) d += a.A.c[2][id];
-      if (k < m2 - 1) d += a.A.c[2][id + st2];
-    }
+    double ax, d;
+    box_row<double, double, true>(a.A.m, a.A.D, a.A.c, a.x, id, i, j, k, ax, d);
+    const double bP = a.b[id], r0 = bP - ax;
+    a.r64[id] = r0;
     const T dT = (T)d;
-    const T sP = (T)1 / sqrt(dT);
     a.dg[id] = dT;
-    a.sc[id] = sP;
-    a.r[0][id] = nu * sP * (T)a.r64[id];
-    a.s[0][id] = 0;
-    a.p[id] = 0;
-    a.dx[id] = 0;
+    a.sc[id] = (T)1 / sqrt(dT);
+    q64[0] += bP * bP;
+    q64[1] += r0 * r0;
   }
-  T v[3] = {0, 0, 0};
-  bool ok = grid_sum3<T>(v, 0, phase++, a.part, a.bar, a.err);
-  // setup 2: c^ on the low faces, w = A^ r^0, gamma, delta, weighted |r^|^2
-  if (ok) {
-    const T* r = a.r[0];
-    T g = 0, dl = 0, q = 0;
-    for (int id = id0; id < N; id += gs) {
-      int i, j, k;
-      bdecomp(a.A.m, id, i, j, k);
-      const T sP = a.sc[id], rP = r[id];
-      T y = rP;
-      if (i > 0) {
-        const T c = (T)a.A.c[0][id] * sP * a.sc[id - 1];
-        a.ch[0][id] = c;
-        y -= c * r[id - 1];
-      } else {
-        a.ch[0][id] = 0;
-      }
-      if (i < m0 - 1) y -= (T)a.A.c[0][id + 1] * sP * a.sc[id + 1] * r[id + 1];
-      if (j > 0) {
-        const T c = (T)a.A.c[1][id] * sP * a.sc[id - st1];
-        a.ch[1][id] = c;
-        y -= c * r[id - st1];
-      } else {
-        a.ch[1][id] = 0;
-      }
-      if (j < m1 - 1) y -= (T)a.A.c[1][id + st1] * sP * a.sc[id + st1] * r[id + st1];
-      if (has2) {
-        if (k > 0) {
-          const T c = (T)a.A.c[2][id] * sP * a.sc[id - st2];
-          a.ch[2][id] = c;
-          y -= c * r[id - st2];
-        } else {
-          a.ch[2][id] = 0;
-        }
-        if (k < m2 - 1) y -= (T)a.A.c[2][id + st2] * sP * a.sc[id + st2] * r[id + st2];
-      }
-      a.w[0][id] = y;
-      g += rP * rP;
-      dl += y * rP;
-      q += a.dg[id] * rP * rP;
-    }
-    v[0] = g; v[1] = dl; v[2] = q;
-    ok = grid_sum3<T>(v, 3, phase++, a.part, a.bar, a.err);
-  }
-  const int maxit = (int)a.stat[S_MAXIT];
-  T gamma = v[0], alpha = v[0] / v[1], beta = 0, rho = v[2];
+  bool ok = grid_sum3<double>(q64, 2, phase++, a.part64, a.bar, a.err);
+  const double bb = q64[0], rr0 = q64[1];
   int its = 0, result = ok ? 2 : 3;
-  for (int cur = 0; ok && its < maxit; cur ^= 1) {
-    const T al = alpha, bt = beta;
-    const T *r = a.r[cur], *s = a.s[cur], *w = a.w[cur];
-    T *rn = a.r[cur ^ 1], *sn = a.s[cur ^ 1], *wn = a.w[cur ^ 1];
-    T g = 0, dl = 0, q = 0;
-    for (int id = id0; id < N; id += gs) {
-      int i, j, k;
-      bdecomp(a.A.m, id, i, j, k);
-      const T rP = r[id];
-      const T pP = rP + bt * a.p[id];       // p = r^ + beta p
-      const T sP = w[id] + bt * s[id];      // s = w + beta s
-      a.p[id] = pP;
-      a.dx[id] += al * pP;                  // x^ += alpha p
-      const T rN = rP - al * sP;            // r^ -= alpha s
-      // neighbours: clamped indices and zero couplings at the box edges, so that all
-      // loads issue together; r^_new of a neighbour from its r^, s, w
-      const int iw = i > 0 ? id - 1 : id, ie = i < m0 - 1 ? id + 1 : id;
-      const int is = j > 0 ? id - st1 : id, in = j < m1 - 1 ? id + st1 : id;
-      const T cw = a.ch[0][id], ce = i < m0 - 1 ? a.ch[0][ie] : (T)0;
-      const T cs = a.ch[1][id], cn = j < m1 - 1 ? a.ch[1][in] : (T)0;
-#define UNB(o) (r[o] - al * (w[o] + bt * s[o]))
-      T y = rN - (cw * UNB(iw) + ce * UNB(ie) + cs * UNB(is) + cn * UNB(in));
-      if (has2) {
-        const int ib = k > 0 ? id - st2 : id, it = k < m2 - 1 ? id + st2 : id;
-        const T cb = a.ch[2][id], ct = k < m2 - 1 ? a.ch[2][it] : (T)0;
-        y -= cb * UNB(ib) + ct * UNB(it);
-      }
-#undef UNB
-      rn[id] = rN;
-      sn[id] = sP;
-      wn[id] = y;
-      g += rN * rN;
-      dl += y * rN;
-      q += a.dg[id] * rN * rN;
-    }
-    v[0] = g; v[1] = dl; v[2] = q;
-    ok = grid_sum3<T>(v, 3, phase++, a.part, a.bar, a.err);
-    ++its;
-    if (!ok) { result = 3; break; }
+  double rr_out = rr0;
+  if (ok && (bb == 0.0 || rr0 <= a.tol2 * bb)) {
+    result = 1;                             // converged at the initial guess
+  } else if (ok) {
+    // per-solve scalars, formed once (FP64 work repeated by every thread is slow on GB300)
     if (threadIdx.x == 0) {
-      const T bn = v[0] / gamma;
-      bc[0] = v[0] / (v[1] - bn * v[0] / alpha);
-      bc[1] = bn;
+      sd[0] = sqrt(rr0);                    // |r0| = 1 / nu
+      sd[1] = 1.0 / sd[0];                  // nu
+      sd[2] = a.tol2 * bb / rr0;            // rtol^2 |b|^2 / |r0|^2
     }
-    rho = v[2];
-    if (v[2] <= thr) { result = 1; break; }
     __syncthreads();
-    alpha = bc[0];
-    beta = bc[1];
-    gamma = v[0];
-    __syncthreads();
+    const double inv_nu = sd[0];
+    const T nu = (T)sd[1];
+    const T thr = (T)sd[2];
+    // setup: r^0 = nu S r0 (the neighbours' formed on the fly), c^ on the low faces,
+    // w = A^ r^0, s = p = x^ = 0; gamma, delta, weighted |r^|^2
+    T v[3] = {0, 0, 0};
+    {
+      T g = 0, dl = 0, q = 0;
+#define RH(o) (nu * a.sc[o] * (T)a.r64[o])
+      for (int id = id0; id < N; id += gs) {
+        int i, j, k;
+        bdecomp(a.A.m, id, i, j, k);
+        const T sP = a.sc[id], rP = RH(id);
+        a.r[0][id] = rP;
+        a.s[0][id] = 0;
+        a.p[id] = 0;
+        a.dx[id] = 0;
+        T y = rP;
+        if (i > 0) {
+          const T c = (T)a.A.c[0][id] * sP * a.sc[id - 1];
+          a.ch[0][id] = c;
+          y -= c * RH(id - 1);
+        } else {
+          a.ch[0][id] = 0;
+        }
+        if (i < m0 - 1) y -= (T)a.A.c[0][id + 1] * sP * a.sc[id + 1] * RH(id + 1);
+        if (j > 0) {
+          const T c = (T)a.A.c[1][id] * sP * a.sc[id - st1];
+          a.ch[1][id] = c;
+          y -= c * RH(id - st1);
+        } else {
+          a.ch[1][id] = 0;
+        }
+        if (j < m1 - 1) y -= (T)a.A.c[1][id + st1] * sP * a.sc[id + st1] * RH(id + st1);
+        if (has2) {
+          if (k > 0) {
+            const T c = (T)a.A.c[2][id] * sP * a.sc[id - st2];
+            a.ch[2][id] = c;
+            y -= c * RH(id - st2);
+          } else {
+            a.ch[2][id] = 0;
+          }
+          if (k < m2 - 1) y -= (T)a.A.c[2][id + st2] * sP * a.sc[id + st2] * RH(id + st2);
+        }
+        a.w[0][id] = y;
+        g += rP * rP;
+        dl += y * rP;
+        q += a.dg[id] * rP * rP;
+      }
+#undef RH
+      v[0] = g; v[1] = dl; v[2] = q;
+      ok = grid_sum3<T>(v, 3, phase++, a.part, a.bar, a.err);
+    }
+    T gamma = v[0], alpha = v[0] / v[1], beta = 0, rho = v[2];
+    if (!ok) result = 3;
+    for (int cur = 0; ok && its < a.maxit; cur ^= 1) {
+      const T al = alpha, bt = beta;
+      const T *r = a.r[cur], *s = a.s[cur], *w = a.w[cur];
+      T *rn = a.r[cur ^ 1], *sn = a.s[cur ^ 1], *wn = a.w[cur ^ 1];
+      T g = 0, dl = 0, q = 0;
+      for (int id = id0; id < N; id += gs) {
+        int i, j, k;
+        bdecomp(a.A.m, id, i, j, k);
+        const T rP = r[id];
+        const T pP = rP + bt * a.p[id];       // p = r^ + beta p
+        const T sP = w[id] + bt * s[id];      // s = w + beta s
+        a.p[id] = pP;
+        a.dx[id] += al * pP;                  // x^ += alpha p
+        const T rN = rP - al * sP;            // r^ -= alpha s
+        // neighbours: clamped indices and zero couplings at the box edges, so that all
+        // loads issue together; r^_new of a neighbour from its r^, s, w
+        const int iw = i > 0 ? id - 1 : id, ie = i < m0 - 1 ? id + 1 : id;
+        const int is = j > 0 ? id - st1 : id, in = j < m1 - 1 ? id + st1 : id;
+        const T cw = a.ch[0][id], ce = i < m0 - 1 ? a.ch[0][ie] : (T)0;
+        const T cs = a.ch[1][id], cn = j < m1 - 1 ? a.ch[1][in] : (T)0;
+#define UNB(o) (r[o] - al * (w[o] + bt * s[o]))
+        T y = rN - (cw * UNB(iw) + ce * UNB(ie) + cs * UNB(is) + cn * UNB(in));
+        if (has2) {
+          const int ib = k > 0 ? id - st2 : id, it = k < m2 - 1 ? id + st2 : id;
+          const T cb = a.ch[2][id], ct = k < m2 - 1 ? a.ch[2][it] : (T)0;
+          y -= cb * UNB(ib) + ct * UNB(it);
+        }
+#undef UNB
+        rn[id] = rN;
+        sn[id] = sP;
+        wn[id] = y;
+        g += rN * rN;
+        dl += y * rN;
+        q += a.dg[id] * rN * rN;
+      }
+      v[0] = g; v[1] = dl; v[2] = q;
+      ok = grid_sum3<T>(v, 3, phase++, a.part, a.bar, a.err);
+      ++its;
+      if (!ok) { result = 3; break; }
+      if (threadIdx.x == 0) {
+        const T bn = v[0] / gamma;
+        bc[0] = v[0] / (v[1] - bn * v[0] / alpha);
+        bc[1] = bn;
+      }
+      rho = v[2];
+      if (v[2] <= thr) { result = 1; break; }
+      __syncthreads();
+      alpha = bc[0];
+      beta = bc[1];
+      gamma = v[0];
+      __syncthreads();
+    }
+    // x += S x^ / nu
+    for (int id = id0; id < N; id += gs) a.x[id] += (double)(a.sc[id] * a.dx[id]) * inv_nu;
+    rr_out = (double)rho * inv_nu * inv_nu;
   }
-  // x += S x^ / nu
-  for (int id = id0; id < N; id += gs) a.x[id] += (double)(a.sc[id] * a.dx[id]) * inv_nu;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.stat[S_ITS] = (double)its;
-    a.stat[S_RR] = (double)rho * inv_nu * inv_nu;
-    *a.done = result == 1 ? 1 : 2;
-  }
+  persist_finish(a.stat, a.done, a.rec, its, rr_out, bb, result, a.bar, a.err);
 }
+
 
 // condition of a solver WHILE node: run another iteration while not done
 __global__ void k_set_cond(cudaGraphConditionalHandle h, const int* done) {
@@ -688,6 +728,22 @@ __global__ void k_mg_smooth(LevV<T> L, int col, int first, const int* done) {
 }
 
 // inverse total diagonal of a level
+// 1 / (D + sum of adjacent couplings) of one cell, summed in FP64 over the level's values
+template <typename T>
+__device__ __forceinline__ T mg_idg_cell(const LevV<T>& L, long long id) {
+  int i, j, k;
+  bdecomp(L.m, id, i, j, k);
+  long long st[3] = {1, (long long)L.m[0], (long long)L.m[0] * L.m[1]};
+  int q[3] = {i, j, k};
+  double dt = (double)L.D[id];
+  for (int a = 0; a < 3; ++a) {
+    if (!L.c[a] || L.m[a] < 2) continue;
+    if (q[a] > 0) dt += (double)L.c[a][id];
+    if (q[a] < L.m[a] - 1) dt += (double)L.c[a][id + st[a]];
+  }
+  return (T)(1.0 / dt);
+}
+
 template <typename T>
 __global__ void k_mg_idg(LevV<T> L, T* idg) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -756,9 +812,19 @@ __global__ void k_mg_prolong(LevV<T> F, LevV<T> C, const int* done) {
 
 // coarse operator: couplings = 1/2 sum of the fine couplings across the coarse face, D = 1/2 sum
 template <typename T>
+__device__ __forceinline__ void mg_coarsen_cell(const LevV<T>& F, const LevV<T>& C, long long id, T* Dc, T* c0, T* c1,
+                                                T* c2);
+
+template <typename T>
 __global__ void k_mg_coarsen(LevV<T> F, LevV<T> C, T* Dc, T* c0, T* c1, T* c2) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= C.N) return;
+  mg_coarsen_cell<T>(F, C, id, Dc, c0, c1, c2);
+}
+
+template <typename T>
+__device__ __forceinline__ void mg_coarsen_cell(const LevV<T>& F, const LevV<T>& C, long long id, T* Dc, T* c0, T* c1,
+                                                T* c2) {
   int I, J, K;
   bdecomp(C.m, id, I, J, K);
   int kz = F.m[2] > 1 ? 2 : 1;
@@ -1128,7 +1194,12 @@ __device__ void tiled_post(const TileSmem<T>& S, const LevV<T>& F, const LevV<T>
 template <typename T>
 struct MgArgs {
   BoxV A;                      // FP64 pressure operator
-  double* x;                   // solution
+  const double* b;             // right-hand side
+  double tol2;                 // rtol^2
+  int maxit;
+  int cast0;                   // level 0 holds FP32 copies of the operator
+  RecordSpec rec;
+  double* x;                   // initial guess in, solution out
   double *r[2], *q[2];         // residual and q = A p, double buffered (tiles read neighbours')
   double *p, *w;               // direction, w = A z
   TailLevels<T> TL;            // hierarchy views and the tail's shared-memory layout
@@ -1190,7 +1261,6 @@ __device__ double tiled_phase_a(const TileSmem<T>& S, const MgArgs<T>& a, int cu
 
 template <typename T>
 __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
-  if (*a.done) return;                      // converged at the initial guess
   extern __shared__ __align__(16) unsigned char pmg_smem[];
   T* sm = reinterpret_cast<T*>(pmg_smem);
   TileSmem<T> S;
@@ -1207,12 +1277,61 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const LevV<T>& L0 = a.TL.L[0];
   const long long N = a.A.N;
-  const double thr = a.stat[S_TOL2] * a.stat[S_BB];
-  const int maxit = (int)a.stat[S_MAXIT], lt = a.lt;
-  double alpha = 0.0, beta = 0.0, gamma = 1.0, rr_last = a.stat[S_RR];
+  const int maxit = a.maxit, lt = a.lt;
   int phase = 0, its = 0, result = 2, cur = 0;
   auto sync = [&](double (&v)[3], int nv) { return grid_sum3<double>(v, nv, phase++, a.part, a.bar, a.err); };
-  for (;;) {
+  // phase H0: r0 = b - A x0 in FP64, |b|^2 and |r0|^2; the level-0 operator in the
+  // hierarchy precision and its 1 / diag
+  double h[3] = {0.0, 0.0, 0.0};
+  for (long long id = gid; id < N; id += gs) {
+    int i, j, k;
+    bdecomp(a.A.m, id, i, j, k);
+    double ax, dt;
+    box_row<double, double, false>(a.A.m, a.A.D, a.A.c, a.x, id, i, j, k, ax, dt);
+    const double bP = a.b[id], r0 = bP - ax;
+    a.r[0][id] = r0;
+    h[0] += bP * bP;
+    h[1] += r0 * r0;
+    if (a.cast0) {
+      ((T*)L0.D)[id] = (T)a.A.D[id];
+      for (int q = 0; q < 3; ++q)
+        if (a.A.c[q]) ((T*)L0.c[q])[id] = (T)a.A.c[q][id];
+    }
+    // 1 / diag from the values as the level holds them (FP32 copies or the FP64 box)
+    LevV<T> V = L0;
+    double dd = (double)(T)a.A.D[id];
+    {
+      long long st[3] = {1, (long long)V.m[0], (long long)V.m[0] * V.m[1]};
+      int qq[3] = {i, j, k};
+      for (int q = 0; q < 3; ++q) {
+        if (!a.A.c[q] || V.m[q] < 2) continue;
+        if (qq[q] > 0) dd += (double)(T)a.A.c[q][id];
+        if (qq[q] < V.m[q] - 1) dd += (double)(T)a.A.c[q][id + st[q]];
+      }
+    }
+    ((T*)L0.idg)[id] = (T)(1.0 / dd);
+  }
+  bool ok = sync(h, 2);
+  const double bb = h[0], thr = a.tol2 * bb;
+  double alpha = 0.0, beta = 0.0, gamma = 1.0, rr_last = h[1];
+  if (!ok) result = 3;
+  else if (bb == 0.0 || h[1] <= thr) result = 1;     // converged at the initial guess
+  // the coarse levels: level l coarsened from l - 1 together with 1 / diag of l - 1
+  for (int l = 1; ok && result != 1 && l <= a.nlev; ++l) {
+    if (l < a.nlev) {
+      const LevV<T>& F = a.TL.L[l - 1];
+      const LevV<T>& C = a.TL.L[l];
+      for (long long id = gid; id < C.N; id += gs)
+        mg_coarsen_cell<T>(F, C, id, (T*)C.D, (T*)C.c[0], (T*)C.c[1], (T*)C.c[2]);
+    }
+    if (l >= 2) {
+      const LevV<T>& P = a.TL.L[l - 1];
+      for (long long id = gid; id < P.N; id += gs) ((T*)P.idg)[id] = mg_idg_cell<T>(P, id);
+    }
+    if (l < a.nlev || l >= 2) ok = sync(h, 0);
+    if (!ok) result = 3;
+  }
+  for (; ok && result != 1;) {
     double v[3] = {0.0, 0.0, 0.0};
     const bool tiled0 = lt > 0 && L0.m[2] == 1;
     // phase A: CG update, level-0 right-hand side and the start of the pre-smoothing
@@ -1333,11 +1452,7 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
     __syncthreads();
     ++its;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    a.stat[S_ITS] = (double)its;
-    a.stat[S_RR] = rr_last;
-    *a.done = result == 1 ? 1 : 2;
-  }
+  persist_finish(a.stat, a.done, a.rec, its, rr_last, bb, result, a.bar, a.err);
 }
 
 template <typename TO, typename TI>
@@ -1477,7 +1592,19 @@ static void fill_stats(const double* hsc, int conv, SolveStats* out) {
 }
 
 void Solver::record(double* scal, int slot_its, int slot_res, int accumulate) {
+  rec_scal = nullptr;   // a launched solve does not consume the slots set for it
+  if (recorded) {       // the persistent solve wrote its statistics itself
+    recorded = false;
+    return;
+  }
   ++g_launches, k_record<<<1, 1, 0, stream>>>(sc, done, scal, slot_its, slot_res, accumulate);
+}
+
+RecordSpec Solver::take_record() {
+  RecordSpec r{rec_scal, rec_its, rec_res, rec_acc};
+  recorded = rec_scal != nullptr;
+  rec_scal = nullptr;
+  return r;
 }
 
 // Inside a stream capture: a conditional WHILE node whose body is one solver
@@ -1521,13 +1648,15 @@ int Solver::device_loop(F body) {
 template <typename T>
 int Solver::pcg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
   BoxV A = view(s);
-  int nb = red_grid_cap(s.N, rb);
-  ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
-  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, bar, err);
   PersistArgs<T> a;
+  memset(&a, 0, sizeof(a));
   a.A = A;
-  a.r64 = r;
+  a.b = s.b;
   a.x = s.x;
+  a.r64 = r;
+  a.tol2 = rtol * rtol;
+  a.maxit = maxit;
+  a.rec = take_record();
   constexpr bool f32 = sizeof(T) == 4;
   for (int q = 0; q < 3; ++q) a.ch[q] = (T*)pw[q];
   a.dg = (T*)pw[3];
@@ -1540,6 +1669,7 @@ int Solver::pcg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out
   a.p = (T*)pw[11];
   a.dx = (T*)pw[12];
   a.part = (T*)part;
+  a.part64 = part + 4 * RED_BLOCKS;   // beyond the 2 x 3 x grid values of precision T
   a.stat = sc;
   a.done = done;
   a.bar = bar;
@@ -1857,15 +1987,22 @@ void Solver::vcycle(int fp32) {
 template <typename T>
 int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
   constexpr bool f32 = sizeof(T) == 4;
-  int rc = build_mg(s, f32);
+  // the hierarchy is built inside the kernel; an FP64 hierarchy's level 0 is the box
+  int rc = prepare_mg(s.m, f32);
   if (rc) return rc;
+  if (!f32) {
+    lev[0].D = (void*)s.D;
+    for (int q = 0; q < 3; ++q) lev[0].c[q] = (void*)s.c[q];
+  }
   BoxV A = view(s);
-  int nb = red_grid_cap(s.N, rb);
-  ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
-  ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, bar, err);
   MgArgs<T> a;
   memset(&a, 0, sizeof(a));
   a.A = A;
+  a.b = s.b;
+  a.tol2 = rtol * rtol;
+  a.maxit = maxit;
+  a.cast0 = f32;
+  a.rec = take_record();
   a.x = s.x;
   a.r[0] = r;
   a.r[1] = z;
