@@ -283,46 +283,73 @@ __device__ inline double rho_gas(const Phys& p, double T, double Y) {
 
 // ------------------------------------------------------------------ reductions
 // Block-level sums of NV values, written to partials[v * gridDim.x + blockIdx.x].
+// GB300 retires about two FP64 operations per SM clock, so the values are transposed
+// through shared memory and value q is summed by warp q alone (blockDim.x / 32 adds
+// per lane and a five-step shuffle), instead of a shuffle tree in every warp.  Fixed
+// order: deterministic.  Blocks of at most TPB threads.
 template <int NV>
 __device__ inline void block_sum_store(double (&v)[NV], double* partials) {
-  __shared__ double sh[NV][TPB / 32];
+  __shared__ double sh[NV][TPB];
 #pragma unroll
-  for (int q = 0; q < NV; ++q)
-    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
+  for (int q = 0; q < NV; ++q) sh[q][threadIdx.x] = v[q];
   __syncthreads();
-  if (w == 0) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      double t = lane < (int)(blockDim.x >> 5) ? sh[q][lane] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-      if (lane == 0) partials[q * gridDim.x + blockIdx.x] = t;
-    }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  for (int q = w; q < NV; q += nw) {
+    double t = 0.0;
+    for (int u = 0; u < nw; ++u) t += sh[q][lane + 32 * u];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (lane == 0) partials[q * gridDim.x + blockIdx.x] = t;
   }
 }
 
 template <int NV>
 __device__ inline void block_max_store(double (&v)[NV], double* partials) {
-  __shared__ double sh[NV][TPB / 32];
+  __shared__ double sh[NV][TPB];
 #pragma unroll
-  for (int q = 0; q < NV; ++q)
-    for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_down_sync(0xffffffffu, v[q], o));
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < NV; ++q) sh[q][w] = v[q];
+  for (int q = 0; q < NV; ++q) sh[q][threadIdx.x] = v[q];
   __syncthreads();
-  if (w == 0) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  for (int q = w; q < NV; q += nw) {
+    double t = -1e300;
+    for (int u = 0; u < nw; ++u) t = fmax(t, sh[q][lane + 32 * u]);
+    for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+    if (lane == 0) partials[q * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Single-block sums (MAX = false) or maxima (MAX = true) of NV values from nblk
+// partials each (partials[q * nblk + b]): all loads issue together, each value is
+// finished by one warp through shared memory.  Result in thread 0.  Deterministic.
+template <int NV, bool MAX>
+__device__ inline void block_reduce_partials(const double* part, int nblk, double (&out)[NV]) {
+  __shared__ double sh[NV][TPB];
+  double t[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) t[q] = MAX ? -1e300 : 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double t = lane < (int)(blockDim.x >> 5) ? sh[q][lane] : -1e300;
-      for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
-      if (lane == 0) partials[q * gridDim.x + blockIdx.x] = t;
+      const double x = __ldcg(part + q * nblk + b);
+      t[q] = MAX ? fmax(t[q], x) : t[q] + x;
     }
+#pragma unroll
+  for (int q = 0; q < NV; ++q) sh[q][threadIdx.x] = t[q];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  for (int q = w; q < NV; q += nw) {
+    double r = MAX ? -1e300 : 0.0;
+    for (int u = 0; u < nw; ++u) r = MAX ? fmax(r, sh[q][lane + 32 * u]) : r + sh[q][lane + 32 * u];
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, r, o);
+      r = MAX ? fmax(r, y) : r + y;
+    }
+    __syncwarp();
+    if (lane == 0) sh[q][0] = r;
   }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) out[q] = sh[q][0];
+  __syncthreads();
 }
 
 // Single-block sum of nblk partials per value (fixed order: deterministic).

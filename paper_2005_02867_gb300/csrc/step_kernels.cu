@@ -862,8 +862,8 @@ __global__ void k_diag(Geo g, const double* alpha, const double* T, const double
 
 __global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal) {
   double v[6], m[3];
-  for (int q = 0; q < 6; ++q) { v[q] = block_sum_partials(psum + q * nblk, nblk); __syncthreads(); }
-  for (int q = 0; q < 3; ++q) { m[q] = block_max_partials(pmax + q * nblk, nblk); __syncthreads(); }
+  block_reduce_partials<6, false>(psum, nblk, v);
+  block_reduce_partials<3, true>(pmax, nblk, m);
   if (threadIdx.x == 0) {
     scal[SC_SUM_ALPHA_V] = v[0];
     scal[SC_SUM_MDOT_V] = v[1];
