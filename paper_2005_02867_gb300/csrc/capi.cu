@@ -8,6 +8,8 @@
 #include <cstring>
 #include <new>
 #include <vector>
+#include <algorithm>
+#include <cmath>
 #include "kernels.h"
 
 using namespace dg;
@@ -188,8 +190,9 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
       cudaMallocHost((void**)&c->hscal, sizeof(double) * SC_COUNT) != cudaSuccess ||
       cudaMallocHost((void**)&c->hflags, sizeof(unsigned)) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_NOMEM; }
   c->solver.f32_helm = c->cfg.precision == 1;
-  // one droplet of a latency-bound size: persistent solver; batches overlap their branches instead
-  c->solver.persistent = !own_stream && N <= Solver::PERSIST_MAX_CELLS;
+  // latency-bound sizes: persistent solvers (in a batch each droplet is later given an
+  // SM budget so that the cooperative solves of all branches fit the GPU together)
+  c->solver.persistent = N <= Solver::PERSIST_MAX_CELLS;
   c->solver.rb = c->rb;
   if ((rc = c->solver.setup(N, c->st))) { free_all(c); delete c; return rc; }
   c->solver.prof = &c->prof;
@@ -506,6 +509,33 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
     c->d.push_back(x);
   }
   if (batch) {
+    // SM budgets of the persistent solvers: proportional to the cells, at least one SM
+    // each, summing to at most the SM count, so that the cooperative solves of all
+    // droplets, running concurrently on the branches of the step graph, are co-resident
+    // at once; with more droplets than SMs the batch uses the launched solvers.
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    bool persist = n_droplets <= nsm;
+    for (auto x : c->d) persist = persist && x->solver.persistent;
+    if (persist) {
+      double tot = 0.0;
+      for (auto x : c->d) tot += (double)x->g.N;
+      std::vector<int> bud(n_droplets);
+      int sum = 0;
+      for (int i = 0; i < n_droplets; ++i) {
+        bud[i] = std::max(1, (int)std::floor(nsm * (double)c->d[i]->g.N / tot));
+        sum += bud[i];
+      }
+      while (sum > nsm) {   // trim the largest budgets
+        int k = (int)(std::max_element(bud.begin(), bud.end()) - bud.begin());
+        --bud[k];
+        --sum;
+      }
+      for (int i = 0; i < n_droplets; ++i) c->d[i]->solver.sm_budget = bud[i];
+    } else {
+      for (auto x : c->d) x->solver.persistent = false;
+    }
     c->ev.resize(n_droplets + 1);
     for (auto& e : c->ev)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { free_ctx(c); return DROPLET_ERR_CUDA; }

@@ -173,6 +173,7 @@ class Solver {
   bool capturing = false;           // the step is being captured into a CUDA graph
   bool f32_helm = false;            // Jacobi-PCG as FP32 defect correction (set before setup)
   bool persistent = false;          // Jacobi-PCG in one cooperative launch (set before setup)
+  int sm_budget = 0;                // SMs the persistent solves may use (0: the whole GPU)
   static constexpr long long PERSIST_MAX_CELLS = 1LL << 22;   // latency-bound sizes only
   int rb = RED_BLOCKS;              // block cap of the reduction kernels (tuned for batches)
   Prof* prof = nullptr;
@@ -191,6 +192,7 @@ class Solver {
   template <typename T>
   int pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out);
   int pmg_blocks = 0;           // co-resident blocks of the persistent MG-PCG
+  int nsm_ = 1;                 // SMs of the device
   double* mg_q2 = nullptr;      // second buffer of its q = A p
   float *fD = nullptr, *fc[3] = {nullptr, nullptr, nullptr}, *fidg = nullptr, *fr = nullptr, *fz = nullptr,
         *fp = nullptr, *fAp = nullptr, *fdx = nullptr;

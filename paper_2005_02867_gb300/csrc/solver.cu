@@ -7,6 +7,7 @@
 // host only reads the status every few iterations.
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include "kernels.h"
 
 namespace dg {
@@ -1676,6 +1677,7 @@ int Solver::pcg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out
   a.err = err;
   int grid = (int)((s.N + PTPB - 1) / PTPB);
   int cap = persist_blocks(f32);
+  if (sm_budget > 0) cap = std::min(cap, sm_budget * std::max(1, cap / nsm_));
   if (grid > cap) grid = cap;
   if (grid > RED_BLOCKS) grid = RED_BLOCKS;   // partials: 2 x 3 x grid values in part[0, 8 RED_BLOCKS)
   if (grid < 1) grid = 1;
@@ -1714,6 +1716,7 @@ int Solver::persist_blocks(bool f32) {
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  nsm_ = nsm;
   if (f32) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persist<float>, PTPB, 0);
   else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_persist<double>, PTPB, 0);
   cache = per * nsm;
@@ -1876,6 +1879,7 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mgpcg_persist<double>, PTPB, psm));
     }
     pmg_blocks = per * nsm;
+    nsm_ = nsm;
     if (pmg_blocks < 1) return DROPLET_ERR_SIZE;
   }
   mg_fp32 = fp32;
@@ -2026,6 +2030,7 @@ int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* 
   const size_t smem = pmg_smem_bytes(a.TL.total, sizeof(T));
   int grid = (int)((s.N + PTPB - 1) / PTPB);
   if (grid > pmg_blocks) grid = pmg_blocks;
+  if (sm_budget > 0) grid = std::min(grid, sm_budget * std::max(1, pmg_blocks / nsm_));
   if (grid > RED_BLOCKS) grid = RED_BLOCKS;
   if (grid < 1) grid = 1;
   cudaLaunchConfig_t lc;
