@@ -420,16 +420,23 @@ static void set_rb(droplet_ctx* c, int rb) {
   for (auto x : c->d) { x->rb = rb; x->solver.rb = rb; }
 }
 
-// Autotuner of the batch: the reduction kernels of every droplet run with at most rb blocks,
-// so that the branches of the batch graph share the SMs.  Each candidate is captured and
-// timed over a few steps on copies of the state; the fastest is kept and the state restored.
+// Autotuner.  (1) The tile shape of the persistent multigrid's temporal blocking (2D
+// hierarchies): larger tiles cut the halo overhead and the number of tiles a block runs
+// in turn, smaller ones spread a level over more blocks.  (2) For batches, the block cap
+// of the launched reduction kernels, so that the branches of the batch graph share the
+// SMs.  Each candidate is captured and timed over a few steps on copies of the state;
+// the fastest is kept and the state restored.
 static int autotune(droplet_ctx* c) {
-  const int cand[] = {RED_BLOCKS, 304, 152, 76, 38};
   // snapshot the state of every droplet
   std::vector<std::vector<double*>> snap(c->d.size());
+  auto fields = [](dctx* x, double* fs[8]) {
+    double* f[8] = {x->alpha, x->T, x->omega, x->pr, x->rhoG, x->u[0], x->u[1], x->u[2]};
+    for (int q = 0; q < 8; ++q) fs[q] = f[q];
+  };
   for (size_t i = 0; i < c->d.size(); ++i) {
     dctx* x = c->d[i];
-    double* fs[8] = {x->alpha, x->T, x->omega, x->pr, x->rhoG, x->u[0], x->u[1], x->u[2]};
+    double* fs[8];
+    fields(x, fs);
     for (int f = 0; f < 8; ++f) {
       if (!fs[f]) { snap[i].push_back(nullptr); continue; }
       long long n = f < 5 ? x->g.N : nfaces(x->g, f - 5);
@@ -442,25 +449,22 @@ static int autotune(droplet_ctx* c) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  int best_rb = RED_BLOCKS;
-  for (int rb : cand) {
-    set_rb(c, rb);
+  int rc = 0;
+  // time three graph steps of the current settings, then put the state back
+  auto trial = [&](float* ms) -> int {
     if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
-    int rc = capture_step(c);
-    if (rc) return rc;
+    int r = capture_step(c);
+    if (r) return r;
     CKR(cudaGraphLaunch(c->exec, c->st));   // warm-up
     CKR(cudaEventRecord(e0, c->st));
     for (int k = 0; k < 3; ++k) CKR(cudaGraphLaunch(c->exec, c->st));
     CKR(cudaEventRecord(e1, c->st));
     CKR(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) { best = ms; best_rb = rb; }
-    // restore the state
+    cudaEventElapsedTime(ms, e0, e1);
     for (size_t i = 0; i < c->d.size(); ++i) {
       dctx* x = c->d[i];
-      double* fs[8] = {x->alpha, x->T, x->omega, x->pr, x->rhoG, x->u[0], x->u[1], x->u[2]};
+      double* fs[8];
+      fields(x, fs);
       for (int f = 0; f < 8; ++f) {
         if (!fs[f]) continue;
         long long n = f < 5 ? x->g.N : nfaces(x->g, f - 5);
@@ -473,11 +477,40 @@ static int autotune(droplet_ctx* c) {
       cudaMemsetAsync(x->dirty, 0xff, sizeof(int), c->st);
     }
     CKR(cudaStreamSynchronize(c->st));
+    return 0;
+  };
+  bool tiles = false;
+  for (auto x : c->d)
+    tiles = tiles || (x->solver.persistent && (x->cfg.physics_mask & DROPLET_PHYS_FLOW) && x->g.n[2] == 1);
+  if (tiles) {
+    const int cand[][2] = {{32, 32}, {64, 32}, {64, 64}, {128, 32}};
+    float best = 1e30f;
+    int bt = 0;
+    for (int k = 0; k < 4 && !rc; ++k) {
+      for (auto x : c->d) { x->solver.mg_tile[0] = cand[k][0]; x->solver.mg_tile[1] = cand[k][1]; }
+      float ms = 0.f;
+      rc = trial(&ms);
+      if (!rc && ms < best) { best = ms; bt = k; }
+    }
+    for (auto x : c->d) { x->solver.mg_tile[0] = cand[bt][0]; x->solver.mg_tile[1] = cand[bt][1]; }
+  }
+  if (c->d.size() > 1 && !rc) {
+    const int cand[] = {RED_BLOCKS, 304, 152, 76, 38};
+    float best = 1e30f;
+    int best_rb = RED_BLOCKS;
+    for (int rb : cand) {
+      set_rb(c, rb);
+      float ms = 0.f;
+      rc = trial(&ms);
+      if (rc) break;
+      if (ms < best) { best = ms; best_rb = rb; }
+    }
+    set_rb(c, best_rb);
   }
   for (auto& v : snap) for (auto q : v) cudaFree(q);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  set_rb(c, best_rb);
+  if (rc) return rc;
   if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
   for (auto x : c->d) if (run_diag(x)) return DROPLET_ERR_CUDA;
   CKR(cudaStreamSynchronize(c->st));
@@ -539,6 +572,11 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
     c->ev.resize(n_droplets + 1);
     for (auto& e : c->ev)
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { free_ctx(c); return DROPLET_ERR_CUDA; }
+  }
+  // batches, and single 2D droplets with flow large enough for the tile shape to matter
+  const dctx* x0 = c->d[0];
+  if (batch || (x0->solver.persistent && (x0->cfg.physics_mask & DROPLET_PHYS_FLOW) && x0->g.n[2] == 1 &&
+                x0->g.N >= 32768)) {
     int rc = autotune(c);
     if (rc) { free_ctx(c); return rc; }
   }

@@ -174,6 +174,8 @@ class Solver {
   bool f32_helm = false;            // Jacobi-PCG as FP32 defect correction (set before setup)
   bool persistent = false;          // Jacobi-PCG in one cooperative launch (set before setup)
   int sm_budget = 0;                // SMs the persistent solves may use (0: the whole GPU)
+  int mg_tile[2] = {32, 32};        // tile of the persistent MG's temporal blocking (autotuned)
+  size_t pmg_smem_max = 0;          // dynamic shared memory the persistent MG may request
   static constexpr long long PERSIST_MAX_CELLS = 1LL << 22;   // latency-bound sizes only
   int rb = RED_BLOCKS;              // block cap of the reduction kernels (tuned for batches)
   Prof* prof = nullptr;

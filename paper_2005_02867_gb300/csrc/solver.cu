@@ -1058,20 +1058,23 @@ __device__ __forceinline__ void grid_prolong_black(const LevV<T>& F, const LevV<
   }
 }
 
-// Temporal blocking of the smoothing on 2D levels: each block takes a TLX x TLY tile,
+// Temporal blocking of the smoothing on 2D levels: each block takes a tx x ty tile,
 // loads it with THALO rings into shared memory and runs all 2 nu half sweeps there.
 // Half sweep s updates the cells within THALO - s rings of the tile (clipped to the
 // level), which read only cells updated by half sweep s - 1, so the tile's cells end
 // with exactly the values of the level-wide sweeps (same arithmetic, same order) and a
 // whole pre- or post-smoothing costs one grid barrier instead of 2 nu.
 constexpr int MG_NU = 2;                       // red-black sweeps before and after
-constexpr int TLX = 32, TLY = 32;              // owned tile
 constexpr int THALO = 2 * MG_NU;               // rings: one per half sweep
-constexpr int TRX = TLX + 2 * THALO, TRY = TLY + 2 * THALO;
-constexpr int TREG = TRX * TRY;                // cells of a tile region
+
+// cells of the region of a tx x ty tile (the tile shape is a launch parameter, chosen
+// by the autotuner)
+__host__ __device__ constexpr int tile_region(int tx, int ty) { return (tx + 2 * THALO) * (ty + 2 * THALO); }
 
 // dynamic shared memory of the persistent MG-PCG: the tail, then five tile arrays
-static size_t pmg_smem_bytes(int tail_elems, size_t es) { return ((size_t)(tail_elems + 3) / 4 * 4 + 5 * (size_t)TREG) * es; }
+static size_t pmg_smem_bytes(int tail_elems, size_t es, int tx, int ty) {
+  return ((size_t)(tail_elems + 3) / 4 * 4 + 5 * (size_t)tile_region(tx, ty)) * es;
+}
 
 template <typename T>
 struct TileSmem {
@@ -1083,14 +1086,14 @@ struct TileBox {
   int i0, j0, rx, ry;       // region origin and extent (owned + THALO rings, clipped)
 };
 
-__device__ __forceinline__ TileBox tile_box(int m0, int m1, int t) {
-  const int ntx = (m0 + TLX - 1) / TLX;
+__device__ __forceinline__ TileBox tile_box(int m0, int m1, int t, int TX, int TY) {
+  const int ntx = (m0 + TX - 1) / TX;
   const int ty = t / ntx, tx = t - ty * ntx;
   TileBox B;
-  B.oi0 = tx * TLX;
-  B.oi1 = min(B.oi0 + TLX, m0);
-  B.oj0 = ty * TLY;
-  B.oj1 = min(B.oj0 + TLY, m1);
+  B.oi0 = tx * TX;
+  B.oi1 = min(B.oi0 + TX, m0);
+  B.oj0 = ty * TY;
+  B.oj1 = min(B.oj0 + TY, m1);
   B.i0 = max(B.oi0 - THALO, 0);
   B.j0 = max(B.oj0 - THALO, 0);
   B.rx = min(B.oi1 + THALO, m0) - B.i0;
@@ -1098,7 +1101,9 @@ __device__ __forceinline__ TileBox tile_box(int m0, int m1, int t) {
   return B;
 }
 
-__device__ __forceinline__ int tile_count(int m0, int m1) { return ((m0 + TLX - 1) / TLX) * ((m1 + TLY - 1) / TLY); }
+__device__ __forceinline__ int tile_count(int m0, int m1, int TX, int TY) {
+  return ((m0 + TX - 1) / TX) * ((m1 + TY - 1) / TY);
+}
 
 // the 2 nu half sweeps of a loaded tile; pre: red (from b alone), black, red, black;
 // post: black, red, black, red (gs_cell's arithmetic)
@@ -1150,10 +1155,10 @@ __device__ __forceinline__ void tile_store_x(const TileSmem<T>& S, const TileBox
 
 // pre-smoothing of a 2D level l >= 1 (b from the restriction), tile by tile
 template <typename T>
-__device__ void tiled_pre(const TileSmem<T>& S, const LevV<T>& F) {
+__device__ void tiled_pre(const TileSmem<T>& S, const LevV<T>& F, int TX, int TY) {
   const int m0 = F.m[0], m1 = F.m[1];
-  for (int t = blockIdx.x; t < tile_count(m0, m1); t += gridDim.x) {
-    const TileBox B = tile_box(m0, m1, t);
+  for (int t = blockIdx.x; t < tile_count(m0, m1, TX, TY); t += gridDim.x) {
+    const TileBox B = tile_box(m0, m1, t, TX, TY);
     const int n = B.rx * B.ry;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
       const int lj = c / B.rx;
@@ -1172,10 +1177,10 @@ __device__ void tiled_pre(const TileSmem<T>& S, const LevV<T>& F) {
 // F.x and the coarse level's final iterate cx, writes F.xp (tiles of other blocks
 // still read F.x in their halos during the phase)
 template <typename T>
-__device__ void tiled_post(const TileSmem<T>& S, const LevV<T>& F, const LevV<T>& C, const T* cx) {
+__device__ void tiled_post(const TileSmem<T>& S, const LevV<T>& F, const LevV<T>& C, const T* cx, int TX, int TY) {
   const int m0 = F.m[0], m1 = F.m[1];
-  for (int t = blockIdx.x; t < tile_count(m0, m1); t += gridDim.x) {
-    const TileBox B = tile_box(m0, m1, t);
+  for (int t = blockIdx.x; t < tile_count(m0, m1, TX, TY); t += gridDim.x) {
+    const TileBox B = tile_box(m0, m1, t, TX, TY);
     const int n = B.rx * B.ry;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
       const int lj = c / B.rx;
@@ -1205,6 +1210,7 @@ struct MgArgs {
   double *p, *w;               // direction, w = A z
   TailLevels<T> TL;            // hierarchy views and the tail's shared-memory layout
   const T* z0;                 // level-0 iterate at the end of a V-cycle (z = M r)
+  int tx, ty;                  // tile shape of the temporal blocking
   int nlev, lt, ncoarse;       // levels, first tail level, coarsest-level sweeps
   double* part;
   double* stat;
@@ -1225,8 +1231,9 @@ __device__ double tiled_phase_a(const TileSmem<T>& S, const MgArgs<T>& a, int cu
   const double *r = a.r[cur], *q = a.q[cur];
   double *rn = a.r[cur ^ 1], *qn = a.q[cur ^ 1];
   double rr = 0.0;
-  for (int t = blockIdx.x; t < tile_count(m0, m1); t += gridDim.x) {
-    const TileBox B = tile_box(m0, m1, t);
+  const int TX = a.tx, TY = a.ty;
+  for (int t = blockIdx.x; t < tile_count(m0, m1, TX, TY); t += gridDim.x) {
+    const TileBox B = tile_box(m0, m1, t, TX, TY);
     const int n = B.rx * B.ry;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
       const int lj = c / B.rx;
@@ -1267,11 +1274,12 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
   TileSmem<T> S;
   {
     T* tb = sm + (a.TL.total + 3) / 4 * 4;
+    const int treg = tile_region(a.tx, a.ty);
     S.x = tb;
-    S.b = tb + TREG;
-    S.idg = tb + 2 * TREG;
-    S.c0 = tb + 3 * TREG;
-    S.c1 = tb + 4 * TREG;
+    S.b = tb + treg;
+    S.idg = tb + 2 * treg;
+    S.c0 = tb + 3 * treg;
+    S.c1 = tb + 4 * treg;
   }
   __shared__ double bc[2];
   const int gs = gridDim.x * blockDim.x;
@@ -1391,7 +1399,7 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
       grid_restrict<T>(F, C, l + 1 < lt && !ctl, gid, gs);
       ok = sync(v, 0);
       if (ok && ctl) {
-        tiled_pre<T>(S, C);
+        tiled_pre<T>(S, C, a.tx, a.ty);
         ok = sync(v, 0);
       }
     }
@@ -1404,7 +1412,7 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
       const LevV<T>& F = a.TL.L[l];
       if (F.m[2] == 1) {
         const LevV<T>& C = a.TL.L[l + 1];
-        tiled_post<T>(S, F, C, l + 1 < lt ? C.xp : C.x);
+        tiled_post<T>(S, F, C, l + 1 < lt ? C.xp : C.x, a.tx, a.ty);
         ok = sync(v, 0);
         continue;
       }
@@ -1860,7 +1868,7 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
     // the persistent MG-PCG: its own (smaller) tail; co-resident blocks at that size
     int ltp = nlev - 1;
     while (ltp > 0 && lev[ltp - 1].N <= PMG_TAIL_MAX_CELLS) --ltp;
-    const size_t psm = pmg_smem_bytes((int)tail_layout(lev, ltp, nlev, es, nullptr, nullptr), es);
+    const size_t psm = pmg_smem_bytes((int)tail_layout(lev, ltp, nlev, es, nullptr, nullptr), es, 32, 32);
     int nsm = 0, per = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     // (dynamic limit: the opt-in maximum less the kernel's static shared memory)
@@ -1870,12 +1878,14 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
       if (psm + fa.sharedSizeBytes > (size_t)optin) return DROPLET_ERR_SIZE;
       CK(cudaFuncSetAttribute(k_mgpcg_persist<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               optin - (int)fa.sharedSizeBytes));
+      pmg_smem_max = (size_t)(optin - (int)fa.sharedSizeBytes);
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mgpcg_persist<float>, PTPB, psm));
     } else {
       CK(cudaFuncGetAttributes(&fa, k_mgpcg_persist<double>));
       if (psm + fa.sharedSizeBytes > (size_t)optin) return DROPLET_ERR_SIZE;
       CK(cudaFuncSetAttribute(k_mgpcg_persist<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               optin - (int)fa.sharedSizeBytes));
+      pmg_smem_max = (size_t)(optin - (int)fa.sharedSizeBytes);
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mgpcg_persist<double>, PTPB, psm));
     }
     pmg_blocks = per * nsm;
@@ -2027,7 +2037,13 @@ int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* 
   a.done = done;
   a.bar = bar;
   a.err = err;
-  const size_t smem = pmg_smem_bytes(a.TL.total, sizeof(T));
+  a.tx = mg_tile[0];
+  a.ty = mg_tile[1];
+  size_t smem = pmg_smem_bytes(a.TL.total, sizeof(T), a.tx, a.ty);
+  if (smem > pmg_smem_max) {   // the chosen tile does not fit: the default one does
+    a.tx = a.ty = 32;
+    smem = pmg_smem_bytes(a.TL.total, sizeof(T), a.tx, a.ty);
+  }
   int grid = (int)((s.N + PTPB - 1) / PTPB);
   if (grid > pmg_blocks) grid = pmg_blocks;
   if (sm_budget > 0) grid = std::min(grid, sm_budget * std::max(1, pmg_blocks / nsm_));
