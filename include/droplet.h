@@ -216,7 +216,14 @@ int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0,
  *   4 MG_PROLONG  injection prolongation               [(2 + 1/2^d) N w; FP64: N flops]
  *   5 MOM_ASSEMBLE momentum system assembly            [(12 + 2d) N 8]
  *   6 SCALAR_ASSEMBLE energy / species assembly        [(12 + 2d) N 8]
- * (w = 8 for FP64 launches, 4 for FP32 ones.)                                     */
+ * (w = 8 for FP64 launches, 4 for FP32 ones.)
+ * Single droplets of at most 2^22 cells, and the droplets of a batch, solve with
+ * persistent kernels: class 0 then times the whole multigrid-preconditioned CG of
+ * the pressure (one launch per solve; bytes: per iteration the level-0 FP64 CG
+ * vectors, each grid level's operator, b and x once per smoothing side, the
+ * transfers and the coarse tail, times the iterations) and class 1 the whole
+ * Jacobi-preconditioned CG of a Helmholtz system (one launch; bytes: the setup and
+ * (11 + d) N w per iteration); classes 2 - 4 then stay empty.                     */
 #define DROPLET_KCLASS_COUNT 7
 
 /* Start (enable = 1) or stop (0) timing every launch of the kernel classes above
@@ -264,6 +271,15 @@ int droplet_adjoint(droplet_ctx* ctx, int n_steps, int ckpt_every, double* J, do
  * those of the saved run.  File errors: DROPLET_ERR_IO. */
 int droplet_save(droplet_ctx* ctx, const char* path);
 int droplet_load(droplet_ctx* ctx, const char* path);
+
+/* Round n doubles (host array `in`) to binary32 on the device with the integer-pipe
+ * conversion the mixed-precision (precision 1) assembly kernels use, and widen the
+ * results back to binary64 with their exact integer-pipe widening: out32[i] and
+ * back64[i] (host arrays).  The paper has no counterpart: the entry point exists so
+ * that the conversion can be checked against IEEE 754 round-to-nearest-even.  Runs
+ * on the current device and synchronises.  Errors: DROPLET_ERR_ARG (a NULL array or
+ * n > 2^30), DROPLET_ERR_NOMEM, DROPLET_ERR_CUDA. */
+int droplet_round_f32(const double* in, float* out32, double* back64, size_t n);
 
 /* Block until all work enqueued by the context has finished. */
 int droplet_sync(droplet_ctx* ctx);

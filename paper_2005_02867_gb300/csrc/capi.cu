@@ -279,8 +279,9 @@ static int one_step(dctx* c, int* nc_flag) {
   if ((mask & DROPLET_PHYS_ENERGY) && !p.const_props) {
     {
     ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
-    L_scalar_assemble(st, gc, g, p, 0, c->T, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2,
-                                          c->alpha, c->yq, p.T_amb, c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+    (c->cfg.precision == 1 ? L_scalar_assemble_mx : L_scalar_assemble)(
+        st, gc, g, p, 0, c->T, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2, c->alpha, c->yq, p.T_amb,
+        c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
     }
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
@@ -296,8 +297,9 @@ static int one_step(dctx* c, int* nc_flag) {
   if (mask & DROPLET_PHYS_SPECIES) {
     {
     ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
-    L_scalar_assemble(st, gc, g, p, 1, c->omega, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2,
-                                          c->alpha, c->yq, 0.0, c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+    (c->cfg.precision == 1 ? L_scalar_assemble_mx : L_scalar_assemble)(
+        st, gc, g, p, 1, c->omega, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2, c->alpha, c->yq, 0.0,
+        c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
     }
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
@@ -319,8 +321,9 @@ static int one_step(dctx* c, int* nc_flag) {
       long long nbx = (long long)m[0] * m[1] * m[2];
       {
       ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, st, (12.0 + 2 * na) * nbx * 8.0);
-      L_mom_assemble(st, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi,
-                                                    c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+      (c->cfg.precision == 1 ? L_mom_assemble_mx : L_mom_assemble)(
+          st, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi, c->bD, c->bc[0],
+          c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
       }
       for (int a = 0; a < 3; ++a) bs.m[a] = m[a];
       bs.N = nbx;

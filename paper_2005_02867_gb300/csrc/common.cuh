@@ -171,6 +171,37 @@ __device__ __forceinline__ double cellc(const Geo& g, const double* f, int i, in
   return f[cidx(g, i, j, k)];
 }
 
+// ------------------------------------------------------------------ FP64 <-> FP32 on the integer pipe
+// On GB300 the hardware conversions issue on the FP64 pipe (about two per SM clock), so
+// the mixed-precision kernels convert with integer operations instead.  Binary64 to
+// binary32, round to nearest even (IEEE 754), written out for results in the normal
+// binary32 range; zeros keep their sign; every other input (results that would be
+// subnormal or overflow, infinities, NaN) takes the hardware conversion.
+__device__ __forceinline__ float f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned e = (hi >> 20) & 0x7FFu;                       // biased binary64 exponent
+  if (e - 897u <= 253u) {                                       // binary32 exponent 1 .. 254
+    unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);           // leading 23 fraction bits
+    const unsigned rest = lo & 0x1FFFFFFFu, half = 0x10000000u;  // the 29 dropped bits
+    m += (rest > half) | ((rest == half) & (m & 1u));           // ties to even
+    return __uint_as_float((hi & 0x80000000u) | (((e - 896u) << 23) + m));   // a carry bumps the exponent
+  }
+  if ((b << 1) == 0ull) return __uint_as_float(hi & 0x80000000u);
+  return (float)x;
+}
+// binary32 to binary64 (exact) for normal numbers and zeros
+__device__ __forceinline__ double f64_of(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xFFu;
+  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e - 1u < 254u)
+    return __longlong_as_double((long long)(s | ((unsigned long long)(e + 896u) << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+  if ((u << 1) == 0u) return __longlong_as_double((long long)s);
+  return (double)x;
+}
+
 // ------------------------------------------------------------------ small formulas
 __device__ __forceinline__ double minmod(double x, double y) {
   return (x * y > 0.0) ? (x > 0.0 ? fmin(fabs(x), fabs(y)) : -fmin(fabs(x), fabs(y))) : 0.0;
@@ -219,6 +250,22 @@ __device__ inline double cubic_largest(double c2, double c1, double c0) {
     t = m * cos(acos(arg) / 3.0);
   }
   return t - c2 / 3.0;
+}
+
+// binary (fuel, inert) Peng-Robinson compressibility alone (the vapour root), for the
+// gas density: the same arithmetic as pr_binary's Z without the fugacity terms
+__device__ inline double pr_binary_Z(const Phys& p, double T, double P, double y) {
+  double a0, b0, a1, b1;
+  pr_pure(T, p.Tc, p.Pc, p.om, a0, b0);
+  pr_pure(T, p.Tc_g, p.Pc_g, p.om_g, a1, b1);
+  double a01 = sqrt(a0 * a1) * (1.0 - p.kij);
+  double y1 = 1.0 - y;
+  double am = y * y * a0 + y * y1 * a01 + y1 * y * a01 + y1 * y1 * a1;
+  double bm = y * b0 + y1 * b1;
+  double RT = R_GAS * T;
+  double A = am * P / (RT * RT);
+  double B = bm * P / RT;
+  return cubic_largest(-(1.0 - B), A - 3.0 * B * B - 2.0 * B, -(A * B - B * B - B * B * B));
 }
 
 // binary (fuel, inert) Peng-Robinson: vapour Z and ln phi_hat of the fuel at mole fraction y
@@ -274,10 +321,7 @@ __device__ inline double rho_gas(const Phys& p, double T, double Y) {
   if (p.const_props) return p.rhoG_const;
   double inv_m = Y / p.M_l + (1.0 - Y) / p.M_g;
   double Z = 1.0;
-  if (p.eq_model != 0) {
-    double l0;
-    pr_binary(p, T, p.P, y_from_Y(p, Y), Z, l0);
-  }
+  if (p.eq_model != 0) Z = pr_binary_Z(p, T, p.P, y_from_Y(p, Y));
   return p.P / (Z * R_GAS * T * inv_m);
 }
 
