@@ -40,6 +40,9 @@ WORKLOADS = {
     "cfg3_cart3d_256": lambda: W.cfg3_cart3d(),
     "cfg3_cart3d_256_fp64": lambda: W.cfg3_cart3d(precision=0),
     "cfg3_cart3d_128_fp64": lambda: W.cfg3_cart3d(nc=128, precision=0),
+    # the 3D launched path (more than 2^22 cells) at ~2.5 GB on the device: the size of
+    # the full ncu captures of its kernels
+    "cfg3_cart3d_176": lambda: W.cfg3_cart3d(nc=176),
     "cfg4_batch64": lambda: W.cfg4_batch(),
     "cfg4_batch64_fp64": lambda: [dict(c, precision=0) for c in W.cfg4_batch()],
     "cfg4_serial64_fp64": lambda: [dict(c, precision=0) for c in W.cfg4_batch()],

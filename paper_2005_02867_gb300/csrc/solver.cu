@@ -877,17 +877,79 @@ static long long tail_layout(const MGLevel* lev, int l0, int nl, size_t es, int*
 }
 
 // one red-black half sweep over the cells of colour `col` only (half rows)
-template <typename T>
+// the threads that run the tail: the whole block
+struct TailBlock {
+  __device__ static int tid() { return threadIdx.x; }
+  __device__ static int n() { return blockDim.x; }
+  __device__ static void sync() { __syncthreads(); }
+};
+
+// one red-black half sweep over the cells of colour `col` only (half rows)
+template <typename T, class G = TailBlock>
 __device__ void tail_smooth(const LevV<T>& L, int col, int first) {
   const int m0 = L.m[0], m1 = L.m[1], h = (m0 + 1) >> 1;
   const int n = h * m1 * L.m[2];
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+  for (int t = G::tid(); t < n; t += G::n()) {
     const int row = t / h, q = t - row * h;
     const int k = row / m1, j = row - k * m1;
     const int i = 2 * q + ((j + k + col) & 1);
     if (i < m0) gs_cell<T>(L, (long long)i + (long long)m0 * row, i, j, k, first);
   }
-  __syncthreads();
+  G::sync();
+}
+
+// pre-smoothing of F and the restriction of its residual into C.b
+template <typename T, class G>
+__device__ void tail_down(const LevV<T>& F, const LevV<T>& C, int nu) {
+  for (int s = 0; s < nu; ++s) {
+    tail_smooth<T, G>(F, 0, s == 0);
+    tail_smooth<T, G>(F, 1, 0);
+  }
+  const int kz = F.m[2] > 1 ? 2 : 1;
+  for (long long id = G::tid(); id < C.N; id += G::n()) {
+    int I, J, K;
+    bdecomp(C.m, id, I, J, K);
+    T s = 0;
+    for (int dk = 0; dk < kz; ++dk)
+      for (int dj = 0; dj < 2; ++dj)
+        for (int di = 0; di < 2; ++di) {
+          int i = 2 * I + di, j = 2 * J + dj, k = kz == 2 ? 2 * K + dk : 0;
+          long long fi = (long long)i + (long long)F.m[0] * ((long long)j + (long long)F.m[1] * k);
+          s += mg_resid<T>(F, fi, i, j, k);
+        }
+    ((T*)C.b)[id] = s;
+  }
+  G::sync();
+}
+
+// the coarsest level: ncoarse symmetric sweep pairs
+template <typename T, class G>
+__device__ void tail_coarsest(const LevV<T>& L, int ncoarse) {
+  for (int s = 0; s < ncoarse; ++s) {
+    tail_smooth<T, G>(L, 0, s == 0);
+    tail_smooth<T, G>(L, 1, 0);
+  }
+  for (int s = 0; s < ncoarse; ++s) {
+    tail_smooth<T, G>(L, 1, 0);
+    tail_smooth<T, G>(L, 0, 0);
+  }
+}
+
+// prolongation F.x += C.x and post-smoothing of F
+template <typename T, class G>
+__device__ void tail_up(const LevV<T>& F, const LevV<T>& C, int nu) {
+  for (long long id = G::tid(); id < F.N; id += G::n()) {
+    int i, j, k;
+    bdecomp(F.m, id, i, j, k);
+    int K = F.m[2] > 1 ? k / 2 : 0;
+    long long ci = (long long)(i / 2) + (long long)C.m[0] * ((long long)(j / 2) + (long long)C.m[1] * K);
+    F.x[id] = F.x[id] + C.x[ci];
+  }
+  G::sync();
+  for (int s = 0; s < nu; ++s) {
+    tail_smooth<T, G>(F, 1, 0);
+    tail_smooth<T, G>(F, 0, 0);
+  }
 }
 
 template <typename T>
@@ -903,56 +965,11 @@ __device__ __forceinline__ LevV<T> tail_level(const TailLevels<T>& TL, T* sm, in
 // memory and its x written back there at the end.
 template <typename T>
 __device__ void tail_vcycle(const TailLevels<T>& TL, T* sm, int l0, int nl, int nu, int ncoarse) {
-  for (int l = l0; l < nl - 1; ++l) {
-    const LevV<T> F = tail_level<T>(TL, sm, l, l0);
-    for (int s = 0; s < nu; ++s) {
-      tail_smooth<T>(F, 0, s == 0);
-      tail_smooth<T>(F, 1, 0);
-    }
-    const LevV<T> C = tail_level<T>(TL, sm, l + 1, l0);
-    const int kz = F.m[2] > 1 ? 2 : 1;
-    for (long long id = threadIdx.x; id < C.N; id += blockDim.x) {
-      int I, J, K;
-      bdecomp(C.m, id, I, J, K);
-      T s = 0;
-      for (int dk = 0; dk < kz; ++dk)
-        for (int dj = 0; dj < 2; ++dj)
-          for (int di = 0; di < 2; ++di) {
-            int i = 2 * I + di, j = 2 * J + dj, k = kz == 2 ? 2 * K + dk : 0;
-            long long fi = (long long)i + (long long)F.m[0] * ((long long)j + (long long)F.m[1] * k);
-            s += mg_resid<T>(F, fi, i, j, k);
-          }
-      ((T*)C.b)[id] = s;
-    }
-    __syncthreads();
-  }
-  {
-    const LevV<T> L = tail_level<T>(TL, sm, nl - 1, l0);
-    for (int s = 0; s < ncoarse; ++s) {
-      tail_smooth<T>(L, 0, s == 0);
-      tail_smooth<T>(L, 1, 0);
-    }
-    for (int s = 0; s < ncoarse; ++s) {
-      tail_smooth<T>(L, 1, 0);
-      tail_smooth<T>(L, 0, 0);
-    }
-  }
-  for (int l = nl - 2; l >= l0; --l) {
-    const LevV<T> F = tail_level<T>(TL, sm, l, l0);
-    const LevV<T> C = tail_level<T>(TL, sm, l + 1, l0);
-    for (long long id = threadIdx.x; id < F.N; id += blockDim.x) {
-      int i, j, k;
-      bdecomp(F.m, id, i, j, k);
-      int K = F.m[2] > 1 ? k / 2 : 0;
-      long long ci = (long long)(i / 2) + (long long)C.m[0] * ((long long)(j / 2) + (long long)C.m[1] * K);
-      F.x[id] = F.x[id] + C.x[ci];
-    }
-    __syncthreads();
-    for (int s = 0; s < nu; ++s) {
-      tail_smooth<T>(F, 1, 0);
-      tail_smooth<T>(F, 0, 0);
-    }
-  }
+  for (int l = l0; l < nl - 1; ++l)
+    tail_down<T, TailBlock>(tail_level<T>(TL, sm, l, l0), tail_level<T>(TL, sm, l + 1, l0), nu);
+  tail_coarsest<T, TailBlock>(tail_level<T>(TL, sm, nl - 1, l0), ncoarse);
+  for (int l = nl - 2; l >= l0; --l)
+    tail_up<T, TailBlock>(tail_level<T>(TL, sm, l, l0), tail_level<T>(TL, sm, l + 1, l0), nu);
   // the first tail level's x goes back to global memory for the prolongation above
   const T* xs = sm + TL.xo[l0];
   for (long long id = threadIdx.x; id < TL.L[l0].N; id += blockDim.x) TL.L[l0].x[id] = xs[id];
@@ -1878,6 +1895,10 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
       if (psm + fa.sharedSizeBytes > (size_t)optin) return DROPLET_ERR_SIZE;
       CK(cudaFuncSetAttribute(k_mgpcg_persist<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               optin - (int)fa.sharedSizeBytes));
+      // prefer L1 over shared memory beyond what a launch requests: the tail and the
+      // tiles re-read the operator from L1
+      CK(cudaFuncSetAttribute(k_mgpcg_persist<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxL1));
       pmg_smem_max = (size_t)(optin - (int)fa.sharedSizeBytes);
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mgpcg_persist<float>, PTPB, psm));
     } else {
@@ -1885,6 +1906,8 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
       if (psm + fa.sharedSizeBytes > (size_t)optin) return DROPLET_ERR_SIZE;
       CK(cudaFuncSetAttribute(k_mgpcg_persist<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               optin - (int)fa.sharedSizeBytes));
+      CK(cudaFuncSetAttribute(k_mgpcg_persist<double>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              (int)cudaSharedmemCarveoutMaxL1));
       pmg_smem_max = (size_t)(optin - (int)fa.sharedSizeBytes);
       CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mgpcg_persist<double>, PTPB, psm));
     }
