@@ -54,6 +54,36 @@ METRIC = "Mcell-steps/s"
 FLUSH_BYTES = 512 << 20      # larger than the 129 MB L2
 
 
+# DRAM traffic of the dominant kernel from a committed ncu capture: profiles/ncu_traffic.json
+# maps a workload to {class, kernel, dram_bytes_per_launch, sources_sha256, ...}; the value
+# is reported only while the sources that define the kernel hash as they did when the
+# counters were taken (else null: the kernel has changed since).
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+TRAFFIC_SOURCES = ["paper_2005_02867_gb300/csrc/solver.cu", "paper_2005_02867_gb300/csrc/step_kernels.cu",
+                   "paper_2005_02867_gb300/csrc/step_mixed.cu", "paper_2005_02867_gb300/csrc/common.cuh",
+                   "paper_2005_02867_gb300/csrc/kernels.h", "include/droplet.h"]
+
+
+def sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def captured_traffic(workload, kclass):
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh).get(workload)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("class") != kclass or rec.get("sources_sha256") != sources_sha256():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def cells_of(cfg):
     if isinstance(cfg, list):
         return sum(cells_of(c) for c in cfg)
@@ -368,7 +398,8 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "f64" if cl[0]["precision"] == 0 else "f64 state, f32 stencil solves (multigrid, Helmholtz increments)",
             "data": "synthetic", "config": describe(name, cfg),
-            "roofline": dict(roof, kernel=dom, traffic=None, launches=nl, kernel_ms_total=ms, profiled_steps=kprof,
+            "roofline": dict(roof, kernel=dom, traffic=captured_traffic(name, dom), launches=nl, kernel_ms_total=ms,
+                             profiled_steps=kprof,
                              share_of_graph_step=(ms / kprof) / (t_ms / args.steps) if t_ms > 0 else None),
             "kernel_classes": {k: {"ms": v[0], "launches": v[1],
                                    "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else 0,
