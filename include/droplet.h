@@ -93,6 +93,11 @@ typedef struct droplet_config {
   int    const_props_check; /* 1 = constant-property d2-law check mode                 */
   int    physics_mask;  /* DROPLET_PHYS_* bits of the active stages                     */
   double C_alpha;       /* interface-compression coefficient of the alpha flux         */
+  int    mg_tile[2];    /* tile (cells along r / x, along z / y) of the temporal blocking of
+                           the persistent multigrid smoothing on 2D levels; {0, 0}: 32 x 32,
+                           or the autotuner's choice where it runs.  Owned cells get the same
+                           values whatever the tile: a pure performance setting.  Each entry
+                           0 or 8 .. 256.                                                   */
 } droplet_config;
 
 /* Diagnostics of one droplet after the last completed step (Sec. 4 reports

@@ -69,6 +69,8 @@ static int check_cfg(const droplet_config& c) {
   if (c.cp_v != c.cp_g) return DROPLET_ERR_ARG;   // the j_d (cp_v - cp_g) . grad T term is not carried
   if (c.cg_maxit < 1 || c.helm_maxit < 1 || !(c.cg_rtol > 0.0) || !(c.helm_rtol > 0.0)) return DROPLET_ERR_ARG;
   if (c.precision != 0 && c.precision != 1) return DROPLET_ERR_ARG;
+  for (int a = 0; a < 2; ++a)
+    if (c.mg_tile[a] != 0 && (c.mg_tile[a] < 8 || c.mg_tile[a] > 256)) return DROPLET_ERR_ARG;
   long long nn = (long long)c.n[0] * c.n[1] * (c.geom == 0 ? 1 : c.n[2]);
   if (nn + (long long)c.n[0] * c.n[1] >= (1LL << 31)) return DROPLET_ERR_ARG;   // 32-bit cell and face indices
   return 0;
@@ -193,6 +195,10 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
   // latency-bound sizes: persistent solvers (in a batch each droplet is later given an
   // SM budget so that the cooperative solves of all branches fit the GPU together)
   c->solver.persistent = N <= Solver::PERSIST_MAX_CELLS;
+  if (cfg.mg_tile[0] > 0 || cfg.mg_tile[1] > 0) {
+    c->solver.mg_tile[0] = cfg.mg_tile[0] > 0 ? cfg.mg_tile[0] : 32;
+    c->solver.mg_tile[1] = cfg.mg_tile[1] > 0 ? cfg.mg_tile[1] : 32;
+  }
   c->solver.rb = c->rb;
   if ((rc = c->solver.setup(N, c->st))) { free_all(c); delete c; return rc; }
   c->solver.prof = &c->prof;
@@ -483,19 +489,23 @@ static int autotune(droplet_ctx* c) {
     return 0;
   };
   bool tiles = false;
+  auto fixed_tile = [](const dctx* x) { return x->cfg.mg_tile[0] > 0 || x->cfg.mg_tile[1] > 0; };
   for (auto x : c->d)
-    tiles = tiles || (x->solver.persistent && (x->cfg.physics_mask & DROPLET_PHYS_FLOW) && x->g.n[2] == 1);
+    tiles = tiles || (x->solver.persistent && (x->cfg.physics_mask & DROPLET_PHYS_FLOW) && x->g.n[2] == 1 &&
+                      !fixed_tile(x));
   if (tiles) {
     const int cand[][2] = {{32, 32}, {64, 32}, {64, 64}, {128, 32}};
     float best = 1e30f;
     int bt = 0;
     for (int k = 0; k < 4 && !rc; ++k) {
-      for (auto x : c->d) { x->solver.mg_tile[0] = cand[k][0]; x->solver.mg_tile[1] = cand[k][1]; }
+      for (auto x : c->d)
+        if (!fixed_tile(x)) { x->solver.mg_tile[0] = cand[k][0]; x->solver.mg_tile[1] = cand[k][1]; }
       float ms = 0.f;
       rc = trial(&ms);
       if (!rc && ms < best) { best = ms; bt = k; }
     }
-    for (auto x : c->d) { x->solver.mg_tile[0] = cand[bt][0]; x->solver.mg_tile[1] = cand[bt][1]; }
+    for (auto x : c->d)
+      if (!fixed_tile(x)) { x->solver.mg_tile[0] = cand[bt][0]; x->solver.mg_tile[1] = cand[bt][1]; }
   }
   if (c->d.size() > 1 && !rc) {
     const int cand[] = {RED_BLOCKS, 304, 152, 76, 38};
@@ -579,7 +589,7 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
   // batches, and single 2D droplets with flow large enough for the tile shape to matter
   const dctx* x0 = c->d[0];
   if (batch || (x0->solver.persistent && (x0->cfg.physics_mask & DROPLET_PHYS_FLOW) && x0->g.n[2] == 1 &&
-                x0->g.N >= 32768)) {
+                x0->g.N >= 32768 && x0->cfg.mg_tile[0] == 0 && x0->cfg.mg_tile[1] == 0)) {
     int rc = autotune(c);
     if (rc) { free_ctx(c); return rc; }
   }

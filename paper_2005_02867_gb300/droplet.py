@@ -34,6 +34,7 @@ class DropletConfig(ctypes.Structure):
         ("cg_rtol", _c_dbl), ("cg_maxit", _c_int), ("helm_rtol", _c_dbl), ("helm_maxit", _c_int),
         ("seed", ctypes.c_ulonglong), ("T_perturb", _c_dbl),
         ("const_props_check", _c_int), ("physics_mask", _c_int), ("C_alpha", _c_dbl),
+        ("mg_tile", _c_int * 2),
     ]
 
 

@@ -56,7 +56,8 @@ def test_struct_layout_matches_header(tmp_path):
     assert offs == py
 
 
-@pytest.mark.parametrize("bad", [dict(dt=0.0), dict(n=(2, 128, 1)), dict(D0=-1.0), dict(geom=5),
+@pytest.mark.parametrize("bad", [dict(dt=0.0), dict(n=(2, 128, 1)), dict(D0=-1.0), dict(geom=5), dict(mg_tile=(4, 32)),
+                                 dict(mg_tile=(32, 512)),
                                  dict(xc=(1e-3, 4e-3, 0.0)), dict(cp_v=1200.0), dict(eq_model=3),
                                  dict(cg_maxit=0)])
 def test_invalid_config_rejected_without_device(lib, bad):
