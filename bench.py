@@ -81,7 +81,7 @@ def captured_traffic(workload, kclass):
         return None
     if not rec or rec.get("class") != kclass or rec.get("sources_sha256") != sources_sha256():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec
 
 
 def cells_of(cfg):
@@ -392,14 +392,17 @@ def run_ours(args):
         else:
             roof = {"bound": "hbm", "achieved": hbm_gbs, "peak": peak, "unit": "GB/s", "frac": hbm_gbs / peak,
                     "peak_source": src, "fp64_achieved_TFs": fp64_tfs}
+        tr = captured_traffic(name, dom)
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": "f64" if cl[0]["precision"] == 0 else "f64 state, f32 stencil solves (multigrid, Helmholtz increments)",
             "data": "synthetic", "config": describe(name, cfg),
-            "roofline": dict(roof, kernel=dom, traffic=captured_traffic(name, dom), launches=nl, kernel_ms_total=ms,
-                             profiled_steps=kprof,
+            "roofline": dict(roof, kernel=dom, traffic=(tr or {}).get("dram_bytes_per_launch"),
+                             traffic_source=({k: tr[k] for k in ("kernel", "summary", "scaled_from") if k in tr}
+                                             if tr else None),
+                             launches=nl, kernel_ms_total=ms, profiled_steps=kprof,
                              share_of_graph_step=(ms / kprof) / (t_ms / args.steps) if t_ms > 0 else None),
             "kernel_classes": {k: {"ms": v[0], "launches": v[1],
                                    "GBps": (v[2] / (v[0] / 1e3) / 1e9) if v[0] > 0 else 0,
