@@ -117,6 +117,16 @@ static void make_phys(const droplet_config& c, Phys& p) {
   p.eq_model = c.eq_model;
   p.const_props = c.const_props_check;
   p.physics = c.physics_mask;
+  const double Tc[2] = {c.Tc, c.Tc_g}, Pc[2] = {c.Pc, c.Pc_g}, om[2] = {c.omega_ac, c.omega_g};
+  for (int s = 0; s < 2; ++s) {
+    p.pr_ac[s] = 0.45724 * R_GAS * R_GAS * Tc[s] * Tc[s] / Pc[s];
+    p.pr_b[s] = 0.07780 * R_GAS * Tc[s] / Pc[s];
+    p.pr_k[s] = 0.37464 + 1.54226 * om[s] - 0.26992 * om[s] * om[s];
+    p.pr_iTc[s] = 1.0 / Tc[s];
+  }
+  p.pr_sqac01 = std::sqrt(p.pr_ac[0] * p.pr_ac[1]) * (1.0 - c.kij);
+  p.iM_l = 1.0 / c.M_l;
+  p.iM_g = 1.0 / c.M_g;
 }
 
 static int dalloc(double** q, long long n) {

@@ -46,6 +46,11 @@ struct Phys {
   double rhoG_const;   // frozen gas density of the constant-property check
   unsigned long long seed;
   int eq_model, const_props, physics;
+  // Peng-Robinson constants of the fuel (0) and the inert gas (1), formed on the host:
+  // a_c = 0.45724 R^2 Tc^2 / Pc, b = 0.07780 R Tc / Pc, kappa(omega), 1 / Tc, and
+  // sqrt(a_c0 a_c1) (1 - k_ij); inverse molar masses
+  double pr_ac[2], pr_b[2], pr_k[2], pr_iTc[2], pr_sqac01;
+  double iM_l, iM_g;
 };
 
 __host__ __device__ inline int nact(const Geo& g) { return g.act3 ? 3 : 2; }
@@ -220,21 +225,37 @@ __device__ __forceinline__ double Y_from_y(const Phys& p, double y) {
   return y * p.M_l / (y * p.M_l + (1.0 - y) * p.M_g);
 }
 __device__ __forceinline__ double y_from_Y(const Phys& p, double Y) {
-  return (Y / p.M_l) / (Y / p.M_l + (1.0 - Y) / p.M_g);
+  const double m = Y * p.iM_l;
+  return m / (m + (1.0 - Y) * p.iM_g);
 }
 
-__device__ inline void pr_pure(double T, double Tc, double Pc, double om, double& a, double& b) {
-  double kappa = 0.37464 + 1.54226 * om - 0.26992 * om * om;
-  double sq = 1.0 + kappa * (1.0 - sqrt(T / Tc));
-  a = 0.45724 * R_GAS * R_GAS * Tc * Tc / Pc * sq * sq;
-  b = 0.07780 * R_GAS * Tc / Pc;
+// Peng-Robinson pure-component alpha factor sqrt(alpha(T)) = 1 + kappa (1 - sqrt(T / Tc))
+// of component s; a(T) = a_c sq^2 (the constants come from the host, Phys::pr_*)
+__device__ __forceinline__ double pr_sq(const Phys& p, int s, double T) {
+  return 1.0 + p.pr_k[s] * (1.0 - sqrt(T * p.pr_iTc[s]));
+}
+
+// van der Waals mixing of the binary at fuel mole fraction y; A, B of the cubic
+__device__ __forceinline__ void pr_mix_AB(const Phys& p, double T, double P, double y, double& A, double& B,
+                                          double& a0, double& a01, double& am, double& bm) {
+  const double s0 = pr_sq(p, 0, T), s1 = pr_sq(p, 1, T);
+  a0 = p.pr_ac[0] * s0 * s0;
+  const double a1 = p.pr_ac[1] * s1 * s1;
+  a01 = p.pr_sqac01 * fabs(s0 * s1);          // sqrt(a0 a1) (1 - k_ij)
+  const double y1 = 1.0 - y;
+  am = y * y * a0 + y * y1 * a01 + y1 * y * a01 + y1 * y1 * a1;
+  bm = y * p.pr_b[0] + y1 * p.pr_b[1];
+  const double iRT = 1.0 / (R_GAS * T);
+  A = am * P * iRT * iRT;
+  B = bm * P * iRT;
 }
 
 // largest real root of z^3 + c2 z^2 + c1 z + c0 (Cardano; trigonometric form for three real roots)
 __device__ inline double cubic_largest(double c2, double c1, double c0) {
-  double p = c1 - c2 * c2 / 3.0;
-  double q = 2.0 * c2 * c2 * c2 / 27.0 - c2 * c1 / 3.0 + c0;
-  double disc = 0.25 * q * q + p * p * p / 27.0;
+  constexpr double third = 1.0 / 3.0, twentyseventh = 1.0 / 27.0;
+  double p = c1 - c2 * c2 * third;
+  double q = 2.0 * c2 * c2 * c2 * twentyseventh - c2 * c1 * third + c0;
+  double disc = 0.25 * q * q + p * p * p * twentyseventh;
   double t;
   if (disc > 0.0) {
     double h = -0.5 * q;
@@ -244,46 +265,31 @@ __device__ inline double cubic_largest(double c2, double c1, double c0) {
   } else if (p == 0.0) {
     t = 0.0;
   } else {
-    double m = 2.0 * sqrt(-p / 3.0);
+    double m = 2.0 * sqrt(-p * third);
     double arg = 3.0 * q / (p * m);
     arg = fmin(1.0, fmax(-1.0, arg));
-    t = m * cos(acos(arg) / 3.0);
+    t = m * cos(acos(arg) * third);
   }
-  return t - c2 / 3.0;
+  return t - c2 * third;
 }
 
 // binary (fuel, inert) Peng-Robinson compressibility alone (the vapour root), for the
 // gas density: the same arithmetic as pr_binary's Z without the fugacity terms
 __device__ inline double pr_binary_Z(const Phys& p, double T, double P, double y) {
-  double a0, b0, a1, b1;
-  pr_pure(T, p.Tc, p.Pc, p.om, a0, b0);
-  pr_pure(T, p.Tc_g, p.Pc_g, p.om_g, a1, b1);
-  double a01 = sqrt(a0 * a1) * (1.0 - p.kij);
-  double y1 = 1.0 - y;
-  double am = y * y * a0 + y * y1 * a01 + y1 * y * a01 + y1 * y1 * a1;
-  double bm = y * b0 + y1 * b1;
-  double RT = R_GAS * T;
-  double A = am * P / (RT * RT);
-  double B = bm * P / RT;
+  double A, B, a0, a01, am, bm;
+  pr_mix_AB(p, T, P, y, A, B, a0, a01, am, bm);
   return cubic_largest(-(1.0 - B), A - 3.0 * B * B - 2.0 * B, -(A * B - B * B - B * B * B));
 }
 
 // binary (fuel, inert) Peng-Robinson: vapour Z and ln phi_hat of the fuel at mole fraction y
 __device__ inline void pr_binary(const Phys& p, double T, double P, double y, double& Z, double& lnphi0) {
-  double a0, b0, a1, b1;
-  pr_pure(T, p.Tc, p.Pc, p.om, a0, b0);
-  pr_pure(T, p.Tc_g, p.Pc_g, p.om_g, a1, b1);
-  double a01 = sqrt(a0 * a1) * (1.0 - p.kij);
-  double y1 = 1.0 - y;
-  double am = y * y * a0 + y * y1 * a01 + y1 * y * a01 + y1 * y1 * a1;
-  double bm = y * b0 + y1 * b1;
-  double RT = R_GAS * T;
-  double A = am * P / (RT * RT);
-  double B = bm * P / RT;
+  double A, B, a0, a01, am, bm;
+  pr_mix_AB(p, T, P, y, A, B, a0, a01, am, bm);
   Z = cubic_largest(-(1.0 - B), A - 3.0 * B * B - 2.0 * B, -(A * B - B * B - B * B * B));
   const double s2 = 1.4142135623730951;
+  const double b0 = p.pr_b[0];
   double logterm = log((Z + (1.0 + s2) * B) / (Z + (1.0 - s2) * B));
-  double sa = y * a0 + y1 * a01;
+  double sa = y * a0 + (1.0 - y) * a01;
   lnphi0 = b0 / bm * (Z - 1.0) - log(Z - B) - A / (2.0 * s2 * B) * (2.0 * sa / am - b0 / bm) * logterm;
 }
 
@@ -319,7 +325,7 @@ __device__ __forceinline__ double Y_eq(const Phys& p, double T, unsigned* boil, 
 
 __device__ inline double rho_gas(const Phys& p, double T, double Y) {
   if (p.const_props) return p.rhoG_const;
-  double inv_m = Y / p.M_l + (1.0 - Y) / p.M_g;
+  double inv_m = Y * p.iM_l + (1.0 - Y) * p.iM_g;
   double Z = 1.0;
   if (p.eq_model != 0) Z = pr_binary_Z(p, T, p.P, y_from_Y(p, Y));
   return p.P / (Z * R_GAS * T * inv_m);
