@@ -30,6 +30,10 @@ struct dctx {
   double *rho = nullptr, *mu = nullptr, *kc = nullptr, *cp = nullptr, *Dm = nullptr, *yq = nullptr, *dp = nullptr, *S = nullptr;
   int* adj = nullptr;
   double *bD = nullptr, *bc[3] = {nullptr, nullptr, nullptr}, *brhs = nullptr, *bx = nullptr;
+  // box systems of the second and third velocity component for the joint momentum solve
+  // (D, c0, c1, c2, rhs, x each)
+  double* xb[2][6] = {{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
+                      {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}};
   double *part = nullptr, *psum = nullptr, *pmax = nullptr, *scal = nullptr;
   unsigned* flags = nullptr;
   int* dirty = nullptr;              // a state field was overwritten: S0 re-evaluates rho_G everywhere
@@ -143,6 +147,8 @@ static void free_all(dctx* c) {
     cudaFree(c->u[a]); cudaFree(c->FL[a]); cudaFree(c->AF[a]); cudaFree(c->us[a]); cudaFree(c->bc[a]);
     c->u[a] = c->FL[a] = c->AF[a] = c->us[a] = c->bc[a] = nullptr;
   }
+  for (auto& set : c->xb)
+    for (auto& q : set) { cudaFree(q); q = nullptr; }
   cudaFree(c->adj); cudaFree(c->flags); cudaFree(c->dirty);
   c->adj = nullptr; c->flags = nullptr; c->dirty = nullptr;
   cudaFreeHost(c->hscal); cudaFreeHost(c->hflags);
@@ -188,6 +194,7 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
                       &c->bD, &c->brhs, &c->bx, &c->xi};
   for (auto q : cells)
     if ((rc = dalloc(q, N))) { free_all(c); delete c; return rc; }
+
   for (int a = 0; a < 3; ++a) {
     if ((rc = dalloc(&c->bc[a], N))) { free_all(c); delete c; return rc; }
     if (a >= na) continue;
@@ -205,6 +212,13 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
   // latency-bound sizes: persistent solvers (in a batch each droplet is later given an
   // SM budget so that the cooperative solves of all branches fit the GPU together)
   c->solver.persistent = N <= Solver::PERSIST_MAX_CELLS;
+  // the velocity components are solved together (one persistent launch)
+  const bool joint = c->solver.persistent && (cfg.physics_mask & DROPLET_PHYS_FLOW);
+  c->solver.nsys_extra = joint ? nact(c->g) - 1 : 0;
+  for (int k = 0; k < c->solver.nsys_extra; ++k)
+    for (int q = 0; q < 6; ++q)
+      if (q != 3 || na == 3)
+        if ((rc = dalloc(&c->xb[k][q], N))) { free_all(c); delete c; return rc; }
   if (cfg.mg_tile[0] > 0 || cfg.mg_tile[1] > 0) {
     c->solver.mg_tile[0] = cfg.mg_tile[0] > 0 ? cfg.mg_tile[0] : 32;
     c->solver.mg_tile[1] = cfg.mg_tile[1] > 0 ? cfg.mg_tile[1] : 32;
@@ -331,25 +345,62 @@ static int one_step(dctx* c, int* nc_flag) {
   ++g_launches, k_rhoG<<<gc, TPB, 0, st>>>(g, p, c->T, c->omega, c->rhoG);
   // S7 - S10
   if (mask & DROPLET_PHYS_FLOW) {
-    for (int cc = 0; cc < na; ++cc) {
-      int m[3] = {g.n[0], g.n[1], g.n[2]};
-      m[cc] -= 1;
-      long long nbx = (long long)m[0] * m[1] * m[2];
-      {
-      ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, st, (12.0 + 2 * na) * nbx * 8.0);
-      (c->cfg.precision == 1 ? L_mom_assemble_mx : L_mom_assemble)(
-          st, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi, c->bD, c->bc[0],
-          c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+    if (c->solver.persistent && c->solver.nsys_extra == na - 1 && (na == 1 || c->xb[na - 2][5])) {
+      // the components' systems are independent (each is assembled from the old
+      // velocities): assemble all, solve them together, scatter all
+      BoxSys sys[3];
+      RecordSpec recs[3];
+      for (int cc = 0; cc < na; ++cc) {
+        int m[3] = {g.n[0], g.n[1], g.n[2]};
+        m[cc] -= 1;
+        long long nbx = (long long)m[0] * m[1] * m[2];
+        BoxSys& b = sys[cc];
+        if (cc == 0) {
+          b.D = c->bD; b.b = c->brhs; b.x = c->bx;
+          for (int a = 0; a < 3; ++a) b.c[a] = a < na ? c->bc[a] : nullptr;
+        } else {
+          double* const* xs = c->xb[cc - 1];
+          b.D = xs[0]; b.b = xs[4]; b.x = xs[5];
+          for (int a = 0; a < 3; ++a) b.c[a] = a < na ? xs[1 + a] : nullptr;
+        }
+        for (int a = 0; a < 3; ++a) b.m[a] = m[a];
+        b.N = nbx;
+        {
+        ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, st, (12.0 + 2 * na) * nbx * 8.0);
+        (c->cfg.precision == 1 ? L_mom_assemble_mx : L_mom_assemble)(
+            st, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi, b.D, b.c[0],
+            b.c[1], na == 3 ? b.c[2] : b.c[0], (double*)b.b);
+        }
+        L_faces_to_box(st, lin_grid(nbx), g, cc, c->u[cc], b.x);
+        recs[cc] = RecordSpec{c->scal, SC_ITS_U, -1, cc > 0};
       }
-      for (int a = 0; a < 3; ++a) bs.m[a] = m[a];
-      bs.N = nbx;
-      L_faces_to_box(st, lin_grid(nbx), g, cc, c->u[cc], c->bx);
-      c->solver.record_next(c->scal, SC_ITS_U, -1, cc > 0);
-      rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
+      rc = c->solver.pcg_jacobi_multi(sys, na, c->cfg.helm_rtol, c->cfg.helm_maxit, recs, &ss);
       if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
-      c->solver.record(c->scal, SC_ITS_U, -1, cc > 0);
-      cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, st);
-      L_mom_scatter(st, lin_grid(nfaces(g, cc)), g, p, cc, c->bx, c->us[cc]);
+      for (int cc = 0; cc < na; ++cc) {
+        cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, st);
+        L_mom_scatter(st, lin_grid(nfaces(g, cc)), g, p, cc, sys[cc].x, c->us[cc]);
+      }
+    } else {
+      for (int cc = 0; cc < na; ++cc) {
+        int m[3] = {g.n[0], g.n[1], g.n[2]};
+        m[cc] -= 1;
+        long long nbx = (long long)m[0] * m[1] * m[2];
+        {
+        ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, st, (12.0 + 2 * na) * nbx * 8.0);
+        (c->cfg.precision == 1 ? L_mom_assemble_mx : L_mom_assemble)(
+            st, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi, c->bD, c->bc[0],
+            c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+        }
+        for (int a = 0; a < 3; ++a) bs.m[a] = m[a];
+        bs.N = nbx;
+        L_faces_to_box(st, lin_grid(nbx), g, cc, c->u[cc], c->bx);
+        c->solver.record_next(c->scal, SC_ITS_U, -1, cc > 0);
+        rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
+        if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
+        c->solver.record(c->scal, SC_ITS_U, -1, cc > 0);
+        cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, st);
+        L_mom_scatter(st, lin_grid(nfaces(g, cc)), g, p, cc, c->bx, c->us[cc]);
+      }
     }
     double* us2 = c->us[2] ? c->us[2] : c->us[0];
     L_poisson_assemble(st, gc, g, p, c->mdot, c->alpha, c->rhoG_old, c->rhoG, c->u[0], c->u[1], u2,

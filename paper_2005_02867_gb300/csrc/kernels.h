@@ -175,6 +175,10 @@ class Solver {
   bool capturing = false;           // the step is being captured into a CUDA graph
   bool f32_helm = false;            // Jacobi-PCG as FP32 defect correction (set before setup)
   bool persistent = false;          // Jacobi-PCG in one cooperative launch (set before setup)
+  int nsys_extra = 0;               // further systems a joint persistent solve may carry (set before setup)
+  // K (<= 1 + nsys_extra) independent Helmholtz systems in one persistent launch; the
+  // statistics of system k go to recs[k]
+  int pcg_jacobi_multi(const BoxSys* s, int K, double rtol, int maxit, const RecordSpec* recs, SolveStats* out);
   int sm_budget = 0;                // SMs the persistent solves may use (0: the whole GPU)
   int mg_tile[2] = {32, 32};        // tile of the persistent MG's temporal blocking (autotuned)
   size_t pmg_smem_max = 0;          // dynamic shared memory the persistent MG may request
@@ -187,7 +191,7 @@ class Solver {
   int device_loop(F body);
   int pcg_jacobi_f32(const BoxSys& s, double rtol, int maxit, SolveStats* out);
   template <typename T>
-  int pcg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out);
+  int pcg_persist(const BoxSys* s, int K, double rtol, int maxit, const RecordSpec* recs, SolveStats* out);
   int persist_blocks(bool f32);
   RecordSpec take_record();
   double* rec_scal = nullptr;
@@ -202,6 +206,8 @@ class Solver {
         *fp = nullptr, *fAp = nullptr, *fdx = nullptr;
   static constexpr int PERSIST_VECTORS = 13;
   void* pw[PERSIST_VECTORS] = {};   // persistent-solve vectors
+  void* pwx[2][PERSIST_VECTORS] = {};   // those of the second and third system of a joint solve
+  double* r64x[2] = {nullptr, nullptr};
   unsigned* bar = nullptr;      // grid barrier counter and generation
   int* err = nullptr;           // set when a grid barrier wait ran out
   int pb_f32 = 0, pb_f64 = 0;   // co-resident blocks of the persistent solver

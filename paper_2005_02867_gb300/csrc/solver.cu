@@ -399,19 +399,22 @@ constexpr int PTPB = 512;   // threads per block of the persistent solver
 
 // Grid-wide sums of up to 3 values (nv = 0: a plain barrier) for a cooperative launch
 // of PTPB-thread blocks; `phase` counts the grid syncs of the launch (uniform), bar[0]
-// the arrivals (zero at launch), `part` holds 2 x 3 x blocks partials.  The totals are
+// the arrivals (zero at launch), `part` holds 2 x NVM x blocks partials.  The totals are
 // returned to every thread; false when a wait ran out.  FP32 block sums use warp
 // shuffles; FP64 ones go through shared memory so that only three warps do FP64 adds.
-template <typename T>
-__device__ __forceinline__ bool grid_sum3(T (&v)[3], int nv, int phase, T* part_all, unsigned* bar, int* err) {
-  __shared__ T sh[3][PTPB / 32];
+template <typename T, int NVM>
+__device__ __forceinline__ bool grid_sum(T (&v)[NVM], int nv, int phase, T* part_all, unsigned* bar, int* err) {
+  static_assert(NVM <= PTPB / 32, "one warp per value");
+  __shared__ T sh[NVM][PTPB / 32];
   __shared__ int ok;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, G = gridDim.x;
-  T* part = part_all + (phase & 1) * 3 * G;
+  T* part = part_all + (phase & 1) * NVM * G;
   if (nv > 0) {
     if constexpr (sizeof(T) == 8) {
-      __shared__ double red[3][PTPB];
-      for (int q = 0; q < nv; ++q) red[q][threadIdx.x] = v[q];
+      __shared__ double red[NVM][PTPB];
+#pragma unroll
+      for (int q = 0; q < NVM; ++q)
+        if (q < nv) red[q][threadIdx.x] = v[q];
       __syncthreads();
       if (wid < nv) {
         double t = 0.0;
@@ -422,7 +425,9 @@ __device__ __forceinline__ bool grid_sum3(T (&v)[3], int nv, int phase, T* part_
         if (lane == 0) part[wid * G + blockIdx.x] = t;
       }
     } else {
-      for (int q = 0; q < nv; ++q) {
+#pragma unroll
+      for (int q = 0; q < NVM; ++q) {
+        if (q >= nv) break;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
         if (lane == 0) sh[q][wid] = v[q];
@@ -459,10 +464,17 @@ __device__ __forceinline__ bool grid_sum3(T (&v)[3], int nv, int phase, T* part_
     if (lane == 0) sh[wid][0] = t;
   }
   __syncthreads();
-  for (int q = 0; q < nv; ++q) v[q] = sh[q][0];
+#pragma unroll
+  for (int q = 0; q < NVM; ++q)
+    if (q < nv) v[q] = sh[q][0];
   const bool r = ok != 0;
   __syncthreads();
   return r;
+}
+
+template <typename T>
+__device__ __forceinline__ bool grid_sum3(T (&v)[3], int nv, int phase, T* part_all, unsigned* bar, int* err) {
+  return grid_sum<T, 3>(v, nv, phase, part_all, bar, err);
 }
 
 
@@ -507,69 +519,109 @@ struct PersistArgs {
   T *dg, *sc;               // diag(A) and S = diag^(-1/2)
   T *r[2], *s[2], *w[2];    // double-buffered r^, s = A^ p, w = A^ r^
   T *p, *dx;                // search direction, x^
-  T* part;                  // 2 x 3 x blocks partial sums
-  double* part64;           // FP64 partials of the initial norms
   double tol2;              // rtol^2
   int maxit;
-  double* stat;             // solver scalars (S_*)
+  RecordSpec rec;           // statistics slots of this system
+};
+
+// Up to three independent systems solved together (the velocity components of the
+// momentum predictor are assembled from the same old velocities): each iteration does
+// the work of every system still running and one grid-wide sum serves them all, so the
+// synchronisation cost of the solves is paid once.  Each system keeps its own
+// convergence test, iteration count and statistics.
+constexpr int PMAXSYS = 3;
+template <typename T>
+struct PersistMulti {
+  PersistArgs<T> s[PMAXSYS];
+  int K;                    // systems
+  T* part;                  // 2 x 3K x blocks partial sums
+  double* part64;           // FP64 partials of the initial norms (2 x 2K x blocks)
+  double* stat;             // solver scalars (S_*) of the whole solve
   int* done;
   unsigned* bar;            // [0] arrivals, [1] departures (zero at launch)
   int* err;
-  RecordSpec rec;
 };
 
 template <typename T>
-__global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(PersistArgs<T> a) {
-  __shared__ T bc[3];                       // broadcast: alpha, beta
-  __shared__ double sd[3];
-  const int m0 = a.A.m[0], m1 = a.A.m[1], m2 = a.A.m[2];
-  const int N = (int)a.A.N;                 // at most PERSIST_MAX_CELLS: 32-bit indices
-  const int st1 = m0, st2 = m0 * m1;
-  const bool has2 = a.A.c[2] != nullptr;
+__global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(PersistMulti<T> M) {
+  // block-uniform state of each system (written by thread 0 between barriers)
+  __shared__ double s_bb[PMAXSYS], s_rr[PMAXSYS], s_inv_nu[PMAXSYS];
+  __shared__ T s_nu[PMAXSYS], s_thr[PMAXSYS], s_gamma[PMAXSYS], s_alpha[PMAXSYS], s_beta[PMAXSYS], s_rho[PMAXSYS];
+  __shared__ int s_its[PMAXSYS], s_res[PMAXSYS], s_act[PMAXSYS], s_any;
+  const int K = M.K;
   const int gs = gridDim.x * blockDim.x;
   const int id0 = blockIdx.x * blockDim.x + threadIdx.x;
   int phase = 0;
-  // phase 0: r0 = b - A x0 in FP64, diag, S = diag^(-1/2); |b|^2 and |r0|^2
-  double q64[3] = {0.0, 0.0, 0.0};
-  for (int id = id0; id < N; id += gs) {
-    int i, j, k;
-    bdecomp(a.A.m, id, i, j, k);
-    double ax, d;
-    box_row<double, double, true>(a.A.m, a.A.D, a.A.c, a.x, id, i, j, k, ax, d);
-    const double bP = a.b[id], r0 = bP - ax;
-    a.r64[id] = r0;
-    const T dT = (T)d;
-    a.dg[id] = dT;
-    a.sc[id] = (T)1 / sqrt(dT);
-    q64[0] += bP * bP;
-    q64[1] += r0 * r0;
-  }
-  bool ok = grid_sum3<double>(q64, 2, phase++, a.part64, a.bar, a.err);
-  const double bb = q64[0], rr0 = q64[1];
-  int its = 0, result = ok ? 2 : 3;
-  double rr_out = rr0;
-  if (ok && (bb == 0.0 || rr0 <= a.tol2 * bb)) {
-    result = 1;                             // converged at the initial guess
-  } else if (ok) {
-    // per-solve scalars, formed once (FP64 work repeated by every thread is slow on GB300)
+  // phase 0: r0 = b - A x0 in FP64, diag, S = diag^(-1/2); |b|^2 and |r0|^2 per system
+  {
+    double q64[2 * PMAXSYS];
+#pragma unroll
+    for (int k = 0; k < 2 * PMAXSYS; ++k) q64[k] = 0.0;
+#pragma unroll
+    for (int k = 0; k < PMAXSYS; ++k) {
+      if (k >= K) break;
+      const PersistArgs<T>& a = M.s[k];
+      const int N = (int)a.A.N;               // at most PERSIST_MAX_CELLS: 32-bit indices
+      for (int id = id0; id < N; id += gs) {
+        int i, j, kk;
+        bdecomp(a.A.m, id, i, j, kk);
+        double ax, d;
+        box_row<double, double, true>(a.A.m, a.A.D, a.A.c, a.x, id, i, j, kk, ax, d);
+        const double bP = a.b[id], r0 = bP - ax;
+        a.r64[id] = r0;
+        const T dT = (T)d;
+        a.dg[id] = dT;
+        a.sc[id] = (T)1 / sqrt(dT);
+        q64[2 * k] += bP * bP;
+        q64[2 * k + 1] += r0 * r0;
+      }
+    }
+    const bool ok = grid_sum<double, 2 * PMAXSYS>(q64, 2 * K, phase++, M.part64, M.bar, M.err);
     if (threadIdx.x == 0) {
-      sd[0] = sqrt(rr0);                    // |r0| = 1 / nu
-      sd[1] = 1.0 / sd[0];                  // nu
-      sd[2] = a.tol2 * bb / rr0;            // rtol^2 |b|^2 / |r0|^2
+      s_any = 0;
+#pragma unroll
+      for (int k = 0; k < PMAXSYS; ++k) {
+        s_bb[k] = q64[2 * k];
+        s_rr[k] = q64[2 * k + 1];
+        s_its[k] = 0;
+        s_res[k] = ok ? 2 : 3;
+        s_act[k] = 0;
+        if (k < K && ok) {
+          if (s_bb[k] == 0.0 || s_rr[k] <= M.s[k].tol2 * s_bb[k]) {
+            s_res[k] = 1;                            // converged at the initial guess
+          } else {
+            // per-solve scalars, formed once (FP64 work repeated by every thread is slow on GB300)
+            s_act[k] = 1;
+            s_any = 1;
+            s_inv_nu[k] = sqrt(s_rr[k]);             // |r0| = 1 / nu
+            s_nu[k] = (T)(1.0 / s_inv_nu[k]);
+            s_thr[k] = (T)(M.s[k].tol2 * s_bb[k] / s_rr[k]);   // rtol^2 |b|^2 / |r0|^2
+          }
+        }
+      }
     }
     __syncthreads();
-    const double inv_nu = sd[0];
-    const T nu = (T)sd[1];
-    const T thr = (T)sd[2];
+  }
+  if (s_any) {
     // setup: r^0 = nu S r0 (the neighbours' formed on the fly), c^ on the low faces,
     // w = A^ r^0, s = p = x^ = 0; gamma, delta, weighted |r^|^2
-    T v[3] = {0, 0, 0};
-    {
+    T v[3 * PMAXSYS];
+#pragma unroll
+    for (int k = 0; k < 3 * PMAXSYS; ++k) v[k] = 0;
+#pragma unroll
+    for (int k = 0; k < PMAXSYS; ++k) {
+      if (k >= K) break;
+      if (!s_act[k]) continue;
+      const PersistArgs<T>& a = M.s[k];
+      const int m0 = a.A.m[0], m1 = a.A.m[1], m2 = a.A.m[2];
+      const int N = (int)a.A.N, st1 = m0, st2 = m0 * m1;
+      const bool has2 = a.A.c[2] != nullptr;
+      const T nu = s_nu[k];
       T g = 0, dl = 0, q = 0;
 #define RH(o) (nu * a.sc[o] * (T)a.r64[o])
       for (int id = id0; id < N; id += gs) {
-        int i, j, k;
-        bdecomp(a.A.m, id, i, j, k);
+        int i, j, kk;
+        bdecomp(a.A.m, id, i, j, kk);
         const T sP = a.sc[id], rP = RH(id);
         a.r[0][id] = rP;
         a.s[0][id] = 0;
@@ -593,14 +645,14 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
         }
         if (j < m1 - 1) y -= (T)a.A.c[1][id + st1] * sP * a.sc[id + st1] * RH(id + st1);
         if (has2) {
-          if (k > 0) {
+          if (kk > 0) {
             const T c = (T)a.A.c[2][id] * sP * a.sc[id - st2];
             a.ch[2][id] = c;
             y -= c * RH(id - st2);
           } else {
             a.ch[2][id] = 0;
           }
-          if (k < m2 - 1) y -= (T)a.A.c[2][id + st2] * sP * a.sc[id + st2] * RH(id + st2);
+          if (kk < m2 - 1) y -= (T)a.A.c[2][id + st2] * sP * a.sc[id + st2] * RH(id + st2);
         }
         a.w[0][id] = y;
         g += rP * rP;
@@ -608,69 +660,129 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
         q += a.dg[id] * rP * rP;
       }
 #undef RH
-      v[0] = g; v[1] = dl; v[2] = q;
-      ok = grid_sum3<T>(v, 3, phase++, a.part, a.bar, a.err);
+      v[3 * k] = g;
+      v[3 * k + 1] = dl;
+      v[3 * k + 2] = q;
     }
-    T gamma = v[0], alpha = v[0] / v[1], beta = 0, rho = v[2];
-    if (!ok) result = 3;
-    for (int cur = 0; ok && its < a.maxit; cur ^= 1) {
-      const T al = alpha, bt = beta;
-      const T *r = a.r[cur], *s = a.s[cur], *w = a.w[cur];
-      T *rn = a.r[cur ^ 1], *sn = a.s[cur ^ 1], *wn = a.w[cur ^ 1];
-      T g = 0, dl = 0, q = 0;
-      for (int id = id0; id < N; id += gs) {
-        int i, j, k;
-        bdecomp(a.A.m, id, i, j, k);
-        const T rP = r[id];
-        const T pP = rP + bt * a.p[id];       // p = r^ + beta p
-        const T sP = w[id] + bt * s[id];      // s = w + beta s
-        a.p[id] = pP;
-        a.dx[id] += al * pP;                  // x^ += alpha p
-        const T rN = rP - al * sP;            // r^ -= alpha s
-        // neighbours: clamped indices and zero couplings at the box edges, so that all
-        // loads issue together; r^_new of a neighbour from its r^, s, w
-        const int iw = i > 0 ? id - 1 : id, ie = i < m0 - 1 ? id + 1 : id;
-        const int is = j > 0 ? id - st1 : id, in = j < m1 - 1 ? id + st1 : id;
-        const T cw = a.ch[0][id], ce = i < m0 - 1 ? a.ch[0][ie] : (T)0;
-        const T cs = a.ch[1][id], cn = j < m1 - 1 ? a.ch[1][in] : (T)0;
+    bool ok = grid_sum<T, 3 * PMAXSYS>(v, 3 * K, phase++, M.part, M.bar, M.err);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < PMAXSYS; ++k) {
+        s_gamma[k] = v[3 * k];
+        s_alpha[k] = s_act[k] ? v[3 * k] / v[3 * k + 1] : (T)0;
+        s_beta[k] = 0;
+        s_rho[k] = v[3 * k + 2];
+        if (!ok && s_act[k]) { s_act[k] = 0; s_res[k] = 3; }
+      }
+    }
+    __syncthreads();
+    for (int cur = 0;; cur ^= 1) {
+      int any = 0;
+#pragma unroll
+      for (int k = 0; k < PMAXSYS; ++k) any |= (k < K) ? s_act[k] : 0;
+      if (!any) break;
+#pragma unroll
+      for (int k = 0; k < 3 * PMAXSYS; ++k) v[k] = 0;
+#pragma unroll
+      for (int k = 0; k < PMAXSYS; ++k) {
+        if (k >= K) break;
+        if (!s_act[k]) continue;
+        const PersistArgs<T>& a = M.s[k];
+        const int m0 = a.A.m[0], m1 = a.A.m[1], m2 = a.A.m[2];
+        const int N = (int)a.A.N, st1 = m0, st2 = m0 * m1;
+        const bool has2 = a.A.c[2] != nullptr;
+        const T al = s_alpha[k], bt = s_beta[k];
+        const T *r = a.r[cur], *s = a.s[cur], *w = a.w[cur];
+        T *rn = a.r[cur ^ 1], *sn = a.s[cur ^ 1], *wn = a.w[cur ^ 1];
+        T g = 0, dl = 0, q = 0;
+        for (int id = id0; id < N; id += gs) {
+          int i, j, kk;
+          bdecomp(a.A.m, id, i, j, kk);
+          const T rP = r[id];
+          const T pP = rP + bt * a.p[id];       // p = r^ + beta p
+          const T sP = w[id] + bt * s[id];      // s = w + beta s
+          a.p[id] = pP;
+          a.dx[id] += al * pP;                  // x^ += alpha p
+          const T rN = rP - al * sP;            // r^ -= alpha s
+          // neighbours: clamped indices and zero couplings at the box edges, so that all
+          // loads issue together; r^_new of a neighbour from its r^, s, w
+          const int iw = i > 0 ? id - 1 : id, ie = i < m0 - 1 ? id + 1 : id;
+          const int is = j > 0 ? id - st1 : id, in = j < m1 - 1 ? id + st1 : id;
+          const T cw = a.ch[0][id], ce = i < m0 - 1 ? a.ch[0][ie] : (T)0;
+          const T cs = a.ch[1][id], cn = j < m1 - 1 ? a.ch[1][in] : (T)0;
 #define UNB(o) (r[o] - al * (w[o] + bt * s[o]))
-        T y = rN - (cw * UNB(iw) + ce * UNB(ie) + cs * UNB(is) + cn * UNB(in));
-        if (has2) {
-          const int ib = k > 0 ? id - st2 : id, it = k < m2 - 1 ? id + st2 : id;
-          const T cb = a.ch[2][id], ct = k < m2 - 1 ? a.ch[2][it] : (T)0;
-          y -= cb * UNB(ib) + ct * UNB(it);
-        }
+          T y = rN - (cw * UNB(iw) + ce * UNB(ie) + cs * UNB(is) + cn * UNB(in));
+          if (has2) {
+            const int ib = kk > 0 ? id - st2 : id, it = kk < m2 - 1 ? id + st2 : id;
+            const T cb = a.ch[2][id], ct = kk < m2 - 1 ? a.ch[2][it] : (T)0;
+            y -= cb * UNB(ib) + ct * UNB(it);
+          }
 #undef UNB
-        rn[id] = rN;
-        sn[id] = sP;
-        wn[id] = y;
-        g += rN * rN;
-        dl += y * rN;
-        q += a.dg[id] * rN * rN;
+          rn[id] = rN;
+          sn[id] = sP;
+          wn[id] = y;
+          g += rN * rN;
+          dl += y * rN;
+          q += a.dg[id] * rN * rN;
+        }
+        v[3 * k] = g;
+        v[3 * k + 1] = dl;
+        v[3 * k + 2] = q;
       }
-      v[0] = g; v[1] = dl; v[2] = q;
-      ok = grid_sum3<T>(v, 3, phase++, a.part, a.bar, a.err);
-      ++its;
-      if (!ok) { result = 3; break; }
+      ok = grid_sum<T, 3 * PMAXSYS>(v, 3 * K, phase++, M.part, M.bar, M.err);
       if (threadIdx.x == 0) {
-        const T bn = v[0] / gamma;
-        bc[0] = v[0] / (v[1] - bn * v[0] / alpha);
-        bc[1] = bn;
+#pragma unroll
+        for (int k = 0; k < PMAXSYS; ++k) {
+          if (k >= K || !s_act[k]) continue;
+          ++s_its[k];
+          if (!ok) { s_act[k] = 0; s_res[k] = 3; continue; }
+          s_rho[k] = v[3 * k + 2];
+          if (v[3 * k + 2] <= s_thr[k]) { s_act[k] = 0; s_res[k] = 1; continue; }
+          if (s_its[k] >= M.s[k].maxit) { s_act[k] = 0; s_res[k] = 2; continue; }
+          const T bn = v[3 * k] / s_gamma[k];
+          s_alpha[k] = v[3 * k] / (v[3 * k + 1] - bn * v[3 * k] / s_alpha[k]);
+          s_beta[k] = bn;
+          s_gamma[k] = v[3 * k];
+        }
       }
-      rho = v[2];
-      if (v[2] <= thr) { result = 1; break; }
-      __syncthreads();
-      alpha = bc[0];
-      beta = bc[1];
-      gamma = v[0];
       __syncthreads();
     }
-    // x += S x^ / nu
-    for (int id = id0; id < N; id += gs) a.x[id] += (double)(a.sc[id] * a.dx[id]) * inv_nu;
-    rr_out = (double)rho * inv_nu * inv_nu;
+    // x += S x^ / nu for every system that iterated
+#pragma unroll
+    for (int k = 0; k < PMAXSYS; ++k) {
+      if (k >= K) break;
+      if (s_its[k] == 0) continue;
+      const PersistArgs<T>& a = M.s[k];
+      const int N = (int)a.A.N;
+      const double inv_nu = s_inv_nu[k];
+      for (int id = id0; id < N; id += gs) a.x[id] += (double)(a.sc[id] * a.dx[id]) * inv_nu;
+    }
   }
-  persist_finish(a.stat, a.done, a.rec, its, rr_out, bb, result, a.bar, a.err);
+  // statistics of each system, then of the whole solve, then the barrier reset
+  int all = 1, itmax = 0;
+  double rrs = 0.0, bbs = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < PMAXSYS; ++k) {
+      if (k >= K) break;
+      const double rr = s_its[k] > 0 ? (double)s_rho[k] * s_inv_nu[k] * s_inv_nu[k] : s_rr[k];
+      const RecordSpec& rec = M.s[k].rec;
+      if (blockIdx.x == 0 && rec.scal) {
+        if (rec.acc) rec.scal[rec.its] += (double)s_its[k];
+        else rec.scal[rec.its] = (double)s_its[k];
+        if (rec.res >= 0) rec.scal[rec.res] = s_bb[k] > 0.0 ? sqrt(rr / s_bb[k]) : 0.0;
+        if (s_res[k] != 1) rec.scal[SC_NC] = 1.0;
+      }
+      all = all && s_res[k] == 1;
+      itmax = s_its[k] > itmax ? s_its[k] : itmax;
+      rrs += rr;
+      bbs += s_bb[k];
+    }
+  }
+  const RecordSpec none{nullptr, 0, -1, 0};
+  persist_finish(M.stat, M.done, none, itmax, rrs, bbs, all ? 1 : 2, M.bar, M.err);
 }
+
 
 
 // condition of a solver WHILE node: run another iteration while not done
@@ -1571,6 +1683,12 @@ int Solver::setup(long long maxN, cudaStream_t s) {
   }
   if (persistent) CK(cudaMalloc(&mg_q2, sizeof(double) * (size_t)maxN));
   if (persistent)
+    for (int k = 0; k < nsys_extra; ++k) {
+      CK(cudaMalloc(&r64x[k], sizeof(double) * (size_t)maxN));
+      for (int q = 0; q < PERSIST_VECTORS; ++q)
+        CK(cudaMalloc(&pwx[k][q], (f32_helm ? sizeof(float) : sizeof(double)) * (size_t)maxN));
+    }
+  if (persistent)
     for (int q = 0; q < PERSIST_VECTORS; ++q) CK(cudaMalloc(&pw[q], (f32_helm ? sizeof(float) : sizeof(double)) * (size_t)maxN));
   return 0;
 }
@@ -1582,6 +1700,11 @@ void Solver::release() {
     float** fa[] = {&fD, &fc[0], &fc[1], &fc[2], &fidg, &fr, &fz, &fp, &fAp, &fdx};
     for (auto q : fa) { cudaFree(*q); *q = nullptr; }
     for (int q = 0; q < PERSIST_VECTORS; ++q) { cudaFree(pw[q]); pw[q] = nullptr; }
+    for (int k = 0; k < 2; ++k) {
+      cudaFree(r64x[k]);
+      r64x[k] = nullptr;
+      for (int q = 0; q < PERSIST_VECTORS; ++q) { cudaFree(pwx[k][q]); pwx[k][q] = nullptr; }
+    }
     cudaFree(bar); cudaFree(err); cudaFree(mg_q2);
     mg_q2 = nullptr;
     bar = nullptr; err = nullptr;
@@ -1672,40 +1795,57 @@ int Solver::device_loop(F body) {
 }
 
 template <typename T>
-int Solver::pcg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
-  BoxV A = view(s);
-  PersistArgs<T> a;
-  memset(&a, 0, sizeof(a));
-  a.A = A;
-  a.b = s.b;
-  a.x = s.x;
-  a.r64 = r;
-  a.tol2 = rtol * rtol;
-  a.maxit = maxit;
-  a.rec = take_record();
+int Solver::pcg_persist(const BoxSys* sys, int K, double rtol, int maxit, const RecordSpec* recs, SolveStats* out) {
   constexpr bool f32 = sizeof(T) == 4;
-  for (int q = 0; q < 3; ++q) a.ch[q] = (T*)pw[q];
-  a.dg = (T*)pw[3];
-  a.sc = (T*)pw[4];
-  for (int q = 0; q < 2; ++q) {
-    a.r[q] = (T*)pw[5 + q];
-    a.s[q] = (T*)pw[7 + q];
-    a.w[q] = (T*)pw[9 + q];
+  PersistMulti<T> M;
+  memset(&M, 0, sizeof(M));
+  M.K = K;
+  long long nmax = 0;
+  double setup_b = 0.0, iter_b = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const BoxSys& s = sys[k];
+    PersistArgs<T>& a = M.s[k];
+    void* const* v = k == 0 ? pw : pwx[k - 1];
+    a.A = view(s);
+    a.b = s.b;
+    a.x = s.x;
+    a.r64 = k == 0 ? r : r64x[k - 1];
+    a.tol2 = rtol * rtol;
+    a.maxit = maxit;
+    a.rec = recs[k];
+    for (int q = 0; q < 3; ++q) a.ch[q] = (T*)v[q];
+    a.dg = (T*)v[3];
+    a.sc = (T*)v[4];
+    for (int q = 0; q < 2; ++q) {
+      a.r[q] = (T*)v[5 + q];
+      a.s[q] = (T*)v[7 + q];
+      a.w[q] = (T*)v[9 + q];
+    }
+    a.p = (T*)v[11];
+    a.dx = (T*)v[12];
+    nmax = std::max(nmax, s.N);
+    // algorithmic bytes: setup (FP64 operator read twice and defect in; diag, S, r^, s,
+    // p, x^, c^, w out), the final x += S x^ / nu, and per iteration r^, s, w, p, x^,
+    // diag and c^ in, r^, s, w, p, x^ out
+    const double na = s.c[2] ? 3.0 : 2.0, wb = (double)sizeof(T);
+    setup_b += ((2.0 + 2.0 * na) * 8.0 + (7.0 + na) * wb + 2.0 * wb + 16.0) * s.N;
+    iter_b += (11.0 + na) * wb * s.N;
   }
-  a.p = (T*)pw[11];
-  a.dx = (T*)pw[12];
-  a.part = (T*)part;
-  a.part64 = part + 4 * RED_BLOCKS;   // beyond the 2 x 3 x grid values of precision T
-  a.stat = sc;
-  a.done = done;
-  a.bar = bar;
-  a.err = err;
-  int grid = (int)((s.N + PTPB - 1) / PTPB);
+  M.stat = sc;
+  M.done = done;
+  M.bar = bar;
+  M.err = err;
+  int grid = (int)((nmax + PTPB - 1) / PTPB);
   int cap = persist_blocks(f32);
   if (sm_budget > 0) cap = std::min(cap, sm_budget * std::max(1, cap / nsm_));
   if (grid > cap) grid = cap;
-  if (grid > RED_BLOCKS) grid = RED_BLOCKS;   // partials: 2 x 3 x grid values in part[0, 8 RED_BLOCKS)
+  // partials in `part` (8 RED_BLOCKS doubles): the FP64 initial norms (2 x 2 PMAXSYS per
+  // block) first, then the sums of precision T (2 x 3 PMAXSYS per block)
+  const int per_blk = 4 * PMAXSYS + (f32 ? 3 * PMAXSYS : 6 * PMAXSYS);   // doubles per block
+  if (grid > 8 * RED_BLOCKS / per_blk) grid = 8 * RED_BLOCKS / per_blk;
   if (grid < 1) grid = 1;
+  M.part64 = part;
+  M.part = (T*)(part + 4 * PMAXSYS * grid);
   cudaLaunchConfig_t lc;
   memset(&lc, 0, sizeof(lc));
   lc.gridDim = dim3(grid);
@@ -1716,23 +1856,26 @@ int Solver::pcg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* out
   at[0].val.cooperative = 1;
   lc.attrs = at;
   lc.numAttrs = 1;
-  // algorithmic bytes: setup (FP64 operator read twice and defect in; diag, S, r^, s, p,
-  // x^, c^, w out), the final x += S x^ / nu, and per iteration r^, s, w, p, x^, diag
-  // and c^ in, r^, s, w, p, x^ out
-  const double na = s.c[2] ? 3.0 : 2.0, wb = (double)sizeof(T);
-  const double setup_b = ((2.0 + 2.0 * na) * 8.0 + (7.0 + na) * wb + 2.0 * wb + 16.0) * s.N;
-  const double iter_b = (11.0 + na) * wb * s.N;
   ++g_launches;
   {
     ProfScope ps(prof, KC_SPMV, stream, setup_b);
-    CK(cudaLaunchKernelEx(&lc, k_pcg_persist<T>, a));
+    CK(cudaLaunchKernelEx(&lc, k_pcg_persist<T>, M));
   }
   if (capturing) return 0;
   int conv = 0;
   poll(hsc, sc, done, stream, maxit, &conv);
+  // (the iteration bytes of the slower system stand for all: the systems iterate together)
   if (prof && prof->on) prof->bytes[KC_SPMV] += hsc[S_ITS] * iter_b;
   fill_stats(hsc, conv, out);
   return conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
+}
+
+int Solver::pcg_jacobi_multi(const BoxSys* s, int K, double rtol, int maxit, const RecordSpec* recs,
+                             SolveStats* out) {
+  if (!persistent || K < 1 || K > 1 + nsys_extra) return DROPLET_ERR_ARG;
+  recorded = false;
+  rec_scal = nullptr;
+  return f32_helm ? pcg_persist<float>(s, K, rtol, maxit, recs, out) : pcg_persist<double>(s, K, rtol, maxit, recs, out);
 }
 
 int Solver::persist_blocks(bool f32) {
@@ -1749,7 +1892,10 @@ int Solver::persist_blocks(bool f32) {
 }
 
 int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
-  if (persistent) return f32_helm ? pcg_persist<float>(s, rtol, maxit, out) : pcg_persist<double>(s, rtol, maxit, out);
+  if (persistent) {
+    const RecordSpec rec = take_record();
+    return f32_helm ? pcg_persist<float>(&s, 1, rtol, maxit, &rec, out) : pcg_persist<double>(&s, 1, rtol, maxit, &rec, out);
+  }
   if (f32_helm) return pcg_jacobi_f32(s, rtol, maxit, out);
   BoxV A = view(s);
   int nb = red_grid_cap(s.N, rb);
