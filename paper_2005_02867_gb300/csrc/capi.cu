@@ -288,7 +288,8 @@ static int one_step(dctx* c, int* nc_flag) {
   // S3
   if (mask & DROPLET_PHYS_FLOW) {
     for (int a = 0; a < na; ++a)
-      L_adv_faces(st, lin_grid(nfaces(g, a)), g, p, a, c->astar, c->u[a], c->FL[a], c->AF[a]);
+      (c->cfg.precision == 1 ? L_adv_faces_mx : L_adv_faces)(st, lin_grid(nfaces(g, a)), g, p, a, c->astar, c->u[a],
+                                                             c->FL[a], c->AF[a]);
     double* F2 = c->FL[2] ? c->FL[2] : c->FL[0];
     double* A2 = c->AF[2] ? c->AF[2] : c->AF[0];
     ++g_launches, k_adv_low<<<gc, TPB, 0, st>>>(g, c->astar, c->FL[0], c->FL[1], F2, c->aL);

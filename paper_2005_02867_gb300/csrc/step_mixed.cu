@@ -366,6 +366,79 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
   rhs[id] = r;
 }
 
+// alpha gradient of a cell (central differences, the ghost rule of alpha), FP32
+__device__ __forceinline__ void grad_alpha_f(const Geo& g, const GeoF& q, const double* al, int i, int j, int k,
+                                             float gr[3]) {
+  gr[0] = (cellg_f(g, al, i + 1, j, k, R_ALPHA, 0.f, 0, 0, 0) - cellg_f(g, al, i - 1, j, k, R_ALPHA, 0.f, 0, 0, 0)) *
+          (0.5f * q.ih[0]);
+  gr[1] = (cellg_f(g, al, i, j + 1, k, R_ALPHA, 0.f, 0, 0, 0) - cellg_f(g, al, i, j - 1, k, R_ALPHA, 0.f, 0, 0, 0)) *
+          (0.5f * q.ih[1]);
+  gr[2] = g.act3 ? (cellg_f(g, al, i, j, k + 1, R_ALPHA, 0.f, 0, 0, 0) -
+                    cellg_f(g, al, i, j, k - 1, R_ALPHA, 0.f, 0, 0, 0)) * (0.5f * q.ih[2])
+                 : 0.f;
+}
+
+// Face fluxes of the alpha advection (Sec. 2.1 with the compressive flux), mixed
+// precision: the low-order upwind flux phi alpha_up stays FP64 (it decides the bounds
+// of the low-order solution); the antidiffusive flux A = FH - FL is formed directly as
+// phi (van Leer increment) + C_alpha |phi| (n_f . e) a_c (1 - a_c) in FP32 -- equal to
+// the difference in exact arithmetic, without its cancellation.  Fluxes are applied
+// antisymmetrically, so the volume stays conserved whatever their precision, and the
+// limiter bounds the result as in k_adv_faces.
+template <int DIR, int NA>
+__global__ void k_adv_faces_mx(Geo g, Phys p, const double* as, const double* ua, double* FL, double* AF) {
+  constexpr int a = DIR;
+  long long nf = nfaces(g, a);
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= nf) return;
+  int m0 = g.n[0] + (a == 0), m1 = g.n[1] + (a == 1);
+  int f[3];
+  decomp(id, m0, m1, f[0], f[1], f[2]);
+  int L[3] = {f[0], f[1], f[2]}, R[3] = {f[0], f[1], f[2]};
+  L[a] -= 1;
+  const double phi = ua[id] * faceA(g, a, f[0]) * p.dt;
+  const double aL = cellg(g, as, L[0], L[1], L[2], R_ALPHA, 0, 0, 0, 0);
+  const double aR = cellg(g, as, R[0], R[1], R[2], R_ALPHA, 0, 0, 0, 0);
+  const bool pos = phi >= 0.0;
+  FL[id] = phi * (pos ? aL : aR);
+  float A = 0.f;
+  if (f[a] > 0 && f[a] < g.n[a]) {
+    const GeoF q = geof(g);
+    int LL[3] = {L[0], L[1], L[2]}, RR[3] = {R[0], R[1], R[2]};
+    LL[a] -= 1;
+    RR[a] += 1;
+    const float aLf = f32_rn(aL), aRf = f32_rn(aR);
+    const float aLL = cellg_f(g, as, LL[0], LL[1], LL[2], R_ALPHA, 0.f, 0, 0, 0);
+    const float aRR = cellg_f(g, as, RR[0], RR[1], RR[2], R_ALPHA, 0.f, 0, 0, 0);
+    // van Leer increment over the upwind value
+    const float dU = pos ? aLf - aLL : aRf - aRR, dD = pos ? aRf - aLf : aLf - aRf, pr = dU * dD;
+    const float inc = pr > 0.f ? pr / (dU + dD) : 0.f;
+    float gL[3], gR[3];
+    grad_alpha_f(g, q, as, L[0], L[1], L[2], gL);
+    grad_alpha_f(g, q, as, R[0], R[1], R[2], gR);
+    const float gf[3] = {gL[0] + gR[0], gL[1] + gR[1], gL[2] + gR[2]};
+    const float gfm = sqrtf(gf[0] * gf[0] + gf[1] * gf[1] + (g.act3 ? gf[2] * gf[2] : 0.f));
+    const float ne = gfm > 1e-8f / f32_rn(g.hmin) ? gf[a] / gfm : 0.f;
+    const float ac = 0.5f * (aLf + aRf);
+    const float phif = f32_rn(phi);
+    A = phif * inc + f32_rn(p.C_alpha) * fabsf(phif) * ne * ac * (1.f - ac);
+  }
+  AF[id] = f64_of(A);
+}
+
+void L_adv_faces_mx(cudaStream_t st, int grid, Geo g, Phys p, int a, const double* as, const double* ua, double* FL,
+                    double* AF) {
+  ++g_launches;
+  if (nact(g) == 3) {
+    if (a == 0) k_adv_faces_mx<0, 3><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
+    else if (a == 1) k_adv_faces_mx<1, 3><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
+    else k_adv_faces_mx<2, 3><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
+  } else {
+    if (a == 0) k_adv_faces_mx<0, 2><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
+    else k_adv_faces_mx<1, 2><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
+  }
+}
+
 void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi,
                           const double* rho, const double* cp, const double* kc, const double* D, const double* mdot,
                           const double* u0, const double* u1, const double* u2, const double* alpha_new,
