@@ -1064,6 +1064,137 @@ __device__ void tail_up(const LevV<T>& F, const LevV<T>& C, int nu) {
   }
 }
 
+// ---------------------------------------------------------------- dense coarsest level
+// The coarsest level of the persistent V-cycle (at most DENSE_MAX_CELLS cells) is solved
+// exactly instead of by red-black sweeps: its operator A (SPD: diagonal D + adjacent
+// couplings, off-diagonals -c) is factored once per solve by Gaussian elimination
+// without pivoting on [A | I].  Elimination turns A into U = diag(d) L^T and I into
+// E = L^-1 (A = L diag(d) L^T, L unit lower triangular), so A^-1 = W^T W with
+// W = diag(d)^-1/2 E.  Applying x = W^T (W b) is two dense triangular products -- a
+// handful of block-wide steps where the sweeps took dozens -- and keeps the coarse
+// solve symmetric positive definite, as the CG preconditioner requires.
+constexpr int DENSE_MAX_CELLS = 64;
+constexpr int DENSE_GROUPS = PTPB / DENSE_MAX_CELLS;   // row groups of the factorisation
+static_assert(DENSE_GROUPS >= 1, "one thread per (column, row group)");
+
+// shared-memory elements of the dense coarse solve: W (n x (n + 1)) and y = W b
+__host__ __device__ constexpr int dense_elems(int n) {
+  return n > 0 ? n * (n + 1) + DENSE_MAX_CELLS : 0;
+}
+
+// Factor the operator of level L (n cells) into W at `W` (row stride n + 1), using
+// `A` (n x n) as scratch.  Called by a whole block of at least DENSE_GROUPS x
+// DENSE_MAX_CELLS threads (PTPB).  Returns (to every thread) whether all pivots were positive
+// and finite; otherwise W must not be used.
+template <typename T>
+__device__ bool dense_factor(const LevV<T>& L, int n, T* W, T* A) {
+  const int ws = n + 1;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    A[e] = T(0);
+    const int r = e / n, c = e - r * n;
+    W[r * ws + c] = r == c ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int id = threadIdx.x; id < n; id += blockDim.x) {
+    int q[3];
+    bdecomp(L.m, id, q[0], q[1], q[2]);
+    const int st[3] = {1, L.m[0], L.m[0] * L.m[1]};
+    double dt = (double)L.D[id];
+    for (int a = 0; a < 3; ++a) {
+      if (!L.c[a] || L.m[a] < 2) continue;
+      if (q[a] > 0) {
+        dt += (double)L.c[a][id];
+        A[id * n + id - st[a]] = -L.c[a][id];
+      }
+      if (q[a] < L.m[a] - 1) {
+        dt += (double)L.c[a][id + st[a]];
+        A[id * n + id + st[a]] = -L.c[a][id + st[a]];
+      }
+    }
+    A[id * n + id] = (T)dt;
+  }
+  __syncthreads();
+  // step k: rows i > k of the lower triangle, A_ij -= (A_ik / A_kk) A_jk for k < j <= i
+  // (the trailing matrix stays symmetric), and E_ij -= (A_ik / A_kk) E_kj for j <= k.
+  // Thread (g, j): column j, rows k + 1 + g, k + 1 + g + DENSE_GROUPS, ..., taken
+  // DENSE_UNROLL at a time with all loads ahead of the stores (column k and row k of E,
+  // which the step reads, are not written by it).
+  constexpr int DENSE_UNROLL = 8;
+  const int j = threadIdx.x % DENSE_MAX_CELLS, g = threadIdx.x / DENSE_MAX_CELLS;
+  const bool act = g < DENSE_GROUPS && j < n;
+  for (int k = 0; k < n; ++k) {
+    if (act) {
+      const T rp = T(1) / A[k * n + k];
+      const bool upd_a = j > k;
+      const T m = upd_a ? A[j * n + k] * rp : W[k * ws + j] * rp;
+      T* col = upd_a ? A + j : W + j;
+      const int cs = upd_a ? n : ws;
+      for (int i0 = k + 1 + g; i0 < n; i0 += DENSE_GROUPS * DENSE_UNROLL) {
+        T f[DENSE_UNROLL], v[DENSE_UNROLL];
+#pragma unroll
+        for (int u = 0; u < DENSE_UNROLL; ++u) {
+          const int i = i0 + u * DENSE_GROUPS;
+          const bool in = i < n && (!upd_a || j <= i);
+          f[u] = in ? A[i * n + k] : T(0);
+          v[u] = in ? col[i * cs] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < DENSE_UNROLL; ++u) {
+          const int i = i0 + u * DENSE_GROUPS;
+          if (i < n && (!upd_a || j <= i)) col[i * cs] = v[u] - f[u] * m;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // W = diag(d)^-1/2 E with the pivots d_k = A_kk (their scales in A's first column,
+  // which nothing reads any more)
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const T d = A[r * n + r];
+    if (!(d > T(0)) || !(d < T(1e30))) bad = 1;
+    A[r * n] = T(1) / sqrt(d);
+  }
+  __syncthreads();
+  if (act)
+    for (int r = j + g; r < n; r += DENSE_GROUPS) W[r * ws + j] *= A[r * n];
+  __syncthreads();
+  return bad == 0;
+}
+
+// x = W^T (W b) on n <= DENSE_MAX_CELLS cells by the calling block, y = W b held in
+// P.  One thread per cell and product; consecutive threads take consecutive cells, so
+// the padded row stride n + 1 keeps both products free of bank conflicts.
+template <typename T, class G>
+__device__ void dense_apply(const T* W, int n, T* P, const T* b, T* x) {
+  const int ws = n + 1;
+  for (int c = G::tid(); c < n; c += G::n()) {   // y_c = sum_{i <= c} W_ci b_i
+    T s = T(0);
+#pragma unroll 4
+    for (int i = 0; i <= c; ++i) s += W[c * ws + i] * b[i];
+    P[c] = s;
+  }
+  G::sync();
+  for (int c = G::tid(); c < n; c += G::n()) {   // x_c = sum_{r >= c} W_rc y_r
+    T s = T(0);
+#pragma unroll 4
+    for (int r = c; r < n; ++r) s += W[r * ws + c] * P[r];
+    x[c] = s;
+  }
+  G::sync();
+}
+
+// the dense coarsest level of a tail: W and y in shared memory (n = 0: none, the
+// coarsest level is swept)
+template <typename T>
+struct DenseCoarse {
+  const T* W;
+  T* P;
+  int n;
+};
+
 template <typename T>
 __device__ __forceinline__ LevV<T> tail_level(const TailLevels<T>& TL, T* sm, int l, int l0) {
   LevV<T> L = TL.L[l];
@@ -1076,10 +1207,15 @@ __device__ __forceinline__ LevV<T> tail_level(const TailLevels<T>& TL, T* sm, in
 // in shared memory `sm` (layout TL.xo / TL.bo); level l0's b is read from global
 // memory and its x written back there at the end.
 template <typename T>
-__device__ void tail_vcycle(const TailLevels<T>& TL, T* sm, int l0, int nl, int nu, int ncoarse) {
+__device__ void tail_vcycle(const TailLevels<T>& TL, T* sm, int l0, int nl, int nu, int ncoarse,
+                            const DenseCoarse<T>& dc = DenseCoarse<T>{nullptr, nullptr, 0}) {
   for (int l = l0; l < nl - 1; ++l)
     tail_down<T, TailBlock>(tail_level<T>(TL, sm, l, l0), tail_level<T>(TL, sm, l + 1, l0), nu);
-  tail_coarsest<T, TailBlock>(tail_level<T>(TL, sm, nl - 1, l0), ncoarse);
+  {
+    const LevV<T> Lc = tail_level<T>(TL, sm, nl - 1, l0);
+    if (dc.n > 0) dense_apply<T, TailBlock>(dc.W, dc.n, dc.P, Lc.b, Lc.x);
+    else tail_coarsest<T, TailBlock>(Lc, ncoarse);
+  }
   for (int l = nl - 2; l >= l0; --l)
     tail_up<T, TailBlock>(tail_level<T>(TL, sm, l, l0), tail_level<T>(TL, sm, l + 1, l0), nu);
   // the first tail level's x goes back to global memory for the prolongation above
@@ -1200,9 +1336,29 @@ constexpr int THALO = 2 * MG_NU;               // rings: one per half sweep
 // by the autotuner)
 __host__ __device__ constexpr int tile_region(int tx, int ty) { return (tx + 2 * THALO) * (ty + 2 * THALO); }
 
-// dynamic shared memory of the persistent MG-PCG: the tail, then five tile arrays
-static size_t pmg_smem_bytes(int tail_elems, size_t es, int tx, int ty) {
-  return ((size_t)(tail_elems + 3) / 4 * 4 + 5 * (size_t)tile_region(tx, ty)) * es;
+// dynamic shared memory of the persistent MG-PCG (elements): the tail, then the five
+// tile arrays (the dense factorisation's scratch matrix while it runs, before the
+// first V-cycle), then W and the partial sums of a dense coarsest level of dn cells
+struct PmgLayout {
+  int tiles, dw, dp;
+  size_t bytes;
+};
+static PmgLayout pmg_layout(int tail_elems, size_t es, int tx, int ty, int dn) {
+  PmgLayout L;
+  L.tiles = (tail_elems + 3) / 4 * 4;
+  L.dw = L.tiles + std::max(5 * tile_region(tx, ty), dn * dn);
+  L.dp = L.dw + dn * (dn + 1);
+  L.bytes = (size_t)(L.dw + dense_elems(dn)) * es;
+  return L;
+}
+
+// the level solved densely by the persistent V-cycle of an FP32 hierarchy: the first
+// tail level (from lt on) of at most DENSE_MAX_CELLS cells, or -1 (coarsest level swept)
+static int dense_level(const MGLevel* lev, int lt, int nlev, bool f32) {
+  if (!f32) return -1;
+  for (int l = lt; l < nlev; ++l)
+    if (lev[l].N <= DENSE_MAX_CELLS) return l;
+  return -1;
 }
 
 template <typename T>
@@ -1341,6 +1497,7 @@ struct MgArgs {
   const T* z0;                 // level-0 iterate at the end of a V-cycle (z = M r)
   int tx, ty;                  // tile shape of the temporal blocking
   int nlev, lt, ncoarse;       // levels, first tail level, coarsest-level sweeps
+  int dn, dw, dp;              // dense coarsest level: cells (0: swept), smem offsets of W and sums
   double* part;
   double* stat;
   int* done;
@@ -1469,6 +1626,11 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
     if (l < a.nlev || l >= 2) ok = sync(h, 0);
     if (!ok) result = 3;
   }
+  // the dense coarsest level, factored once per solve by block 0 (tile arrays as scratch)
+  DenseCoarse<T> dc{nullptr, nullptr, 0};
+  if (blockIdx.x == 0 && a.dn > 0 && ok && result != 1) {
+    if (dense_factor<T>(a.TL.L[a.nlev - 1], a.dn, sm + a.dw, S.x)) dc = DenseCoarse<T>{sm + a.dw, sm + a.dp, a.dn};
+  }
   for (; ok && result != 1;) {
     double v[3] = {0.0, 0.0, 0.0};
     const bool tiled0 = lt > 0 && L0.m[2] == 1;
@@ -1534,7 +1696,7 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
     }
     if (!ok) { result = 3; break; }
     // the tail levels in block 0, out of shared memory
-    if (blockIdx.x == 0) tail_vcycle<T>(a.TL, sm, lt, a.nlev, MG_NU, a.ncoarse);
+    if (blockIdx.x == 0) tail_vcycle<T>(a.TL, sm, lt, a.nlev, MG_NU, a.ncoarse, dc);
     if (!sync(v, 0)) { result = 3; break; }
     // V-cycle up: prolongation and post-smoothing on the grid levels
     for (int l = lt - 1; l >= 0 && ok; --l) {
@@ -2031,7 +2193,10 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
     // the persistent MG-PCG: its own (smaller) tail; co-resident blocks at that size
     int ltp = nlev - 1;
     while (ltp > 0 && lev[ltp - 1].N <= PMG_TAIL_MAX_CELLS) --ltp;
-    const size_t psm = pmg_smem_bytes((int)tail_layout(lev, ltp, nlev, es, nullptr, nullptr), es, 32, 32);
+    const int lcp = dense_level(lev, ltp, nlev, fp32);
+    const int nlp = lcp >= 0 ? lcp + 1 : nlev;
+    const size_t psm = pmg_layout((int)tail_layout(lev, ltp, nlp, es, nullptr, nullptr), es, 32, 32,
+                                  lcp >= 0 ? (int)lev[lcp].N : 0).bytes;
     int nsm = 0, per = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     // (dynamic limit: the opt-in maximum less the kernel's static shared memory)
@@ -2196,11 +2361,13 @@ int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* 
   for (int l = 0; l < nlev; ++l) a.TL.L[l] = lv<T>(lev[l]);
   int lt = nlev - 1;
   while (lt > 0 && lev[lt - 1].N <= PMG_TAIL_MAX_CELLS) --lt;
-  a.nlev = nlev;
+  const int ldn = dense_level(lev, lt, nlev, f32);
+  a.nlev = ldn >= 0 ? ldn + 1 : nlev;
+  a.dn = ldn >= 0 ? (int)lev[ldn].N : 0;
   a.lt = lt;
   a.ncoarse = 4;
   a.z0 = (lt > 0 && lev[0].m[2] == 1) ? (const T*)lev[0].xp : (const T*)lev[0].x;
-  a.TL.total = (int)tail_layout(lev, lt, nlev, sizeof(T), a.TL.xo, a.TL.bo);
+  a.TL.total = (int)tail_layout(lev, lt, a.nlev, sizeof(T), a.TL.xo, a.TL.bo);
   a.part = part;
   a.stat = sc;
   a.done = done;
@@ -2208,11 +2375,14 @@ int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* 
   a.err = err;
   a.tx = mg_tile[0];
   a.ty = mg_tile[1];
-  size_t smem = pmg_smem_bytes(a.TL.total, sizeof(T), a.tx, a.ty);
-  if (smem > pmg_smem_max) {   // the chosen tile does not fit: the default one does
+  PmgLayout pl = pmg_layout(a.TL.total, sizeof(T), a.tx, a.ty, a.dn);
+  if (pl.bytes > pmg_smem_max) {   // the chosen tile does not fit: the default one does
     a.tx = a.ty = 32;
-    smem = pmg_smem_bytes(a.TL.total, sizeof(T), a.tx, a.ty);
+    pl = pmg_layout(a.TL.total, sizeof(T), a.tx, a.ty, a.dn);
   }
+  a.dw = pl.dw;
+  a.dp = pl.dp;
+  const size_t smem = pl.bytes;
   int grid = (int)((s.N + PTPB - 1) / PTPB);
   if (grid > pmg_blocks) grid = pmg_blocks;
   if (sm_budget > 0) grid = std::min(grid, sm_budget * std::max(1, pmg_blocks / nsm_));
