@@ -97,7 +97,7 @@ typedef struct droplet_config {
                            the persistent multigrid smoothing on 2D levels; {0, 0}: 32 x 32,
                            or the autotuner's choice where it runs.  Owned cells get the same
                            values whatever the tile: a pure performance setting.  Each entry
-                           0 or 8 .. 256.                                                   */
+                           0 or 8 .. 256; an odd entry is rounded up to the next even one. */
 } droplet_config;
 
 /* Diagnostics of one droplet after the last completed step (Sec. 4 reports

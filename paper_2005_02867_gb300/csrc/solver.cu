@@ -1328,17 +1328,21 @@ __device__ __forceinline__ void grid_prolong_black(const LevV<T>& F, const LevV<
 // Half sweep s updates the cells within THALO - s rings of the tile (clipped to the
 // level), which read only cells updated by half sweep s - 1, so the tile's cells end
 // with exactly the values of the level-wide sweeps (same arithmetic, same order) and a
-// whole pre- or post-smoothing costs one grid barrier instead of 2 nu.
+// whole pre- or post-smoothing costs one grid barrier instead of 2 nu.  One ring more
+// than the half sweeps need leaves the owned cells' neighbours exact too, so the
+// pre-smoothing phase also forms the owned cells' residuals and restricts them into
+// the coarse right-hand side (tiles are even, so 2 x 2 aggregates never straddle two).
 constexpr int MG_NU = 2;                       // red-black sweeps before and after
-constexpr int THALO = 2 * MG_NU;               // rings: one per half sweep
+constexpr int THALO = 2 * MG_NU + 1;           // rings: one per half sweep, plus one
 
 // cells of the region of a tx x ty tile (the tile shape is a launch parameter, chosen
 // by the autotuner)
 __host__ __device__ constexpr int tile_region(int tx, int ty) { return (tx + 2 * THALO) * (ty + 2 * THALO); }
+constexpr int TILE_ARRAYS = 6;                 // x, b, 1 / diag, c0, c1, D
 
-// dynamic shared memory of the persistent MG-PCG (elements): the tail, then the five
-// tile arrays (the dense factorisation's scratch matrix while it runs, before the
-// first V-cycle), then W and the partial sums of a dense coarsest level of dn cells
+// dynamic shared memory of the persistent MG-PCG (elements): the tail, then the
+// TILE_ARRAYS tile arrays (the dense factorisation's scratch matrix while it runs,
+// before the first V-cycle), then W and y of a dense coarsest level of dn cells
 struct PmgLayout {
   int tiles, dw, dp;
   size_t bytes;
@@ -1346,7 +1350,7 @@ struct PmgLayout {
 static PmgLayout pmg_layout(int tail_elems, size_t es, int tx, int ty, int dn) {
   PmgLayout L;
   L.tiles = (tail_elems + 3) / 4 * 4;
-  L.dw = L.tiles + std::max(5 * tile_region(tx, ty), dn * dn);
+  L.dw = L.tiles + std::max(TILE_ARRAYS * tile_region(tx, ty), dn * dn);
   L.dp = L.dw + dn * (dn + 1);
   L.bytes = (size_t)(L.dw + dense_elems(dn)) * es;
   return L;
@@ -1363,7 +1367,7 @@ static int dense_level(const MGLevel* lev, int lt, int nlev, bool f32) {
 
 template <typename T>
 struct TileSmem {
-  T *x, *b, *idg, *c0, *c1;
+  T *x, *b, *idg, *c0, *c1, *D;
 };
 
 struct TileBox {
@@ -1419,13 +1423,40 @@ __device__ void tile_sweeps(const TileSmem<T>& S, const TileBox& B, int m0, int 
   }
 }
 
-// operator of a tile region into shared memory
+// operator of a tile region into shared memory (with D: for the residual)
 template <typename T>
 __device__ __forceinline__ void tile_load_op(const TileSmem<T>& S, const TileBox& B, const LevV<T>& F, int c,
-                                             long long g) {
+                                             long long g, bool withD = false) {
   S.idg[c] = F.idg[g];
   S.c0[c] = F.c[0][g];
   S.c1[c] = F.c[1][g];
+  if (withD) S.D[c] = F.D[g];
+}
+
+// residual b - A x of the owned cells of a pre-smoothed tile, restricted (summed over
+// each 2 x 2 aggregate) into C.b: mg_resid's arithmetic and grid_restrict's order on
+// the values the tile holds
+template <typename T>
+__device__ void tile_restrict(const TileSmem<T>& S, const TileBox& B, int m0, int m1, const LevV<T>& C) {
+  const int cw = (B.oi1 - B.oi0) / 2, n = cw * ((B.oj1 - B.oj0) / 2);
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int JJ = t / cw;
+    const int I = B.oi0 / 2 + (t - JJ * cw), J = B.oj0 / 2 + JJ;
+    T s = 0;
+    for (int dj = 0; dj < 2; ++dj)
+      for (int di = 0; di < 2; ++di) {
+        const int i = 2 * I + di, j = 2 * J + dj;
+        const int c = (i - B.i0) + B.rx * (j - B.j0);
+        const T xp = S.x[c];
+        T y = S.D[c] * xp;
+        if (i > 0) y += S.c0[c] * (xp - S.x[c - 1]);
+        if (i < m0 - 1) y += S.c0[c + 1] * (xp - S.x[c + 1]);
+        if (j > 0) y += S.c1[c] * (xp - S.x[c - B.rx]);
+        if (j < m1 - 1) y += S.c1[c + B.rx] * (xp - S.x[c + B.rx]);
+        s += S.b[c] - y;
+      }
+    ((T*)C.b)[(long long)I + (long long)C.m[0] * J] = s;
+  }
 }
 
 template <typename T>
@@ -1438,9 +1469,10 @@ __device__ __forceinline__ void tile_store_x(const TileSmem<T>& S, const TileBox
   }
 }
 
-// pre-smoothing of a 2D level l >= 1 (b from the restriction), tile by tile
+// pre-smoothing of a 2D level l >= 1 (b from the restriction), tile by tile, and the
+// restriction of its residual into C.b
 template <typename T>
-__device__ void tiled_pre(const TileSmem<T>& S, const LevV<T>& F, int TX, int TY) {
+__device__ void tiled_pre(const TileSmem<T>& S, const LevV<T>& F, const LevV<T>& C, int TX, int TY) {
   const int m0 = F.m[0], m1 = F.m[1];
   for (int t = blockIdx.x; t < tile_count(m0, m1, TX, TY); t += gridDim.x) {
     const TileBox B = tile_box(m0, m1, t, TX, TY);
@@ -1449,11 +1481,12 @@ __device__ void tiled_pre(const TileSmem<T>& S, const LevV<T>& F, int TX, int TY
       const int lj = c / B.rx;
       const long long g = (long long)(B.i0 + c - lj * B.rx) + (long long)m0 * (B.j0 + lj);
       S.b[c] = F.b[g];
-      tile_load_op<T>(S, B, F, c, g);
+      tile_load_op<T>(S, B, F, c, g, true);
     }
     __syncthreads();
     tile_sweeps<T>(S, B, m0, m1, true);
     tile_store_x<T>(S, B, m0, F.x);
+    tile_restrict<T>(S, B, m0, m1, C);
     __syncthreads();
   }
 }
@@ -1507,8 +1540,9 @@ struct MgArgs {
 
 // Phase A on a 2D level 0: the CG update (x, p of the tile's cells; r and q of the
 // tile region into the other buffers, halo cells recomputed from the neighbours'
-// current values), b = r, and the whole pre-smoothing of the tile.  Returns the
-// block's share of |r_new|^2 over its owned cells.
+// current values), b = r, the whole pre-smoothing of the tile and the restriction of
+// its residual into level 1.  Returns the block's share of |r_new|^2 over its owned
+// cells.
 template <typename T>
 __device__ double tiled_phase_a(const TileSmem<T>& S, const MgArgs<T>& a, int cur, int its, double alpha,
                                 double beta) {
@@ -1543,11 +1577,12 @@ __device__ double tiled_phase_a(const TileSmem<T>& S, const MgArgs<T>& a, int cu
       const T bP = (T)rP;
       S.b[c] = bP;
       if (own) ((T*)L0.b)[g] = bP;
-      tile_load_op<T>(S, B, L0, c, g);
+      tile_load_op<T>(S, B, L0, c, g, true);
     }
     __syncthreads();
     tile_sweeps<T>(S, B, m0, m1, true);
     tile_store_x<T>(S, B, m0, L0.x);
+    tile_restrict<T>(S, B, m0, m1, a.TL.L[1]);
     __syncthreads();
   }
   return rr;
@@ -1566,6 +1601,7 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
     S.idg = tb + 2 * treg;
     S.c0 = tb + 3 * treg;
     S.c1 = tb + 4 * treg;
+    S.D = tb + 5 * treg;
   }
   __shared__ double bc[2];
   const int gs = gridDim.x * blockDim.x;
@@ -1673,8 +1709,9 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
     bool ok = true;
     for (int l = 0; l < lt && ok; ++l) {
       const LevV<T>& F = a.TL.L[l];
-      const bool tl = F.m[2] == 1;
-      if (!tl) {   // level-wide half sweeps (the red half sweep of sweep 0 came before)
+      const LevV<T>& C = a.TL.L[l + 1];
+      if (F.m[2] > 1) {   // 3D: level-wide half sweeps (the red half sweep of sweep 0
+                          // came before), then the restriction with C's first red half sweep
         for (int s = 0; s < MG_NU && ok; ++s) {
           if (s > 0) {
             grid_half_sweep<T>(F, 0, 0, gid, gs);
@@ -1684,13 +1721,13 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
           ok = ok && sync(v, 0);
         }
         if (!ok) break;
+        grid_restrict<T>(F, C, l + 1 < lt, gid, gs);
+        ok = sync(v, 0);
+        continue;
       }
-      const LevV<T>& C = a.TL.L[l + 1];
-      const bool ctl = l + 1 < lt && C.m[2] == 1;
-      grid_restrict<T>(F, C, l + 1 < lt && !ctl, gid, gs);
-      ok = sync(v, 0);
-      if (ok && ctl) {
-        tiled_pre<T>(S, C, a.tx, a.ty);
+      // 2D: F's tiled phase restricted into C.b; C's own tiled phase restricts further
+      if (l + 1 < lt) {
+        tiled_pre<T>(S, C, a.TL.L[l + 2], a.tx, a.ty);
         ok = sync(v, 0);
       }
     }
@@ -2373,8 +2410,8 @@ int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* 
   a.done = done;
   a.bar = bar;
   a.err = err;
-  a.tx = mg_tile[0];
-  a.ty = mg_tile[1];
+  a.tx = (mg_tile[0] + 1) & ~1;   // even: the fused restriction's aggregates stay in a tile
+  a.ty = (mg_tile[1] + 1) & ~1;
   PmgLayout pl = pmg_layout(a.TL.total, sizeof(T), a.tx, a.ty, a.dn);
   if (pl.bytes > pmg_smem_max) {   // the chosen tile does not fit: the default one does
     a.tx = a.ty = 32;
