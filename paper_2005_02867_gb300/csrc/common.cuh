@@ -273,12 +273,54 @@ __device__ inline double cubic_largest(double c2, double c1, double c0) {
   return t - c2 * third;
 }
 
+// The same root, refined instead of formed in binary64: Cardano's formula in binary32
+// gives an estimate z0 within a few binary32 ulps of a well-separated largest root; a
+// fixed-slope Newton iteration z <- z - f(z) / f'(z0) in binary64 (f evaluated in
+// binary64, the slope rounded to binary32) contracts the error by about
+// |f'(z0) - f'(z*)| / f'(z*) per step, which three steps take to rounding level.  The
+// binary64 formula is used instead where the estimate is not clearly at a simple root
+// (f'(z0) not well above zero: near a double root, where the contraction fails) or the
+// last step still moved the root by more than 1e-8 relative.
+__device__ inline double cubic_largest_refined(double c2, double c1, double c0) {
+  const float a2 = f32_rn(c2), a1 = f32_rn(c1), a0 = f32_rn(c0);
+  constexpr float third = 1.f / 3.f, twentyseventh = 1.f / 27.f;
+  const float pp = a1 - a2 * a2 * third;
+  const float qq = 2.f * a2 * a2 * a2 * twentyseventh - a2 * a1 * third + a0;
+  const float disc = 0.25f * qq * qq + pp * pp * pp * twentyseventh;
+  float t;
+  if (disc > 0.f) {
+    const float h = -0.5f * qq;
+    const float w = h + copysignf(sqrtf(disc), h);
+    const float u = copysignf(cbrtf(fabsf(w)), w);
+    t = (u != 0.f) ? u - pp / (3.f * u) : 0.f;
+  } else if (pp == 0.f) {
+    t = 0.f;
+  } else {
+    const float m = 2.f * sqrtf(-pp * third);
+    const float arg = fminf(1.f, fmaxf(-1.f, 3.f * qq / (pp * m)));
+    t = m * cosf(acosf(arg) * third);
+  }
+  const float z0 = t - a2 * third;
+  const float fp = (3.f * z0 + 2.f * a2) * z0 + a1;
+  const float scale = 3.f * z0 * z0 + fabsf(2.f * a2 * z0) + fabsf(a1);
+  if (!(fp > 1e-3f * scale)) return cubic_largest(c2, c1, c0);
+  const double r = f64_of(1.f / fp);
+  double z = f64_of(z0), dz = 0.0;
+#pragma unroll
+  for (int it = 0; it < 3; ++it) {
+    dz = (((z + c2) * z + c1) * z + c0) * r;
+    z -= dz;
+  }
+  if (!(fabs(dz) <= 1e-8 * fabs(z))) return cubic_largest(c2, c1, c0);
+  return z;
+}
+
 // binary (fuel, inert) Peng-Robinson compressibility alone (the vapour root), for the
-// gas density: the same arithmetic as pr_binary's Z without the fugacity terms
+// gas density: pr_binary's cubic, its root refined (cubic_largest_refined)
 __device__ inline double pr_binary_Z(const Phys& p, double T, double P, double y) {
   double A, B, a0, a01, am, bm;
   pr_mix_AB(p, T, P, y, A, B, a0, a01, am, bm);
-  return cubic_largest(-(1.0 - B), A - 3.0 * B * B - 2.0 * B, -(A * B - B * B - B * B * B));
+  return cubic_largest_refined(-(1.0 - B), A - 3.0 * B * B - 2.0 * B, -(A * B - B * B - B * B * B));
 }
 
 // binary (fuel, inert) Peng-Robinson: vapour Z and ln phi_hat of the fuel at mole fraction y

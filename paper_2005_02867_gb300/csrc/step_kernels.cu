@@ -811,7 +811,7 @@ __global__ void k_add(long long n, double* y, const double* x) {
 // sums: alpha V, mdot V, T |grad alpha| V, |grad alpha| V, (1-alpha) rhoG omega V, open-boundary vapour outflow
 // maxima: |u|, alpha, -alpha
 template <int NA>
-__global__ void k_diag(Geo g, const double* alpha, const double* T, const double* mdot, const double* omega,
+__global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, const double* T, const double* mdot, const double* omega,
                        const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum,
                        double* pmax) {
   double s[6] = {0, 0, 0, 0, 0, 0};

@@ -113,7 +113,7 @@ __device__ __forceinline__ float cellg_f(const Geo& g, const double* f, int i, i
 }
 
 template <int C, int NA>
-__global__ void k_mom_assemble_mx(Geo g, Phys p, const double* u0, const double* u1, const double* u2,
+__global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const double* u0, const double* u1, const double* u2,
                                   const double* rho, const double* mu, const double* pr, const double* alpha,
                                   const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
   constexpr int c = C;
