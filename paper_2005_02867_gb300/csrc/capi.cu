@@ -212,8 +212,9 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
   // latency-bound sizes: persistent solvers (in a batch each droplet is later given an
   // SM budget so that the cooperative solves of all branches fit the GPU together)
   c->solver.persistent = N <= Solver::PERSIST_MAX_CELLS;
+  c->solver.persist_pcg = N <= (c->solver.f32_helm ? Solver::PERSIST_PCG_MAX_CELLS : Solver::PERSIST_MAX_CELLS);
   // the velocity components are solved together (one persistent launch)
-  const bool joint = c->solver.persistent && (cfg.physics_mask & DROPLET_PHYS_FLOW);
+  const bool joint = c->solver.persist_pcg && (cfg.physics_mask & DROPLET_PHYS_FLOW);
   c->solver.nsys_extra = joint ? nact(c->g) - 1 : 0;
   for (int k = 0; k < c->solver.nsys_extra; ++k)
     for (int q = 0; q < 6; ++q)
@@ -346,7 +347,7 @@ static int one_step(dctx* c, int* nc_flag) {
   ++g_launches, k_rhoG<<<gc, TPB, 0, st>>>(g, p, c->T, c->omega, c->rhoG);
   // S7 - S10
   if (mask & DROPLET_PHYS_FLOW) {
-    if (c->solver.persistent && c->solver.nsys_extra == na - 1 && (na == 1 || c->xb[na - 2][5])) {
+    if (c->solver.persist_pcg && c->solver.nsys_extra == na - 1 && (na == 1 || c->xb[na - 2][5])) {
       // the components' systems are independent (each is assembled from the old
       // velocities): assemble all, solve them together, scatter all
       BoxSys sys[3];
@@ -642,7 +643,7 @@ extern "C" int droplet_init(const droplet_config* cfgs, int n_droplets, void* cu
       }
       for (int i = 0; i < n_droplets; ++i) c->d[i]->solver.sm_budget = bud[i];
     } else {
-      for (auto x : c->d) x->solver.persistent = false;
+      for (auto x : c->d) x->solver.persistent = x->solver.persist_pcg = false;
     }
     c->ev.resize(n_droplets + 1);
     for (auto& e : c->ev)

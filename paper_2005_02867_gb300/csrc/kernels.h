@@ -175,7 +175,8 @@ class Solver {
   cudaStream_t stream2 = nullptr;   // captures the bodies of the device-driven solver loops
   bool capturing = false;           // the step is being captured into a CUDA graph
   bool f32_helm = false;            // Jacobi-PCG as FP32 defect correction (set before setup)
-  bool persistent = false;          // Jacobi-PCG in one cooperative launch (set before setup)
+  bool persistent = false;          // MG-PCG in one cooperative launch (set before setup)
+  bool persist_pcg = false;         // Jacobi-PCG in one cooperative launch (set before setup)
   int nsys_extra = 0;               // further systems a joint persistent solve may carry (set before setup)
   // K (<= 1 + nsys_extra) independent Helmholtz systems in one persistent launch; the
   // statistics of system k go to recs[k]
@@ -183,7 +184,11 @@ class Solver {
   int sm_budget = 0;                // SMs the persistent solves may use (0: the whole GPU)
   int mg_tile[2] = {32, 32};        // tile of the persistent MG's temporal blocking (autotuned)
   size_t pmg_smem_max = 0;          // dynamic shared memory the persistent MG may request
-  static constexpr long long PERSIST_MAX_CELLS = 1LL << 22;   // latency-bound sizes only
+  static constexpr long long PERSIST_MAX_CELLS = 1LL << 22;   // persistent MG: latency-bound sizes only
+  // persistent FP32 Jacobi-PCG: one fused pass and one grid barrier per iteration pays at
+  // every size (32-bit cell indices); the FP64 one (one block per SM) only up to
+  // PERSIST_MAX_CELLS
+  static constexpr long long PERSIST_PCG_MAX_CELLS = 1LL << 30;
   int rb = RED_BLOCKS;              // block cap of the reduction kernels (tuned for batches)
   Prof* prof = nullptr;
 

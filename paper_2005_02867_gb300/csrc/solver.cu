@@ -1881,13 +1881,13 @@ int Solver::setup(long long maxN, cudaStream_t s) {
     for (auto q : fa) CK(cudaMalloc((void**)q, bf));
   }
   if (persistent) CK(cudaMalloc(&mg_q2, sizeof(double) * (size_t)maxN));
-  if (persistent)
+  if (persist_pcg)
     for (int k = 0; k < nsys_extra; ++k) {
       CK(cudaMalloc(&r64x[k], sizeof(double) * (size_t)maxN));
       for (int q = 0; q < PERSIST_VECTORS; ++q)
         CK(cudaMalloc(&pwx[k][q], (f32_helm ? sizeof(float) : sizeof(double)) * (size_t)maxN));
     }
-  if (persistent)
+  if (persist_pcg)
     for (int q = 0; q < PERSIST_VECTORS; ++q) CK(cudaMalloc(&pw[q], (f32_helm ? sizeof(float) : sizeof(double)) * (size_t)maxN));
   return 0;
 }
@@ -2071,7 +2071,7 @@ int Solver::pcg_persist(const BoxSys* sys, int K, double rtol, int maxit, const 
 
 int Solver::pcg_jacobi_multi(const BoxSys* s, int K, double rtol, int maxit, const RecordSpec* recs,
                              SolveStats* out) {
-  if (!persistent || K < 1 || K > 1 + nsys_extra) return DROPLET_ERR_ARG;
+  if (!persist_pcg || K < 1 || K > 1 + nsys_extra) return DROPLET_ERR_ARG;
   recorded = false;
   rec_scal = nullptr;
   return f32_helm ? pcg_persist<float>(s, K, rtol, maxit, recs, out) : pcg_persist<double>(s, K, rtol, maxit, recs, out);
@@ -2091,7 +2091,7 @@ int Solver::persist_blocks(bool f32) {
 }
 
 int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
-  if (persistent) {
+  if (persist_pcg) {
     const RecordSpec rec = take_record();
     return f32_helm ? pcg_persist<float>(&s, 1, rtol, maxit, &rec, out) : pcg_persist<double>(&s, 1, rtol, maxit, &rec, out);
   }
