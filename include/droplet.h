@@ -286,6 +286,15 @@ int droplet_load(droplet_ctx* ctx, const char* path);
  * n > 2^30), DROPLET_ERR_NOMEM, DROPLET_ERR_CUDA. */
 int droplet_round_f32(const double* in, float* out32, double* back64, size_t n);
 
+/* The binary64 reciprocal the step kernels use in place of a division (a binary32
+ * seed refined by two Newton-Raphson steps; a division outside binary32's normal
+ * range), applied on the device to n doubles of the host array `in`, results in the
+ * host array `out`.  No counterpart in the paper: it exists so that the reciprocal
+ * can be checked against the correctly rounded 1 / x (at most one ulp apart).  Runs
+ * on the current device and synchronises.  Errors: DROPLET_ERR_ARG (a NULL array or
+ * n > 2^30), DROPLET_ERR_NOMEM, DROPLET_ERR_CUDA. */
+int droplet_rcp_f64(const double* in, double* out, size_t n);
+
 /* Block until all work enqueued by the context has finished. */
 int droplet_sync(droplet_ctx* ctx);
 

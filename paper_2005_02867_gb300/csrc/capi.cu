@@ -131,6 +131,9 @@ static void make_phys(const droplet_config& c, Phys& p) {
   p.pr_sqac01 = std::sqrt(p.pr_ac[0] * p.pr_ac[1]) * (1.0 - c.kij);
   p.iM_l = 1.0 / c.M_l;
   p.iM_g = 1.0 / c.M_g;
+  p.cc_LMR = c.Lv * c.M_l / R_GAS;
+  p.iTb = 1.0 / c.Tb;
+  p.irho_l = 1.0 / c.rho_l;
 }
 
 static int dalloc(double** q, long long n) {

@@ -51,6 +51,8 @@ struct Phys {
   // sqrt(a_c0 a_c1) (1 - k_ij); inverse molar masses
   double pr_ac[2], pr_b[2], pr_k[2], pr_iTc[2], pr_sqac01;
   double iM_l, iM_g;
+  // Clausius-Clapeyron exponent L M_l / R and 1 / T_b; 1 / rho_l
+  double cc_LMR, iTb, irho_l;
 };
 
 __host__ __device__ inline int nact(const Geo& g) { return g.act3 ? 3 : 2; }
@@ -207,6 +209,23 @@ __device__ __forceinline__ double f64_of(float x) {
   return (double)x;
 }
 
+// 1 / x in binary64 without the division sequence (GB300 retires about two binary64
+// operations per SM clock, and a division takes a dozen): the binary32 reciprocal of x,
+// rounded to nearest, as the seed of the Newton-Raphson iteration for f(y) = 1/y - x,
+// y <- y + y (1 - x y) (each step squares the relative error: 2^-24, 2^-48, then below
+// binary64 rounding; the result lies within one ulp of the correctly rounded 1 / x).
+// Outside binary32's normal range (zero, subnormal, huge, inf, NaN) it divides.
+__device__ __forceinline__ double rcp64(double x) {
+  const float xf = f32_rn(x);
+  const float ax = fabsf(xf);
+  if (!(ax >= 1.5e-38f && ax <= 1.5e38f)) return 1.0 / x;
+  double y = f64_of(__frcp_rn(xf));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 // ------------------------------------------------------------------ small formulas
 __device__ __forceinline__ double minmod(double x, double y) {
   return (x * y > 0.0) ? (x > 0.0 ? fmin(fabs(x), fabs(y)) : -fmin(fabs(x), fabs(y))) : 0.0;
@@ -219,14 +238,14 @@ __device__ __forceinline__ double van_leer(double uu, double u, double d) {
 
 // ------------------------------------------------------------------ thermodynamics
 __device__ __forceinline__ double psat(const Phys& p, double T) {
-  return P_ATM * exp((p.Lv * p.M_l / R_GAS) * (1.0 / p.Tb - 1.0 / T));
+  return P_ATM * exp(p.cc_LMR * (p.iTb - rcp64(T)));
 }
 __device__ __forceinline__ double Y_from_y(const Phys& p, double y) {
   return y * p.M_l / (y * p.M_l + (1.0 - y) * p.M_g);
 }
 __device__ __forceinline__ double y_from_Y(const Phys& p, double Y) {
   const double m = Y * p.iM_l;
-  return m / (m + (1.0 - Y) * p.iM_g);
+  return m * rcp64(m + (1.0 - Y) * p.iM_g);
 }
 
 // Peng-Robinson pure-component alpha factor sqrt(alpha(T)) = 1 + kappa (1 - sqrt(T / Tc))
@@ -245,7 +264,7 @@ __device__ __forceinline__ void pr_mix_AB(const Phys& p, double T, double P, dou
   const double y1 = 1.0 - y;
   am = y * y * a0 + y * y1 * a01 + y1 * y * a01 + y1 * y1 * a1;
   bm = y * p.pr_b[0] + y1 * p.pr_b[1];
-  const double iRT = 1.0 / (R_GAS * T);
+  const double iRT = rcp64(R_GAS * T);
   A = am * P * iRT * iRT;
   B = bm * P * iRT;
 }
@@ -370,7 +389,7 @@ __device__ inline double rho_gas(const Phys& p, double T, double Y) {
   double inv_m = Y * p.iM_l + (1.0 - Y) * p.iM_g;
   double Z = 1.0;
   if (p.eq_model != 0) Z = pr_binary_Z(p, T, p.P, y_from_Y(p, Y));
-  return p.P / (Z * R_GAS * T * inv_m);
+  return p.P * rcp64(Z * R_GAS * T * inv_m);
 }
 
 // ------------------------------------------------------------------ reductions

@@ -237,7 +237,7 @@ __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double*
   double cap = p.rho_l * a * p.idt;
   if (m > cap) { m = cap; atomicOr(flags, (unsigned)DROPLET_FLAG_MDOT_CAPPED); }
   mdot[id] = m;
-  alpha_star[id] = a - p.dt * m / p.rho_l;
+  alpha_star[id] = a - p.dt * m * p.irho_l;
 }
 
 // ============================================================== S3 alpha advection (FCT)
@@ -294,7 +294,7 @@ __global__ void k_adv_low(Geo g, const double* as, const double* F0, const doubl
   if (id >= g.N) return;
   int i, j, k;
   decomp(id, g.n[0], g.n[1], i, j, k);
-  aL[id] = as[id] - face_net(g, F0, F1, F2, i, j, k) / cellV(g, i);
+  aL[id] = as[id] - face_net(g, F0, F1, F2, i, j, k) * rcp64(cellV(g, i));
 }
 
 // Zalesak limiter ratios R+ and R- from the local bounds over the cell and its face neighbours.
@@ -333,8 +333,8 @@ __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const dou
   }
   double V = cellV(g, i);
   double Qp = (amax - aL[id]) * V, Qm = (aL[id] - amin) * V;
-  Rp[id] = Pp > 0.0 ? fmin(1.0, fmax(0.0, Qp / Pp)) : 0.0;
-  Rm[id] = Pm > 0.0 ? fmin(1.0, fmax(0.0, Qm / Pm)) : 0.0;
+  Rp[id] = Pp > 0.0 ? fmin(1.0, fmax(0.0, Qp * rcp64(Pp))) : 0.0;
+  Rm[id] = Pm > 0.0 ? fmin(1.0, fmax(0.0, Qm * rcp64(Pm))) : 0.0;
 }
 
 __device__ __forceinline__ double limited_flux(const Geo& g, int a, const double* A, const double* Rp,
@@ -366,7 +366,7 @@ __global__ void k_adv_update(Geo g, const double* aL, const double* A0, const do
       s += limited_flux(g, a, AA[a], Rp, Rm, hi[0], hi[1], hi[2]) - limited_flux(g, a, AA[a], Rp, Rm, i, j, k);
     }
     double V = cellV(g, i);
-    double an = aL[id] - s / V;
+    double an = aL[id] - s * rcp64(V);
     double ac = fmin(1.0, fmax(0.0, an));
     if (ac != an) { acc[1] += 1.0; acc[0] += (an - ac) * V; }
     alpha[id] = ac;
@@ -746,8 +746,8 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
     double gr = (cellg(g, rgn, qp[0], qp[1], qp[2], R_ZG, 0, 0, 0, 0) - cellg(g, rgn, qm[0], qm[1], qm[2], R_ZG, 0, 0, 0, 0)) * (0.5 * g.ih[a]);
     adv = adv + vc * gr;
   }
-  double rn = rgn[id];
-  double s = mdot[id] * (1.0 / rn - 1.0 / p.rho_l) - (1.0 - alpha[id]) / rn * ((rn - rgo[id]) * p.idt + adv);
+  double rn = rgn[id], irn = rcp64(rn);
+  double s = mdot[id] * (irn - p.irho_l) - (1.0 - alpha[id]) * irn * ((rn - rgo[id]) * p.idt + adv);
   S[id] = s;
   double dg = 0.0, div = 0.0;
   double rP = rho[id];
@@ -760,8 +760,8 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
     if (ci[a] > 0) {
       int Lc[3] = {i, j, k};
       Lc[a] -= 1;
-      double rf = 0.5 * (rho[cidx(g, Lc[0], Lc[1], Lc[2])] + rP);
-      cl = faceA(g, a, i) * g.ih[a] / rf;
+      // A / h over the mean density of the two cells
+      cl = faceA(g, a, i) * g.ih[a] * (2.0 * rcp64(rho[cidx(g, Lc[0], Lc[1], Lc[2])] + rP));
     }
     C[a][id] = cl;
     if (ci[a] == 0 && g.bc[a][0] == BC_OPEN) dg += faceA(g, a, i) * (2.0 * g.ih[a]) / rP;
@@ -771,7 +771,8 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
   rhs[id] = (s * cellV(g, i) - div) * p.idt;
 }
 
-// u = u* - dt beta_f (dp_R - dp_L)/A_f with dp = 0 beyond open faces (half-cell distance)
+// u = u* - dt beta_f (dp_R - dp_L)/A_f with dp = 0 beyond open faces (half-cell distance);
+// beta_f / A_f = 1 / (h rho_f)
 template <int C>
 __global__ void k_correct(Geo g, Phys p, const double* us, const double* dp, const double* rho, double* u) {
   constexpr int c = C;
@@ -788,14 +789,13 @@ __global__ void k_correct(Geo g, Phys p, const double* us, const double* dp, con
     L[c] -= 1;
     if (f[c] > 0 && f[c] < g.n[c]) {
       long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, f[0], f[1], f[2]);
-      double beta = A * g.ih[c] / (0.5 * (rho[li] + rho[ri]));
-      corr = p.dt * beta * (dp[ri] - dp[li]) / A;
+      corr = p.dt * g.ih[c] * (2.0 * rcp64(rho[li] + rho[ri])) * (dp[ri] - dp[li]);
     } else {
       int side = f[c] == 0 ? 0 : 1;
       if ((side ? g.bc[c][1] : g.bc[c][0]) == BC_OPEN) {
         long long pi = side ? cidx(g, L[0], L[1], L[2]) : cidx(g, f[0], f[1], f[2]);
-        double beta = A * (2.0 * g.ih[c]) / rho[pi];
-        corr = side ? p.dt * beta * (0.0 - dp[pi]) / A : p.dt * beta * (dp[pi] - 0.0) / A;
+        const double bA = (2.0 * g.ih[c]) * rcp64(rho[pi]);
+        corr = side ? p.dt * bA * (0.0 - dp[pi]) : p.dt * bA * (dp[pi] - 0.0);
       }
     }
   }

@@ -476,6 +476,12 @@ __global__ void k_round_f32(const double* in, float* out32, double* back64, long
   back64[id] = f64_of(f);
 }
 
+__global__ void k_rcp64(const double* in, double* out, long long n) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= n) return;
+  out[id] = rcp64(in[id]);
+}
+
 }  // namespace dg
 
 extern "C" int droplet_round_f32(const double* in, float* out32, double* back64, size_t n) {
@@ -499,6 +505,27 @@ extern "C" int droplet_round_f32(const double* in, float* out32, double* back64,
   }
   cudaFree(din);
   cudaFree(dback);
+  cudaFree(dout);
+  return rc;
+}
+
+extern "C" int droplet_rcp_f64(const double* in, double* out, size_t n) {
+  using namespace dg;
+  if (n == 0) return 0;
+  if (!in || !out || n > ((size_t)1 << 30)) return DROPLET_ERR_ARG;
+  double *din = nullptr, *dout = nullptr;
+  int rc = 0;
+  if (cudaMalloc(&din, n * sizeof(double)) != cudaSuccess || cudaMalloc(&dout, n * sizeof(double)) != cudaSuccess) {
+    rc = DROPLET_ERR_NOMEM;
+  } else if (cudaMemcpy(din, in, n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    rc = DROPLET_ERR_CUDA;
+  } else {
+    ++g_launches;
+    k_rcp64<<<(unsigned)((n + TPB - 1) / TPB), TPB>>>(din, dout, (long long)n);
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpy(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      rc = DROPLET_ERR_CUDA;
+  }
+  cudaFree(din);
   cudaFree(dout);
   return rc;
 }

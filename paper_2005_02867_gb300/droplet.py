@@ -54,7 +54,7 @@ FIELDS = dict(alpha=0, T=1, omega=2, p=3, rhoG=4, u0=5, u1=6, u2=7, mdot=8, mraw
 EXPORTS = ["droplet_init", "droplet_step", "droplet_diag", "droplet_field_size", "droplet_get_field",
            "droplet_set_field", "droplet_sync", "droplet_free", "droplet_strerror", "droplet_profile",
            "droplet_profile_read", "droplet_launch_count", "droplet_box_solve", "droplet_box_solve_noalloc", "droplet_save", "droplet_load", "droplet_adjoint",
-           "droplet_round_f32"]
+           "droplet_round_f32", "droplet_rcp_f64"]
 
 NOALLOC_MAX_UNKNOWNS = 262144
 
@@ -100,6 +100,7 @@ def load_library(path=LIBPATH):
     D = ctypes.POINTER(_c_dbl)
     lib.droplet_adjoint.argtypes = [P, _c_int, _c_int, D, D, D, D, ctypes.c_size_t]
     lib.droplet_round_f32.argtypes = [P, P, P, ctypes.c_size_t]
+    lib.droplet_rcp_f64.argtypes = [P, P, ctypes.c_size_t]
     lib.droplet_save.argtypes = [P, ctypes.c_char_p]
     lib.droplet_load.argtypes = [P, ctypes.c_char_p]
     lib.droplet_strerror.argtypes = [_c_int]
@@ -235,6 +236,18 @@ def droplet_round_f32(x):
     if rc:
         raise DropletError(rc, "droplet_round_f32")
     return out, back
+
+
+def droplet_rcp_f64(x):
+    """The device's binary64 reciprocal (binary32 seed, two Newton-Raphson steps)
+    applied to a float64 numpy array."""
+    import numpy as np
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty(x.size, dtype=np.float64)
+    rc = load_library().droplet_rcp_f64(x.ctypes.data, out.ctypes.data, x.size)
+    if rc:
+        raise DropletError(rc, "droplet_rcp_f64")
+    return out
 
 
 def droplet_launch_count(h):

@@ -50,3 +50,27 @@ def test_round_to_nearest_even_bitwise(D):
 def test_nan_stays_nan(D):
     out, back = D.droplet_round_f32(np.array([np.nan, -np.nan]))
     assert np.isnan(out).all() and np.isnan(back).all()
+
+
+def test_reciprocal_within_one_ulp(D):
+    """The binary64 reciprocal that stands in for divisions in the step kernels (a
+    binary32 seed and two Newton-Raphson steps) against the correctly rounded 1 / x:
+    at most one ulp apart over binary32's normal range, identical (a division) outside
+    it, including zeros, infinities and NaN."""
+    rng = np.random.default_rng(11)
+    x = np.concatenate([
+        rng.standard_normal(300000) * 10.0 ** rng.uniform(-37, 37, 300000),
+        rng.uniform(0.01, 2000.0, 100000),                          # densities, temperatures
+        np.nextafter(2.0 ** rng.integers(-120, 120, 2000).astype(np.float64), np.inf),
+        2.0 ** rng.integers(-120, 120, 2000).astype(np.float64),    # exact powers of two
+    ])
+    y = D.droplet_rcp_f64(x)
+    ref = 1.0 / x
+    ulps = np.abs(y - ref) / np.spacing(np.abs(ref))
+    assert ulps.max() <= 1.0, (ulps.max(), x[np.argmax(ulps)])
+    assert np.array_equal(y[-2000:], ref[-2000:])                 # powers of two: exact
+    edge = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e-300, -1e-300, 1e300, 1e-39, 3e38, 1e39])
+    ye = D.droplet_rcp_f64(edge)
+    with np.errstate(divide="ignore"):
+        re = 1.0 / edge
+    assert np.array_equal(ye, re, equal_nan=True)
