@@ -90,6 +90,7 @@ static void make_geo(const droplet_config& c, Geo& g) {
   for (int a = 0; a < 3; ++a) g.h[a] = (a < 2 || !g.axisym) ? c.L[a] / g.n[a] : 1.0;
   for (int a = 0; a < 3; ++a) g.ih[a] = 1.0 / g.h[a];
   g.hmin = g.axisym ? fmin(g.h[0], g.h[1]) : fmin(g.h[0], fmin(g.h[1], g.h[2]));
+  g.gthr = 1e-8 / g.hmin;
   g.s = g.axisym ? 1 : 2;
   int inlet = c.bc_mode == 1 ? BC_FORCED : BC_OPEN;
   if (g.axisym) {

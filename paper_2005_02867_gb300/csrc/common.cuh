@@ -31,6 +31,7 @@ struct Geo {
   double h[3];
   double ih[3];      // 1 / h
   double hmin;
+  double gthr;       // 1e-8 / h_min: |grad alpha| above it marks an interface cell
   long long N;       // number of cells (< 2^31)
 };
 
@@ -225,6 +226,20 @@ __device__ __forceinline__ double rcp64(double x) {
   e = fma(-x, y, 1.0);
   return fma(y, e, y);
 }
+
+// Minimum and maximum of binary64 values on the integer pipe (GB300's binary64 pipe
+// also executes the comparisons and min/max): the IEEE 754 encodings, with the
+// magnitude bits of negative values flipped, order as signed 64-bit integers exactly
+// as the values do (-0 below +0), so the results equal fmin / fmax bit for bit for
+// every non-NaN operand.
+__device__ __forceinline__ long long ord64(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double imax64(double a, double b) { return ord64(a) >= ord64(b) ? a : b; }
+__device__ __forceinline__ double imin64(double a, double b) { return ord64(a) <= ord64(b) ? a : b; }
+// clamp to [0, 1]
+__device__ __forceinline__ double iclamp01(double a) { return imin64(1.0, imax64(0.0, a)); }
 
 // ------------------------------------------------------------------ small formulas
 __device__ __forceinline__ double minmod(double x, double y) {

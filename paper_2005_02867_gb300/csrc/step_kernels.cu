@@ -134,6 +134,24 @@ __device__ __forceinline__ void grad_alpha(const Geo& g, const double* al, int i
   gr[1] = (cellg(g, al, i, j + 1, k, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i, j - 1, k, R_ALPHA, 0, 0, 0, 0)) * (0.5 * g.ih[1]);
   gr[2] = g.act3 ? (cellg(g, al, i, j, k + 1, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i, j, k - 1, R_ALPHA, 0, 0, 0, 0)) * (0.5 * g.ih[2]) : 0.0;
 }
+// grad_alpha, and whether it vanishes identically: equal neighbours on every axis
+// (compared as encodings, on the integer pipe) give exactly +0 differences, so such a
+// flat cell can skip the binary64 arithmetic that depends on the gradient
+__device__ __forceinline__ bool grad_alpha_flat(const Geo& g, const double* al, int i, int j, int k, double gr[3]) {
+  const double e = cellg(g, al, i + 1, j, k, R_ALPHA, 0, 0, 0, 0), w = cellg(g, al, i - 1, j, k, R_ALPHA, 0, 0, 0, 0);
+  const double n = cellg(g, al, i, j + 1, k, R_ALPHA, 0, 0, 0, 0), s = cellg(g, al, i, j - 1, k, R_ALPHA, 0, 0, 0, 0);
+  const double t = g.act3 ? cellg(g, al, i, j, k + 1, R_ALPHA, 0, 0, 0, 0) : 0.0;
+  const double b = g.act3 ? cellg(g, al, i, j, k - 1, R_ALPHA, 0, 0, 0, 0) : 0.0;
+  if (__double_as_longlong(e) == __double_as_longlong(w) && __double_as_longlong(n) == __double_as_longlong(s) &&
+      __double_as_longlong(t) == __double_as_longlong(b)) {
+    gr[0] = gr[1] = gr[2] = 0.0;
+    return true;
+  }
+  gr[0] = (e - w) * (0.5 * g.ih[0]);
+  gr[1] = (n - s) * (0.5 * g.ih[1]);
+  gr[2] = g.act3 ? (t - b) * (0.5 * g.ih[2]) : 0.0;
+  return false;
+}
 __device__ __forceinline__ double norm_rn(const double gr[3], int na) {
   double s = __dadd_rn(__dmul_rn(gr[0], gr[0]), __dmul_rn(gr[1], gr[1]));
   if (na == 3) s = __dadd_rn(s, __dmul_rn(gr[2], gr[2]));
@@ -156,11 +174,11 @@ __global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* ome
     int i, j, k;
     decomp(id, g.n[0], g.n[1], i, j, k);
     double gr[3];
-    grad_alpha(g, alpha, i, j, k, gr);
-    double gm = norm_rn(gr, na);
+    const bool flat = grad_alpha_flat(g, alpha, i, j, k, gr);
+    const double gm = flat ? 0.0 : norm_rn(gr, na);
     double m = 0.0;
     int found = -1;
-    if (gm > 1e-8 / g.hmin) {
+    if (gm > g.gthr) {
       double nh[3] = {-gr[0] / gm, -gr[1] / gm, -gr[2] / gm};
       int ci[3] = {i, j, k};
       int q[3] = {0, 0, 0};
@@ -208,10 +226,12 @@ __global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* ome
     }
     mraw[id] = m;
     adj[id] = found;
-    double V = cellV(g, i);
-    double a = alpha[id];
-    acc[0] += m * V;
-    acc[1] += sqrt(a * (1.0 - a)) * m * V;
+    if (m != 0.0) {   // (a zero m adds zeros: alpha is in [0, 1], the root finite)
+      double V = cellV(g, i);
+      double a = alpha[id];
+      acc[0] += m * V;
+      acc[1] += sqrt(a * (1.0 - a)) * m * V;
+    }
   }
   block_sum_store<2>(acc, partials);
 }
@@ -273,7 +293,7 @@ __global__ void k_adv_faces(Geo g, Phys p, const double* as, const double* ua, d
     grad_alpha(g, as, R[0], R[1], R[2], gR);
     double gf[3] = {gL[0] + gR[0], gL[1] + gR[1], gL[2] + gR[2]};
     double gfm = sqrt(gf[0] * gf[0] + gf[1] * gf[1] + (g.act3 ? gf[2] * gf[2] : 0.0));
-    double ne = gfm > 1e-8 / g.hmin ? gf[a] / gfm : 0.0;
+    double ne = gfm > g.gthr ? gf[a] / gfm : 0.0;
     double ac = 0.5 * (aL + aR);
     double FH = phi * aVL + p.C_alpha * fabs(phi) * ne * ac * (1.0 - ac);
     A = FH - FL[id];
@@ -305,7 +325,7 @@ __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const dou
   if (id >= g.N) return;
   int i, j, k;
   decomp(id, g.n[0], g.n[1], i, j, k);
-  double amax = fmax(as[id], aL[id]), amin = fmin(as[id], aL[id]);
+  double amax = imax64(as[id], aL[id]), amin = imin64(as[id], aL[id]);
   constexpr int na = NA;
   #pragma unroll
   for (int a = 0; a < na; ++a)
@@ -315,11 +335,12 @@ __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const dou
       q[a] += sh;
       if (q[a] < 0 || q[a] >= g.n[a]) continue;
       long long qi = cidx(g, q[0], q[1], q[2]);
-      amax = fmax(amax, fmax(as[qi], aL[qi]));
-      amin = fmin(amin, fmin(as[qi], aL[qi]));
+      const double sq = as[qi], lq = aL[qi];
+      amax = imax64(amax, imax64(sq, lq));
+      amin = imin64(amin, imin64(sq, lq));
     }
-  amax = fmin(amax, 1.0);
-  amin = fmax(amin, 0.0);
+  amax = imin64(amax, 1.0);
+  amin = imax64(amin, 0.0);
   const double* AA[3] = {A0, A1, A2};
   double Pp = 0.0, Pm = 0.0;
   #pragma unroll
@@ -328,13 +349,13 @@ __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const dou
     hi[a] += 1;
     double Alo = AA[a][fidx(g, a, i, j, k)];
     double Ahi = AA[a][fidx(g, a, hi[0], hi[1], hi[2])];
-    Pp += fmax(0.0, Alo) + fmax(0.0, -Ahi);
-    Pm += fmax(0.0, -Alo) + fmax(0.0, Ahi);
+    Pp += imax64(0.0, Alo) + imax64(0.0, -Ahi);
+    Pm += imax64(0.0, -Alo) + imax64(0.0, Ahi);
   }
   double V = cellV(g, i);
   double Qp = (amax - aL[id]) * V, Qm = (aL[id] - amin) * V;
-  Rp[id] = Pp > 0.0 ? fmin(1.0, fmax(0.0, Qp * rcp64(Pp))) : 0.0;
-  Rm[id] = Pm > 0.0 ? fmin(1.0, fmax(0.0, Qm * rcp64(Pm))) : 0.0;
+  Rp[id] = Pp > 0.0 ? iclamp01(Qp * rcp64(Pp)) : 0.0;
+  Rm[id] = Pm > 0.0 ? iclamp01(Qm * rcp64(Pm)) : 0.0;
 }
 
 __device__ __forceinline__ double limited_flux(const Geo& g, int a, const double* A, const double* Rp,
@@ -344,7 +365,7 @@ __device__ __forceinline__ double limited_flux(const Geo& g, int a, const double
   int L[3] = {f0, f1, f2};
   L[a] -= 1;
   long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, f0, f1, f2);
-  double C = Af >= 0.0 ? fmin(Rp[ri], Rm[li]) : fmin(Rp[li], Rm[ri]);
+  double C = Af >= 0.0 ? imin64(Rp[ri], Rm[li]) : imin64(Rp[li], Rm[ri]);
   return C * Af;
 }
 
@@ -367,7 +388,7 @@ __global__ void k_adv_update(Geo g, const double* aL, const double* A0, const do
     }
     double V = cellV(g, i);
     double an = aL[id] - s * rcp64(V);
-    double ac = fmin(1.0, fmax(0.0, an));
+    double ac = iclamp01(an);
     if (ac != an) { acc[1] += 1.0; acc[0] += (an - ac) * V; }
     alpha[id] = ac;
   }
@@ -389,7 +410,7 @@ __global__ void k_alpha_clip_only(Geo g, const double* as, double* alpha, double
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     decomp(id, g.n[0], g.n[1], i, j, k);
-    double an = as[id], ac = fmin(1.0, fmax(0.0, an));
+    double an = as[id], ac = iclamp01(an);
     if (ac != an) { acc[1] += 1.0; acc[0] += (an - ac) * cellV(g, i); }
     alpha[id] = ac;
   }
@@ -824,23 +845,25 @@ __global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, con
     double V = cellV(g, i);
     double a = alpha[id];
     double gr[3];
-    grad_alpha(g, alpha, i, j, k, gr);
-    double gm = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + (g.act3 ? gr[2] * gr[2] : 0.0));
     s[0] += a * V;
-    s[1] += mdot[id] * V;
-    s[2] += T[id] * gm * V;
-    s[3] += gm * V;
+    const double md = mdot[id];
+    if (md != 0.0) s[1] += md * V;
+    if (!grad_alpha_flat(g, alpha, i, j, k, gr)) {   // (a flat cell adds zeros)
+      double gm = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + (g.act3 ? gr[2] * gr[2] : 0.0));
+      s[2] += T[id] * gm * V;
+      s[3] += gm * V;
+    }
     s[4] += (1.0 - a) * rhoG[id] * omega[id] * V;
-    mx[1] = fmax(mx[1], a);
-    mx[2] = fmax(mx[2], -a);
+    mx[1] = imax64(mx[1], a);
+    mx[2] = imax64(mx[2], -a);
     int ci[3] = {i, j, k};
     #pragma unroll
     for (int q = 0; q < na; ++q) {
-      mx[0] = fmax(mx[0], fabs(U[q][fidx(g, q, i, j, k)]));
+      mx[0] = imax64(mx[0], fabs(U[q][fidx(g, q, i, j, k)]));
       if (ci[q] == g.n[q] - 1) {
         int hi[3] = {i, j, k};
         hi[q] += 1;
-        mx[0] = fmax(mx[0], fabs(U[q][fidx(g, q, hi[0], hi[1], hi[2])]));
+        mx[0] = imax64(mx[0], fabs(U[q][fidx(g, q, hi[0], hi[1], hi[2])]));
       }
       #pragma unroll
       for (int side = 0; side < 2; ++side) {

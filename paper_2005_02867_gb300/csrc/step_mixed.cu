@@ -418,7 +418,7 @@ __global__ void k_adv_faces_mx(Geo g, Phys p, const double* as, const double* ua
     grad_alpha_f(g, q, as, R[0], R[1], R[2], gR);
     const float gf[3] = {gL[0] + gR[0], gL[1] + gR[1], gL[2] + gR[2]};
     const float gfm = sqrtf(gf[0] * gf[0] + gf[1] * gf[1] + (g.act3 ? gf[2] * gf[2] : 0.f));
-    const float ne = gfm > 1e-8f / f32_rn(g.hmin) ? gf[a] / gfm : 0.f;
+    const float ne = gfm > f32_rn(g.gthr) ? gf[a] / gfm : 0.f;
     const float ac = 0.5f * (aLf + aRf);
     const float phif = f32_rn(phi);
     A = phif * inc + f32_rn(p.C_alpha) * fabsf(phif) * ne * ac * (1.f - ac);
