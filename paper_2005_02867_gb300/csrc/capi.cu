@@ -76,7 +76,11 @@ static int check_cfg(const droplet_config& c) {
   for (int a = 0; a < 2; ++a)
     if (c.mg_tile[a] != 0 && (c.mg_tile[a] < 8 || c.mg_tile[a] > 256)) return DROPLET_ERR_ARG;
   long long nn = (long long)c.n[0] * c.n[1] * (c.geom == 0 ? 1 : c.n[2]);
-  if (nn + (long long)c.n[0] * c.n[1] >= (1LL << 31)) return DROPLET_ERR_ARG;   // 32-bit cell and face indices
+  {   // 32-bit cell and face indices: the cells plus the largest extra face plane
+    const long long n2 = c.geom == 0 ? 1 : c.n[2];
+    const long long plane = std::max((long long)c.n[0] * c.n[1], std::max((long long)c.n[1] * n2, (long long)c.n[0] * n2));
+    if (nn + plane >= (1LL << 31)) return DROPLET_ERR_ARG;
+  }
   return 0;
 }
 

@@ -58,13 +58,15 @@ struct Phys {
 
 __host__ __device__ inline int nact(const Geo& g) { return g.act3 ? 3 : 2; }
 
+// cell and face indices in 32-bit arithmetic: every array here has fewer than 2^31
+// entries (cells and faces of a direction; checked when a context is created)
 __device__ __forceinline__ long long cidx(const Geo& g, int i, int j, int k) {
-  return (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k);
+  return (long long)(i + g.n[0] * (j + g.n[1] * k));
 }
 // face of direction a at integer face coords (i, j, k)
 __device__ __forceinline__ long long fidx(const Geo& g, int a, int i, int j, int k) {
-  long long f0 = g.n[0] + (a == 0), f1 = g.n[1] + (a == 1);
-  return (long long)i + f0 * ((long long)j + f1 * k);
+  const int f0 = g.n[0] + (a == 0), f1 = g.n[1] + (a == 1);
+  return (long long)(i + f0 * (j + f1 * k));
 }
 __host__ __device__ inline long long nfaces(const Geo& g, int a) {
   return (long long)(g.n[0] + (a == 0)) * (g.n[1] + (a == 1)) * (g.n[2] + (a == 2));
@@ -240,6 +242,8 @@ __device__ __forceinline__ double imax64(double a, double b) { return ord64(a) >
 __device__ __forceinline__ double imin64(double a, double b) { return ord64(a) <= ord64(b) ? a : b; }
 // clamp to [0, 1]
 __device__ __forceinline__ double iclamp01(double a) { return imin64(1.0, imax64(0.0, a)); }
+// a >= b, the same way (non-NaN operands)
+__device__ __forceinline__ bool ige64(double a, double b) { return ord64(a) >= ord64(b); }
 
 // ------------------------------------------------------------------ small formulas
 __device__ __forceinline__ double minmod(double x, double y) {

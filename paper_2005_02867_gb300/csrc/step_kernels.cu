@@ -459,7 +459,7 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
   double r = coef * V * phi[id] * p.idt + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
   double net = 0.0, Fsum = 0.0;
   double gP = gam(mode, kc, rho, D, id);
-  bool pin = (mode == 1) && (alpha_new[id] >= 0.5);
+  bool pin = (mode == 1) && ige64(alpha_new[id], 0.5);
   int ci[3] = {i, j, k};
   #pragma unroll
   for (int a = 0; a < na; ++a) {
@@ -495,7 +495,7 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
       long long li = cidx(g, Lc[0], Lc[1], Lc[2]);
       cl = harm(gam(mode, kc, rho, D, li), gP) * faceA(g, a, i) * g.ih[a];
       if (mode == 1) {
-        bool lp = alpha_new[li] >= 0.5;
+        bool lp = ige64(alpha_new[li], 0.5);
         if (!pin && lp) { r += cl * pinv[li]; dP += cl; }
         if (pin || lp) cl = 0.0;
       }
@@ -506,7 +506,7 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
       int Hc[3] = {i, j, k};
       Hc[a] += 1;
       long long hi = cidx(g, Hc[0], Hc[1], Hc[2]);
-      if (alpha_new[hi] >= 0.5) {
+      if (ige64(alpha_new[hi], 0.5)) {
         double ch = harm(gP, gam(mode, kc, rho, D, hi)) * faceA(g, a, Hc[0]) * g.ih[a];
         r += ch * pinv[hi];
         dP += ch;
@@ -558,7 +558,7 @@ __global__ void k_yeq(Geo g, Phys p, const double* T, const double* alpha, const
 __global__ void k_species_noflow(Geo g, const double* alpha_new, const double* yq, double* omega) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
-  if (alpha_new[id] >= 0.5) omega[id] = yq[id];
+  if (ige64(alpha_new[id], 0.5)) omega[id] = yq[id];
 }
 
 __global__ void k_rhoG(Geo g, Phys p, const double* T, const double* w, double* rhoG) {

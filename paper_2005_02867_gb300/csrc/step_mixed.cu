@@ -262,7 +262,7 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
   const double coef = mode == 0 ? rho[id] * cp[id] : rho[id];
   double dP = coef * V * p.idt;
   double r = coef * V * phi[id] * p.idt + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
-  const bool pin = (mode == 1) && (alpha_new[id] >= 0.5);
+  const bool pin = (mode == 1) && ige64(alpha_new[id], 0.5);
   // the increments, FP32
   const float phiP = f32_rn(phi[id]), ambf = f32_rn(amb);
   const float gP = mode == 0 ? ldf(kc, id) : f32_rn(rho[id] * D[id]);
@@ -309,7 +309,7 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
                               : (g.axisym ? ((i + 0.5f) * q.h[0]) * q.h[0] : q.h[0] * q.h[1] * q.h[2] * q.ih[a]);
       cl = 2.f * gL * gP / (gL + gP) * Aa * q.ih[a];
       if (mode == 1) {
-        bool lp = alpha_new[li] >= 0.5;
+        bool lp = ige64(alpha_new[li], 0.5);
         if (!pin && lp) { r += f64_of(cl) * pinv[li]; dinc += cl; }
         if (pin || lp) cl = 0.f;
       }
@@ -320,7 +320,7 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
       int Hc[3] = {i, j, k};
       Hc[a] += 1;
       long long hi = cidx(g, Hc[0], Hc[1], Hc[2]);
-      if (alpha_new[hi] >= 0.5) {
+      if (ige64(alpha_new[hi], 0.5)) {
         const float gH = f32_rn(rho[hi] * D[hi]);
         const float Ah = a == 0 ? (g.axisym ? (Hc[0] * q.h[0]) * q.h[1] : q.h[0] * q.h[1] * q.h[2] * q.ih[0])
                                 : (g.axisym ? ((i + 0.5f) * q.h[0]) * q.h[0] : q.h[0] * q.h[1] * q.h[2] * q.ih[a]);
