@@ -270,7 +270,9 @@ int droplet_adjoint(droplet_ctx* ctx, int n_steps, int ckpt_every, double* J, do
 /* Checkpoint / resume.  droplet_save writes, for every droplet, its config, time,
  * step count, the accumulated diagnostics (clipped volume, vapour outflow) and the
  * state fields (alpha, T, omega, p_rgh, rho_G and the face velocities, FP64,
- * little-endian) to `path`.  droplet_load reads such a file into a context
+ * little-endian) to `path`, followed by the previous step's T, omega and face
+ * velocities, from which the next step extrapolates the initial guesses of its
+ * Helmholtz solves (a state set with droplet_set_field starts them from itself).  droplet_load reads such a file into a context
  * created with the same configs (byte-identical droplet_config structs, else
  * DROPLET_ERR_ARG) and continues from there: the next steps are bit-identical to
  * those of the saved run.  File errors: DROPLET_ERR_IO. */

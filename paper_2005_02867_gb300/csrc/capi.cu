@@ -27,6 +27,9 @@ struct dctx {
   double *rhoG_old = nullptr, *mdot = nullptr, *mraw = nullptr, *astar = nullptr, *aL = nullptr, *Rp = nullptr, *Rm = nullptr;
   double *FL[3] = {nullptr, nullptr, nullptr}, *AF[3] = {nullptr, nullptr, nullptr}, *us[3] = {nullptr, nullptr, nullptr};
   double *xi = nullptr;
+  // history of the Helmholtz unknowns (previous step's T, omega, face velocities) for the
+  // extrapolated initial guesses; valid while scal[SC_HIST] = 1
+  double *hT = nullptr, *hW = nullptr, *hu[3] = {nullptr, nullptr, nullptr};
   double *rho = nullptr, *mu = nullptr, *kc = nullptr, *cp = nullptr, *Dm = nullptr, *yq = nullptr, *dp = nullptr, *S = nullptr;
   int* adj = nullptr;
   double *bD = nullptr, *bc[3] = {nullptr, nullptr, nullptr}, *brhs = nullptr, *bx = nullptr;
@@ -149,11 +152,11 @@ static int dalloc(double** q, long long n) {
 static void free_all(dctx* c) {
   double** arrs[] = {&c->alpha, &c->T, &c->omega, &c->pr, &c->rhoG, &c->rhoG_old, &c->mdot, &c->mraw, &c->astar,
                      &c->aL, &c->Rp, &c->Rm, &c->rho, &c->mu, &c->kc, &c->cp, &c->Dm, &c->yq, &c->dp, &c->S,
-                     &c->bD, &c->brhs, &c->bx, &c->part, &c->psum, &c->pmax, &c->scal, &c->xi};
+                     &c->bD, &c->brhs, &c->bx, &c->part, &c->psum, &c->pmax, &c->scal, &c->xi, &c->hT, &c->hW};
   for (auto q : arrs) { cudaFree(*q); *q = nullptr; }
   for (int a = 0; a < 3; ++a) {
-    cudaFree(c->u[a]); cudaFree(c->FL[a]); cudaFree(c->AF[a]); cudaFree(c->us[a]); cudaFree(c->bc[a]);
-    c->u[a] = c->FL[a] = c->AF[a] = c->us[a] = c->bc[a] = nullptr;
+    cudaFree(c->u[a]); cudaFree(c->FL[a]); cudaFree(c->AF[a]); cudaFree(c->us[a]); cudaFree(c->bc[a]); cudaFree(c->hu[a]);
+    c->u[a] = c->FL[a] = c->AF[a] = c->us[a] = c->bc[a] = c->hu[a] = nullptr;
   }
   for (auto& set : c->xb)
     for (auto& q : set) { cudaFree(q); q = nullptr; }
@@ -168,12 +171,14 @@ static void free_all(dctx* c) {
   c->st2 = nullptr; c->own = nullptr;
 }
 
-static int run_diag(dctx* c) {
+// diagnostics of the current state; step_end: at the end of a step (the history fields
+// then hold the step's starting values), else the history is marked invalid
+static int run_diag(dctx* c, int step_end) {
   Geo& g = c->g;
   int nb = red_grid_cap(g.N, c->rb);
   L_diag(c->st, nb, g, c->alpha, c->T, c->mdot, c->omega, c->rhoG, c->u[0], c->u[1], c->u[2] ? c->u[2] : c->u[0],
                                 c->psum, c->pmax);
-  ++g_launches, k_diag_finish<<<1, TPB, 0, c->st>>>(c->psum, c->pmax, nb, c->scal);
+  ++g_launches, k_diag_finish<<<1, TPB, 0, c->st>>>(c->psum, c->pmax, nb, c->scal, step_end);
   CKR(cudaGetLastError());
   return 0;
 }
@@ -199,7 +204,7 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
   int na = nact(g);
   double** cells[] = {&c->alpha, &c->T, &c->omega, &c->pr, &c->rhoG, &c->rhoG_old, &c->mdot, &c->mraw, &c->astar,
                       &c->aL, &c->Rp, &c->Rm, &c->rho, &c->mu, &c->kc, &c->cp, &c->Dm, &c->yq, &c->dp, &c->S,
-                      &c->bD, &c->brhs, &c->bx, &c->xi};
+                      &c->bD, &c->brhs, &c->bx, &c->xi, &c->hT, &c->hW};
   for (auto q : cells)
     if ((rc = dalloc(q, N))) { free_all(c); delete c; return rc; }
 
@@ -208,7 +213,7 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
     if (a >= na) continue;
     long long nf = nfaces(g, a);
     if ((rc = dalloc(&c->u[a], nf)) || (rc = dalloc(&c->FL[a], nf)) || (rc = dalloc(&c->AF[a], nf)) ||
-        (rc = dalloc(&c->us[a], nf))) { free_all(c); delete c; return rc; }
+        (rc = dalloc(&c->us[a], nf)) || (rc = dalloc(&c->hu[a], nf))) { free_all(c); delete c; return rc; }
   }
   if ((rc = dalloc(&c->part, RED_BLOCKS * 8)) || (rc = dalloc(&c->psum, RED_BLOCKS * 6)) ||
       (rc = dalloc(&c->pmax, RED_BLOCKS * 3)) || (rc = dalloc(&c->scal, SC_COUNT))) { free_all(c); delete c; return rc; }
@@ -251,7 +256,10 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
   for (int a = 0; a < na; ++a) {
     cudaMemsetAsync(c->u[a], 0, sizeof(double) * nfaces(g, a), st);
     cudaMemsetAsync(c->us[a], 0, sizeof(double) * nfaces(g, a), st);
+    cudaMemsetAsync(c->hu[a], 0, sizeof(double) * nfaces(g, a), st);
   }
+  cudaMemsetAsync(c->hT, 0, sizeof(double) * N, st);
+  cudaMemsetAsync(c->hW, 0, sizeof(double) * N, st);
   double dtv = c->cfg.dt;
   cudaMemcpyAsync(c->scal + SC_DT, &dtv, sizeof(double), cudaMemcpyHostToDevice, st);
   ++g_launches, k_init<<<gc, TPB, 0, st>>>(g, c->p, c->alpha, c->T, c->omega, c->rhoG);
@@ -266,7 +274,7 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
     cudaStreamSynchronize(st);
     free(hv);
   }
-  if ((rc = run_diag(c))) { free_all(c); delete c; return rc; }
+  if ((rc = run_diag(c, 0))) { free_all(c); delete c; return rc; }
   if (cudaStreamSynchronize(st) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_CUDA; }
   *out = c;
   return 0;
@@ -325,7 +333,8 @@ static int one_step(dctx* c, int* nc_flag) {
     }
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
-    bs.x = c->T;   // solved in place: T is the initial guess and receives the solution
+    bs.x = c->T;   // solved in place: T receives the solution
+    ++g_launches, k_extrap<<<gc, TPB, 0, st>>>(N, c->T, c->hT, c->scal);
     c->solver.record_next(c->scal, SC_ITS_T, -1, 0);
     rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
     if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
@@ -344,6 +353,7 @@ static int one_step(dctx* c, int* nc_flag) {
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
     bs.x = c->omega;   // in place
+    ++g_launches, k_extrap<<<gc, TPB, 0, st>>>(N, c->omega, c->hW, c->scal);
     c->solver.record_next(c->scal, SC_ITS_W, -1, 0);
     rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
     if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
@@ -381,7 +391,7 @@ static int one_step(dctx* c, int* nc_flag) {
             st, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi, b.D, b.c[0],
             b.c[1], na == 3 ? b.c[2] : b.c[0], (double*)b.b);
         }
-        L_faces_to_box(st, lin_grid(nbx), g, cc, c->u[cc], b.x);
+        L_faces_to_box(st, lin_grid(nbx), g, cc, c->u[cc], b.x, c->hu[cc], c->scal);
         recs[cc] = RecordSpec{c->scal, SC_ITS_U, -1, cc > 0};
       }
       rc = c->solver.pcg_jacobi_multi(sys, na, c->cfg.helm_rtol, c->cfg.helm_maxit, recs, &ss);
@@ -403,7 +413,7 @@ static int one_step(dctx* c, int* nc_flag) {
         }
         for (int a = 0; a < 3; ++a) bs.m[a] = m[a];
         bs.N = nbx;
-        L_faces_to_box(st, lin_grid(nbx), g, cc, c->u[cc], c->bx);
+        L_faces_to_box(st, lin_grid(nbx), g, cc, c->u[cc], c->bx, c->hu[cc], c->scal);
         c->solver.record_next(c->scal, SC_ITS_U, -1, cc > 0);
         rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
         if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
@@ -433,7 +443,7 @@ static int one_step(dctx* c, int* nc_flag) {
     cudaMemsetAsync(c->S, 0, sizeof(double) * N, st);
   }
   // S11
-  if ((rc = run_diag(c))) return rc;
+  if ((rc = run_diag(c, 1))) return rc;
   CKR(cudaGetLastError());
   return 0;
 }
@@ -596,7 +606,7 @@ static int autotune(droplet_ctx* c) {
   cudaEventDestroy(e1);
   if (rc) return rc;
   if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
-  for (auto x : c->d) if (run_diag(x)) return DROPLET_ERR_CUDA;
+  for (auto x : c->d) if (run_diag(x, 0)) return DROPLET_ERR_CUDA;
   CKR(cudaStreamSynchronize(c->st));
   return 0;
 }
@@ -840,6 +850,7 @@ extern "C" int droplet_set_field(droplet_ctx* cc, int droplet, int field_id, con
   CKR(cudaStreamSynchronize(cc->st));
   CKR(cudaMemcpyAsync(d, host, sizeof(double) * n, cudaMemcpyHostToDevice, c->st));
   CKR(cudaMemsetAsync(c->dirty, 0xff, sizeof(int), c->st));
+  CKR(cudaMemsetAsync(c->scal + SC_HIST, 0, sizeof(double), c->st));   // no previous step for this state
   CKR(cudaStreamSynchronize(c->st));
   return 0;
 }
@@ -895,11 +906,17 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
     cudaMemcpyAsync(x->omega, src + 2 * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
     cudaMemsetAsync(x->dirty, 0xff, sizeof(int), st);   // rho_G from T and omega at S0
   };
+  // every forward step starts from its state alone (no extrapolated guesses), so that
+  // the steps recomputed from the checkpoints repeat the first pass bit for bit
+  auto step_alone = [&](int* ncp) {
+    cudaMemsetAsync(x->scal + SC_HIST, 0, sizeof(double), st);
+    return one_step(x, ncp);
+  };
   int nc = 0, rc = 0;
   // forward with checkpoints every ckpt_every steps, J accumulated on the device
   for (int n = 0; n < n_steps && !rc; ++n) {
     if (n % ckpt_every == 0) save_state(ck + S3 * (n / ckpt_every));
-    rc = one_step(x, &nc);
+    rc = step_alone(&nc);
     L_acc_J(st, x->scal, jweight, acc);
   }
   save_state(fin);
@@ -923,14 +940,14 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
       load_state(ck + S3 * sgi);
       for (int n = n0; n < n1 && !rc; ++n) {
         save_state(seg + S3 * (n - n0));
-        if (n + 1 < n1) rc = one_step(x, &nc);
+        if (n + 1 < n1) rc = step_alone(&nc);
       }
       for (int n = n1 - 1; n >= n0 && !rc; --n) {
         const double* sA = seg + S3 * (n - n0);
         const double* sT = sA + N;
         const double* sW = sA + 2 * N;
         load_state(sA);
-        rc = one_step(x, &nc);           // leaves step n's intermediates and state n+1
+        rc = step_alone(&nc);            // leaves step n's intermediates and state n+1
         if (rc) break;
         L_adj_pin(st, g, p, sA, sT, sW, wp);
         // species: adjoint solve on the free rows, pinned rows and coefficients
@@ -981,13 +998,17 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
 }
 
 // ---------------------------------------------------------------- checkpoint / resume
-static const char kMagic[8] = {'D', 'R', 'O', 'P', 'C', 'K', 'P', '1'};
+static const char kMagic[8] = {'D', 'R', 'O', 'P', 'C', 'K', 'P', '2'};
 
-static int state_fields(dctx* x, double* f[8], long long n[8]) {
-  double* fs[8] = {x->alpha, x->T, x->omega, x->pr, x->rhoG, x->u[0], x->u[1], x->u[2]};
-  for (int q = 0; q < 8; ++q) {
+// the checkpointed fields: the state, then the history of the extrapolated guesses
+constexpr int NCKPT = 13;
+static int state_fields(dctx* x, double* f[NCKPT], long long n[NCKPT]) {
+  double* fs[NCKPT] = {x->alpha, x->T, x->omega, x->pr, x->rhoG, x->u[0], x->u[1], x->u[2],
+                       x->hT, x->hW, x->hu[0], x->hu[1], x->hu[2]};
+  for (int q = 0; q < NCKPT; ++q) {
     f[q] = fs[q];
-    n[q] = fs[q] ? (q < 5 ? x->g.N : nfaces(x->g, q - 5)) : 0;
+    const int fa = q >= 10 ? q - 10 : q - 5;
+    n[q] = fs[q] ? ((q < 5 || q == 8 || q == 9) ? x->g.N : nfaces(x->g, fa)) : 0;
   }
   return 0;
 }
@@ -1006,10 +1027,10 @@ extern "C" int droplet_save(droplet_ctx* c, const char* path) {
     CKR(cudaMemcpy(x->hscal, x->scal, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost));
     ok = fwrite(&x->cfg, sizeof(droplet_config), 1, fp) == 1 && fwrite(&x->t, sizeof(double), 1, fp) == 1 &&
          fwrite(&x->step, sizeof(long long), 1, fp) == 1 && fwrite(x->hscal, sizeof(double), SC_COUNT, fp) == SC_COUNT;
-    double* f[8];
-    long long n[8];
+    double* f[NCKPT];
+    long long n[NCKPT];
     state_fields(x, f, n);
-    for (int q = 0; q < 8 && ok; ++q) {
+    for (int q = 0; q < NCKPT && ok; ++q) {
       if (!n[q]) continue;
       host.resize((size_t)n[q]);
       if (cudaMemcpy(host.data(), f[q], sizeof(double) * n[q], cudaMemcpyDeviceToHost) != cudaSuccess) { fclose(fp); return DROPLET_ERR_CUDA; }
@@ -1038,10 +1059,10 @@ extern "C" int droplet_load(droplet_ctx* c, const char* path) {
         fread(x->hscal, sizeof(double), SC_COUNT, fp) != SC_COUNT) { fclose(fp); return DROPLET_ERR_IO; }
     if (memcmp(&cf, &x->cfg, sizeof(cf)) != 0) { fclose(fp); return DROPLET_ERR_ARG; }
     CKR(cudaStreamSynchronize(x->st));
-    double* f[8];
-    long long n[8];
+    double* f[NCKPT];
+    long long n[NCKPT];
     state_fields(x, f, n);
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < NCKPT; ++q) {
       if (!n[q]) continue;
       host.resize((size_t)n[q]);
       if (fread(host.data(), sizeof(double), (size_t)n[q], fp) != (size_t)n[q]) { fclose(fp); return DROPLET_ERR_IO; }

@@ -44,6 +44,7 @@ enum {
   SC_K = 0, SC_CLIP, SC_VAPOUT, SC_DT,
   SC_SUM_ALPHA_V, SC_SUM_MDOT_V, SC_SUM_TG, SC_SUM_G, SC_SUM_VAP, SC_MAXU, SC_AMAX, SC_AMIN,
   SC_ITS_P, SC_ITS_T, SC_ITS_W, SC_ITS_U, SC_RES_P, SC_NC,
+  SC_HIST,   // 1: the history fields hold the previous step's T, omega, u (extrapolated guesses)
   SC_COUNT
 };
 
@@ -71,7 +72,8 @@ __global__ void k_rhoG(Geo g, Phys p, const double* T, const double* w, double* 
 
 __global__ void k_add(long long n, double* y, const double* x);
 
-__global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal);
+__global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal, int step_end);
+__global__ void k_extrap(long long n, double* x, double* xh, const double* scal);
 
 // launch wrappers of the kernels templated on the active axes / face direction (step_kernels.cu)
 void L_evap_raw(cudaStream_t st, int grid, Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* mraw, int* adj, double* partials, unsigned* flags);
@@ -88,7 +90,8 @@ void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* 
 void L_correct(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u);
 void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax);
 
-void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x);
+void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x, double* uh,
+                    const double* scal);
 
 // ---- adjoint of the step without flow (adjoint.cu)
 enum { AC_DGAS = 0, AC_J, AC_TAMB, AC_COUNT };

@@ -723,9 +723,22 @@ __global__ void k_mom_scatter(Geo g, Phys p, const double* x, double* us) {
   // axis / wall: stays 0; forced inlet: keeps u_in (both already stored)
 }
 
-// initial guess of the momentum solve of direction c: u^n on the interior faces
+// Initial guess of a Helmholtz solve: the linear extrapolation in time x^n + (x^n -
+// x^{n-1}) where the previous step's field is held (scal[SC_HIST] = 1), else x^n; the
+// history then takes x^n.  Only the starting point of the iteration changes: the
+// solution is the system's, to the solver's tolerance, either way.
+__global__ void k_extrap(long long n, double* x, double* xh, const double* scal) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= n) return;
+  const double v = x[id];
+  if (scal[SC_HIST] != 0.0) x[id] = 2.0 * v - xh[id];
+  xh[id] = v;
+}
+
+// initial guess of the momentum solve of direction c on the interior faces: u^n,
+// extrapolated in time as in k_extrap (history uh on the faces)
 template <int C>
-__global__ void k_faces_to_box(Geo g, const double* u, double* x) {
+__global__ void k_faces_to_box(Geo g, const double* u, double* x, double* uh, const double* scal) {
   constexpr int c = C;
   int m[3] = {g.n[0], g.n[1], g.n[2]};
   m[c] -= 1;
@@ -735,7 +748,10 @@ __global__ void k_faces_to_box(Geo g, const double* u, double* x) {
   int b[3];
   decomp(id, m[0], m[1], b[0], b[1], b[2]);
   b[c] += 1;
-  x[id] = u[fidx(g, c, b[0], b[1], b[2])];
+  const long long f = fidx(g, c, b[0], b[1], b[2]);
+  const double v = u[f];
+  x[id] = scal[SC_HIST] != 0.0 ? 2.0 * v - uh[f] : v;
+  uh[f] = v;
 }
 
 // ============================================================== S8 - S10 projection
@@ -883,7 +899,9 @@ __global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, con
   block_max_store<3>(mx, pmax);
 }
 
-__global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal) {
+// (step_end: the end of a step, whose solves have filled the history fields; 0 after
+// a state that did not come from a step)
+__global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal, int step_end) {
   double v[6], m[3];
   block_reduce_partials<6, false>(psum, nblk, v);
   block_reduce_partials<3, true>(pmax, nblk, m);
@@ -897,6 +915,7 @@ __global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, 
     scal[SC_MAXU] = m[0];
     scal[SC_AMAX] = m[1];
     scal[SC_AMIN] = -m[2];
+    scal[SC_HIST] = step_end ? 1.0 : 0.0;
   }
 }
 
@@ -975,11 +994,12 @@ void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double*
   else k_diag<2><<<grid, TPB, 0, st>>>(g, alpha, T, mdot, omega, rhoG, u0, u1, u2, psum, pmax);
 }
 
-void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x) {
+void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x, double* uh,
+                    const double* scal) {
   ++g_launches;
-  if (c == 0) k_faces_to_box<0><<<grid, TPB, 0, st>>>(g, u, x);
-  else if (c == 1) k_faces_to_box<1><<<grid, TPB, 0, st>>>(g, u, x);
-  else k_faces_to_box<2><<<grid, TPB, 0, st>>>(g, u, x);
+  if (c == 0) k_faces_to_box<0><<<grid, TPB, 0, st>>>(g, u, x, uh, scal);
+  else if (c == 1) k_faces_to_box<1><<<grid, TPB, 0, st>>>(g, u, x, uh, scal);
+  else k_faces_to_box<2><<<grid, TPB, 0, st>>>(g, u, x, uh, scal);
 }
 
 }  // namespace dg
