@@ -374,7 +374,6 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value, _ = replica_throughput(e2e_s * 1e3, ncell, e2e_steps)
-    diag = sim.diag()
     sim.close()
 
     if rank == 0:
