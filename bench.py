@@ -55,19 +55,19 @@ FLUSH_BYTES = 512 << 20      # larger than the 129 MB L2
 
 
 # DRAM traffic of the dominant kernel from a committed ncu capture: profiles/ncu_traffic.json
-# maps a workload to {class, kernel, dram_bytes_per_launch, sources_sha256, ...}; the value
-# is reported only while the sources that define the kernel hash as they did when the
+# maps a workload to {class, kernel, dram_bytes_per_launch, sources, sources_sha256, ...};
+# the value is reported only while the sources that define the kernel (its translation
+# unit and the headers it includes, listed in the record) hash as they did when the
 # counters were taken (else null: the kernel has changed since).
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-TRAFFIC_SOURCES = ["paper_2005_02867_gb300/csrc/solver.cu", "paper_2005_02867_gb300/csrc/step_kernels.cu",
-                   "paper_2005_02867_gb300/csrc/step_mixed.cu", "paper_2005_02867_gb300/csrc/common.cuh",
-                   "paper_2005_02867_gb300/csrc/kernels.h", "include/droplet.h"]
+SOLVER_SOURCES = ["paper_2005_02867_gb300/csrc/solver.cu", "paper_2005_02867_gb300/csrc/common.cuh",
+                  "paper_2005_02867_gb300/csrc/kernels.h", "include/droplet.h"]
 
 
-def sources_sha256():
+def sources_sha256(files=SOLVER_SOURCES):
     import hashlib
     h = hashlib.sha256()
-    for f in TRAFFIC_SOURCES:
+    for f in files:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -79,7 +79,12 @@ def captured_traffic(workload, kclass):
             rec = json.load(fh).get(workload)
     except (OSError, ValueError):
         return None
-    if not rec or rec.get("class") != kclass or rec.get("sources_sha256") != sources_sha256():
+    if not rec or rec.get("class") != kclass:
+        return None
+    try:
+        if rec.get("sources_sha256") != sources_sha256(rec.get("sources", SOLVER_SOURCES)):
+            return None
+    except OSError:
         return None
     return rec
 

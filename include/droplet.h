@@ -221,15 +221,18 @@ int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0,
  *   4 MG_PROLONG  injection prolongation               [(2 + 1/2^d) N w; FP64: N flops]
  *   5 MOM_ASSEMBLE momentum system assembly            [(12 + 2d) N 8]
  *   6 SCALAR_ASSEMBLE energy / species assembly        [(12 + 2d) N 8]
+ *   7 PCG_PERSIST the whole Jacobi-preconditioned CG of one to three Helmholtz
+ *                 systems in one persistent launch     [setup, then (11 + d) N w per
+ *                                                       iteration of each system]
  * (w = 8 for FP64 launches, 4 for FP32 ones.)
- * Single droplets of at most 2^22 cells, and the droplets of a batch, solve with
- * persistent kernels: class 0 then times the whole multigrid-preconditioned CG of
- * the pressure (one launch per solve; bytes: per iteration the level-0 FP64 CG
- * vectors, each grid level's operator, b and x once per smoothing side, the
- * transfers and the coarse tail, times the iterations) and class 1 the whole
- * Jacobi-preconditioned CG of a Helmholtz system (one launch; bytes: the setup and
- * (11 + d) N w per iteration); classes 2 - 4 then stay empty.                     */
-#define DROPLET_KCLASS_COUNT 7
+ * The Helmholtz systems solve with the persistent kernel of class 7 in mixed
+ * precision at every size, in FP64 up to 2^22 cells.  Single droplets of at most
+ * 2^22 cells, and the droplets of a batch, solve the pressure with a persistent
+ * kernel too: class 0 then times the whole multigrid-preconditioned CG (one launch
+ * per solve; bytes: per iteration the level-0 FP64 CG vectors, each grid level's
+ * operator, b and x once per smoothing side, the transfers and the coarse tail,
+ * times the iterations); classes 2 - 4 then stay empty.                            */
+#define DROPLET_KCLASS_COUNT 8
 
 /* Start (enable = 1) or stop (0) timing every launch of the kernel classes above
  * with CUDA events on the context's stream; starting clears the totals. */

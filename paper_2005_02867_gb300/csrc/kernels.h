@@ -9,7 +9,8 @@ namespace dg {
 // launches issued by the library in this process
 extern long long g_launches;
 
-enum { KC_MG_SMOOTH = 0, KC_SPMV, KC_UPDATE, KC_MG_RESTRICT, KC_MG_PROLONG, KC_MOM_ASSEMBLE, KC_SCALAR_ASSEMBLE, KC_COUNT };
+enum { KC_MG_SMOOTH = 0, KC_SPMV, KC_UPDATE, KC_MG_RESTRICT, KC_MG_PROLONG, KC_MOM_ASSEMBLE, KC_SCALAR_ASSEMBLE,
+       KC_PCG_PERSIST, KC_COUNT };
 
 // Optional CUDA-event timing of the kernel classes above (per context).
 struct Prof {

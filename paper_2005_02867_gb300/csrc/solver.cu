@@ -12,7 +12,8 @@
 
 namespace dg {
 
-enum { S_RZ = 0, S_PAP, S_RR, S_BB, S_ALPHA, S_BETA, S_ITS, S_TOL2, S_MAXIT, S_COUNT };
+// (S_ITSK: the iterations of each system of a joint persistent solve)
+enum { S_RZ = 0, S_PAP, S_RR, S_BB, S_ALPHA, S_BETA, S_ITS, S_TOL2, S_MAXIT, S_ITSK, S_COUNT = S_ITSK + 3 };
 
 // done flag values: 0 running, 1 converged, 2 stopped at the iteration cap
 
@@ -767,6 +768,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
       if (k >= K) break;
       const double rr = s_its[k] > 0 ? (double)s_rho[k] * s_inv_nu[k] * s_inv_nu[k] : s_rr[k];
       const RecordSpec& rec = M.s[k].rec;
+      if (blockIdx.x == 0) M.stat[S_ITSK + k] = (double)s_its[k];
       if (blockIdx.x == 0 && rec.scal) {
         if (rec.acc) rec.scal[rec.its] += (double)s_its[k];
         else rec.scal[rec.its] = (double)s_its[k];
@@ -2000,7 +2002,7 @@ int Solver::pcg_persist(const BoxSys* sys, int K, double rtol, int maxit, const 
   memset(&M, 0, sizeof(M));
   M.K = K;
   long long nmax = 0;
-  double setup_b = 0.0, iter_b = 0.0;
+  double setup_b = 0.0, iter_b[PMAXSYS] = {0.0, 0.0, 0.0};
   for (int k = 0; k < K; ++k) {
     const BoxSys& s = sys[k];
     PersistArgs<T>& a = M.s[k];
@@ -2028,7 +2030,7 @@ int Solver::pcg_persist(const BoxSys* sys, int K, double rtol, int maxit, const 
     // diag and c^ in, r^, s, w, p, x^ out
     const double na = s.c[2] ? 3.0 : 2.0, wb = (double)sizeof(T);
     setup_b += ((2.0 + 2.0 * na) * 8.0 + (7.0 + na) * wb + 2.0 * wb + 16.0) * s.N;
-    iter_b += (11.0 + na) * wb * s.N;
+    iter_b[k] = (11.0 + na) * wb * s.N;
   }
   M.stat = sc;
   M.done = done;
@@ -2057,14 +2059,15 @@ int Solver::pcg_persist(const BoxSys* sys, int K, double rtol, int maxit, const 
   lc.numAttrs = 1;
   ++g_launches;
   {
-    ProfScope ps(prof, KC_SPMV, stream, setup_b);
+    ProfScope ps(prof, KC_PCG_PERSIST, stream, setup_b);
     CK(cudaLaunchKernelEx(&lc, k_pcg_persist<T>, M));
   }
   if (capturing) return 0;
   int conv = 0;
   poll(hsc, sc, done, stream, maxit, &conv);
-  // (the iteration bytes of the slower system stand for all: the systems iterate together)
-  if (prof && prof->on) prof->bytes[KC_SPMV] += hsc[S_ITS] * iter_b;
+  // (each system's iterations times its bytes per iteration)
+  if (prof && prof->on)
+    for (int k = 0; k < K; ++k) prof->bytes[KC_PCG_PERSIST] += hsc[S_ITSK + k] * iter_b[k];
   fill_stats(hsc, conv, out);
   return conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
 }

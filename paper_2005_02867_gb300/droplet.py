@@ -59,7 +59,8 @@ EXPORTS = ["droplet_init", "droplet_step", "droplet_diag", "droplet_field_size",
 NOALLOC_MAX_UNKNOWNS = 262144
 
 # kernel classes timed by droplet_profile
-KCLASS = dict(mg_smooth=0, spmv=1, update=2, mg_restrict=3, mg_prolong=4, mom_assemble=5, scalar_assemble=6)
+KCLASS = dict(mg_smooth=0, spmv=1, update=2, mg_restrict=3, mg_prolong=4, mom_assemble=5, scalar_assemble=6,
+              pcg_persist=7)
 
 ERR_NOT_CONVERGED = -3
 
