@@ -33,9 +33,11 @@ struct dctx {
   double *rho = nullptr, *mu = nullptr, *kc = nullptr, *cp = nullptr, *Dm = nullptr, *yq = nullptr, *dp = nullptr, *S = nullptr;
   int* adj = nullptr;
   double *bD = nullptr, *bc[3] = {nullptr, nullptr, nullptr}, *brhs = nullptr, *bx = nullptr;
-  // box systems of the second and third velocity component for the joint momentum solve
-  // (D, c0, c1, c2, rhs, x each)
-  double* xb[2][6] = {{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
+  // box systems (D, c0, c1, c2, rhs, x each) of the joint momentum solve: of the second and
+  // third velocity component (the first uses the shared box), or of every component when
+  // the momentum stage runs on its own branch
+  double* xb[3][6] = {{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
+                      {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
                       {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}};
   double *part = nullptr, *psum = nullptr, *pmax = nullptr, *scal = nullptr;
   unsigned* flags = nullptr;
@@ -43,6 +45,12 @@ struct dctx {
   double* hscal = nullptr;
   unsigned* hflags = nullptr;
   Solver solver;
+  // the momentum stage of a single droplet on a branch of its own, concurrent with energy
+  // and species: its solver workspace, stream and fork / join events
+  bool conc = false;
+  Solver solver_m;
+  cudaStream_t stm = nullptr;
+  cudaEvent_t evf = nullptr, evj = nullptr;
   Prof prof;
   cudaStream_t st2 = nullptr;        // capture stream of the solver loop bodies
   cudaStream_t own = nullptr;        // the droplet's own stream in a batch
@@ -165,6 +173,12 @@ static void free_all(dctx* c) {
   cudaFreeHost(c->hscal); cudaFreeHost(c->hflags);
   c->hscal = nullptr; c->hflags = nullptr;
   c->solver.release();
+  c->solver_m.release();
+  if (c->evf) cudaEventDestroy(c->evf);
+  if (c->evj) cudaEventDestroy(c->evj);
+  if (c->stm) cudaStreamDestroy(c->stm);
+  c->evf = c->evj = nullptr;
+  c->stm = nullptr;
   c->prof.destroy();
   if (c->st2) cudaStreamDestroy(c->st2);
   if (c->own) cudaStreamDestroy(c->own);
@@ -229,7 +243,12 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
   // the velocity components are solved together (one persistent launch)
   const bool joint = c->solver.persist_pcg && (cfg.physics_mask & DROPLET_PHYS_FLOW);
   c->solver.nsys_extra = joint ? nact(c->g) - 1 : 0;
-  for (int k = 0; k < c->solver.nsys_extra; ++k)
+  // a single droplet whose solves all run persistently forks the momentum stage (S7) onto a
+  // branch of its own, concurrent with energy and species (S5, S6): neither reads what the
+  // other writes, and both latency-bound chains then share the GPU
+  c->conc = joint && !own_stream && c->solver.persistent;
+  const int nsets = c->conc ? na : c->solver.nsys_extra;
+  for (int k = 0; k < nsets; ++k)
     for (int q = 0; q < 6; ++q)
       if (q != 3 || na == 3)
         if ((rc = dalloc(&c->xb[k][q], N))) { free_all(c); delete c; return rc; }
@@ -241,6 +260,27 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
   if ((rc = c->solver.setup(N, c->st))) { free_all(c); delete c; return rc; }
   c->solver.prof = &c->prof;
   c->solver.stream2 = c->st2;
+  if (c->conc) {
+    if (cudaStreamCreateWithFlags(&c->stm, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->evf, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->evj, cudaEventDisableTiming) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_CUDA; }
+    Solver& m = c->solver_m;
+    m.f32_helm = c->solver.f32_helm;
+    m.persistent = false;
+    m.persist_pcg = true;
+    m.nsys_extra = na - 1;
+    m.rb = c->rb;
+    if ((rc = m.setup(N, c->stm))) { free_all(c); delete c; return rc; }
+    m.prof = &c->prof;
+    m.stream2 = c->st2;
+    // SM budgets of the two branches' cooperative Jacobi-PCG launches: together at most the
+    // SM count, so that both are co-resident; the momentum solve (the longer chain) gets 7/12
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    m.pcg_budget = std::max(1, nsm * 7 / 12);
+    c->solver.pcg_budget = std::max(1, nsm - m.pcg_budget);
+  }
   if (c->cfg.physics_mask & DROPLET_PHYS_FLOW) {
     int mm[3] = {g.n[0], g.n[1], g.n[2]};
     if ((rc = c->solver.prepare_mg(mm, c->cfg.precision == 1))) { free_all(c); delete c; return rc; }
@@ -323,6 +363,78 @@ static int one_step(dctx* c, int* nc_flag) {
   for (int a = 0; a < 3; ++a) bs.c[a] = a < na ? c->bc[a] : nullptr;
   SolveStats ss;
   int rc;
+  // S7 momentum predictor, on stream ms with solver sv: the components' box systems are
+  // assembled from the old velocities (independent of S5 and S6), solved together in one
+  // persistent launch where possible, and scattered into u*
+  auto momentum = [&](cudaStream_t ms, Solver& sv) -> int {
+    int nc7 = 0, rc7 = 0;
+    SolveStats ss7;
+    if (sv.persist_pcg && sv.nsys_extra == na - 1 && (c->conc || na == 1 || c->xb[na - 2][5])) {
+      BoxSys sys[3];
+      RecordSpec recs[3];
+      for (int cc = 0; cc < na; ++cc) {
+        int m[3] = {g.n[0], g.n[1], g.n[2]};
+        m[cc] -= 1;
+        long long nbx = (long long)m[0] * m[1] * m[2];
+        BoxSys& b = sys[cc];
+        if (cc == 0 && !c->conc) {
+          b.D = c->bD; b.b = c->brhs; b.x = c->bx;
+          for (int a = 0; a < 3; ++a) b.c[a] = a < na ? c->bc[a] : nullptr;
+        } else {
+          double* const* xs = c->xb[c->conc ? cc : cc - 1];
+          b.D = xs[0]; b.b = xs[4]; b.x = xs[5];
+          for (int a = 0; a < 3; ++a) b.c[a] = a < na ? xs[1 + a] : nullptr;
+        }
+        for (int a = 0; a < 3; ++a) b.m[a] = m[a];
+        b.N = nbx;
+        {
+        ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, ms, (12.0 + 2 * na) * nbx * 8.0);
+        (c->cfg.precision == 1 ? L_mom_assemble_mx : L_mom_assemble)(
+            ms, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi, b.D, b.c[0],
+            b.c[1], na == 3 ? b.c[2] : b.c[0], (double*)b.b);
+        }
+        L_faces_to_box(ms, lin_grid(nbx), g, cc, c->u[cc], b.x, c->hu[cc], c->scal);
+        recs[cc] = RecordSpec{c->scal, SC_ITS_U, -1, cc > 0};
+      }
+      rc7 = sv.pcg_jacobi_multi(sys, na, c->cfg.helm_rtol, c->cfg.helm_maxit, recs, &ss7);
+      if (rc7 == DROPLET_ERR_NOT_CONVERGED) nc7 = 1; else if (rc7) return rc7;
+      for (int cc = 0; cc < na; ++cc) {
+        cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, ms);
+        L_mom_scatter(ms, lin_grid(nfaces(g, cc)), g, p, cc, sys[cc].x, c->us[cc]);
+      }
+      return nc7 ? DROPLET_ERR_NOT_CONVERGED : 0;
+    }
+    BoxSys bm = bs;
+    bm.x = c->bx;
+    for (int cc = 0; cc < na; ++cc) {
+      int m[3] = {g.n[0], g.n[1], g.n[2]};
+      m[cc] -= 1;
+      long long nbx = (long long)m[0] * m[1] * m[2];
+      {
+      ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, ms, (12.0 + 2 * na) * nbx * 8.0);
+      (c->cfg.precision == 1 ? L_mom_assemble_mx : L_mom_assemble)(
+          ms, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi, c->bD, c->bc[0],
+          c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+      }
+      for (int a = 0; a < 3; ++a) bm.m[a] = m[a];
+      bm.N = nbx;
+      L_faces_to_box(ms, lin_grid(nbx), g, cc, c->u[cc], c->bx, c->hu[cc], c->scal);
+      sv.record_next(c->scal, SC_ITS_U, -1, cc > 0);
+      rc7 = sv.pcg_jacobi(bm, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss7);
+      if (rc7 == DROPLET_ERR_NOT_CONVERGED) nc7 = 1; else if (rc7) return rc7;
+      sv.record(c->scal, SC_ITS_U, -1, cc > 0);
+      cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, ms);
+      L_mom_scatter(ms, lin_grid(nfaces(g, cc)), g, p, cc, c->bx, c->us[cc]);
+    }
+    return nc7 ? DROPLET_ERR_NOT_CONVERGED : 0;
+  };
+  if (c->conc && (mask & DROPLET_PHYS_FLOW)) {   // fork: S7 on its own branch
+    CKR(cudaEventRecord(c->evf, st));
+    CKR(cudaStreamWaitEvent(c->stm, c->evf, 0));
+    rc = momentum(c->stm, c->solver_m);
+    if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
+    CKR(cudaEventRecord(c->evj, c->stm));
+  }
   // S5 energy
   if ((mask & DROPLET_PHYS_ENERGY) && !p.const_props) {
     {
@@ -365,62 +477,11 @@ static int one_step(dctx* c, int* nc_flag) {
   ++g_launches, k_rhoG<<<gc, TPB, 0, st>>>(g, p, c->T, c->omega, c->rhoG);
   // S7 - S10
   if (mask & DROPLET_PHYS_FLOW) {
-    if (c->solver.persist_pcg && c->solver.nsys_extra == na - 1 && (na == 1 || c->xb[na - 2][5])) {
-      // the components' systems are independent (each is assembled from the old
-      // velocities): assemble all, solve them together, scatter all
-      BoxSys sys[3];
-      RecordSpec recs[3];
-      for (int cc = 0; cc < na; ++cc) {
-        int m[3] = {g.n[0], g.n[1], g.n[2]};
-        m[cc] -= 1;
-        long long nbx = (long long)m[0] * m[1] * m[2];
-        BoxSys& b = sys[cc];
-        if (cc == 0) {
-          b.D = c->bD; b.b = c->brhs; b.x = c->bx;
-          for (int a = 0; a < 3; ++a) b.c[a] = a < na ? c->bc[a] : nullptr;
-        } else {
-          double* const* xs = c->xb[cc - 1];
-          b.D = xs[0]; b.b = xs[4]; b.x = xs[5];
-          for (int a = 0; a < 3; ++a) b.c[a] = a < na ? xs[1 + a] : nullptr;
-        }
-        for (int a = 0; a < 3; ++a) b.m[a] = m[a];
-        b.N = nbx;
-        {
-        ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, st, (12.0 + 2 * na) * nbx * 8.0);
-        (c->cfg.precision == 1 ? L_mom_assemble_mx : L_mom_assemble)(
-            st, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi, b.D, b.c[0],
-            b.c[1], na == 3 ? b.c[2] : b.c[0], (double*)b.b);
-        }
-        L_faces_to_box(st, lin_grid(nbx), g, cc, c->u[cc], b.x, c->hu[cc], c->scal);
-        recs[cc] = RecordSpec{c->scal, SC_ITS_U, -1, cc > 0};
-      }
-      rc = c->solver.pcg_jacobi_multi(sys, na, c->cfg.helm_rtol, c->cfg.helm_maxit, recs, &ss);
-      if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
-      for (int cc = 0; cc < na; ++cc) {
-        cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, st);
-        L_mom_scatter(st, lin_grid(nfaces(g, cc)), g, p, cc, sys[cc].x, c->us[cc]);
-      }
+    if (c->conc) {
+      CKR(cudaStreamWaitEvent(st, c->evj, 0));   // join the momentum branch
     } else {
-      for (int cc = 0; cc < na; ++cc) {
-        int m[3] = {g.n[0], g.n[1], g.n[2]};
-        m[cc] -= 1;
-        long long nbx = (long long)m[0] * m[1] * m[2];
-        {
-        ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, st, (12.0 + 2 * na) * nbx * 8.0);
-        (c->cfg.precision == 1 ? L_mom_assemble_mx : L_mom_assemble)(
-            st, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi, c->bD, c->bc[0],
-            c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
-        }
-        for (int a = 0; a < 3; ++a) bs.m[a] = m[a];
-        bs.N = nbx;
-        L_faces_to_box(st, lin_grid(nbx), g, cc, c->u[cc], c->bx, c->hu[cc], c->scal);
-        c->solver.record_next(c->scal, SC_ITS_U, -1, cc > 0);
-        rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
-        if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
-        c->solver.record(c->scal, SC_ITS_U, -1, cc > 0);
-        cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, st);
-        L_mom_scatter(st, lin_grid(nfaces(g, cc)), g, p, cc, c->bx, c->us[cc]);
-      }
+      rc = momentum(st, c->solver);
+      if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
     }
     double* us2 = c->us[2] ? c->us[2] : c->us[0];
     L_poisson_assemble(st, gc, g, p, c->mdot, c->alpha, c->rhoG_old, c->rhoG, c->u[0], c->u[1], u2,
@@ -488,9 +549,9 @@ static int capture_step(droplet_ctx* c) {
   for (size_t i = 0; i < c->d.size() && !rc; ++i) {
     dctx* x = c->d[i];
     if (batch) cudaStreamWaitEvent(x->st, c->ev[0], 0);
-    x->solver.capturing = true;
+    x->solver.capturing = x->solver_m.capturing = true;
     rc = one_step(x, &nc);
-    x->solver.capturing = false;
+    x->solver.capturing = x->solver_m.capturing = false;
     if (batch) {
       cudaEventRecord(c->ev[1 + i], x->st);
       cudaStreamWaitEvent(c->st, c->ev[1 + i], 0);

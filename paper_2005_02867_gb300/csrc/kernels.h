@@ -186,6 +186,7 @@ class Solver {
   // statistics of system k go to recs[k]
   int pcg_jacobi_multi(const BoxSys* s, int K, double rtol, int maxit, const RecordSpec* recs, SolveStats* out);
   int sm_budget = 0;                // SMs the persistent solves may use (0: the whole GPU)
+  int pcg_budget = 0;               // SMs the persistent Jacobi-PCG may use (0: sm_budget)
   int mg_tile[2] = {32, 32};        // tile of the persistent MG's temporal blocking (autotuned)
   size_t pmg_smem_max = 0;          // dynamic shared memory the persistent MG may request
   static constexpr long long PERSIST_MAX_CELLS = 1LL << 22;   // persistent MG: latency-bound sizes only

@@ -2038,7 +2038,8 @@ int Solver::pcg_persist(const BoxSys* sys, int K, double rtol, int maxit, const 
   M.err = err;
   int grid = (int)((nmax + PTPB - 1) / PTPB);
   int cap = persist_blocks(f32);
-  if (sm_budget > 0) cap = std::min(cap, sm_budget * std::max(1, cap / nsm_));
+  const int bud = pcg_budget > 0 ? pcg_budget : sm_budget;
+  if (bud > 0) cap = std::min(cap, bud * std::max(1, cap / nsm_));
   if (grid > cap) grid = cap;
   // partials in `part` (8 RED_BLOCKS doubles): the FP64 initial norms (2 x 2 PMAXSYS per
   // block) first, then the sums of precision T (2 x 3 PMAXSYS per block)
