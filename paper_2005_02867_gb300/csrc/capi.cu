@@ -329,10 +329,9 @@ static int one_step(dctx* c, int* nc_flag) {
   int gc = lin_grid(N), nb = red_grid_cap(N, c->rb);
   double* u2 = c->u[2] ? c->u[2] : c->u[0];
   int mask = p.physics;
-  cudaMemsetAsync(c->scal + SC_ITS_P, 0, sizeof(double) * 5, st);
-  // S0
-  ++g_launches, k_thermo_pin<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->T, c->omega, c->rhoG, c->rhoG_old, c->flags, c->dirty);
-  cudaMemsetAsync(c->dirty, 0, sizeof(int), st);
+  // S0 (with the reset of the step's solver statistics)
+  ++g_launches, k_thermo_pin<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->T, c->omega, c->rhoG, c->rhoG_old, c->flags, c->dirty,
+                                                 c->scal);
   // S1, S2
   if (mask & DROPLET_PHYS_EVAP) {
     L_evap_raw(st, nb, g, p, c->alpha, c->omega, c->rhoG_old, c->u[0], c->u[1], u2, c->mraw, c->adj, c->part, c->flags);
@@ -341,23 +340,26 @@ static int one_step(dctx* c, int* nc_flag) {
     cudaMemsetAsync(c->mraw, 0, sizeof(double) * N, st);
     cudaMemsetAsync(c->scal + SC_K, 0, sizeof(double), st);
   }
-  ++g_launches, k_alpha_source<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->mraw, c->scal, c->mdot, c->astar, c->flags);
-  // S3
+  ++g_launches, k_alpha_source<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->mraw, c->scal, c->mdot, c->astar, c->flags,
+                                                   c->dirty);
+  // S3, and S4 (the mixture properties) in the kernel that forms alpha^{n+1}
+  const PropsOut po{c->rhoG_old, c->omega, c->rho, c->mu, c->kc, c->cp, c->Dm};
   if (mask & DROPLET_PHYS_FLOW) {
-    for (int a = 0; a < na; ++a)
-      (c->cfg.precision == 1 ? L_adv_faces_mx : L_adv_faces)(st, lin_grid(nfaces(g, a)), g, p, a, c->astar, c->u[a],
-                                                             c->FL[a], c->AF[a]);
+    if (c->cfg.precision == 1) {
+      L_adv_faces_mx_all(st, g, p, c->astar, c->u, c->FL, c->AF);
+    } else {
+      for (int a = 0; a < na; ++a)
+        L_adv_faces(st, lin_grid(nfaces(g, a)), g, p, a, c->astar, c->u[a], c->FL[a], c->AF[a]);
+    }
     double* F2 = c->FL[2] ? c->FL[2] : c->FL[0];
     double* A2 = c->AF[2] ? c->AF[2] : c->AF[0];
     ++g_launches, k_adv_low<<<gc, TPB, 0, st>>>(g, c->astar, c->FL[0], c->FL[1], F2, c->aL);
     L_adv_limit(st, gc, g, c->astar, c->aL, c->AF[0], c->AF[1], A2, c->Rp, c->Rm);
-    L_adv_update(st, nb, g, c->aL, c->AF[0], c->AF[1], A2, c->Rp, c->Rm, c->alpha, c->part, c->flags);
+    L_adv_update(st, nb, g, p, c->aL, c->AF[0], c->AF[1], A2, c->Rp, c->Rm, c->alpha, c->part, c->flags, po);
   } else {
-    ++g_launches, k_alpha_clip_only<<<nb, TPB, 0, st>>>(g, c->astar, c->alpha, c->part);
+    ++g_launches, k_alpha_clip_only<<<nb, TPB, 0, st>>>(g, p, c->astar, c->alpha, c->part, po);
   }
   ++g_launches, k_clip_finish<<<1, TPB, 0, st>>>(c->part, nb, c->scal, c->flags);
-  // S4
-  ++g_launches, k_props<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->rhoG_old, c->omega, c->rho, c->mu, c->kc, c->cp, c->Dm);
   BoxSys bs;
   bs.D = c->bD; bs.b = c->brhs; bs.x = c->bx;
   for (int a = 0; a < 3; ++a) bs.c[a] = a < na ? c->bc[a] : nullptr;
@@ -486,19 +488,16 @@ static int one_step(dctx* c, int* nc_flag) {
     double* us2 = c->us[2] ? c->us[2] : c->us[0];
     L_poisson_assemble(st, gc, g, p, c->mdot, c->alpha, c->rhoG_old, c->rhoG, c->u[0], c->u[1], u2,
                                            c->us[0], c->us[1], us2, c->rho, c->S, c->bD, c->bc[0], c->bc[1],
-                                           na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+                                           na == 3 ? c->bc[2] : c->bc[0], c->brhs, c->dp);
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
-    bs.x = c->dp;   // pressure increment from a zero initial guess, solved in place
-    cudaMemsetAsync(c->dp, 0, sizeof(double) * N, st);
+    bs.x = c->dp;   // pressure increment from a zero initial guess (set by the assembly), solved in place
     c->solver.record_next(c->scal, SC_ITS_P, SC_RES_P, 0);
     rc = c->solver.pcg_mg(bs, c->cfg.cg_rtol, c->cfg.cg_maxit, c->cfg.precision == 1, &ss);
     if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
     c->solver.record(c->scal, SC_ITS_P, SC_RES_P, 0);
     bs.x = c->bx;
-    for (int cc = 0; cc < na; ++cc)
-      L_correct(st, lin_grid(nfaces(g, cc)), g, p, cc, c->us[cc], c->dp, c->rho, c->u[cc]);
-    ++g_launches, k_add<<<gc, TPB, 0, st>>>(N, c->pr, c->dp);
+    L_correct_all(st, g, p, c->us, c->dp, c->rho, c->u, c->pr);
   } else {
     cudaMemsetAsync(c->dp, 0, sizeof(double) * N, st);
     cudaMemsetAsync(c->S, 0, sizeof(double) * N, st);

@@ -53,16 +53,21 @@ enum {
 __global__ void k_init(Geo g, Phys p, double* alpha, double* T, double* omega, double* rhoG);
 __global__ void k_xi(Geo g, Phys p, double* xi);
 __global__ void k_thermo_pin(Geo g, Phys p, const double* alpha, const double* T, double* omega,
-                             const double* rhoG, double* rhoG_old, unsigned* flags, const int* dirty);
+                             const double* rhoG, double* rhoG_old, unsigned* flags, const int* dirty, double* scal);
 
 __global__ void k_evap_K(const double* partials, int nblk, double* scal, unsigned* flags);
 __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double* mraw, const double* scal,
-                               double* mdot, double* alpha_star, unsigned* flags);
+                               double* mdot, double* alpha_star, unsigned* flags, int* dirty);
 
 __global__ void k_adv_low(Geo g, const double* as, const double* F0, const double* F1, const double* F2, double* aL);
 
 __global__ void k_clip_finish(const double* partials, int nblk, double* scal, unsigned* flags);
-__global__ void k_alpha_clip_only(Geo g, const double* as, double* alpha, double* partials);
+// mixture properties of a cell (S4), formed where alpha^{n+1} is (the FCT update, the clip)
+struct PropsOut {
+  const double *rhoG, *omega;
+  double *rho, *mu, *kc, *cp, *D;
+};
+__global__ void k_alpha_clip_only(Geo g, Phys p, const double* as, double* alpha, double* partials, PropsOut po);
 __global__ void k_props(Geo g, Phys p, const double* alpha, const double* rhoG, const double* omega, double* rho,
                         double* mu, double* kc, double* cp, double* D);
 
@@ -80,15 +85,20 @@ __global__ void k_extrap(long long n, double* x, double* xh, const double* scal)
 void L_evap_raw(cudaStream_t st, int grid, Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* mraw, int* adj, double* partials, unsigned* flags);
 void L_adv_faces(cudaStream_t st, int grid, Geo g, Phys p, int a, const double* as, const double* ua, double* FL, double* AF);
 void L_adv_limit(cudaStream_t st, int grid, Geo g, const double* as, const double* aL, const double* A0, const double* A1, const double* A2, double* Rp, double* Rm);
-void L_adv_update(cudaStream_t st, int grid, Geo g, const double* aL, const double* A0, const double* A1, const double* A2, const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags);
+void L_adv_update(cudaStream_t st, int grid, Geo g, Phys p, const double* aL, const double* A0, const double* A1, const double* A2, const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags, PropsOut po);
 void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs);
-void L_adv_faces_mx(cudaStream_t st, int grid, Geo g, Phys p, int a, const double* as, const double* ua, double* FL, double* AF);
+// the alpha face fluxes of every direction in one launch (mixed precision)
+void L_adv_faces_mx_all(cudaStream_t st, Geo g, Phys p, const double* as, double* const u[3], double* const FL[3],
+                        double* const AF[3]);
 void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs);
 void L_mom_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs);
 void L_mom_assemble(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs);
 void L_mom_scatter(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* x, double* us);
-void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo, const double* rgn, const double* u0, const double* u1, const double* u2, const double* us0, const double* us1, const double* us2, const double* rho, double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs);
+void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo, const double* rgn, const double* u0, const double* u1, const double* u2, const double* us0, const double* us1, const double* us2, const double* rho, double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs, double* dp0);
 void L_correct(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u);
+// the velocity correction of every direction and p_rgh += dp in one launch
+void L_correct_all(cudaStream_t st, Geo g, Phys p, double* const us[3], const double* dp, const double* rho,
+                   double* const u[3], double* pr);
 void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax);
 
 void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x, double* uh,

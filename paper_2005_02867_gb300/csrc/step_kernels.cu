@@ -116,10 +116,12 @@ __global__ void k_xi(Geo g, Phys p, double* xi) {
 // The state rho_G left by the previous step is rho_gas(T, omega) of the same T and
 // omega (and the pinned values Y_eq(T) are unchanged), so only liquid cells are
 // re-evaluated, unless a field was overwritten since (*dirty != 0).
+// (also resets the step's solver statistics, scal[SC_ITS_P .. SC_RES_P])
 __global__ void k_thermo_pin(Geo g, Phys p, const double* alpha, const double* T, double* omega,
-                             const double* rhoG, double* rhoG_old, unsigned* flags, const int* dirty) {
+                             const double* rhoG, double* rhoG_old, unsigned* flags, const int* dirty, double* scal) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
+  if (id <= SC_RES_P - SC_ITS_P) scal[SC_ITS_P + id] = 0.0;
   unsigned boil = 0;
   double w = omega[id];
   bool liq = alpha[id] >= 0.5;
@@ -247,10 +249,12 @@ __global__ void k_evap_K(const double* partials, int nblk, double* scal, unsigne
 }
 
 // ============================================================== S2 alpha source
+// (also clears the state-overwritten flag that S0 consumed)
 __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double* mraw, const double* scal,
-                               double* mdot, double* alpha_star, unsigned* flags) {
+                               double* mdot, double* alpha_star, unsigned* flags, int* dirty) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
+  if (id == 0) *dirty = 0;
   double a = alpha[id];
   double K = scal[SC_K];
   double m = (K == 0.0) ? 0.0 : K * sqrt(a * (1.0 - a)) * mraw[id];
@@ -317,6 +321,26 @@ __global__ void k_adv_low(Geo g, const double* as, const double* F0, const doubl
   aL[id] = as[id] - face_net(g, F0, F1, F2, i, j, k) * rcp64(cellV(g, i));
 }
 
+// ============================================================== S4 mixture properties
+__device__ __forceinline__ void props_cell(const Phys& p, long long id, double a, const double* rhoG,
+                                           const double* omega, double* rho, double* mu, double* kc, double* cp,
+                                           double* D) {
+  const double w = omega[id];
+  rho[id] = a * p.rho_l + (1.0 - a) * rhoG[id];
+  mu[id] = a * p.mu_l + (1.0 - a) * p.mu_g;
+  kc[id] = a * p.k_l + (1.0 - a) * p.k_g;
+  double cpG = w * p.cp_v + (1.0 - w) * p.cp_g;
+  cp[id] = a * p.cp_l + (1.0 - a) * cpG;
+  D[id] = a * p.D_l + (1.0 - a) * p.D_gas;
+}
+
+__global__ void k_props(Geo g, Phys p, const double* alpha, const double* rhoG, const double* omega, double* rho,
+                        double* mu, double* kc, double* cp, double* D) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  props_cell(p, id, alpha[id], rhoG, omega, rho, mu, kc, cp, D);
+}
+
 // Zalesak limiter ratios R+ and R- from the local bounds over the cell and its face neighbours.
 template <int NA>
 __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const double* A0, const double* A1,
@@ -371,8 +395,10 @@ __device__ __forceinline__ double limited_flux(const Geo& g, int a, const double
 
 // alpha^{n+1} = alpha^L - sum C A / V, clipped to [0, 1] with the clipped volume summed.
 template <int NA>
-__global__ void k_adv_update(Geo g, const double* aL, const double* A0, const double* A1, const double* A2,
-                             const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags) {
+// (and the mixture properties of the cell from alpha^{n+1}, S4)
+__global__ void k_adv_update(Geo g, Phys p, const double* aL, const double* A0, const double* A1, const double* A2,
+                             const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags,
+                             PropsOut po) {
   double acc[2] = {0.0, 0.0};
   const double* AA[3] = {A0, A1, A2};
   constexpr int na = NA;
@@ -391,6 +417,7 @@ __global__ void k_adv_update(Geo g, const double* aL, const double* A0, const do
     double ac = iclamp01(an);
     if (ac != an) { acc[1] += 1.0; acc[0] += (an - ac) * V; }
     alpha[id] = ac;
+    props_cell(p, id, ac, po.rhoG, po.omega, po.rho, po.mu, po.kc, po.cp, po.D);
   }
   block_sum_store<2>(acc, partials);
 }
@@ -405,7 +432,7 @@ __global__ void k_clip_finish(const double* partials, int nblk, double* scal, un
 }
 
 // no advection: clip alpha* into alpha
-__global__ void k_alpha_clip_only(Geo g, const double* as, double* alpha, double* partials) {
+__global__ void k_alpha_clip_only(Geo g, Phys p, const double* as, double* alpha, double* partials, PropsOut po) {
   double acc[2] = {0.0, 0.0};
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
@@ -413,22 +440,9 @@ __global__ void k_alpha_clip_only(Geo g, const double* as, double* alpha, double
     double an = as[id], ac = iclamp01(an);
     if (ac != an) { acc[1] += 1.0; acc[0] += (an - ac) * cellV(g, i); }
     alpha[id] = ac;
+    props_cell(p, id, ac, po.rhoG, po.omega, po.rho, po.mu, po.kc, po.cp, po.D);
   }
   block_sum_store<2>(acc, partials);
-}
-
-// ============================================================== S4 mixture properties
-__global__ void k_props(Geo g, Phys p, const double* alpha, const double* rhoG, const double* omega, double* rho,
-                        double* mu, double* kc, double* cp, double* D) {
-  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (id >= g.N) return;
-  double a = alpha[id], w = omega[id];
-  rho[id] = a * p.rho_l + (1.0 - a) * rhoG[id];
-  mu[id] = a * p.mu_l + (1.0 - a) * p.mu_g;
-  kc[id] = a * p.k_l + (1.0 - a) * p.k_g;
-  double cpG = w * p.cp_v + (1.0 - w) * p.cp_g;
-  cp[id] = a * p.cp_l + (1.0 - a) * cpG;
-  D[id] = a * p.D_l + (1.0 - a) * p.D_gas;
 }
 
 // ============================================================== S5 / S6 scalar transport systems
@@ -761,9 +775,11 @@ template <int NA>
 __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo,
                                    const double* rgn, const double* u0, const double* u1, const double* u2,
                                    const double* us0, const double* us1, const double* us2, const double* rho,
-                                   double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+                                   double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs,
+                                   double* dp0) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
+  dp0[id] = 0.0;   // the solve's zero initial guess
   int i, j, k;
   decomp(id, g.n[0], g.n[1], i, j, k);
   constexpr int na = NA;
@@ -811,11 +827,9 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
 // u = u* - dt beta_f (dp_R - dp_L)/A_f with dp = 0 beyond open faces (half-cell distance);
 // beta_f / A_f = 1 / (h rho_f)
 template <int C>
-__global__ void k_correct(Geo g, Phys p, const double* us, const double* dp, const double* rho, double* u) {
+__device__ __forceinline__ void correct_face(const Geo& g, const Phys& p, const double* us, const double* dp,
+                                             const double* rho, double* u, long long id) {
   constexpr int c = C;
-  long long nf = nfaces(g, c);
-  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (id >= nf) return;
   int m0 = g.n[0] + (c == 0), m1 = g.n[1] + (c == 1);
   int f[3];
   decomp(id, m0, m1, f[0], f[1], f[2]);
@@ -837,6 +851,39 @@ __global__ void k_correct(Geo g, Phys p, const double* us, const double* dp, con
     }
   }
   u[id] = us[id] - corr;
+}
+
+template <int C>
+__global__ void k_correct(Geo g, Phys p, const double* us, const double* dp, const double* rho, double* u) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= nfaces(g, C)) return;
+  correct_face<C>(g, p, us, dp, rho, u, id);
+}
+
+// every direction's correction and p_rgh += dp, one launch: blocks [0, b0) take the faces
+// of direction 0, then direction 1 (and 2), then the cells
+struct CorrectArgs {
+  const double* us[3];
+  double* u[3];
+  const double *dp, *rho;
+  double* pr;
+  int b[4];   // first block of each segment (directions, then cells)
+};
+__global__ void k_correct_all(Geo g, Phys p, CorrectArgs a) {
+  const int bx = blockIdx.x;
+  if (bx < a.b[1]) {
+    long long id = (long long)(bx - a.b[0]) * blockDim.x + threadIdx.x;
+    if (id < nfaces(g, 0)) correct_face<0>(g, p, a.us[0], a.dp, a.rho, a.u[0], id);
+  } else if (bx < a.b[2]) {
+    long long id = (long long)(bx - a.b[1]) * blockDim.x + threadIdx.x;
+    if (id < nfaces(g, 1)) correct_face<1>(g, p, a.us[1], a.dp, a.rho, a.u[1], id);
+  } else if (bx < a.b[3]) {
+    long long id = (long long)(bx - a.b[2]) * blockDim.x + threadIdx.x;
+    if (id < nfaces(g, 2)) correct_face<2>(g, p, a.us[2], a.dp, a.rho, a.u[2], id);
+  } else {
+    long long id = (long long)(bx - a.b[3]) * blockDim.x + threadIdx.x;
+    if (id < g.N) a.pr[id] += a.dp[id];
+  }
 }
 
 __global__ void k_add(long long n, double* y, const double* x) {
@@ -944,10 +991,10 @@ void L_adv_limit(cudaStream_t st, int grid, Geo g, const double* as, const doubl
   else k_adv_limit<2><<<grid, TPB, 0, st>>>(g, as, aL, A0, A1, A2, Rp, Rm);
 }
 
-void L_adv_update(cudaStream_t st, int grid, Geo g, const double* aL, const double* A0, const double* A1, const double* A2, const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags) {
+void L_adv_update(cudaStream_t st, int grid, Geo g, Phys p, const double* aL, const double* A0, const double* A1, const double* A2, const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags, PropsOut po) {
   ++g_launches;
-  if (nact(g) == 3) k_adv_update<3><<<grid, TPB, 0, st>>>(g, aL, A0, A1, A2, Rp, Rm, alpha, partials, flags);
-  else k_adv_update<2><<<grid, TPB, 0, st>>>(g, aL, A0, A1, A2, Rp, Rm, alpha, partials, flags);
+  if (nact(g) == 3) k_adv_update<3><<<grid, TPB, 0, st>>>(g, p, aL, A0, A1, A2, Rp, Rm, alpha, partials, flags, po);
+  else k_adv_update<2><<<grid, TPB, 0, st>>>(g, p, aL, A0, A1, A2, Rp, Rm, alpha, partials, flags, po);
 }
 
 void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
@@ -975,10 +1022,10 @@ void L_mom_scatter(cudaStream_t st, int grid, Geo g, Phys p, int c, const double
   else k_mom_scatter<2><<<grid, TPB, 0, st>>>(g, p, x, us);
 }
 
-void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo, const double* rgn, const double* u0, const double* u1, const double* u2, const double* us0, const double* us1, const double* us2, const double* rho, double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo, const double* rgn, const double* u0, const double* u1, const double* u2, const double* us0, const double* us1, const double* us2, const double* rho, double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs, double* dp0) {
   ++g_launches;
-  if (nact(g) == 3) k_poisson_assemble<3><<<grid, TPB, 0, st>>>(g, p, mdot, alpha, rgo, rgn, u0, u1, u2, us0, us1, us2, rho, S, Dg, c0, c1, c2, rhs);
-  else k_poisson_assemble<2><<<grid, TPB, 0, st>>>(g, p, mdot, alpha, rgo, rgn, u0, u1, u2, us0, us1, us2, rho, S, Dg, c0, c1, c2, rhs);
+  if (nact(g) == 3) k_poisson_assemble<3><<<grid, TPB, 0, st>>>(g, p, mdot, alpha, rgo, rgn, u0, u1, u2, us0, us1, us2, rho, S, Dg, c0, c1, c2, rhs, dp0);
+  else k_poisson_assemble<2><<<grid, TPB, 0, st>>>(g, p, mdot, alpha, rgo, rgn, u0, u1, u2, us0, us1, us2, rho, S, Dg, c0, c1, c2, rhs, dp0);
 }
 
 void L_correct(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u) {
@@ -986,6 +1033,25 @@ void L_correct(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* us
   if (c == 0) k_correct<0><<<grid, TPB, 0, st>>>(g, p, us, dp, rho, u);
   else if (c == 1) k_correct<1><<<grid, TPB, 0, st>>>(g, p, us, dp, rho, u);
   else k_correct<2><<<grid, TPB, 0, st>>>(g, p, us, dp, rho, u);
+}
+
+void L_correct_all(cudaStream_t st, Geo g, Phys p, double* const us[3], const double* dp, const double* rho,
+                   double* const u[3], double* pr) {
+  CorrectArgs a;
+  const int na = nact(g);
+  int b = 0;
+  for (int c = 0; c < 3; ++c) {
+    a.b[c] = b;
+    a.us[c] = us[c];
+    a.u[c] = u[c];
+    if (c < na) b += lin_grid(nfaces(g, c));
+  }
+  a.b[3] = b;
+  a.dp = dp;
+  a.rho = rho;
+  a.pr = pr;
+  ++g_launches;
+  k_correct_all<<<b + lin_grid(g.N), TPB, 0, st>>>(g, p, a);
 }
 
 void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax) {

@@ -386,11 +386,9 @@ __device__ __forceinline__ void grad_alpha_f(const Geo& g, const GeoF& q, const 
 // antisymmetrically, so the volume stays conserved whatever their precision, and the
 // limiter bounds the result as in k_adv_faces.
 template <int DIR, int NA>
-__global__ void k_adv_faces_mx(Geo g, Phys p, const double* as, const double* ua, double* FL, double* AF) {
+__device__ __forceinline__ void adv_face_mx(const Geo& g, const Phys& p, const double* as, const double* ua,
+                                            double* FL, double* AF, long long id) {
   constexpr int a = DIR;
-  long long nf = nfaces(g, a);
-  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (id >= nf) return;
   int m0 = g.n[0] + (a == 0), m1 = g.n[1] + (a == 1);
   int f[3];
   decomp(id, m0, m1, f[0], f[1], f[2]);
@@ -426,17 +424,43 @@ __global__ void k_adv_faces_mx(Geo g, Phys p, const double* as, const double* ua
   AF[id] = f64_of(A);
 }
 
-void L_adv_faces_mx(cudaStream_t st, int grid, Geo g, Phys p, int a, const double* as, const double* ua, double* FL,
-                    double* AF) {
-  ++g_launches;
-  if (nact(g) == 3) {
-    if (a == 0) k_adv_faces_mx<0, 3><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
-    else if (a == 1) k_adv_faces_mx<1, 3><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
-    else k_adv_faces_mx<2, 3><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
-  } else {
-    if (a == 0) k_adv_faces_mx<0, 2><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
-    else k_adv_faces_mx<1, 2><<<grid, TPB, 0, st>>>(g, p, as, ua, FL, AF);
+// the faces of every direction in one launch: blocks [b[d], b[d + 1]) take direction d
+struct AdvFacesArgs {
+  const double* ua[3];
+  double *FL[3], *AF[3];
+  int b[4];
+};
+template <int NA>
+__global__ void k_adv_faces_mx(Geo g, Phys p, const double* as, AdvFacesArgs f) {
+  const int bx = blockIdx.x;
+  if (bx < f.b[1]) {
+    const long long id = (long long)(bx - f.b[0]) * blockDim.x + threadIdx.x;
+    if (id < nfaces(g, 0)) adv_face_mx<0, NA>(g, p, as, f.ua[0], f.FL[0], f.AF[0], id);
+  } else if (bx < f.b[2]) {
+    const long long id = (long long)(bx - f.b[1]) * blockDim.x + threadIdx.x;
+    if (id < nfaces(g, 1)) adv_face_mx<1, NA>(g, p, as, f.ua[1], f.FL[1], f.AF[1], id);
+  } else if (NA == 3) {
+    const long long id = (long long)(bx - f.b[2]) * blockDim.x + threadIdx.x;
+    if (id < nfaces(g, 2)) adv_face_mx<2, NA>(g, p, as, f.ua[2], f.FL[2], f.AF[2], id);
   }
+}
+
+void L_adv_faces_mx_all(cudaStream_t st, Geo g, Phys p, const double* as, double* const u[3], double* const FL[3],
+                        double* const AF[3]) {
+  AdvFacesArgs f;
+  const int na = nact(g);
+  int b = 0;
+  for (int c = 0; c < 3; ++c) {
+    f.b[c] = b;
+    f.ua[c] = u[c];
+    f.FL[c] = FL[c];
+    f.AF[c] = AF[c];
+    if (c < na) b += lin_grid(nfaces(g, c));
+  }
+  f.b[3] = b;
+  ++g_launches;
+  if (na == 3) k_adv_faces_mx<3><<<b, TPB, 0, st>>>(g, p, as, f);
+  else k_adv_faces_mx<2><<<b, TPB, 0, st>>>(g, p, as, f);
 }
 
 void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi,
