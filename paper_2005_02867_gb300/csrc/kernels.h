@@ -233,7 +233,7 @@ class Solver {
   int* err = nullptr;           // set when a grid barrier wait ran out
   int pb_f32 = 0, pb_f64 = 0;   // co-resident blocks of the persistent solver
   int build_mg(const BoxSys& s, int fp32);
-  void vcycle(int fp32);
+  void vcycle(int fp32, bool casts);
   long long cap = 0;
   double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *idg = nullptr;
   double* part = nullptr;       // reduction partials

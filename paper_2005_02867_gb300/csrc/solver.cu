@@ -142,9 +142,11 @@ __global__ void k_fin_alpha(const double* part, int nblk, double* sc, const int*
   }
 }
 
-// x += alpha p, r -= alpha Ap; Jacobi: z = r / diag and r.z; both: r.r
+// x += alpha p, r -= alpha Ap; Jacobi: z = r / diag and r.z; both: r.r.  bf (optional): the
+// new r rounded to FP32 as the right-hand side of an FP32 multigrid's level 0
 __global__ void k_update(long long N, double* x, double* r, const double* p, const double* Ap, const double* idg,
-                         double* z, int jacobi, double* sc, double* part, int* done, unsigned* cnt) {
+                         double* z, int jacobi, double* sc, double* part, int* done, unsigned* cnt,
+                         float* bf = nullptr) {
   if (*done) return;
   double al = sc[S_ALPHA];
   double acc[2] = {0, 0};
@@ -152,6 +154,7 @@ __global__ void k_update(long long N, double* x, double* r, const double* p, con
     x[id] += al * p[id];
     double rr = r[id] - al * Ap[id];
     r[id] = rr;
+    if (bf) bf[id] = (float)rr;
     acc[1] += rr * rr;
     if (jacobi) {
       double zz = idg[id] * rr;
@@ -197,13 +200,22 @@ __global__ void k_fin_iter(const double* part, int nblk, double* sc, int* done, 
   }
 }
 
-// r.z; with a counter the last block also sets beta = rz_new / rz (first = 1: only rz)
-__global__ void k_dot_rz(long long N, const double* r, const double* z, double* part, const int* done, double* sc,
-                         unsigned* cnt, int first) {
+// r.z; with a counter the last block also sets beta = rz_new / rz (first = 1: only rz).
+// zf (optional): z as an FP32 multigrid left it, widened into z here
+__global__ void k_dot_rz(long long N, const double* r, double* z, double* part, const int* done, double* sc,
+                         unsigned* cnt, int first, const float* zf = nullptr) {
   if (*done) return;
   double acc[1] = {0.0};
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N; id += (long long)gridDim.x * blockDim.x)
-    acc[0] += r[id] * z[id];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N; id += (long long)gridDim.x * blockDim.x) {
+    double zz;
+    if (zf) {
+      zz = (double)zf[id];
+      z[id] = zz;
+    } else {
+      zz = z[id];
+    }
+    acc[0] += r[id] * zz;
+  }
   block_sum_store<1>(acc, part);
   if (cnt && last_block(cnt)) {
     double rz = block_sum_partials(part, gridDim.x);
@@ -2361,13 +2373,15 @@ static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaSt
   }
 }
 
-void Solver::vcycle(int fp32) {
+// z = M r by one V-cycle; in an FP32 hierarchy with casts = false the caller has rounded r
+// into level 0's b and widens level 0's x into z itself (fused into its CG kernels)
+void Solver::vcycle(int fp32, bool casts) {
   MGLevel& L0 = lev[0];
   int g0 = lin_grid(L0.N);
   if (fp32) {
-    ++g_launches, k_cast_done<float, double><<<g0, TPB, 0, stream>>>(L0.N, (float*)L0.b, r, done);
+    if (casts) ++g_launches, k_cast_done<float, double><<<g0, TPB, 0, stream>>>(L0.N, (float*)L0.b, r, done);
     vcycle_t<float>(prof, lev, nlev, done, stream);
-    ++g_launches, k_cast_done<double, float><<<g0, TPB, 0, stream>>>(L0.N, z, (const float*)L0.x, done);
+    if (casts) ++g_launches, k_cast_done<double, float><<<g0, TPB, 0, stream>>>(L0.N, z, (const float*)L0.x, done);
   } else {
     vcycle_t<double>(prof, lev, nlev, done, stream);
   }
@@ -2481,8 +2495,10 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
   int g = lin_grid(s.N);
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, nullptr, nullptr);
-  vcycle(fp32);
+  vcycle(fp32, true);
   ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done, sc, cnt, 1);
+  float* const bf = fp32 ? (float*)lev[0].b : nullptr;
+  const float* const zf = fp32 ? (const float*)lev[0].x : nullptr;
   ++g_launches, k_cast_done<double, double><<<g, TPB, 0, stream>>>(s.N, p, z, done);
   auto iteration = [&]() {
     {
@@ -2490,11 +2506,11 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
       ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt);
     }
     {
-      ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0, 6.0 * s.N);
-      ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 0, sc, part, done, cnt);
+      ProfScope ps(prof, KC_UPDATE, stream, (5.0 * 8.0 + (fp32 ? 4.0 : 0.0)) * s.N, 6.0 * s.N);
+      ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 0, sc, part, done, cnt, bf);
     }
-    vcycle(fp32);
-    ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done, sc, cnt, 0);
+    vcycle(fp32, false);
+    ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done, sc, cnt, 0, zf);
     ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
   };
   if (capturing) return device_loop(iteration);
