@@ -230,6 +230,21 @@ class SerialDroplets:
             s.close()
 
 
+def step_model_bytes(cfg, its):
+    """Algorithmic HBM bytes of one step of one droplet (the whole step, not one kernel),
+    with its = {"p", "T", "w", "u"} the step's iteration counts (u summed over the
+    velocity components): the stage sweeps (32 + 14 d + d^2) w_s per cell, the
+    Jacobi-PCG 11 w_s per cell and iteration of each Helmholtz system, and per MG-PCG
+    iteration (d + 12) 8 + c (5 d + 18) w_s per cell (c = 4/3 in 2D, 8/7 in 3D: the level
+    sum), w_s = 8 in FP64 and 4 in mixed precision (the stencil word)."""
+    d = 3 if cfg["geom"] == 1 else 2
+    ws = 8.0 if cfg["precision"] == 0 else 4.0
+    c = 4.0 / 3.0 if d == 2 else 8.0 / 7.0
+    per_cell = (32 + 14 * d + d * d) * ws + (its["T"] + its["w"] + its["u"]) * 11.0 * ws \
+        + its["p"] * ((d + 12) * 8.0 + c * (5 * d + 18) * ws)
+    return per_cell * cells_of(cfg)
+
+
 def replica_throughput(t_ms, ncell, steps):
     """Whole-job throughput of independent replicas: every rank advanced ncell
     cells by `steps` steps in its own t_ms; the job's time is the slowest
@@ -347,6 +362,11 @@ def run_ours(args):
     prof = {k: D.droplet_profile_read(sim.h, k) for k in D.KCLASS}
     D.droplet_profile(sim.h, 0)
     diag_run = sim.diag()   # solver iterations of a step of the run (the e2e leg restarts from uploads)
+    cl_run = cfg if isinstance(cfg, list) else [cfg]
+    model_b = 0.0
+    for di, cd in enumerate(cl_run):
+        dd = diag_run if di == 0 else sim.diag(di)
+        model_b += step_model_bytes(cd, {"p": dd["its_p"], "T": dd["its_T"], "w": dd["its_w"], "u": dd["its_u"]})
     launches = int(round(launches_per_step * args.steps))
     value, t_ms = replica_throughput(t_ms_local, ncell, args.steps)
 
@@ -419,6 +439,12 @@ def run_ours(args):
             "gpu_launches_note": "kernel nodes per step counted on the directly launched profiling steps x timed steps",
             "solver_iterations_last_step": {"p": diag_run["its_p"], "T": diag_run["its_T"],
                                             "omega": diag_run["its_w"], "u": diag_run["its_u"]},
+            # the whole step against HBM: algorithmic bytes of the step's model (stage sweeps,
+            # Helmholtz and MG-PCG iterations as counted) over the device-timed step
+            "step_model": {"bytes_per_step": model_b,
+                           "GBps": model_b / (t_ms / args.steps / 1e3) / 1e9 if t_ms > 0 else 0.0,
+                           "frac": (model_b / (t_ms / args.steps / 1e3) / 1e9) / peak if t_ms > 0 else 0.0,
+                           "peak_GBps": peak},
             "status": status,
             "clocks": ck,
         }

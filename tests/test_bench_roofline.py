@@ -54,3 +54,21 @@ def test_committed_records_resolve():
         assert os.path.exists(os.path.join(ROOT, rec["summary"])), rec["summary"]
         for src in rec.get("sources", bench.SOLVER_SOURCES):
             assert os.path.exists(os.path.join(ROOT, src)), src
+
+
+def test_step_model_bytes():
+    """The whole-step model: per cell, the stage sweeps (32 + 14 d + d^2) w_s, 11 w_s
+    per Helmholtz iteration, (d + 12) 8 + c (5 d + 18) w_s per MG-PCG iteration."""
+    import bench
+    its = {"p": 15, "T": 10, "w": 10}
+    c2 = {"geom": 0, "n": (1, 1, 1), "precision": 0}
+    b2 = bench.step_model_bytes(c2, dict(its, u=20))          # two velocity components
+    assert abs(b2 - (64 * 8 + 40 * 88 + 15 * (14 * 8 + 4.0 / 3.0 * 28 * 8))) < 1e-9
+    assert 10100 < b2 < 10300                                # ~10.2 kB per cell-step
+    c3 = {"geom": 1, "n": (1, 1, 1), "precision": 0}
+    b3 = bench.step_model_bytes(c3, dict(its, u=30))
+    assert 11300 < b3 < 11500                                # ~11.4 kB per cell-step
+    mixed = bench.step_model_bytes(dict(c3, precision=1), dict(its, u=30))
+    assert mixed < b3                                        # FP32 stencil words
+    big = bench.step_model_bytes(dict(c2, n=(256, 512, 1)), dict(its, u=20))
+    assert abs(big - b2 * 256 * 512) < 1e-3 * big            # per cell times the cells
