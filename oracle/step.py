@@ -18,7 +18,12 @@ The stage order is the paper's (Sec. 3.1, Fig. Scheme):
      correction
   S11 diagnostics
 Linear systems are assembled as sparse matrices and solved with a direct
-factorisation.  Discrete readings of points the paper leaves open are listed in
+factorisation.
+
+Parity unpinned: the interface-cell threshold on |grad(alpha)| and the adjacent
+gas-cell threshold ALPHA_GAS (the paper gives neither number), and the coupled
+Peng-Robinson 3D forced-convection dynamics as a whole; these rest on the
+comparison with the CUDA path alone.  Every other stage has a pin in the tests.  Discrete readings of points the paper leaves open are listed in
 the repository's design notes; the code states each where it is used.
 """
 import math
