@@ -228,7 +228,6 @@ class Solver {
   static constexpr int PERSIST_VECTORS = 13;
   void* pw[PERSIST_VECTORS] = {};   // persistent-solve vectors
   void* pwx[2][PERSIST_VECTORS] = {};   // those of the second and third system of a joint solve
-  double* r64x[2] = {nullptr, nullptr};
   unsigned* bar = nullptr;      // grid barrier counter and generation
   int* err = nullptr;           // set when a grid barrier wait ran out
   int pb_f32 = 0, pb_f64 = 0;   // co-resident blocks of the persistent solver

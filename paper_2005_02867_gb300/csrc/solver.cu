@@ -407,6 +407,9 @@ __global__ void k_mx_finish(long long N, double* x, const float* dx) {
 // were not all resident cannot hang.
 constexpr long long BARRIER_SPIN_LIMIT = 1LL << 22;
 constexpr int PTPB = 512;   // threads per block of the persistent solver
+// Boxes from this size on iterate in two passes per CG iteration (the working vectors,
+// 13 words a cell, no longer fit in the 129 MB L2)
+constexpr long long PERSIST_SPLIT_CELLS = 1LL << 21;
 
 
 
@@ -527,7 +530,6 @@ struct PersistArgs {
   BoxV A;                   // FP64 operator (difference form)
   const double* b;          // FP64 right-hand side
   double* x;                // FP64 initial guess in, solution out
-  double* r64;              // FP64 defect r0 = b - A x0 (scratch)
   T *ch[3];                 // c^ on the low face of each cell, per axis
   T *dg, *sc;               // diag(A) and S = diag^(-1/2)
   T *r[2], *s[2], *w[2];    // double-buffered r^, s = A^ p, w = A^ r^
@@ -547,6 +549,7 @@ template <typename T>
 struct PersistMulti {
   PersistArgs<T> s[PMAXSYS];
   int K;                    // systems
+  int split;                // iterate in two passes (large boxes; see the iteration loop)
   T* part;                  // 2 x 3K x blocks partial sums
   double* part64;           // FP64 partials of the initial norms (2 x 2K x blocks)
   double* stat;             // solver scalars (S_*) of the whole solve
@@ -581,7 +584,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
         double ax, d;
         box_row<double, double, true>(a.A.m, a.A.D, a.A.c, a.x, id, i, j, kk, ax, d);
         const double bP = a.b[id], r0 = bP - ax;
-        a.r64[id] = r0;
+        a.r[1][id] = (T)r0;                   // rounded once; r[1] is free until the first iteration
         const T dT = (T)d;
         a.dg[id] = dT;
         a.sc[id] = (T)1 / sqrt(dT);
@@ -630,8 +633,9 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
       const int N = (int)a.A.N, st1 = m0, st2 = m0 * m1;
       const bool has2 = a.A.c[2] != nullptr;
       const T nu = s_nu[k];
+      const T* r0T = a.r[1];                    // the defect r0 in precision T (phase 0)
       T g = 0, dl = 0, q = 0;
-#define RH(o) (nu * a.sc[o] * (T)a.r64[o])
+#define RH(o) (nu * a.sc[o] * r0T[o])
       for (int id = id0; id < N; id += gs) {
         int i, j, kk;
         bdecomp(a.A.m, id, i, j, kk);
@@ -696,53 +700,118 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
       if (!any) break;
 #pragma unroll
       for (int k = 0; k < 3 * PMAXSYS; ++k) v[k] = 0;
+      bool okA = true;
+      if (M.split) {
+        // Two passes with a plain grid barrier between them, for boxes far larger than
+        // L2: the first updates p, s, x^ and r^ in place, the second forms w = A^ r^ from
+        // the stored r^ of the neighbours.  Each pass streams with few loads per cell
+        // (the fused form gathers r^, s and w of six neighbours to rebuild their r^);
+        // the barrier costs microseconds against a pass of hundreds.  Same arithmetic.
 #pragma unroll
-      for (int k = 0; k < PMAXSYS; ++k) {
-        if (k >= K) break;
-        if (!s_act[k]) continue;
-        const PersistArgs<T>& a = M.s[k];
-        const int m0 = a.A.m[0], m1 = a.A.m[1], m2 = a.A.m[2];
-        const int N = (int)a.A.N, st1 = m0, st2 = m0 * m1;
-        const bool has2 = a.A.c[2] != nullptr;
-        const T al = s_alpha[k], bt = s_beta[k];
-        const T *r = a.r[cur], *s = a.s[cur], *w = a.w[cur];
-        T *rn = a.r[cur ^ 1], *sn = a.s[cur ^ 1], *wn = a.w[cur ^ 1];
-        T g = 0, dl = 0, q = 0;
-        for (int id = id0; id < N; id += gs) {
-          int i, j, kk;
-          bdecomp(a.A.m, id, i, j, kk);
-          const T rP = r[id];
-          const T pP = rP + bt * a.p[id];       // p = r^ + beta p
-          const T sP = w[id] + bt * s[id];      // s = w + beta s
-          a.p[id] = pP;
-          a.dx[id] += al * pP;                  // x^ += alpha p
-          const T rN = rP - al * sP;            // r^ -= alpha s
-          // neighbours: clamped indices and zero couplings at the box edges, so that all
-          // loads issue together; r^_new of a neighbour from its r^, s, w
-          const int iw = i > 0 ? id - 1 : id, ie = i < m0 - 1 ? id + 1 : id;
-          const int is = j > 0 ? id - st1 : id, in = j < m1 - 1 ? id + st1 : id;
-          const T cw = a.ch[0][id], ce = i < m0 - 1 ? a.ch[0][ie] : (T)0;
-          const T cs = a.ch[1][id], cn = j < m1 - 1 ? a.ch[1][in] : (T)0;
-#define UNB(o) (r[o] - al * (w[o] + bt * s[o]))
-          T y = rN - (cw * UNB(iw) + ce * UNB(ie) + cs * UNB(is) + cn * UNB(in));
-          if (has2) {
-            const int ib = kk > 0 ? id - st2 : id, it = kk < m2 - 1 ? id + st2 : id;
-            const T cb = a.ch[2][id], ct = kk < m2 - 1 ? a.ch[2][it] : (T)0;
-            y -= cb * UNB(ib) + ct * UNB(it);
+        for (int k = 0; k < PMAXSYS; ++k) {
+          if (k >= K) break;
+          if (!s_act[k]) continue;
+          const PersistArgs<T>& a = M.s[k];
+          const int N = (int)a.A.N;
+          const T al = s_alpha[k], bt = s_beta[k];
+          T *r = a.r[0], *s = a.s[0];
+          const T* w = a.w[0];
+          T g = 0, q = 0;
+          for (int id = id0; id < N; id += gs) {
+            const T rP = r[id];
+            const T pP = rP + bt * a.p[id];       // p = r^ + beta p
+            const T sP = w[id] + bt * s[id];      // s = w + beta s
+            a.p[id] = pP;
+            a.dx[id] += al * pP;                  // x^ += alpha p
+            const T rN = rP - al * sP;            // r^ -= alpha s
+            r[id] = rN;
+            s[id] = sP;
+            g += rN * rN;
+            q += a.dg[id] * rN * rN;
           }
-#undef UNB
-          rn[id] = rN;
-          sn[id] = sP;
-          wn[id] = y;
-          g += rN * rN;
-          dl += y * rN;
-          q += a.dg[id] * rN * rN;
+          v[3 * k] = g;
+          v[3 * k + 2] = q;
         }
-        v[3 * k] = g;
-        v[3 * k + 1] = dl;
-        v[3 * k + 2] = q;
+        okA = grid_sum<T, 3 * PMAXSYS>(v, 0, phase++, M.part, M.bar, M.err);
+#pragma unroll
+        for (int k = 0; k < PMAXSYS; ++k) {
+          if (k >= K) break;
+          if (!s_act[k]) continue;
+          const PersistArgs<T>& a = M.s[k];
+          const int m0 = a.A.m[0], m1 = a.A.m[1], m2 = a.A.m[2];
+          const int N = (int)a.A.N, st1 = m0, st2 = m0 * m1;
+          const bool has2 = a.A.c[2] != nullptr;
+          const T* r = a.r[0];
+          T* w = a.w[0];
+          T dl = 0;
+          for (int id = id0; id < N; id += gs) {
+            int i, j, kk;
+            bdecomp(a.A.m, id, i, j, kk);
+            const T rN = r[id];
+            const int iw = i > 0 ? id - 1 : id, ie = i < m0 - 1 ? id + 1 : id;
+            const int is = j > 0 ? id - st1 : id, in = j < m1 - 1 ? id + st1 : id;
+            const T cw = a.ch[0][id], ce = i < m0 - 1 ? a.ch[0][ie] : (T)0;
+            const T cs = a.ch[1][id], cn = j < m1 - 1 ? a.ch[1][in] : (T)0;
+            T y = rN - (cw * r[iw] + ce * r[ie] + cs * r[is] + cn * r[in]);
+            if (has2) {
+              const int ib = kk > 0 ? id - st2 : id, it = kk < m2 - 1 ? id + st2 : id;
+              const T cb = a.ch[2][id], ct = kk < m2 - 1 ? a.ch[2][it] : (T)0;
+              y -= cb * r[ib] + ct * r[it];
+            }
+            w[id] = y;
+            dl += y * rN;
+          }
+          v[3 * k + 1] = dl;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < PMAXSYS; ++k) {
+          if (k >= K) break;
+          if (!s_act[k]) continue;
+          const PersistArgs<T>& a = M.s[k];
+          const int m0 = a.A.m[0], m1 = a.A.m[1], m2 = a.A.m[2];
+          const int N = (int)a.A.N, st1 = m0, st2 = m0 * m1;
+          const bool has2 = a.A.c[2] != nullptr;
+          const T al = s_alpha[k], bt = s_beta[k];
+          const T *r = a.r[cur], *s = a.s[cur], *w = a.w[cur];
+          T *rn = a.r[cur ^ 1], *sn = a.s[cur ^ 1], *wn = a.w[cur ^ 1];
+          T g = 0, dl = 0, q = 0;
+          for (int id = id0; id < N; id += gs) {
+            int i, j, kk;
+            bdecomp(a.A.m, id, i, j, kk);
+            const T rP = r[id];
+            const T pP = rP + bt * a.p[id];       // p = r^ + beta p
+            const T sP = w[id] + bt * s[id];      // s = w + beta s
+            a.p[id] = pP;
+            a.dx[id] += al * pP;                  // x^ += alpha p
+            const T rN = rP - al * sP;            // r^ -= alpha s
+            // neighbours: clamped indices and zero couplings at the box edges, so that all
+            // loads issue together; r^_new of a neighbour from its r^, s, w
+            const int iw = i > 0 ? id - 1 : id, ie = i < m0 - 1 ? id + 1 : id;
+            const int is = j > 0 ? id - st1 : id, in = j < m1 - 1 ? id + st1 : id;
+            const T cw = a.ch[0][id], ce = i < m0 - 1 ? a.ch[0][ie] : (T)0;
+            const T cs = a.ch[1][id], cn = j < m1 - 1 ? a.ch[1][in] : (T)0;
+#define UNB(o) (r[o] - al * (w[o] + bt * s[o]))
+            T y = rN - (cw * UNB(iw) + ce * UNB(ie) + cs * UNB(is) + cn * UNB(in));
+            if (has2) {
+              const int ib = kk > 0 ? id - st2 : id, it = kk < m2 - 1 ? id + st2 : id;
+              const T cb = a.ch[2][id], ct = kk < m2 - 1 ? a.ch[2][it] : (T)0;
+              y -= cb * UNB(ib) + ct * UNB(it);
+            }
+#undef UNB
+            rn[id] = rN;
+            sn[id] = sP;
+            wn[id] = y;
+            g += rN * rN;
+            dl += y * rN;
+            q += a.dg[id] * rN * rN;
+          }
+          v[3 * k] = g;
+          v[3 * k + 1] = dl;
+          v[3 * k + 2] = q;
+        }
       }
-      ok = grid_sum<T, 3 * PMAXSYS>(v, 3 * K, phase++, M.part, M.bar, M.err);
+      ok = grid_sum<T, 3 * PMAXSYS>(v, 3 * K, phase++, M.part, M.bar, M.err) && okA;
       if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < PMAXSYS; ++k) {
@@ -1896,11 +1965,9 @@ int Solver::setup(long long maxN, cudaStream_t s) {
   }
   if (persistent) CK(cudaMalloc(&mg_q2, sizeof(double) * (size_t)maxN));
   if (persist_pcg)
-    for (int k = 0; k < nsys_extra; ++k) {
-      CK(cudaMalloc(&r64x[k], sizeof(double) * (size_t)maxN));
+    for (int k = 0; k < nsys_extra; ++k)
       for (int q = 0; q < PERSIST_VECTORS; ++q)
         CK(cudaMalloc(&pwx[k][q], (f32_helm ? sizeof(float) : sizeof(double)) * (size_t)maxN));
-    }
   if (persist_pcg)
     for (int q = 0; q < PERSIST_VECTORS; ++q) CK(cudaMalloc(&pw[q], (f32_helm ? sizeof(float) : sizeof(double)) * (size_t)maxN));
   return 0;
@@ -1913,11 +1980,8 @@ void Solver::release() {
     float** fa[] = {&fD, &fc[0], &fc[1], &fc[2], &fidg, &fr, &fz, &fp, &fAp, &fdx};
     for (auto q : fa) { cudaFree(*q); *q = nullptr; }
     for (int q = 0; q < PERSIST_VECTORS; ++q) { cudaFree(pw[q]); pw[q] = nullptr; }
-    for (int k = 0; k < 2; ++k) {
-      cudaFree(r64x[k]);
-      r64x[k] = nullptr;
+    for (int k = 0; k < 2; ++k)
       for (int q = 0; q < PERSIST_VECTORS; ++q) { cudaFree(pwx[k][q]); pwx[k][q] = nullptr; }
-    }
     cudaFree(bar); cudaFree(err); cudaFree(mg_q2);
     mg_q2 = nullptr;
     bar = nullptr; err = nullptr;
@@ -2022,7 +2086,6 @@ int Solver::pcg_persist(const BoxSys* sys, int K, double rtol, int maxit, const 
     a.A = view(s);
     a.b = s.b;
     a.x = s.x;
-    a.r64 = k == 0 ? r : r64x[k - 1];
     a.tol2 = rtol * rtol;
     a.maxit = maxit;
     a.rec = recs[k];
@@ -2048,6 +2111,7 @@ int Solver::pcg_persist(const BoxSys* sys, int K, double rtol, int maxit, const 
   M.done = done;
   M.bar = bar;
   M.err = err;
+  M.split = nmax >= PERSIST_SPLIT_CELLS;
   int grid = (int)((nmax + PTPB - 1) / PTPB);
   int cap = persist_blocks(f32);
   const int bud = pcg_budget > 0 ? pcg_budget : sm_budget;
