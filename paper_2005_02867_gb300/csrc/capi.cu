@@ -25,6 +25,7 @@ struct dctx {
   double *alpha = nullptr, *T = nullptr, *omega = nullptr, *pr = nullptr, *rhoG = nullptr, *u[3] = {nullptr, nullptr, nullptr};
   // step work arrays
   double *rhoG_old = nullptr, *mdot = nullptr, *mraw = nullptr, *astar = nullptr, *aL = nullptr, *Rp = nullptr, *Rm = nullptr;
+  float* astar_f = nullptr;          // alpha* in binary32 for the face stencils (mixed precision)
   double *FL[3] = {nullptr, nullptr, nullptr}, *AF[3] = {nullptr, nullptr, nullptr}, *us[3] = {nullptr, nullptr, nullptr};
   double *xi = nullptr;
   // history of the Helmholtz unknowns (previous step's T, omega, face velocities) for the
@@ -142,7 +143,7 @@ static void make_phys(const droplet_config& c, Phys& p) {
     p.pr_ac[s] = 0.45724 * R_GAS * R_GAS * Tc[s] * Tc[s] / Pc[s];
     p.pr_b[s] = 0.07780 * R_GAS * Tc[s] / Pc[s];
     p.pr_k[s] = 0.37464 + 1.54226 * om[s] - 0.26992 * om[s] * om[s];
-    p.pr_iTc[s] = 1.0 / Tc[s];
+    p.pr_siTc[s] = sqrt(1.0 / Tc[s]);
   }
   p.pr_sqac01 = std::sqrt(p.pr_ac[0] * p.pr_ac[1]) * (1.0 - c.kij);
   p.iM_l = 1.0 / c.M_l;
@@ -168,8 +169,8 @@ static void free_all(dctx* c) {
   }
   for (auto& set : c->xb)
     for (auto& q : set) { cudaFree(q); q = nullptr; }
-  cudaFree(c->adj); cudaFree(c->flags); cudaFree(c->dirty);
-  c->adj = nullptr; c->flags = nullptr; c->dirty = nullptr;
+  cudaFree(c->adj); cudaFree(c->flags); cudaFree(c->dirty); cudaFree(c->astar_f);
+  c->adj = nullptr; c->flags = nullptr; c->dirty = nullptr; c->astar_f = nullptr;
   cudaFreeHost(c->hscal); cudaFreeHost(c->hflags);
   c->hscal = nullptr; c->hflags = nullptr;
   c->solver.release();
@@ -221,6 +222,11 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
                       &c->bD, &c->brhs, &c->bx, &c->xi, &c->hT, &c->hW};
   for (auto q : cells)
     if ((rc = dalloc(q, N))) { free_all(c); delete c; return rc; }
+  if (c->cfg.precision == 1 && cudaMalloc((void**)&c->astar_f, sizeof(float) * (size_t)N) != cudaSuccess) {
+    free_all(c);
+    delete c;
+    return DROPLET_ERR_NOMEM;
+  }
 
   for (int a = 0; a < 3; ++a) {
     if ((rc = dalloc(&c->bc[a], N))) { free_all(c); delete c; return rc; }
@@ -340,13 +346,13 @@ static int one_step(dctx* c, int* nc_flag) {
     cudaMemsetAsync(c->mraw, 0, sizeof(double) * N, st);
     cudaMemsetAsync(c->scal + SC_K, 0, sizeof(double), st);
   }
-  ++g_launches, k_alpha_source<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->mraw, c->scal, c->mdot, c->astar, c->flags,
+  ++g_launches, k_alpha_source<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->mraw, c->scal, c->mdot, c->astar, c->astar_f, c->flags,
                                                    c->dirty);
   // S3, and S4 (the mixture properties) in the kernel that forms alpha^{n+1}
   const PropsOut po{c->rhoG_old, c->omega, c->rho, c->mu, c->kc, c->cp, c->Dm};
   if (mask & DROPLET_PHYS_FLOW) {
     if (c->cfg.precision == 1) {
-      L_adv_faces_mx_all(st, g, p, c->astar, c->u, c->FL, c->AF);
+      L_adv_faces_mx_all(st, g, p, c->astar, c->astar_f, c->u, c->FL, c->AF);
     } else {
       for (int a = 0; a < na; ++a)
         L_adv_faces(st, lin_grid(nfaces(g, a)), g, p, a, c->astar, c->u[a], c->FL[a], c->AF[a]);

@@ -50,7 +50,7 @@ struct Phys {
   // Peng-Robinson constants of the fuel (0) and the inert gas (1), formed on the host:
   // a_c = 0.45724 R^2 Tc^2 / Pc, b = 0.07780 R Tc / Pc, kappa(omega), 1 / Tc, and
   // sqrt(a_c0 a_c1) (1 - k_ij); inverse molar masses
-  double pr_ac[2], pr_b[2], pr_k[2], pr_iTc[2], pr_sqac01;
+  double pr_ac[2], pr_b[2], pr_k[2], pr_siTc[2], pr_sqac01;   // pr_siTc = sqrt(1 / Tc)
   double iM_l, iM_g;
   // Clausius-Clapeyron exponent L M_l / R and 1 / T_b; 1 / rho_l
   double cc_LMR, iTb, irho_l;
@@ -268,15 +268,17 @@ __device__ __forceinline__ double y_from_Y(const Phys& p, double Y) {
 }
 
 // Peng-Robinson pure-component alpha factor sqrt(alpha(T)) = 1 + kappa (1 - sqrt(T / Tc))
-// of component s; a(T) = a_c sq^2 (the constants come from the host, Phys::pr_*)
-__device__ __forceinline__ double pr_sq(const Phys& p, int s, double T) {
-  return 1.0 + p.pr_k[s] * (1.0 - sqrt(T * p.pr_iTc[s]));
+// of component s, from sqrt(T) (shared by both components) and sqrt(1 / Tc); a(T) = a_c sq^2
+// (the constants come from the host, Phys::pr_*)
+__device__ __forceinline__ double pr_sq(const Phys& p, int s, double sqrtT) {
+  return 1.0 + p.pr_k[s] * (1.0 - sqrtT * p.pr_siTc[s]);
 }
 
 // van der Waals mixing of the binary at fuel mole fraction y; A, B of the cubic
 __device__ __forceinline__ void pr_mix_AB(const Phys& p, double T, double P, double y, double& A, double& B,
                                           double& a0, double& a01, double& am, double& bm) {
-  const double s0 = pr_sq(p, 0, T), s1 = pr_sq(p, 1, T);
+  const double sT = sqrt(T);
+  const double s0 = pr_sq(p, 0, sT), s1 = pr_sq(p, 1, sT);
   a0 = p.pr_ac[0] * s0 * s0;
   const double a1 = p.pr_ac[1] * s1 * s1;
   a01 = p.pr_sqac01 * fabs(s0 * s1);          // sqrt(a0 a1) (1 - k_ij)

@@ -57,7 +57,7 @@ __global__ void k_thermo_pin(Geo g, Phys p, const double* alpha, const double* T
 
 __global__ void k_evap_K(const double* partials, int nblk, double* scal, unsigned* flags);
 __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double* mraw, const double* scal,
-                               double* mdot, double* alpha_star, unsigned* flags, int* dirty);
+                               double* mdot, double* alpha_star, float* alpha_star_f, unsigned* flags, int* dirty);
 
 __global__ void k_adv_low(Geo g, const double* as, const double* F0, const double* F1, const double* F2, double* aL);
 
@@ -88,8 +88,8 @@ void L_adv_limit(cudaStream_t st, int grid, Geo g, const double* as, const doubl
 void L_adv_update(cudaStream_t st, int grid, Geo g, Phys p, const double* aL, const double* A0, const double* A1, const double* A2, const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags, PropsOut po);
 void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs);
 // the alpha face fluxes of every direction in one launch (mixed precision)
-void L_adv_faces_mx_all(cudaStream_t st, Geo g, Phys p, const double* as, double* const u[3], double* const FL[3],
-                        double* const AF[3]);
+void L_adv_faces_mx_all(cudaStream_t st, Geo g, Phys p, const double* as, const float* asf, double* const u[3],
+                        double* const FL[3], double* const AF[3]);
 void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs);
 void L_mom_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs);
 void L_mom_assemble(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs);

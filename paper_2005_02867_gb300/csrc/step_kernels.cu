@@ -250,18 +250,28 @@ __global__ void k_evap_K(const double* partials, int nblk, double* scal, unsigne
 
 // ============================================================== S2 alpha source
 // (also clears the state-overwritten flag that S0 consumed)
+// (alpha_star_f, when given: alpha* rounded to binary32 for the mixed-precision face
+// stencils.)  Cells without a raw flux (all but the interface band) keep alpha* = alpha
+// and m = 0 without the binary64 square root, cap and update, whose results there are
+// exactly those values.
 __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double* mraw, const double* scal,
-                               double* mdot, double* alpha_star, unsigned* flags, int* dirty) {
+                               double* mdot, double* alpha_star, float* alpha_star_f, unsigned* flags, int* dirty) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
   if (id == 0) *dirty = 0;
-  double a = alpha[id];
-  double K = scal[SC_K];
-  double m = (K == 0.0) ? 0.0 : K * sqrt(a * (1.0 - a)) * mraw[id];
-  double cap = p.rho_l * a * p.idt;
-  if (m > cap) { m = cap; atomicOr(flags, (unsigned)DROPLET_FLAG_MDOT_CAPPED); }
+  const double a = alpha[id];
+  const double mr = mraw[id];
+  double m = 0.0, as = a;
+  if ((__double_as_longlong(mr) << 1) != 0) {      // mraw != 0, tested on the integer pipe
+    const double K = scal[SC_K];
+    m = (K == 0.0) ? 0.0 : K * sqrt(a * (1.0 - a)) * mr;
+    const double cap = p.rho_l * a * p.idt;
+    if (m > cap) { m = cap; atomicOr(flags, (unsigned)DROPLET_FLAG_MDOT_CAPPED); }
+    as = a - p.dt * m * p.irho_l;
+  }
   mdot[id] = m;
-  alpha_star[id] = a - p.dt * m * p.irho_l;
+  alpha_star[id] = as;
+  if (alpha_star_f) alpha_star_f[id] = f32_rn(as);
 }
 
 // ============================================================== S3 alpha advection (FCT)

@@ -366,16 +366,27 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
   rhs[id] = r;
 }
 
+// alpha of a cell or ghost from its binary32 copy, with the ghost rule of alpha (the
+// axis mirrors, every other boundary has alpha = 0 outside): cellg_f(..., R_ALPHA, ...)
+// of the binary64 field, without a rounding per reference
+__device__ __forceinline__ float alpha_gf(const Geo& g, const float* f, int i, int j, int k) {
+  int a, side;
+  if (i < 0) { a = 0; side = 0; i = 0; }
+  else if (i >= g.n[0]) { a = 0; side = 1; i = g.n[0] - 1; }
+  else if (j < 0) { a = 1; side = 0; j = 0; }
+  else if (j >= g.n[1]) { a = 1; side = 1; j = g.n[1] - 1; }
+  else if (k < 0) { a = 2; side = 0; k = 0; }
+  else if (k >= g.n[2]) { a = 2; side = 1; k = g.n[2] - 1; }
+  else return f[cidx(g, i, j, k)];
+  return bc_of(g, a, side) == BC_AXIS ? f[cidx(g, i, j, k)] : 0.f;
+}
+
 // alpha gradient of a cell (central differences, the ghost rule of alpha), FP32
-__device__ __forceinline__ void grad_alpha_f(const Geo& g, const GeoF& q, const double* al, int i, int j, int k,
+__device__ __forceinline__ void grad_alpha_f(const Geo& g, const GeoF& q, const float* al, int i, int j, int k,
                                              float gr[3]) {
-  gr[0] = (cellg_f(g, al, i + 1, j, k, R_ALPHA, 0.f, 0, 0, 0) - cellg_f(g, al, i - 1, j, k, R_ALPHA, 0.f, 0, 0, 0)) *
-          (0.5f * q.ih[0]);
-  gr[1] = (cellg_f(g, al, i, j + 1, k, R_ALPHA, 0.f, 0, 0, 0) - cellg_f(g, al, i, j - 1, k, R_ALPHA, 0.f, 0, 0, 0)) *
-          (0.5f * q.ih[1]);
-  gr[2] = g.act3 ? (cellg_f(g, al, i, j, k + 1, R_ALPHA, 0.f, 0, 0, 0) -
-                    cellg_f(g, al, i, j, k - 1, R_ALPHA, 0.f, 0, 0, 0)) * (0.5f * q.ih[2])
-                 : 0.f;
+  gr[0] = (alpha_gf(g, al, i + 1, j, k) - alpha_gf(g, al, i - 1, j, k)) * (0.5f * q.ih[0]);
+  gr[1] = (alpha_gf(g, al, i, j + 1, k) - alpha_gf(g, al, i, j - 1, k)) * (0.5f * q.ih[1]);
+  gr[2] = g.act3 ? (alpha_gf(g, al, i, j, k + 1) - alpha_gf(g, al, i, j, k - 1)) * (0.5f * q.ih[2]) : 0.f;
 }
 
 // Face fluxes of the alpha advection (Sec. 2.1 with the compressive flux), mixed
@@ -384,10 +395,11 @@ __device__ __forceinline__ void grad_alpha_f(const Geo& g, const GeoF& q, const 
 // phi (van Leer increment) + C_alpha |phi| (n_f . e) a_c (1 - a_c) in FP32 -- equal to
 // the difference in exact arithmetic, without its cancellation.  Fluxes are applied
 // antisymmetrically, so the volume stays conserved whatever their precision, and the
-// limiter bounds the result as in k_adv_faces.
+// limiter bounds the result as in k_adv_faces.  The FP32 stencil reads alpha* from its
+// binary32 copy asf.
 template <int DIR, int NA>
-__device__ __forceinline__ void adv_face_mx(const Geo& g, const Phys& p, const double* as, const double* ua,
-                                            double* FL, double* AF, long long id) {
+__device__ __forceinline__ void adv_face_mx(const Geo& g, const Phys& p, const double* as, const float* asf,
+                                            const double* ua, double* FL, double* AF, long long id) {
   constexpr int a = DIR;
   int m0 = g.n[0] + (a == 0), m1 = g.n[1] + (a == 1);
   int f[3];
@@ -405,15 +417,15 @@ __device__ __forceinline__ void adv_face_mx(const Geo& g, const Phys& p, const d
     int LL[3] = {L[0], L[1], L[2]}, RR[3] = {R[0], R[1], R[2]};
     LL[a] -= 1;
     RR[a] += 1;
-    const float aLf = f32_rn(aL), aRf = f32_rn(aR);
-    const float aLL = cellg_f(g, as, LL[0], LL[1], LL[2], R_ALPHA, 0.f, 0, 0, 0);
-    const float aRR = cellg_f(g, as, RR[0], RR[1], RR[2], R_ALPHA, 0.f, 0, 0, 0);
+    const float aLf = alpha_gf(g, asf, L[0], L[1], L[2]), aRf = alpha_gf(g, asf, R[0], R[1], R[2]);
+    const float aLL = alpha_gf(g, asf, LL[0], LL[1], LL[2]);
+    const float aRR = alpha_gf(g, asf, RR[0], RR[1], RR[2]);
     // van Leer increment over the upwind value
     const float dU = pos ? aLf - aLL : aRf - aRR, dD = pos ? aRf - aLf : aLf - aRf, pr = dU * dD;
     const float inc = pr > 0.f ? pr / (dU + dD) : 0.f;
     float gL[3], gR[3];
-    grad_alpha_f(g, q, as, L[0], L[1], L[2], gL);
-    grad_alpha_f(g, q, as, R[0], R[1], R[2], gR);
+    grad_alpha_f(g, q, asf, L[0], L[1], L[2], gL);
+    grad_alpha_f(g, q, asf, R[0], R[1], R[2], gR);
     const float gf[3] = {gL[0] + gR[0], gL[1] + gR[1], gL[2] + gR[2]};
     const float gfm = sqrtf(gf[0] * gf[0] + gf[1] * gf[1] + (g.act3 ? gf[2] * gf[2] : 0.f));
     const float ne = gfm > f32_rn(g.gthr) ? gf[a] / gfm : 0.f;
@@ -431,22 +443,22 @@ struct AdvFacesArgs {
   int b[4];
 };
 template <int NA>
-__global__ void k_adv_faces_mx(Geo g, Phys p, const double* as, AdvFacesArgs f) {
+__global__ void k_adv_faces_mx(Geo g, Phys p, const double* as, const float* asf, AdvFacesArgs f) {
   const int bx = blockIdx.x;
   if (bx < f.b[1]) {
     const long long id = (long long)(bx - f.b[0]) * blockDim.x + threadIdx.x;
-    if (id < nfaces(g, 0)) adv_face_mx<0, NA>(g, p, as, f.ua[0], f.FL[0], f.AF[0], id);
+    if (id < nfaces(g, 0)) adv_face_mx<0, NA>(g, p, as, asf, f.ua[0], f.FL[0], f.AF[0], id);
   } else if (bx < f.b[2]) {
     const long long id = (long long)(bx - f.b[1]) * blockDim.x + threadIdx.x;
-    if (id < nfaces(g, 1)) adv_face_mx<1, NA>(g, p, as, f.ua[1], f.FL[1], f.AF[1], id);
+    if (id < nfaces(g, 1)) adv_face_mx<1, NA>(g, p, as, asf, f.ua[1], f.FL[1], f.AF[1], id);
   } else if (NA == 3) {
     const long long id = (long long)(bx - f.b[2]) * blockDim.x + threadIdx.x;
-    if (id < nfaces(g, 2)) adv_face_mx<2, NA>(g, p, as, f.ua[2], f.FL[2], f.AF[2], id);
+    if (id < nfaces(g, 2)) adv_face_mx<2, NA>(g, p, as, asf, f.ua[2], f.FL[2], f.AF[2], id);
   }
 }
 
-void L_adv_faces_mx_all(cudaStream_t st, Geo g, Phys p, const double* as, double* const u[3], double* const FL[3],
-                        double* const AF[3]) {
+void L_adv_faces_mx_all(cudaStream_t st, Geo g, Phys p, const double* as, const float* asf, double* const u[3],
+                        double* const FL[3], double* const AF[3]) {
   AdvFacesArgs f;
   const int na = nact(g);
   int b = 0;
@@ -459,8 +471,8 @@ void L_adv_faces_mx_all(cudaStream_t st, Geo g, Phys p, const double* as, double
   }
   f.b[3] = b;
   ++g_launches;
-  if (na == 3) k_adv_faces_mx<3><<<b, TPB, 0, st>>>(g, p, as, f);
-  else k_adv_faces_mx<2><<<b, TPB, 0, st>>>(g, p, as, f);
+  if (na == 3) k_adv_faces_mx<3><<<b, TPB, 0, st>>>(g, p, as, asf, f);
+  else k_adv_faces_mx<2><<<b, TPB, 0, st>>>(g, p, as, asf, f);
 }
 
 void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi,
