@@ -26,6 +26,7 @@ struct dctx {
   // step work arrays
   double *rhoG_old = nullptr, *mdot = nullptr, *mraw = nullptr, *astar = nullptr, *aL = nullptr, *Rp = nullptr, *Rm = nullptr;
   float* astar_f = nullptr;          // alpha* in binary32 for the face stencils (mixed precision)
+  Shadow32 s32{};                    // binary32 copies for the assembly stencils (mixed precision)
   double *FL[3] = {nullptr, nullptr, nullptr}, *AF[3] = {nullptr, nullptr, nullptr}, *us[3] = {nullptr, nullptr, nullptr};
   double *xi = nullptr;
   // history of the Helmholtz unknowns (previous step's T, omega, face velocities) for the
@@ -171,6 +172,10 @@ static void free_all(dctx* c) {
     for (auto& q : set) { cudaFree(q); q = nullptr; }
   cudaFree(c->adj); cudaFree(c->flags); cudaFree(c->dirty); cudaFree(c->astar_f);
   c->adj = nullptr; c->flags = nullptr; c->dirty = nullptr; c->astar_f = nullptr;
+  {
+    float** sh[] = {&c->s32.T, &c->s32.w, &c->s32.k, &c->s32.gD, &c->s32.mu, &c->s32.u[0], &c->s32.u[1], &c->s32.u[2]};
+    for (auto q : sh) { cudaFree(*q); *q = nullptr; }
+  }
   cudaFreeHost(c->hscal); cudaFreeHost(c->hflags);
   c->hscal = nullptr; c->hflags = nullptr;
   c->solver.release();
@@ -222,10 +227,13 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
                       &c->bD, &c->brhs, &c->bx, &c->xi, &c->hT, &c->hW};
   for (auto q : cells)
     if ((rc = dalloc(q, N))) { free_all(c); delete c; return rc; }
-  if (c->cfg.precision == 1 && cudaMalloc((void**)&c->astar_f, sizeof(float) * (size_t)N) != cudaSuccess) {
-    free_all(c);
-    delete c;
-    return DROPLET_ERR_NOMEM;
+  if (c->cfg.precision == 1) {
+    bool ok = cudaMalloc((void**)&c->astar_f, sizeof(float) * (size_t)N) == cudaSuccess;
+    float** sh[] = {&c->s32.T, &c->s32.w, &c->s32.k, &c->s32.gD, &c->s32.mu};
+    for (auto q : sh) ok = ok && cudaMalloc((void**)q, sizeof(float) * (size_t)N) == cudaSuccess;
+    for (int a = 0; a < na; ++a)
+      ok = ok && cudaMalloc((void**)&c->s32.u[a], sizeof(float) * (size_t)nfaces(g, a)) == cudaSuccess;
+    if (!ok) { free_all(c); delete c; return DROPLET_ERR_NOMEM; }
   }
 
   for (int a = 0; a < 3; ++a) {
@@ -338,6 +346,11 @@ static int one_step(dctx* c, int* nc_flag) {
   // S0 (with the reset of the step's solver statistics)
   ++g_launches, k_thermo_pin<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->T, c->omega, c->rhoG, c->rhoG_old, c->flags, c->dirty,
                                                  c->scal);
+  if (c->s32.u[0]) {   // mixed precision: u^n in binary32 for the assembly stencils of this step
+    const long long n0 = nfaces(g, 0), n1 = nfaces(g, 1), n2 = na == 3 ? nfaces(g, 2) : 0;
+    ++g_launches, k_faces_f32<<<lin_grid(n0 + n1 + n2), TPB, 0, st>>>(c->u[0], c->u[1], na == 3 ? c->u[2] : c->u[0],
+                                                                     c->s32.u[0], c->s32.u[1], c->s32.u[2], n0, n1, n2);
+  }
   // S1, S2
   if (mask & DROPLET_PHYS_EVAP) {
     L_evap_raw(st, nb, g, p, c->alpha, c->omega, c->rhoG_old, c->u[0], c->u[1], u2, c->mraw, c->adj, c->part, c->flags);
@@ -349,7 +362,7 @@ static int one_step(dctx* c, int* nc_flag) {
   ++g_launches, k_alpha_source<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->mraw, c->scal, c->mdot, c->astar, c->astar_f, c->flags,
                                                    c->dirty);
   // S3, and S4 (the mixture properties) in the kernel that forms alpha^{n+1}
-  const PropsOut po{c->rhoG_old, c->omega, c->rho, c->mu, c->kc, c->cp, c->Dm};
+  const PropsOut po{c->rhoG_old, c->omega, c->T, c->rho, c->mu, c->kc, c->cp, c->Dm, c->s32};
   if (mask & DROPLET_PHYS_FLOW) {
     if (c->cfg.precision == 1) {
       L_adv_faces_mx_all(st, g, p, c->astar, c->astar_f, c->u, c->FL, c->AF);
@@ -399,7 +412,7 @@ static int one_step(dctx* c, int* nc_flag) {
         ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, ms, (12.0 + 2 * na) * nbx * 8.0);
         (c->cfg.precision == 1 ? L_mom_assemble_mx : L_mom_assemble)(
             ms, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi, b.D, b.c[0],
-            b.c[1], na == 3 ? b.c[2] : b.c[0], (double*)b.b);
+            b.c[1], na == 3 ? b.c[2] : b.c[0], (double*)b.b, &c->s32);
         }
         L_faces_to_box(ms, lin_grid(nbx), g, cc, c->u[cc], b.x, c->hu[cc], c->scal);
         recs[cc] = RecordSpec{c->scal, SC_ITS_U, -1, cc > 0};
@@ -422,7 +435,7 @@ static int one_step(dctx* c, int* nc_flag) {
       ProfScope ps(&c->prof, KC_MOM_ASSEMBLE, ms, (12.0 + 2 * na) * nbx * 8.0);
       (c->cfg.precision == 1 ? L_mom_assemble_mx : L_mom_assemble)(
           ms, lin_grid(nbx), g, p, cc, c->u[0], c->u[1], u2, c->rho, c->mu, c->pr, c->alpha, c->xi, c->bD, c->bc[0],
-          c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+          c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs, &c->s32);
       }
       for (int a = 0; a < 3; ++a) bm.m[a] = m[a];
       bm.N = nbx;
@@ -449,7 +462,7 @@ static int one_step(dctx* c, int* nc_flag) {
     ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
     (c->cfg.precision == 1 ? L_scalar_assemble_mx : L_scalar_assemble)(
         st, gc, g, p, 0, c->T, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2, c->alpha, c->yq, p.T_amb,
-        c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+        c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs, &c->s32);
     }
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
@@ -468,7 +481,7 @@ static int one_step(dctx* c, int* nc_flag) {
     ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
     (c->cfg.precision == 1 ? L_scalar_assemble_mx : L_scalar_assemble)(
         st, gc, g, p, 1, c->omega, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2, c->alpha, c->yq, 0.0,
-        c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs);
+        c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs, &c->s32);
     }
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
@@ -1018,7 +1031,8 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
         L_adj_pin(st, g, p, sA, sT, sW, wp);
         // species: adjoint solve on the free rows, pinned rows and coefficients
         L_scalar_assemble(st, lin_grid(N), g, p, 1, wp, x->rho, x->cp, x->kc, x->Dm, x->mdot, x->u[0], x->u[1], u2,
-                          x->alpha, x->yq, 0.0, x->bD, x->bc[0], x->bc[1], na == 3 ? x->bc[2] : x->bc[0], x->brhs);
+                          x->alpha, x->yq, 0.0, x->bD, x->bc[0], x->bc[1], na == 3 ? x->bc[2] : x->bc[0], x->brhs,
+                          nullptr);
         L_adj_rhs(st, g, aW, x->alpha, 1, x->brhs, x->bx);
         rc = x->solver.pcg_jacobi(bs, 1e-14, 4 * cf.helm_maxit, &ss);
         if (rc == DROPLET_ERR_NOT_CONVERGED) { nc = 1; rc = 0; }
@@ -1026,7 +1040,8 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
         L_adj_species(st, g, p, x->bx, aW, aT, x->alpha, wp, x->omega, x->T, x->rho, x->Dm, Tn1bar, wpbar, rhobar, Dbar);
         // energy
         L_scalar_assemble(st, lin_grid(N), g, p, 0, sT, x->rho, x->cp, x->kc, x->Dm, x->mdot, x->u[0], x->u[1], u2,
-                          x->alpha, x->yq, p.T_amb, x->bD, x->bc[0], x->bc[1], na == 3 ? x->bc[2] : x->bc[0], x->brhs);
+                          x->alpha, x->yq, p.T_amb, x->bD, x->bc[0], x->bc[1], na == 3 ? x->bc[2] : x->bc[0], x->brhs,
+                          nullptr);
         L_adj_rhs(st, g, Tn1bar, x->alpha, 0, x->brhs, x->bx);
         rc = x->solver.pcg_jacobi(bs, 1e-14, 4 * cf.helm_maxit, &ss);
         if (rc == DROPLET_ERR_NOT_CONVERGED) { nc = 1; rc = 0; }

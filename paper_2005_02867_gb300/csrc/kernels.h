@@ -62,11 +62,25 @@ __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double*
 __global__ void k_adv_low(Geo g, const double* as, const double* F0, const double* F1, const double* F2, double* aL);
 
 __global__ void k_clip_finish(const double* partials, int nblk, double* scal, unsigned* flags);
+// Binary32 copies of the stencil inputs of the mixed-precision assembly kernels (null
+// pointers in FP64 runs): each element is f32_rn of its binary64 source, formed once
+// where that value is formed (the S4 properties, with the step's old T and omega) or at
+// the start of the step (the face velocities u^n), instead of once per stencil reference.
+struct Shadow32 {
+  float *T, *w;             // temperature and vapour mass fraction entering S5 / S6
+  float *k, *gD;            // conductivity and rho D of the cell
+  float *mu;                // viscosity
+  float *u[3];              // face velocities
+};
 // mixture properties of a cell (S4), formed where alpha^{n+1} is (the FCT update, the clip)
 struct PropsOut {
-  const double *rhoG, *omega;
+  const double *rhoG, *omega, *T;
   double *rho, *mu, *kc, *cp, *D;
+  Shadow32 s;               // binary32 copies to write (s.T null: none)
 };
+// u^n rounded to binary32 (faces of every active direction in one launch)
+__global__ void k_faces_f32(const double* u0, const double* u1, const double* u2, float* f0, float* f1, float* f2,
+                            long long n0, long long n1, long long n2);
 __global__ void k_alpha_clip_only(Geo g, Phys p, const double* as, double* alpha, double* partials, PropsOut po);
 __global__ void k_props(Geo g, Phys p, const double* alpha, const double* rhoG, const double* omega, double* rho,
                         double* mu, double* kc, double* cp, double* D);
@@ -86,13 +100,13 @@ void L_evap_raw(cudaStream_t st, int grid, Geo g, Phys p, const double* alpha, c
 void L_adv_faces(cudaStream_t st, int grid, Geo g, Phys p, int a, const double* as, const double* ua, double* FL, double* AF);
 void L_adv_limit(cudaStream_t st, int grid, Geo g, const double* as, const double* aL, const double* A0, const double* A1, const double* A2, double* Rp, double* Rm);
 void L_adv_update(cudaStream_t st, int grid, Geo g, Phys p, const double* aL, const double* A0, const double* A1, const double* A2, const double* Rp, const double* Rm, double* alpha, double* partials, unsigned* flags, PropsOut po);
-void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs);
+void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32* s32);
 // the alpha face fluxes of every direction in one launch (mixed precision)
 void L_adv_faces_mx_all(cudaStream_t st, Geo g, Phys p, const double* as, const float* asf, double* const u[3],
                         double* const FL[3], double* const AF[3]);
-void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs);
-void L_mom_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs);
-void L_mom_assemble(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs);
+void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32* s32);
+void L_mom_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32* s32);
+void L_mom_assemble(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32* s32);
 void L_mom_scatter(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* x, double* us);
 void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo, const double* rgn, const double* u0, const double* u1, const double* u2, const double* us0, const double* us1, const double* us2, const double* rho, double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs, double* dp0);
 void L_correct(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u);

@@ -344,6 +344,28 @@ __device__ __forceinline__ void props_cell(const Phys& p, long long id, double a
   D[id] = a * p.D_l + (1.0 - a) * p.D_gas;
 }
 
+// props_cell into the PropsOut arrays, and their binary32 copies when asked for
+__device__ __forceinline__ void props_out(const Phys& p, long long id, double a, const PropsOut& po) {
+  props_cell(p, id, a, po.rhoG, po.omega, po.rho, po.mu, po.kc, po.cp, po.D);
+  if (po.s.T) {
+    po.s.T[id] = f32_rn(po.T[id]);
+    po.s.w[id] = f32_rn(po.omega[id]);
+    po.s.k[id] = f32_rn(po.kc[id]);
+    po.s.gD[id] = f32_rn(po.rho[id] * po.D[id]);
+    po.s.mu[id] = f32_rn(po.mu[id]);
+  }
+}
+
+__global__ void k_faces_f32(const double* u0, const double* u1, const double* u2, float* f0, float* f1, float* f2,
+                            long long n0, long long n1, long long n2) {
+  const long long n = n0 + n1 + n2;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n; id += (long long)gridDim.x * blockDim.x) {
+    if (id < n0) f0[id] = f32_rn(u0[id]);
+    else if (id < n0 + n1) f1[id - n0] = f32_rn(u1[id - n0]);
+    else f2[id - n0 - n1] = f32_rn(u2[id - n0 - n1]);
+  }
+}
+
 __global__ void k_props(Geo g, Phys p, const double* alpha, const double* rhoG, const double* omega, double* rho,
                         double* mu, double* kc, double* cp, double* D) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -427,7 +449,7 @@ __global__ void k_adv_update(Geo g, Phys p, const double* aL, const double* A0, 
     double ac = iclamp01(an);
     if (ac != an) { acc[1] += 1.0; acc[0] += (an - ac) * V; }
     alpha[id] = ac;
-    props_cell(p, id, ac, po.rhoG, po.omega, po.rho, po.mu, po.kc, po.cp, po.D);
+    props_out(p, id, ac, po);
   }
   block_sum_store<2>(acc, partials);
 }
@@ -450,7 +472,7 @@ __global__ void k_alpha_clip_only(Geo g, Phys p, const double* as, double* alpha
     double an = as[id], ac = iclamp01(an);
     if (ac != an) { acc[1] += 1.0; acc[0] += (an - ac) * cellV(g, i); }
     alpha[id] = ac;
-    props_cell(p, id, ac, po.rhoG, po.omega, po.rho, po.mu, po.kc, po.cp, po.D);
+    props_out(p, id, ac, po);
   }
   block_sum_store<2>(acc, partials);
 }
@@ -1007,13 +1029,13 @@ void L_adv_update(cudaStream_t st, int grid, Geo g, Phys p, const double* aL, co
   else k_adv_update<2><<<grid, TPB, 0, st>>>(g, p, aL, A0, A1, A2, Rp, Rm, alpha, partials, flags, po);
 }
 
-void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32*) {
   ++g_launches;
   if (nact(g) == 3) k_scalar_assemble<3><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, kc, D, mdot, u0, u1, u2, alpha_new, pinv, amb, Dg, c0, c1, c2, rhs);
   else k_scalar_assemble<2><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, kc, D, mdot, u0, u1, u2, alpha_new, pinv, amb, Dg, c0, c1, c2, rhs);
 }
 
-void L_mom_assemble(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+void L_mom_assemble(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32*) {
   ++g_launches;
   if (nact(g) == 3) {
     if (c == 0) k_mom_assemble<0, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);

@@ -26,6 +26,8 @@ __device__ __forceinline__ GeoF geof(const Geo& g) {
 }
 
 __device__ __forceinline__ float ldf(const double* p, long long i) { return f32_rn(p[i]); }
+// a binary32 copy holds the rounded values already (the accessors below take either)
+__device__ __forceinline__ float ldf(const float* p, long long i) { return p[i]; }
 
 __device__ __forceinline__ float minmod_f(float x, float y) {
   return (x * y > 0.f) ? (x > 0.f ? fminf(fabsf(x), fabsf(y)) : -fminf(fabsf(x), fabsf(y))) : 0.f;
@@ -38,7 +40,8 @@ __device__ __forceinline__ float areaN_f(const Geo& g, const GeoF& q, int a, flo
 }
 
 // face velocity of direction c with ghosts (the rules of ufg), rounded to FP32
-__device__ __forceinline__ float ufg_f(const Geo& g, const double* uc, int c, int i, int j, int k) {
+template <typename FT>
+__device__ __forceinline__ float ufg_f(const Geo& g, const FT* uc, int c, int i, int j, int k) {
   int m0 = g.n[0] + (c == 0), m1 = g.n[1] + (c == 1), m2 = g.n[2] + (c == 2);
   int a, side, q, m;
   if (i < 0 || i >= m0) { a = 0; q = i; m = m0; }
@@ -66,14 +69,16 @@ __device__ __forceinline__ float ufg_f(const Geo& g, const double* uc, int c, in
   return base + sign * v;
 }
 
-__device__ __forceinline__ float cellc_f(const Geo& g, const double* f, int i, int j, int k) {
+template <typename FT>
+__device__ __forceinline__ float cellc_f(const Geo& g, const FT* f, int i, int j, int k) {
   i = i < 0 ? 0 : (i >= g.n[0] ? g.n[0] - 1 : i);
   j = j < 0 ? 0 : (j >= g.n[1] ? g.n[1] - 1 : j);
   k = k < 0 ? 0 : (k >= g.n[2] ? g.n[2] - 1 : k);
   return ldf(f, cidx(g, i, j, k));
 }
 
-__device__ __forceinline__ float mu_edge_f(const Geo& g, const double* mu, const int L[3], const int R[3], int a,
+template <typename FT>
+__device__ __forceinline__ float mu_edge_f(const Geo& g, const FT* mu, const int L[3], const int R[3], int a,
                                            int sh) {
   int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
   La[a] += sh;
@@ -84,7 +89,8 @@ __device__ __forceinline__ float mu_edge_f(const Geo& g, const double* mu, const
 }
 
 // scalar cell value with ghosts (the rules of cellg), rounded to FP32
-__device__ __forceinline__ float cellg_f(const Geo& g, const double* f, int i, int j, int k, int rule, float amb,
+template <typename FT>
+__device__ __forceinline__ float cellg_f(const Geo& g, const FT* f, int i, int j, int k, int rule, float amb,
                                          const double* u0, const double* u1, const double* u2) {
   int a, side;
   if (i < 0) { a = 0; side = 0; i = 0; }
@@ -114,8 +120,9 @@ __device__ __forceinline__ float cellg_f(const Geo& g, const double* f, int i, i
 
 template <int C, int NA>
 __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const double* u0, const double* u1, const double* u2,
-                                  const double* rho, const double* mu, const double* pr, const double* alpha,
-                                  const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+                                  const double* rho, const double* pr, const double* alpha, const double* xi,
+                                  const float* muf, const float* uf0, const float* uf1, const float* uf2,
+                                  double* Dg, double* c0, double* c1, double* c2, double* rhs) {
   constexpr int c = C;
   int m[3] = {g.n[0], g.n[1], g.n[2]};
   m[c] -= 1;
@@ -131,6 +138,8 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
   const GeoF q = geof(g);
   const double* U[3] = {u0, u1, u2};
   const double* uc = U[c];
+  const float* UF[3] = {uf0, uf1, uf2};
+  const float* ucf = UF[c];
   double* Cc[3] = {c0, c1, c2};
   constexpr int na = NA;
   long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, R[0], R[1], R[2]);
@@ -149,9 +158,9 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
   // the increments, FP32
   const float rho_ff = f32_rn(rho_f), V_ff = f32_rn(V_f), r_ff = f32_rn(r_f);
   const float A_ff = V_ff * q.ih[c];
-  const float muL = ldf(mu, li), muR = ldf(mu, ri);
+  const float muL = muf[li], muR = muf[ri];
   const float mu_f = 0.5f * (muL + muR);
-  const float u_ff = f32_rn(u_f);
+  const float u_ff = ucf[fidx(g, c, f[0], f[1], f[2])];
   float t_adv = 0.f, t_vT = 0.f, d_visc = 0.f, t_bnd = 0.f;
 #pragma unroll
   for (int a = 0; a < na; ++a) {
@@ -159,7 +168,7 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
     float ubar;
     if (a == c) ubar = u_ff;
     else {
-      const double* ua = U[a];
+      const float* ua = UF[a];
       int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
       La[a] += 1;
       Ra[a] += 1;
@@ -172,7 +181,7 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
     for (int s = -2; s <= 2; ++s) {
       qq[0] = f[0]; qq[1] = f[1]; qq[2] = f[2];
       qq[a] += s;
-      us[s + 2] = ufg_f(g, uc, c, qq[0], qq[1], qq[2]);
+      us[s + 2] = ufg_f(g, ucf, c, qq[0], qq[1], qq[2]);
     }
     float uplus, uminus;
     if (ubar >= 0.f) { uplus = lim_up_f(us[1], us[2], us[3]); uminus = lim_up_f(us[0], us[1], us[2]); }
@@ -197,13 +206,13 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
         int fb[3] = {f[0], f[1], f[2]};
         fb[c] = 0;
         d_visc += kL;
-        t_bnd += kL * ldf(uc, fidx(g, c, fb[0], fb[1], fb[2]));
+        t_bnd += kL * ucf[fidx(g, c, fb[0], fb[1], fb[2])];
       }
       if (b[c] == m[c] - 1 && g.bc[c][1] != BC_OPEN) {
         int fb[3] = {f[0], f[1], f[2]};
         fb[c] = g.n[c];
         d_visc += kR;
-        t_bnd += kR * ldf(uc, fidx(g, c, fb[0], fb[1], fb[2]));
+        t_bnd += kR * ucf[fidx(g, c, fb[0], fb[1], fb[2])];
       }
     } else {
       float App, Apm;
@@ -215,9 +224,9 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
       } else {
         App = Apm = areaN_f(g, q, a, 0.f);
       }
-      float mup = mu_edge_f(g, mu, L, R, a, 1), mum = mu_edge_f(g, mu, L, R, a, -1);
+      float mup = mu_edge_f(g, muf, L, R, a, 1), mum = mu_edge_f(g, muf, L, R, a, -1);
       float kp = mup * App * q.ih[a], km = mum * Apm * q.ih[a];
-      const double* ua = U[a];
+      const float* ua = UF[a];
       int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
       La[a] += 1;
       Ra[a] += 1;
@@ -245,10 +254,12 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
 }
 
 template <int NA>
+// phif, gf, uf*: binary32 copies of phi, of gamma (k, or rho D) and of the face velocities
 __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
-                                     const double* kc, const double* D, const double* mdot, const double* u0,
-                                     const double* u1, const double* u2, const double* alpha_new, const double* pinv,
-                                     double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+                                     const double* mdot, const double* u0, const double* u1, const double* u2,
+                                     const double* alpha_new, const double* pinv, double amb, const float* phif,
+                                     const float* gf, const float* uf0, const float* uf1, const float* uf2,
+                                     double* Dg, double* c0, double* c1, double* c2, double* rhs) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
   int i, j, k;
@@ -256,6 +267,7 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
   constexpr int na = NA;
   const GeoF q = geof(g);
   const double* U[3] = {u0, u1, u2};
+  const float* UF[3] = {uf0, uf1, uf2};
   double* C[3] = {c0, c1, c2};
   // the state terms, FP64 (storage c V / dt and its phi term, the phase-change source)
   const double V = cellV(g, i);
@@ -264,8 +276,8 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
   double r = coef * V * phi[id] * p.idt + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
   const bool pin = (mode == 1) && ige64(alpha_new[id], 0.5);
   // the increments, FP32
-  const float phiP = f32_rn(phi[id]), ambf = f32_rn(amb);
-  const float gP = mode == 0 ? ldf(kc, id) : f32_rn(rho[id] * D[id]);
+  const float phiP = phif[id], ambf = f32_rn(amb);
+  const float gP = gf[id];
   float net = 0.f, Fsum = 0.f, dinc = 0.f, rinc = 0.f;
   int ci[3] = {i, j, k};
 #pragma unroll
@@ -276,7 +288,7 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
       if (side) f[a] += 1;
       const float Af = a == 0 ? (g.axisym ? (f[0] * q.h[0]) * q.h[1] : q.h[0] * q.h[1] * q.h[2] * q.ih[0])
                               : (g.axisym ? ((f[0] + 0.5f) * q.h[0]) * q.h[0] : q.h[0] * q.h[1] * q.h[2] * q.ih[a]);
-      const float F = ldf(U[a], fidx(g, a, f[0], f[1], f[2])) * Af;
+      const float F = UF[a][fidx(g, a, f[0], f[1], f[2])] * Af;
       float val;
       if (f[a] == 0 || f[a] == g.n[a]) {
         int kind = (side ? g.bc[a][1] : g.bc[a][0]);
@@ -288,9 +300,9 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
         int LL[3] = {Lc[0], Lc[1], Lc[2]}, RR[3] = {f[0], f[1], f[2]};
         LL[a] -= 1;
         RR[a] += 1;
-        float vL = ldf(phi, cidx(g, Lc[0], Lc[1], Lc[2])), vR = ldf(phi, cidx(g, f[0], f[1], f[2]));
-        if (F >= 0.f) val = lim_up_f(cellg_f(g, phi, LL[0], LL[1], LL[2], R_TO, ambf, u0, u1, u2), vL, vR);
-        else val = lim_up_f(cellg_f(g, phi, RR[0], RR[1], RR[2], R_TO, ambf, u0, u1, u2), vR, vL);
+        float vL = phif[cidx(g, Lc[0], Lc[1], Lc[2])], vR = phif[cidx(g, f[0], f[1], f[2])];
+        if (F >= 0.f) val = lim_up_f(cellg_f(g, phif, LL[0], LL[1], LL[2], R_TO, ambf, u0, u1, u2), vL, vR);
+        else val = lim_up_f(cellg_f(g, phif, RR[0], RR[1], RR[2], R_TO, ambf, u0, u1, u2), vR, vL);
       }
       // advected value relative to the cell's own: the flux difference then carries
       // only the increment (net - phi Fsum of the FP64 form, without its cancellation)
@@ -304,7 +316,7 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
       int Lc[3] = {i, j, k};
       Lc[a] -= 1;
       long long li = cidx(g, Lc[0], Lc[1], Lc[2]);
-      const float gL = mode == 0 ? ldf(kc, li) : f32_rn(rho[li] * D[li]);
+      const float gL = gf[li];
       const float Aa = a == 0 ? (g.axisym ? (i * q.h[0]) * q.h[1] : q.h[0] * q.h[1] * q.h[2] * q.ih[0])
                               : (g.axisym ? ((i + 0.5f) * q.h[0]) * q.h[0] : q.h[0] * q.h[1] * q.h[2] * q.ih[a]);
       cl = 2.f * gL * gP / (gL + gP) * Aa * q.ih[a];
@@ -321,7 +333,7 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
       Hc[a] += 1;
       long long hi = cidx(g, Hc[0], Hc[1], Hc[2]);
       if (ige64(alpha_new[hi], 0.5)) {
-        const float gH = f32_rn(rho[hi] * D[hi]);
+        const float gH = gf[hi];
         const float Ah = a == 0 ? (g.axisym ? (Hc[0] * q.h[0]) * q.h[1] : q.h[0] * q.h[1] * q.h[2] * q.ih[0])
                                 : (g.axisym ? ((i + 0.5f) * q.h[0]) * q.h[0] : q.h[0] * q.h[1] * q.h[2] * q.ih[a]);
         const float ch = 2.f * gP * gH / (gP + gH) * Ah * q.ih[a];
@@ -478,28 +490,38 @@ void L_adv_faces_mx_all(cudaStream_t st, Geo g, Phys p, const double* as, const 
 void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi,
                           const double* rho, const double* cp, const double* kc, const double* D, const double* mdot,
                           const double* u0, const double* u1, const double* u2, const double* alpha_new,
-                          const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+                          const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs,
+                          const Shadow32* s32) {
+  // kc and D enter through their binary32 copies (gamma = k or rho D, formed with the
+  // properties); phi's copy is that of the step's old T or omega
+  (void)kc;
+  (void)D;
+  const float* phif = mode == 0 ? s32->T : s32->w;
+  const float* gf = mode == 0 ? s32->k : s32->gD;
+  const float* uf2 = s32->u[2] ? s32->u[2] : s32->u[0];
   ++g_launches;
   if (nact(g) == 3)
-    k_scalar_assemble_mx<3><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, kc, D, mdot, u0, u1, u2, alpha_new, pinv,
-                                                  amb, Dg, c0, c1, c2, rhs);
+    k_scalar_assemble_mx<3><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, mdot, u0, u1, u2, alpha_new, pinv, amb,
+                                                  phif, gf, s32->u[0], s32->u[1], uf2, Dg, c0, c1, c2, rhs);
   else
-    k_scalar_assemble_mx<2><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, kc, D, mdot, u0, u1, u2, alpha_new, pinv,
-                                                  amb, Dg, c0, c1, c2, rhs);
+    k_scalar_assemble_mx<2><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, mdot, u0, u1, u2, alpha_new, pinv, amb,
+                                                  phif, gf, s32->u[0], s32->u[1], uf2, Dg, c0, c1, c2, rhs);
 }
 
 void L_mom_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0,
                        const double* u1, const double* u2, const double* rho, const double* mu, const double* pr,
                        const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2,
-                       double* rhs) {
+                       double* rhs, const Shadow32* s32) {
+  (void)mu;   // through its binary32 copy
+  const float *m32 = s32->mu, *f0 = s32->u[0], *f1 = s32->u[1], *f2 = s32->u[2] ? s32->u[2] : s32->u[0];
   ++g_launches;
   if (nact(g) == 3) {
-    if (c == 0) k_mom_assemble_mx<0, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
-    else if (c == 1) k_mom_assemble_mx<1, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
-    else k_mom_assemble_mx<2, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
+    if (c == 0) k_mom_assemble_mx<0, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, pr, alpha, xi, m32, f0, f1, f2, Dg, c0, c1, c2, rhs);
+    else if (c == 1) k_mom_assemble_mx<1, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, pr, alpha, xi, m32, f0, f1, f2, Dg, c0, c1, c2, rhs);
+    else k_mom_assemble_mx<2, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, pr, alpha, xi, m32, f0, f1, f2, Dg, c0, c1, c2, rhs);
   } else {
-    if (c == 0) k_mom_assemble_mx<0, 2><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
-    else k_mom_assemble_mx<1, 2><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
+    if (c == 0) k_mom_assemble_mx<0, 2><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, pr, alpha, xi, m32, f0, f1, f2, Dg, c0, c1, c2, rhs);
+    else k_mom_assemble_mx<1, 2><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, pr, alpha, xi, m32, f0, f1, f2, Dg, c0, c1, c2, rhs);
   }
 }
 
