@@ -22,8 +22,9 @@ factorisation.
 
 Parity unpinned: the interface-cell threshold on |grad(alpha)| and the adjacent
 gas-cell threshold ALPHA_GAS (the paper gives neither number), and the coupled
-Peng-Robinson 3D forced-convection dynamics as a whole; these rest on the
-comparison with the CUDA path alone.  Every other stage has a pin in the tests.  Discrete readings of points the paper leaves open are listed in
+dynamics of the 3D forced-convection case with an evaporating Peng-Robinson droplet
+as a whole (its thermodynamics and its flow without a droplet have pins); these rest
+on the comparison with the CUDA path alone.  Every other stage has a pin in the tests.  Discrete readings of points the paper leaves open are listed in
 the repository's design notes; the code states each where it is used.
 """
 import math

@@ -138,6 +138,46 @@ def test_compressive_flux_converges_to_the_continuum_term():
     assert err0 < 1e-3
 
 
+def test_forced_inflow_duct_flow_3d():
+    """3D forced convection (Table tableboundary: fixed-velocity inlet, open outlet,
+    no-slip side walls) without a droplet and at uniform T and omega, so S = 0: every
+    step conserves volume exactly (discrete div u = 0, outflow = inflow), keeps the
+    inlet velocity, and keeps the mirror symmetries of the square duct (a transposed
+    index or a one-sided stencil breaks them).  After a few steps the no-slip walls
+    have slowed the wall-adjacent fluid below U and the core has sped up above it, and
+    the pressure that drives the flow falls monotonically from the inlet to the open
+    outlet (p_rgh = 0 outside)."""
+    U = 0.5
+    base = W.cfg3_cart3d(nc=12, L=(1.2e-3,) * 3, xc=(0.6e-3,) * 3, D0=1e-12, precision=0, T_perturb=0.0,
+                         physics_mask=W.PHYS_FLOW, g=(0.0, 0.0, 0.0), u_inflow=U)
+    for dt, steps in ((2e-6, 3), (2e-5, 5)):
+        cfg = dict(base, dt=dt)
+        G = Grid(cfg)
+        st = O.init_state(cfg)
+        assert st["alpha"].max() == 0.0
+        scale = U * G.A[2][0, 0, 0]
+        for _ in range(steps):
+            st = O.step(cfg, st, keep=True)
+            u = st["u"]
+            assert np.abs(st["aux"]["S"]).max() == 0.0
+            div = O.divergence_sum(G, [u[a] * G.A[a] for a in range(3)])
+            assert np.abs(div).max() < 1e-12 * scale
+            assert np.all(u[2][:, :, 0] == U)
+            qin = float(np.sum(u[2][:, :, 0] * G.A[2][:, :, 0]))
+            qout = float(np.sum(u[2][:, :, -1] * G.A[2][:, :, -1]))
+            assert qout == pytest.approx(qin, rel=1e-12)
+            uz = u[2]
+            assert np.abs(uz - uz[::-1, :, :]).max() < 1e-12 * U
+            assert np.abs(uz - uz[:, ::-1, :]).max() < 1e-12 * U
+            assert np.abs(uz - uz.transpose(1, 0, 2)).max() < 1e-12 * U
+            assert np.abs(u[0] + u[0][::-1, :, :]).max() < 1e-12 * U
+    uz, p = st["u"][2], st["p"]
+    mid = G.n[2] // 2
+    assert uz[5:7, 5:7, mid].mean() > U > uz[0, 5:7, mid].mean()
+    pc = p[5:7, 5:7, :].mean(axis=(0, 1))
+    assert np.all(np.diff(pc) < 0.0) and pc[-1] > 0.0
+
+
 def test_step_divergence_matches_source_and_K_invariant():
     cfg = W.cfg1_axisym_64x128()
     G = Grid(cfg)
