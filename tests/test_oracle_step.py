@@ -178,6 +178,35 @@ def test_forced_inflow_duct_flow_3d():
     assert np.all(np.diff(pc) < 0.0) and pc[-1] > 0.0
 
 
+def test_pr_forced_droplet_invariants_3d():
+    """The coupled 3D case (Peng-Robinson equilibrium at 20 bar, forced inflow, an
+    evaporating droplet) on a 16^3 grid: each step keeps alpha in [0, 1], changes the
+    liquid volume only by the evaporated and clipped volumes, leaves a velocity whose
+    discrete divergence is the Stefan source S V of Eq. pequation (which is far from
+    zero here), keeps the inlet velocity, and (without a capped cell) keeps the K
+    normalisation sum(m V) = sum(m_raw V)."""
+    cfg = W.cfg3_cart3d(nc=16, L=(1.6e-3,) * 3, xc=(0.8e-3,) * 3, precision=0)
+    G = Grid(cfg)
+    st = O.init_state(cfg)
+    V0 = float(np.sum(st["alpha"] * G.V))
+    scale = cfg["u_inflow"] * G.A[2][0, 0, 0]
+    for _ in range(2):
+        st1 = O.step(cfg, st, keep=True)
+        aux, u = st1["aux"], st1["u"]
+        assert st1["alpha"].min() >= 0.0 and st1["alpha"].max() <= 1.0
+        lhs = np.sum(st1["alpha"] * G.V) - np.sum(st["alpha"] * G.V)
+        rhs = -cfg["dt"] * np.sum(aux["mdot"] * G.V) / cfg["rho_l"] - (st1["clip_mass"] - st["clip_mass"])
+        assert abs(lhs - rhs) < 1e-13 * V0
+        div = O.divergence_sum(G, [u[a] * G.A[a] for a in range(3)])
+        SV = aux["S"] * G.V
+        assert np.abs(SV).max() > 0.05 * scale
+        assert np.abs(div - SV).max() < 1e-11 * scale
+        assert np.all(u[2][:, :, 0] == cfg["u_inflow"])
+        if st1["ncap"] == 0:
+            assert np.sum(aux["mdot"] * G.V) == pytest.approx(np.sum(aux["mraw"] * G.V), rel=1e-12)
+        st = st1
+
+
 def test_step_divergence_matches_source_and_K_invariant():
     cfg = W.cfg1_axisym_64x128()
     G = Grid(cfg)
