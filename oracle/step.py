@@ -23,8 +23,9 @@ factorisation.
 Parity unpinned: the interface-cell threshold on |grad(alpha)| and the adjacent
 gas-cell threshold ALPHA_GAS (the paper gives neither number), and the coupled
 dynamics of the 3D forced-convection case with an evaporating Peng-Robinson droplet
-as a whole (its thermodynamics and its flow without a droplet have pins); these rest
-on the comparison with the CUDA path alone.  Every other stage has a pin in the tests.  Discrete readings of points the paper leaves open are listed in
+beyond its invariants (its thermodynamics, its flow without a droplet and its
+conservation properties have pins); these rest on the comparison with the CUDA path
+alone.  Every other stage has a pin in the tests.  Discrete readings of points the paper leaves open are listed in
 the repository's design notes; the code states each where it is used.
 """
 import math
