@@ -45,6 +45,7 @@ class Grid:
     # -- broadcasting helpers ------------------------------------------------
     @staticmethod
     def along(v, a):
+        """The 1D array v as a (3D) array varying along axis a only, for broadcasting."""
         shape = [1, 1, 1]
         shape[a] = v.shape[0]
         return v.reshape(shape)
@@ -77,7 +78,9 @@ class Grid:
         return h[0] * h[1] * h[2] / h[a]
 
     def ncell(self):
+        """Number of cells."""
         return self.n[0] * self.n[1] * self.n[2]
 
     def lin(self, i, j, k):
+        """Linear cell index, i fastest."""
         return i + self.n[0] * (j + self.n[1] * k)

@@ -181,6 +181,7 @@ def pad_velocity(G, u, c, u_in):
 
 
 def fshape(G, a):
+    """Shape of a face array of direction a (n_a + 1 faces along a)."""
     s = list(G.n)
     s[a] += 1
     return tuple(s)
@@ -189,6 +190,7 @@ def fshape(G, a):
 # ============================================================ small formulas
 
 def minmod(x, y):
+    """minmod(x, y): the smaller magnitude when x and y share a sign, else 0."""
     return np.where(x * y > 0.0, np.sign(x) * np.minimum(np.abs(x), np.abs(y)), 0.0)
 
 
@@ -803,6 +805,8 @@ def momentum_predictor(cfg, G, st, pr, alpha, dt, parts=None):
             else:
                 # edges at f +- e_a/2; mu = mean of the 4 cells around the edge
                 def mu_edge(sh):
+                    # viscosity on the edge between this face and its neighbour at
+                    # offset sh along a: the mean of the four cells around the edge
                     s = _view(G, Pmu, fs, {c: -1}) + _view(G, Pmu, fs, {c: 0}) \
                         + _view(G, Pmu, fs, {c: -1, a: sh}) + _view(G, Pmu, fs, {c: 0, a: sh})
                     return 0.25 * s
@@ -1052,6 +1056,7 @@ def diagnostics(cfg, st):
 
 
 def run(cfg, nsteps, st=None):
+    """nsteps time steps from the initial state of cfg (or from st)."""
     st = init_state(cfg) if st is None else st
     for _ in range(nsteps):
         st = step(cfg, st)
