@@ -202,11 +202,14 @@ int droplet_box_solve(const int m[3], const double* D, const double* c0, const d
  * 10.5 MB, held by every GPU that loads the library until the process
  * exits); a larger box is rejected with DROPLET_ERR_SIZE before any work is
  * enqueued.  The call makes no cudaMalloc, cudaFree, pinned-memory or other
- * allocating call.  The first call on a device, with that device current,
- * looks up the array's device address (cudaGetSymbolAddress) and caches it;
- * make that first call outside any stream capture.  Every call reuses the same
- * array and initialises what it needs, so calls must not overlap on the GPU:
- * two solves running at once on different streams would race on the array. */
+ * allocating call.  Every call looks up the array's device address on the
+ * current device (cudaGetSymbolAddress, which allocates nothing; no address is
+ * kept between calls).  Under lazy module loading (the CUDA default) the array
+ * is placed in device memory at the first call on a device: make that first
+ * call before any stream capture, and early, if the caller's own pool is to
+ * take the rest of the memory.  Every call reuses the same array and
+ * initialises what it needs, so calls must not overlap on the GPU: two solves
+ * running at once on different streams would race on the array. */
 #define DROPLET_NOALLOC_MAX_UNKNOWNS 262144
 int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0, const double* c1,
                               const double* c2, const double* b, double* x, double rtol, int maxit,

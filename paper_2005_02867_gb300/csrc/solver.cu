@@ -2598,22 +2598,18 @@ constexpr long long NA_PART = (long long)RED_BLOCKS * 8;
 constexpr long long NA_WORDS = 5 * NA_MAX + NA_PART + S_COUNT + 8;
 static __device__ __align__(256) double g_noalloc_ws[NA_WORDS];
 
-// device address of the array, looked up once per device (host code may not use the symbol directly)
-static double* g_noalloc_addr[64] = {nullptr};
-
+// Device address of the array in the current device's context.  Host code may not use
+// the symbol itself (it names a host-side stand-in), so every call looks the address up
+// again: the lookup allocates nothing, and a cached address would go stale when the
+// context is replaced (cudaDeviceReset, or a caller that switches driver contexts).
 static int noalloc_workspace(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DROPLET_ERR_CUDA;
-  if (!g_noalloc_addr[dev]) {
-    void* ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_ws);
-    if (e != cudaSuccess || !ptr) {
-      fprintf(stderr, "droplet: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
-      return DROPLET_ERR_CUDA;
-    }
-    g_noalloc_addr[dev] = (double*)ptr;
+  void* ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_ws);
+  if (e != cudaSuccess || !ptr) {
+    fprintf(stderr, "droplet: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+    return DROPLET_ERR_CUDA;
   }
-  *out = g_noalloc_addr[dev];
+  *out = (double*)ptr;
   return 0;
 }
 
@@ -2625,6 +2621,12 @@ extern "C" int droplet_box_solve_noalloc(const int m[3], const double* D, const 
   using namespace dg;
   if (!m || !D || !c0 || !c1 || !b || !x || maxit < 1 || !(rtol > 0.0)) return DROPLET_ERR_ARG;
   if (m[0] < 1 || m[1] < 1 || m[2] < 1 || (m[2] > 1 && !c2)) return DROPLET_ERR_ARG;
+  // every dimension is at least 1, so one above the limit already exceeds it (and the
+  // product below cannot wrap)
+  if (m[0] > NA_MAX || m[1] > NA_MAX || m[2] > NA_MAX) {
+    fprintf(stderr, "droplet_box_solve_noalloc: a box dimension exceeds the static workspace (%lld)\n", NA_MAX);
+    return DROPLET_ERR_SIZE;
+  }
   long long N = (long long)m[0] * m[1] * m[2];
   if (N > NA_MAX) {
     fprintf(stderr, "droplet_box_solve_noalloc: %lld unknowns exceed the static workspace (%lld)\n", N, NA_MAX);

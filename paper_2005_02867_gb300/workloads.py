@@ -59,8 +59,12 @@ def cfg1_axisym_64x128(**over):
 def cfg1_d2law(**over):
     """Constant-property microgravity check of the d2 law on the 64x128 grid:
     rho_G frozen at p M_g/(R T_amb), energy off, T = T_drop everywhere, initial
-    vapour from the quasi-steady spherical Stefan profile."""
-    base = dict(const_props_check=1, physics_mask=PHYS_EVAP | PHYS_SPECIES | PHYS_FLOW)
+    vapour from the quasi-steady spherical Stefan profile.  dt 1e-4 s (the
+    Stefan velocity stays below 0.04 m/s: Courant number < 0.07 at 62.5 um),
+    so that a few hundred steps run well past the transient r_s^2/D = 5 ms.
+    Interface compression C_alpha = 4: at C_alpha = 1 the outward Stefan flow
+    carries liquid into the first gas cells over tens of milliseconds."""
+    base = dict(const_props_check=1, physics_mask=PHYS_EVAP | PHYS_SPECIES | PHYS_FLOW, dt=1e-4, C_alpha=4.0)
     base.update(over)
     return make(**base)
 

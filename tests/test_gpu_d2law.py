@@ -1,9 +1,17 @@
-"""Config 1 as a d2-law check (Sec. 4: the squared diameter of an isolated droplet
-decreases linearly, K = 8 rho_g D ln(1 + B_Y) / rho_l): the constant-property
-microgravity case on the 64 x 128 grid, 200 steps, in FP64 and in mixed precision.
-Mixed precision must reproduce the FP64 d2 slope within 1e-3 and the droplet volume
-within 1e-5; the FP64 slope must sit near K (the coarse-grid flux is taken one to two
-cells outside the surface, so within [0.5, 1.3] K, as for the oracle)."""
+"""The d2 law on the GPU (Sec. 1 and Sec. 4: once the initial transient is over the
+squared diameter of an isolated droplet falls linearly, K = 8 rho_g D ln(1 + B_Y) /
+rho_l): the constant-property microgravity case run for 25 ms (five times r_s^2/D),
+the slope fitted over the second half, as in the oracle's pin.
+
+- FP64 on 64 x 128 against the oracle's run of the same case: the same slope.
+- Mixed precision against FP64 at the accuracy the spec asks of it: d2 slope
+  within 1e-3, droplet volume within 1e-5 -- at the benchmark's solver tolerances
+  (1e-8) as well as at tight ones.
+- Refinement 64 x 128 -> 128 x 256 -> 256 x 512: the method reads the flux one to
+  two cells outside the surface, where the spherical flux density is lower by
+  (r_s / r)^2, so the rate approaches K at first order (the error at least a third
+  smaller per halving of h) and lies within [1.0, 1.143] K +- 15 % from 128 x 256 on.
+"""
 import math
 
 import numpy as np
@@ -12,6 +20,8 @@ import pytest
 from paper_2005_02867_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
+
+STEPS = 250
 
 
 @pytest.fixture(scope="module")
@@ -26,35 +36,63 @@ def D():
     return droplet
 
 
-def run(D, precision, steps=200):
-    cfg = W.cfg1_d2law(precision=precision, cg_rtol=1e-10, helm_rtol=1e-10)
+def slope(t, d2):
+    t, d2 = np.asarray(t), np.asarray(d2)
+    h = len(t) // 2
+    return -float(np.polyfit(t[h:], d2[h:], 1)[0])
+
+
+def run(D, n=64, precision=0, rtol=1e-10):
+    cfg = W.cfg1_d2law(n=(n, 2 * n, 1), precision=precision, cg_rtol=rtol, helm_rtol=rtol)
     sim = D.Droplet(cfg)
-    t, d2, V = [], [], []
-    for _ in range(steps):
+    t, d2 = [], []
+    for _ in range(STEPS):
         assert sim.step(1) == 0
         d = sim.diag()
         t.append(d["t"])
         d2.append(d["d2"])
-        V.append(d["V_l"])
+    V = d["V_l"]
     sim.close()
-    t, d2 = np.array(t), np.array(d2)
-    half = steps // 2
-    slope = -np.polyfit(t[half:], d2[half:], 1)[0]   # quasi-steady second half
-    return slope, V[-1], cfg
+    return slope(t, d2), V, cfg
 
 
-def test_d2_slope_mixed_vs_fp64_and_K(D):
-    k64, v64, cfg = run(D, 0)
-    k32, v32, _ = run(D, 1)
-    assert k64 > 0.0
-    assert abs(k32 - k64) <= 1e-3 * k64
-    assert abs(v32 - v64) <= 1e-5 * v64
-    # the d2-law constant from the thermodynamics of the configuration (Raoult,
-    # Clausius-Clapeyron at T_drop, ideal-gas rho_g at T_amb)
+def d2_constant(cfg):
+    """K from the thermodynamics of the configuration: Raoult with Clausius-Clapeyron
+    at T_drop, ideal-gas rho_g at T_amb (frozen in the check mode)."""
     R = 8.314462618
     p0 = 101325.0 * math.exp(cfg["Lv"] * cfg["M_l"] / R * (1.0 / cfg["Tb"] - 1.0 / cfg["T_drop"]))
     y = p0 / cfg["P"]
     Ys = y * cfg["M_l"] / (y * cfg["M_l"] + (1.0 - y) * cfg["M_g"])
     rg = cfg["P"] * cfg["M_g"] / (R * cfg["T_amb"])
-    K = 8.0 * rg * cfg["D_g"] * math.log(1.0 + Ys / (1.0 - Ys)) / cfg["rho_l"]
-    assert 0.5 * K < k64 < 1.3 * K
+    return 8.0 * rg * cfg["D_g"] * math.log(1.0 + Ys / (1.0 - Ys)) / cfg["rho_l"]
+
+
+def test_d2_slope_fp64_matches_oracle(D):
+    from oracle import step as O
+    k64, _, cfg = run(D, 64, 0, rtol=1e-12)
+    st = O.init_state(cfg)
+    t, d2 = [], []
+    for _ in range(STEPS):
+        st = O.step(cfg, st)
+        d = O.diagnostics(cfg, st)
+        t.append(d["t"])
+        d2.append(d["d2"])
+    ko = slope(t, d2)
+    assert abs(k64 - ko) <= 1e-6 * ko, (k64, ko)
+
+
+@pytest.mark.parametrize("rtol", [1e-10, 1e-8])
+def test_d2_slope_mixed_vs_fp64(D, rtol):
+    k64, v64, _ = run(D, 64, 0, rtol)
+    k32, v32, _ = run(D, 64, 1, rtol)
+    assert k64 > 0.0
+    assert abs(k32 - k64) <= 1e-3 * k64, (k32, k64)
+    assert abs(v32 - v64) <= 1e-5 * v64, (v32, v64)
+
+
+def test_d2_slope_converges_to_K(D):
+    K = d2_constant(W.cfg1_d2law())
+    r = {n: run(D, n, 0)[0] / K for n in (64, 128, 256)}
+    err = {n: abs(1.0 - v) for n, v in r.items()}
+    assert err[128] < 0.67 * err[64] and err[256] < 0.67 * err[128], r
+    assert 0.85 <= r[128] <= 1.31 and 0.85 <= r[256] <= 1.31, r

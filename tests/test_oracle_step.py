@@ -271,40 +271,92 @@ def test_uniform_state_is_steady():
     assert max(np.abs(st1["u"][a]).max() for a in (0, 1)) < 1e-12
 
 
-@pytest.mark.slow
-def test_d2_law_trend_and_total_mass_constant_properties():
-    """d2 law in the constant-property microgravity mode (Sec. 4 states the
-    linear d2 decrease; K = 8 rho_g D ln(1 + B_Y)/rho_l).  The method takes the
-    flux one to two cells outside the surface, where the spherical flux density
-    is lower by (r_s/r)^2, so the rate is below K on coarse grids and must
-    approach it under refinement."""
-    def rate(n, steps):
-        cfg = W.cfg1_d2law(n=(n, 2 * n, 1), dt=5e-5 * 64 / n)
-        st = O.init_state(cfg)
-        d0 = O.diagnostics(cfg, st)
-        vals = []
-        for _ in range(steps):
-            st = O.step(cfg, st)
-            d = O.diagnostics(cfg, st)
-            vals.append((2 / 3) * (6 / math.pi) ** (2 / 3) * d["V_l"] ** (-1 / 3) * d["mdot_tot"] / cfg["rho_l"])
-        # total mass: liquid lost (evaporated, clipping excluded) against vapour
-        # gained in the domain plus vapour carried out through the open boundaries
-        lost = d0["M_liq"] - d["M_liq"] - cfg["rho_l"] * (d["clip_mass"] - d0["clip_mass"])
-        gained = d["M_vap"] - d0["M_vap"] + d["vap_out_cum"] - d0["vap_out_cum"]
-        return float(np.mean(vals[steps // 2:])), gained / lost
-    cfg = W.cfg1_d2law()
+def _d2_law_run(args):
+    """One constant-property microgravity run (module level: runs in a worker
+    process).  Returns the least-squares d2 slope over the second half, the
+    surface-weighted flux dilution F = <(r_s / r_adj)^2> of the last step's
+    interface cells, the discrete surface area against 4 pi r_s^2, and the
+    vapour gained (in the domain and through the open boundaries) over the
+    liquid evaporated in the second half."""
+    n, steps = args
+    cfg = W.cfg1_d2law(n=(n, 2 * n, 1))
+    G = Grid(cfg)
+    st = O.init_state(cfg)
+    half = steps // 2
+    t, d2 = [], []
+    for k in range(steps):
+        prev = st
+        st = O.step(cfg, st, keep=(k == steps - 1))
+        d = O.diagnostics(cfg, st)
+        t.append(d["t"])
+        d2.append(d["d2"])
+        if k == half - 1:
+            dh = d
+    rate = -float(np.polyfit(t[half:], d2[half:], 1)[0])
+    # liquid lost (clipping excluded) against vapour gained in the second half
+    lost = dh["M_liq"] - d["M_liq"] - cfg["rho_l"] * (d["clip_mass"] - dh["clip_mass"])
+    gained = d["M_vap"] - dh["M_vap"] + d["vap_out_cum"] - dh["vap_out_cum"]
+    # the flux is read at the adjacent gas cell Q, at distance r_Q from the centre,
+    # and multiplied by |grad alpha| of the interface cell P (Eqs. massflux ff.)
+    g = O.grad_central(G, O.pad_scalar(G, prev["alpha"], "alpha"))
+    gm = np.sqrt(g[0] ** 2 + g[1] ** 2)
+    adj = st["aux"]["adj"]
+    X = np.meshgrid(G.xc[0], G.xc[1], G.xc[2], indexing="ij")
+    r = np.sqrt(X[0] ** 2 + (X[1] - cfg["xc"][1]) ** 2).ravel(order="F")
+    rs = 0.5 * d["d_eq"]
+    m = adj >= 0
+    w = (gm * G.V)[m]
+    F = float(np.sum((rs / r[adj[m]]) ** 2 * w) / np.sum(w))
+    area = 2.0 * math.pi * float(np.sum(gm * G.V)) / (4.0 * math.pi * rs * rs)
+    return dict(n=n, rate=rate, F=F, area=area, mass=gained / lost)
+
+
+def _d2_constant(cfg):
+    """K = 8 rho_g D ln(1 + B_Y) / rho_l at the surface state of the check mode."""
     Ys = float(th.Y_eq(cfg, np.array([cfg["T_drop"]]))[0])
     rg = cfg["P"] * cfg["M_g"] / (th.R_GAS * cfg["T_amb"])
-    K = 8 * rg * cfg["D_g"] * math.log(1 + Ys / (1 - Ys)) / cfg["rho_l"]
-    r64, m64 = rate(64, 40)
-    r128, m128 = rate(128, 40)
-    r64, r128 = r64 / K, r128 / K
-    assert 0.5 < r64 < 1.3 and 0.5 < r128 < 1.3
-    assert abs(1.0 - r128) < abs(1.0 - r64)
-    # Total (liquid + vapour) mass.  The vapour enters the gas by diffusion from the
-    # liquid cells held at Y_eq (Eq. speciesequation has no interface source), the
-    # liquid leaves at the rate m taken one to two cells out: the two agree only up
-    # to that discretisation error, which shrinks under refinement (the same
-    # (r_s / r)^2 deficit as the rate above, plus the Stefan-flow share).
-    assert 1.0 < m128 < m64 < 2.5
-    assert (m128 - 1.0) < 0.75 * (m64 - 1.0)
+    return 8 * rg * cfg["D_g"] * math.log(1 + Ys / (1 - Ys)) / cfg["rho_l"]
+
+
+@pytest.mark.slow
+def test_d2_law_and_total_mass_after_transient():
+    """d2 law in the constant-property microgravity mode (Sec. 1 and Sec. 4: the
+    squared diameter of an isolated droplet falls linearly once the initial
+    transient is over, K = 8 rho_g D ln(1 + B_Y) / rho_l), run for 25 ms, five
+    times r_s^2/D, the slope fitted over the second half, on 32 x 64, 64 x 128
+    and 128 x 256.
+
+    The method reads the flux j at the adjacent gas cell Q and weights it with
+    |grad alpha| of the interface cell P.  In the quasi-steady spherical state
+    the total vapour flux density falls as (r_s / r)^2, so the computed rate is
+    K times the finite-domain factor (between 1, unbounded, and 1/(1 - r_s/R) =
+    1.143 for the nearest boundary R = 4 mm) times the surface-weighted dilution
+    F = <(r_s / r_Q)^2> of the cells actually read: F = 0.57 / 0.74 / 0.85 on the
+    three grids.  So: rate / (K F) within [1.0, 1.143] +- 15 %; the raw rate
+    approaches K at first order under refinement (0.61 / 0.77 / 0.87 K) and is
+    inside that band on 128 x 256.  A 1.5x error in j, a dropped convective part
+    rho omega v (a quarter of j at the surface) or a flipped sign fail it.
+
+    Total mass: the vapour enters the gas by diffusion from the liquid cells held
+    at Y_eq (Eq. speciesequation has no interface source, the saturation value is
+    assigned to the liquid, Sec. 2.5), while the liquid loses mass at the rate
+    read at Q.  The vapour gained therefore exceeds the liquid lost by the same
+    dilution: ratio x F = 1 within [0.95, 1.2] (measured 1.127 / 1.089 / 1.108),
+    with the excess of the ratio over 1 shrinking at first order (1.96, 1.47,
+    1.29)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(3) as pool:
+        res = {r["n"]: r for r in pool.map(_d2_law_run, [(32, 250), (64, 250), (128, 200)])}
+    K = _d2_constant(W.cfg1_d2law())
+    err = {}
+    for n, r in res.items():
+        rK = r["rate"] / K
+        err[n] = abs(1.0 - rK)
+        assert 0.85 <= rK / r["F"] <= 1.31, (n, rK, r["F"])
+        assert abs(r["area"] - 1.0) < 0.05, (n, r["area"])
+        assert 0.95 <= r["mass"] * r["F"] <= 1.2, (n, r["mass"], r["F"])
+    # first order: the error at least a third smaller per halving of h
+    assert err[64] < 0.67 * err[32] and err[128] < 0.67 * err[64], err
+    assert 0.85 <= res[128]["rate"] / K <= 1.31
+    ex = {n: r["mass"] - 1.0 for n, r in res.items()}
+    assert ex[64] < 0.75 * ex[32] and ex[128] < 0.75 * ex[64], ex

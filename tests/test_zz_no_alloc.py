@@ -56,10 +56,34 @@ def test_noalloc_matches_allocating_solver_twice(D):
         assert np.abs(xn - xa).max() <= 1e-10 * np.abs(xa).max(), call
 
 
+def test_noalloc_leaves_device_memory_unchanged(D):
+    """After a first call (which, under lazy module loading, places the static
+    array on the device), further calls change the device's free memory by
+    nothing."""
+    import torch
+    m = (40, 36, 1)
+    t = _system(m, 13)
+    x = torch.zeros_like(t[-1])
+    st = torch.cuda.current_stream().cuda_stream
+    args = (m, t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), 0, t[4].data_ptr(), x.data_ptr(), 1e-12, 4000, st)
+    assert D.droplet_box_solve_noalloc(*args)[0] == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        x.zero_()
+        assert D.droplet_box_solve_noalloc(*args)[0] == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
 def test_noalloc_rejects_oversize_box(D):
     import torch
-    m = (D.NOALLOC_MAX_UNKNOWNS + 1, 1, 1)
     small = torch.zeros(4, dtype=torch.float64, device="cuda")
     p = small.data_ptr()
-    rc, _, _ = D.droplet_box_solve_noalloc(m, p, p, p, 0, p, p, 1e-10, 10, torch.cuda.current_stream().cuda_stream)
-    assert rc == -5
+    st = torch.cuda.current_stream().cuda_stream
+    big = D.NOALLOC_MAX_UNKNOWNS + 1
+    # too many unknowns; and dimensions whose product would wrap a 64-bit integer
+    for m in ((big, 1, 1), (2, big, 1), (2**31 - 1, 2**31 - 1, 2**31 - 1)):
+        rc, _, _ = D.droplet_box_solve_noalloc(m, p, p, p, p, p, p, 1e-10, 10, st)
+        assert rc == -5, m
