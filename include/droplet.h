@@ -46,6 +46,9 @@ extern "C" {
 #define DROPLET_ERR_SIZE          -5  /* host buffer size does not match the field     */
 #define DROPLET_ERR_NOMEM         -6  /* device allocation failed                      */
 #define DROPLET_ERR_IO            -7  /* checkpoint file could not be written or read  */
+#define DROPLET_ERR_TIMEOUT       -8  /* a bounded device wait (grid barrier of a
+                                         persistent solve) ran out; the step finished
+                                         with that solve stopped where it was          */
 
 /* diagnostic flag bits (droplet_diag_t.flags), accumulated since the last read */
 #define DROPLET_FLAG_NO_INTERFACE   1u   /* sum f(alpha) m_raw V = 0: mdot set to 0         */
@@ -53,6 +56,8 @@ extern "C" {
 #define DROPLET_FLAG_ALPHA_CLIPPED  4u   /* alpha left [0, 1] and was clipped              */
 #define DROPLET_FLAG_ADJ_NOT_FOUND  8u   /* an interface cell found no adjacent gas cell   */
 #define DROPLET_FLAG_BOILING       16u   /* saturation mole fraction clamped below 1       */
+#define DROPLET_FLAG_NONFINITE     32u   /* a NaN or infinity in alpha, T, omega, rho_G, mdot
+                                            or a face velocity (seen by the diagnostics)  */
 
 /* physics_mask bits */
 #define DROPLET_PHYS_EVAP     1
@@ -98,6 +103,14 @@ typedef struct droplet_config {
                            or the autotuner's choice where it runs.  Owned cells get the same
                            values whatever the tile: a pure performance setting.  Each entry
                            0 or 8 .. 256; an odd entry is rounded up to the next even one. */
+  int    wait_limit;    /* polls of the arrival counter after which a grid-barrier wait of a
+                           persistent (cooperative) solve gives up; 0 = 2^22.  A wait that
+                           runs out stops that solve and the step reports DROPLET_ERR_TIMEOUT
+                           instead of hanging (a launch whose blocks are not all resident) */
+  int    solver_select; /* 0 = by size: persistent solvers for the latency-bound sizes, the
+                           launched multi-kernel ones beyond; 1 = the launched solvers at
+                           every size (the path of the largest grids, e.g. for checking it
+                           on small ones).  The answers agree to the solver tolerance. */
 } droplet_config;
 
 /* Diagnostics of one droplet after the last completed step (Sec. 4 reports
@@ -154,11 +167,15 @@ int droplet_init(const droplet_config* cfgs, int n_droplets, void* cuda_stream, 
  * while profiling, the kernels are launched one by one instead).  Returns when
  * the steps have finished (one stream synchronisation per call).
  * DROPLET_ERR_NOT_CONVERGED is returned when a linear solve of any droplet
- * reached its cap (the state is still advanced). */
+ * reached its cap, DROPLET_ERR_TIMEOUT (which takes precedence) when a
+ * grid-barrier wait of a persistent solve ran out (wait_limit); in both cases
+ * the state is still advanced and the context stays usable. */
 int droplet_step(droplet_ctx* ctx, int n_steps);
 
 /* Copy the diagnostics of droplet `droplet` into the caller-owned *out
- * (synchronises the stream).  Clears the accumulated flags. */
+ * (synchronises the stream).  Clears the accumulated flags.  Returns
+ * DROPLET_ERR_NONFINITE (with *out filled) when a diagnostic is not finite or
+ * DROPLET_FLAG_NONFINITE is set: a NaN or infinity in a state field. */
 int droplet_diag(droplet_ctx* ctx, int droplet, droplet_diag_t* out);
 
 /* Number of doubles of field `field_id` (cells, or faces for velocities). */
@@ -302,6 +319,15 @@ int droplet_round_f32(const double* in, float* out32, double* back64, size_t n);
  * on the current device and synchronises.  Errors: DROPLET_ERR_ARG (a NULL array or
  * n > 2^30), DROPLET_ERR_NOMEM, DROPLET_ERR_CUDA. */
 int droplet_rcp_f64(const double* in, double* out, size_t n);
+
+/* Measured binary64 fused multiply-add throughput of the current device in TFLOP/s
+ * (an FMA counts two operations): eight independent FMA chains per thread on every
+ * SM, the best of five timed launches after a warm-up, CUDA events on the legacy
+ * default stream.  No counterpart in the paper: it gives the FP64-bound stencil
+ * kernels a measured roof (on GB300 the binary64 pipe retires about two FMAs per SM
+ * per clock).  Synchronises the device.  Errors: DROPLET_ERR_ARG (NULL),
+ * DROPLET_ERR_NOMEM, DROPLET_ERR_CUDA. */
+int droplet_fp64_rate(double* tflops);
 
 /* Block until all work enqueued by the context has finished. */
 int droplet_sync(droplet_ctx* ctx);

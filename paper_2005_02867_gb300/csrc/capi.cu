@@ -64,11 +64,20 @@ struct dctx {
 
 static const char* kErr[] = {"ok", "invalid argument", "CUDA error", "linear solve not converged",
                              "non-finite value", "buffer size mismatch", "device allocation failed",
-                             "checkpoint file error"};
+                             "checkpoint file error", "device wait timed out"};
 
 extern "C" const char* droplet_strerror(int s) {
-  if (s > 0 || s < -7) return "unknown status";
+  if (s > 0 || s < -8) return "unknown status";
   return kErr[-s];
+}
+
+// A solve that reached its cap (NOT_CONVERGED) or whose grid-barrier wait ran out
+// (TIMEOUT) leaves the step running: the mark goes to *nc (1 = not converged, 2 = timed
+// out, the larger kept) and 0 is returned; any other error is returned as it is.
+static int soft_status(int rc, int* nc) {
+  if (rc == DROPLET_ERR_NOT_CONVERGED) { if (*nc < 1) *nc = 1; return 0; }
+  if (rc == DROPLET_ERR_TIMEOUT) { *nc = 2; return 0; }
+  return rc;
 }
 
 static int check_cfg(const droplet_config& c) {
@@ -88,6 +97,7 @@ static int check_cfg(const droplet_config& c) {
   if (c.precision != 0 && c.precision != 1) return DROPLET_ERR_ARG;
   for (int a = 0; a < 2; ++a)
     if (c.mg_tile[a] != 0 && (c.mg_tile[a] < 8 || c.mg_tile[a] > 256)) return DROPLET_ERR_ARG;
+  if (c.wait_limit < 0 || (c.solver_select != 0 && c.solver_select != 1)) return DROPLET_ERR_ARG;
   long long nn = (long long)c.n[0] * c.n[1] * (c.geom == 0 ? 1 : c.n[2]);
   {   // 32-bit cell and face indices: the cells plus the largest extra face plane
     const long long n2 = c.geom == 0 ? 1 : c.n[2];
@@ -197,7 +207,7 @@ static int run_diag(dctx* c, int step_end) {
   Geo& g = c->g;
   int nb = red_grid_cap(g.N, c->rb);
   L_diag(c->st, nb, g, c->alpha, c->T, c->mdot, c->omega, c->rhoG, c->u[0], c->u[1], c->u[2] ? c->u[2] : c->u[0],
-                                c->psum, c->pmax);
+                                c->psum, c->pmax, c->flags);
   ++g_launches, k_diag_finish<<<1, TPB, 0, c->st>>>(c->psum, c->pmax, nb, c->scal, step_end);
   CKR(cudaGetLastError());
   return 0;
@@ -254,6 +264,8 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
   // SM budget so that the cooperative solves of all branches fit the GPU together)
   c->solver.persistent = N <= Solver::PERSIST_MAX_CELLS;
   c->solver.persist_pcg = N <= (c->solver.f32_helm ? Solver::PERSIST_PCG_MAX_CELLS : Solver::PERSIST_MAX_CELLS);
+  if (cfg.solver_select == 1) c->solver.persistent = c->solver.persist_pcg = false;   // launched solvers at any size
+  if (cfg.wait_limit > 0) c->solver.spin_limit = cfg.wait_limit;
   // the velocity components are solved together (one persistent launch)
   const bool joint = c->solver.persist_pcg && (cfg.physics_mask & DROPLET_PHYS_FLOW);
   c->solver.nsys_extra = joint ? nact(c->g) - 1 : 0;
@@ -282,6 +294,7 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
     m.f32_helm = c->solver.f32_helm;
     m.persistent = false;
     m.persist_pcg = true;
+    m.spin_limit = c->solver.spin_limit;
     m.nsys_extra = na - 1;
     m.rb = c->rb;
     if ((rc = m.setup(N, c->stm))) { free_all(c); delete c; return rc; }
@@ -418,12 +431,12 @@ static int one_step(dctx* c, int* nc_flag) {
         recs[cc] = RecordSpec{c->scal, SC_ITS_U, -1, cc > 0};
       }
       rc7 = sv.pcg_jacobi_multi(sys, na, c->cfg.helm_rtol, c->cfg.helm_maxit, recs, &ss7);
-      if (rc7 == DROPLET_ERR_NOT_CONVERGED) nc7 = 1; else if (rc7) return rc7;
+      if ((rc7 = soft_status(rc7, &nc7))) return rc7;
       for (int cc = 0; cc < na; ++cc) {
         cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, ms);
         L_mom_scatter(ms, lin_grid(nfaces(g, cc)), g, p, cc, sys[cc].x, c->us[cc]);
       }
-      return nc7 ? DROPLET_ERR_NOT_CONVERGED : 0;
+      return nc7 == 2 ? DROPLET_ERR_TIMEOUT : nc7 ? DROPLET_ERR_NOT_CONVERGED : 0;
     }
     BoxSys bm = bs;
     bm.x = c->bx;
@@ -442,18 +455,18 @@ static int one_step(dctx* c, int* nc_flag) {
       L_faces_to_box(ms, lin_grid(nbx), g, cc, c->u[cc], c->bx, c->hu[cc], c->scal);
       sv.record_next(c->scal, SC_ITS_U, -1, cc > 0);
       rc7 = sv.pcg_jacobi(bm, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss7);
-      if (rc7 == DROPLET_ERR_NOT_CONVERGED) nc7 = 1; else if (rc7) return rc7;
+      if ((rc7 = soft_status(rc7, &nc7))) return rc7;
       sv.record(c->scal, SC_ITS_U, -1, cc > 0);
       cudaMemcpyAsync(c->us[cc], c->u[cc], sizeof(double) * nfaces(g, cc), cudaMemcpyDeviceToDevice, ms);
       L_mom_scatter(ms, lin_grid(nfaces(g, cc)), g, p, cc, c->bx, c->us[cc]);
     }
-    return nc7 ? DROPLET_ERR_NOT_CONVERGED : 0;
+    return nc7 == 2 ? DROPLET_ERR_TIMEOUT : nc7 ? DROPLET_ERR_NOT_CONVERGED : 0;
   };
   if (c->conc && (mask & DROPLET_PHYS_FLOW)) {   // fork: S7 on its own branch
     CKR(cudaEventRecord(c->evf, st));
     CKR(cudaStreamWaitEvent(c->stm, c->evf, 0));
     rc = momentum(c->stm, c->solver_m);
-    if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
+    if ((rc = soft_status(rc, nc_flag))) return rc;
     CKR(cudaEventRecord(c->evj, c->stm));
   }
   // S5 energy
@@ -470,7 +483,7 @@ static int one_step(dctx* c, int* nc_flag) {
     ++g_launches, k_extrap<<<gc, TPB, 0, st>>>(N, c->T, c->hT, c->scal);
     c->solver.record_next(c->scal, SC_ITS_T, -1, 0);
     rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
-    if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
+    if ((rc = soft_status(rc, nc_flag))) return rc;
     c->solver.record(c->scal, SC_ITS_T, -1, 0);
     bs.x = c->bx;
   }
@@ -489,7 +502,7 @@ static int one_step(dctx* c, int* nc_flag) {
     ++g_launches, k_extrap<<<gc, TPB, 0, st>>>(N, c->omega, c->hW, c->scal);
     c->solver.record_next(c->scal, SC_ITS_W, -1, 0);
     rc = c->solver.pcg_jacobi(bs, c->cfg.helm_rtol, c->cfg.helm_maxit, &ss);
-    if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
+    if ((rc = soft_status(rc, nc_flag))) return rc;
     c->solver.record(c->scal, SC_ITS_W, -1, 0);
     bs.x = c->bx;
   } else {
@@ -502,7 +515,7 @@ static int one_step(dctx* c, int* nc_flag) {
       CKR(cudaStreamWaitEvent(st, c->evj, 0));   // join the momentum branch
     } else {
       rc = momentum(st, c->solver);
-      if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
+      if ((rc = soft_status(rc, nc_flag))) return rc;
     }
     double* us2 = c->us[2] ? c->us[2] : c->us[0];
     L_poisson_assemble(st, gc, g, p, c->mdot, c->alpha, c->rhoG_old, c->rhoG, c->u[0], c->u[1], u2,
@@ -513,7 +526,7 @@ static int one_step(dctx* c, int* nc_flag) {
     bs.x = c->dp;   // pressure increment from a zero initial guess (set by the assembly), solved in place
     c->solver.record_next(c->scal, SC_ITS_P, SC_RES_P, 0);
     rc = c->solver.pcg_mg(bs, c->cfg.cg_rtol, c->cfg.cg_maxit, c->cfg.precision == 1, &ss);
-    if (rc == DROPLET_ERR_NOT_CONVERGED) *nc_flag = 1; else if (rc) return rc;
+    if ((rc = soft_status(rc, nc_flag))) return rc;
     c->solver.record(c->scal, SC_ITS_P, SC_RES_P, 0);
     bs.x = c->bx;
     L_correct_all(st, g, p, c->us, c->dp, c->rho, c->u, c->pr);
@@ -785,9 +798,11 @@ extern "C" int droplet_step(droplet_ctx* c, int n_steps) {
   for (size_t i = 0; i < c->d.size(); ++i)
     CKR(cudaMemcpyAsync(c->hnc + i, c->d[i]->scal + SC_NC, sizeof(double), cudaMemcpyDeviceToHost, c->st));
   CKR(cudaStreamSynchronize(c->st));
-  for (size_t i = 0; i < c->d.size(); ++i)
-    if (c->hnc[i] != 0.0) nc = 1;
-  return nc ? DROPLET_ERR_NOT_CONVERGED : 0;
+  for (size_t i = 0; i < c->d.size(); ++i) {
+    if (c->hnc[i] >= 2.0) nc = 2;
+    else if (c->hnc[i] != 0.0 && nc < 1) nc = 1;
+  }
+  return nc == 2 ? DROPLET_ERR_TIMEOUT : nc ? DROPLET_ERR_NOT_CONVERGED : 0;
 }
 
 extern "C" int droplet_profile(droplet_ctx* c, int enable) {
@@ -862,7 +877,11 @@ extern "C" int droplet_diag(droplet_ctx* cc, int droplet, droplet_diag_t* out) {
   out->its_u = (int)s[SC_ITS_U];
   out->res_p = s[SC_RES_P];
   out->flags = *c->hflags;
-  if (!std::isfinite(out->V_l) || !std::isfinite(out->max_u) || !std::isfinite(out->T_s_mean)) return DROPLET_ERR_NONFINITE;
+  if (out->flags & DROPLET_FLAG_NONFINITE) return DROPLET_ERR_NONFINITE;
+  const double chk[] = {out->V_l, out->mdot_tot, out->K_norm, out->T_s_mean, out->M_vap, out->vap_out_cum,
+                        out->max_u, out->alpha_min, out->alpha_max, out->clip_mass, out->res_p};
+  for (double v : chk)
+    if (!std::isfinite(v)) return DROPLET_ERR_NONFINITE;
   return 0;
 }
 

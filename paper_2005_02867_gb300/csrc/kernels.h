@@ -113,7 +113,7 @@ void L_correct(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* us
 // the velocity correction of every direction and p_rgh += dp in one launch
 void L_correct_all(cudaStream_t st, Geo g, Phys p, double* const us[3], const double* dp, const double* rho,
                    double* const u[3], double* pr);
-void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax);
+void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax, unsigned* flags);
 
 void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x, double* uh,
                     const double* scal);
@@ -209,6 +209,7 @@ class Solver {
   // K (<= 1 + nsys_extra) independent Helmholtz systems in one persistent launch; the
   // statistics of system k go to recs[k]
   int pcg_jacobi_multi(const BoxSys* s, int K, double rtol, int maxit, const RecordSpec* recs, SolveStats* out);
+  long long spin_limit = 1LL << 22;   // polls of a persistent solve's grid-barrier wait before it gives up
   int sm_budget = 0;                // SMs the persistent solves may use (0: the whole GPU)
   int pcg_budget = 0;               // SMs the persistent Jacobi-PCG may use (0: sm_budget)
   int mg_tile[2] = {32, 32};        // tile of the persistent MG's temporal blocking (autotuned)

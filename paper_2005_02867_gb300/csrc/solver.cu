@@ -13,7 +13,9 @@
 namespace dg {
 
 // (S_ITSK: the iterations of each system of a joint persistent solve)
-enum { S_RZ = 0, S_PAP, S_RR, S_BB, S_ALPHA, S_BETA, S_ITS, S_TOL2, S_MAXIT, S_ITSK, S_COUNT = S_ITSK + 3 };
+// S_TMO: 1 when a grid-barrier wait of the last persistent solve ran out (written by the
+// last block to leave the launch)
+enum { S_RZ = 0, S_PAP, S_RR, S_BB, S_ALPHA, S_BETA, S_ITS, S_TOL2, S_MAXIT, S_ITSK, S_TMO = S_ITSK + 3, S_COUNT };
 
 // done flag values: 0 running, 1 converged, 2 stopped at the iteration cap
 
@@ -403,9 +405,9 @@ __global__ void k_mx_finish(long long N, double* x, const float* dx) {
 // every block obtains the same totals (deterministic).  One thread forms the scalars
 // and broadcasts them through shared memory: GB300 retires about two FP64 FMAs per SM
 // clock, so scalar work repeated by every thread is not free.  Waits are bounded:
-// past the limit the solve stops (done = 2) and *err is set, so a launch whose blocks
-// were not all resident cannot hang.
-constexpr long long BARRIER_SPIN_LIMIT = 1LL << 22;
+// past the limit (polls of the arrival counter; a launch argument, so that a caller can
+// shorten it) the solve stops (done = 2) and *err is set, so a launch whose blocks were
+// not all resident cannot hang; the solve then reports a timeout.
 constexpr int PTPB = 512;   // threads per block of the persistent solver
 // Boxes from this size on iterate in two passes per CG iteration (the working vectors,
 // 13 words a cell, no longer fit in the 129 MB L2)
@@ -419,7 +421,8 @@ constexpr long long PERSIST_SPLIT_CELLS = 1LL << 21;
 // returned to every thread; false when a wait ran out.  FP32 block sums use warp
 // shuffles; FP64 ones go through shared memory so that only three warps do FP64 adds.
 template <typename T, int NVM>
-__device__ __forceinline__ bool grid_sum(T (&v)[NVM], int nv, int phase, T* part_all, unsigned* bar, int* err) {
+__device__ __forceinline__ bool grid_sum(T (&v)[NVM], int nv, int phase, T* part_all, unsigned* bar, int* err,
+                                         long long spin_limit) {
   static_assert(NVM <= PTPB / 32, "one warp per value");
   __shared__ T sh[NVM][PTPB / 32];
   __shared__ int ok;
@@ -466,7 +469,7 @@ __device__ __forceinline__ bool grid_sum(T (&v)[NVM], int nv, int phase, T* part
     long long spins = 0;
     int good = 1;
     while (*cnt < target) {
-      if (++spins > BARRIER_SPIN_LIMIT) { atomicExch(err, 1); good = 0; break; }
+      if (++spins > spin_limit) { atomicExch(err, 1); good = 0; break; }
     }
     __threadfence();
     ok = good;
@@ -489,16 +492,18 @@ __device__ __forceinline__ bool grid_sum(T (&v)[NVM], int nv, int phase, T* part
 }
 
 template <typename T>
-__device__ __forceinline__ bool grid_sum3(T (&v)[3], int nv, int phase, T* part_all, unsigned* bar, int* err) {
-  return grid_sum<T, 3>(v, nv, phase, part_all, bar, err);
+__device__ __forceinline__ bool grid_sum3(T (&v)[3], int nv, int phase, T* part_all, unsigned* bar, int* err,
+                                          long long spin_limit) {
+  return grid_sum<T, 3>(v, nv, phase, part_all, bar, err, spin_limit);
 }
 
 
 // End of a persistent solve: statistics (block 0), then the last block to leave
-// returns the barrier counters to zero for the next launch (no block can still be
-// waiting on them once every block has counted itself out).
+// records whether any wait ran out (stat[S_TMO]; scal_nc[SC_NC] = 2, the step's timeout
+// mark, when scal_nc is given) and returns the barrier counters to zero for the next
+// launch (no block can still be waiting on them once every block has counted itself out).
 __device__ __forceinline__ void persist_finish(double* stat, int* done, const RecordSpec& rec, int its, double rr,
-                                               double bb, int result, unsigned* bar, int* err) {
+                                               double bb, int result, unsigned* bar, int* err, double* scal_nc) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     stat[S_ITS] = (double)its;
     stat[S_RR] = rr;
@@ -517,6 +522,10 @@ __device__ __forceinline__ void persist_finish(double* stat, int* done, const Re
     __threadfence();
     const unsigned e = atomicAdd(bar + 1, 1u);
     if (e == gridDim.x - 1) {
+      __threadfence();
+      const int timed_out = atomicAdd(err, 0) != 0;
+      stat[S_TMO] = timed_out ? 1.0 : 0.0;
+      if (timed_out && scal_nc) scal_nc[SC_NC] = 2.0;
       atomicExch(bar, 0u);
       atomicExch(bar + 1, 0u);
       atomicExch(err, 0);
@@ -556,6 +565,7 @@ struct PersistMulti {
   int* done;
   unsigned* bar;            // [0] arrivals, [1] departures (zero at launch)
   int* err;
+  long long spin;           // polls of a grid-barrier wait before it gives up
 };
 
 template <typename T>
@@ -592,7 +602,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
         q64[2 * k + 1] += r0 * r0;
       }
     }
-    const bool ok = grid_sum<double, 2 * PMAXSYS>(q64, 2 * K, phase++, M.part64, M.bar, M.err);
+    const bool ok = grid_sum<double, 2 * PMAXSYS>(q64, 2 * K, phase++, M.part64, M.bar, M.err, M.spin);
     if (threadIdx.x == 0) {
       s_any = 0;
 #pragma unroll
@@ -681,7 +691,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
       v[3 * k + 1] = dl;
       v[3 * k + 2] = q;
     }
-    bool ok = grid_sum<T, 3 * PMAXSYS>(v, 3 * K, phase++, M.part, M.bar, M.err);
+    bool ok = grid_sum<T, 3 * PMAXSYS>(v, 3 * K, phase++, M.part, M.bar, M.err, M.spin);
     if (threadIdx.x == 0) {
 #pragma unroll
       for (int k = 0; k < PMAXSYS; ++k) {
@@ -732,7 +742,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
           v[3 * k] = g;
           v[3 * k + 2] = q;
         }
-        okA = grid_sum<T, 3 * PMAXSYS>(v, 0, phase++, M.part, M.bar, M.err);
+        okA = grid_sum<T, 3 * PMAXSYS>(v, 0, phase++, M.part, M.bar, M.err, M.spin);
 #pragma unroll
         for (int k = 0; k < PMAXSYS; ++k) {
           if (k >= K) break;
@@ -811,7 +821,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
           v[3 * k + 2] = q;
         }
       }
-      ok = grid_sum<T, 3 * PMAXSYS>(v, 3 * K, phase++, M.part, M.bar, M.err) && okA;
+      ok = grid_sum<T, 3 * PMAXSYS>(v, 3 * K, phase++, M.part, M.bar, M.err, M.spin) && okA;
       if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < PMAXSYS; ++k) {
@@ -863,7 +873,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
     }
   }
   const RecordSpec none{nullptr, 0, -1, 0};
-  persist_finish(M.stat, M.done, none, itmax, rrs, bbs, all ? 1 : 2, M.bar, M.err);
+  persist_finish(M.stat, M.done, none, itmax, rrs, bbs, all ? 1 : 2, M.bar, M.err, M.s[0].rec.scal);
 }
 
 
@@ -1619,6 +1629,7 @@ struct MgArgs {
   int* done;
   unsigned* bar;
   int* err;
+  long long spin;              // polls of a grid-barrier wait before it gives up
 };
 
 // Phase A on a 2D level 0: the CG update (x, p of the tile's cells; r and q of the
@@ -1693,7 +1704,7 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
   const long long N = a.A.N;
   const int maxit = a.maxit, lt = a.lt;
   int phase = 0, its = 0, result = 2, cur = 0;
-  auto sync = [&](double (&v)[3], int nv) { return grid_sum3<double>(v, nv, phase++, a.part, a.bar, a.err); };
+  auto sync = [&](double (&v)[3], int nv) { return grid_sum3<double>(v, nv, phase++, a.part, a.bar, a.err, a.spin); };
   // phase H0: r0 = b - A x0 in FP64, |b|^2 and |r0|^2; the level-0 operator in the
   // hierarchy precision and its 1 / diag
   double h[3] = {0.0, 0.0, 0.0};
@@ -1872,7 +1883,7 @@ __global__ void __launch_bounds__(PTPB, 1) k_mgpcg_persist(MgArgs<T> a) {
     __syncthreads();
     ++its;
   }
-  persist_finish(a.stat, a.done, a.rec, its, rr_last, bb, result, a.bar, a.err);
+  persist_finish(a.stat, a.done, a.rec, its, rr_last, bb, result, a.bar, a.err, a.rec.scal);
 }
 
 template <typename TO, typename TI>
@@ -2010,6 +2021,12 @@ static int poll(double* hsc, const double* sc, const int* done, cudaStream_t st,
   return d != 0 || (int)hsc[S_ITS] >= maxit;
 }
 
+// status of a persistent solve after poll(): a wait that ran out before not converging
+static int persist_status(const double* hsc, int conv) {
+  if (hsc[S_TMO] != 0.0) return DROPLET_ERR_TIMEOUT;
+  return conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
+}
+
 static void fill_stats(const double* hsc, int conv, SolveStats* out) {
   if (!out) return;
   out->its = (int)hsc[S_ITS];
@@ -2111,6 +2128,7 @@ int Solver::pcg_persist(const BoxSys* sys, int K, double rtol, int maxit, const 
   M.done = done;
   M.bar = bar;
   M.err = err;
+  M.spin = spin_limit;
   M.split = nmax >= PERSIST_SPLIT_CELLS;
   int grid = (int)((nmax + PTPB - 1) / PTPB);
   int cap = persist_blocks(f32);
@@ -2146,7 +2164,7 @@ int Solver::pcg_persist(const BoxSys* sys, int K, double rtol, int maxit, const 
   if (prof && prof->on)
     for (int k = 0; k < K; ++k) prof->bytes[KC_PCG_PERSIST] += hsc[S_ITSK + k] * iter_b[k];
   fill_stats(hsc, conv, out);
-  return conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
+  return persist_status(hsc, conv);
 }
 
 int Solver::pcg_jacobi_multi(const BoxSys* s, int K, double rtol, int maxit, const RecordSpec* recs,
@@ -2492,6 +2510,7 @@ int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* 
   a.done = done;
   a.bar = bar;
   a.err = err;
+  a.spin = spin_limit;
   a.tx = (mg_tile[0] + 1) & ~1;   // even: the fused restriction's aggregates stay in a tile
   a.ty = (mg_tile[1] + 1) & ~1;
   PmgLayout pl = pmg_layout(a.TL.total, sizeof(T), a.tx, a.ty, a.dn);
@@ -2546,7 +2565,7 @@ int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* 
     prof->flops[KC_MG_SMOOTH] += hsc[S_ITS] * iter_f;
   }
   fill_stats(hsc, conv, out);
-  return conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
+  return persist_status(hsc, conv);
 }
 
 int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats* out) {

@@ -926,12 +926,18 @@ __global__ void k_add(long long n, double* y, const double* x) {
 // ============================================================== S11 diagnostics
 // sums: alpha V, mdot V, T |grad alpha| V, |grad alpha| V, (1-alpha) rhoG omega V, open-boundary vapour outflow
 // maxima: |u|, alpha, -alpha
+// Every value read is also tested for NaN / infinity (all exponent bits set, on the
+// integer pipe); one is enough to set DROPLET_FLAG_NONFINITE (the max reductions drop NaN).
+__device__ __forceinline__ unsigned nonfinite_bits(double x) {
+  return (unsigned)((__double_as_longlong(x) & 0x7FF0000000000000LL) == 0x7FF0000000000000LL);
+}
 template <int NA>
 __global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, const double* T, const double* mdot, const double* omega,
                        const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum,
-                       double* pmax) {
+                       double* pmax, unsigned* flags) {
   double s[6] = {0, 0, 0, 0, 0, 0};
   double mx[3] = {0.0, -1e300, -1e300};
+  unsigned bad = 0u;
   constexpr int na = NA;
   const double* U[3] = {u0, u1, u2};
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += (long long)gridDim.x * blockDim.x) {
@@ -939,6 +945,8 @@ __global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, con
     decomp(id, g.n[0], g.n[1], i, j, k);
     double V = cellV(g, i);
     double a = alpha[id];
+    bad |= nonfinite_bits(a) | nonfinite_bits(T[id]) | nonfinite_bits(omega[id]) | nonfinite_bits(rhoG[id]) |
+           nonfinite_bits(mdot[id]);
     double gr[3];
     s[0] += a * V;
     const double md = mdot[id];
@@ -954,11 +962,15 @@ __global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, con
     int ci[3] = {i, j, k};
     #pragma unroll
     for (int q = 0; q < na; ++q) {
-      mx[0] = imax64(mx[0], fabs(U[q][fidx(g, q, i, j, k)]));
+      const double uq = U[q][fidx(g, q, i, j, k)];
+      bad |= nonfinite_bits(uq);
+      mx[0] = imax64(mx[0], fabs(uq));
       if (ci[q] == g.n[q] - 1) {
         int hi[3] = {i, j, k};
         hi[q] += 1;
-        mx[0] = imax64(mx[0], fabs(U[q][fidx(g, q, hi[0], hi[1], hi[2])]));
+        const double uh = U[q][fidx(g, q, hi[0], hi[1], hi[2])];
+        bad |= nonfinite_bits(uh);
+        mx[0] = imax64(mx[0], fabs(uh));
       }
       #pragma unroll
       for (int side = 0; side < 2; ++side) {
@@ -973,6 +985,7 @@ __global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, con
       }
     }
   }
+  if (__syncthreads_or((int)bad) && threadIdx.x == 0) atomicOr(flags, (unsigned)DROPLET_FLAG_NONFINITE);
   block_sum_store<6>(s, psum);
   __syncthreads();
   block_max_store<3>(mx, pmax);
@@ -1086,10 +1099,10 @@ void L_correct_all(cudaStream_t st, Geo g, Phys p, double* const us[3], const do
   k_correct_all<<<b + lin_grid(g.N), TPB, 0, st>>>(g, p, a);
 }
 
-void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax) {
+void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax, unsigned* flags) {
   ++g_launches;
-  if (nact(g) == 3) k_diag<3><<<grid, TPB, 0, st>>>(g, alpha, T, mdot, omega, rhoG, u0, u1, u2, psum, pmax);
-  else k_diag<2><<<grid, TPB, 0, st>>>(g, alpha, T, mdot, omega, rhoG, u0, u1, u2, psum, pmax);
+  if (nact(g) == 3) k_diag<3><<<grid, TPB, 0, st>>>(g, alpha, T, mdot, omega, rhoG, u0, u1, u2, psum, pmax, flags);
+  else k_diag<2><<<grid, TPB, 0, st>>>(g, alpha, T, mdot, omega, rhoG, u0, u1, u2, psum, pmax, flags);
 }
 
 void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x, double* uh,

@@ -34,7 +34,7 @@ class DropletConfig(ctypes.Structure):
         ("cg_rtol", _c_dbl), ("cg_maxit", _c_int), ("helm_rtol", _c_dbl), ("helm_maxit", _c_int),
         ("seed", ctypes.c_ulonglong), ("T_perturb", _c_dbl),
         ("const_props_check", _c_int), ("physics_mask", _c_int), ("C_alpha", _c_dbl),
-        ("mg_tile", _c_int * 2),
+        ("mg_tile", _c_int * 2), ("wait_limit", _c_int), ("solver_select", _c_int),
     ]
 
 
@@ -54,7 +54,7 @@ FIELDS = dict(alpha=0, T=1, omega=2, p=3, rhoG=4, u0=5, u1=6, u2=7, mdot=8, mraw
 EXPORTS = ["droplet_init", "droplet_step", "droplet_diag", "droplet_field_size", "droplet_get_field",
            "droplet_set_field", "droplet_sync", "droplet_free", "droplet_strerror", "droplet_profile",
            "droplet_profile_read", "droplet_launch_count", "droplet_box_solve", "droplet_box_solve_noalloc", "droplet_save", "droplet_load", "droplet_adjoint",
-           "droplet_round_f32", "droplet_rcp_f64"]
+           "droplet_round_f32", "droplet_rcp_f64", "droplet_fp64_rate"]
 
 NOALLOC_MAX_UNKNOWNS = 262144
 
@@ -63,6 +63,10 @@ KCLASS = dict(mg_smooth=0, spmv=1, update=2, mg_restrict=3, mg_prolong=4, mom_as
               pcg_persist=7)
 
 ERR_NOT_CONVERGED = -3
+ERR_NONFINITE = -4
+ERR_TIMEOUT = -8
+FLAG_ADJ_NOT_FOUND = 8
+FLAG_NONFINITE = 32
 
 _lib = None
 
@@ -102,6 +106,7 @@ def load_library(path=LIBPATH):
     lib.droplet_adjoint.argtypes = [P, _c_int, _c_int, D, D, D, D, ctypes.c_size_t]
     lib.droplet_round_f32.argtypes = [P, P, P, ctypes.c_size_t]
     lib.droplet_rcp_f64.argtypes = [P, P, ctypes.c_size_t]
+    lib.droplet_fp64_rate.argtypes = [ctypes.POINTER(_c_dbl)]
     lib.droplet_save.argtypes = [P, ctypes.c_char_p]
     lib.droplet_load.argtypes = [P, ctypes.c_char_p]
     lib.droplet_strerror.argtypes = [_c_int]
@@ -152,7 +157,7 @@ def droplet_init(cfg, stream=None):
 
 def droplet_step(h, n_steps=1):
     rc = load_library().droplet_step(ctypes.c_void_p(h), int(n_steps))
-    if rc and rc != ERR_NOT_CONVERGED:
+    if rc and rc not in (ERR_NOT_CONVERGED, ERR_TIMEOUT):   # the state advanced: status returned
         raise DropletError(rc, "droplet_step")
     return rc
 
@@ -310,6 +315,15 @@ def droplet_adjoint(h, n_steps, ckpt_every, gradients=True):
     if rc and rc != ERR_NOT_CONVERGED:
         raise DropletError(rc, "droplet_adjoint")
     return J.value, gTa.value, gDg.value, gT0
+
+
+def droplet_fp64_rate():
+    """Measured binary64 FMA throughput of the current device [TFLOP/s]."""
+    v = _c_dbl()
+    rc = load_library().droplet_fp64_rate(ctypes.byref(v))
+    if rc:
+        raise DropletError(rc, "droplet_fp64_rate")
+    return v.value
 
 
 def droplet_sync(h):

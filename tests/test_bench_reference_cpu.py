@@ -41,3 +41,17 @@ def test_reference_arm_other_ranks_silent():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_reference_arm_default_3d_workload_samples_a_downscale():
+    """The default workload (3D 256^3, plain FP64) is beyond the oracle's direct
+    solves: each reference step is one oracle step of the same case on 20^3 cells,
+    the value counts those cells, and the line says so."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "3"]
+    r = subprocess.run(cmd, cwd=ROOT, env=dict(os.environ, RANK="0"), capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.strip()][-1])
+    assert d["config"]["workload"] == "cfg3_cart3d_256_fp64" and d["config"]["cells"] == 256 ** 3
+    assert d["dtype"] == "f64"
+    assert abs(d["value"] - 20 ** 3 / (d["ms_per_step"] * 1e-3) / 1e6) < 1e-9 * d["value"]
+    assert "20^3" in d["cpu_baseline"]["sample"]

@@ -76,6 +76,17 @@ CASES = {
 }
 
 
+# The launched (multi-kernel) solvers that grids beyond 2^22 cells use -- the
+# multigrid-preconditioned CG with its one-block coarse tail, and the FP64 Jacobi-PCG
+# -- selected at small sizes (solver_select = 1), so that the path of the 256^3 grid
+# is held to the same element-wise parity.
+LAUNCHED = {name + "-launched": (dict(cfg, solver_select=1), pre)
+            for name, (cfg, pre) in CASES.items()
+            if name in ("axisym-natural", "axisym-gravity", "axisym-ragged-24x40", "cart3d-natural-16",
+                        "cart3d-pr-forced-16", "cart3d-ragged-12x10x14")}
+CASES.update(LAUNCHED)
+
+
 @pytest.mark.parametrize("name", list(CASES))
 def test_init_parity(D, name):
     cfg, _ = CASES[name]
@@ -113,19 +124,22 @@ def test_single_step_parity_from_identical_state(D, name):
 
 
 def test_trajectory_parity_config1(D):
-    """Config 1 (64 x 128, zero gravity, Raoult, 773 K, 1 bar, FP64): the two
-    trajectories from the same initial state after 50 steps."""
+    """Config 1 as specified (64 x 128, zero gravity, Raoult, 773 K, 1 bar, FP64,
+    dt 1e-5 s, 200 steps): the two trajectories from the same initial state, every
+    field and the diagnostics, at 1e-10 (each system solved to 1e-16 on both sides;
+    the per-step differences, 1e-12 ... 1e-15, add up along the run)."""
     cfg = W.cfg1_axisym_64x128(**PAR)
     G = Grid(cfg)
     sim = D.Droplet(cfg)
     st = O.init_state(cfg)
-    for _ in range(50):
+    for _ in range(200):
         assert sim.step(1) == 0
         st = O.step(cfg, st)
-    errs = compare_state(sim, G, st, 1e-9)
+    errs = compare_state(sim, G, st, TOL)
+    print("config 1, 200 steps:", {k: float("%.2g" % v) for k, v in errs.items()})
     d, od = sim.diag(), O.diagnostics(cfg, st)
     for k in ("V_l", "d2", "mdot_tot", "T_s_mean", "M_vap", "vap_out_cum"):
-        assert abs(d[k] - od[k]) <= 1e-9 * max(abs(od[k]), 1e-30), (k, d[k], od[k], errs)
+        assert abs(d[k] - od[k]) <= TOL * max(abs(od[k]), 1e-30), (k, d[k], od[k], errs)
     sim.close()
 
 

@@ -59,7 +59,7 @@ def test_struct_layout_matches_header(tmp_path):
 @pytest.mark.parametrize("bad", [dict(dt=0.0), dict(n=(2, 128, 1)), dict(D0=-1.0), dict(geom=5), dict(mg_tile=(4, 32)),
                                  dict(mg_tile=(32, 512)),
                                  dict(xc=(1e-3, 4e-3, 0.0)), dict(cp_v=1200.0), dict(eq_model=3),
-                                 dict(cg_maxit=0)])
+                                 dict(cg_maxit=0), dict(wait_limit=-1), dict(solver_select=2)])
 def test_invalid_config_rejected_without_device(lib, bad):
     cfg = W.cfg1_axisym_64x128(**bad)
     c = D.make_config(cfg)
@@ -73,3 +73,11 @@ def test_null_arguments(lib):
     assert lib.droplet_step(None, 1) == -1
     assert lib.droplet_sync(None) == -1
     lib.droplet_free(None)
+
+
+def test_status_names(lib):
+    names = {rc: lib.droplet_strerror(rc).decode() for rc in range(-9, 1)}
+    assert names[-3] == "linear solve not converged"
+    assert names[-4] == "non-finite value"
+    assert names[-8] == "device wait timed out"
+    assert names[-9] == "unknown status"
