@@ -111,6 +111,13 @@ typedef struct droplet_config {
                            launched multi-kernel ones beyond; 1 = the launched solvers at
                            every size (the path of the largest grids, e.g. for checking it
                            on small ones).  The answers agree to the solver tolerance. */
+  double co_max;        /* threshold Courant number of the time step (Sec. 3.1: the step is
+                           computed from a Courant threshold; the paper gives no value).
+                           0 = the fixed step dt.  > 0: each step takes
+                           dt^{n+1} = min(dt, co_max h_min / max|u^{n+1}|, 1.2 dt^n) over
+                           every face velocity, the configured dt the upper bound, the first
+                           step min(dt, co_max h_min / max|u^0|); the clock (diag t) is the
+                           sum of the steps taken.  Not available with droplet_adjoint. */
 } droplet_config;
 
 /* Diagnostics of one droplet after the last completed step (Sec. 4 reports
@@ -235,7 +242,8 @@ int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0,
 /* Kernel classes timed by droplet_profile (algorithmic bytes per launch in brackets,
  * w = word size of the launch, d = 2 or 3 active axes, N = unknowns of the launch):
  *   0 MG_SMOOTH   red-black Gauss-Seidel half sweep    [(2.5 + d) N w; FP64: (4d + 1) N/2 flops]
- *   1 SPMV        CG operator application + dot        [(3 + d) N w; FP64: (6d + 3) N flops]
+ *   1 SPMV        CG operator application + dot        [(3 + d) N w; FP64: (4d + 3) N flops,
+ *                                                        the diagonal form a_P x_P - sum c x_N]
  *   2 UPDATE      CG x/r update + dot                  [5 N 8 or 8 N 4; FP64: 9 N (Jacobi), 6 N flops]
  *   3 MG_RESTRICT residual + restriction               [(3 + d) N w + N/2^d w; FP64: (6d + 3) N flops]
  *   4 MG_PROLONG  injection prolongation               [(2 + 1/2^d) N w; FP64: N flops]

@@ -42,12 +42,24 @@ struct ProfScope {
 
 // indices of the per-droplet device scalar array
 enum {
-  SC_K = 0, SC_CLIP, SC_VAPOUT, SC_DT,
+  SC_K = 0, SC_CLIP, SC_VAPOUT, SC_DT, SC_IDT, SC_TIME,
   SC_SUM_ALPHA_V, SC_SUM_MDOT_V, SC_SUM_TG, SC_SUM_G, SC_SUM_VAP, SC_MAXU, SC_AMAX, SC_AMIN,
   SC_ITS_P, SC_ITS_T, SC_ITS_W, SC_ITS_U, SC_RES_P, SC_NC,
   SC_HIST,   // 1: the history fields hold the previous step's T, omega, u (extrapolated guesses)
   SC_COUNT
 };
+
+static_assert(SC_IDT == SC_DT + 1 && SC_TIME == SC_DT + 2, "the clock scalars are set together");
+
+// dt and 1 / dt of the current step: the device scalars of a Courant-adaptive run (set by
+// the diagnostics at the end of the previous step), else the configured constants
+__device__ __forceinline__ double dt_of(const Phys& p) { return p.dyn ? p.dyn[SC_DT] : p.dt; }
+__device__ __forceinline__ double idt_of(const Phys& p) { return p.dyn ? p.dyn[SC_IDT] : p.idt; }
+
+// k_diag_finish modes: a state set from outside (dt and clock kept), the end of a step
+// (clock advanced by the step's dt, the next dt from the Courant rule), an initial state
+// (the first dt from the Courant rule, clock kept)
+enum { DIAG_SET = 0, DIAG_STEP_END = 1, DIAG_INITIAL = 2 };
 
 // ---- step kernels (step_kernels.cu)
 __global__ void k_init(Geo g, Phys p, double* alpha, double* T, double* omega, double* rhoG);
@@ -92,7 +104,8 @@ __global__ void k_rhoG(Geo g, Phys p, const double* T, const double* w, double* 
 
 __global__ void k_add(long long n, double* y, const double* x);
 
-__global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal, int step_end);
+__global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal, int mode,
+                              double co_hmin, double dt_max);
 __global__ void k_extrap(long long n, double* x, double* xh, const double* scal);
 
 // launch wrappers of the kernels templated on the active axes / face direction (step_kernels.cu)
@@ -250,6 +263,7 @@ class Solver {
   void vcycle(int fp32, bool casts);
   long long cap = 0;
   double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *idg = nullptr;
+  double* adg = nullptr;        // total diagonal of the launched FP64 solves' operator (diagonal form)
   double* part = nullptr;       // reduction partials
   double* sc = nullptr;         // device scalars
   int* done = nullptr;

@@ -63,14 +63,17 @@ __device__ __forceinline__ void box_row(const int m[3], const T* D, const T* con
 }
 
 // ---------------------------------------------------------------- CG kernels
+// (adg, when given, receives the total diagonal D + sum of adjacent couplings, for the
+// diagonal form of the operator in k_spmv_dot)
 __global__ void k_pcg_init(BoxV A, const double* b, const double* x, double* r, double* z, double* p, double* idg,
-                           int jacobi, double* part) {
+                           int jacobi, double* part, double* adg = nullptr) {
   double acc[3] = {0, 0, 0};   // r.z, b.b, r.r
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < A.N; id += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     bdecomp(A.m, id, i, j, k);
     double ax, dt;
     box_row<double, double>(A.m, A.D, A.c, x, id, i, j, k, ax, dt);
+    if (adg) adg[id] = dt;
     double rr = b[id] - ax;
     r[id] = rr;
     double bb = b[id];
@@ -111,16 +114,40 @@ __global__ void k_fin_init(const double* part, int nblk, double* sc, int* done, 
   }
 }
 
-// Ap = A p and p.Ap; with a counter (cnt != null) the last block also sets alpha = rz / pAp
+// y = A x at cell id in the diagonal form a_P x_P - sum c x_N, a_P = D + sum of the
+// adjacent couplings formed once per solve: one multiply and one FMA per neighbour, against
+// a subtraction and an FMA per neighbour in the difference form (the binary64 pipe is the
+// bound of an FP64 stencil on GB300; the bytes are the same, a_P read in place of D)
+__device__ __forceinline__ double box_row_diag(const int m[3], const double* ad, const double* const c[3],
+                                               const double* x, long long id, int i, int j, int k) {
+  double y = ad[id] * x[id];
+  const int q[3] = {i, j, k};
+  const long long st[3] = {1, (long long)m[0], (long long)m[0] * m[1]};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!c[a] || m[a] < 2) continue;
+    if (q[a] > 0) y = fma(-c[a][id], x[id - st[a]], y);
+    if (q[a] < m[a] - 1) y = fma(-c[a][id + st[a]], x[id + st[a]], y);
+  }
+  return y;
+}
+
+// Ap = A p and p.Ap; with a counter (cnt != null) the last block also sets alpha = rz / pAp.
+// adg (the total diagonal from k_pcg_init) selects the diagonal form of the operator.
 __global__ void k_spmv_dot(BoxV A, const double* p, double* Ap, double* part, const int* done, double* sc,
-                           unsigned* cnt) {
+                           unsigned* cnt, const double* adg = nullptr) {
   if (*done) return;
   double acc[1] = {0.0};
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < A.N; id += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     bdecomp(A.m, id, i, j, k);
-    double ax, dt;
-    box_row<double, double, false>(A.m, A.D, A.c, p, id, i, j, k, ax, dt);
+    double ax;
+    if (adg) {
+      ax = box_row_diag(A.m, adg, A.c, p, id, i, j, k);
+    } else {
+      double dt;
+      box_row<double, double, false>(A.m, A.D, A.c, p, id, i, j, k, ax, dt);
+    }
     Ap[id] = ax;
     acc[0] += p[id] * ax;
   }
@@ -922,16 +949,23 @@ __device__ __forceinline__ void gs_cell(const LevV<T>& L, long long id, int i, i
   L.x[id] = s * L.idg[id];
 }
 
+// One half sweep of colour col over a whole level, one thread per updated cell: thread t
+// takes the (t mod h)-th cell of colour col in row t / h (h = ceil(m0 / 2)), so every lane
+// of a warp updates a cell.  (A thread per cell with half of them returning issues the
+// same binary64 warp instructions for half the work: GB300's FP64 pipe, which retires a
+// warp instruction in a fixed number of cycles however many lanes are active, was 91 %
+// busy on such a sweep while DRAM ran at 61 %.)
+template <typename T>
+__device__ __forceinline__ void grid_half_sweep(const LevV<T>& L, int col, int first, int gid, int gs);
+
 template <typename T>
 __global__ void k_mg_smooth(LevV<T> L, int col, int first, const int* done) {
   if (*done) return;
-  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (id >= L.N) return;
-  int i, j, k;
-  bdecomp(L.m, id, i, j, k);
-  if (((i + j + k) & 1) != col) return;
-  gs_cell<T>(L, id, i, j, k, first);
+  grid_half_sweep<T>(L, col, first, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
+
+// threads of a launched half sweep (one per cell of one colour, rows padded to ceil(m0 / 2))
+inline long long half_sweep_threads(const int m[3]) { return (long long)((m[0] + 1) >> 1) * m[1] * m[2]; }
 
 // inverse total diagonal of a level
 // 1 / (D + sum of adjacent couplings) of one cell, summed in FP64 over the level's values
@@ -1959,6 +1993,7 @@ int Solver::setup(long long maxN, cudaStream_t s) {
   CK(cudaMalloc(&p, b));
   CK(cudaMalloc(&Ap, b));
   CK(cudaMalloc(&idg, b));
+  CK(cudaMalloc(&adg, b));
   CK(cudaMalloc(&part, sizeof(double) * RED_BLOCKS * 8));
   CK(cudaMalloc(&sc, sizeof(double) * S_COUNT));
   CK(cudaMalloc(&done, sizeof(int)));
@@ -1985,7 +2020,8 @@ int Solver::setup(long long maxN, cudaStream_t s) {
 }
 
 void Solver::release() {
-  cudaFree(r); cudaFree(z); cudaFree(p); cudaFree(Ap); cudaFree(idg);
+  cudaFree(r); cudaFree(z); cudaFree(p); cudaFree(Ap); cudaFree(idg); cudaFree(adg);
+  adg = nullptr;
   cudaFree(part); cudaFree(sc); cudaFree(done); cudaFree(cnt); cudaFreeHost(hsc);
   {
     float** fa[] = {&fD, &fc[0], &fc[1], &fc[2], &fidg, &fr, &fz, &fp, &fAp, &fdx};
@@ -2196,12 +2232,12 @@ int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out)
   if (f32_helm) return pcg_jacobi_f32(s, rtol, maxit, out);
   BoxV A = view(s);
   int nb = red_grid_cap(s.N, rb);
-  ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 1, part);
+  ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 1, part, adg);
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, nullptr, nullptr);
   auto iteration = [&]() {
     {
-      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0, (6.0 * (s.c[2] ? 3 : 2) + 3.0) * s.N);
-      ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt);
+      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0, (4.0 * (s.c[2] ? 3 : 2) + 3.0) * s.N);
+      ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt, adg);
     }
     {
       ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0, 9.0 * s.N);
@@ -2405,7 +2441,7 @@ static void smooth(Prof* prof, LevV<T> L, int col, int first, const int* done, c
   int d = L.c[2] ? 3 : 2;
   ProfScope ps(prof, KC_MG_SMOOTH, st, (2.5 + d) * L.N * (double)sizeof(T),
                sizeof(T) == 8 ? (4.0 * d + 1.0) * 0.5 * L.N : 0.0);
-  ++g_launches, k_mg_smooth<T><<<lin_grid(L.N), TPB, 0, st>>>(L, col, first, done);
+  ++g_launches, k_mg_smooth<T><<<lin_grid(half_sweep_threads(L.m)), TPB, 0, st>>>(L, col, first, done);
 }
 
 template <typename T>
@@ -2576,7 +2612,7 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
   BoxV A = view(s);
   int nb = red_grid_cap(s.N, rb);
   int g = lin_grid(s.N);
-  ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
+  ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part, adg);
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, nullptr, nullptr);
   vcycle(fp32, true);
   ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done, sc, cnt, 1);
@@ -2585,8 +2621,8 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
   ++g_launches, k_cast_done<double, double><<<g, TPB, 0, stream>>>(s.N, p, z, done);
   auto iteration = [&]() {
     {
-      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0, (6.0 * (s.c[2] ? 3 : 2) + 3.0) * s.N);
-      ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt);
+      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0, (4.0 * (s.c[2] ? 3 : 2) + 3.0) * s.N);
+      ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt, adg);
     }
     {
       ProfScope ps(prof, KC_UPDATE, stream, (5.0 * 8.0 + (fp32 ? 4.0 : 0.0)) * s.N, 6.0 * s.N);
