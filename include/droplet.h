@@ -241,18 +241,21 @@ int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0,
 
 /* Kernel classes timed by droplet_profile (algorithmic bytes per launch in brackets,
  * w = word size of the launch, d = 2 or 3 active axes, N = unknowns of the launch):
- *   0 MG_SMOOTH   red-black Gauss-Seidel half sweep    [(2.5 + d) N w; FP64: (4d + 1) N/2 flops]
- *   1 SPMV        CG operator application + dot        [(3 + d) N w; FP64: (4d + 3) N flops,
+ *   0 MG_SMOOTH   red-black Gauss-Seidel half sweep    [(2.5 + d) N w; FP64: (2d + 1) N/2 instructions]
+ *   1 SPMV        CG operator application + dot        [(3 + d) N w; FP64: (2d + 2) N instructions,
  *                                                        the diagonal form a_P x_P - sum c x_N]
- *   2 UPDATE      CG x/r update + dot                  [5 N 8 or 8 N 4; FP64: 9 N (Jacobi), 6 N flops]
- *   3 MG_RESTRICT residual + restriction               [(3 + d) N w + N/2^d w; FP64: (6d + 3) N flops]
- *   4 MG_PROLONG  injection prolongation               [(2 + 1/2^d) N w; FP64: N flops]
+ *   2 UPDATE      CG x/r update + dot                  [5 N 8 or 8 N 4; FP64: 5 N (Jacobi), 3 N]
+ *   3 MG_RESTRICT residual + restriction               [(3 + d) N w + N/2^d w; FP64: (4d + 3) N]
+ *   4 MG_PROLONG  injection prolongation               [(2 + 1/2^d) N w; FP64: N]
  *   5 MOM_ASSEMBLE momentum system assembly            [(12 + 2d) N 8]
  *   6 SCALAR_ASSEMBLE energy / species assembly        [(12 + 2d) N 8]
  *   7 PCG_PERSIST the whole Jacobi-preconditioned CG of one to three Helmholtz
  *                 systems in one persistent launch     [setup, then (11 + d) N w per
  *                                                       iteration of each system]
- * (w = 8 for FP64 launches, 4 for FP32 ones.)
+ * (w = 8 for FP64 launches, 4 for FP32 ones.  The FP64 figures count binary64 pipe
+ * instructions the arithmetic needs, an FMA once: on GB300 that pipe, not HBM, bounds
+ * the FP64 stencils.  The assembly classes carry none: their issued counts come from
+ * counter captures.)
  * The Helmholtz systems solve with the persistent kernel of class 7 in mixed
  * precision at every size, in FP64 up to 2^22 cells.  Single droplets of at most
  * 2^22 cells, and the droplets of a batch, solve the pressure with a persistent
@@ -267,8 +270,9 @@ int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0,
 int droplet_profile(droplet_ctx* ctx, int enable);
 
 /* Totals since profiling started for one kernel class: summed event time [ms],
- * number of launches, summed algorithmic bytes and summed algorithmic FP64 flops
- * (flops64 may be NULL; launches computing in FP32 add none).  Synchronises. */
+ * number of launches, summed algorithmic bytes and summed binary64 instructions
+ * (flops64, may be NULL; the figures above, an FMA counted once; launches computing in
+ * FP32 add none).  Synchronises. */
 int droplet_profile_read(droplet_ctx* ctx, int kclass, double* ms_total, long long* launches, double* bytes_total,
                          double* flops64);
 

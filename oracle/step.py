@@ -332,6 +332,7 @@ def init_state(cfg):
         _face_slab(u[G.s], G.s, 0)[...] = cfg["u_inflow"]
     st = dict(alpha=alpha, T=T, omega=omega, p=np.zeros(G.n), u=u,
               t=0.0, step=0, vap_out_cum=0.0, clip_mass=0.0, flags=0)
+    st["dt"] = courant_dt(cfg, G, u)
     st["rhoG"] = th.rho_gas(cfg, T, omega)
     return st
 
@@ -968,11 +969,31 @@ def boundary_vapour_outflow(cfg, G, u, omega, rhoG):
     return tot
 
 
+def courant_dt(cfg, G, u, dt_prev=None):
+    """Time step from the threshold Courant number (Sec. 3.1: the step is computed
+    automatically from a Courant threshold; the paper gives neither the threshold nor
+    the growth rule, reading R29).  With co_max > 0:
+        dt = min(dt_max, co_max h_min / max|u|, 1.2 dt_prev)
+    over every face velocity u, dt_max the configured dt (no velocity limit while u = 0,
+    no growth limit for the first step); with co_max = 0 the configured dt."""
+    co = cfg.get("co_max", 0.0)
+    if not co > 0.0:
+        return cfg["dt"]
+    umax = max(float(np.max(np.abs(u[a]))) for a in G.act)
+    d = cfg["dt"]
+    if umax > 0.0:
+        d = min(d, (co * G.hmin) / umax)
+    if dt_prev is not None:
+        d = min(d, 1.2 * dt_prev)
+    return d
+
+
 def step(cfg, st, keep=False):
-    """Advance the state by one time step dt.  Returns the new state; with
-    keep=True the intermediate fields of every stage are attached under 'aux'."""
+    """Advance the state by one time step dt (the state's, from the Courant rule, or
+    the configured one).  Returns the new state; with keep=True the intermediate fields
+    of every stage are attached under 'aux'."""
     G = Grid(cfg)
-    dt = cfg["dt"]
+    dt = st.get("dt", cfg["dt"])
     mask = cfg["physics_mask"]
     const = bool(cfg["const_props_check"])
     alpha, T, omega, u = st["alpha"], st["T"], st["omega"], st["u"]
@@ -1024,6 +1045,7 @@ def step(cfg, st, keep=False):
                clip_mass=st["clip_mass"] + clip_vol,
                flags=flags, K=K, mdot=mdot, ncap=ncap, nclip=nclip)
     out["vap_out_cum"] = st["vap_out_cum"] + dt * boundary_vapour_outflow(cfg, G, u_new, omega_new, rhoG_new)
+    out["dt"] = courant_dt(cfg, G, u_new, dt)
     if keep:
         out["aux"] = dict(omega_pinned=omega, rhoG_old=rhoG_old, mraw=mraw, adj=adj, mdot=mdot,
                           alpha_star=alpha_star, alphaL=alphaL, ustar=ustar, dp=dp, S=S, psys=psys,

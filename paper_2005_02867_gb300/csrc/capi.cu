@@ -98,6 +98,7 @@ static int check_cfg(const droplet_config& c) {
   for (int a = 0; a < 2; ++a)
     if (c.mg_tile[a] != 0 && (c.mg_tile[a] < 8 || c.mg_tile[a] > 256)) return DROPLET_ERR_ARG;
   if (c.wait_limit < 0 || (c.solver_select != 0 && c.solver_select != 1)) return DROPLET_ERR_ARG;
+  if (!(c.co_max >= 0.0) || !std::isfinite(c.co_max)) return DROPLET_ERR_ARG;
   long long nn = (long long)c.n[0] * c.n[1] * (c.geom == 0 ? 1 : c.n[2]);
   {   // 32-bit cell and face indices: the cells plus the largest extra face plane
     const long long n2 = c.geom == 0 ? 1 : c.n[2];
@@ -117,6 +118,8 @@ static void make_geo(const droplet_config& c, Geo& g) {
   for (int a = 0; a < 3; ++a) g.h[a] = (a < 2 || !g.axisym) ? c.L[a] / g.n[a] : 1.0;
   for (int a = 0; a < 3; ++a) g.ih[a] = 1.0 / g.h[a];
   g.hmin = g.axisym ? fmin(g.h[0], g.h[1]) : fmin(g.h[0], fmin(g.h[1], g.h[2]));
+  g.vol3 = g.h[0] * g.h[1] * g.h[2];
+  for (int a = 0; a < 3; ++a) g.area3[a] = g.vol3 * g.ih[a];
   g.gthr = 1e-8 / g.hmin;
   g.s = g.axisym ? 1 : 2;
   int inlet = c.bc_mode == 1 ? BC_FORCED : BC_OPEN;
@@ -143,6 +146,8 @@ static void make_phys(const droplet_config& c, Phys& p) {
   p.Tc = c.Tc; p.Pc = c.Pc; p.om = c.omega_ac; p.Tc_g = c.Tc_g; p.Pc_g = c.Pc_g; p.om_g = c.omega_g; p.kij = c.kij;
   p.xi0 = c.xi0; p.Df = c.fiber_radius; p.dt = c.dt; p.C_alpha = c.C_alpha; p.T_perturb = c.T_perturb;
   p.idt = 1.0 / c.dt;
+  p.dyn = nullptr;            // set once the device scalars exist (adaptive runs)
+  p.co_hmin = 0.0;
   p.D_gas = c.D_g * (1.0e5 / c.P);
   p.rhoG_const = c.P * c.M_g / (R_GAS * c.T_amb);
   p.seed = c.seed;
@@ -201,16 +206,25 @@ static void free_all(dctx* c) {
   c->st2 = nullptr; c->own = nullptr;
 }
 
-// diagnostics of the current state; step_end: at the end of a step (the history fields
-// then hold the step's starting values), else the history is marked invalid
-static int run_diag(dctx* c, int step_end) {
+// diagnostics of the current state; mode (DIAG_*): the end of a step (the history fields
+// then hold the step's starting values; the clock advances and an adaptive run takes its
+// next dt), an initial state (an adaptive run takes its first dt), or a state set from
+// outside (history marked invalid, clock and dt kept)
+static int run_diag(dctx* c, int mode) {
   Geo& g = c->g;
   int nb = red_grid_cap(g.N, c->rb);
   L_diag(c->st, nb, g, c->alpha, c->T, c->mdot, c->omega, c->rhoG, c->u[0], c->u[1], c->u[2] ? c->u[2] : c->u[0],
                                 c->psum, c->pmax, c->flags);
-  ++g_launches, k_diag_finish<<<1, TPB, 0, c->st>>>(c->psum, c->pmax, nb, c->scal, step_end);
+  ++g_launches, k_diag_finish<<<1, TPB, 0, c->st>>>(c->psum, c->pmax, nb, c->scal, mode, c->p.co_hmin, c->cfg.dt);
   CKR(cudaGetLastError());
   return 0;
+}
+
+// The clock at t = 0 with the configured dt (the first step of an adaptive run then takes
+// its dt from the initial velocities, DIAG_INITIAL); enqueued on st.
+static void reset_clock(dctx* c, cudaStream_t st) {
+  const double v[3] = {c->cfg.dt, 1.0 / c->cfg.dt, 0.0};   // SC_DT, SC_IDT, SC_TIME
+  cudaMemcpyAsync(c->scal + SC_DT, v, sizeof(v), cudaMemcpyHostToDevice, st);
 }
 
 // One droplet's context: device memory, solver workspace and the initial state (Sec. 3.3).
@@ -327,8 +341,11 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
   }
   cudaMemsetAsync(c->hT, 0, sizeof(double) * N, st);
   cudaMemsetAsync(c->hW, 0, sizeof(double) * N, st);
-  double dtv = c->cfg.dt;
-  cudaMemcpyAsync(c->scal + SC_DT, &dtv, sizeof(double), cudaMemcpyHostToDevice, st);
+  reset_clock(c, st);
+  if (cfg.co_max > 0.0) {
+    c->p.dyn = c->scal;
+    c->p.co_hmin = cfg.co_max * g.hmin;
+  }
   ++g_launches, k_init<<<gc, TPB, 0, st>>>(g, c->p, c->alpha, c->T, c->omega, c->rhoG);
   ++g_launches, k_xi<<<gc, TPB, 0, st>>>(g, c->p, c->xi);
   if (g.bc[g.s][0] == BC_FORCED) {
@@ -341,7 +358,7 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
     cudaStreamSynchronize(st);
     free(hv);
   }
-  if ((rc = run_diag(c, 0))) { free_all(c); delete c; return rc; }
+  if ((rc = run_diag(c, DIAG_INITIAL))) { free_all(c); delete c; return rc; }
   if (cudaStreamSynchronize(st) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_CUDA; }
   *out = c;
   return 0;
@@ -535,7 +552,7 @@ static int one_step(dctx* c, int* nc_flag) {
     cudaMemsetAsync(c->S, 0, sizeof(double) * N, st);
   }
   // S11
-  if ((rc = run_diag(c, 1))) return rc;
+  if ((rc = run_diag(c, DIAG_STEP_END))) return rc;
   CKR(cudaGetLastError());
   return 0;
 }
@@ -653,8 +670,7 @@ static int autotune(droplet_ctx* c) {
         cudaMemcpyAsync(fs[f], snap[i][f], sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st);
       }
       cudaMemsetAsync(x->scal, 0, sizeof(double) * SC_COUNT, c->st);
-      double dtv = x->cfg.dt;
-      cudaMemcpyAsync(x->scal + SC_DT, &dtv, sizeof(double), cudaMemcpyHostToDevice, c->st);
+      reset_clock(x, c->st);
       cudaMemsetAsync(x->flags, 0, sizeof(unsigned), c->st);
       cudaMemsetAsync(x->dirty, 0xff, sizeof(int), c->st);
     }
@@ -698,7 +714,7 @@ static int autotune(droplet_ctx* c) {
   cudaEventDestroy(e1);
   if (rc) return rc;
   if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
-  for (auto x : c->d) if (run_diag(x, 0)) return DROPLET_ERR_CUDA;
+  for (auto x : c->d) if (run_diag(x, DIAG_INITIAL)) return DROPLET_ERR_CUDA;
   CKR(cudaStreamSynchronize(c->st));
   return 0;
 }
@@ -781,7 +797,6 @@ extern "C" int droplet_step(droplet_ctx* c, int n_steps) {
       for (auto x : c->d) {
         int rc = one_step(x, &nc);
         if (rc) return rc;
-        x->t += x->p.dt;
         x->step += 1;
       }
     for (auto x : c->d) if (x->st != c->st) CKR(cudaStreamSynchronize(x->st));
@@ -792,7 +807,7 @@ extern "C" int droplet_step(droplet_ctx* c, int n_steps) {
     }
     for (int s = 0; s < n_steps; ++s) {
       CKR(cudaGraphLaunch(c->exec, c->st));
-      for (auto x : c->d) { x->t += x->p.dt; x->step += 1; }
+      for (auto x : c->d) x->step += 1;
     }
   }
   for (size_t i = 0; i < c->d.size(); ++i)
@@ -858,7 +873,7 @@ extern "C" int droplet_diag(droplet_ctx* cc, int droplet, droplet_diag_t* out) {
   const double* s = c->hscal;
   double w = c->g.axisym ? 2.0 * M_PI : 1.0;
   memset(out, 0, sizeof(*out));
-  out->t = c->t;
+  out->t = s[SC_TIME];
   out->step = c->step;
   out->V_l = w * s[SC_SUM_ALPHA_V];
   out->d_eq = cbrt(6.0 * out->V_l / M_PI);
@@ -962,7 +977,7 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
   dctx* x = cc->d[0];
   const droplet_config& cf = x->cfg;
   if (cf.physics_mask != (DROPLET_PHYS_EVAP | DROPLET_PHYS_ENERGY | DROPLET_PHYS_SPECIES) || cf.precision != 0 ||
-      cf.eq_model != 0 || cf.const_props_check != 0 || cf.bc_mode != 0 || x->step != 0)
+      cf.eq_model != 0 || cf.const_props_check != 0 || cf.bc_mode != 0 || cf.co_max != 0.0 || x->step != 0)
     return DROPLET_ERR_ARG;
   Geo& g = x->g;
   Phys& p = x->p;
@@ -1091,14 +1106,17 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
   load_state(fin);
   CKR(cudaStreamSynchronize(st));
   cleanup();
-  x->t = n_steps * p.dt;
+  {
+    const double tn = n_steps * p.dt;   // the clock the forward and recomputed steps advanced
+    CKR(cudaMemcpy(x->scal + SC_TIME, &tn, sizeof(double), cudaMemcpyHostToDevice));
+  }
   x->step = n_steps;
   if (rc) return rc;
   return nc ? DROPLET_ERR_NOT_CONVERGED : 0;
 }
 
 // ---------------------------------------------------------------- checkpoint / resume
-static const char kMagic[8] = {'D', 'R', 'O', 'P', 'C', 'K', 'P', '2'};
+static const char kMagic[8] = {'D', 'R', 'O', 'P', 'C', 'K', 'P', '3'};
 
 // the checkpointed fields: the state, then the history of the extrapolated guesses
 constexpr int NCKPT = 13;
@@ -1125,7 +1143,7 @@ extern "C" int droplet_save(droplet_ctx* c, const char* path) {
     if (!ok) break;
     CKR(cudaStreamSynchronize(x->st));
     CKR(cudaMemcpy(x->hscal, x->scal, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost));
-    ok = fwrite(&x->cfg, sizeof(droplet_config), 1, fp) == 1 && fwrite(&x->t, sizeof(double), 1, fp) == 1 &&
+    ok = fwrite(&x->cfg, sizeof(droplet_config), 1, fp) == 1 && fwrite(&x->hscal[SC_TIME], sizeof(double), 1, fp) == 1 &&
          fwrite(&x->step, sizeof(long long), 1, fp) == 1 && fwrite(x->hscal, sizeof(double), SC_COUNT, fp) == SC_COUNT;
     double* f[NCKPT];
     long long n[NCKPT];
@@ -1169,7 +1187,7 @@ extern "C" int droplet_load(droplet_ctx* c, const char* path) {
       if (cudaMemcpy(f[q], host.data(), sizeof(double) * n[q], cudaMemcpyHostToDevice) != cudaSuccess) { fclose(fp); return DROPLET_ERR_CUDA; }
     }
     if (cudaMemcpy(x->scal, x->hscal, sizeof(double) * SC_COUNT, cudaMemcpyHostToDevice) != cudaSuccess) { fclose(fp); return DROPLET_ERR_CUDA; }
-    x->t = t;
+    (void)t;   // the clock is restored with the device scalars
     x->step = step;
     // the saved rho_G is rho_gas(T, omega) of the saved state: S0 may reuse it
     if (cudaMemset(x->dirty, 0, sizeof(int)) != cudaSuccess) { fclose(fp); return DROPLET_ERR_CUDA; }

@@ -32,6 +32,8 @@ struct Geo {
   double ih[3];      // 1 / h
   double hmin;
   double gthr;       // 1e-8 / h_min: |grad alpha| above it marks an interface cell
+  double vol3;       // 3D: cell volume h0 h1 h2, and face areas vol3 / h_a, formed on the host in
+  double area3[3];   // the order the kernels used (the same values, no FP64 work per reference)
   long long N;       // number of cells (< 2^31)
 };
 
@@ -54,6 +56,10 @@ struct Phys {
   double iM_l, iM_g;
   // Clausius-Clapeyron exponent L M_l / R and 1 / T_b; 1 / rho_l
   double cc_LMR, iTb, irho_l;
+  // Courant-adaptive step: the droplet's device scalars, where the step's dt and 1 / dt
+  // are kept (null: the fixed dt, idt above); co_hmin = threshold Courant number x h_min
+  const double* dyn;
+  double co_hmin;
 };
 
 __host__ __device__ inline int nact(const Geo& g) { return g.act3 ? 3 : 2; }
@@ -83,18 +89,18 @@ __device__ __forceinline__ void decomp(long long id, int n0, int n1, int& i, int
 
 __device__ __forceinline__ double rc(const Geo& g, int i) { return (i + 0.5) * g.h[0]; }
 __device__ __forceinline__ double cellV(const Geo& g, int i) {
-  return g.axisym ? rc(g, i) * g.h[0] * g.h[1] : g.h[0] * g.h[1] * g.h[2];
+  return g.axisym ? rc(g, i) * g.h[0] * g.h[1] : g.vol3;
 }
 // area of the face of direction a whose low-side cell index along 0 is i
 // (for a = 0, i is the face index)
 __device__ __forceinline__ double faceA(const Geo& g, int a, int i) {
   if (g.axisym) return a == 0 ? (i * g.h[0]) * g.h[1] : rc(g, i) * g.h[0];
-  return g.h[0] * g.h[1] * g.h[2] * g.ih[a];
+  return g.area3[a];
 }
 // area of a face normal to a located at radial coordinate rl (control volumes of the momentum)
 __device__ __forceinline__ double areaN(const Geo& g, int a, double rl) {
   if (g.axisym) return rl * (a == 0 ? g.h[1] : g.h[0]);
-  return g.h[0] * g.h[1] * g.h[2] * g.ih[a];
+  return g.area3[a];
 }
 
 // ------------------------------------------------------------------ ghosts
@@ -246,13 +252,21 @@ __device__ __forceinline__ double iclamp01(double a) { return imin64(1.0, imax64
 __device__ __forceinline__ bool ige64(double a, double b) { return ord64(a) >= ord64(b); }
 
 // ------------------------------------------------------------------ small formulas
+// minmod(x, y): the operand of smaller magnitude when x and y are non-zero with the same
+// sign, else 0 -- decided on the integer pipe (sign bits equal, magnitudes compared as
+// unsigned encodings), with no binary64 instruction.  The same operand as the form
+// x y > 0 ? sign(x) min(|x|, |y|) : 0 for every pair whose product does not underflow
+// below the smallest subnormal (there the product test gives 0).
 __device__ __forceinline__ double minmod(double x, double y) {
-  return (x * y > 0.0) ? (x > 0.0 ? fmin(fabs(x), fabs(y)) : -fmin(fabs(x), fabs(y))) : 0.0;
+  const long long bx = __double_as_longlong(x), by = __double_as_longlong(y);
+  const long long ax = bx & 0x7FFFFFFFFFFFFFFFLL, ay = by & 0x7FFFFFFFFFFFFFFFLL;
+  const bool same = (bx ^ by) >= 0 && ax != 0 && ay != 0;
+  return same ? (ax <= ay ? x : y) : 0.0;
 }
 __device__ __forceinline__ double lim_up(double uu, double u, double d) { return u + 0.5 * minmod(u - uu, d - u); }
 __device__ __forceinline__ double van_leer(double uu, double u, double d) {
   double dU = u - uu, dD = d - u, pr = dU * dD;
-  return u + (pr > 0.0 ? pr / (dU + dD) : 0.0);
+  return u + (pr > 0.0 ? pr * rcp64(dU + dD) : 0.0);
 }
 
 // ------------------------------------------------------------------ thermodynamics

@@ -2236,11 +2236,11 @@ int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out)
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, nullptr, nullptr);
   auto iteration = [&]() {
     {
-      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0, (4.0 * (s.c[2] ? 3 : 2) + 3.0) * s.N);
+      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0, (2.0 * (s.c[2] ? 3 : 2) + 2.0) * s.N);
       ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt, adg);
     }
     {
-      ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0, 9.0 * s.N);
+      ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0, 5.0 * s.N);
       ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 1, sc, part, done, cnt);
     }
     ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
@@ -2440,7 +2440,7 @@ template <typename T>
 static void smooth(Prof* prof, LevV<T> L, int col, int first, const int* done, cudaStream_t st) {
   int d = L.c[2] ? 3 : 2;
   ProfScope ps(prof, KC_MG_SMOOTH, st, (2.5 + d) * L.N * (double)sizeof(T),
-               sizeof(T) == 8 ? (4.0 * d + 1.0) * 0.5 * L.N : 0.0);
+               sizeof(T) == 8 ? (2.0 * d + 1.0) * 0.5 * L.N : 0.0);
   ++g_launches, k_mg_smooth<T><<<lin_grid(half_sweep_threads(L.m)), TPB, 0, st>>>(L, col, first, done);
 }
 
@@ -2461,7 +2461,7 @@ static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaSt
     {
       int d = L.c[2] ? 3 : 2;
       ProfScope ps(prof, KC_MG_RESTRICT, st, ((3.0 + d) * L.N + C.N) * (double)sizeof(T),
-                   sizeof(T) == 8 ? (6.0 * d + 3.0) * L.N : 0.0);
+                   sizeof(T) == 8 ? (4.0 * d + 3.0) * L.N : 0.0);
       ++g_launches, k_mg_restrict<T><<<lin_grid(C.N), TPB, 0, st>>>(L, C, done);
     }
   }
@@ -2576,11 +2576,11 @@ int Solver::pcg_mg_persist(const BoxSys& s, double rtol, int maxit, SolveStats* 
   // algorithmic bytes per iteration: level-0 FP64 vectors (update: x, r, p, q, w in,
   // x, r, p, q out; w = A z: operator in, w out), the level-0 b and z in the hierarchy
   // precision, each grid level's operator, b and x once per smoothing side and the
-  // transfers, and the tail; FP64 flops: the update and w = A z, plus the sweeps of an
-  // FP64 hierarchy
+  // transfers, and the tail; binary64 instructions: the CG update (four FMAs, three dot
+  // products) and w = A z (difference form), plus the sweeps of an FP64 hierarchy
   const double d = s.c[2] ? 3.0 : 2.0, es = (double)sizeof(T), N0 = (double)s.N;
   double iter_b = (9.0 * 8.0 + 3.0 * es) * N0 + ((1.0 + d) * 8.0 + 16.0 + es) * N0;
-  double iter_f = (10.0 + 4.0 * d) * N0;
+  double iter_f = (8.0 + 4.0 * d) * N0;
   for (int l = 0; l < lt; ++l) {
     const double Nl = (double)lev[l].N, Nc = (double)lev[l + 1].N;
     iter_b += 2.0 * (3.0 + d) * Nl * es + ((3.0 + d) * Nl + Nc) * es + (2.0 * Nl + Nc) * es;
@@ -2625,7 +2625,7 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
       ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt, adg);
     }
     {
-      ProfScope ps(prof, KC_UPDATE, stream, (5.0 * 8.0 + (fp32 ? 4.0 : 0.0)) * s.N, 6.0 * s.N);
+      ProfScope ps(prof, KC_UPDATE, stream, (5.0 * 8.0 + (fp32 ? 4.0 : 0.0)) * s.N, 3.0 * s.N);
       ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 0, sc, part, done, cnt, bf);
     }
     vcycle(fp32, false);

@@ -265,9 +265,9 @@ __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double*
   if ((__double_as_longlong(mr) << 1) != 0) {      // mraw != 0, tested on the integer pipe
     const double K = scal[SC_K];
     m = (K == 0.0) ? 0.0 : K * sqrt(a * (1.0 - a)) * mr;
-    const double cap = p.rho_l * a * p.idt;
+    const double cap = p.rho_l * a * idt_of(p);
     if (m > cap) { m = cap; atomicOr(flags, (unsigned)DROPLET_FLAG_MDOT_CAPPED); }
-    as = a - p.dt * m * p.irho_l;
+    as = a - dt_of(p) * m * p.irho_l;
   }
   mdot[id] = m;
   alpha_star[id] = as;
@@ -289,7 +289,7 @@ __global__ void k_adv_faces(Geo g, Phys p, const double* as, const double* ua, d
   decomp(id, m0, m1, f[0], f[1], f[2]);
   int L[3] = {f[0], f[1], f[2]}, R[3] = {f[0], f[1], f[2]};
   L[a] -= 1;
-  double phi = ua[id] * faceA(g, a, f[0]) * p.dt;
+  double phi = ua[id] * faceA(g, a, f[0]) * dt_of(p);
   double aL = cellg(g, as, L[0], L[1], L[2], R_ALPHA, 0, 0, 0, 0);
   double aR = cellg(g, as, R[0], R[1], R[2], R_ALPHA, 0, 0, 0, 0);
   bool pos = phi >= 0.0;
@@ -485,7 +485,7 @@ __global__ void k_alpha_clip_only(Geo g, Phys p, const double* as, double* alpha
 __device__ __forceinline__ double gam(int mode, const double* kc, const double* rho, const double* D, long long q) {
   return mode == 0 ? kc[q] : rho[q] * D[q];
 }
-__device__ __forceinline__ double harm(double x, double y) { return 2.0 * x * y / (x + y); }
+__device__ __forceinline__ double harm(double x, double y) { return 2.0 * x * y * rcp64(x + y); }
 
 template <int NA>
 __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
@@ -501,8 +501,8 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
   double* C[3] = {c0, c1, c2};
   double V = cellV(g, i);
   double coef = mode == 0 ? rho[id] * cp[id] : rho[id];
-  double dP = coef * V * p.idt;
-  double r = coef * V * phi[id] * p.idt + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
+  double dP = coef * V * idt_of(p);
+  double r = coef * V * phi[id] * idt_of(p) + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
   double net = 0.0, Fsum = 0.0;
   double gP = gam(mode, kc, rho, D, id);
   bool pin = (mode == 1) && ige64(alpha_new[id], 0.5);
@@ -582,7 +582,7 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
   r -= coef * (net - phi[id] * Fsum);
   if (pin) {
     // pinned row, scaled like the other rows: (coef V/dt) x = (coef V/dt) Y_eq
-    double dd = coef * V * p.idt;
+    double dd = coef * V * idt_of(p);
     r = dd * pinv[id];
     dP = dd;
   }
@@ -654,12 +654,12 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
     r_f = (c == 0) ? f[0] * g.h[0] : (f[0] + 0.5) * g.h[0];
     V_f = r_f * g.h[0] * g.h[1];
   } else {
-    V_f = g.h[0] * g.h[1] * g.h[2];
+    V_f = g.vol3;
   }
   double A_f = V_f * g.ih[c];
   double u_f = uc[fidx(g, c, f[0], f[1], f[2])];
-  double d = rho_f * V_f * p.idt;
-  double r = rho_f * V_f * u_f * p.idt;
+  double d = rho_f * V_f * idt_of(p);
+  double r = rho_f * V_f * u_f * idt_of(p);
   double t_adv = 0.0, t_vT = 0.0, d_visc = 0.0;
   #pragma unroll
   for (int a = 0; a < na; ++a) {
@@ -832,7 +832,7 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
     adv = adv + vc * gr;
   }
   double rn = rgn[id], irn = rcp64(rn);
-  double s = mdot[id] * (irn - p.irho_l) - (1.0 - alpha[id]) * irn * ((rn - rgo[id]) * p.idt + adv);
+  double s = mdot[id] * (irn - p.irho_l) - (1.0 - alpha[id]) * irn * ((rn - rgo[id]) * idt_of(p) + adv);
   S[id] = s;
   double dg = 0.0, div = 0.0;
   double rP = rho[id];
@@ -853,7 +853,7 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
     if (ci[a] == g.n[a] - 1 && g.bc[a][1] == BC_OPEN) dg += faceA(g, a, hi[0]) * (2.0 * g.ih[a]) / rP;
   }
   Dg[id] = dg;
-  rhs[id] = (s * cellV(g, i) - div) * p.idt;
+  rhs[id] = (s * cellV(g, i) - div) * idt_of(p);
 }
 
 // u = u* - dt beta_f (dp_R - dp_L)/A_f with dp = 0 beyond open faces (half-cell distance);
@@ -872,13 +872,13 @@ __device__ __forceinline__ void correct_face(const Geo& g, const Phys& p, const 
     L[c] -= 1;
     if (f[c] > 0 && f[c] < g.n[c]) {
       long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, f[0], f[1], f[2]);
-      corr = p.dt * g.ih[c] * (2.0 * rcp64(rho[li] + rho[ri])) * (dp[ri] - dp[li]);
+      corr = dt_of(p) * g.ih[c] * (2.0 * rcp64(rho[li] + rho[ri])) * (dp[ri] - dp[li]);
     } else {
       int side = f[c] == 0 ? 0 : 1;
       if ((side ? g.bc[c][1] : g.bc[c][0]) == BC_OPEN) {
         long long pi = side ? cidx(g, L[0], L[1], L[2]) : cidx(g, f[0], f[1], f[2]);
         const double bA = (2.0 * g.ih[c]) * rcp64(rho[pi]);
-        corr = side ? p.dt * bA * (0.0 - dp[pi]) : p.dt * bA * (dp[pi] - 0.0);
+        corr = side ? dt_of(p) * bA * (0.0 - dp[pi]) : dt_of(p) * bA * (dp[pi] - 0.0);
       }
     }
   }
@@ -991,9 +991,13 @@ __global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, con
   block_max_store<3>(mx, pmax);
 }
 
-// (step_end: the end of a step, whose solves have filled the history fields; 0 after
-// a state that did not come from a step)
-__global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal, int step_end) {
+// mode (DIAG_*): DIAG_STEP_END after a step, whose solves have filled the history fields
+// and whose dt advances the clock; then, and for an initial state, a Courant-adaptive run
+// (co_hmin = threshold Courant number x h_min > 0) takes its next dt from the face
+// velocities just reduced: min(dt_max, co_hmin / max|u|, 1.2 dt) (the growth limit not for
+// the first step).
+__global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal, int mode,
+                              double co_hmin, double dt_max) {
   double v[6], m[3];
   block_reduce_partials<6, false>(psum, nblk, v);
   block_reduce_partials<3, true>(pmax, nblk, m);
@@ -1007,7 +1011,16 @@ __global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, 
     scal[SC_MAXU] = m[0];
     scal[SC_AMAX] = m[1];
     scal[SC_AMIN] = -m[2];
-    scal[SC_HIST] = step_end ? 1.0 : 0.0;
+    scal[SC_HIST] = mode == DIAG_STEP_END ? 1.0 : 0.0;
+    const double dt = scal[SC_DT];
+    if (mode == DIAG_STEP_END) scal[SC_TIME] += dt;
+    if (co_hmin > 0.0 && mode != DIAG_SET) {
+      double d = dt_max;
+      if (m[0] > 0.0) d = fmin(d, co_hmin / m[0]);
+      if (mode == DIAG_STEP_END) d = fmin(d, 1.2 * dt);
+      scal[SC_DT] = d;
+      scal[SC_IDT] = 1.0 / d;
+    }
   }
 }
 

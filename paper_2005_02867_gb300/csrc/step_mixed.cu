@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
     V_f = g.h[0] * g.h[1] * g.h[2];
   }
   const double u_f = uc[fidx(g, c, f[0], f[1], f[2])];
-  const double d0 = rho_f * V_f * p.idt;
+  const double d0 = rho_f * V_f * idt_of(p);
   // the increments, FP32
   const float rho_ff = f32_rn(rho_f), V_ff = f32_rn(V_f), r_ff = f32_rn(r_f);
   const float A_ff = V_ff * q.ih[c];
@@ -272,8 +272,8 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
   // the state terms, FP64 (storage c V / dt and its phi term, the phase-change source)
   const double V = cellV(g, i);
   const double coef = mode == 0 ? rho[id] * cp[id] : rho[id];
-  double dP = coef * V * p.idt;
-  double r = coef * V * phi[id] * p.idt + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
+  double dP = coef * V * idt_of(p);
+  double r = coef * V * phi[id] * idt_of(p) + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
   const bool pin = (mode == 1) && ige64(alpha_new[id], 0.5);
   // the increments, FP32
   const float phiP = phif[id], ambf = f32_rn(amb);
@@ -370,7 +370,7 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
   dP += f64_of(dinc);
   if (pin) {
     // pinned row, scaled like the other rows: (coef V/dt) x = (coef V/dt) Y_eq
-    double dd = coef * V * p.idt;
+    double dd = coef * V * idt_of(p);
     r = dd * pinv[id];
     dP = dd;
   }
@@ -418,7 +418,7 @@ __device__ __forceinline__ void adv_face_mx(const Geo& g, const Phys& p, const d
   decomp(id, m0, m1, f[0], f[1], f[2]);
   int L[3] = {f[0], f[1], f[2]}, R[3] = {f[0], f[1], f[2]};
   L[a] -= 1;
-  const double phi = ua[id] * faceA(g, a, f[0]) * p.dt;
+  const double phi = ua[id] * faceA(g, a, f[0]) * dt_of(p);
   const double aL = cellg(g, as, L[0], L[1], L[2], R_ALPHA, 0, 0, 0, 0);
   const double aR = cellg(g, as, R[0], R[1], R[2], R_ALPHA, 0, 0, 0, 0);
   const bool pos = phi >= 0.0;

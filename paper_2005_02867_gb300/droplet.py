@@ -34,7 +34,7 @@ class DropletConfig(ctypes.Structure):
         ("cg_rtol", _c_dbl), ("cg_maxit", _c_int), ("helm_rtol", _c_dbl), ("helm_maxit", _c_int),
         ("seed", ctypes.c_ulonglong), ("T_perturb", _c_dbl),
         ("const_props_check", _c_int), ("physics_mask", _c_int), ("C_alpha", _c_dbl),
-        ("mg_tile", _c_int * 2), ("wait_limit", _c_int), ("solver_select", _c_int),
+        ("mg_tile", _c_int * 2), ("wait_limit", _c_int), ("solver_select", _c_int), ("co_max", _c_dbl),
     ]
 
 
@@ -220,7 +220,7 @@ def droplet_profile(h, enable):
 
 
 def droplet_profile_read(h, kclass):
-    """(ms_total, launches, algorithmic_bytes_total, algorithmic_fp64_flops_total) of a kernel
+    """(ms_total, launches, algorithmic_bytes_total, binary64_instructions_total) of a kernel
     class since droplet_profile(h, 1)."""
     ms, n, b, f = _c_dbl(), ctypes.c_longlong(), _c_dbl(), _c_dbl()
     k = KCLASS[kclass] if isinstance(kclass, str) else int(kclass)

@@ -143,6 +143,25 @@ def test_trajectory_parity_config1(D):
     sim.close()
 
 
+@pytest.mark.parametrize("solver_select", [0, 1])
+def test_courant_adaptive_step_parity(D, solver_select):
+    """Courant-adaptive time step (co_max > 0): the device forms each next dt from the
+    face velocities it has just reduced, with the oracle's rule and operations, so the
+    clocks agree step by step to the velocities' rounding differences and the fields to
+    1e-10 after eight steps in which the Courant limit binds."""
+    cfg = W.cfg5_axisym_128x256(**SMALL, dt=4e-5, co_max=0.01, solver_select=solver_select, **PAR)
+    G = Grid(cfg)
+    sim = D.Droplet(cfg)
+    st = O.init_state(cfg)
+    for _ in range(8):
+        assert sim.step(1) == 0
+        st = O.step(cfg, st)
+        assert sim.diag()["t"] == pytest.approx(st["t"], rel=1e-12, abs=0.0)
+    assert st["dt"] < cfg["dt"]                  # the limit binds
+    compare_state(sim, G, st, TOL)
+    sim.close()
+
+
 def test_mixed_precision_matches_fp64(D):
     """FP32 multigrid preconditioner inside the FP64 CG: same discrete answer."""
     cfg64 = W.cfg5_axisym_128x256(**SMALL, cg_rtol=1e-12, helm_rtol=1e-12)

@@ -360,3 +360,39 @@ def test_d2_law_and_total_mass_after_transient():
     assert 0.85 <= res[128]["rate"] / K <= 1.31
     ex = {n: r["mass"] - 1.0 for n, r in res.items()}
     assert ex[64] < 0.75 * ex[32] and ex[128] < 0.75 * ex[64], ex
+
+
+def test_courant_adaptive_time_step():
+    """Sec. 3.1: the time step follows a threshold Courant number (reading R29).
+    Along a run with buoyancy-driven flow every step obeys the threshold, never grows
+    by more than 20 %, stays below the configured maximum, and the clock is the sum of
+    the steps taken; the Courant limit binds once the flow has grown."""
+    co = 0.01      # the flow reaches ~0.033 m/s: the limit binds near 1.9e-5 s
+    cfg = W.cfg5_axisym_128x256(n=(32, 64, 1), L=(2e-3, 4e-3, 0.0), xc=(0.0, 2e-3, 0.0), dt=4e-5, co_max=co)
+    G = Grid(cfg)
+    st = O.init_state(cfg)
+    assert st["dt"] == cfg["dt"]                    # u = 0: no velocity limit
+    dts, bound = [], 0
+    for _ in range(25):
+        dt = st["dt"]
+        st = O.step(cfg, st)
+        dts.append(dt)
+        umax = max(float(np.abs(st["u"][a]).max()) for a in G.act)
+        nxt = st["dt"]
+        assert 0.0 < nxt <= cfg["dt"] and nxt <= 1.2 * dt * (1 + 1e-15)
+        assert nxt * umax / G.hmin <= co * (1 + 1e-12)
+        bound += nxt < min(cfg["dt"], 1.2 * dt)
+    assert st["t"] == pytest.approx(sum(dts), rel=1e-14)
+    assert bound > 0
+
+
+def test_courant_step_reduces_to_fixed_step():
+    """With a threshold that never binds the adaptive run is the fixed-step run, bit for bit."""
+    base = W.cfg5_axisym_128x256(n=(24, 40, 1), L=(1.5e-3, 2.5e-3, 0.0), xc=(0.0, 1.25e-3, 0.0), D0=0.8e-3)
+    a, b = O.init_state(base), O.init_state(dict(base, co_max=1e6))
+    for _ in range(3):
+        a = O.step(base, a)
+        b = O.step(dict(base, co_max=1e6), b)
+        assert b["dt"] == base["dt"]
+    for nm in ("alpha", "T", "omega", "p"):
+        assert np.array_equal(a[nm], b[nm]), nm
