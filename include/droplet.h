@@ -118,6 +118,11 @@ typedef struct droplet_config {
                            every face velocity, the configured dt the upper bound, the first
                            step min(dt, co_max h_min / max|u^0|); the clock (diag t) is the
                            sum of the steps taken.  Not available with droplet_adjoint. */
+  int    adv_scheme;    /* interface advection (Eq. advection): 0 = upwind + compressive flux
+                           with a Zalesak limiter (C_alpha); 1 = geometric, the paper's
+                           kind (Sec. 2.1): a plane per partly filled cell (Youngs normal),
+                           one sweep per axis passing the liquid of each donor's swept slab,
+                           volume-conserving whatever div u; FP64 in both precisions */
 } droplet_config;
 
 /* Diagnostics of one droplet after the last completed step (Sec. 4 reports

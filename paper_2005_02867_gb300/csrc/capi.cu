@@ -99,6 +99,7 @@ static int check_cfg(const droplet_config& c) {
     if (c.mg_tile[a] != 0 && (c.mg_tile[a] < 8 || c.mg_tile[a] > 256)) return DROPLET_ERR_ARG;
   if (c.wait_limit < 0 || (c.solver_select != 0 && c.solver_select != 1)) return DROPLET_ERR_ARG;
   if (!(c.co_max >= 0.0) || !std::isfinite(c.co_max)) return DROPLET_ERR_ARG;
+  if (c.adv_scheme != 0 && c.adv_scheme != 1) return DROPLET_ERR_ARG;
   long long nn = (long long)c.n[0] * c.n[1] * (c.geom == 0 ? 1 : c.n[2]);
   {   // 32-bit cell and face indices: the cells plus the largest extra face plane
     const long long n2 = c.geom == 0 ? 1 : c.n[2];
@@ -393,7 +394,13 @@ static int one_step(dctx* c, int* nc_flag) {
                                                    c->dirty);
   // S3, and S4 (the mixture properties) in the kernel that forms alpha^{n+1}
   const PropsOut po{c->rhoG_old, c->omega, c->T, c->rho, c->mu, c->kc, c->cp, c->Dm, c->s32};
-  if (mask & DROPLET_PHYS_FLOW) {
+  if ((mask & DROPLET_PHYS_FLOW) && c->cfg.adv_scheme == 1) {
+    // geometric advection, FP64 in both precisions: the planes in FL (normal) and AF[0]
+    // (constant), the sweeps' intermediate alpha in aL and Rp
+    double* const w[2] = {c->aL, c->Rp};
+    double* const Nn[3] = {c->FL[0], c->FL[1], na == 3 ? c->FL[2] : nullptr};
+    L_geo_advect(st, nb, g, p, c->astar, w, Nn, c->AF[0], c->u, c->alpha, c->part, po);
+  } else if (mask & DROPLET_PHYS_FLOW) {
     if (c->cfg.precision == 1) {
       L_adv_faces_mx_all(st, g, p, c->astar, c->astar_f, c->u, c->FL, c->AF);
     } else {

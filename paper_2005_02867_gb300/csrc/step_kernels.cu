@@ -454,6 +454,253 @@ __global__ void k_adv_update(Geo g, Phys p, const double* aL, const double* A0, 
   block_sum_store<2>(acc, partials);
 }
 
+// ============================================================== S3, geometric (reading R30)
+// The paper moves the interface geometrically (Sec. 2.1, Eq. advection, isoAdvector).  On
+// the uniform grid: one sweep per axis; in each, every partly filled cell holds a plane
+// (PLIC) and a face passes the liquid of its donor's swept slab.  Geometry of a plane in
+// the unit box [0, 1]^d, liquid side n . xi <= beta, normal in box coordinates (component a
+// times h_a): the clipped volume by inclusion-exclusion over the box corners, arranged so
+// that a vanishing component is only ever divided into a bounded ratio.
+
+// fraction of the unit square below m1 x + m2 y = a (m1 <= m2, m1 + m2 = 1, 0 <= a <= 1/2)
+__device__ __forceinline__ double geo_frac2(double m1, double m2, double a) {
+  if (a <= m1) return m1 > 0.0 ? (a / m1) * a / (2.0 * m2) : 0.0;
+  return (2.0 * a - m1) / (2.0 * m2);
+}
+
+// fraction of the unit cube below m . x = a (m1 <= m2 <= m3, sum 1, 0 <= a <= 1/2):
+// 6 m1 m2 m3 V = a^3 - sum_i (a - m_i)_+^3, each corner term (a - m_i)^3 / m1 taken as
+// (t / m1) t^2 with t <= m1; the slab beyond a = m1 + m2 when m3 >= m1 + m2 is linear
+__device__ __forceinline__ double geo_frac3(double m1, double m2, double m3, double a) {
+  if (a <= m1) return m1 > 0.0 ? (a / m1) * a * a / (6.0 * m2 * m3) : 0.0;
+  if (a <= m2) return (a * a - a * m1 + m1 * m1 / 3.0) / (2.0 * m2 * m3);
+  const double m12 = m1 + m2;
+  if (m12 <= m3 && a > m12) return (2.0 * a - m12) / (2.0 * m3);
+  const double t2 = fmax(a - m2, 0.0), t3 = fmax(a - m3, 0.0);
+  const double r2 = m1 > 0.0 ? t2 / m1 : 0.0, r3 = m1 > 0.0 ? t3 / m1 : 0.0;
+  return (3.0 * a * a - 3.0 * a * m1 + m1 * m1 - r2 * t2 * t2 - r3 * t3 * t3) / (6.0 * m2 * m3);
+}
+
+// |n| sorted ascending and scaled to unit sum; s = sum |n| (0: no plane)
+__device__ __forceinline__ void geo_sorted(int d, double n0, double n1, double n2, double m[3], double& s) {
+  double x = fabs(n0), y = fabs(n1), z = d == 3 ? fabs(n2) : 0.0;
+  s = d == 3 ? (x + y) + z : x + y;
+  const double ss = s > 0.0 ? s : 1.0;
+  x = x / ss;
+  y = y / ss;
+  z = z / ss;
+  if (d == 2) {
+    m[0] = fmin(x, y);
+    m[1] = fmax(x, y);
+    m[2] = 0.0;
+    return;
+  }
+  // three-element sorting network
+  double t;
+  if (x > y) { t = x; x = y; y = t; }
+  if (y > z) { t = y; y = z; z = t; }
+  if (x > y) { t = x; x = y; y = t; }
+  m[0] = x;
+  m[1] = y;
+  m[2] = z;
+}
+
+// fraction of the unit box on the side n . xi <= beta
+__device__ double geo_cut_fraction(int d, double n0, double n1, double n2, double beta) {
+  const double neg = d == 3 ? (fmin(n0, 0.0) + fmin(n1, 0.0)) + fmin(n2, 0.0) : fmin(n0, 0.0) + fmin(n1, 0.0);
+  beta -= neg;                          // reflect the axes with negative components
+  double m[3], s;
+  geo_sorted(d, n0, n1, n2, m, s);
+  if (!(s > 0.0)) return beta >= 0.0 ? 1.0 : 0.0;
+  const double a = beta / s;
+  if (a <= 0.0) return 0.0;
+  if (a >= 1.0) return 1.0;
+  const bool hi = a > 0.5;
+  const double b = fmin(fmax(hi ? 1.0 - a : a, 0.0), 0.5);
+  const double v = d == 2 ? geo_frac2(m[0], m[1], b) : geo_frac3(m[0], m[1], m[2], b);
+  return hi ? 1.0 - v : v;
+}
+
+// the plane constant beta that cuts the fraction f (0 < f < 1) from the unit box: closed
+// forms on the square-root, cube-root, quadratic and linear pieces, bisection on the cubic
+// pieces (60 halvings); 0 for a zero normal
+__device__ double geo_plane_constant(int d, double n0, double n1, double n2, double f) {
+  double m[3], s;
+  geo_sorted(d, n0, n1, n2, m, s);
+  if (!(s > 0.0)) return 0.0;
+  const bool hi = f > 0.5;
+  const double gv = hi ? 1.0 - f : f;
+  const double m1 = m[0], m2 = m[1];
+  double a;
+  if (d == 2) {
+    const double g1 = m1 > 0.0 ? m1 / (2.0 * m2) : 0.0;
+    a = gv <= g1 ? sqrt(2.0 * m1 * m2 * gv) : gv * m2 + 0.5 * m1;
+  } else {
+    const double m3 = m[2], m12 = m1 + m2;
+    if (gv <= geo_frac3(m1, m2, m3, m1)) {
+      a = cbrt(6.0 * m1 * m2 * m3 * gv);
+    } else if (gv <= geo_frac3(m1, m2, m3, m2)) {
+      a = 0.5 * (m1 + sqrt(fmax(8.0 * m2 * m3 * gv - m1 * m1 / 3.0, 0.0)));
+    } else if (m12 <= m3 && gv >= geo_frac3(m1, m2, m3, m12)) {
+      a = gv * m3 + 0.5 * m12;
+    } else {
+      double lo = m2, up = m12 <= m3 ? m12 : 0.5;
+      for (int it = 0; it < 60; ++it) {
+        const double mid = 0.5 * (lo + up);
+        if (geo_frac3(m1, m2, m3, mid) < gv) lo = mid;
+        else up = mid;
+      }
+      a = 0.5 * (lo + up);
+    }
+  }
+  if (hi) a = 1.0 - a;
+  const double neg = d == 3 ? (fmin(n0, 0.0) + fmin(n1, 0.0)) + fmin(n2, 0.0) : fmin(n0, 0.0) + fmin(n1, 0.0);
+  return a * s + neg;
+}
+
+// alpha of cell (i, j, k) for the reconstruction, clamped into [0, 1]: across the axis the
+// mirror image, beyond every other boundary (and at a corner beyond two) 0
+__device__ __forceinline__ double geo_alpha(const Geo& g, const double* a, int i, int j, int k) {
+  const bool oi = i < 0 || i >= g.n[0], oj = j < 0 || j >= g.n[1], ok = k < 0 || k >= g.n[2];
+  if (!oi && !oj && !ok) return iclamp01(a[cidx(g, i, j, k)]);
+  if (oi && !oj && !ok && i == -1 && g.bc[0][0] == BC_AXIS) return iclamp01(a[cidx(g, 0, j, k)]);
+  return 0.0;
+}
+
+// Plane of every partly filled cell of the sweep's input: Youngs' normal (minus the
+// gradient, each difference along an axis summed over the neighbouring rows with weights
+// (1, 2, 1) per other axis; box coordinates) and the constant that cuts the cell's alpha.
+template <int NA>
+__global__ void k_geo_plane(Geo g, const double* a, double* N0, double* N1, double* N2, double* B) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  int i, j, k;
+  decomp(id, g.n[0], g.n[1], i, j, k);
+  const double ac = iclamp01(a[id]);
+  double n[3] = {0.0, 0.0, 0.0}, beta = 0.0;
+  if (ac > 0.0 && ac < 1.0) {
+    constexpr double w[3] = {1.0, 2.0, 1.0};
+    #pragma unroll
+    for (int ax = 0; ax < NA; ++ax) {
+      double acc = 0.0;
+      const int o1 = ax == 0 ? 1 : 0, o2 = NA == 3 ? (ax == 2 ? 1 : 2) : -1;
+      #pragma unroll
+      for (int ib = 0; ib < 3; ++ib) {
+        #pragma unroll
+        for (int ic = 0; ic < (NA == 3 ? 3 : 1); ++ic) {
+          int p[3] = {i, j, k}, q[3] = {i, j, k};
+          p[ax] += 1;
+          q[ax] -= 1;
+          p[o1] += ib - 1;
+          q[o1] += ib - 1;
+          if (NA == 3) {
+            p[o2] += ic - 1;
+            q[o2] += ic - 1;
+          }
+          const double wt = NA == 3 ? w[ib] * w[ic] : w[ib];
+          acc += wt * (geo_alpha(g, a, p[0], p[1], p[2]) - geo_alpha(g, a, q[0], q[1], q[2]));
+        }
+      }
+      n[ax] = -acc;
+    }
+    beta = geo_plane_constant(NA, n[0], n[1], n[2], ac);
+  }
+  N0[id] = n[0];
+  N1[id] = n[1];
+  if (NA == 3) N2[id] = n[2];
+  B[id] = beta;
+}
+
+// Liquid passed in the sweep by the face of direction K at face coordinates f: phi_f =
+// u_f A_f dt times the fraction of the donor's slab (width |u_f| dt / h) on the liquid side
+// of its plane; a full donor passes phi_f, an empty one or one outside the domain nothing,
+// one whose normal vanishes its own alpha.  Returns phi_f through *phi.
+template <int NA, int K>
+__device__ double geo_face_flux(const Geo& g, const Phys& p, const double* a, const double* N0, const double* N1,
+                                const double* N2, const double* B, const double* uk, int f0, int f1, int f2,
+                                double* phi_out) {
+  const double u = uk[fidx(g, K, f0, f1, f2)];
+  const double dt = dt_of(p);
+  const double phi = u * faceA(g, K, f0) * dt;
+  *phi_out = phi;
+  const bool pos = phi >= 0.0;
+  int d[3] = {f0, f1, f2};
+  if (pos) d[K] -= 1;
+  if (d[K] < 0 || d[K] >= g.n[K]) return 0.0;
+  const long long q = cidx(g, d[0], d[1], d[2]);
+  const double ad = iclamp01(a[q]);
+  if (ad >= 1.0) return phi;
+  if (ad <= 0.0) return 0.0;
+  double n[3] = {N0[q], N1[q], NA == 3 ? N2[q] : 0.0};
+  if (n[0] == 0.0 && n[1] == 0.0 && n[2] == 0.0) return phi * ad;
+  const double c = fmin(fabs(u) * dt / g.h[K], 1.0);
+  const double nk = n[K];
+  n[K] = c * nk;
+  const double bs = pos ? B[q] - nk * (1.0 - c) : B[q];
+  return phi * geo_cut_fraction(NA, n[0], n[1], n[2], bs);
+}
+
+// sweep K of cell (i, j, k): alpha - (F_hi - F_lo)/V + a_c (dphi_K - dphi / D)/V, a_c = 1
+// where alpha* > 1/2; the cell's mean divergence is taken out of each sweep, so the terms
+// cancel over the sweeps and the liquid volume is conserved whatever div u is
+template <int NA, int K>
+__device__ __forceinline__ double geo_sweep_cell(const Geo& g, const Phys& p, const double* a, const double* astar,
+                                                 const double* N0, const double* N1, const double* N2, const double* B,
+                                                 const double* const U[3], int i, int j, int k, long long id) {
+  double phiK_lo, phiK_hi;
+  int hi[3] = {i, j, k};
+  hi[K] += 1;
+  const double Flo = geo_face_flux<NA, K>(g, p, a, N0, N1, N2, B, U[K], i, j, k, &phiK_lo);
+  const double Fhi = geo_face_flux<NA, K>(g, p, a, N0, N1, N2, B, U[K], hi[0], hi[1], hi[2], &phiK_hi);
+  const double dt = dt_of(p);
+  double div = 0.0;
+  #pragma unroll
+  for (int ax = 0; ax < NA; ++ax) {
+    int h2[3] = {i, j, k};
+    h2[ax] += 1;
+    const double plo = U[ax][fidx(g, ax, i, j, k)] * faceA(g, ax, i) * dt;
+    const double phi2 = U[ax][fidx(g, ax, h2[0], h2[1], h2[2])] * faceA(g, ax, h2[0]) * dt;
+    div += phi2 - plo;
+  }
+  const double V = cellV(g, i);
+  const double acw = astar[id] > 0.5 ? 1.0 : 0.0;
+  return a[id] - (Fhi - Flo) / V + acw * ((phiK_hi - phiK_lo) - div / (double)NA) / V;
+}
+
+template <int NA, int K>
+__global__ void k_geo_sweep(Geo g, Phys p, const double* a, const double* astar, const double* N0, const double* N1,
+                            const double* N2, const double* B, const double* u0, const double* u1, const double* u2,
+                            double* out) {
+  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (id >= g.N) return;
+  int i, j, k;
+  decomp(id, g.n[0], g.n[1], i, j, k);
+  const double* U[3] = {u0, u1, u2};
+  out[id] = geo_sweep_cell<NA, K>(g, p, a, astar, N0, N1, N2, B, U, i, j, k, id);
+}
+
+// the last sweep: clip into [0, 1] with the clipped volume and count summed per block
+// (reading R14), mixture properties of alpha^{n+1} (S4)
+template <int NA, int K>
+__global__ void __launch_bounds__(TPB, 4) k_geo_sweep_last(Geo g, Phys p, const double* a, const double* astar,
+                                                           const double* N0, const double* N1, const double* N2,
+                                                           const double* B, const double* u0, const double* u1,
+                                                           const double* u2, double* alpha, double* partials,
+                                                           PropsOut po) {
+  double acc[2] = {0.0, 0.0};
+  const double* U[3] = {u0, u1, u2};
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < g.N; id += (long long)gridDim.x * blockDim.x) {
+    int i, j, k;
+    decomp(id, g.n[0], g.n[1], i, j, k);
+    const double an = geo_sweep_cell<NA, K>(g, p, a, astar, N0, N1, N2, B, U, i, j, k, id);
+    const double ac = iclamp01(an);
+    if (ac != an) { acc[1] += 1.0; acc[0] += (an - ac) * cellV(g, i); }
+    alpha[id] = ac;
+    props_out(p, id, ac, po);
+  }
+  block_sum_store<2>(acc, partials);
+}
+
 __global__ void k_clip_finish(const double* partials, int nblk, double* scal, unsigned* flags) {
   double v = block_sum_partials(partials, nblk);
   double c = block_sum_partials(partials + nblk, nblk);
@@ -1053,6 +1300,33 @@ void L_adv_update(cudaStream_t st, int grid, Geo g, Phys p, const double* aL, co
   ++g_launches;
   if (nact(g) == 3) k_adv_update<3><<<grid, TPB, 0, st>>>(g, p, aL, A0, A1, A2, Rp, Rm, alpha, partials, flags, po);
   else k_adv_update<2><<<grid, TPB, 0, st>>>(g, p, aL, A0, A1, A2, Rp, Rm, alpha, partials, flags, po);
+}
+
+// geometric advection (S3 with adv_scheme 1): one plane reconstruction and one sweep per
+// axis; ping-pong through w[0], w[1] (alpha after sweeps 1 and 2), the last sweep writing
+// alpha^{n+1}, its clip partials and the mixture properties
+void L_geo_advect(cudaStream_t st, int grid, Geo g, Phys p, const double* astar, double* const w[2],
+                  double* const N[3], double* B, double* const u[3], double* alpha, double* partials, PropsOut po) {
+  const int na = nact(g), gc = lin_grid(g.N);
+  const double* in = astar;
+  double* u2 = u[2] ? u[2] : u[0];
+  double* n2 = N[2] ? N[2] : N[0];
+  for (int s = 0; s < na; ++s) {
+    ++g_launches;
+    if (na == 3) k_geo_plane<3><<<gc, TPB, 0, st>>>(g, in, N[0], N[1], n2, B);
+    else k_geo_plane<2><<<gc, TPB, 0, st>>>(g, in, N[0], N[1], n2, B);
+    ++g_launches;
+    if (s < na - 1) {
+      if (na == 3 && s == 0) k_geo_sweep<3, 0><<<gc, TPB, 0, st>>>(g, p, in, astar, N[0], N[1], n2, B, u[0], u[1], u2, w[s]);
+      else if (na == 3) k_geo_sweep<3, 1><<<gc, TPB, 0, st>>>(g, p, in, astar, N[0], N[1], n2, B, u[0], u[1], u2, w[s]);
+      else k_geo_sweep<2, 0><<<gc, TPB, 0, st>>>(g, p, in, astar, N[0], N[1], n2, B, u[0], u[1], u2, w[s]);
+      in = w[s];
+    } else if (na == 3) {
+      k_geo_sweep_last<3, 2><<<grid, TPB, 0, st>>>(g, p, in, astar, N[0], N[1], n2, B, u[0], u[1], u2, alpha, partials, po);
+    } else {
+      k_geo_sweep_last<2, 1><<<grid, TPB, 0, st>>>(g, p, in, astar, N[0], N[1], n2, B, u[0], u[1], u2, alpha, partials, po);
+    }
+  }
 }
 
 void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32*) {

@@ -36,7 +36,7 @@ BASE = dict(
     cg_rtol=1e-12, cg_maxit=400, helm_rtol=1e-13, helm_maxit=400,
     seed=20050286, T_perturb=0.0,
     const_props_check=0, physics_mask=PHYS_ALL, C_alpha=1.0,
-    mg_tile=(0, 0), wait_limit=0, solver_select=0, co_max=0.0,
+    mg_tile=(0, 0), wait_limit=0, solver_select=0, co_max=0.0, adv_scheme=0,
 )
 
 

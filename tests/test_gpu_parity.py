@@ -85,6 +85,13 @@ LAUNCHED = {name + "-launched": (dict(cfg, solver_select=1), pre)
             if name in ("axisym-natural", "axisym-gravity", "axisym-ragged-24x40", "cart3d-natural-16",
                         "cart3d-pr-forced-16", "cart3d-ragged-12x10x14")}
 CASES.update(LAUNCHED)
+# Geometric interface advection (adv_scheme = 1): a plane per partly filled cell and one
+# sweep per axis, FP64 in both precisions
+GEOMETRIC = {name + "-geometric": (dict(cfg, adv_scheme=1), pre)
+             for name, (cfg, pre) in list(CASES.items())
+             if name in ("axisym-gravity", "axisym-ragged-24x40", "axisym-d2law", "axisym-forced-inlet",
+                         "cart3d-natural-16", "cart3d-pr-forced-16", "cart3d-ragged-12x10x14")}
+CASES.update(GEOMETRIC)
 
 
 @pytest.mark.parametrize("name", list(CASES))

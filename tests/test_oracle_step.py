@@ -396,3 +396,69 @@ def test_courant_step_reduces_to_fixed_step():
         assert b["dt"] == base["dt"]
     for nm in ("alpha", "T", "omega", "p"):
         assert np.array_equal(a[nm], b[nm]), nm
+
+
+def test_geometric_advection_bounded_and_conservative():
+    """Geometric advection (reading R30) in a discretely divergence-free field at
+    Courant number 0.3: the liquid volume, with the clipped volume counted, is conserved
+    to rounding over 40 steps; Weymouth & Yue's term keeps the split sweeps bounded up
+    to the error of the reconstructed normals (no undershoot, overshoot below 2e-4,
+    measured 1.0e-4; clipped volume below 1e-5 of the droplet, measured 5.1e-6)."""
+    cfg = W.make(n=(32, 64, 1), D0=2e-3, adv_scheme=1)
+    G = Grid(cfg)
+    st = O.init_state(cfg)
+    u = _divfree_axisym(G)
+    a = st["alpha"]
+    vol0 = float(np.sum(a * G.V))
+    clipped = 0.0
+    for _ in range(40):
+        a, clip_vol, nclip, raw = O.alpha_advection_geometric(cfg, G, a, u, cfg["dt"])
+        clipped += clip_vol
+        assert raw.min() > -1e-12 and raw.max() < 1.0 + 2e-4
+    assert float(np.sum(a * G.V)) + clipped == pytest.approx(vol0, rel=1e-13)
+    assert 0.0 <= clipped < 1e-5 * vol0
+
+
+def test_geometric_advection_translates_a_plane_exactly():
+    """A horizontal liquid band in a uniform axial flow (axisymmetric, div u = 0): the
+    geometric flux of a plane is exact, so after each step every column holds the exact
+    cell averages of the translated band (all columns but the outermost, whose normal
+    sees the empty ghost beyond the wall)."""
+    cfg = W.make(n=(16, 48, 1), adv_scheme=1)
+    G = Grid(cfg)
+    h = G.h[1]
+    U, dt = 0.3, 0.37 * h / 0.3              # Courant number 0.37
+    z1, z0 = 4.6 * h, 10.3 * h
+    lo_f = G.xc[1] - 0.5 * h
+
+    def band(s):
+        """cell averages of the liquid band [z1 + s, z0 + s]"""
+        return np.clip((np.minimum(z0 + s, lo_f + h) - np.maximum(z1 + s, lo_f)) / h, 0.0, 1.0)
+
+    a = band(0.0)[None, :, None] * np.ones(G.n)
+    u = [np.zeros(O.fshape(G, 0)), np.full(O.fshape(G, 1), U), None]
+    for m in range(1, 9):
+        a, _, _, _ = O.alpha_advection_geometric(cfg, G, a, u, dt)
+        assert np.abs(a[:-1, :, 0] - band(m * U * dt)[None, :]).max() < 1e-13, m
+
+
+def test_geometric_advection_keeps_the_interface_sharp():
+    """A droplet carried by a uniform oblique flow in 3D: after 40 steps the geometric
+    scheme keeps the band of partial cells within 10 % of its initial size (measured
+    401 -> 417 cells) and the droplet's volume; the compressive scheme widens it more
+    (452)."""
+    cfg = W.make(geom=1, n=(24, 24, 24), L=(1.5e-3,) * 3, xc=(0.6e-3, 0.6e-3, 0.6e-3), D0=0.6e-3,
+                 g=(0.0, 0.0, 0.0), adv_scheme=1)
+    G = Grid(cfg)
+    a0 = O.init_state(cfg)["alpha"]
+    dt = 1e-5
+    u = [np.full(O.fshape(G, 0), 1.0), np.full(O.fshape(G, 1), 0.7), np.full(O.fshape(G, 2), 0.4)]
+    mixed0 = int(np.count_nonzero((a0 > 1e-6) & (a0 < 1 - 1e-6)))
+    ag, af = a0.copy(), a0.copy()
+    for _ in range(40):
+        ag, _, _, _ = O.alpha_advection_geometric(cfg, G, ag, u, dt)
+        af, _, _, _ = O.alpha_advection(dict(cfg, adv_scheme=0), G, af, u, dt)
+    mg = int(np.count_nonzero((ag > 1e-6) & (ag < 1 - 1e-6)))
+    mf = int(np.count_nonzero((af > 1e-6) & (af < 1 - 1e-6)))
+    assert mg <= 1.1 * mixed0 and mg < mf
+    assert float(np.sum(ag * G.V)) == pytest.approx(float(np.sum(a0 * G.V)), rel=1e-12)
