@@ -123,6 +123,17 @@ typedef struct droplet_config {
                            kind (Sec. 2.1): a plane per partly filled cell (Youngs normal),
                            one sweep per axis passing the liquid of each donor's swept slab,
                            volume-conserving whatever div u; FP64 in both precisions */
+  double drho_l_dT;     /* temperature dependence of the liquid density (Sec. 2.7 takes rho_L
+                           from correlations in T and lets it change the volume through
+                           Eqs. alphasource and pequation): rho_L(T) = rho_l + drho_l_dT
+                           (T - T_drop) [kg m^-3 K^-1], entering the mixture density, the
+                           evaporation flux, the alpha source and its cap, the Poynting
+                           factor, and the continuity source through
+                           - alpha/rho_L D(rho_L)/Dt (with the time derivative and the
+                           advective term of the gas density's), whose value the next alpha
+                           source subtracts again; diag M_liq is then sum rho_L(T) alpha V.
+                           0 = the constant rho_l.  Must keep rho_L > 0 at T_amb and Tb.
+                           Not available with droplet_adjoint. */
 } droplet_config;
 
 /* Diagnostics of one droplet after the last completed step (Sec. 4 reports
@@ -156,7 +167,11 @@ enum droplet_field {
   DROPLET_F_MDOT = 8, DROPLET_F_MRAW = 9, DROPLET_F_ALPHA_STAR = 10, DROPLET_F_DP = 11, DROPLET_F_S = 12,
   DROPLET_F_USTAR0 = 13, DROPLET_F_USTAR1 = 14, DROPLET_F_USTAR2 = 15, DROPLET_F_RHOG_OLD = 16,
   DROPLET_F_OMEGA_PINNED = 17,
-  DROPLET_F_COUNT = 18
+  /* the liquid's expansion term alpha/rho_L D(rho_L)/Dt of the last continuity source
+     (cell field), which the next alpha source subtracts: part of the step's state, and
+     writable, with a temperature-dependent liquid density (drho_l_dT != 0) only */
+  DROPLET_F_EXPAND = 18,
+  DROPLET_F_COUNT = 19
 };
 
 /* Create a context for n_droplets independent droplets (cfgs[0..n-1], each

@@ -210,10 +210,11 @@ def van_leer(uu, u, d):
     return u + corr
 
 
-def props(cfg, alpha, rhoG, omega):
-    """Mixture properties chi = alpha chi_L + (1 - alpha) chi_G (Sec. 2.7)."""
+def props(cfg, alpha, rhoG, omega, T):
+    """Mixture properties chi = alpha chi_L + (1 - alpha) chi_G (Sec. 2.7), the liquid
+    density at the cell's temperature (rho_L(T), reading R31)."""
     a = alpha
-    rho = a * cfg["rho_l"] + (1.0 - a) * rhoG
+    rho = a * th.rho_liquid(cfg, T) + (1.0 - a) * rhoG
     mu = a * cfg["mu_l"] + (1.0 - a) * cfg["mu_g"]
     k = a * cfg["k_l"] + (1.0 - a) * cfg["k_g"]
     cpG = omega * cfg["cp_v"] + (1.0 - omega) * cfg["cp_g"]
@@ -421,7 +422,7 @@ def cell_velocity(G, u):
     return out
 
 
-def evaporation_flux(cfg, G, alpha, omega, rhoG, u):
+def evaporation_flux(cfg, G, alpha, omega, rhoG, u, T):
     """S1: Eqs. (9)-(17).
 
     grad(alpha) by central differences; interface cells |grad alpha| > 1e-8/h_min
@@ -440,7 +441,7 @@ def evaporation_flux(cfg, G, alpha, omega, rhoG, u):
     gm = np.sqrt(sum(g[a] * g[a] for a in G.act))
     iface = gm > 1e-8 / G.hmin
     # total flux j at every cell (only gathered at adjacent cells)
-    pr = props(cfg, alpha, rhoG, omega)
+    pr = props(cfg, alpha, rhoG, omega, T)
     Pw = pad_scalar(G, omega, "TO", u=u, amb=0.0)
     gw = grad_central(G, Pw)
     vc = cell_velocity(G, u)
@@ -488,12 +489,19 @@ def evaporation_flux(cfg, G, alpha, omega, rhoG, u):
     return mdot, mraw, adj, K, flags
 
 
-def alpha_source(cfg, alpha, mdot, dt):
-    """S2: Eq. (alphasource) with constant rho_L, mdot capped at rho_L alpha/dt."""
-    cap = cfg["rho_l"] * alpha / dt
+def alpha_source(cfg, alpha, mdot, dt, rhoL=None, expand=None):
+    """S2: Eq. (alphasource), d(alpha)/dt = -mdot/rho_L - (alpha/rho_L) D(rho_L)/Dt, mdot
+    capped at rho_L alpha/dt.  rhoL: the liquid density at T^n (default the constant
+    one); expand: the term (alpha/rho_L) D(rho_L)/Dt of the previous step's continuity
+    source, which the divergence of the advecting velocity u^n carries (reading R31), so
+    that the two cancel in the liquid."""
+    rhoL = cfg["rho_l"] if rhoL is None else rhoL
+    cap = rhoL * alpha / dt
     capped = mdot > cap
     mdot = np.where(capped, cap, mdot)
-    alpha_star = alpha - dt * mdot / cfg["rho_l"]
+    alpha_star = alpha - dt * mdot / rhoL
+    if expand is not None:
+        alpha_star = alpha_star - dt * expand
     return alpha_star, mdot, int(capped.sum())
 
 
@@ -587,7 +595,7 @@ def alpha_advection(cfg, G, alpha_star, u, dt):
         Pm += np.maximum(0.0, -A_lo) + np.maximum(0.0, A_hi)
     Qp = (amax - alphaL) * G.V
     Qm = (alphaL - amin) * G.V
-    with np.errstate(divide="ignore", invalid="ignore"):
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
         Rp = np.where(Pp > 0.0, np.minimum(1.0, np.maximum(0.0, Qp / Pp)), 0.0)
         Rm = np.where(Pm > 0.0, np.minimum(1.0, np.maximum(0.0, Qm / Pm)), 0.0)
     CA = [None] * 3
@@ -994,10 +1002,12 @@ def momentum_predictor(cfg, G, st, pr, alpha, dt, parts=None):
     return ustar
 
 
-def projection(cfg, G, st, ustar, pr, mdot, alpha, rhoG_old, rhoG_new, dt):
-    """S8-S10: Eq. (pequation) with constant rho_L,
-        div u = S = mdot (1/rho_G - 1/rho_L) - (1 - alpha)/rho_G (D rho_G/Dt),
-    D rho_G/Dt = (rho_G^{n+1} - rho_G^n)/dt + vbar^n . grad rho_G^{n+1}.
+def projection(cfg, G, st, ustar, pr, mdot, alpha, rhoG_old, rhoG_new, dt, rhoL_old=None, rhoL_new=None):
+    """S8-S10: Eq. (pequation),
+        div u = S = mdot (1/rho_G - 1/rho_L) - (1 - alpha)/rho_G (D rho_G/Dt)
+                    - alpha/rho_L (D rho_L/Dt),
+    D rho/Dt = (rho^{n+1} - rho^n)/dt + vbar^n . grad rho^{n+1} for both densities (the
+    liquid one rho_L(T), reading R31; its term vanishes for a constant density).
     Pressure increment:  sum_f beta_f (dp_P - dp_N) + sum_open beta_b dp_P
                         = (S_P V_P - sum_f u*_f A_f)/dt,
     beta_f = A_f/(rho_f h), beta_b = A_b/(rho_P h/2) on open (p_rgh = p_ext) faces.
@@ -1009,7 +1019,14 @@ def projection(cfg, G, st, ustar, pr, mdot, alpha, rhoG_old, rhoG_new, dt):
     vc = cell_velocity(G, st["u"])
     gr = grad_central(G, pad_scalar(G, rhoG_new, "zg"))
     adv = sum(vc[a] * gr[a] for a in G.act)
-    S = mdot * (1.0 / rhoG_new - 1.0 / cfg["rho_l"]) - (1.0 - alpha) / rhoG_new * ((rhoG_new - rhoG_old) / dt + adv)
+    rL1 = cfg["rho_l"] if rhoL_new is None else rhoL_new
+    S = mdot * (1.0 / rhoG_new - 1.0 / rL1) - (1.0 - alpha) / rhoG_new * ((rhoG_new - rhoG_old) / dt + adv)
+    expand = np.zeros(n)
+    if rhoL_new is not None and cfg.get("drho_l_dT", 0.0) != 0.0:
+        grl = grad_central(G, pad_scalar(G, rhoL_new, "zg"))
+        advl = sum(vc[a] * grl[a] for a in G.act)
+        expand = alpha / rhoL_new * ((rhoL_new - rhoL_old) / dt + advl)
+        S = S - expand
     diag, coup, beta = pressure_system(G, rho)
     div_star = divergence_sum(G, [ustar[a] * G.A[a] if a in G.act else None for a in range(3)])
     rhs = (S * G.V - div_star) / dt
@@ -1023,7 +1040,7 @@ def projection(cfg, G, st, ustar, pr, mdot, alpha, rhoG_old, rhoG_new, dt):
         with np.errstate(divide="ignore", invalid="ignore"):
             corr = np.where(G.A[a] > 0.0, dt * beta[a] * (dR - dL) / G.A[a], 0.0)
         unew[a] = ustar[a] - corr
-    return unew, st["p"] + dp, dp, S, (diag, coup, rhs)
+    return unew, st["p"] + dp, dp, S, (diag, coup, rhs), expand
 
 
 def pressure_system(G, rho):
@@ -1108,11 +1125,12 @@ def step(cfg, st, keep=False):
     omega, rhoG_old = thermo_pin(cfg, G, alpha, T, omega)
     # S1, S2
     if mask & PHYS_EVAP:
-        mdot, mraw, adj, K, f1 = evaporation_flux(cfg, G, alpha, omega, rhoG_old, u)
+        mdot, mraw, adj, K, f1 = evaporation_flux(cfg, G, alpha, omega, rhoG_old, u, T)
         flags |= f1
     else:
         mdot, mraw, adj, K = np.zeros(G.n), np.zeros(G.n), np.full(G.n, -1), 0.0
-    alpha_star, mdot, ncap = alpha_source(cfg, alpha, mdot, dt)
+    rhoL_old = th.rho_liquid(cfg, T)
+    alpha_star, mdot, ncap = alpha_source(cfg, alpha, mdot, dt, rhoL_old, st.get("expand"))
     if ncap:
         flags |= FLAG_MDOT_CAPPED
     # S3
@@ -1127,7 +1145,7 @@ def step(cfg, st, keep=False):
     if nclip:
         flags |= FLAG_ALPHA_CLIPPED
     # S4
-    pr = props(cfg, alpha_new, rhoG_old, omega)
+    pr = props(cfg, alpha_new, rhoG_old, omega, T)
     # S5
     if (mask & PHYS_ENERGY) and not const:
         T_new = scalar_transport(cfg, G, T, pr["rho"] * pr["cp"], pr["k"], -mdot * cfg["Lv"], u, dt, cfg["T_amb"])
@@ -1145,15 +1163,18 @@ def step(cfg, st, keep=False):
     # S7 - S10
     if mask & PHYS_FLOW:
         ustar = momentum_predictor(cfg, G, st, pr, alpha_new, dt)
-        u_new, p_new, dp, S, psys = projection(cfg, G, st, ustar, pr, mdot, alpha_new, rhoG_old, rhoG_new, dt)
+        u_new, p_new, dp, S, psys, expand = projection(cfg, G, st, ustar, pr, mdot, alpha_new, rhoG_old, rhoG_new,
+                                                       dt, rhoL_old, th.rho_liquid(cfg, T_new))
     else:
         ustar, u_new, p_new, dp, S, psys = u, u, st["p"], np.zeros(G.n), np.zeros(G.n), None
+        expand = np.zeros(G.n)      # no flow to carry an expansion
     out = dict(alpha=alpha_new, T=T_new, omega=omega_new, p=p_new, u=u_new, rhoG=rhoG_new,
                t=st["t"] + dt, step=st["step"] + 1,
                clip_mass=st["clip_mass"] + clip_vol,
                flags=flags, K=K, mdot=mdot, ncap=ncap, nclip=nclip)
     out["vap_out_cum"] = st["vap_out_cum"] + dt * boundary_vapour_outflow(cfg, G, u_new, omega_new, rhoG_new)
     out["dt"] = courant_dt(cfg, G, u_new, dt)
+    out["expand"] = expand
     if keep:
         out["aux"] = dict(omega_pinned=omega, rhoG_old=rhoG_old, mraw=mraw, adj=adj, mdot=mdot,
                           alpha_star=alpha_star, alphaL=alphaL, ustar=ustar, dp=dp, S=S, psys=psys,
@@ -1177,7 +1198,7 @@ def diagnostics(cfg, st):
     return dict(
         t=st["t"], step=st["step"], V_l=V_l, d_eq=d_eq, d2=d_eq * d_eq,
         mdot_tot=w * float(np.sum(mdot * G.V)), K_norm=st.get("K", 0.0), T_s_mean=Ts,
-        M_liq=cfg["rho_l"] * V_l,
+        M_liq=w * float(np.sum(th.rho_liquid(cfg, st["T"]) * alpha * G.V)),
         M_vap=w * float(np.sum((1.0 - alpha) * st["rhoG"] * st["omega"] * G.V)),
         vap_out_cum=w * st["vap_out_cum"],
         max_u=max(float(np.max(np.abs(st["u"][a]))) for a in G.act),

@@ -139,6 +139,14 @@ def _crit(cfg):
     return [(cfg["Tc"], cfg["Pc"], cfg["omega_ac"]), (cfg["Tc_g"], cfg["Pc_g"], cfg["omega_g"])]
 
 
+def rho_liquid(cfg, T):
+    """Liquid density rho_L(T) = rho_l + (d rho_L / dT)(T - T_drop): the paper takes it from
+    property correlations (Sec. 2.7) and lets it change the volume (Eqs. alphasource,
+    pequation); here a linear law through the configured density at the initial liquid
+    temperature stands in for them (reading R31; drho_l_dT = 0: constant density)."""
+    return cfg["rho_l"] + cfg.get("drho_l_dT", 0.0) * (np.asarray(T, dtype=np.float64) - cfg["T_drop"])
+
+
 def y_pr_scalar(cfg, T):
     """Eq. (equilibirumyi) for one cell: x = 1 (pure liquid fuel), fixed point in y.
 
@@ -149,7 +157,7 @@ def y_pr_scalar(cfg, T):
     crit = _crit(cfg)
     kij = cfg["kij"]
     p0 = float(psat(cfg, T))
-    vL = cfg["M_l"] / cfg["rho_l"]
+    vL = cfg["M_l"] / float(rho_liquid(cfg, T))
     lnphi_pure, _ = pr_lnphi(T, p0, [1.0, 0.0], crit, kij)
     num = p0 * math.exp(lnphi_pure[0]) * math.exp(vL * (P - p0) / (R_GAS * T))
     y = min(p0 / P, Y_CLAMP)

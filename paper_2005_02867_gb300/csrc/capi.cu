@@ -42,6 +42,9 @@ struct dctx {
                       {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
                       {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}};
   double *part = nullptr, *psum = nullptr, *pmax = nullptr, *scal = nullptr;
+  // the liquid's expansion term of the last continuity source (a temperature-dependent
+  // liquid density only, else null): the next alpha source subtracts it
+  double* expand = nullptr;
   unsigned* flags = nullptr;
   int* dirty = nullptr;              // a state field was overwritten: S0 re-evaluates rho_G everywhere
   double* hscal = nullptr;
@@ -100,6 +103,10 @@ static int check_cfg(const droplet_config& c) {
   if (c.wait_limit < 0 || (c.solver_select != 0 && c.solver_select != 1)) return DROPLET_ERR_ARG;
   if (!(c.co_max >= 0.0) || !std::isfinite(c.co_max)) return DROPLET_ERR_ARG;
   if (c.adv_scheme != 0 && c.adv_scheme != 1) return DROPLET_ERR_ARG;
+  // a liquid density linear in T stays positive up to the ambient and boiling temperatures
+  if (!std::isfinite(c.drho_l_dT) || !(c.rho_l + c.drho_l_dT * (c.T_amb - c.T_drop) > 0.0) ||
+      !(c.rho_l + c.drho_l_dT * (c.Tb - c.T_drop) > 0.0))
+    return DROPLET_ERR_ARG;
   long long nn = (long long)c.n[0] * c.n[1] * (c.geom == 0 ? 1 : c.n[2]);
   {   // 32-bit cell and face indices: the cells plus the largest extra face plane
     const long long n2 = c.geom == 0 ? 1 : c.n[2];
@@ -168,6 +175,7 @@ static void make_phys(const droplet_config& c, Phys& p) {
   p.cc_LMR = c.Lv * c.M_l / R_GAS;
   p.iTb = 1.0 / c.Tb;
   p.irho_l = 1.0 / c.rho_l;
+  p.drl = c.drho_l_dT;
 }
 
 static int dalloc(double** q, long long n) {
@@ -178,7 +186,8 @@ static int dalloc(double** q, long long n) {
 static void free_all(dctx* c) {
   double** arrs[] = {&c->alpha, &c->T, &c->omega, &c->pr, &c->rhoG, &c->rhoG_old, &c->mdot, &c->mraw, &c->astar,
                      &c->aL, &c->Rp, &c->Rm, &c->rho, &c->mu, &c->kc, &c->cp, &c->Dm, &c->yq, &c->dp, &c->S,
-                     &c->bD, &c->brhs, &c->bx, &c->part, &c->psum, &c->pmax, &c->scal, &c->xi, &c->hT, &c->hW};
+                     &c->bD, &c->brhs, &c->bx, &c->part, &c->psum, &c->pmax, &c->scal, &c->xi, &c->hT, &c->hW,
+                     &c->expand};
   for (auto q : arrs) { cudaFree(*q); *q = nullptr; }
   for (int a = 0; a < 3; ++a) {
     cudaFree(c->u[a]); cudaFree(c->FL[a]); cudaFree(c->AF[a]); cudaFree(c->us[a]); cudaFree(c->bc[a]); cudaFree(c->hu[a]);
@@ -214,7 +223,7 @@ static void free_all(dctx* c) {
 static int run_diag(dctx* c, int mode) {
   Geo& g = c->g;
   int nb = red_grid_cap(g.N, c->rb);
-  L_diag(c->st, nb, g, c->alpha, c->T, c->mdot, c->omega, c->rhoG, c->u[0], c->u[1], c->u[2] ? c->u[2] : c->u[0],
+  L_diag(c->st, nb, g, c->p, c->alpha, c->T, c->mdot, c->omega, c->rhoG, c->u[0], c->u[1], c->u[2] ? c->u[2] : c->u[0],
                                 c->psum, c->pmax, c->flags);
   ++g_launches, k_diag_finish<<<1, TPB, 0, c->st>>>(c->psum, c->pmax, nb, c->scal, mode, c->p.co_hmin, c->cfg.dt);
   CKR(cudaGetLastError());
@@ -268,7 +277,7 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
     if ((rc = dalloc(&c->u[a], nf)) || (rc = dalloc(&c->FL[a], nf)) || (rc = dalloc(&c->AF[a], nf)) ||
         (rc = dalloc(&c->us[a], nf)) || (rc = dalloc(&c->hu[a], nf))) { free_all(c); delete c; return rc; }
   }
-  if ((rc = dalloc(&c->part, RED_BLOCKS * 8)) || (rc = dalloc(&c->psum, RED_BLOCKS * 6)) ||
+  if ((rc = dalloc(&c->part, RED_BLOCKS * 8)) || (rc = dalloc(&c->psum, RED_BLOCKS * 7)) ||
       (rc = dalloc(&c->pmax, RED_BLOCKS * 3)) || (rc = dalloc(&c->scal, SC_COUNT))) { free_all(c); delete c; return rc; }
   if (cudaMalloc((void**)&c->adj, sizeof(int) * N) != cudaSuccess || cudaMalloc((void**)&c->flags, sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc((void**)&c->dirty, sizeof(int)) != cudaSuccess ||
@@ -342,6 +351,10 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
   }
   cudaMemsetAsync(c->hT, 0, sizeof(double) * N, st);
   cudaMemsetAsync(c->hW, 0, sizeof(double) * N, st);
+  if (c->p.drl != 0.0) {
+    if ((rc = dalloc(&c->expand, N))) { free_all(c); delete c; return rc; }
+    cudaMemsetAsync(c->expand, 0, sizeof(double) * N, st);
+  }
   reset_clock(c, st);
   if (cfg.co_max > 0.0) {
     c->p.dyn = c->scal;
@@ -384,14 +397,14 @@ static int one_step(dctx* c, int* nc_flag) {
   }
   // S1, S2
   if (mask & DROPLET_PHYS_EVAP) {
-    L_evap_raw(st, nb, g, p, c->alpha, c->omega, c->rhoG_old, c->u[0], c->u[1], u2, c->mraw, c->adj, c->part, c->flags);
+    L_evap_raw(st, nb, g, p, c->alpha, c->omega, c->rhoG_old, c->T, c->u[0], c->u[1], u2, c->mraw, c->adj, c->part, c->flags);
     ++g_launches, k_evap_K<<<1, TPB, 0, st>>>(c->part, nb, c->scal, c->flags);
   } else {
     cudaMemsetAsync(c->mraw, 0, sizeof(double) * N, st);
     cudaMemsetAsync(c->scal + SC_K, 0, sizeof(double), st);
   }
-  ++g_launches, k_alpha_source<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->mraw, c->scal, c->mdot, c->astar, c->astar_f, c->flags,
-                                                   c->dirty);
+  ++g_launches, k_alpha_source<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->mraw, c->scal, c->T, c->expand, c->mdot, c->astar,
+                                                   c->astar_f, c->flags, c->dirty);
   // S3, and S4 (the mixture properties) in the kernel that forms alpha^{n+1}
   const PropsOut po{c->rhoG_old, c->omega, c->T, c->rho, c->mu, c->kc, c->cp, c->Dm, c->s32};
   if ((mask & DROPLET_PHYS_FLOW) && c->cfg.adv_scheme == 1) {
@@ -542,8 +555,10 @@ static int one_step(dctx* c, int* nc_flag) {
       if ((rc = soft_status(rc, nc_flag))) return rc;
     }
     double* us2 = c->us[2] ? c->us[2] : c->us[0];
+    // T^n: the history field the energy solve's guess kept, or T itself when T is not solved
+    const double* T0 = ((mask & DROPLET_PHYS_ENERGY) && !p.const_props) ? c->hT : c->T;
     L_poisson_assemble(st, gc, g, p, c->mdot, c->alpha, c->rhoG_old, c->rhoG, c->u[0], c->u[1], u2,
-                                           c->us[0], c->us[1], us2, c->rho, c->S, c->bD, c->bc[0], c->bc[1],
+                                           c->us[0], c->us[1], us2, c->rho, c->T, T0, c->expand, c->S, c->bD, c->bc[0], c->bc[1],
                                            na == 3 ? c->bc[2] : c->bc[0], c->brhs, c->dp);
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
@@ -888,7 +903,7 @@ extern "C" int droplet_diag(droplet_ctx* cc, int droplet, droplet_diag_t* out) {
   out->mdot_tot = w * s[SC_SUM_MDOT_V];
   out->K_norm = s[SC_K];
   out->T_s_mean = s[SC_SUM_G] > 0.0 ? s[SC_SUM_TG] / s[SC_SUM_G] : 0.0;
-  out->M_liq = c->cfg.rho_l * out->V_l;
+  out->M_liq = c->p.drl == 0.0 ? c->cfg.rho_l * out->V_l : w * s[SC_SUM_MLIQ];
   out->M_vap = w * s[SC_SUM_VAP];
   out->vap_out_cum = w * s[SC_VAPOUT];
   out->max_u = s[SC_MAXU];
@@ -924,6 +939,7 @@ static double* field_ptr(dctx* c, int id, long long* n, bool* writable) {
     case DROPLET_F_S: return c->S;
     case DROPLET_F_RHOG_OLD: return c->rhoG_old;
     case DROPLET_F_OMEGA_PINNED: return nullptr;
+    case DROPLET_F_EXPAND: *writable = true; return c->expand;   // (null: constant liquid density)
     default: break;
   }
   int a = -1;
@@ -984,7 +1000,8 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
   dctx* x = cc->d[0];
   const droplet_config& cf = x->cfg;
   if (cf.physics_mask != (DROPLET_PHYS_EVAP | DROPLET_PHYS_ENERGY | DROPLET_PHYS_SPECIES) || cf.precision != 0 ||
-      cf.eq_model != 0 || cf.const_props_check != 0 || cf.bc_mode != 0 || cf.co_max != 0.0 || x->step != 0)
+      cf.eq_model != 0 || cf.const_props_check != 0 || cf.bc_mode != 0 || cf.co_max != 0.0 || cf.drho_l_dT != 0.0 ||
+      x->step != 0)
     return DROPLET_ERR_ARG;
   Geo& g = x->g;
   Phys& p = x->p;
@@ -1123,17 +1140,19 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
 }
 
 // ---------------------------------------------------------------- checkpoint / resume
-static const char kMagic[8] = {'D', 'R', 'O', 'P', 'C', 'K', 'P', '3'};
+static const char kMagic[8] = {'D', 'R', 'O', 'P', 'C', 'K', 'P', '4'};
 
-// the checkpointed fields: the state, then the history of the extrapolated guesses
-constexpr int NCKPT = 13;
+// the checkpointed fields: the state, the history of the extrapolated guesses, and the
+// liquid's expansion term of the last step (a temperature-dependent liquid density only)
+constexpr int NCKPT = 14;
 static int state_fields(dctx* x, double* f[NCKPT], long long n[NCKPT]) {
   double* fs[NCKPT] = {x->alpha, x->T, x->omega, x->pr, x->rhoG, x->u[0], x->u[1], x->u[2],
-                       x->hT, x->hW, x->hu[0], x->hu[1], x->hu[2]};
+                       x->hT, x->hW, x->hu[0], x->hu[1], x->hu[2], x->expand};
   for (int q = 0; q < NCKPT; ++q) {
     f[q] = fs[q];
-    const int fa = q >= 10 ? q - 10 : q - 5;
-    n[q] = fs[q] ? ((q < 5 || q == 8 || q == 9) ? x->g.N : nfaces(x->g, fa)) : 0;
+    const int fa = q >= 10 && q < 13 ? q - 10 : q - 5;
+    const bool cell = q < 5 || q == 8 || q == 9 || q == 13;
+    n[q] = fs[q] ? (cell ? x->g.N : nfaces(x->g, fa)) : 0;
   }
   return 0;
 }

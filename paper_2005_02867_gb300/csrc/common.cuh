@@ -56,6 +56,7 @@ struct Phys {
   double iM_l, iM_g;
   // Clausius-Clapeyron exponent L M_l / R and 1 / T_b; 1 / rho_l
   double cc_LMR, iTb, irho_l;
+  double drl;                // d rho_L / dT (0: constant liquid density rho_l)
   // Courant-adaptive step: the droplet's device scalars, where the step's dt and 1 / dt
   // are kept (null: the fixed dt, idt above); co_hmin = threshold Courant number x h_min
   const double* dyn;
@@ -389,6 +390,13 @@ __device__ inline void pr_binary(const Phys& p, double T, double P, double y, do
   lnphi0 = b0 / bm * (Z - 1.0) - log(Z - B) - A / (2.0 * s2 * B) * (2.0 * sa / am - b0 / bm) * logterm;
 }
 
+// liquid density at temperature T, linear through rho_l at the initial liquid temperature
+// (Sec. 2.7 takes rho_L from correlations in T): rho_l + drl (T - T_drop), product and sum
+// rounded separately; exactly rho_l for a constant density
+__device__ __forceinline__ double rho_liq(const Phys& p, double T) {
+  return __dadd_rn(p.rho_l, __dmul_rn(p.drl, T - p.T_drop));
+}
+
 // saturation mole fraction (Raoult, or the Peng-Robinson fixed point with the Poynting factor).
 // y_start > 0 starts the fixed point there instead of at the Raoult value (a pinned cell's
 // previous saturation value: the iteration then stops after a few steps at the same
@@ -401,7 +409,7 @@ __device__ inline double y_eq(const Phys& p, double T, unsigned* boil, double y_
   if (y_start > 0.0 && y_start < Y_CLAMP) y = y_start;
   double Zp, lp;
   pr_binary(p, T, p0, 1.0, Zp, lp);
-  double vL = p.M_l / p.rho_l;
+  double vL = p.M_l / rho_liq(p, T);
   double num = p0 * exp(lp) * exp(vL * (p.P - p0) / (R_GAS * T));
   for (int it = 0; it < 50; ++it) {
     double Z, l0;

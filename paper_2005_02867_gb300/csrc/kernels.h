@@ -43,7 +43,7 @@ struct ProfScope {
 // indices of the per-droplet device scalar array
 enum {
   SC_K = 0, SC_CLIP, SC_VAPOUT, SC_DT, SC_IDT, SC_TIME,
-  SC_SUM_ALPHA_V, SC_SUM_MDOT_V, SC_SUM_TG, SC_SUM_G, SC_SUM_VAP, SC_MAXU, SC_AMAX, SC_AMIN,
+  SC_SUM_ALPHA_V, SC_SUM_MDOT_V, SC_SUM_TG, SC_SUM_G, SC_SUM_VAP, SC_SUM_MLIQ, SC_MAXU, SC_AMAX, SC_AMIN,
   SC_ITS_P, SC_ITS_T, SC_ITS_W, SC_ITS_U, SC_RES_P, SC_NC,
   SC_HIST,   // 1: the history fields hold the previous step's T, omega, u (extrapolated guesses)
   SC_COUNT
@@ -69,7 +69,8 @@ __global__ void k_thermo_pin(Geo g, Phys p, const double* alpha, const double* T
 
 __global__ void k_evap_K(const double* partials, int nblk, double* scal, unsigned* flags);
 __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double* mraw, const double* scal,
-                               double* mdot, double* alpha_star, float* alpha_star_f, unsigned* flags, int* dirty);
+                               const double* T, const double* expand, double* mdot, double* alpha_star,
+                               float* alpha_star_f, unsigned* flags, int* dirty);
 
 __global__ void k_adv_low(Geo g, const double* as, const double* F0, const double* F1, const double* F2, double* aL);
 
@@ -94,8 +95,6 @@ struct PropsOut {
 __global__ void k_faces_f32(const double* u0, const double* u1, const double* u2, float* f0, float* f1, float* f2,
                             long long n0, long long n1, long long n2);
 __global__ void k_alpha_clip_only(Geo g, Phys p, const double* as, double* alpha, double* partials, PropsOut po);
-__global__ void k_props(Geo g, Phys p, const double* alpha, const double* rhoG, const double* omega, double* rho,
-                        double* mu, double* kc, double* cp, double* D);
 
 __global__ void k_yeq(Geo g, Phys p, const double* T, const double* alpha, const double* omega, double* yq,
                       unsigned* flags);
@@ -109,7 +108,7 @@ __global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, 
 __global__ void k_extrap(long long n, double* x, double* xh, const double* scal);
 
 // launch wrappers of the kernels templated on the active axes / face direction (step_kernels.cu)
-void L_evap_raw(cudaStream_t st, int grid, Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* mraw, int* adj, double* partials, unsigned* flags);
+void L_evap_raw(cudaStream_t st, int grid, Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG, const double* T, const double* u0, const double* u1, const double* u2, double* mraw, int* adj, double* partials, unsigned* flags);
 void L_adv_faces(cudaStream_t st, int grid, Geo g, Phys p, int a, const double* as, const double* ua, double* FL, double* AF);
 void L_adv_limit(cudaStream_t st, int grid, Geo g, const double* as, const double* aL, const double* A0, const double* A1, const double* A2, double* Rp, double* Rm);
 void L_geo_advect(cudaStream_t st, int grid, Geo g, Phys p, const double* astar, double* const w[2],
@@ -123,12 +122,12 @@ void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, co
 void L_mom_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32* s32);
 void L_mom_assemble(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32* s32);
 void L_mom_scatter(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* x, double* us);
-void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo, const double* rgn, const double* u0, const double* u1, const double* u2, const double* us0, const double* us1, const double* us2, const double* rho, double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs, double* dp0);
+void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo, const double* rgn, const double* u0, const double* u1, const double* u2, const double* us0, const double* us1, const double* us2, const double* rho, const double* T1, const double* T0, double* expand, double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs, double* dp0);
 void L_correct(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u);
 // the velocity correction of every direction and p_rgh += dp in one launch
 void L_correct_all(cudaStream_t st, Geo g, Phys p, double* const us[3], const double* dp, const double* rho,
                    double* const u[3], double* pr);
-void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax, unsigned* flags);
+void L_diag(cudaStream_t st, int grid, Geo g, Phys p, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax, unsigned* flags);
 
 void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x, double* uh,
                     const double* scal);

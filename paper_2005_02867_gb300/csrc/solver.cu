@@ -1018,9 +1018,28 @@ __device__ __forceinline__ T mg_resid(const LevV<T>& L, long long id, int i, int
   return L.b[id] - y;
 }
 
-// residual of the fine level restricted (summed) into the coarse right-hand side
+// the residual with the level's total diagonal a_P = D + sum c given: b - a_P x_P + sum c x_N
+// (one FMA per term: the diagonal form of the FP64 CG operator, for level 0 of an FP64
+// hierarchy, whose total diagonal the CG's set-up has formed)
+__device__ __forceinline__ double mg_resid_diag(const LevV<double>& L, const double* ad, long long id, int i, int j,
+                                                int k) {
+  const long long st1 = L.m[0], st2 = (long long)L.m[0] * L.m[1];
+  double r = fma(-ad[id], L.x[id], L.b[id]);
+  if (i > 0) r = fma(L.c[0][id], L.x[id - 1], r);
+  if (i < L.m[0] - 1) r = fma(L.c[0][id + 1], L.x[id + 1], r);
+  if (j > 0) r = fma(L.c[1][id], L.x[id - st1], r);
+  if (j < L.m[1] - 1) r = fma(L.c[1][id + st1], L.x[id + st1], r);
+  if (L.c[2]) {
+    if (k > 0) r = fma(L.c[2][id], L.x[id - st2], r);
+    if (k < L.m[2] - 1) r = fma(L.c[2][id + st2], L.x[id + st2], r);
+  }
+  return r;
+}
+
+// residual of the fine level restricted (summed) into the coarse right-hand side; ad (FP64
+// levels only, may be null): the fine level's total diagonal, for the diagonal form
 template <typename T>
-__global__ void k_mg_restrict(LevV<T> F, LevV<T> C, const int* done) {
+__global__ void k_mg_restrict(LevV<T> F, LevV<T> C, const int* done, const T* ad = nullptr) {
   if (*done) return;
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= C.N) return;
@@ -1033,6 +1052,12 @@ __global__ void k_mg_restrict(LevV<T> F, LevV<T> C, const int* done) {
       for (int di = 0; di < 2; ++di) {
         int i = 2 * I + di, j = 2 * J + dj, k = kz == 2 ? 2 * K + dk : 0;
         long long fi = (long long)i + (long long)F.m[0] * ((long long)j + (long long)F.m[1] * k);
+        if constexpr (sizeof(T) == 8) {
+          if (ad) {
+            s += mg_resid_diag(F, ad, fi, i, j, k);
+            continue;
+          }
+        }
         s += mg_resid<T>(F, fi, i, j, k);
       }
   ((T*)C.b)[id] = s;
@@ -2444,8 +2469,9 @@ static void smooth(Prof* prof, LevV<T> L, int col, int first, const int* done, c
   ++g_launches, k_mg_smooth<T><<<lin_grid(half_sweep_threads(L.m)), TPB, 0, st>>>(L, col, first, done);
 }
 
+// (ad0: the total diagonal of level 0 when it is the FP64 box whose CG formed it, else null)
 template <typename T>
-static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaStream_t st) {
+static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaStream_t st, const T* ad0 = nullptr) {
   const int nu = 2;          // smoothing sweeps (red + black) before and after
   const int ncoarse = 4;     // symmetric sweep pairs on the coarsest level (at most 2^d x ... cells)
   // levels from `lt` on run inside one block (k_mg_tail)
@@ -2460,9 +2486,10 @@ static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaSt
     LevV<T> C = lv<T>(lev[l + 1]);
     {
       int d = L.c[2] ? 3 : 2;
+      const T* ad = l == 0 ? ad0 : nullptr;
       ProfScope ps(prof, KC_MG_RESTRICT, st, ((3.0 + d) * L.N + C.N) * (double)sizeof(T),
-                   sizeof(T) == 8 ? (4.0 * d + 3.0) * L.N : 0.0);
-      ++g_launches, k_mg_restrict<T><<<lin_grid(C.N), TPB, 0, st>>>(L, C, done);
+                   sizeof(T) == 8 ? (ad ? 2.0 * d + 2.0 : 4.0 * d + 3.0) * L.N : 0.0);
+      ++g_launches, k_mg_restrict<T><<<lin_grid(C.N), TPB, 0, st>>>(L, C, done, ad);
     }
   }
   TailLevels<T> TL;
@@ -2501,7 +2528,8 @@ void Solver::vcycle(int fp32, bool casts) {
     vcycle_t<float>(prof, lev, nlev, done, stream);
     if (casts) ++g_launches, k_cast_done<double, float><<<g0, TPB, 0, stream>>>(L0.N, z, (const float*)L0.x, done);
   } else {
-    vcycle_t<double>(prof, lev, nlev, done, stream);
+    // level 0 of an FP64 hierarchy is the CG's box: its total diagonal is adg
+    vcycle_t<double>(prof, lev, nlev, done, stream, adg);
   }
 }
 
@@ -2621,7 +2649,7 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
   ++g_launches, k_cast_done<double, double><<<g, TPB, 0, stream>>>(s.N, p, z, done);
   auto iteration = [&]() {
     {
-      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0, (4.0 * (s.c[2] ? 3 : 2) + 3.0) * s.N);
+      ProfScope ps(prof, KC_SPMV, stream, (3.0 + (s.c[2] ? 3 : 2)) * s.N * 8.0, (2.0 * (s.c[2] ? 3 : 2) + 2.0) * s.N);
       ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt, adg);
     }
     {

@@ -168,7 +168,7 @@ __device__ __forceinline__ double norm_rn(const double gr[3], int na) {
 // Partial sums of m_raw V and f(alpha) m_raw V per block.
 template <int NA>
 __global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG,
-                           const double* u0, const double* u1, const double* u2,
+                           const double* T, const double* u0, const double* u1, const double* u2,
                            double* mraw, int* adj, double* partials, unsigned* flags) {
   double acc[2] = {0.0, 0.0};
   constexpr int na = NA;
@@ -205,7 +205,7 @@ __global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* ome
       } else {
         // total flux at the adjacent cell Q
         double aQ = alpha[found], rgQ = rhoG[found], wQ = omega[found];
-        double rhoQ = aQ * p.rho_l + (1.0 - aQ) * rgQ;
+        double rhoQ = aQ * (p.drl == 0.0 ? p.rho_l : rho_liq(p, T[found])) + (1.0 - aQ) * rgQ;
         double DQ = aQ * p.D_l + (1.0 - aQ) * p.D_gas;
         int qi, qj, qk;
         decomp(found, g.n[0], g.n[1], qi, qj, qk);
@@ -255,7 +255,8 @@ __global__ void k_evap_K(const double* partials, int nblk, double* scal, unsigne
 // and m = 0 without the binary64 square root, cap and update, whose results there are
 // exactly those values.
 __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double* mraw, const double* scal,
-                               double* mdot, double* alpha_star, float* alpha_star_f, unsigned* flags, int* dirty) {
+                               const double* T, const double* expand, double* mdot, double* alpha_star,
+                               float* alpha_star_f, unsigned* flags, int* dirty) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
   if (id == 0) *dirty = 0;
@@ -265,10 +266,12 @@ __global__ void k_alpha_source(Geo g, Phys p, const double* alpha, const double*
   if ((__double_as_longlong(mr) << 1) != 0) {      // mraw != 0, tested on the integer pipe
     const double K = scal[SC_K];
     m = (K == 0.0) ? 0.0 : K * sqrt(a * (1.0 - a)) * mr;
-    const double cap = p.rho_l * a * idt_of(p);
+    const double rl = p.drl == 0.0 ? p.rho_l : rho_liq(p, T[id]);
+    const double cap = rl * a * idt_of(p);
     if (m > cap) { m = cap; atomicOr(flags, (unsigned)DROPLET_FLAG_MDOT_CAPPED); }
-    as = a - dt_of(p) * m * p.irho_l;
+    as = p.drl == 0.0 ? a - dt_of(p) * m * p.irho_l : a - dt_of(p) * m / rl;
   }
+  if (expand) as = as - dt_of(p) * expand[id];
   mdot[id] = m;
   alpha_star[id] = as;
   if (alpha_star_f) alpha_star_f[id] = f32_rn(as);
@@ -333,10 +336,10 @@ __global__ void k_adv_low(Geo g, const double* as, const double* F0, const doubl
 
 // ============================================================== S4 mixture properties
 __device__ __forceinline__ void props_cell(const Phys& p, long long id, double a, const double* rhoG,
-                                           const double* omega, double* rho, double* mu, double* kc, double* cp,
-                                           double* D) {
+                                           const double* omega, const double* T, double* rho, double* mu,
+                                           double* kc, double* cp, double* D) {
   const double w = omega[id];
-  rho[id] = a * p.rho_l + (1.0 - a) * rhoG[id];
+  rho[id] = a * (p.drl == 0.0 ? p.rho_l : rho_liq(p, T[id])) + (1.0 - a) * rhoG[id];
   mu[id] = a * p.mu_l + (1.0 - a) * p.mu_g;
   kc[id] = a * p.k_l + (1.0 - a) * p.k_g;
   double cpG = w * p.cp_v + (1.0 - w) * p.cp_g;
@@ -346,7 +349,7 @@ __device__ __forceinline__ void props_cell(const Phys& p, long long id, double a
 
 // props_cell into the PropsOut arrays, and their binary32 copies when asked for
 __device__ __forceinline__ void props_out(const Phys& p, long long id, double a, const PropsOut& po) {
-  props_cell(p, id, a, po.rhoG, po.omega, po.rho, po.mu, po.kc, po.cp, po.D);
+  props_cell(p, id, a, po.rhoG, po.omega, po.T, po.rho, po.mu, po.kc, po.cp, po.D);
   if (po.s.T) {
     po.s.T[id] = f32_rn(po.T[id]);
     po.s.w[id] = f32_rn(po.omega[id]);
@@ -364,13 +367,6 @@ __global__ void k_faces_f32(const double* u0, const double* u1, const double* u2
     else if (id < n0 + n1) f1[id - n0] = f32_rn(u1[id - n0]);
     else f2[id - n0 - n1] = f32_rn(u2[id - n0 - n1]);
   }
-}
-
-__global__ void k_props(Geo g, Phys p, const double* alpha, const double* rhoG, const double* omega, double* rho,
-                        double* mu, double* kc, double* cp, double* D) {
-  long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (id >= g.N) return;
-  props_cell(p, id, alpha[id], rhoG, omega, rho, mu, kc, cp, D);
 }
 
 // Zalesak limiter ratios R+ and R- from the local bounds over the cell and its face neighbours.
@@ -410,8 +406,9 @@ __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const dou
   }
   double V = cellV(g, i);
   double Qp = (amax - aL[id]) * V, Qm = (aL[id] - amin) * V;
-  Rp[id] = Pp > 0.0 ? iclamp01(Qp * rcp64(Pp)) : 0.0;
-  Rm[id] = Pm > 0.0 ? iclamp01(Qm * rcp64(Pm)) : 0.0;
+  // (Q = 0 gives 0 directly: Q / P for a subnormal P would be 0 x inf through the reciprocal)
+  Rp[id] = Pp > 0.0 && Qp > 0.0 ? iclamp01(Qp * rcp64(Pp)) : 0.0;
+  Rm[id] = Pm > 0.0 && Qm > 0.0 ? iclamp01(Qm * rcp64(Pm)) : 0.0;
 }
 
 __device__ __forceinline__ double limited_flux(const Geo& g, int a, const double* A, const double* Rp,
@@ -863,12 +860,13 @@ __global__ void k_rhoG(Geo g, Phys p, const double* T, const double* w, double* 
 // ============================================================== S7 momentum predictor
 // For each interior face of direction c (box index b, face index f = b + e_c),
 // V_f-weighted: rho_f V_f/dt u* - [implicit viscous] = rho_f V_f u^n/dt + adv + visc^T + forces.
-__device__ __forceinline__ double mu_edge(const Geo& g, const double* mu, const int L[3], const int R[3], int a, int sh) {
+// muLR = mu_L + mu_R of the face's two cells, shared by its edges (the sum in the same order)
+__device__ __forceinline__ double mu_edge(const Geo& g, const double* mu, double muLR, const int L[3], const int R[3],
+                                          int a, int sh) {
   int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
   La[a] += sh;
   Ra[a] += sh;
-  double s = cellc(g, mu, L[0], L[1], L[2]) + cellc(g, mu, R[0], R[1], R[2]) + cellc(g, mu, La[0], La[1], La[2]) +
-             cellc(g, mu, Ra[0], Ra[1], Ra[2]);
+  double s = muLR + cellc(g, mu, La[0], La[1], La[2]) + cellc(g, mu, Ra[0], Ra[1], Ra[2]);
   return 0.25 * s;
 }
 
@@ -905,9 +903,11 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
   }
   double A_f = V_f * g.ih[c];
   double u_f = uc[fidx(g, c, f[0], f[1], f[2])];
-  double d = rho_f * V_f * idt_of(p);
-  double r = rho_f * V_f * u_f * idt_of(p);
-  double t_adv = 0.0, t_vT = 0.0, d_visc = 0.0;
+  const double rV = rho_f * V_f, muLR = muL + muR;
+  double d = rV * idt_of(p);
+  double r = d * u_f;
+  // advection accumulated without its common factor -rho_f V_f
+  double s_adv = 0.0, t_vT = 0.0, d_visc = 0.0;
   #pragma unroll
   for (int a = 0; a < na; ++a) {
     // ---- advection (advective form, minmod limited linear upwind)
@@ -932,16 +932,15 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
     double uplus, uminus;
     if (ubar >= 0.0) { uplus = lim_up(us[1], us[2], us[3]); uminus = lim_up(us[0], us[1], us[2]); }
     else { uplus = lim_up(us[4], us[3], us[2]); uminus = lim_up(us[3], us[2], us[1]); }
-    t_adv = t_adv - rho_f * V_f * ubar * (uplus - uminus) * g.ih[a];
+    s_adv += ubar * (uplus - uminus) * g.ih[a];
     // ---- viscous
     if (a == c) {
       double ApL, ApR;
       if (g.axisym && c == 0) { ApL = areaN(g, 0, (L[0] + 0.5) * g.h[0]); ApR = areaN(g, 0, (R[0] + 0.5) * g.h[0]); }
       else if (g.axisym) { ApL = ApR = areaN(g, 1, r_f); }
       else { ApL = ApR = areaN(g, c, 0.0); }
-      double kR = muR * ApR * g.ih[c], kL = muL * ApL * g.ih[c];
-      double dR = (us[3] - us[2]) * g.ih[c], dL = (us[2] - us[1]) * g.ih[c];
-      t_vT = t_vT + muR * ApR * dR - muL * ApL * dL;
+      double kR = muR * (ApR * g.ih[c]), kL = muL * (ApL * g.ih[c]);
+      t_vT = t_vT + (kR * (us[3] - us[2]) - kL * (us[2] - us[1]));
       // coupling with the lower neighbour face (stored at this box cell)
       Cc[c][id] = (b[c] > 0) ? kL : 0.0;
       if (b[c] == 0 && g.bc[c][0] != BC_OPEN) {
@@ -961,15 +960,15 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
       if (g.axisym && a == 0) { App = areaN(g, 0, (f[0] + 1) * g.h[0]); Apm = areaN(g, 0, f[0] * g.h[0]); }
       else if (g.axisym) { App = Apm = areaN(g, 1, r_f); }
       else { App = Apm = areaN(g, a, 0.0); }
-      double mup = mu_edge(g, mu, L, R, a, 1), mum = mu_edge(g, mu, L, R, a, -1);
-      double kp = mup * App * g.ih[a], km = mum * Apm * g.ih[a];
+      double mup = mu_edge(g, mu, muLR, L, R, a, 1), mum = mu_edge(g, mu, muLR, L, R, a, -1);
+      double kp = mup * (App * g.ih[a]), km = mum * (Apm * g.ih[a]);
       const double* ua = U[a];
       int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
       La[a] += 1;
       Ra[a] += 1;
       double uaR_hi = ua[fidx(g, a, Ra[0], Ra[1], Ra[2])], uaL_hi = ua[fidx(g, a, La[0], La[1], La[2])];
       double uaR_lo = ua[fidx(g, a, R[0], R[1], R[2])], uaL_lo = ua[fidx(g, a, L[0], L[1], L[2])];
-      t_vT = t_vT + mup * App * (uaR_hi - uaL_hi) * g.ih[c] - mum * Apm * (uaR_lo - uaL_lo) * g.ih[c];
+      t_vT = t_vT + (mup * App * (uaR_hi - uaL_hi) - mum * Apm * (uaR_lo - uaL_lo)) * g.ih[c];
       Cc[a][id] = (b[a] > 0) ? km : 0.0;
       if (b[a] == 0 && (g.bc[a][0] == BC_WALL || g.bc[a][0] == BC_FORCED)) d_visc += 2.0 * km;
       if (b[a] == m[a] - 1 && (g.bc[a][1] == BC_WALL || g.bc[a][1] == BC_FORCED)) d_visc += 2.0 * kp;
@@ -985,9 +984,9 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
   }
   double xiL = xi[li], xiR = xi[ri];
   double raL = rhoL * alpha[li], raR = rhoR * alpha[ri];
-  double t_force = -A_f * (pr[ri] - pr[li]) - A_f * gx * (rhoR - rhoL) + A_f * 0.5 * (raL + raR) * (xiR - xiL);
+  double t_force = A_f * ((0.5 * (raL + raR) * (xiR - xiL) - gx * (rhoR - rhoL)) - (pr[ri] - pr[li]));
   d = d + d_visc;
-  r = r + t_adv + t_vT + t_force;
+  r = r - rV * s_adv + t_vT + t_force;
   Dg[id] = d;
   rhs[id] = r;
 }
@@ -1049,11 +1048,17 @@ __global__ void k_faces_to_box(Geo g, const double* u, double* x, double* uh, co
 
 // ============================================================== S8 - S10 projection
 // S = mdot (1/rho_G - 1/rho_L) - (1 - alpha)/rho_G [(rho_G^{n+1} - rho_G^n)/dt + vbar . grad rho_G^{n+1}]
+//     - E,  E = alpha/rho_L [(rho_L^{n+1} - rho_L^n)/dt + vbar . grad rho_L^{n+1}]
 // sum beta_f (dp_P - dp_N) + sum_open beta_b dp_P = (S V - sum u* A)/dt
+// The liquid's expansion term E (a temperature-dependent liquid density, rho_L^n = rho_L(T^n)
+// from T0, rho_L^{n+1} from T1) is formed when `expand` is given, and stored there: the next
+// step's alpha source subtracts it, so that in the liquid it cancels the divergence it puts
+// into the advecting velocity.
 template <int NA>
 __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo,
                                    const double* rgn, const double* u0, const double* u1, const double* u2,
                                    const double* us0, const double* us1, const double* us2, const double* rho,
+                                   const double* T1, const double* T0, double* expand,
                                    double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs,
                                    double* dp0) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1066,7 +1071,7 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
   const double* US[3] = {us0, us1, us2};
   double* C[3] = {c0, c1, c2};
   int ci[3] = {i, j, k};
-  double adv = 0.0;
+  double adv = 0.0, advl = 0.0;
   #pragma unroll
   for (int a = 0; a < na; ++a) {
     int hi[3] = {i, j, k};
@@ -1077,9 +1082,22 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
     qm[a] -= 1;
     double gr = (cellg(g, rgn, qp[0], qp[1], qp[2], R_ZG, 0, 0, 0, 0) - cellg(g, rgn, qm[0], qm[1], qm[2], R_ZG, 0, 0, 0, 0)) * (0.5 * g.ih[a]);
     adv = adv + vc * gr;
+    if (expand) {   // rho_L(T^{n+1}) with zero-gradient ghosts: the liquid density of the ghost temperature
+      double gl = (rho_liq(p, cellg(g, T1, qp[0], qp[1], qp[2], R_ZG, 0, 0, 0, 0)) -
+                   rho_liq(p, cellg(g, T1, qm[0], qm[1], qm[2], R_ZG, 0, 0, 0, 0))) * (0.5 * g.ih[a]);
+      advl = advl + vc * gl;
+    }
   }
   double rn = rgn[id], irn = rcp64(rn);
-  double s = mdot[id] * (irn - p.irho_l) - (1.0 - alpha[id]) * irn * ((rn - rgo[id]) * idt_of(p) + adv);
+  double s;
+  if (expand) {
+    const double rl1 = rho_liq(p, T1[id]), rl0 = rho_liq(p, T0[id]);
+    const double e = alpha[id] / rl1 * ((rl1 - rl0) * idt_of(p) + advl);
+    expand[id] = e;
+    s = mdot[id] * (irn - 1.0 / rl1) - (1.0 - alpha[id]) * irn * ((rn - rgo[id]) * idt_of(p) + adv) - e;
+  } else {
+    s = mdot[id] * (irn - p.irho_l) - (1.0 - alpha[id]) * irn * ((rn - rgo[id]) * idt_of(p) + adv);
+  }
   S[id] = s;
   double dg = 0.0, div = 0.0;
   double rP = rho[id];
@@ -1179,10 +1197,10 @@ __device__ __forceinline__ unsigned nonfinite_bits(double x) {
   return (unsigned)((__double_as_longlong(x) & 0x7FF0000000000000LL) == 0x7FF0000000000000LL);
 }
 template <int NA>
-__global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, const double* T, const double* mdot, const double* omega,
+__global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, Phys p, const double* alpha, const double* T, const double* mdot, const double* omega,
                        const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum,
                        double* pmax, unsigned* flags) {
-  double s[6] = {0, 0, 0, 0, 0, 0};
+  double s[7] = {0, 0, 0, 0, 0, 0, 0};
   double mx[3] = {0.0, -1e300, -1e300};
   unsigned bad = 0u;
   constexpr int na = NA;
@@ -1204,6 +1222,7 @@ __global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, con
       s[3] += gm * V;
     }
     s[4] += (1.0 - a) * rhoG[id] * omega[id] * V;
+    if (p.drl != 0.0) s[6] += rho_liq(p, T[id]) * a * V;   // the liquid mass (constant density: rho_l V_l)
     mx[1] = imax64(mx[1], a);
     mx[2] = imax64(mx[2], -a);
     int ci[3] = {i, j, k};
@@ -1233,7 +1252,7 @@ __global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, con
     }
   }
   if (__syncthreads_or((int)bad) && threadIdx.x == 0) atomicOr(flags, (unsigned)DROPLET_FLAG_NONFINITE);
-  block_sum_store<6>(s, psum);
+  block_sum_store<7>(s, psum);
   __syncthreads();
   block_max_store<3>(mx, pmax);
 }
@@ -1245,8 +1264,8 @@ __global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, const double* alpha, con
 // the first step).
 __global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, double* scal, int mode,
                               double co_hmin, double dt_max) {
-  double v[6], m[3];
-  block_reduce_partials<6, false>(psum, nblk, v);
+  double v[7], m[3];
+  block_reduce_partials<7, false>(psum, nblk, v);
   block_reduce_partials<3, true>(pmax, nblk, m);
   if (threadIdx.x == 0) {
     scal[SC_SUM_ALPHA_V] = v[0];
@@ -1254,6 +1273,7 @@ __global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, 
     scal[SC_SUM_TG] = v[2];
     scal[SC_SUM_G] = v[3];
     scal[SC_SUM_VAP] = v[4];
+    scal[SC_SUM_MLIQ] = v[6];
     scal[SC_VAPOUT] += v[5] * scal[SC_DT];
     scal[SC_MAXU] = m[0];
     scal[SC_AMAX] = m[1];
@@ -1272,10 +1292,10 @@ __global__ void k_diag_finish(const double* psum, const double* pmax, int nblk, 
 }
 
 // ============================================================== launch wrappers
-void L_evap_raw(cudaStream_t st, int grid, Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* mraw, int* adj, double* partials, unsigned* flags) {
+void L_evap_raw(cudaStream_t st, int grid, Geo g, Phys p, const double* alpha, const double* omega, const double* rhoG, const double* T, const double* u0, const double* u1, const double* u2, double* mraw, int* adj, double* partials, unsigned* flags) {
   ++g_launches;
-  if (nact(g) == 3) k_evap_raw<3><<<grid, TPB, 0, st>>>(g, p, alpha, omega, rhoG, u0, u1, u2, mraw, adj, partials, flags);
-  else k_evap_raw<2><<<grid, TPB, 0, st>>>(g, p, alpha, omega, rhoG, u0, u1, u2, mraw, adj, partials, flags);
+  if (nact(g) == 3) k_evap_raw<3><<<grid, TPB, 0, st>>>(g, p, alpha, omega, rhoG, T, u0, u1, u2, mraw, adj, partials, flags);
+  else k_evap_raw<2><<<grid, TPB, 0, st>>>(g, p, alpha, omega, rhoG, T, u0, u1, u2, mraw, adj, partials, flags);
 }
 
 void L_adv_faces(cudaStream_t st, int grid, Geo g, Phys p, int a, const double* as, const double* ua, double* FL, double* AF) {
@@ -1354,10 +1374,10 @@ void L_mom_scatter(cudaStream_t st, int grid, Geo g, Phys p, int c, const double
   else k_mom_scatter<2><<<grid, TPB, 0, st>>>(g, p, x, us);
 }
 
-void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo, const double* rgn, const double* u0, const double* u1, const double* u2, const double* us0, const double* us1, const double* us2, const double* rho, double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs, double* dp0) {
+void L_poisson_assemble(cudaStream_t st, int grid, Geo g, Phys p, const double* mdot, const double* alpha, const double* rgo, const double* rgn, const double* u0, const double* u1, const double* u2, const double* us0, const double* us1, const double* us2, const double* rho, const double* T1, const double* T0, double* expand, double* S, double* Dg, double* c0, double* c1, double* c2, double* rhs, double* dp0) {
   ++g_launches;
-  if (nact(g) == 3) k_poisson_assemble<3><<<grid, TPB, 0, st>>>(g, p, mdot, alpha, rgo, rgn, u0, u1, u2, us0, us1, us2, rho, S, Dg, c0, c1, c2, rhs, dp0);
-  else k_poisson_assemble<2><<<grid, TPB, 0, st>>>(g, p, mdot, alpha, rgo, rgn, u0, u1, u2, us0, us1, us2, rho, S, Dg, c0, c1, c2, rhs, dp0);
+  if (nact(g) == 3) k_poisson_assemble<3><<<grid, TPB, 0, st>>>(g, p, mdot, alpha, rgo, rgn, u0, u1, u2, us0, us1, us2, rho, T1, T0, expand, S, Dg, c0, c1, c2, rhs, dp0);
+  else k_poisson_assemble<2><<<grid, TPB, 0, st>>>(g, p, mdot, alpha, rgo, rgn, u0, u1, u2, us0, us1, us2, rho, T1, T0, expand, S, Dg, c0, c1, c2, rhs, dp0);
 }
 
 void L_correct(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* us, const double* dp, const double* rho, double* u) {
@@ -1386,10 +1406,10 @@ void L_correct_all(cudaStream_t st, Geo g, Phys p, double* const us[3], const do
   k_correct_all<<<b + lin_grid(g.N), TPB, 0, st>>>(g, p, a);
 }
 
-void L_diag(cudaStream_t st, int grid, Geo g, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax, unsigned* flags) {
+void L_diag(cudaStream_t st, int grid, Geo g, Phys p, const double* alpha, const double* T, const double* mdot, const double* omega, const double* rhoG, const double* u0, const double* u1, const double* u2, double* psum, double* pmax, unsigned* flags) {
   ++g_launches;
-  if (nact(g) == 3) k_diag<3><<<grid, TPB, 0, st>>>(g, alpha, T, mdot, omega, rhoG, u0, u1, u2, psum, pmax, flags);
-  else k_diag<2><<<grid, TPB, 0, st>>>(g, alpha, T, mdot, omega, rhoG, u0, u1, u2, psum, pmax, flags);
+  if (nact(g) == 3) k_diag<3><<<grid, TPB, 0, st>>>(g, p, alpha, T, mdot, omega, rhoG, u0, u1, u2, psum, pmax, flags);
+  else k_diag<2><<<grid, TPB, 0, st>>>(g, p, alpha, T, mdot, omega, rhoG, u0, u1, u2, psum, pmax, flags);
 }
 
 void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double* u, double* x, double* uh,

@@ -35,7 +35,7 @@ class DropletConfig(ctypes.Structure):
         ("seed", ctypes.c_ulonglong), ("T_perturb", _c_dbl),
         ("const_props_check", _c_int), ("physics_mask", _c_int), ("C_alpha", _c_dbl),
         ("mg_tile", _c_int * 2), ("wait_limit", _c_int), ("solver_select", _c_int), ("co_max", _c_dbl),
-        ("adv_scheme", _c_int),
+        ("adv_scheme", _c_int), ("drho_l_dT", _c_dbl),
     ]
 
 
@@ -50,7 +50,7 @@ class DropletDiag(ctypes.Structure):
 
 
 FIELDS = dict(alpha=0, T=1, omega=2, p=3, rhoG=4, u0=5, u1=6, u2=7, mdot=8, mraw=9, alpha_star=10, dp=11, S=12,
-              ustar0=13, ustar1=14, ustar2=15, rhoG_old=16)
+              ustar0=13, ustar1=14, ustar2=15, rhoG_old=16, expand=18)
 
 EXPORTS = ["droplet_init", "droplet_step", "droplet_diag", "droplet_field_size", "droplet_get_field",
            "droplet_set_field", "droplet_sync", "droplet_free", "droplet_strerror", "droplet_profile",

@@ -35,8 +35,8 @@ BASE = dict(
     dt=1e-5, precision=0,
     cg_rtol=1e-12, cg_maxit=400, helm_rtol=1e-13, helm_maxit=400,
     seed=20050286, T_perturb=0.0,
-    const_props_check=0, physics_mask=PHYS_ALL, C_alpha=1.0,
-    mg_tile=(0, 0), wait_limit=0, solver_select=0, co_max=0.0, adv_scheme=0,
+    const_props_check=0, physics_mask=PHYS_ALL, C_alpha=4.0,
+    mg_tile=(0, 0), wait_limit=0, solver_select=0, co_max=0.0, adv_scheme=0, drho_l_dT=0.0,
 )
 
 
@@ -62,8 +62,9 @@ def cfg1_d2law(**over):
     vapour from the quasi-steady spherical Stefan profile.  dt 1e-4 s (the
     Stefan velocity stays below 0.04 m/s: Courant number < 0.07 at 62.5 um),
     so that a few hundred steps run well past the transient r_s^2/D = 5 ms.
-    Interface compression C_alpha = 4: at C_alpha = 1 the outward Stefan flow
-    carries liquid into the first gas cells over tens of milliseconds."""
+    Interface compression C_alpha = 4 (the default of every case: at C_alpha = 1
+    the outward Stefan flow carries liquid into the first gas cells over tens of
+    milliseconds)."""
     base = dict(const_props_check=1, physics_mask=PHYS_EVAP | PHYS_SPECIES | PHYS_FLOW, dt=1e-4, C_alpha=4.0)
     base.update(over)
     return make(**base)

@@ -29,7 +29,7 @@ def _oracle_energy_system(cfg, G, alpha, T, omega):
     """diag, couplings and right-hand side of the energy system of one step from the
     given state (energy alone: no evaporation, no flow), as the oracle assembles them."""
     omega_p, rhoG_old = O.thermo_pin(cfg, G, alpha, T, omega)
-    pr = O.props(cfg, alpha, rhoG_old, omega_p)
+    pr = O.props(cfg, alpha, rhoG_old, omega_p, T)
     u = [np.zeros(O.fshape(G, a)) for a in range(3)]
     captured = {}
     solve = O.solve_box

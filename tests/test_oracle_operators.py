@@ -107,7 +107,7 @@ def _momentum_parts(n):
          _grid_eval(G, uz, (r_, z_), (G.xc[0], G.xf[1]))[:, :, None], None]
     st = O.init_state(cfg)
     st["u"] = u
-    pr = O.props(cfg, st["alpha"], st["rhoG"], st["omega"])
+    pr = O.props(cfg, st["alpha"], st["rhoG"], st["omega"], st["T"])
     mu = cfg["mu_g"]
     parts = {}
     O.momentum_predictor(cfg, G, st, pr, st["alpha"], 1e300, parts=parts)

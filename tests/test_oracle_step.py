@@ -445,8 +445,8 @@ def test_geometric_advection_translates_a_plane_exactly():
 def test_geometric_advection_keeps_the_interface_sharp():
     """A droplet carried by a uniform oblique flow in 3D: after 40 steps the geometric
     scheme keeps the band of partial cells within 10 % of its initial size (measured
-    401 -> 417 cells) and the droplet's volume; the compressive scheme widens it more
-    (452)."""
+    401 -> 417 cells) and the droplet's volume; the compressive scheme at C_alpha = 1
+    widens it more (452)."""
     cfg = W.make(geom=1, n=(24, 24, 24), L=(1.5e-3,) * 3, xc=(0.6e-3, 0.6e-3, 0.6e-3), D0=0.6e-3,
                  g=(0.0, 0.0, 0.0), adv_scheme=1)
     G = Grid(cfg)
@@ -457,8 +457,80 @@ def test_geometric_advection_keeps_the_interface_sharp():
     ag, af = a0.copy(), a0.copy()
     for _ in range(40):
         ag, _, _, _ = O.alpha_advection_geometric(cfg, G, ag, u, dt)
-        af, _, _, _ = O.alpha_advection(dict(cfg, adv_scheme=0), G, af, u, dt)
+        af, _, _, _ = O.alpha_advection(dict(cfg, adv_scheme=0, C_alpha=1.0), G, af, u, dt)
     mg = int(np.count_nonzero((ag > 1e-6) & (ag < 1 - 1e-6)))
     mf = int(np.count_nonzero((af > 1e-6) & (af < 1 - 1e-6)))
     assert mg <= 1.1 * mixed0 and mg < mf
     assert float(np.sum(ag * G.V)) == pytest.approx(float(np.sum(a0 * G.V)), rel=1e-12)
+
+
+def _centroid_run(xi0, steps=500):
+    """Centroid height (in cells) of a 1 mm droplet under normal gravity, evaporation off,
+    every 100 steps of 4e-5 s, and the largest face velocity at the end."""
+    cfg = W.make(n=(32, 64, 1), L=(2e-3, 4e-3, 0.0), xc=(0.0, 2e-3, 0.0), D0=1e-3, g=(0.0, -9.81, 0.0),
+                 physics_mask=W.PHYS_FLOW, T_amb=300.0, xi0=xi0, dt=4e-5)
+    G = Grid(cfg)
+    st = O.init_state(cfg)
+
+    def zc(a):
+        return float(np.sum(a * G.V * G.xc[1][None, :, None]) / np.sum(a * G.V)) / G.h[1]
+    z0, drift = zc(st["alpha"]), []
+    for k in range(steps):
+        st = O.step(cfg, st)
+        if k % 100 == 99:
+            drift.append(zc(st["alpha"]) - z0)
+    return np.array(drift), max(float(np.abs(st["u"][a]).max()) for a in G.act)
+
+
+@pytest.mark.slow
+def test_centripetal_force_holds_the_droplet_and_a_weak_one_lets_it_fall():
+    """Sec. 5 (Eqs. magneticfield, magneticpotential): the potential xi = xi0 D_f/(2r)
+    holds a droplet against gravity for xi0 = 1 m2/s2, while below about 0.35 the
+    droplet falls.  Over 20 ms (32 x 64, 1 mm droplet, evaporation off): with xi0 = 1
+    the centroid stays within two cells (it sags and oscillates by about one cell as
+    gravity sets in) and the flow stays weak; with xi0 = 0.2 it falls more than eight
+    cells, every 4 ms further down (measured 12.7 cells, near a drag-limited rate)."""
+    held, u_held = _centroid_run(1.0)
+    fall, u_fall = _centroid_run(0.2)
+    assert np.abs(held).max() < 2.0 and u_held < 0.06, (held, u_held)
+    assert fall[-1] < -8.0 and np.all(np.diff(fall) < -1.0), fall
+    assert u_fall > 2.0 * u_held
+
+
+def _expansion_run(n, scheme=0, drho=-0.9, t_end=0.01):
+    """A 1 mm droplet at 300 K heated by a 500 K gas, no evaporation: only the liquid's
+    thermal expansion (rho_L(T), Eqs. alphasource and pequation) moves its volume."""
+    dt = 1e-4 * 32 / n
+    cfg = W.make(n=(n, 2 * n, 1), L=(2e-3, 4e-3, 0.0), xc=(0.0, 2e-3, 0.0), D0=1e-3, T_amb=500.0,
+                 physics_mask=W.PHYS_ENERGY | W.PHYS_FLOW, dt=dt, drho_l_dT=drho, adv_scheme=scheme)
+    G = Grid(cfg)
+    st = O.init_state(cfg)
+    d0 = O.diagnostics(cfg, st)
+    for _ in range(int(round(t_end / dt))):
+        st = O.step(cfg, st)
+    d = O.diagnostics(cfg, st)
+    a = st["alpha"]
+    T_liq = float(np.sum(st["T"] * a * G.V) / np.sum(a * G.V))
+    # volume growth that would keep the liquid's mass at its mean temperature
+    want = float(th.rho_liquid(cfg, cfg["T_drop"]) / th.rho_liquid(cfg, T_liq)) - 1.0
+    return d["V_l"] / d0["V_l"] - 1.0, d["M_liq"] / d0["M_liq"] - 1.0, want, T_liq
+
+
+def test_thermal_expansion_conserves_the_liquid_mass_under_refinement():
+    """Variable liquid density (reading of Sec. 2.7 with Eqs. alphasource and pequation):
+    the heated droplet's volume grows and its mass sum rho_L(T) alpha V stays.  The mass
+    drift is a discretisation error of the product rule (rho_L alpha advected as alpha
+    times rho_L): it falls under refinement, 16 -> 32 -> 64 cells per radius, by more
+    than a factor 4 each time, to under 3% of the volume change that mass conservation
+    requires.  Dropping the expansion term leaves the volume fixed and the drift equal to
+    minus that change; a wrong sign doubles it; both fail."""
+    runs = [_expansion_run(n) for n in (16, 32, 64)]
+    drift = [abs(r[1]) for r in runs]
+    assert drift[1] < drift[0] / 4 and drift[2] < drift[1] / 4, drift
+    growth, _, want, T_liq = runs[2]
+    assert T_liq > 301.0 and want > 1e-3, (T_liq, want)
+    assert drift[2] < 0.03 * want, (drift, want)
+    assert abs(growth - want) < 0.1 * want, (growth, want)
+    # constant density: the volume stays up to the clipping
+    g0, m0, _, _ = _expansion_run(32, drho=0.0)
+    assert abs(g0) < 1e-6 and abs(m0) < 1e-6, (g0, m0)
