@@ -299,28 +299,63 @@ int droplet_profile_read(droplet_ctx* ctx, int kclass, double* ms_total, long lo
 /* Number of kernel launches the library has issued for this context so far. */
 int droplet_launch_count(droplet_ctx* ctx, long long* launches);
 
-/* Hand-written discrete adjoint of the step without flow (physics_mask =
- * EVAP | ENERGY | SPECIES: evaporation flux with the K normalisation of
- * Eq. alphafunction, alpha source of Eq. alphasource, energy Eq. Teqn, species
- * Eq. speciesequation with the liquid pinned to the Raoult saturation value,
- * gas density Eq. densitygas; FP64, Raoult, natural boundaries, one droplet).
+/* Hand-written discrete adjoint of the step.  Two forms:
+ *  - without flow (physics_mask = EVAP | ENERGY | SPECIES): evaporation flux with
+ *    the K normalisation of Eq. alphafunction, alpha source of Eq. alphasource,
+ *    energy Eq. Teqn, species Eq. speciesequation with the liquid pinned to the
+ *    Raoult saturation value, gas density Eq. densitygas; natural boundaries;
+ *  - with flow (all four physics terms, adv_scheme 0, either boundary mode): also
+ *    the convective part of the evaporation flux, the FCT advection of alpha
+ *    (Eq. advection), convection in energy and species, the momentum predictor
+ *    with buoyancy and the centripetal force (Eqs. NavierStokesModified,
+ *    magneticfield), the Stefan source and the variable-density pressure equation
+ *    (Eq. pequation) and the velocity correction; the ambient temperature then
+ *    also enters through the energy equation's inflow boundary values.
+ * Both: FP64, Raoult, one droplet, constant liquid density, fixed dt.
  * Starting from the initial state of droplet_init (step 0) it runs n_steps
  * forward, keeping the state every ckpt_every steps, and returns
  *   *J = (1/n_steps) sum_n mdot_tot^n   (mean evaporation rate, kg/s)
  * and, through a reverse sweep that recomputes each segment from its
- * checkpoint, the derivatives of J with respect to T_amb (which enters through
- * the initial temperature profile), D_g, and the initial temperature field
- * (dJ_dT0, host array of nT0 = cell-count doubles).  Any gradient pointer may be
- * NULL; with all three NULL only J is computed.  The branch decisions of the
- * forward step (interface cells, adjacent cells, the mdot cap, clipping,
- * pinned cells) are held fixed.  The context is left at the state after
- * n_steps.  Errors: DROPLET_ERR_ARG (another physics mask, precision,
- * equilibrium model or boundary mode, a batch, or step != 0), DROPLET_ERR_SIZE,
- * DROPLET_ERR_NOMEM (work memory: 3 N doubles per checkpoint plus
- * 3 N (ckpt_every + 18) doubles), DROPLET_ERR_NOT_CONVERGED (a solve reached its
- * cap; results still returned). */
+ * checkpoint, the derivatives of J with respect to T_amb (through the initial
+ * temperature profile and, with flow, the boundary values), D_g, and the
+ * initial temperature field (dJ_dT0, host array of nT0 = cell-count doubles).
+ * Any gradient pointer may be NULL; with all three NULL only J is computed.  The
+ * branch decisions of the forward step (interface cells, adjacent cells, the
+ * mdot cap, upwind sides, minmod, van Leer and limiter choices, clipping, pinned
+ * cells) are held fixed.  Every linear system is symmetric: its adjoint is the
+ * same system solved again (to a relative residual of 1e-14) for the adjoint
+ * right-hand side.  The context is left at the state after n_steps.  Errors:
+ * DROPLET_ERR_ARG (another physics mask, precision, equilibrium model,
+ * adv_scheme, co_max or drho_l_dT, a batch, or step != 0), DROPLET_ERR_SIZE,
+ * DROPLET_ERR_NOMEM (work memory: one state per checkpoint plus
+ * ckpt_every + 1 states and about 40 cell and 12 face arrays with flow),
+ * DROPLET_ERR_NOT_CONVERGED (a solve reached its cap; results still returned). */
 int droplet_adjoint(droplet_ctx* ctx, int n_steps, int ckpt_every, double* J, double* dJ_dTamb, double* dJ_dDg,
                     double* dJ_dT0, size_t nT0);
+
+/* One step of the flow adjoint, for checking it against finite differences: from
+ * the context's current state s (which must satisfy the flow form's conditions
+ * above, at any step) it takes one step s' = F(s) with the solves started from s
+ * alone (as after droplet_set_field) and returns
+ *   lam_prev = (dF/ds)^T lam_next + mdot_weight d(mdot_tot)/ds
+ * and dpar[0], dpar[1] = the same derivative of <lam_next, F(s)> + mdot_weight
+ * mdot_tot with respect to T_amb (boundary values; the initial field is not part of
+ * a step) and D_g.  State vectors (host, n doubles): alpha, T, omega, p_rgh (each N
+ * cells, field order), then the face velocities of each active direction
+ * (droplet_field_size of u0, u1, u2).  dpar may be NULL.  The context is left at
+ * s'.  Errors as droplet_adjoint; DROPLET_ERR_SIZE when n is not the state size. */
+int droplet_adjoint_vjp(droplet_ctx* ctx, const double* lam_next, double* lam_prev, size_t n, double mdot_weight,
+                        double* dpar);
+
+/* Forward check of the flow adjoint's stage formulas: takes one step from the
+ * current state (as droplet_adjoint_vjp does) and evaluates, for each stage, the
+ * formulas the adjoint differentiates; rel[k] (k < 20, nrel >= 20) receives
+ * max |formula - forward kernel| / max |forward kernel| for: the FCT face fluxes
+ * (low order, antidiffusive), alpha^L, R+, R-, alpha^{n+1}, m_raw; the diagonal,
+ * right-hand side and couplings of the energy, species, momentum (all components)
+ * and pressure systems; and the corrected velocities.  The context is left after
+ * the step.  Errors as droplet_adjoint_vjp. */
+int droplet_adjoint_check(droplet_ctx* ctx, double* rel, int nrel);
 
 /* Checkpoint / resume.  droplet_save writes, for every droplet, its config, time,
  * step count, the accumulated diagnostics (clipped volume, vapour outflow) and the

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libdroplet.so")
 BUILD = os.path.join(ROOT, "_build")
-SOURCES = ["capi.cu", "step_kernels.cu", "step_mixed.cu", "solver.cu", "adjoint.cu"]
+SOURCES = ["capi.cu", "step_kernels.cu", "step_mixed.cu", "solver.cu", "adjoint.cu", "adjoint_flow.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INC, "-I", CSRC]
 

@@ -17,15 +17,6 @@
 
 namespace dg {
 
-// d Y_eq / d T for the Raoult model (0 where the mole fraction is clamped)
-__device__ __forceinline__ double dYeq_dT(const Phys& p, double T) {
-  double y = psat(p, T) / p.P;
-  if (y > Y_CLAMP) return 0.0;
-  double dy = y * (p.Lv * p.M_l / R_GAS) / (T * T);
-  double den = y * p.M_l + (1.0 - y) * p.M_g;
-  return dy * p.M_l * p.M_g / (den * den);
-}
-
 __device__ __forceinline__ double harm_(double x, double y) { return 2.0 * x * y / (x + y); }
 // d/dx of the harmonic mean 2xy/(x+y)
 __device__ __forceinline__ double dharm_dx(double x, double y) { return 2.0 * y * y / ((x + y) * (x + y)); }
@@ -378,6 +369,10 @@ void L_adj_source(cudaStream_t st, const Geo& g, const Phys& p, const double* aA
   ++g_launches, k_adj_props_source<<<nb, TPB, 0, st>>>(g, p, aA, alpha_n, alpha_new, astar, rgn, mraw, scal, rhobar,
                                                       kbar, cpbar, Dbar, jweight, aAn, rgbar, mdbar, part);
   ++g_launches, k_adj_K<<<nb, TPB, 0, st>>>(g, p, part, nb, alpha_n, mraw, scal, mdbar, mrbar, aAn, acc_out);
+}
+void L_adj_K(cudaStream_t st, const Geo& g, const Phys& p, const double* part, int nblk, const double* alpha_n,
+             const double* mraw, const double* scal, const double* mdbar, double* mrbar, double* aAn, double* acc_out) {
+  ++g_launches, k_adj_K<<<nblk, TPB, 0, st>>>(g, p, part, nblk, alpha_n, mraw, scal, mdbar, mrbar, aAn, acc_out);
 }
 void L_adj_evap(cudaStream_t st, const Geo& g, const Phys& p, const double* alpha_n, const double* wp,
                 const double* rgn, const int* adj, const double* mrbar, double* aAn, double* wpbar, double* rgbar,

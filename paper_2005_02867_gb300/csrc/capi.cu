@@ -994,11 +994,14 @@ extern "C" int droplet_set_field(droplet_ctx* cc, int droplet, int field_id, con
 extern "C" void droplet_free(droplet_ctx* c) { free_ctx(c); }
 
 // ---------------------------------------------------------------- adjoint (no flow)
+static int adjoint_flow(droplet_ctx* cc, int n_steps, int ckpt_every, double* J, double* dJ_dTamb, double* dJ_dDg,
+                        double* dJ_dT0, size_t nT0);
 extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, double* J, double* dJ_dTamb,
                                double* dJ_dDg, double* dJ_dT0, size_t nT0) {
   if (!cc || cc->d.size() != 1 || n_steps < 1 || ckpt_every < 1 || !J) return DROPLET_ERR_ARG;
   dctx* x = cc->d[0];
   const droplet_config& cf = x->cfg;
+  if (cf.physics_mask & DROPLET_PHYS_FLOW) return adjoint_flow(cc, n_steps, ckpt_every, J, dJ_dTamb, dJ_dDg, dJ_dT0, nT0);
   if (cf.physics_mask != (DROPLET_PHYS_EVAP | DROPLET_PHYS_ENERGY | DROPLET_PHYS_SPECIES) || cf.precision != 0 ||
       cf.eq_model != 0 || cf.const_props_check != 0 || cf.bc_mode != 0 || cf.co_max != 0.0 || cf.drho_l_dT != 0.0 ||
       x->step != 0)
@@ -1135,6 +1138,447 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
     CKR(cudaMemcpy(x->scal + SC_TIME, &tn, sizeof(double), cudaMemcpyHostToDevice));
   }
   x->step = n_steps;
+  if (rc) return rc;
+  return nc ? DROPLET_ERR_NOT_CONVERGED : 0;
+}
+
+// ---------------------------------------------------------------- adjoint with flow
+// The state of a step as the flow adjoint keeps it: alpha, T, omega, p_rgh (cells), then the
+// face velocities of each active direction.
+static long long flow_state_size(const dctx* x) {
+  long long s = 4 * x->g.N;
+  for (int a = 0; a < nact(x->g); ++a) s += nfaces(x->g, a);
+  return s;
+}
+static void flow_save(dctx* x, double* dst) {
+  const long long N = x->g.N;
+  cudaStream_t st = x->st;
+  cudaMemcpyAsync(dst, x->alpha, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(dst + N, x->T, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(dst + 2 * N, x->omega, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(dst + 3 * N, x->pr, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  long long o = 4 * N;
+  for (int a = 0; a < nact(x->g); ++a) {
+    cudaMemcpyAsync(dst + o, x->u[a], sizeof(double) * nfaces(x->g, a), cudaMemcpyDeviceToDevice, st);
+    o += nfaces(x->g, a);
+  }
+}
+// load a state; S0 then re-evaluates rho_G from it and the solves start from it alone, so
+// that a recomputed step repeats the first pass bit for bit
+static void flow_load(dctx* x, const double* src) {
+  const long long N = x->g.N;
+  cudaStream_t st = x->st;
+  cudaMemcpyAsync(x->alpha, src, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(x->T, src + N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(x->omega, src + 2 * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(x->pr, src + 3 * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  long long o = 4 * N;
+  for (int a = 0; a < nact(x->g); ++a) {
+    cudaMemcpyAsync(x->u[a], src + o, sizeof(double) * nfaces(x->g, a), cudaMemcpyDeviceToDevice, st);
+    o += nfaces(x->g, a);
+  }
+  cudaMemsetAsync(x->dirty, 0xff, sizeof(int), st);
+}
+static int flow_step_alone(dctx* x, int* nc) {
+  cudaMemsetAsync(x->scal + SC_HIST, 0, sizeof(double), x->st);
+  return one_step(x, nc);
+}
+
+// Work memory of the flow adjoint: the adjoints of every stage input (AdjArr order), of the
+// state before and after the step, and the scratch of the adjoint solves
+struct FlowWork {
+  double* lam[J_COUNT] = {};
+  double *lA = nullptr, *lT = nullptr, *lW = nullptr, *lP = nullptr, *lU[3] = {nullptr, nullptr, nullptr};
+  double *lT1 = nullptr, *lW1 = nullptr;     // adjoints of T^{n+1}, omega^{n+1} within the step
+  const double *sA = nullptr, *sT = nullptr, *sW = nullptr, *sP = nullptr, *sU[3] = {nullptr, nullptr, nullptr};
+  double *wp = nullptr, *mu = nullptr, *bxa = nullptr, *bmu = nullptr, *mrbar = nullptr, *scr1 = nullptr,
+         *scr2 = nullptr, *part = nullptr, *acc = nullptr;
+  std::vector<double*> owned;
+  int get(double** q, long long n) {
+    if (cudaMalloc((void**)q, sizeof(double) * (size_t)(n > 0 ? n : 1)) != cudaSuccess) return DROPLET_ERR_NOMEM;
+    owned.push_back(*q);
+    return 0;
+  }
+  int alloc(const Geo& g) {
+    const long long N = g.N;
+    const int na = nact(g);
+    int rc = 0;
+    for (int q = 0; q < J_COUNT && !rc; ++q) {
+      int a = -1;
+      if (q >= J_U0 && q <= J_U2) a = q - J_U0;
+      if (q >= J_FL0 && q <= J_FL2) a = q - J_FL0;
+      if (q >= J_AF0 && q <= J_AF2) a = q - J_AF0;
+      if (q >= J_US0 && q <= J_US2) a = q - J_US0;
+      if (a >= na) continue;
+      rc = get(&lam[q], a >= 0 ? nfaces(g, a) : N);
+    }
+    double** cells[] = {&lA, &lT, &lW, &lP, &lT1, &lW1, &wp, &mu, &bxa, &bmu, &mrbar, &scr1, &scr2};
+    for (auto q : cells)
+      if (!rc) rc = get(q, N);
+    for (int a = 0; a < na && !rc; ++a) rc = get(&lU[a], nfaces(g, a));
+    if (!rc) rc = get(&part, RED_BLOCKS * 4);
+    if (!rc) rc = get(&acc, AC_COUNT);
+    return rc;
+  }
+  void release() {
+    for (auto q : owned) cudaFree(q);
+    owned.clear();
+  }
+  // the state n pointers into a saved state
+  void point_state(const Geo& g, const double* s) {
+    const long long N = g.N;
+    sA = s; sT = s + N; sW = s + 2 * N; sP = s + 3 * N;
+    long long o = 4 * N;
+    for (int a = 0; a < 3; ++a) {
+      sU[a] = a < nact(g) ? s + o : s + 4 * N;
+      if (a < nact(g)) o += nfaces(g, a);
+    }
+  }
+};
+
+// Reverse of the step n -> n+1 just re-run from the state w.s*: turns the adjoints of the
+// state after the step (w.lA, lT, lW, lP, lU) into those of the state before it, adds
+// jweight sum mdot V (the step's share of J) and the parameter adjoints into w.acc.
+static int flow_reverse(dctx* x, FlowWork& w, double jweight, int* nc) {
+  Geo& g = x->g;
+  Phys& p = x->p;
+  cudaStream_t st = x->st;
+  const long long N = g.N;
+  const int na = nact(g);
+  const int gc = lin_grid(N);
+  const double ADJ_RTOL = 1e-14;
+  for (int q = 0; q < J_COUNT; ++q) {
+    if (!w.lam[q]) continue;
+    int a = -1;
+    if (q >= J_U0 && q <= J_U2) a = q - J_U0;
+    if (q >= J_FL0 && q <= J_FL2) a = q - J_FL0;
+    if (q >= J_AF0 && q <= J_AF2) a = q - J_AF0;
+    if (q >= J_US0 && q <= J_US2) a = q - J_US0;
+    cudaMemsetAsync(w.lam[q], 0, sizeof(double) * (a >= 0 ? nfaces(g, a) : N), st);
+  }
+  cudaMemcpyAsync(w.lam[J_ALPHA1], w.lA, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(w.lam[J_P_N], w.lP, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(w.lam[J_DP], w.lP, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(w.lT1, w.lT, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(w.lW1, w.lW, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  L_adj_pin(st, g, p, w.sA, w.sT, w.sW, w.wp);
+  FlowIn in;
+  in.alpha_n = w.sA; in.T_n = w.sT; in.wp = w.wp; in.p_n = w.sP;
+  for (int a = 0; a < 3; ++a) {
+    const int aa = a < na ? a : 0;
+    in.u[a] = w.sU[aa];
+    in.FL[a] = x->FL[aa]; in.AF[a] = x->AF[aa]; in.us[a] = x->us[aa];
+  }
+  in.astar = x->astar; in.aL = x->aL; in.Rp = x->Rp; in.Rm = x->Rm;
+  in.alpha1 = x->alpha; in.rho = x->rho; in.mu = x->mu; in.kc = x->kc; in.cp = x->cp; in.Dm = x->Dm;
+  in.mdot = x->mdot; in.rgo = x->rhoG_old; in.rgn = x->rhoG; in.yq = x->yq; in.dp = x->dp; in.xi = x->xi;
+  in.adj = x->adj;
+  AdjT T;
+  for (int q = 0; q < J_COUNT; ++q) T.lam[q] = w.lam[q];
+  T.acc = w.acc;
+  double* const bc2 = na == 3 ? x->bc[2] : x->bc[0];
+  const double* sU2 = na == 3 ? w.sU[2] : w.sU[0];
+  const double* us2 = na == 3 ? x->us[2] : x->us[0];
+  SolveStats ss;
+  int rc;
+  // S10: u^{n+1} = u* - dt grad(dp)/rho_f, p^{n+1} = p^n + dp
+  L_adjf_correct(st, g, p, in, T, w.lU);
+  // S8, S9: the pressure system (symmetric), solved again for the adjoint
+  BoxSys bs;
+  bs.D = x->bD; bs.b = x->brhs; bs.x = x->bx;
+  for (int a = 0; a < 3; ++a) { bs.c[a] = a < na ? x->bc[a] : nullptr; bs.m[a] = g.n[a]; }
+  bs.N = N;
+  L_poisson_assemble(st, gc, g, p, x->mdot, x->alpha, x->rhoG_old, x->rhoG, w.sU[0], w.sU[1], sU2, x->us[0],
+                     x->us[1], us2, x->rho, x->T, x->T, nullptr, w.scr1, x->bD, x->bc[0], x->bc[1], bc2, x->brhs,
+                     w.scr2);
+  cudaMemcpyAsync(x->brhs, w.lam[J_DP], sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(x->bx, 0, sizeof(double) * N, st);
+  rc = x->solver.pcg_mg(bs, ADJ_RTOL, 4 * x->cfg.cg_maxit, 0, &ss);
+  if ((rc = soft_status(rc, nc))) return rc;
+  cudaMemcpyAsync(w.mu, x->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  L_adjf_poisson(st, g, p, in, T, w.mu, x->dp);
+  // S7: each velocity component's Helmholtz system
+  for (int c = 0; c < na; ++c) {
+    int m[3] = {g.n[0], g.n[1], g.n[2]};
+    m[c] -= 1;
+    const long long nbx = (long long)m[0] * m[1] * m[2];
+    BoxSys bm = bs;
+    for (int a = 0; a < 3; ++a) bm.m[a] = m[a];
+    bm.N = nbx;
+    L_mom_assemble(st, lin_grid(nbx), g, p, c, w.sU[0], w.sU[1], sU2, x->rho, x->mu, w.sP, x->alpha, x->xi, x->bD,
+                   x->bc[0], x->bc[1], bc2, x->brhs, nullptr);
+    cudaMemsetAsync(x->brhs, 0, sizeof(double) * nbx, st);
+    L_adjf_box_rhs(st, g, c, w.lam[J_US0 + c], x->brhs, w.lam[J_U0 + c]);
+    cudaMemsetAsync(x->bx, 0, sizeof(double) * nbx, st);
+    rc = x->solver.pcg_jacobi(bm, ADJ_RTOL, 4 * x->cfg.helm_maxit, &ss);
+    if ((rc = soft_status(rc, nc))) return rc;
+    cudaMemcpyAsync(w.bmu, x->bx, sizeof(double) * nbx, cudaMemcpyDeviceToDevice, st);
+    L_adjf_box_gather(st, g, c, x->us[c], w.bxa);
+    L_adjf_mom(st, g, p, in, T, c, w.bmu, w.bxa);
+  }
+  // rho_G^{n+1} (used by the Stefan source only)
+  L_adjf_rhoG(st, g, p, x->T, x->omega, w.lam[J_RGN], w.lT1, w.lW1);
+  // S6 species, then the pinned rows' saturation values
+  L_scalar_assemble(st, gc, g, p, 1, w.wp, x->rho, x->cp, x->kc, x->Dm, x->mdot, w.sU[0], w.sU[1], sU2, x->alpha,
+                    x->yq, 0.0, x->bD, x->bc[0], x->bc[1], bc2, x->brhs, nullptr);
+  cudaMemcpyAsync(x->brhs, w.lW1, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(x->bx, 0, sizeof(double) * N, st);
+  rc = x->solver.pcg_jacobi(bs, ADJ_RTOL, 4 * x->cfg.helm_maxit, &ss);
+  if ((rc = soft_status(rc, nc))) return rc;
+  cudaMemcpyAsync(w.mu, x->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  L_adjf_scalar(st, g, p, in, T, 1, w.mu, x->omega);
+  L_adjf_yq(st, g, p, x->T, x->alpha, w.lam[J_YQ], w.lT1);
+  // S5 energy
+  L_scalar_assemble(st, gc, g, p, 0, w.sT, x->rho, x->cp, x->kc, x->Dm, x->mdot, w.sU[0], w.sU[1], sU2, x->alpha,
+                    x->yq, p.T_amb, x->bD, x->bc[0], x->bc[1], bc2, x->brhs, nullptr);
+  cudaMemcpyAsync(x->brhs, w.lT1, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemsetAsync(x->bx, 0, sizeof(double) * N, st);
+  rc = x->solver.pcg_jacobi(bs, ADJ_RTOL, 4 * x->cfg.helm_maxit, &ss);
+  if ((rc = soft_status(rc, nc))) return rc;
+  cudaMemcpyAsync(w.mu, x->bx, sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  L_adjf_scalar(st, g, p, in, T, 0, w.mu, x->T);
+  // S4, S3, S2 with J, S1, S0
+  L_adjf_props(st, g, p, in, T);
+  L_adjf_fct(st, g, p, in, T);
+  L_adjf_source(st, g, p, in, T, x->mraw, x->scal, jweight, w.mrbar, w.part);
+  L_adjf_mraw(st, g, p, in, T, w.mrbar);
+  L_adj_thermo(st, g, p, w.sA, w.sT, w.wp, x->rhoG_old, w.lam[J_RGO], w.lam[J_WP], w.lam[J_T_N], w.lW);
+  cudaMemcpyAsync(w.lA, w.lam[J_ALPHA_N], sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(w.lT, w.lam[J_T_N], sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  cudaMemcpyAsync(w.lP, w.lam[J_P_N], sizeof(double) * N, cudaMemcpyDeviceToDevice, st);
+  for (int a = 0; a < na; ++a)
+    cudaMemcpyAsync(w.lU[a], w.lam[J_U0 + a], sizeof(double) * nfaces(g, a), cudaMemcpyDeviceToDevice, st);
+  CKR(cudaGetLastError());
+  return 0;
+}
+
+// the configurations the flow adjoint differentiates
+static bool flow_adjoint_ok(const dctx* x) {
+  const droplet_config& cf = x->cfg;
+  return cf.physics_mask == (DROPLET_PHYS_EVAP | DROPLET_PHYS_ENERGY | DROPLET_PHYS_SPECIES | DROPLET_PHYS_FLOW) &&
+         cf.precision == 0 && cf.eq_model == 0 && cf.const_props_check == 0 && cf.co_max == 0.0 &&
+         cf.drho_l_dT == 0.0 && cf.adv_scheme == 0;
+}
+
+static int adjoint_flow(droplet_ctx* cc, int n_steps, int ckpt_every, double* J, double* dJ_dTamb, double* dJ_dDg,
+                        double* dJ_dT0, size_t nT0) {
+  dctx* x = cc->d[0];
+  if (!flow_adjoint_ok(x) || x->step != 0) return DROPLET_ERR_ARG;
+  Geo& g = x->g;
+  Phys& p = x->p;
+  const long long N = g.N;
+  if (dJ_dT0 && nT0 != (size_t)N) return DROPLET_ERR_SIZE;
+  cudaStream_t st = x->st;
+  CKR(cudaStreamSynchronize(cc->st));
+  CKR(cudaStreamSynchronize(st));
+  const int nseg = (n_steps + ckpt_every - 1) / ckpt_every;
+  const long long S = flow_state_size(x);
+  double *ck = nullptr, *seg = nullptr, *fin = nullptr;
+  FlowWork w;
+  auto cleanup = [&]() { cudaFree(ck); cudaFree(seg); cudaFree(fin); w.release(); };
+  if (cudaMalloc(&ck, sizeof(double) * S * nseg) != cudaSuccess ||
+      cudaMalloc(&seg, sizeof(double) * S * (ckpt_every + 1)) != cudaSuccess ||
+      cudaMalloc(&fin, sizeof(double) * S) != cudaSuccess || w.alloc(g)) {
+    cleanup();
+    return DROPLET_ERR_NOMEM;
+  }
+  cudaMemsetAsync(w.acc, 0, sizeof(double) * AC_COUNT, st);
+  const double jweight = (g.axisym ? 2.0 * M_PI : 1.0) / n_steps;
+  int nc = 0, rc = 0;
+  for (int n = 0; n < n_steps && !rc; ++n) {
+    if (n % ckpt_every == 0) flow_save(x, ck + S * (n / ckpt_every));
+    rc = flow_step_alone(x, &nc);
+    L_acc_J(st, x->scal, jweight, w.acc);
+  }
+  flow_save(x, fin);
+  CKR(cudaStreamSynchronize(st));
+  double host_acc[AC_COUNT];
+  CKR(cudaMemcpy(host_acc, w.acc, sizeof(double) * AC_COUNT, cudaMemcpyDeviceToHost));
+  *J = host_acc[AC_J];
+  if (!rc && (dJ_dTamb || dJ_dDg || dJ_dT0)) {
+    const int na = nact(g);
+    cudaMemsetAsync(w.lA, 0, sizeof(double) * N, st);
+    cudaMemsetAsync(w.lT, 0, sizeof(double) * N, st);
+    cudaMemsetAsync(w.lW, 0, sizeof(double) * N, st);
+    cudaMemsetAsync(w.lP, 0, sizeof(double) * N, st);
+    for (int a = 0; a < na; ++a) cudaMemsetAsync(w.lU[a], 0, sizeof(double) * nfaces(g, a), st);
+    for (int sgi = nseg - 1; sgi >= 0 && !rc; --sgi) {
+      const int n0 = sgi * ckpt_every, n1 = n0 + ckpt_every < n_steps ? n0 + ckpt_every : n_steps;
+      flow_load(x, ck + S * sgi);
+      for (int n = n0; n < n1 && !rc; ++n) {
+        flow_save(x, seg + S * (n - n0));
+        if (n + 1 < n1) rc = flow_step_alone(x, &nc);
+      }
+      for (int n = n1 - 1; n >= n0 && !rc; --n) {
+        const double* sn = seg + S * (n - n0);
+        flow_load(x, sn);
+        rc = flow_step_alone(x, &nc);   // leaves step n's intermediates and state n+1
+        if (rc) break;
+        w.point_state(g, sn);
+        rc = flow_reverse(x, w, jweight, &nc);
+      }
+    }
+    if (!rc) {
+      L_adj_tamb(st, g, p, w.lT, w.part, w.acc);
+      CKR(cudaStreamSynchronize(st));
+      CKR(cudaMemcpy(host_acc, w.acc, sizeof(double) * AC_COUNT, cudaMemcpyDeviceToHost));
+      if (dJ_dDg) *dJ_dDg = host_acc[AC_DGAS] * (1.0e5 / x->cfg.P);
+      if (dJ_dTamb) *dJ_dTamb = host_acc[AC_TAMB] + host_acc[AC_TAMB_BC];
+      if (dJ_dT0) CKR(cudaMemcpy(dJ_dT0, w.lT, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    }
+  }
+  flow_load(x, fin);
+  CKR(cudaStreamSynchronize(st));
+  cleanup();
+  {
+    const double tn = n_steps * p.dt;
+    CKR(cudaMemcpy(x->scal + SC_TIME, &tn, sizeof(double), cudaMemcpyHostToDevice));
+  }
+  x->step = n_steps;
+  if (rc) return rc;
+  return nc ? DROPLET_ERR_NOT_CONVERGED : 0;
+}
+
+extern "C" int droplet_adjoint_vjp(droplet_ctx* cc, const double* lam_next, double* lam_prev, size_t n,
+                                   double mdot_weight, double* dpar) {
+  if (!cc || cc->d.size() != 1 || !lam_next || !lam_prev) return DROPLET_ERR_ARG;
+  dctx* x = cc->d[0];
+  if (!flow_adjoint_ok(x)) return DROPLET_ERR_ARG;
+  const long long S = flow_state_size(x);
+  if (n != (size_t)S) return DROPLET_ERR_SIZE;
+  Geo& g = x->g;
+  const long long N = g.N;
+  const int na = nact(g);
+  cudaStream_t st = x->st;
+  CKR(cudaStreamSynchronize(cc->st));
+  double* s0 = nullptr;
+  FlowWork w;
+  if (cudaMalloc(&s0, sizeof(double) * S) != cudaSuccess || w.alloc(g)) {
+    cudaFree(s0);
+    w.release();
+    return DROPLET_ERR_NOMEM;
+  }
+  cudaMemsetAsync(w.acc, 0, sizeof(double) * AC_COUNT, st);
+  flow_save(x, s0);
+  // the adjoint of the state after the step, in the packed layout
+  double* dst[8] = {w.lA, w.lT, w.lW, w.lP, w.lU[0], w.lU[1], w.lU[2], nullptr};
+  long long sz[7] = {N, N, N, N, na > 0 ? nfaces(g, 0) : 0, nfaces(g, 1), na == 3 ? nfaces(g, 2) : 0};
+  long long o = 0;
+  for (int q = 0; q < 4 + na; ++q) {
+    CKR(cudaMemcpyAsync(dst[q], lam_next + o, sizeof(double) * sz[q], cudaMemcpyHostToDevice, st));
+    o += sz[q];
+  }
+  int nc = 0;
+  flow_load(x, s0);
+  int rc = flow_step_alone(x, &nc);
+  if (!rc) {
+    w.point_state(g, s0);
+    rc = flow_reverse(x, w, mdot_weight * (g.axisym ? 2.0 * M_PI : 1.0), &nc);
+  }
+  if (!rc) {
+    CKR(cudaStreamSynchronize(st));
+    o = 0;
+    for (int q = 0; q < 4 + na; ++q) {
+      CKR(cudaMemcpy(lam_prev + o, dst[q], sizeof(double) * sz[q], cudaMemcpyDeviceToHost));
+      o += sz[q];
+    }
+    double host_acc[AC_COUNT];
+    CKR(cudaMemcpy(host_acc, w.acc, sizeof(double) * AC_COUNT, cudaMemcpyDeviceToHost));
+    if (dpar) {
+      dpar[0] = host_acc[AC_TAMB_BC];
+      dpar[1] = host_acc[AC_DGAS] * (1.0e5 / x->cfg.P);
+    }
+  }
+  cudaFree(s0);
+  w.release();
+  ++x->step;
+  if (rc) return rc;
+  return nc ? DROPLET_ERR_NOT_CONVERGED : 0;
+}
+
+extern "C" int droplet_adjoint_check(droplet_ctx* cc, double* rel, int nrel) {
+  if (!cc || cc->d.size() != 1 || !rel || nrel < CHK_COUNT) return DROPLET_ERR_ARG;
+  dctx* x = cc->d[0];
+  if (!flow_adjoint_ok(x)) return DROPLET_ERR_ARG;
+  Geo& g = x->g;
+  Phys& p = x->p;
+  const long long N = g.N;
+  const int na = nact(g);
+  cudaStream_t st = x->st;
+  CKR(cudaStreamSynchronize(cc->st));
+  const long long S = flow_state_size(x);
+  double* s0 = nullptr;
+  double* wp = nullptr;
+  double* scr = nullptr;
+  unsigned long long* chk = nullptr;
+  auto cleanup = [&]() { cudaFree(s0); cudaFree(wp); cudaFree(scr); cudaFree(chk); };
+  if (cudaMalloc(&s0, sizeof(double) * S) != cudaSuccess || cudaMalloc(&wp, sizeof(double) * N) != cudaSuccess ||
+      cudaMalloc(&scr, sizeof(double) * 2 * N) != cudaSuccess ||
+      cudaMalloc(&chk, sizeof(unsigned long long) * 2 * CHK_COUNT) != cudaSuccess) {
+    cleanup();
+    return DROPLET_ERR_NOMEM;
+  }
+  cudaMemsetAsync(chk, 0, sizeof(unsigned long long) * 2 * CHK_COUNT, st);
+  flow_save(x, s0);
+  int nc = 0;
+  flow_load(x, s0);
+  int rc = flow_step_alone(x, &nc);
+  if (!rc) {
+    const double* sA = s0;
+    const double* sT = s0 + N;
+    const double* sW = s0 + 2 * N;
+    const double* sP = s0 + 3 * N;
+    const double* sU[3];
+    long long o = 4 * N;
+    for (int a = 0; a < 3; ++a) {
+      sU[a] = a < na ? s0 + o : s0 + 4 * N;
+      if (a < na) o += nfaces(g, a);
+    }
+    L_adj_pin(st, g, p, sA, sT, sW, wp);
+    FlowIn in;
+    in.alpha_n = sA; in.T_n = sT; in.wp = wp; in.p_n = sP;
+    for (int a = 0; a < 3; ++a) {
+      const int aa = a < na ? a : 0;
+      in.u[a] = sU[aa];
+      in.FL[a] = x->FL[aa]; in.AF[a] = x->AF[aa]; in.us[a] = x->us[aa];
+    }
+    in.astar = x->astar; in.aL = x->aL; in.Rp = x->Rp; in.Rm = x->Rm;
+    in.alpha1 = x->alpha; in.rho = x->rho; in.mu = x->mu; in.kc = x->kc; in.cp = x->cp; in.Dm = x->Dm;
+    in.mdot = x->mdot; in.rgo = x->rhoG_old; in.rgn = x->rhoG; in.yq = x->yq; in.dp = x->dp; in.xi = x->xi;
+    in.adj = x->adj;
+    double* const bc2 = na == 3 ? x->bc[2] : x->bc[0];
+    double* const C[3] = {x->bc[0], x->bc[1], na == 3 ? x->bc[2] : nullptr};
+    L_chk_cells(st, g, p, in, x->mraw, chk);
+    L_chk_faces(st, g, p, in, x->u, chk);
+    for (int mode = 0; mode < 2; ++mode) {
+      L_scalar_assemble(st, lin_grid(N), g, p, mode, mode == 0 ? sT : wp, x->rho, x->cp, x->kc, x->Dm, x->mdot, sU[0],
+                        sU[1], sU[2], x->alpha, x->yq, mode == 0 ? p.T_amb : 0.0, x->bD, x->bc[0], x->bc[1], bc2,
+                        x->brhs, nullptr);
+      L_chk_rows(st, g, p, in, mode, x->bD, C, x->brhs, chk);
+    }
+    L_poisson_assemble(st, lin_grid(N), g, p, x->mdot, x->alpha, x->rhoG_old, x->rhoG, sU[0], sU[1], sU[2], x->us[0],
+                       x->us[1], na == 3 ? x->us[2] : x->us[0], x->rho, x->T, x->T, nullptr, scr, x->bD, x->bc[0],
+                       x->bc[1], bc2, x->brhs, scr + N);
+    L_chk_rows(st, g, p, in, 2, x->bD, C, x->brhs, chk);
+    for (int c = 0; c < na; ++c) {
+      int m[3] = {g.n[0], g.n[1], g.n[2]};
+      m[c] -= 1;
+      L_mom_assemble(st, lin_grid((long long)m[0] * m[1] * m[2]), g, p, c, sU[0], sU[1], sU[2], x->rho, x->mu, sP,
+                     x->alpha, x->xi, x->bD, x->bc[0], x->bc[1], bc2, x->brhs, nullptr);
+      L_chk_rows(st, g, p, in, 3 + c, x->bD, C, x->brhs, chk);
+    }
+    CKR(cudaStreamSynchronize(st));
+    unsigned long long h[2 * CHK_COUNT];
+    CKR(cudaMemcpy(h, chk, sizeof(h), cudaMemcpyDeviceToHost));
+    for (int q = 0; q < CHK_COUNT; ++q) {
+      double d, r;
+      memcpy(&d, &h[2 * q], sizeof(double));
+      memcpy(&r, &h[2 * q + 1], sizeof(double));
+      rel[q] = r > 0.0 ? d / r : d;
+    }
+  }
+  cleanup();
+  ++x->step;
   if (rc) return rc;
   return nc ? DROPLET_ERR_NOT_CONVERGED : 0;
 }

@@ -1,6 +1,7 @@
 // Declarations shared by the translation units of the droplet library.
 #pragma once
 #include "common.cuh"
+#include "adjoint_ad.cuh"
 
 #include <vector>
 
@@ -133,7 +134,9 @@ void L_faces_to_box(cudaStream_t st, int grid, const Geo& g, int c, const double
                     const double* scal);
 
 // ---- adjoint of the step without flow (adjoint.cu)
-enum { AC_DGAS = 0, AC_J, AC_TAMB, AC_COUNT };
+// accumulators: gas diffusivity, J, ambient temperature through the initial field, and
+// through the boundary values of the energy equation (flow only)
+enum { AC_DGAS = 0, AC_J, AC_TAMB, AC_TAMB_BC, AC_COUNT };
 void L_adj_pin(cudaStream_t st, const Geo& g, const Phys& p, const double* alpha, const double* T,
                const double* omega, double* wp);
 void L_adj_rhs(cudaStream_t st, const Geo& g, const double* abar, const double* alpha_new, int pinned_rows,
@@ -156,7 +159,59 @@ void L_adj_thermo(cudaStream_t st, const Geo& g, const Phys& p, const double* al
                   const double* wp, const double* rgn, const double* rgbar, const double* wpbar, double* Tnbar,
                   double* aW);
 void L_acc_J(cudaStream_t st, const double* scal, double weight, double* acc_out);
+// K = S1/S2, mdot = K f m_raw: adjoint of m_raw and of alpha^n through f, from mdbar and the
+// block sums {D_gas, mdbar f m_raw, m_raw V, f m_raw V} in part
+void L_adj_K(cudaStream_t st, const Geo& g, const Phys& p, const double* part, int nblk, const double* alpha_n,
+             const double* mraw, const double* scal, const double* mdbar, double* mrbar, double* aAn, double* acc_out);
 void L_adj_tamb(cudaStream_t st, const Geo& g, const Phys& p, const double* T0bar, double* part, double* acc_out);
+
+// ---- adjoint of the step with flow (adjoint_flow.cu)
+// The forward step's state n and intermediates, as the adjoint reads them (the forward
+// step n -> n+1 just re-run; u, p of state n kept aside)
+struct FlowIn {
+  const double *alpha_n, *T_n, *wp, *u[3], *p_n;
+  const double *astar, *aL, *FL[3], *AF[3], *Rp, *Rm;
+  const double *alpha1, *rho, *mu, *kc, *cp, *Dm, *mdot, *rgo, *rgn, *yq, *us[3], *dp, *xi;
+  const int* adj;
+};
+// each launcher adds sum_j w_j d(out_j)/d(input) into the adjoints T of its inputs; the
+// weights come from the arrays named (see adjoint_flow.cu)
+void L_adjf_correct(cudaStream_t st, const Geo& g, const Phys& p, const FlowIn& in, const AdjT& T,
+                    double* const lU[3]);
+void L_adjf_poisson(cudaStream_t st, const Geo& g, const Phys& p, const FlowIn& in, const AdjT& T, const double* mu,
+                    const double* x);
+void L_adjf_mom(cudaStream_t st, const Geo& g, const Phys& p, const FlowIn& in, const AdjT& T, int c,
+                const double* mu, const double* x);
+void L_adjf_scalar(cudaStream_t st, const Geo& g, const Phys& p, const FlowIn& in, const AdjT& T, int mode,
+                   const double* mu, const double* x);
+void L_adjf_fct(cudaStream_t st, const Geo& g, const Phys& p, const FlowIn& in, const AdjT& T);
+void L_adjf_mraw(cudaStream_t st, const Geo& g, const Phys& p, const FlowIn& in, const AdjT& T, const double* mrbar);
+// box <-> faces of direction c: the interior faces' values into box order, and the adjoint
+// of u* into the box right-hand side (an open boundary face copies its interior neighbour)
+void L_adjf_box_gather(cudaStream_t st, const Geo& g, int c, const double* faces, double* box);
+void L_adjf_box_rhs(cudaStream_t st, const Geo& g, int c, const double* lus, double* box, double* lun);
+// pointwise stages: rho_G^{n+1}, the pinned saturation values, the mixture properties, and
+// the alpha source with J, the mdot cap and the block sums of the K normalisation
+void L_adjf_rhoG(cudaStream_t st, const Geo& g, const Phys& p, const double* T1, const double* w1, const double* lrgn,
+                 double* lT1, double* lW1);
+void L_adjf_yq(cudaStream_t st, const Geo& g, const Phys& p, const double* T1, const double* alpha1,
+               const double* lyq, double* lT1);
+void L_adjf_props(cudaStream_t st, const Geo& g, const Phys& p, const FlowIn& in, const AdjT& T);
+void L_adjf_source(cudaStream_t st, const Geo& g, const Phys& p, const FlowIn& in, const AdjT& T,
+                   const double* mraw, const double* scal, double jweight, double* mrbar, double* part);
+
+// forward check of the adjoint's stage formulas: max |formula - forward value| and max
+// |forward value| per slot (a slot's mom / energy / species / pressure entry is followed
+// by its rhs and coupling entries)
+enum { CHK_FL = 0, CHK_AF, CHK_AL, CHK_RP, CHK_RM, CHK_ALPHA1, CHK_MRAW, CHK_ENERGY, CHK_ENERGY_R, CHK_ENERGY_C,
+       CHK_SPECIES, CHK_SPECIES_R, CHK_SPECIES_C, CHK_MOM, CHK_MOM_R, CHK_MOM_C, CHK_POISSON, CHK_POISSON_R,
+       CHK_POISSON_C, CHK_CORRECT, CHK_COUNT };
+void L_chk_cells(cudaStream_t st, const Geo& g, const Phys& p, const FlowIn& in, const double* mraw,
+                 unsigned long long* chk);
+void L_chk_faces(cudaStream_t st, const Geo& g, const Phys& p, const FlowIn& in, double* const unew[3],
+                 unsigned long long* chk);
+void L_chk_rows(cudaStream_t st, const Geo& g, const Phys& p, const FlowIn& in, int kind, const double* D,
+                double* const C[3], const double* rhs, unsigned long long* chk);
 
 // ---- linear solvers (solver.cu)
 // Box operator on dims m: y_P = D_P x_P + sum_a [c_a[P](x_P - x_{P-e_a}) + c_a[P+e_a](x_P - x_{P+e_a})],

@@ -55,7 +55,7 @@ FIELDS = dict(alpha=0, T=1, omega=2, p=3, rhoG=4, u0=5, u1=6, u2=7, mdot=8, mraw
 EXPORTS = ["droplet_init", "droplet_step", "droplet_diag", "droplet_field_size", "droplet_get_field",
            "droplet_set_field", "droplet_sync", "droplet_free", "droplet_strerror", "droplet_profile",
            "droplet_profile_read", "droplet_launch_count", "droplet_box_solve", "droplet_box_solve_noalloc", "droplet_save", "droplet_load", "droplet_adjoint",
-           "droplet_round_f32", "droplet_rcp_f64", "droplet_fp64_rate"]
+           "droplet_adjoint_vjp", "droplet_adjoint_check", "droplet_round_f32", "droplet_rcp_f64", "droplet_fp64_rate"]
 
 NOALLOC_MAX_UNKNOWNS = 262144
 
@@ -105,6 +105,8 @@ def load_library(path=LIBPATH):
     lib.droplet_box_solve_noalloc.argtypes = BOX
     D = ctypes.POINTER(_c_dbl)
     lib.droplet_adjoint.argtypes = [P, _c_int, _c_int, D, D, D, D, ctypes.c_size_t]
+    lib.droplet_adjoint_vjp.argtypes = [P, D, D, ctypes.c_size_t, _c_dbl, D]
+    lib.droplet_adjoint_check.argtypes = [P, D, _c_int]
     lib.droplet_round_f32.argtypes = [P, P, P, ctypes.c_size_t]
     lib.droplet_rcp_f64.argtypes = [P, P, ctypes.c_size_t]
     lib.droplet_fp64_rate.argtypes = [ctypes.POINTER(_c_dbl)]
@@ -299,7 +301,8 @@ def droplet_load(h, path):
 
 def droplet_adjoint(h, n_steps, ckpt_every, gradients=True):
     """J (mean evaporation rate) and, if gradients, (dJ/dT_amb, dJ/dD_g, dJ/dT0 as a
-    flat array).  The context must be at step 0 with physics_mask = EVAP|ENERGY|SPECIES."""
+    flat array).  The context must be at step 0, with physics_mask EVAP|ENERGY|SPECIES
+    or all four terms (the adjoint with flow)."""
     J = _c_dbl()
     if not gradients:
         rc = load_library().droplet_adjoint(ctypes.c_void_p(h), int(n_steps), int(ckpt_every), ctypes.byref(J),
@@ -316,6 +319,50 @@ def droplet_adjoint(h, n_steps, ckpt_every, gradients=True):
     if rc and rc != ERR_NOT_CONVERGED:
         raise DropletError(rc, "droplet_adjoint")
     return J.value, gTa.value, gDg.value, gT0
+
+
+STATE_FIELDS = ("alpha", "T", "omega", "p")
+
+
+def state_size(h):
+    """Length of the packed state of the flow adjoint: alpha, T, omega, p, then the face
+    velocities of each active direction."""
+    n = 4 * droplet_field_size(h, "T")
+    for a in range(3):
+        try:
+            n += droplet_field_size(h, "u%d" % a)
+        except DropletError:
+            break
+    return n
+
+
+def droplet_adjoint_vjp(h, lam_next, mdot_weight=0.0):
+    """One step of the flow adjoint: (lam_prev, dpar) for the step from the current state,
+    lam_next and lam_prev packed as state_size describes; dpar = (T_amb, D_g)."""
+    lam_next = np.ascontiguousarray(lam_next, dtype=np.float64)
+    out = np.empty_like(lam_next)
+    dpar = np.zeros(2, dtype=np.float64)
+    P = ctypes.POINTER(_c_dbl)
+    rc = load_library().droplet_adjoint_vjp(ctypes.c_void_p(h), lam_next.ctypes.data_as(P), out.ctypes.data_as(P),
+                                            lam_next.size, float(mdot_weight), dpar.ctypes.data_as(P))
+    if rc and rc != ERR_NOT_CONVERGED:
+        raise DropletError(rc, "droplet_adjoint_vjp")
+    return out, dpar
+
+
+CHECK_NAMES = ("FL", "AF", "aL", "Rp", "Rm", "alpha1", "mraw", "energy_D", "energy_rhs", "energy_c", "species_D",
+               "species_rhs", "species_c", "mom_D", "mom_rhs", "mom_c", "p_D", "p_rhs", "p_c", "correct")
+
+
+def droplet_adjoint_check(h):
+    """Relative differences between the flow adjoint's stage formulas and the forward
+    kernels over one step from the current state, by stage name."""
+    rel = np.zeros(len(CHECK_NAMES), dtype=np.float64)
+    rc = load_library().droplet_adjoint_check(ctypes.c_void_p(h), rel.ctypes.data_as(ctypes.POINTER(_c_dbl)),
+                                              len(CHECK_NAMES))
+    if rc and rc != ERR_NOT_CONVERGED:
+        raise DropletError(rc, "droplet_adjoint_check")
+    return dict(zip(CHECK_NAMES, rel.tolist()))
 
 
 def droplet_fp64_rate():

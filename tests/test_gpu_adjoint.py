@@ -124,13 +124,6 @@ def test_autograd_function(D):
     assert np.allclose(dT0.grad.numpy(), gT0, rtol=1e-12, atol=0)
 
 
-def test_adjoint_rejects_flow(D):
-    sim = D.Droplet(W.cfg5_axisym_128x256(n=(32, 64, 1), L=(2e-3, 4e-3, 0.0), xc=(0.0, 2e-3, 0.0)))
-    with pytest.raises(D.DropletError):
-        D.droplet_adjoint(sim.h, 5, 5)
-    sim.close()
-
-
 def test_config5_adjoint_500_steps(D):
     """Config 5 grid (128 x 256, 4 x 8 mm, D0 = 1 mm, 773 K, 1 bar), 500 FP64 steps
     with checkpoints every 50, without flow: scalar gradients against central
