@@ -430,9 +430,9 @@ class Droplet:
 
 def evaporation_rate_function():
     """torch.autograd.Function J(T_amb, D_g, dT0): mean evaporation rate over
-    n_steps of the step without flow, from the initial state with T0 =
-    profile(T_amb) + dT0.  Backward returns the hand-written adjoint's gradient,
-    computed (with checkpointing) when the forward runs."""
+    n_steps of the step (with or without flow, as cfg's physics mask says), from the
+    initial state with T0 = profile(T_amb) + dT0.  Backward returns the hand-written
+    adjoint's gradient, computed (with checkpointing) when the forward runs."""
     import torch
 
     class EvaporationRate(torch.autograd.Function):

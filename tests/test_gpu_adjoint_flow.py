@@ -249,6 +249,26 @@ def test_config5_flow_adjoint_500_steps(D):
         assert g == pytest.approx(fd, rel=1e-4), (key, g, fd)
 
 
+def test_autograd_function_with_flow(D):
+    import torch
+    F = D.evaporation_rate_function()
+    cfg = small()
+    Ta = torch.tensor(cfg["T_amb"], dtype=torch.float64, requires_grad=True)
+    Dg = torch.tensor(cfg["D_g"], dtype=torch.float64, requires_grad=True)
+    dT0 = torch.zeros(32 * 64, dtype=torch.float64, requires_grad=True)
+    J = F.apply(Ta, Dg, dT0, cfg, 10, 5)
+    J.backward()
+    sim = D.Droplet(cfg)
+    J2, gTa, gDg, gT0 = D.droplet_adjoint(sim.h, 10, 5)
+    sim.close()
+    assert float(J.detach()) == pytest.approx(J2, rel=1e-14)
+    # (the reverse sweep adds into the adjoints with atomics, so two runs agree to the
+    # rounding of their summation orders)
+    assert float(Ta.grad) == pytest.approx(gTa, rel=1e-10)
+    assert float(Dg.grad) == pytest.approx(gDg, rel=1e-10)
+    assert np.allclose(dT0.grad.numpy(), gT0, rtol=1e-9, atol=1e-9 * np.abs(gT0).max())
+
+
 def test_flow_adjoint_rejects_unsupported_forms(D):
     for over in (dict(adv_scheme=1), dict(precision=1), dict(co_max=0.2)):
         sim = D.Droplet(small(**over))
