@@ -264,7 +264,10 @@ int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0,
  *   0 MG_SMOOTH   red-black Gauss-Seidel half sweep    [(2.5 + d) N w; FP64: (2d + 1) N/2 instructions]
  *   1 SPMV        CG operator application + dot        [(3 + d) N w; FP64: (2d + 2) N instructions,
  *                                                        the diagonal form a_P x_P - sum c x_N]
- *   2 UPDATE      CG x/r update + dot                  [5 N 8 or 8 N 4; FP64: 5 N (Jacobi), 3 N]
+ *   2 UPDATE      CG x/r update + dot                  [Jacobi 8 N w (x, r in and out, p, Ap,
+ *                                                        1/diag in, z out); MG-PCG 6 N 8 (+ 4 N
+ *                                                        with an FP32 hierarchy); FP64: 5 N
+ *                                                        (Jacobi), 3 N]
  *   3 MG_RESTRICT residual + restriction               [(3 + d) N w + N/2^d w; FP64: (4d + 3) N]
  *   4 MG_PROLONG  injection prolongation               [(2 + 1/2^d) N w; FP64: N]
  *   5 MOM_ASSEMBLE momentum system assembly            [(12 + 2d) N 8]

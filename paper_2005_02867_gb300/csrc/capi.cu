@@ -129,6 +129,24 @@ static void make_geo(const droplet_config& c, Geo& g) {
   g.vol3 = g.h[0] * g.h[1] * g.h[2];
   for (int a = 0; a < 3; ++a) g.area3[a] = g.vol3 * g.ih[a];
   g.gthr = 1e-8 / g.hmin;
+  g.hvol3 = 0.5 * g.vol3;
+  for (int a = 0; a < 3; ++a) {
+    g.aih[a] = g.area3[a] * g.ih[a];
+    g.aih2[a] = 2.0 * g.aih[a];
+    g.qaih[a] = 0.25 * g.aih[a];
+    g.qih[a] = 0.25 * g.ih[a];
+    for (int b = 0; b < 3; ++b) g.qvt[b][a] = 0.25 * g.area3[a] * g.ih[b];
+  }
+  {
+    const int na = g.axisym ? 2 : 3;
+    for (int a = 0; a < na; ++a) {
+      g.gh[a] = c.g[a] * g.h[a];
+      if (c.g[a] != 0.0) g.gmask |= 1 << a;
+    }
+    for (int b = 0; b < na; ++b)
+      for (int a = 0; a < na; ++a)
+        if (a != b && (g.gmask >> a & 1)) g.gxc[b] += 0.5 * g.gh[a];
+  }
   g.s = g.axisym ? 1 : 2;
   int inlet = c.bc_mode == 1 ? BC_FORCED : BC_OPEN;
   if (g.axisym) {

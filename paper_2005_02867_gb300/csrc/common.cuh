@@ -34,6 +34,16 @@ struct Geo {
   double gthr;       // 1e-8 / h_min: |grad alpha| above it marks an interface cell
   double vol3;       // 3D: cell volume h0 h1 h2, and face areas vol3 / h_a, formed on the host in
   double area3[3];   // the order the kernels used (the same values, no FP64 work per reference)
+  // 3D momentum assembly constants, formed on the host: half the cell volume, area3[a] / h_a,
+  // 0.25 area3[a] / h_a and 0.25 area3[a] / h_c (the quarter of the edge viscosity's mean
+  // folded in; a product with a power of two is exact)
+  double hvol3, aih[3], aih2[3], qaih[3], qvt[3][3];   // aih2 = 2 area3[a] / h_a
+  double qih[3];     // 0.25 / h_a: the mean of four face velocities folded into the advection
+  // gravity potential g . x at a face of direction c: gxc[c] + sum over the axes a of gmask
+  // (those with g_a != 0) of gh[a] f_a, f the face's integer coordinates, gh[a] = g_a h_a,
+  // gxc[c] = sum over a != c of g_a h_a / 2
+  double gh[3], gxc[3];
+  int gmask;
   long long N;       // number of cells (< 2^31)
 };
 
@@ -263,6 +273,11 @@ __device__ __forceinline__ double minmod(double x, double y) {
   const long long ax = bx & 0x7FFFFFFFFFFFFFFFLL, ay = by & 0x7FFFFFFFFFFFFFFFLL;
   const bool same = (bx ^ by) >= 0 && ax != 0 && ay != 0;
   return same ? (ax <= ay ? x : y) : 0.0;
+}
+// x and y the same pure phase value: both encodings that of +0 or both that of 1
+__device__ __forceinline__ bool pure_pair(double x, double y) {
+  const long long bx = __double_as_longlong(x);
+  return bx == __double_as_longlong(y) && (bx == 0 || bx == 0x3FF0000000000000LL);
 }
 __device__ __forceinline__ double lim_up(double uu, double u, double d) { return u + 0.5 * minmod(u - uu, d - u); }
 __device__ __forceinline__ double van_leer(double uu, double u, double d) {

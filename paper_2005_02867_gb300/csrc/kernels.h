@@ -290,6 +290,10 @@ class Solver {
   static constexpr long long PERSIST_PCG_MAX_CELLS = 1LL << 30;
   int rb = RED_BLOCKS;              // block cap of the reduction kernels (tuned for batches)
   Prof* prof = nullptr;
+  // grid of the launched CG kernels (k_pcg_init, k_spmv_dot, k_update and those paired with
+  // them, cg_grid): the reduction cap, and at most the CG_BLOCKS_PER_SM blocks per SM their
+  // register bound keeps resident, so that the grid-stride loops run as one full wave
+  static constexpr int CG_BLOCKS_PER_SM = 6;
 
  private:
   template <typename F>
@@ -298,6 +302,7 @@ class Solver {
   template <typename T>
   int pcg_persist(const BoxSys* s, int K, double rtol, int maxit, const RecordSpec* recs, SolveStats* out);
   int persist_blocks(bool f32);
+  int cg_grid(long long N);
   RecordSpec take_record();
   double* rec_scal = nullptr;
   int rec_its = 0, rec_res = -1, rec_acc = 0;

@@ -62,25 +62,70 @@ __device__ __forceinline__ void box_row(const int m[3], const T* D, const T* con
   dtot = dt;
 }
 
+// y = A x at cell id in the diagonal form a_P x_P - sum c x_N, a_P = D + sum of the
+// adjacent couplings formed once per solve: one multiply and one FMA per neighbour, against
+// a subtraction and an FMA per neighbour in the difference form (the binary64 pipe is the
+// bound of an FP64 stencil on GB300; the bytes are the same, a_P read in place of D)
+__device__ __forceinline__ double box_offdiag(const int m[3], const double* const c[3], const double* x,
+                                              long long id, int i, int j, int k, double y) {
+  const int q[3] = {i, j, k};
+  const long long st[3] = {1, (long long)m[0], (long long)m[0] * m[1]};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!c[a] || m[a] < 2) continue;
+    if (q[a] > 0) y = fma(-c[a][id], x[id - st[a]], y);
+    if (q[a] < m[a] - 1) y = fma(-c[a][id + st[a]], x[id + st[a]], y);
+  }
+  return y;
+}
+
+__device__ __forceinline__ double box_row_diag(const int m[3], const double* ad, const double* const c[3],
+                                               const double* x, long long id, int i, int j, int k) {
+  return box_offdiag(m, c, x, id, i, j, k, ad[id] * x[id]);
+}
+
+// the total diagonal D + sum of the adjacent couplings, summed in the order of box_row
+__device__ __forceinline__ double box_diag_total(const int m[3], const double* D, const double* const c[3],
+                                                 long long id, int i, int j, int k) {
+  double dt = D[id];
+  const int q[3] = {i, j, k};
+  const long long st[3] = {1, (long long)m[0], (long long)m[0] * m[1]};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (!c[a] || m[a] < 2) continue;
+    if (q[a] > 0) dt += c[a][id];
+    if (q[a] < m[a] - 1) dt += c[a][id + st[a]];
+  }
+  return dt;
+}
+
 // ---------------------------------------------------------------- CG kernels
 // (adg, when given, receives the total diagonal D + sum of adjacent couplings, for the
 // diagonal form of the operator in k_spmv_dot)
-__global__ void k_pcg_init(BoxV A, const double* b, const double* x, double* r, double* z, double* p, double* idg,
+__global__ void __launch_bounds__(TPB, Solver::CG_BLOCKS_PER_SM) k_pcg_init(BoxV A, const double* b, const double* x, double* r, double* z, double* p, double* idg,
                            int jacobi, double* part, double* adg = nullptr) {
   double acc[3] = {0, 0, 0};   // r.z, b.b, r.r
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < A.N; id += (long long)gridDim.x * blockDim.x) {
     int i, j, k;
     bdecomp(A.m, id, i, j, k);
     double ax, dt;
-    box_row<double, double>(A.m, A.D, A.c, x, id, i, j, k, ax, dt);
-    if (adg) adg[id] = dt;
+    if (adg) {
+      // the diagonal form of the iterations (the residual recurrence then starts from the
+      // operator it continues with), and the reciprocal of the diagonal by rcp64: fewer
+      // binary64 instructions than the difference form and a division
+      dt = box_diag_total(A.m, A.D, A.c, id, i, j, k);
+      adg[id] = dt;
+      ax = box_offdiag(A.m, A.c, x, id, i, j, k, dt * x[id]);
+    } else {
+      box_row<double, double>(A.m, A.D, A.c, x, id, i, j, k, ax, dt);
+    }
     double rr = b[id] - ax;
     r[id] = rr;
     double bb = b[id];
     acc[1] += bb * bb;
     acc[2] += rr * rr;
     if (jacobi) {
-      double iv = 1.0 / dt;
+      double iv = adg ? rcp64(dt) : 1.0 / dt;
       idg[id] = iv;
       double zz = iv * rr;
       z[id] = zz;
@@ -114,27 +159,9 @@ __global__ void k_fin_init(const double* part, int nblk, double* sc, int* done, 
   }
 }
 
-// y = A x at cell id in the diagonal form a_P x_P - sum c x_N, a_P = D + sum of the
-// adjacent couplings formed once per solve: one multiply and one FMA per neighbour, against
-// a subtraction and an FMA per neighbour in the difference form (the binary64 pipe is the
-// bound of an FP64 stencil on GB300; the bytes are the same, a_P read in place of D)
-__device__ __forceinline__ double box_row_diag(const int m[3], const double* ad, const double* const c[3],
-                                               const double* x, long long id, int i, int j, int k) {
-  double y = ad[id] * x[id];
-  const int q[3] = {i, j, k};
-  const long long st[3] = {1, (long long)m[0], (long long)m[0] * m[1]};
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (!c[a] || m[a] < 2) continue;
-    if (q[a] > 0) y = fma(-c[a][id], x[id - st[a]], y);
-    if (q[a] < m[a] - 1) y = fma(-c[a][id + st[a]], x[id + st[a]], y);
-  }
-  return y;
-}
-
 // Ap = A p and p.Ap; with a counter (cnt != null) the last block also sets alpha = rz / pAp.
 // adg (the total diagonal from k_pcg_init) selects the diagonal form of the operator.
-__global__ void k_spmv_dot(BoxV A, const double* p, double* Ap, double* part, const int* done, double* sc,
+__global__ void __launch_bounds__(TPB, Solver::CG_BLOCKS_PER_SM) k_spmv_dot(BoxV A, const double* p, double* Ap, double* part, const int* done, double* sc,
                            unsigned* cnt, const double* adg = nullptr) {
   if (*done) return;
   double acc[1] = {0.0};
@@ -173,7 +200,7 @@ __global__ void k_fin_alpha(const double* part, int nblk, double* sc, const int*
 
 // x += alpha p, r -= alpha Ap; Jacobi: z = r / diag and r.z; both: r.r.  bf (optional): the
 // new r rounded to FP32 as the right-hand side of an FP32 multigrid's level 0
-__global__ void k_update(long long N, double* x, double* r, const double* p, const double* Ap, const double* idg,
+__global__ void __launch_bounds__(TPB, Solver::CG_BLOCKS_PER_SM) k_update(long long N, double* x, double* r, const double* p, const double* Ap, const double* idg,
                          double* z, int jacobi, double* sc, double* part, int* done, unsigned* cnt,
                          float* bf = nullptr) {
   if (*done) return;
@@ -2249,6 +2276,16 @@ int Solver::persist_blocks(bool f32) {
   return cache;
 }
 
+int Solver::cg_grid(long long N) {
+  if (nsm_ <= 1) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm > 0) nsm_ = nsm;
+  }
+  return std::min(red_grid_cap(N, rb), CG_BLOCKS_PER_SM * nsm_);
+}
+
 int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out) {
   if (persist_pcg) {
     const RecordSpec rec = take_record();
@@ -2256,7 +2293,7 @@ int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out)
   }
   if (f32_helm) return pcg_jacobi_f32(s, rtol, maxit, out);
   BoxV A = view(s);
-  int nb = red_grid_cap(s.N, rb);
+  int nb = cg_grid(s.N);
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 1, part, adg);
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, nullptr, nullptr);
   auto iteration = [&]() {
@@ -2265,13 +2302,15 @@ int Solver::pcg_jacobi(const BoxSys& s, double rtol, int maxit, SolveStats* out)
       ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt, adg);
     }
     {
-      ProfScope ps(prof, KC_UPDATE, stream, 5.0 * s.N * 8.0, 5.0 * s.N);
+      ProfScope ps(prof, KC_UPDATE, stream, 8.0 * s.N * 8.0, 5.0 * s.N);
       ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 1, sc, part, done, cnt);
     }
-    ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
+    ++g_launches, k_p_update<<<red_grid_cap(s.N, rb), TPB, 0, stream>>>(s.N, p, z, sc, done);
   };
   if (capturing) return device_loop(iteration);
-  const int chunk = 8;
+  // the host polls after every chunk of iterations; while the kernel classes are timed it
+  // polls after each one, so that no timed launch is one that returned at once
+  const int chunk = (prof && prof->on) ? 1 : 8;
   int conv = 0;
   for (int it = 0; it < maxit; it += chunk) {
     for (int q = 0; q < chunk; ++q) iteration();
@@ -2289,7 +2328,7 @@ int Solver::pcg_jacobi_f32(const BoxSys& s, double rtol, int maxit, SolveStats* 
   for (int a = 0; a < 3; ++a) { Af.m[a] = s.m[a]; Af.c[a] = s.c[a] ? fc[a] : nullptr; }
   Af.N = s.N;
   Af.D = fD;
-  int nb = red_grid_cap(s.N, rb);
+  int nb = cg_grid(s.N);
   // FP64 defect of the initial guess, ||b||, ||r0||
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part);
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, nullptr, nullptr);
@@ -2311,8 +2350,9 @@ int Solver::pcg_jacobi_f32(const BoxSys& s, double rtol, int maxit, SolveStats* 
     rc = device_loop(iteration);
   } else {
     int conv = 0;
-    for (int it = 0; it < maxit; it += 8) {
-      for (int q = 0; q < 8; ++q) iteration();
+    const int chunk = (prof && prof->on) ? 1 : 8;
+    for (int it = 0; it < maxit; it += chunk) {
+      for (int q = 0; q < chunk; ++q) iteration();
       CK(cudaGetLastError());
       if (poll(hsc, sc, done, stream, maxit, &conv)) break;
     }
@@ -2638,7 +2678,7 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
   if (rc) return rc;
   if (!fp32) { lev[0].b = r; lev[0].x = z; }
   BoxV A = view(s);
-  int nb = red_grid_cap(s.N, rb);
+  int nb = cg_grid(s.N);
   int g = lin_grid(s.N);
   ++g_launches, k_pcg_init<<<nb, TPB, 0, stream>>>(A, s.b, s.x, r, z, p, idg, 0, part, adg);
   ++g_launches, k_fin_init<<<1, TPB, 0, stream>>>(part, nb, sc, done, rtol * rtol, maxit, nullptr, nullptr);
@@ -2653,15 +2693,15 @@ int Solver::pcg_mg(const BoxSys& s, double rtol, int maxit, int fp32, SolveStats
       ++g_launches, k_spmv_dot<<<nb, TPB, 0, stream>>>(A, p, Ap, part, done, sc, cnt, adg);
     }
     {
-      ProfScope ps(prof, KC_UPDATE, stream, (5.0 * 8.0 + (fp32 ? 4.0 : 0.0)) * s.N, 3.0 * s.N);
+      ProfScope ps(prof, KC_UPDATE, stream, (6.0 * 8.0 + (fp32 ? 4.0 : 0.0)) * s.N, 3.0 * s.N);
       ++g_launches, k_update<<<nb, TPB, 0, stream>>>(s.N, s.x, r, p, Ap, idg, z, 0, sc, part, done, cnt, bf);
     }
     vcycle(fp32, false);
     ++g_launches, k_dot_rz<<<nb, TPB, 0, stream>>>(s.N, r, z, part, done, sc, cnt, 0, zf);
-    ++g_launches, k_p_update<<<nb, TPB, 0, stream>>>(s.N, p, z, sc, done);
+    ++g_launches, k_p_update<<<red_grid_cap(s.N, rb), TPB, 0, stream>>>(s.N, p, z, sc, done);
   };
   if (capturing) return device_loop(iteration);
-  const int chunk = 4;
+  const int chunk = (prof && prof->on) ? 1 : 4;
   int conv = 0;
   for (int it = 0; it < maxit; it += chunk) {
     for (int q = 0; q < chunk; ++q) iteration();

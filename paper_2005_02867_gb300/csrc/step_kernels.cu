@@ -298,7 +298,11 @@ __global__ void k_adv_faces(Geo g, Phys p, const double* as, const double* ua, d
   bool pos = phi >= 0.0;
   FL[id] = phi * (pos ? aL : aR);
   double A = 0.0;
-  if (f[a] > 0 && f[a] < g.n[a]) {
+  // a face between two cells of the same pure phase (alpha both 0 or both 1, compared as
+  // encodings on the integer pipe) has FH = FL exactly: the van Leer increment vanishes
+  // with the downwind difference and the compression term with a_c (1 - a_c); its
+  // antidiffusive flux is +0 without the gradient arithmetic
+  if (f[a] > 0 && f[a] < g.n[a] && !pure_pair(aL, aR)) {
     int LL[3] = {L[0], L[1], L[2]}, RR[3] = {R[0], R[1], R[2]};
     LL[a] -= 1;
     RR[a] += 1;
@@ -339,6 +343,23 @@ __device__ __forceinline__ void props_cell(const Phys& p, long long id, double a
                                            const double* omega, const double* T, double* rho, double* mu,
                                            double* kc, double* cp, double* D) {
   const double w = omega[id];
+  const long long ba = __double_as_longlong(a);
+  if (ba == 0) {                          // pure gas: the mixture rule gives the gas values exactly
+    rho[id] = rhoG[id];
+    mu[id] = p.mu_g;
+    kc[id] = p.k_g;
+    cp[id] = w * p.cp_v + (1.0 - w) * p.cp_g;
+    D[id] = p.D_gas;
+    return;
+  }
+  if (ba == 0x3FF0000000000000LL) {       // pure liquid (alpha = 1)
+    rho[id] = p.drl == 0.0 ? p.rho_l : rho_liq(p, T[id]);
+    mu[id] = p.mu_l;
+    kc[id] = p.k_l;
+    cp[id] = p.cp_l;
+    D[id] = p.D_l;
+    return;
+  }
   rho[id] = a * (p.drl == 0.0 ? p.rho_l : rho_liq(p, T[id])) + (1.0 - a) * rhoG[id];
   mu[id] = a * p.mu_l + (1.0 - a) * p.mu_g;
   kc[id] = a * p.k_l + (1.0 - a) * p.k_g;
@@ -377,8 +398,24 @@ __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const dou
   if (id >= g.N) return;
   int i, j, k;
   decomp(id, g.n[0], g.n[1], i, j, k);
-  double amax = imax64(as[id], aL[id]), amin = imin64(as[id], aL[id]);
   constexpr int na = NA;
+  const double* AA[3] = {A0, A1, A2};
+  double Alo[3], Ahi[3];
+  long long anyA = 0;   // OR of the encodings without sign: 0 when every face flux is +-0
+  #pragma unroll
+  for (int a = 0; a < na; ++a) {
+    int hi[3] = {i, j, k};
+    hi[a] += 1;
+    Alo[a] = AA[a][fidx(g, a, i, j, k)];
+    Ahi[a] = AA[a][fidx(g, a, hi[0], hi[1], hi[2])];
+    anyA |= (__double_as_longlong(Alo[a]) | __double_as_longlong(Ahi[a])) << 1;
+  }
+  if (anyA == 0) {   // P+ = P- = 0: both ratios are 0
+    Rp[id] = 0.0;
+    Rm[id] = 0.0;
+    return;
+  }
+  double amax = imax64(as[id], aL[id]), amin = imin64(as[id], aL[id]);
   #pragma unroll
   for (int a = 0; a < na; ++a)
     #pragma unroll
@@ -393,16 +430,11 @@ __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const dou
     }
   amax = imin64(amax, 1.0);
   amin = imax64(amin, 0.0);
-  const double* AA[3] = {A0, A1, A2};
   double Pp = 0.0, Pm = 0.0;
   #pragma unroll
   for (int a = 0; a < na; ++a) {
-    int hi[3] = {i, j, k};
-    hi[a] += 1;
-    double Alo = AA[a][fidx(g, a, i, j, k)];
-    double Ahi = AA[a][fidx(g, a, hi[0], hi[1], hi[2])];
-    Pp += imax64(0.0, Alo) + imax64(0.0, -Ahi);
-    Pm += imax64(0.0, -Alo) + imax64(0.0, Ahi);
+    Pp += imax64(0.0, Alo[a]) + imax64(0.0, -Ahi[a]);
+    Pm += imax64(0.0, -Alo[a]) + imax64(0.0, Ahi[a]);
   }
   double V = cellV(g, i);
   double Qp = (amax - aL[id]) * V, Qm = (aL[id] - amin) * V;
@@ -414,7 +446,7 @@ __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const dou
 __device__ __forceinline__ double limited_flux(const Geo& g, int a, const double* A, const double* Rp,
                                                const double* Rm, int f0, int f1, int f2) {
   double Af = A[fidx(g, a, f0, f1, f2)];
-  if (Af == 0.0) return 0.0;
+  if ((__double_as_longlong(Af) << 1) == 0) return 0.0;   // Af == +-0, on the integer pipe
   int L[3] = {f0, f1, f2};
   L[a] -= 1;
   long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, f0, f1, f2);
@@ -442,7 +474,9 @@ __global__ void k_adv_update(Geo g, Phys p, const double* aL, const double* A0, 
       s += limited_flux(g, a, AA[a], Rp, Rm, hi[0], hi[1], hi[2]) - limited_flux(g, a, AA[a], Rp, Rm, i, j, k);
     }
     double V = cellV(g, i);
-    double an = aL[id] - s * rcp64(V);
+    // no limited flux (s = +-0): alpha^L itself, without the reciprocal (the clamp below
+    // maps -0 to +0 either way)
+    double an = ((__double_as_longlong(s) << 1) == 0) ? aL[id] : aL[id] - s * rcp64(V);
     double ac = iclamp01(an);
     if (ac != an) { acc[1] += 1.0; acc[0] += (an - ac) * V; }
     alpha[id] = ac;
@@ -730,6 +764,8 @@ __device__ __forceinline__ double gam(int mode, const double* kc, const double* 
   return mode == 0 ? kc[q] : rho[q] * D[q];
 }
 __device__ __forceinline__ double harm(double x, double y) { return 2.0 * x * y * rcp64(x + y); }
+// half the harmonic mean, x y / (x + y) (the 2 folded into a host constant)
+__device__ __forceinline__ double harm_half(double x, double y) { return x * y * rcp64(x + y); }
 
 template <int NA>
 __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
@@ -746,8 +782,11 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
   double V = cellV(g, i);
   double coef = mode == 0 ? rho[id] * cp[id] : rho[id];
   double dP = coef * V * idt_of(p);
-  double r = coef * V * phi[id] * idt_of(p) + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
-  double net = 0.0, Fsum = 0.0;
+  const double phiP = phi[id];
+  double r = dP * phiP + (mode == 0 ? -mdot[id] * p.Lv : 0.0) * V;
+  // the convection sum of phi_f - phi_P over the faces (outward flux sign), i.e.
+  // sum F phi_f - phi_P sum F
+  double net = 0.0;
   double gP = gam(mode, kc, rho, D, id);
   bool pin = (mode == 1) && ige64(alpha_new[id], 0.5);
   int ci[3] = {i, j, k};
@@ -762,7 +801,7 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
       if (f[a] == 0 || f[a] == g.n[a]) {
         int kind = (side ? g.bc[a][1] : g.bc[a][0]);
         bool inflow = side == 0 ? (F > 0.0) : (F < 0.0);
-        val = ((kind == BC_OPEN || kind == BC_FORCED) && inflow) ? amb : phi[id];
+        val = ((kind == BC_OPEN || kind == BC_FORCED) && inflow) ? amb : phiP;
       } else {
         int L[3] = {f[0], f[1], f[2]};
         L[a] -= 1;
@@ -770,12 +809,14 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
         LL[a] -= 1;
         RR[a] += 1;
         double vL = phi[cidx(g, L[0], L[1], L[2])], vR = phi[cidx(g, f[0], f[1], f[2])];
-        if (F >= 0.0) val = lim_up(cellg(g, phi, LL[0], LL[1], LL[2], R_TO, amb, u0, u1, u2), vL, vR);
-        else val = lim_up(cellg(g, phi, RR[0], RR[1], RR[2], R_TO, amb, u0, u1, u2), vR, vL);
+        // the upwind side's operands chosen by the sign bit of F (integer selects, one
+        // limited value; a zero F multiplies it either way)
+        const bool pos = __double_as_longlong(F) >= 0;
+        const double far = pos ? cellg(g, phi, LL[0], LL[1], LL[2], R_TO, amb, u0, u1, u2)
+                               : cellg(g, phi, RR[0], RR[1], RR[2], R_TO, amb, u0, u1, u2);
+        val = lim_up(far, pos ? vL : vR, pos ? vR : vL);
       }
-      double sgn = side ? 1.0 : -1.0;
-      net += sgn * F * val;
-      Fsum += sgn * F;
+      net = fma(side ? F : -F, val - phiP, net);
     }
     // coupling across the low face, stored at this cell
     double cl = 0.0;
@@ -783,7 +824,8 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
       int Lc[3] = {i, j, k};
       Lc[a] -= 1;
       long long li = cidx(g, Lc[0], Lc[1], Lc[2]);
-      cl = harm(gam(mode, kc, rho, D, li), gP) * faceA(g, a, i) * g.ih[a];
+      cl = NA == 3 ? harm_half(gam(mode, kc, rho, D, li), gP) * g.aih2[a]
+                   : harm(gam(mode, kc, rho, D, li), gP) * faceA(g, a, i) * g.ih[a];
       if (mode == 1) {
         bool lp = ige64(alpha_new[li], 0.5);
         if (!pin && lp) { r += cl * pinv[li]; dP += cl; }
@@ -797,7 +839,8 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
       Hc[a] += 1;
       long long hi = cidx(g, Hc[0], Hc[1], Hc[2]);
       if (ige64(alpha_new[hi], 0.5)) {
-        double ch = harm(gP, gam(mode, kc, rho, D, hi)) * faceA(g, a, Hc[0]) * g.ih[a];
+        double ch = NA == 3 ? harm_half(gP, gam(mode, kc, rho, D, hi)) * g.aih2[a]
+                            : harm(gP, gam(mode, kc, rho, D, hi)) * faceA(g, a, Hc[0]) * g.ih[a];
         r += ch * pinv[hi];
         dP += ch;
       }
@@ -823,7 +866,7 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
       }
     }
   }
-  r -= coef * (net - phi[id] * Fsum);
+  r -= coef * net;
   if (pin) {
     // pinned row, scaled like the other rows: (coef V/dt) x = (coef V/dt) Y_eq
     double dd = coef * V * idt_of(p);
@@ -875,6 +918,7 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
                                const double* rho, const double* mu, const double* pr, const double* alpha,
                                const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
   constexpr int c = C;
+  constexpr bool cart = NA == 3;   // 3D grids are Cartesian, 2D ones axisymmetric
   // box dims: n with n_c - 1 along c
   int m[3] = {g.n[0], g.n[1], g.n[2]};
   m[c] -= 1;
@@ -893,17 +937,20 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
   constexpr int na = NA;
   long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, R[0], R[1], R[2]);
   double rhoL = rho[li], rhoR = rho[ri], muL = mu[li], muR = mu[ri];
-  double rho_f = 0.5 * (rhoL + rhoR), mu_f = 0.5 * (muL + muR);
-  double r_f = 0.0, V_f;
-  if (g.axisym) {
+  // rho_f V_f with rho_f the mean of the two cells, and the face area
+  double r_f = 0.0, V_f, rV, A_f;
+  if (cart) {
+    V_f = g.vol3;
+    rV = (rhoL + rhoR) * g.hvol3;
+    A_f = g.area3[c];
+  } else {
     r_f = (c == 0) ? f[0] * g.h[0] : (f[0] + 0.5) * g.h[0];
     V_f = r_f * g.h[0] * g.h[1];
-  } else {
-    V_f = g.vol3;
+    rV = 0.5 * (rhoL + rhoR) * V_f;
+    A_f = V_f * g.ih[c];
   }
-  double A_f = V_f * g.ih[c];
   double u_f = uc[fidx(g, c, f[0], f[1], f[2])];
-  const double rV = rho_f * V_f, muLR = muL + muR;
+  const double muLR = muL + muR;
   double d = rV * idt_of(p);
   double r = d * u_f;
   // advection accumulated without its common factor -rho_f V_f
@@ -911,15 +958,20 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
   #pragma unroll
   for (int a = 0; a < na; ++a) {
     // ---- advection (advective form, minmod limited linear upwind)
-    double ubar;
-    if (a == c) ubar = u_f;
+    // ubs: the advecting velocity, for a != c four times it (the mean of the four
+    // surrounding faces of direction a; its quarter is folded into the factor qih)
+    double ubs, uaL_lo = 0.0, uaL_hi = 0.0, uaR_lo = 0.0, uaR_hi = 0.0;
+    if (a == c) ubs = u_f;
     else {
       const double* ua = U[a];
       int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
       La[a] += 1;
       Ra[a] += 1;
-      ubar = 0.25 * (((ua[fidx(g, a, L[0], L[1], L[2])] + ua[fidx(g, a, La[0], La[1], La[2])]) +
-                      ua[fidx(g, a, R[0], R[1], R[2])]) + ua[fidx(g, a, Ra[0], Ra[1], Ra[2])]);
+      uaL_lo = ua[fidx(g, a, L[0], L[1], L[2])];
+      uaL_hi = ua[fidx(g, a, La[0], La[1], La[2])];
+      uaR_lo = ua[fidx(g, a, R[0], R[1], R[2])];
+      uaR_hi = ua[fidx(g, a, Ra[0], Ra[1], Ra[2])];
+      ubs = ((uaL_lo + uaL_hi) + uaR_lo) + uaR_hi;
     }
     int q[3];
     double us[5];
@@ -929,18 +981,30 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
       q[a] += s;
       us[s + 2] = ufg(g, uc, c, q[0], q[1], q[2]);
     }
-    double uplus, uminus;
-    if (ubar >= 0.0) { uplus = lim_up(us[1], us[2], us[3]); uminus = lim_up(us[0], us[1], us[2]); }
-    else { uplus = lim_up(us[4], us[3], us[2]); uminus = lim_up(us[3], us[2], us[1]); }
-    s_adv += ubar * (uplus - uminus) * g.ih[a];
+    // u(+1/2) - u(-1/2) of the limited upwind values, without a branch: with the differences
+    // d_k = us[k] - us[k-1] and M = minmod(d21, d32), it is d21 + (M - minmod(d10, d21)) / 2
+    // for ubar >= 0 and d32 + (M - minmod(d32, d43)) / 2 otherwise (the sign taken from the
+    // sign bit on the integer pipe: a zero ubar multiplies the difference either way)
+    const double d10 = us[1] - us[0], d21 = us[2] - us[1], d32 = us[3] - us[2], d43 = us[4] - us[3];
+    const bool pos = __double_as_longlong(ubs) >= 0;
+    const double M2 = minmod(d21, d32);
+    const double X = pos ? minmod(d10, d21) : minmod(d32, d43);
+    const double dd = fma(0.5, M2 - X, pos ? d21 : d32);
+    s_adv = fma(ubs * dd, a == c ? g.ih[a] : g.qih[a], s_adv);
     // ---- viscous
     if (a == c) {
-      double ApL, ApR;
-      if (g.axisym && c == 0) { ApL = areaN(g, 0, (L[0] + 0.5) * g.h[0]); ApR = areaN(g, 0, (R[0] + 0.5) * g.h[0]); }
-      else if (g.axisym) { ApL = ApR = areaN(g, 1, r_f); }
-      else { ApL = ApR = areaN(g, c, 0.0); }
-      double kR = muR * (ApR * g.ih[c]), kL = muL * (ApL * g.ih[c]);
-      t_vT = t_vT + (kR * (us[3] - us[2]) - kL * (us[2] - us[1]));
+      double kR, kL;
+      if (cart) {
+        kR = muR * g.aih[c];
+        kL = muL * g.aih[c];
+      } else {
+        double ApL, ApR;
+        if (c == 0) { ApL = areaN(g, 0, (L[0] + 0.5) * g.h[0]); ApR = areaN(g, 0, (R[0] + 0.5) * g.h[0]); }
+        else { ApL = ApR = areaN(g, 1, r_f); }
+        kR = muR * (ApR * g.ih[c]);
+        kL = muL * (ApL * g.ih[c]);
+      }
+      t_vT = t_vT + (kR * d32 - kL * d21);
       // coupling with the lower neighbour face (stored at this box cell)
       Cc[c][id] = (b[c] > 0) ? kL : 0.0;
       if (b[c] == 0 && g.bc[c][0] != BC_OPEN) {
@@ -956,32 +1020,40 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
         r += kR * uc[fidx(g, c, fb[0], fb[1], fb[2])];
       }
     } else {
-      double App, Apm;
-      if (g.axisym && a == 0) { App = areaN(g, 0, (f[0] + 1) * g.h[0]); Apm = areaN(g, 0, f[0] * g.h[0]); }
-      else if (g.axisym) { App = Apm = areaN(g, 1, r_f); }
-      else { App = Apm = areaN(g, a, 0.0); }
-      double mup = mu_edge(g, mu, muLR, L, R, a, 1), mum = mu_edge(g, mu, muLR, L, R, a, -1);
-      double kp = mup * (App * g.ih[a]), km = mum * (Apm * g.ih[a]);
-      const double* ua = U[a];
-      int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
-      La[a] += 1;
-      Ra[a] += 1;
-      double uaR_hi = ua[fidx(g, a, Ra[0], Ra[1], Ra[2])], uaL_hi = ua[fidx(g, a, La[0], La[1], La[2])];
-      double uaR_lo = ua[fidx(g, a, R[0], R[1], R[2])], uaL_lo = ua[fidx(g, a, L[0], L[1], L[2])];
-      t_vT = t_vT + (mup * App * (uaR_hi - uaL_hi) - mum * Apm * (uaR_lo - uaL_lo)) * g.ih[c];
+      double kp, km;
+      if (cart) {
+        // edge viscosities as sums of their four cells, the quarter in the constants
+        int La[3] = {L[0], L[1], L[2]}, Ra[3] = {R[0], R[1], R[2]};
+        La[a] += 1;
+        Ra[a] += 1;
+        const double sp = muLR + cellc(g, mu, La[0], La[1], La[2]) + cellc(g, mu, Ra[0], Ra[1], Ra[2]);
+        La[a] -= 2;
+        Ra[a] -= 2;
+        const double sm = muLR + cellc(g, mu, La[0], La[1], La[2]) + cellc(g, mu, Ra[0], Ra[1], Ra[2]);
+        kp = sp * g.qaih[a];
+        km = sm * g.qaih[a];
+        t_vT = t_vT + (sp * (uaR_hi - uaL_hi) - sm * (uaR_lo - uaL_lo)) * g.qvt[c][a];
+      } else {
+        double App, Apm;
+        if (a == 0) { App = areaN(g, 0, (f[0] + 1) * g.h[0]); Apm = areaN(g, 0, f[0] * g.h[0]); }
+        else { App = Apm = areaN(g, 1, r_f); }
+        double mup = mu_edge(g, mu, muLR, L, R, a, 1), mum = mu_edge(g, mu, muLR, L, R, a, -1);
+        kp = mup * (App * g.ih[a]);
+        km = mum * (Apm * g.ih[a]);
+        t_vT = t_vT + (mup * App * (uaR_hi - uaL_hi) - mum * Apm * (uaR_lo - uaL_lo)) * g.ih[c];
+      }
       Cc[a][id] = (b[a] > 0) ? km : 0.0;
       if (b[a] == 0 && (g.bc[a][0] == BC_WALL || g.bc[a][0] == BC_FORCED)) d_visc += 2.0 * km;
       if (b[a] == m[a] - 1 && (g.bc[a][1] == BC_WALL || g.bc[a][1] == BC_FORCED)) d_visc += 2.0 * kp;
     }
   }
-  if (g.axisym && c == 0 && r_f > 0.0) d_visc = d_visc + 2.0 * mu_f * V_f / (r_f * r_f);
-  // pressure, buoyancy and centripetal force in the balanced face form
-  double gx = 0.0;
+  if (!cart && c == 0 && r_f > 0.0) d_visc = d_visc + 2.0 * (0.5 * muLR) * V_f / (r_f * r_f);
+  // pressure, buoyancy and centripetal force in the balanced face form; g . x from the
+  // host-formed constants (axes without gravity skipped: a uniform branch)
+  double gx = g.gxc[c];
   #pragma unroll
-  for (int a = 0; a < na; ++a) {
-    double xa = (a == c) ? f[a] * g.h[a] : (f[a] + 0.5) * g.h[a];
-    gx = gx + p.g[a] * xa;
-  }
+  for (int a = 0; a < na; ++a)
+    if (g.gmask >> a & 1) gx = fma(g.gh[a], (double)f[a], gx);
   double xiL = xi[li], xiR = xi[ri];
   double raL = rhoL * alpha[li], raR = rhoR * alpha[ri];
   double t_force = A_f * ((0.5 * (raL + raR) * (xiR - xiL) - gx * (rhoR - rhoL)) - (pr[ri] - pr[li]));
@@ -1110,8 +1182,9 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
     if (ci[a] > 0) {
       int Lc[3] = {i, j, k};
       Lc[a] -= 1;
-      // A / h over the mean density of the two cells
-      cl = faceA(g, a, i) * g.ih[a] * (2.0 * rcp64(rho[cidx(g, Lc[0], Lc[1], Lc[2])] + rP));
+      // A / h over the mean density of the two cells (3D: 2 A / h from the host)
+      const double ir = rcp64(rho[cidx(g, Lc[0], Lc[1], Lc[2])] + rP);
+      cl = NA == 3 ? g.aih2[a] * ir : faceA(g, a, i) * g.ih[a] * (2.0 * ir);
     }
     C[a][id] = cl;
     if (ci[a] == 0 && g.bc[a][0] == BC_OPEN) dg += faceA(g, a, i) * (2.0 * g.ih[a]) / rP;

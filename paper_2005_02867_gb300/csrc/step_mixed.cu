@@ -424,7 +424,8 @@ __device__ __forceinline__ void adv_face_mx(const Geo& g, const Phys& p, const d
   const bool pos = phi >= 0.0;
   FL[id] = phi * (pos ? aL : aR);
   float A = 0.f;
-  if (f[a] > 0 && f[a] < g.n[a]) {
+  // two cells of the same pure phase: no antidiffusive flux (as in the FP64 kernel)
+  if (f[a] > 0 && f[a] < g.n[a] && !pure_pair(aL, aR)) {
     const GeoF q = geof(g);
     int LL[3] = {L[0], L[1], L[2]}, RR[3] = {R[0], R[1], R[2]};
     LL[a] -= 1;
