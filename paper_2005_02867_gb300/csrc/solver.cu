@@ -15,7 +15,10 @@ namespace dg {
 // (S_ITSK: the iterations of each system of a joint persistent solve)
 // S_TMO: 1 when a grid-barrier wait of the last persistent solve ran out (written by the
 // last block to leave the launch)
-enum { S_RZ = 0, S_PAP, S_RR, S_BB, S_ALPHA, S_BETA, S_ITS, S_TOL2, S_MAXIT, S_ITSK, S_TMO = S_ITSK + 3, S_COUNT };
+// S_SCL: the power of two that brings the initial defect's norm into [2^-100, 2^100]
+// (1 when it is there), by which the binary32 defect-correction solve scales its defect
+enum { S_RZ = 0, S_PAP, S_RR, S_BB, S_ALPHA, S_BETA, S_ITS, S_TOL2, S_MAXIT, S_ITSK, S_TMO = S_ITSK + 3, S_SCL,
+       S_ISCL, S_COUNT };   // S_ISCL = 1 / S_SCL
 
 // done flag values: 0 running, 1 converged, 2 stopped at the iteration cap
 
@@ -155,6 +158,10 @@ __global__ void k_fin_init(const double* part, int nblk, double* sc, int* done, 
     sc[S_ITS] = 0.0;
     sc[S_TOL2] = tol2;
     sc[S_MAXIT] = (double)maxit;
+    const double n0 = sqrt(rr);
+    const bool keep = (n0 >= 0x1p-100 && n0 <= 0x1p100) || !(n0 > 0.0) || !(n0 < 1e300);
+    sc[S_SCL] = keep ? 1.0 : ldexp(1.0, -ilogb(n0));
+    sc[S_ISCL] = keep ? 1.0 : ldexp(1.0, ilogb(n0));
     *done = (bb == 0.0 || rr <= tol2 * bb) ? 1 : 0;
   }
 }
@@ -314,7 +321,14 @@ struct BoxVf {
 __global__ void k_mx_setup(BoxV A, const double* r64, float* fD, float* fc0, float* fc1, float* fc2, float* fidg,
                            float* fr, float* fz, float* fp, float* fdx, double* part, const int* done, double* sc,
                            unsigned* cnt) {
-  if (*done) return;
+  if (*done) {   // converged at the initial guess: a zero correction for k_mx_finish
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < A.N; id += (long long)gridDim.x * blockDim.x)
+      fdx[id] = 0.f;
+    return;
+  }
+  // the defect scaled by the power of two S_SCL (exact) so that binary32 holds it whatever
+  // its size; the convergence test and the statistics then use |b|^2 scaled alike
+  const double scl = sc[S_SCL];
   float rz = 0.f;
   float* fc[3] = {fc0, fc1, fc2};
   for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < A.N; id += (long long)gridDim.x * blockDim.x) {
@@ -335,7 +349,7 @@ __global__ void k_mx_setup(BoxV A, const double* r64, float* fD, float* fc0, flo
     fD[id] = D;
     float iv = 1.f / dt;
     fidg[id] = iv;
-    float rr = (float)r64[id];
+    float rr = (float)(r64[id] * scl);
     fr[id] = rr;
     float zz = iv * rr;
     fz[id] = zz;
@@ -349,6 +363,7 @@ __global__ void k_mx_setup(BoxV A, const double* r64, float* fD, float* fc0, flo
     double t = block_sum_partials(part, gridDim.x);
     if (threadIdx.x == 0) {
       sc[S_RZ] = t;
+      sc[S_BB] *= scl * scl;
       *cnt = 0u;
     }
   }
@@ -425,10 +440,10 @@ __global__ void k_p_update_f(long long N, float* p, const float* z, const double
     p[id] = z[id] + be * p[id];
 }
 
-// x = x0 + d (FP64)
-__global__ void k_mx_finish(long long N, double* x, const float* dx) {
+// x = x0 + d (FP64), d the binary32 correction divided by the defect's scale (a power of two)
+__global__ void k_mx_finish(long long N, double* x, const float* dx, const double* sc) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (id < N) x[id] += (double)dx[id];
+  if (id < N) x[id] += (double)dx[id] * sc[S_ISCL];
 }
 
 // ---------------------------------------------------------------- persistent Jacobi-PCG
@@ -627,7 +642,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
   // block-uniform state of each system (written by thread 0 between barriers)
   __shared__ double s_bb[PMAXSYS], s_rr[PMAXSYS], s_inv_nu[PMAXSYS];
   __shared__ T s_nu[PMAXSYS], s_thr[PMAXSYS], s_gamma[PMAXSYS], s_alpha[PMAXSYS], s_beta[PMAXSYS], s_rho[PMAXSYS];
-  __shared__ int s_its[PMAXSYS], s_res[PMAXSYS], s_act[PMAXSYS], s_any;
+  __shared__ int s_its[PMAXSYS], s_res[PMAXSYS], s_act[PMAXSYS], s_any, s_resc[PMAXSYS], s_any_resc;
   const int K = M.K;
   const int gs = gridDim.x * blockDim.x;
   const int id0 = blockIdx.x * blockDim.x + threadIdx.x;
@@ -659,6 +674,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
     const bool ok = grid_sum<double, 2 * PMAXSYS>(q64, 2 * K, phase++, M.part64, M.bar, M.err, M.spin);
     if (threadIdx.x == 0) {
       s_any = 0;
+      s_any_resc = 0;
 #pragma unroll
       for (int k = 0; k < PMAXSYS; ++k) {
         s_bb[k] = q64[2 * k];
@@ -666,6 +682,7 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
         s_its[k] = 0;
         s_res[k] = ok ? 2 : 3;
         s_act[k] = 0;
+        s_resc[k] = 0;
         if (k < K && ok) {
           if (s_bb[k] == 0.0 || s_rr[k] <= M.s[k].tol2 * s_bb[k]) {
             s_res[k] = 1;                            // converged at the initial guess
@@ -676,9 +693,46 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
             s_inv_nu[k] = sqrt(s_rr[k]);             // |r0| = 1 / nu
             s_nu[k] = (T)(1.0 / s_inv_nu[k]);
             s_thr[k] = (T)(M.s[k].tol2 * s_bb[k] / s_rr[k]);   // rtol^2 |b|^2 / |r0|^2
+            // binary32: a defect of norm outside [2^-100, 2^100] does not survive its
+            // rounding to binary32 (entries that matter at the tolerance flush to zero, or
+            // nu overflows); it is then formed again and normalised in FP64 before rounding
+            if (sizeof(T) == 4 && !(s_inv_nu[k] >= 0x1p-100 && s_inv_nu[k] <= 0x1p100)) {
+              s_resc[k] = 1;
+              s_any_resc = 1;
+            }
           }
         }
       }
+    }
+    __syncthreads();
+  }
+  if (s_any_resc) {
+    // (a uniform branch: every block holds the same totals) r0 / |r0| in FP64, rounded once
+#pragma unroll
+    for (int k = 0; k < PMAXSYS; ++k) {
+      if (k >= K) break;
+      if (!s_resc[k]) continue;
+      const PersistArgs<T>& a = M.s[k];
+      const int N = (int)a.A.N;
+      const double nu64 = 1.0 / s_inv_nu[k];
+      for (int id = id0; id < N; id += gs) {
+        int i, j, kk;
+        bdecomp(a.A.m, id, i, j, kk);
+        double ax, d;
+        box_row<double, double, true>(a.A.m, a.A.D, a.A.c, a.x, id, i, j, kk, ax, d);
+        a.r[1][id] = (T)((a.b[id] - ax) * nu64);
+      }
+    }
+    double none[1];
+    const bool okb = grid_sum<double, 1>(none, 0, phase++, M.part64, M.bar, M.err, M.spin);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < PMAXSYS; ++k) {
+        if (k >= K) continue;
+        if (s_resc[k]) s_nu[k] = (T)1;           // r[1] holds the normalised defect
+        if (!okb && s_act[k]) { s_act[k] = 0; s_res[k] = 3; }   // the barrier wait ran out
+      }
+      if (!okb) s_any = 0;
     }
     __syncthreads();
   }
@@ -2360,7 +2414,7 @@ int Solver::pcg_jacobi_f32(const BoxSys& s, double rtol, int maxit, SolveStats* 
     fill_stats(hsc, conv, out);
     rc = conv ? 0 : DROPLET_ERR_NOT_CONVERGED;
   }
-  ++g_launches, k_mx_finish<<<lin_grid(s.N), TPB, 0, stream>>>(s.N, s.x, fdx);
+  ++g_launches, k_mx_finish<<<lin_grid(s.N), TPB, 0, stream>>>(s.N, s.x, fdx, sc);
   return rc;
 }
 
