@@ -134,6 +134,18 @@ typedef struct droplet_config {
                            source subtracts again; diag M_liq is then sum rho_L(T) alpha V.
                            0 = the constant rho_l.  Must keep rho_L > 0 at T_amb and Tb.
                            Not available with droplet_adjoint. */
+  int    fiber;         /* the spherical fibre the droplet is placed around (Sec. 3.1.1: a
+                           sphere of diameter 0.1 mm at the droplet's centre; Table
+                           tableboundary, "sphere" row: no slip, zero gradient of alpha, T,
+                           omega and p_rgh): 0 = none (the fibre is only the centre of the
+                           potential xi), 1 = the cells whose centre lies closer than
+                           fiber_radius to xc are solid.  Their faces carry u = 0 (pinned rows of
+                           the momentum systems), no flux of alpha, T, omega or pressure, and
+                           central differences reaching into them use the fluid cell's own
+                           value; the solid cells hold alpha = 0, T = T_drop, omega = 0 and
+                           are never interface or adjacent gas cells.  Requires precision = 0,
+                           adv_scheme = 0 and drho_l_dT = 0; not available with
+                           droplet_adjoint. */
 } droplet_config;
 
 /* Diagnostics of one droplet after the last completed step (Sec. 4 reports

@@ -210,9 +210,11 @@ def van_leer(uu, u, d):
     return u + corr
 
 
-def props(cfg, alpha, rhoG, omega, T):
+def props(cfg, alpha, rhoG, omega, T, solid=None):
     """Mixture properties chi = alpha chi_L + (1 - alpha) chi_G (Sec. 2.7), the liquid
-    density at the cell's temperature (rho_L(T), reading R31)."""
+    density at the cell's temperature (rho_L(T), reading R31).  The fibre's cells
+    conduct and diffuse nothing (k = D = 0: no flux of T or omega across the sphere,
+    reading R32)."""
     a = alpha
     rho = a * th.rho_liquid(cfg, T) + (1.0 - a) * rhoG
     mu = a * cfg["mu_l"] + (1.0 - a) * cfg["mu_g"]
@@ -220,6 +222,9 @@ def props(cfg, alpha, rhoG, omega, T):
     cpG = omega * cfg["cp_v"] + (1.0 - omega) * cfg["cp_g"]
     cp = a * cfg["cp_l"] + (1.0 - a) * cpG
     D = a * cfg["D_l"] + (1.0 - a) * th.D_gas(cfg)
+    if solid is not None:
+        k = np.where(solid, 0.0, k)
+        D = np.where(solid, 0.0, D)
     return dict(rho=rho, mu=mu, k=k, cp=cp, D=D)
 
 
@@ -329,6 +334,11 @@ def init_state(cfg):
     Ys = float(th.Y_eq(cfg, np.array([cfg["T_drop"]]))[0])
     R_inf = 4e-3 if cfg["const_props_check"] else 2.0 * cfg["D0"]
     omega = np.where(alpha >= 0.5, yeq, stefan_profile(cfg, G, Ys, R_inf))
+    solid = solid_mask(cfg, G)
+    if solid is not None:        # the fibre: no liquid, the liquid's initial temperature, no vapour
+        alpha = np.where(solid, 0.0, alpha)
+        T = np.where(solid, cfg["T_drop"], T)
+        omega = np.where(solid, 0.0, omega)
     u = [np.zeros(fshape(G, a)) if a in G.act else None for a in range(3)]
     if G.bc[G.s][0] == FORCED:
         _face_slab(u[G.s], G.s, 0)[...] = cfg["u_inflow"]
@@ -345,6 +355,16 @@ def _dist_centre(cfg, G):
     for a in G.act:
         d2 = d2 + (X[a] - cfg["xc"][a]) ** 2
     return np.sqrt(d2)
+
+
+def solid_mask(cfg, G):
+    """The spherical fibre's cells (Sec. 3.1.1 and Table tableboundary, "sphere" row;
+    reading R32): with cfg["fiber"] = 1, every cell whose centre lies closer than D_f
+    (cfg["fiber_radius"]) to the droplet centre is solid (a staircase sphere); None
+    without a fibre."""
+    if not cfg.get("fiber", 0):
+        return None
+    return _dist_centre(cfg, G) < cfg["fiber_radius"]
 
 
 def conduction_profile(cfg, G):
@@ -395,13 +415,23 @@ def thermo_pin(cfg, G, alpha, T, omega):
     return omega, rhoG
 
 
-def grad_central(G, P, core=None):
-    """Central-difference gradient of a padded cell field (inactive axes: 0)."""
+def grad_central(G, P, core=None, solid=None):
+    """Central-difference gradient of a padded cell field (inactive axes: 0).  With a
+    solid mask, a neighbour inside the fibre takes the cell's own value (zero gradient
+    across the sphere, reading R32)."""
     n = G.n
+    if solid is not None:
+        Ps = _pad(G, solid)
+        c0 = _view(G, P, n)
     g = []
     for a in range(3):
         if a in G.act:
-            g.append((_view(G, P, n, {a: 1}) - _view(G, P, n, {a: -1})) / (2.0 * G.h[a]))
+            hi = _view(G, P, n, {a: 1})
+            lo = _view(G, P, n, {a: -1})
+            if solid is not None:
+                hi = np.where(_view(G, Ps, n, {a: 1}), c0, hi)
+                lo = np.where(_view(G, Ps, n, {a: -1}), c0, lo)
+            g.append((hi - lo) / (2.0 * G.h[a]))
         else:
             g.append(np.zeros(n))
     return g
@@ -436,14 +466,17 @@ def evaporation_flux(cfg, G, alpha, omega, rhoG, u, T):
     """
     n = G.n
     flags = 0
+    solid = solid_mask(cfg, G)
     Pa = pad_scalar(G, alpha, "alpha")
-    g = grad_central(G, Pa)
+    g = grad_central(G, Pa, solid=solid)
     gm = np.sqrt(sum(g[a] * g[a] for a in G.act))
     iface = gm > 1e-8 / G.hmin
+    if solid is not None:
+        iface &= ~solid
     # total flux j at every cell (only gathered at adjacent cells)
-    pr = props(cfg, alpha, rhoG, omega, T)
+    pr = props(cfg, alpha, rhoG, omega, T, solid)
     Pw = pad_scalar(G, omega, "TO", u=u, amb=0.0)
-    gw = grad_central(G, Pw)
+    gw = grad_central(G, Pw, solid=solid)
     vc = cell_velocity(G, u)
     j = [(-pr["rho"] * pr["D"] * gw[a] + pr["rho"] * omega * vc[a]) if a in G.act else None for a in range(3)]
     mraw = np.zeros(n)
@@ -468,6 +501,8 @@ def evaporation_flux(cfg, G, alpha, omega, rhoG, u, T):
             if not inside:
                 break
             q = tuple(q)
+            if solid is not None and solid[q]:
+                continue                  # the march passes over the fibre's cells
             if alpha[q] < ALPHA_GAS:
                 found = q
                 break
@@ -543,9 +578,10 @@ def alpha_advection(cfg, G, alpha_star, u, dt):
     Returns (alpha_new, clip_volume, n_clipped).
     """
     n = G.n
+    solid = solid_mask(cfg, G)
     phi = face_flux(G, u, dt)
     Pa = pad_scalar(G, alpha_star, "alpha")
-    g = grad_central(G, Pa)
+    g = grad_central(G, Pa, solid=solid)
     Pg = [_pad(G, g[a]) if a in G.act else None for a in range(3)]
     FL = [None] * 3
     AF = [None] * 3
@@ -573,13 +609,20 @@ def alpha_advection(cfg, G, alpha_star, u, dt):
     lo_v = np.minimum(alpha_star, alphaL)
     amax = hi_v.copy()
     amin = lo_v.copy()
+    Ps = _pad(G, solid) if solid is not None else None
     for a in G.act:
         for sh in (-1, 1):
             # neighbours outside the domain do not take part: pad with the cell's own value
             Ph = pad_scalar(G, hi_v, "zg")
             Pl = pad_scalar(G, lo_v, "zg")
-            amax = np.maximum(amax, _view(G, Ph, n, {a: sh}))
-            amin = np.minimum(amin, _view(G, Pl, n, {a: sh}))
+            nh = _view(G, Ph, n, {a: sh})
+            nl = _view(G, Pl, n, {a: sh})
+            if Ps is not None:       # nor do the fibre's cells
+                ns = _view(G, Ps, n, {a: sh})
+                nh = np.where(ns, hi_v, nh)
+                nl = np.where(ns, lo_v, nl)
+            amax = np.maximum(amax, nh)
+            amin = np.minimum(amin, nl)
     amax = np.minimum(amax, 1.0)
     amin = np.maximum(amin, 0.0)
     Pp = np.zeros(n)
@@ -721,7 +764,7 @@ def alpha_advection_geometric(cfg, G, alpha_star, u, dt):
     return clipped, clip_vol, nclip, a
 
 
-def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=None, pin_val=None):
+def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=None, pin_val=None, solid=None):
     """S5 / S6: backward-Euler diffusion, explicit limited-linear-upwind convection.
 
     coef_t V (phi - phi^n)/dt + coef_t [sum_f F_f phi_f - phi_P sum_f F_f]
@@ -731,7 +774,10 @@ def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=Non
     the face; with the paper's mixture rule for k and rho D an arithmetic mean
     lets the liquid-side values leak one cell into the gas).  Dirichlet faces (forced inlet, inflowing open
     faces) use gamma_P A_b/(h/2) towards amb.  Rows in pin_mask are fixed at
-    pin_val and eliminated symmetrically.
+    pin_val and eliminated symmetrically.  With a fibre (solid mask, reading R32) the
+    solid cells carry gamma = 0, so the harmonic mean closes every face of the sphere
+    (two zeros give 0), the faces of the sphere carry no velocity, and a far upwind
+    value inside the fibre is replaced by the near one (zero gradient).
     """
     n = G.n
     P = pad_scalar(G, phi_n, "TO", u=u, amb=amb)
@@ -746,6 +792,10 @@ def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=Non
         R = _view(G, P, fs, {a: 0})
         LL = _view(G, P, fs, {a: -2})
         RR = _view(G, P, fs, {a: 1})
+        if solid is not None:
+            Ps = _pad(G, solid)
+            LL = np.where(_view(G, Ps, fs, {a: -2}), L, LL)
+            RR = np.where(_view(G, Ps, fs, {a: 1}), R, RR)
         F = u[a] * G.A[a]
         pos = F >= 0.0
         val = np.where(pos, lim_upwind(LL, L, R), lim_upwind(RR, R, L))
@@ -764,7 +814,8 @@ def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=Non
         flux[a] = F * val
         gL = _view(G, Pg, fs, {a: -1})
         gR = _view(G, Pg, fs, {a: 0})
-        cf = 2.0 * gL * gR / (gL + gR) * G.A[a] / G.h[a]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            cf = np.where(gL + gR > 0.0, 2.0 * gL * gR / (gL + gR), 0.0) * G.A[a] / G.h[a]
         sl = [slice(None)] * 3
         sl[a] = slice(1, n[a])
         coup[a] = cf[tuple(sl)]
@@ -828,6 +879,7 @@ def momentum_predictor(cfg, G, st, pr, alpha, dt, parts=None):
     """
     n = G.n
     u = st["u"]
+    solid = solid_mask(cfg, G)
     rho, mu = pr["rho"], pr["mu"]
     xi = xi_field(cfg, G)
     Prho = pad_scalar(G, rho, "zg")
@@ -989,7 +1041,25 @@ def momentum_predictor(cfg, G, st, pr, alpha, dt, parts=None):
         if parts is not None:
             parts[c] = dict(sl=sl, shape=tuple(ms), d_visc=d_visc[sl], coup=cpl, adv=t_adv[sl],
                             visc_T=t_vT[sl], force=t_force[sl], V_f=V_f[sl])
-        x = solve_box(tuple(ms), diag[sl], cpl, rhs[sl])
+        dsol, rsol = diag[sl], rhs[sl]
+        if solid is not None:
+            # faces of the sphere (a fibre cell on either side, reading R32): no slip and no
+            # penetration, u* = 0; a neighbour's coupling to one of them goes into that
+            # neighbour's diagonal (the known value 0)
+            Ps = _pad(G, solid)
+            B = (_view(G, Ps, fs, {c: -1}) | _view(G, Ps, fs, {c: 0}))[sl]
+            dsol, rsol = dsol.copy(), np.where(B, 0.0, rsol)
+            for a in G.act:
+                lo = [slice(None)] * 3
+                hi = [slice(None)] * 3
+                lo[a] = slice(0, ms[a] - 1)
+                hi[a] = slice(1, ms[a])
+                lo, hi = tuple(lo), tuple(hi)
+                cc = cpl[a]
+                dsol[lo] += np.where(~B[lo] & B[hi], cc, 0.0)
+                dsol[hi] += np.where(B[lo] & ~B[hi], cc, 0.0)
+                cpl[a] = np.where(B[lo] | B[hi], 0.0, cc)
+        x = solve_box(tuple(ms), dsol, cpl, rsol)
         us = ustar[c]
         us[sl] = x
         for side in (0, 1):
@@ -1016,8 +1086,9 @@ def projection(cfg, G, st, ustar, pr, mdot, alpha, rhoG_old, rhoG_new, dt, rhoL_
     """
     n = G.n
     rho = pr["rho"]
+    solid = solid_mask(cfg, G)
     vc = cell_velocity(G, st["u"])
-    gr = grad_central(G, pad_scalar(G, rhoG_new, "zg"))
+    gr = grad_central(G, pad_scalar(G, rhoG_new, "zg"), solid=solid)
     adv = sum(vc[a] * gr[a] for a in G.act)
     rL1 = cfg["rho_l"] if rhoL_new is None else rhoL_new
     S = mdot * (1.0 / rhoG_new - 1.0 / rL1) - (1.0 - alpha) / rhoG_new * ((rhoG_new - rhoG_old) / dt + adv)
@@ -1027,7 +1098,9 @@ def projection(cfg, G, st, ustar, pr, mdot, alpha, rhoG_old, rhoG_new, dt, rhoL_
         advl = sum(vc[a] * grl[a] for a in G.act)
         expand = alpha / rhoL_new * ((rhoL_new - rhoL_old) / dt + advl)
         S = S - expand
-    diag, coup, beta = pressure_system(G, rho)
+    if solid is not None:
+        S = np.where(solid, 0.0, S)      # the fibre holds no fluid: no continuity source
+    diag, coup, beta = pressure_system(G, rho, solid)
     div_star = divergence_sum(G, [ustar[a] * G.A[a] if a in G.act else None for a in range(3)])
     rhs = (S * G.V - div_star) / dt
     dp = solve_box(n, diag, coup, rhs)
@@ -1043,21 +1116,27 @@ def projection(cfg, G, st, ustar, pr, mdot, alpha, rhoG_old, rhoG_new, dt, rhoL_
     return unew, st["p"] + dp, dp, S, (diag, coup, rhs), expand
 
 
-def pressure_system(G, rho):
+def pressure_system(G, rho, solid=None):
     """Variable-density pressure operator of Eq. (pequation):
     (L x)_P = sum_f beta_f (x_P - x_N) + sum_open beta_b x_P,
     beta_f = A_f/(rho_f h) with rho_f the arithmetic face mean, beta_b =
     A_b/(rho_P h/2) on open (p_rgh = p_ext) faces, zero on walls, the axis and
-    a forced inlet.  Returns (diag, couplings, beta per face)."""
+    a forced inlet.  With a fibre (reading R32) beta vanishes on the faces of the
+    sphere (zero normal gradient) and each solid cell's row is decoupled with the
+    diagonal 2 d V_P / (h_min^2 rho_P) (d the active axes), so that its increment is
+    0.  Returns (diag, couplings, beta per face)."""
     n = G.n
     Prho = pad_scalar(G, rho, "zg")
     diag = np.zeros(n)
     coup = {}
     beta = [None] * 3
+    Ps = _pad(G, solid) if solid is not None else None
     for a in G.act:
         fs = fshape(G, a)
         rho_f = 0.5 * (_view(G, Prho, fs, {a: -1}) + _view(G, Prho, fs, {a: 0}))
         b = G.A[a] / (rho_f * G.h[a])
+        if Ps is not None:
+            b = np.where(_view(G, Ps, fs, {a: -1}) | _view(G, Ps, fs, {a: 0}), 0.0, b)
         for side in (0, 1):
             fidx = 0 if side == 0 else n[a]
             cidx = 0 if side == 0 else n[a] - 1
@@ -1071,6 +1150,8 @@ def pressure_system(G, rho):
         sl = [slice(None)] * 3
         sl[a] = slice(1, n[a])
         coup[a] = b[tuple(sl)]
+    if solid is not None:
+        diag = np.where(solid, 2.0 * len(G.act) * G.V / (G.hmin * G.hmin * rho), diag)
     return diag, coup, beta
 
 
@@ -1145,10 +1226,12 @@ def step(cfg, st, keep=False):
     if nclip:
         flags |= FLAG_ALPHA_CLIPPED
     # S4
-    pr = props(cfg, alpha_new, rhoG_old, omega, T)
+    solid = solid_mask(cfg, G)
+    pr = props(cfg, alpha_new, rhoG_old, omega, T, solid)
     # S5
     if (mask & PHYS_ENERGY) and not const:
-        T_new = scalar_transport(cfg, G, T, pr["rho"] * pr["cp"], pr["k"], -mdot * cfg["Lv"], u, dt, cfg["T_amb"])
+        T_new = scalar_transport(cfg, G, T, pr["rho"] * pr["cp"], pr["k"], -mdot * cfg["Lv"], u, dt, cfg["T_amb"],
+                                 solid=solid)
     else:
         T_new = T.copy()
     # S6
@@ -1156,7 +1239,7 @@ def step(cfg, st, keep=False):
     pin = alpha_new >= 0.5
     if mask & PHYS_SPECIES:
         omega_new = scalar_transport(cfg, G, omega, pr["rho"], pr["rho"] * pr["D"], np.zeros(G.n), u, dt, 0.0,
-                                     pin_mask=pin, pin_val=yeq_new)
+                                     pin_mask=pin, pin_val=yeq_new, solid=solid)
     else:
         omega_new = np.where(pin, yeq_new, omega)
     rhoG_new = th.rho_gas(cfg, T_new, omega_new)
@@ -1190,8 +1273,11 @@ def diagnostics(cfg, st):
     alpha = st["alpha"]
     V_l = w * float(np.sum(alpha * G.V))
     d_eq = (6.0 * V_l / math.pi) ** (1.0 / 3.0)
-    g = grad_central(G, pad_scalar(G, alpha, "alpha"))
+    solid = solid_mask(cfg, G)
+    g = grad_central(G, pad_scalar(G, alpha, "alpha"), solid=solid)
     gm = np.sqrt(sum(g[a] * g[a] for a in G.act))
+    if solid is not None:
+        gm = np.where(solid, 0.0, gm)     # the fibre's cells are not part of the surface
     sw = float(np.sum(gm * G.V))
     Ts = float(np.sum(st["T"] * gm * G.V)) / sw if sw > 0.0 else 0.0
     mdot = st.get("mdot", np.zeros(G.n))

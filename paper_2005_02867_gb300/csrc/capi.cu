@@ -34,6 +34,7 @@ struct dctx {
   double *hT = nullptr, *hW = nullptr, *hu[3] = {nullptr, nullptr, nullptr};
   double *rho = nullptr, *mu = nullptr, *kc = nullptr, *cp = nullptr, *Dm = nullptr, *yq = nullptr, *dp = nullptr, *S = nullptr;
   int* adj = nullptr;
+  unsigned char* solid = nullptr;    // the fibre's cells (droplet_config.fiber = 1), else null
   double *bD = nullptr, *bc[3] = {nullptr, nullptr, nullptr}, *brhs = nullptr, *bx = nullptr;
   // box systems (D, c0, c1, c2, rhs, x each) of the joint momentum solve: of the second and
   // third velocity component (the first uses the shared box), or of every component when
@@ -103,6 +104,10 @@ static int check_cfg(const droplet_config& c) {
   if (c.wait_limit < 0 || (c.solver_select != 0 && c.solver_select != 1)) return DROPLET_ERR_ARG;
   if (!(c.co_max >= 0.0) || !std::isfinite(c.co_max)) return DROPLET_ERR_ARG;
   if (c.adv_scheme != 0 && c.adv_scheme != 1) return DROPLET_ERR_ARG;
+  // the fibre: FP64 throughout, the compressive advection, a constant liquid density
+  if (c.fiber != 0 && c.fiber != 1) return DROPLET_ERR_ARG;
+  if (c.fiber == 1 && (c.precision != 0 || c.adv_scheme != 0 || c.drho_l_dT != 0.0 || !(c.fiber_radius > 0.0)))
+    return DROPLET_ERR_ARG;
   // a liquid density linear in T stays positive up to the ambient and boiling temperatures
   if (!std::isfinite(c.drho_l_dT) || !(c.rho_l + c.drho_l_dT * (c.T_amb - c.T_drop) > 0.0) ||
       !(c.rho_l + c.drho_l_dT * (c.Tb - c.T_drop) > 0.0))
@@ -114,6 +119,29 @@ static int check_cfg(const droplet_config& c) {
     if (nn + plane >= (1LL << 31)) return DROPLET_ERR_ARG;
   }
   return 0;
+}
+
+// Products rounded on their own (no fused multiply-add on any host), so that the fibre's
+// cells below are those of the same formula evaluated operation by operation.
+static __attribute__((noinline)) double mul_rounded(double a, double b) { return a * b; }
+
+// The fibre's solid cells (Sec. 3.1.1, Table tableboundary "sphere" row): the cells whose
+// centre lies closer than fiber_radius to the droplet centre,
+// sqrt(sum over the active axes of ((i_a + 1/2) h_a - xc_a)^2) < fiber_radius.
+static void fibre_cells(const Geo& g, const droplet_config& c, std::vector<unsigned char>& m) {
+  m.assign((size_t)g.N, 0);
+  const int na = nact(g);
+  for (int k = 0; k < g.n[2]; ++k)
+    for (int j = 0; j < g.n[1]; ++j)
+      for (int i = 0; i < g.n[0]; ++i) {
+        const int q[3] = {i, j, k};
+        double d2 = 0.0;
+        for (int a = 0; a < na; ++a) {
+          const double t = mul_rounded(q[a] + 0.5, g.h[a]) - c.xc[a];
+          d2 = d2 + mul_rounded(t, t);
+        }
+        m[(size_t)i + (size_t)g.n[0] * ((size_t)j + (size_t)g.n[1] * k)] = std::sqrt(d2) < c.fiber_radius ? 1 : 0;
+      }
 }
 
 static void make_geo(const droplet_config& c, Geo& g) {
@@ -213,8 +241,8 @@ static void free_all(dctx* c) {
   }
   for (auto& set : c->xb)
     for (auto& q : set) { cudaFree(q); q = nullptr; }
-  cudaFree(c->adj); cudaFree(c->flags); cudaFree(c->dirty); cudaFree(c->astar_f);
-  c->adj = nullptr; c->flags = nullptr; c->dirty = nullptr; c->astar_f = nullptr;
+  cudaFree(c->adj); cudaFree(c->flags); cudaFree(c->dirty); cudaFree(c->astar_f); cudaFree(c->solid);
+  c->adj = nullptr; c->flags = nullptr; c->dirty = nullptr; c->astar_f = nullptr; c->solid = nullptr;
   {
     float** sh[] = {&c->s32.T, &c->s32.w, &c->s32.k, &c->s32.gD, &c->s32.mu, &c->s32.u[0], &c->s32.u[1], &c->s32.u[2]};
     for (auto q : sh) { cudaFree(*q); *q = nullptr; }
@@ -301,6 +329,18 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
       cudaMalloc((void**)&c->dirty, sizeof(int)) != cudaSuccess ||
       cudaMallocHost((void**)&c->hscal, sizeof(double) * SC_COUNT) != cudaSuccess ||
       cudaMallocHost((void**)&c->hflags, sizeof(unsigned)) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_NOMEM; }
+  if (cfg.fiber == 1) {
+    std::vector<unsigned char> m;
+    fibre_cells(g, cfg, m);
+    if (cudaMalloc((void**)&c->solid, (size_t)N) != cudaSuccess) { free_all(c); delete c; return DROPLET_ERR_NOMEM; }
+    if (cudaMemcpy(c->solid, m.data(), (size_t)N, cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_all(c);
+      delete c;
+      return DROPLET_ERR_CUDA;
+    }
+    g.fib = 1;
+    g.solid = c->solid;
+  }
   c->solver.f32_helm = c->cfg.precision == 1;
   // latency-bound sizes: persistent solvers (in a batch each droplet is later given an
   // SM budget so that the cooperative solves of all branches fit the GPU together)
@@ -424,7 +464,7 @@ static int one_step(dctx* c, int* nc_flag) {
   ++g_launches, k_alpha_source<<<gc, TPB, 0, st>>>(g, p, c->alpha, c->mraw, c->scal, c->T, c->expand, c->mdot, c->astar,
                                                    c->astar_f, c->flags, c->dirty);
   // S3, and S4 (the mixture properties) in the kernel that forms alpha^{n+1}
-  const PropsOut po{c->rhoG_old, c->omega, c->T, c->rho, c->mu, c->kc, c->cp, c->Dm, c->s32};
+  const PropsOut po{c->rhoG_old, c->omega, c->T, c->rho, c->mu, c->kc, c->cp, c->Dm, c->s32, c->solid};
   if ((mask & DROPLET_PHYS_FLOW) && c->cfg.adv_scheme == 1) {
     // geometric advection, FP64 in both precisions: the planes in FL (normal) and AF[0]
     // (constant), the sweeps' intermediate alpha in aL and Rp
@@ -1022,7 +1062,7 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
   if (cf.physics_mask & DROPLET_PHYS_FLOW) return adjoint_flow(cc, n_steps, ckpt_every, J, dJ_dTamb, dJ_dDg, dJ_dT0, nT0);
   if (cf.physics_mask != (DROPLET_PHYS_EVAP | DROPLET_PHYS_ENERGY | DROPLET_PHYS_SPECIES) || cf.precision != 0 ||
       cf.eq_model != 0 || cf.const_props_check != 0 || cf.bc_mode != 0 || cf.co_max != 0.0 || cf.drho_l_dT != 0.0 ||
-      x->step != 0)
+      cf.fiber != 0 || x->step != 0)
     return DROPLET_ERR_ARG;
   Geo& g = x->g;
   Phys& p = x->p;
@@ -1375,7 +1415,7 @@ static bool flow_adjoint_ok(const dctx* x) {
   const droplet_config& cf = x->cfg;
   return cf.physics_mask == (DROPLET_PHYS_EVAP | DROPLET_PHYS_ENERGY | DROPLET_PHYS_SPECIES | DROPLET_PHYS_FLOW) &&
          cf.precision == 0 && cf.eq_model == 0 && cf.const_props_check == 0 && cf.co_max == 0.0 &&
-         cf.drho_l_dT == 0.0 && cf.adv_scheme == 0;
+         cf.drho_l_dT == 0.0 && cf.adv_scheme == 0 && cf.fiber == 0;
 }
 
 static int adjoint_flow(droplet_ctx* cc, int n_steps, int ckpt_every, double* J, double* dJ_dTamb, double* dJ_dDg,

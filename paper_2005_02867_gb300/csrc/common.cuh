@@ -44,6 +44,10 @@ struct Geo {
   // gxc[c] = sum over a != c of g_a h_a / 2
   double gh[3], gxc[3];
   int gmask;
+  // the spherical fibre (Table tableboundary, "sphere" row): fib = 1 with solid, one byte
+  // per cell, 1 for the cells whose centre lies closer than D_f to the droplet centre
+  int fib;
+  const unsigned char* solid;
   long long N;       // number of cells (< 2^31)
 };
 
@@ -112,6 +116,22 @@ __device__ __forceinline__ double faceA(const Geo& g, int a, int i) {
 __device__ __forceinline__ double areaN(const Geo& g, int a, double rl) {
   if (g.axisym) return rl * (a == 0 ? g.h[1] : g.h[0]);
   return g.area3[a];
+}
+
+// ------------------------------------------------------------------ the fibre
+// A cell of the fibre: closed to every flux, holding no fluid (zero-gradient and no-slip
+// conditions on the sphere's faces).  All tests are false without a fibre (g.fib = 0).
+__device__ __forceinline__ bool solid_cell(const Geo& g, long long id) { return g.fib && g.solid[id]; }
+// cell (i, j, k), possibly outside the domain (then not solid)
+__device__ __forceinline__ bool solid_nb(const Geo& g, int i, int j, int k) {
+  return g.fib && (unsigned)i < (unsigned)g.n[0] && (unsigned)j < (unsigned)g.n[1] && (unsigned)k < (unsigned)g.n[2] &&
+         g.solid[cidx(g, i, j, k)];
+}
+// a face of the sphere: face (i, j, k) of direction a (cells i - e_a and i) with a fibre cell
+// on either side
+__device__ __forceinline__ bool sphere_face(const Geo& g, int a, int i, int j, int k) {
+  if (!g.fib) return false;
+  return solid_nb(g, i - (a == 0), j - (a == 1), k - (a == 2)) || solid_nb(g, i, j, k);
 }
 
 // ------------------------------------------------------------------ ghosts

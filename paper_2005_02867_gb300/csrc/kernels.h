@@ -91,6 +91,7 @@ struct PropsOut {
   const double *rhoG, *omega, *T;
   double *rho, *mu, *kc, *cp, *D;
   Shadow32 s;               // binary32 copies to write (s.T null: none)
+  const unsigned char* solid = nullptr;   // the fibre's cells (null: no fibre): k = D = 0 there
 };
 // u^n rounded to binary32 (faces of every active direction in one launch)
 __global__ void k_faces_f32(const double* u0, const double* u1, const double* u2, float* f0, float* f1, float* f2,

@@ -90,6 +90,12 @@ __global__ void k_init(Geo g, Phys p, double* alpha, double* T, double* omega, d
     w = 1.0 - exp(log(1.0 - Ys) * ww);
     if (r >= Rinf) w = 0.0;
   }
+  if (solid_cell(g, id)) {   // the fibre: no liquid, the liquid's initial temperature, no vapour
+    alpha[id] = 0.0;
+    t = p.T_drop;
+    T[id] = t;
+    w = 0.0;
+  }
   omega[id] = w;
   rhoG[id] = rho_gas(p, t, w);
 }
@@ -130,20 +136,43 @@ __global__ void k_thermo_pin(Geo g, Phys p, const double* alpha, const double* T
   if (boil) atomicOr(flags, (unsigned)DROPLET_FLAG_BOILING);
 }
 
+// the six neighbour values of a central difference at (i, j, k) with those inside the fibre
+// replaced by the cell's own value (zero gradient across the sphere)
+__device__ __forceinline__ void fibre_mask6(const Geo& g, const double* f, int i, int j, int k, double& e, double& w,
+                                            double& n, double& s, double& t, double& b) {
+  const double own = f[cidx(g, i, j, k)];
+  if (solid_nb(g, i + 1, j, k)) e = own;
+  if (solid_nb(g, i - 1, j, k)) w = own;
+  if (solid_nb(g, i, j + 1, k)) n = own;
+  if (solid_nb(g, i, j - 1, k)) s = own;
+  if (g.act3) {
+    if (solid_nb(g, i, j, k + 1)) t = own;
+    if (solid_nb(g, i, j, k - 1)) b = own;
+  }
+}
+
 // central gradient of alpha at cell (i,j,k) with the alpha ghost rule
+// (a neighbour inside the fibre takes the cell's own value: zero gradient across the sphere)
 __device__ __forceinline__ void grad_alpha(const Geo& g, const double* al, int i, int j, int k, double gr[3]) {
-  gr[0] = (cellg(g, al, i + 1, j, k, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i - 1, j, k, R_ALPHA, 0, 0, 0, 0)) * (0.5 * g.ih[0]);
-  gr[1] = (cellg(g, al, i, j + 1, k, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i, j - 1, k, R_ALPHA, 0, 0, 0, 0)) * (0.5 * g.ih[1]);
-  gr[2] = g.act3 ? (cellg(g, al, i, j, k + 1, R_ALPHA, 0, 0, 0, 0) - cellg(g, al, i, j, k - 1, R_ALPHA, 0, 0, 0, 0)) * (0.5 * g.ih[2]) : 0.0;
+  double e = cellg(g, al, i + 1, j, k, R_ALPHA, 0, 0, 0, 0), w = cellg(g, al, i - 1, j, k, R_ALPHA, 0, 0, 0, 0);
+  double n = cellg(g, al, i, j + 1, k, R_ALPHA, 0, 0, 0, 0), s = cellg(g, al, i, j - 1, k, R_ALPHA, 0, 0, 0, 0);
+  double t = g.act3 ? cellg(g, al, i, j, k + 1, R_ALPHA, 0, 0, 0, 0) : 0.0;
+  double b = g.act3 ? cellg(g, al, i, j, k - 1, R_ALPHA, 0, 0, 0, 0) : 0.0;
+  if (g.fib) fibre_mask6(g, al, i, j, k, e, w, n, s, t, b);
+  gr[0] = (e - w) * (0.5 * g.ih[0]);
+  gr[1] = (n - s) * (0.5 * g.ih[1]);
+  gr[2] = g.act3 ? (t - b) * (0.5 * g.ih[2]) : 0.0;
 }
 // grad_alpha, and whether it vanishes identically: equal neighbours on every axis
 // (compared as encodings, on the integer pipe) give exactly +0 differences, so such a
 // flat cell can skip the binary64 arithmetic that depends on the gradient
 __device__ __forceinline__ bool grad_alpha_flat(const Geo& g, const double* al, int i, int j, int k, double gr[3]) {
-  const double e = cellg(g, al, i + 1, j, k, R_ALPHA, 0, 0, 0, 0), w = cellg(g, al, i - 1, j, k, R_ALPHA, 0, 0, 0, 0);
-  const double n = cellg(g, al, i, j + 1, k, R_ALPHA, 0, 0, 0, 0), s = cellg(g, al, i, j - 1, k, R_ALPHA, 0, 0, 0, 0);
-  const double t = g.act3 ? cellg(g, al, i, j, k + 1, R_ALPHA, 0, 0, 0, 0) : 0.0;
-  const double b = g.act3 ? cellg(g, al, i, j, k - 1, R_ALPHA, 0, 0, 0, 0) : 0.0;
+  const double e0 = cellg(g, al, i + 1, j, k, R_ALPHA, 0, 0, 0, 0), w0 = cellg(g, al, i - 1, j, k, R_ALPHA, 0, 0, 0, 0);
+  const double n0 = cellg(g, al, i, j + 1, k, R_ALPHA, 0, 0, 0, 0), s0 = cellg(g, al, i, j - 1, k, R_ALPHA, 0, 0, 0, 0);
+  const double t0 = g.act3 ? cellg(g, al, i, j, k + 1, R_ALPHA, 0, 0, 0, 0) : 0.0;
+  const double b0 = g.act3 ? cellg(g, al, i, j, k - 1, R_ALPHA, 0, 0, 0, 0) : 0.0;
+  double e = e0, w = w0, n = n0, s = s0, t = t0, b = b0;
+  if (g.fib) fibre_mask6(g, al, i, j, k, e, w, n, s, t, b);
   if (__double_as_longlong(e) == __double_as_longlong(w) && __double_as_longlong(n) == __double_as_longlong(s) &&
       __double_as_longlong(t) == __double_as_longlong(b)) {
     gr[0] = gr[1] = gr[2] = 0.0;
@@ -180,7 +209,7 @@ __global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* ome
     const double gm = flat ? 0.0 : norm_rn(gr, na);
     double m = 0.0;
     int found = -1;
-    if (gm > g.gthr) {
+    if (gm > g.gthr && !solid_cell(g, id)) {   // (the fibre's cells are never interface cells)
       double nh[3] = {-gr[0] / gm, -gr[1] / gm, -gr[2] / gm};
       int ci[3] = {i, j, k};
       int q[3] = {0, 0, 0};
@@ -198,6 +227,7 @@ __global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* ome
         if (!inside) break;
         if (!g.act3) q[2] = 0;
         long long qi = cidx(g, q[0], q[1], q[2]);
+        if (solid_cell(g, qi)) continue;   // the march passes over the fibre's cells
         if (alpha[qi] < ALPHA_GAS) found = (int)qi;
       }
       if (found < 0) {
@@ -210,9 +240,14 @@ __global__ void k_evap_raw(Geo g, Phys p, const double* alpha, const double* ome
         int qi, qj, qk;
         decomp(found, g.n[0], g.n[1], qi, qj, qk);
         double gw[3];
-        gw[0] = (cellg(g, omega, qi + 1, qj, qk, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi - 1, qj, qk, R_TO, 0.0, u0, u1, u2)) * (0.5 * g.ih[0]);
-        gw[1] = (cellg(g, omega, qi, qj + 1, qk, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi, qj - 1, qk, R_TO, 0.0, u0, u1, u2)) * (0.5 * g.ih[1]);
-        gw[2] = g.act3 ? (cellg(g, omega, qi, qj, qk + 1, R_TO, 0.0, u0, u1, u2) - cellg(g, omega, qi, qj, qk - 1, R_TO, 0.0, u0, u1, u2)) * (0.5 * g.ih[2]) : 0.0;
+        double we = cellg(g, omega, qi + 1, qj, qk, R_TO, 0.0, u0, u1, u2), ww = cellg(g, omega, qi - 1, qj, qk, R_TO, 0.0, u0, u1, u2);
+        double wn = cellg(g, omega, qi, qj + 1, qk, R_TO, 0.0, u0, u1, u2), ws = cellg(g, omega, qi, qj - 1, qk, R_TO, 0.0, u0, u1, u2);
+        double wt = g.act3 ? cellg(g, omega, qi, qj, qk + 1, R_TO, 0.0, u0, u1, u2) : 0.0;
+        double wb = g.act3 ? cellg(g, omega, qi, qj, qk - 1, R_TO, 0.0, u0, u1, u2) : 0.0;
+        if (g.fib) fibre_mask6(g, omega, qi, qj, qk, we, ww, wn, ws, wt, wb);
+        gw[0] = (we - ww) * (0.5 * g.ih[0]);
+        gw[1] = (wn - ws) * (0.5 * g.ih[1]);
+        gw[2] = g.act3 ? (wt - wb) * (0.5 * g.ih[2]) : 0.0;
         double vc[3];
         vc[0] = 0.5 * (u0[fidx(g, 0, qi, qj, qk)] + u0[fidx(g, 0, qi + 1, qj, qk)]);
         vc[1] = 0.5 * (u1[fidx(g, 1, qi, qj, qk)] + u1[fidx(g, 1, qi, qj + 1, qk)]);
@@ -368,9 +403,14 @@ __device__ __forceinline__ void props_cell(const Phys& p, long long id, double a
   D[id] = a * p.D_l + (1.0 - a) * p.D_gas;
 }
 
-// props_cell into the PropsOut arrays, and their binary32 copies when asked for
+// props_cell into the PropsOut arrays, and their binary32 copies when asked for; the fibre's
+// cells conduct and diffuse nothing (no flux of T or omega across the sphere)
 __device__ __forceinline__ void props_out(const Phys& p, long long id, double a, const PropsOut& po) {
   props_cell(p, id, a, po.rhoG, po.omega, po.T, po.rho, po.mu, po.kc, po.cp, po.D);
+  if (po.solid && po.solid[id]) {
+    po.kc[id] = 0.0;
+    po.D[id] = 0.0;
+  }
   if (po.s.T) {
     po.s.T[id] = f32_rn(po.T[id]);
     po.s.w[id] = f32_rn(po.omega[id]);
@@ -424,6 +464,7 @@ __global__ void k_adv_limit(Geo g, const double* as, const double* aL, const dou
       q[a] += sh;
       if (q[a] < 0 || q[a] >= g.n[a]) continue;
       long long qi = cidx(g, q[0], q[1], q[2]);
+      if (solid_cell(g, qi)) continue;   // nor do the fibre's cells
       const double sq = as[qi], lq = aL[qi];
       amax = imax64(amax, imax64(sq, lq));
       amin = imin64(amin, imin64(sq, lq));
@@ -763,9 +804,17 @@ __global__ void k_alpha_clip_only(Geo g, Phys p, const double* as, double* alpha
 __device__ __forceinline__ double gam(int mode, const double* kc, const double* rho, const double* D, long long q) {
   return mode == 0 ? kc[q] : rho[q] * D[q];
 }
-__device__ __forceinline__ double harm(double x, double y) { return 2.0 * x * y * rcp64(x + y); }
+// (two zero values, the faces between two cells of the fibre, give 0: the sum is tested on
+// the integer pipe)
+__device__ __forceinline__ double harm(double x, double y) {
+  const double t = x + y;
+  return (__double_as_longlong(t) << 1) == 0 ? 0.0 : 2.0 * x * y * rcp64(t);
+}
 // half the harmonic mean, x y / (x + y) (the 2 folded into a host constant)
-__device__ __forceinline__ double harm_half(double x, double y) { return x * y * rcp64(x + y); }
+__device__ __forceinline__ double harm_half(double x, double y) {
+  const double t = x + y;
+  return (__double_as_longlong(t) << 1) == 0 ? 0.0 : x * y * rcp64(t);
+}
 
 template <int NA>
 __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
@@ -812,8 +861,10 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
         // the upwind side's operands chosen by the sign bit of F (integer selects, one
         // limited value; a zero F multiplies it either way)
         const bool pos = __double_as_longlong(F) >= 0;
-        const double far = pos ? cellg(g, phi, LL[0], LL[1], LL[2], R_TO, amb, u0, u1, u2)
-                               : cellg(g, phi, RR[0], RR[1], RR[2], R_TO, amb, u0, u1, u2);
+        double far = pos ? cellg(g, phi, LL[0], LL[1], LL[2], R_TO, amb, u0, u1, u2)
+                         : cellg(g, phi, RR[0], RR[1], RR[2], R_TO, amb, u0, u1, u2);
+        // a far upwind cell inside the fibre: the near one's value (zero gradient)
+        if (g.fib && (pos ? solid_nb(g, LL[0], LL[1], LL[2]) : solid_nb(g, RR[0], RR[1], RR[2]))) far = pos ? vL : vR;
         val = lim_up(far, pos ? vL : vR, pos ? vR : vL);
       }
       net = fma(side ? F : -F, val - phiP, net);
@@ -913,7 +964,9 @@ __device__ __forceinline__ double mu_edge(const Geo& g, const double* mu, double
   return 0.25 * s;
 }
 
-template <int C, int NA>
+// FIB: with the fibre, whose faces are pinned at u* = 0 (no slip, no penetration) and whose
+// neighbouring faces take their coupling to them into the diagonal (the known value 0)
+template <int C, int NA, bool FIB>
 __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1, const double* u2,
                                const double* rho, const double* mu, const double* pr, const double* alpha,
                                const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
@@ -952,6 +1005,13 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
   double u_f = uc[fidx(g, c, f[0], f[1], f[2])];
   const double muLR = muL + muR;
   double d = rV * idt_of(p);
+  if (FIB && sphere_face(g, c, f[0], f[1], f[2])) {   // a face of the sphere: a decoupled row, u* = 0
+    Dg[id] = d;
+    rhs[id] = 0.0;
+    #pragma unroll
+    for (int a = 0; a < NA; ++a) Cc[a][id] = 0.0;
+    return;
+  }
   double r = d * u_f;
   // advection accumulated without its common factor -rho_f V_f
   double s_adv = 0.0, t_vT = 0.0, d_visc = 0.0;
@@ -1019,6 +1079,13 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
         d_visc += kR;
         r += kR * uc[fidx(g, c, fb[0], fb[1], fb[2])];
       }
+      if (FIB) {   // neighbour faces along c on the sphere
+        if (b[c] > 0 && sphere_face(g, c, f[0] - (c == 0), f[1] - (c == 1), f[2] - (c == 2))) {
+          Cc[c][id] = 0.0;
+          d_visc += kL;
+        }
+        if (b[c] < m[c] - 1 && sphere_face(g, c, f[0] + (c == 0), f[1] + (c == 1), f[2] + (c == 2))) d_visc += kR;
+      }
     } else {
       double kp, km;
       if (cart) {
@@ -1045,6 +1112,13 @@ __global__ void k_mom_assemble(Geo g, Phys p, const double* u0, const double* u1
       Cc[a][id] = (b[a] > 0) ? km : 0.0;
       if (b[a] == 0 && (g.bc[a][0] == BC_WALL || g.bc[a][0] == BC_FORCED)) d_visc += 2.0 * km;
       if (b[a] == m[a] - 1 && (g.bc[a][1] == BC_WALL || g.bc[a][1] == BC_FORCED)) d_visc += 2.0 * kp;
+      if (FIB) {   // neighbour faces along a on the sphere
+        if (b[a] > 0 && sphere_face(g, c, f[0] - (a == 0), f[1] - (a == 1), f[2] - (a == 2))) {
+          Cc[a][id] = 0.0;
+          d_visc += km;
+        }
+        if (b[a] < m[a] - 1 && sphere_face(g, c, f[0] + (a == 0), f[1] + (a == 1), f[2] + (a == 2))) d_visc += kp;
+      }
     }
   }
   if (!cart && c == 0 && r_f > 0.0) d_visc = d_visc + 2.0 * (0.5 * muLR) * V_f / (r_f * r_f);
@@ -1080,7 +1154,11 @@ __global__ void k_mom_scatter(Geo g, Phys p, const double* x, double* us) {
     b[c] = fc - 1;
     return x[(long long)b[0] + (long long)mb[0] * ((long long)b[1] + (long long)mb[1] * b[2])];
   };
-  if (f[c] > 0 && f[c] < g.n[c]) { us[id] = box(f[c]); return; }
+  if (f[c] > 0 && f[c] < g.n[c]) {
+    // (a face of the fibre's sphere: exactly 0, the value its decoupled row solves for)
+    us[id] = sphere_face(g, c, f[0], f[1], f[2]) ? 0.0 : box(f[c]);
+    return;
+  }
   int side = f[c] == 0 ? 0 : 1;
   int kind = (side ? g.bc[c][1] : g.bc[c][0]);
   if (kind == BC_OPEN) us[id] = box(side ? g.n[c] - 1 : 1);
@@ -1152,7 +1230,12 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
     int qp[3] = {i, j, k}, qm[3] = {i, j, k};
     qp[a] += 1;
     qm[a] -= 1;
-    double gr = (cellg(g, rgn, qp[0], qp[1], qp[2], R_ZG, 0, 0, 0, 0) - cellg(g, rgn, qm[0], qm[1], qm[2], R_ZG, 0, 0, 0, 0)) * (0.5 * g.ih[a]);
+    double rgp = cellg(g, rgn, qp[0], qp[1], qp[2], R_ZG, 0, 0, 0, 0), rgm = cellg(g, rgn, qm[0], qm[1], qm[2], R_ZG, 0, 0, 0, 0);
+    if (g.fib) {   // zero gradient across the fibre's sphere
+      if (solid_nb(g, qp[0], qp[1], qp[2])) rgp = rgn[id];
+      if (solid_nb(g, qm[0], qm[1], qm[2])) rgm = rgn[id];
+    }
+    double gr = (rgp - rgm) * (0.5 * g.ih[a]);
     adv = adv + vc * gr;
     if (expand) {   // rho_L(T^{n+1}) with zero-gradient ghosts: the liquid density of the ghost temperature
       double gl = (rho_liq(p, cellg(g, T1, qp[0], qp[1], qp[2], R_ZG, 0, 0, 0, 0)) -
@@ -1170,6 +1253,8 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
   } else {
     s = mdot[id] * (irn - p.irho_l) - (1.0 - alpha[id]) * irn * ((rn - rgo[id]) * idt_of(p) + adv);
   }
+  const bool sol = solid_cell(g, id);
+  if (sol) s = 0.0;   // the fibre holds no fluid: no continuity source
   S[id] = s;
   double dg = 0.0, div = 0.0;
   double rP = rho[id];
@@ -1183,13 +1268,18 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
       int Lc[3] = {i, j, k};
       Lc[a] -= 1;
       // A / h over the mean density of the two cells (3D: 2 A / h from the host)
-      const double ir = rcp64(rho[cidx(g, Lc[0], Lc[1], Lc[2])] + rP);
+      const long long li = cidx(g, Lc[0], Lc[1], Lc[2]);
+      const double ir = rcp64(rho[li] + rP);
       cl = NA == 3 ? g.aih2[a] * ir : faceA(g, a, i) * g.ih[a] * (2.0 * ir);
+      if (g.fib && (sol || g.solid[li])) cl = 0.0;   // a face of the sphere: zero normal gradient
     }
     C[a][id] = cl;
     if (ci[a] == 0 && g.bc[a][0] == BC_OPEN) dg += faceA(g, a, i) * (2.0 * g.ih[a]) / rP;
     if (ci[a] == g.n[a] - 1 && g.bc[a][1] == BC_OPEN) dg += faceA(g, a, hi[0]) * (2.0 * g.ih[a]) / rP;
   }
+  // a cell of the fibre: a decoupled row (its increment is 0), of the size of a Laplacian
+  // diagonal, 2 d V / (h_min^2 rho)
+  if (sol) dg = 2.0 * na * cellV(g, i) / (g.hmin * g.hmin * rP);
   Dg[id] = dg;
   rhs[id] = (s * cellV(g, i) - div) * idt_of(p);
 }
@@ -1211,6 +1301,7 @@ __device__ __forceinline__ void correct_face(const Geo& g, const Phys& p, const 
     if (f[c] > 0 && f[c] < g.n[c]) {
       long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, f[0], f[1], f[2]);
       corr = dt_of(p) * g.ih[c] * (2.0 * rcp64(rho[li] + rho[ri])) * (dp[ri] - dp[li]);
+      if (g.fib && (g.solid[li] || g.solid[ri])) corr = 0.0;   // the sphere's faces keep u* = 0
     } else {
       int side = f[c] == 0 ? 0 : 1;
       if ((side ? g.bc[c][1] : g.bc[c][0]) == BC_OPEN) {
@@ -1289,7 +1380,7 @@ __global__ void __launch_bounds__(TPB, 4) k_diag(Geo g, Phys p, const double* al
     s[0] += a * V;
     const double md = mdot[id];
     if (md != 0.0) s[1] += md * V;
-    if (!grad_alpha_flat(g, alpha, i, j, k, gr)) {   // (a flat cell adds zeros)
+    if (!grad_alpha_flat(g, alpha, i, j, k, gr) && !solid_cell(g, id)) {   // (a flat cell adds zeros; the fibre none)
       double gm = sqrt(gr[0] * gr[0] + gr[1] * gr[1] + (g.act3 ? gr[2] * gr[2] : 0.0));
       s[2] += T[id] * gm * V;
       s[3] += gm * V;
@@ -1430,14 +1521,21 @@ void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const
 
 void L_mom_assemble(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32*) {
   ++g_launches;
+#define DG_MOM(CC, NN, FF) k_mom_assemble<CC, NN, FF><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs)
   if (nact(g) == 3) {
-    if (c == 0) k_mom_assemble<0, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
-    else if (c == 1) k_mom_assemble<1, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
-    else k_mom_assemble<2, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
+    if (g.fib) {
+      if (c == 0) DG_MOM(0, 3, true); else if (c == 1) DG_MOM(1, 3, true); else DG_MOM(2, 3, true);
+    } else {
+      if (c == 0) DG_MOM(0, 3, false); else if (c == 1) DG_MOM(1, 3, false); else DG_MOM(2, 3, false);
+    }
   } else {
-    if (c == 0) k_mom_assemble<0, 2><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
-    else k_mom_assemble<1, 2><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, mu, pr, alpha, xi, Dg, c0, c1, c2, rhs);
+    if (g.fib) {
+      if (c == 0) DG_MOM(0, 2, true); else DG_MOM(1, 2, true);
+    } else {
+      if (c == 0) DG_MOM(0, 2, false); else DG_MOM(1, 2, false);
+    }
   }
+#undef DG_MOM
 }
 
 void L_mom_scatter(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* x, double* us) {

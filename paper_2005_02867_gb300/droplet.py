@@ -35,7 +35,7 @@ class DropletConfig(ctypes.Structure):
         ("seed", ctypes.c_ulonglong), ("T_perturb", _c_dbl),
         ("const_props_check", _c_int), ("physics_mask", _c_int), ("C_alpha", _c_dbl),
         ("mg_tile", _c_int * 2), ("wait_limit", _c_int), ("solver_select", _c_int), ("co_max", _c_dbl),
-        ("adv_scheme", _c_int), ("drho_l_dT", _c_dbl),
+        ("adv_scheme", _c_int), ("drho_l_dT", _c_dbl), ("fiber", _c_int),
     ]
 
 

@@ -31,7 +31,7 @@ BASE = dict(
     Tb=371.6, Lv=3.17e5, M_l=0.100204, rho_l=684.0, cp_l=2250.0, k_l=0.12, mu_l=3.9e-4, D_l=1e-9,
     M_g=0.028013, cp_g=1100.0, cp_v=1100.0, k_g=0.055, mu_g=3.5e-5, D_g=5e-5,
     Tc=540.0, Pc=27.4e5, omega_ac=0.35, Tc_g=126.2, Pc_g=33.9e5, omega_g=0.037, kij=0.0,
-    xi0=1.0, fiber_radius=5e-5,
+    xi0=1.0, fiber_radius=5e-5, fiber=0,
     dt=1e-5, precision=0,
     cg_rtol=1e-12, cg_maxit=400, helm_rtol=1e-13, helm_maxit=400,
     seed=20050286, T_perturb=0.0,

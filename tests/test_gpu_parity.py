@@ -102,6 +102,14 @@ EXPANDING = {name + "-expanding": (dict(cfg, drho_l_dT=-0.9), pre)
              if name in ("axisym-gravity", "axisym-natural", "cart3d-natural-16", "axisym-gravity-launched",
                          "axisym-gravity-geometric", "cart3d-ragged-12x10x14-geometric")}
 CASES.update(EXPANDING)
+# The spherical fibre inside the droplet (fiber = 1, Table tableboundary "sphere" row): 8 solid
+# cells in 2D (radius 0.15 mm at h = 62.5 um), 56 in 3D (0.22 mm at h = 0.1 mm), on both
+# solver paths, with natural convection, gravity and a forced flow past it
+FIBRE = {name + "-fibre": (dict(cfg, fiber=1, fiber_radius=1.5e-4 if cfg["geom"] == 0 else 2.2e-4), pre)
+         for name, (cfg, pre) in list(CASES.items())
+         if name in ("axisym-gravity", "axisym-gravity-launched", "axisym-forced-inlet", "cart3d-natural-16",
+                     "cart3d-natural-16-launched", "cart3d-pr-forced-16")}
+CASES.update(FIBRE)
 
 
 @pytest.mark.parametrize("name", list(CASES))

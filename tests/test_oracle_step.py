@@ -534,3 +534,73 @@ def test_thermal_expansion_conserves_the_liquid_mass_under_refinement():
     # constant density: the volume stays up to the clipping
     g0, m0, _, _ = _expansion_run(32, drho=0.0)
     assert abs(g0) < 1e-6 and abs(m0) < 1e-6, (g0, m0)
+
+
+# ---------------------------------------------------------------- the spherical fibre (reading R32)
+FIBRE_2D = dict(n=(32, 64, 1), L=(2e-3, 4e-3, 0.0), xc=(0.0, 2e-3, 0.0), D0=1e-3, g=(0.0, -9.81, 0.0),
+                fiber=1, fiber_radius=1.5e-4, dt=2e-5)
+FIBRE_3D = dict(geom=W.GEOM_CART3D, n=(16, 16, 16), L=(1.6e-3,) * 3, xc=(0.8e-3,) * 3, D0=0.8e-3,
+                g=(0.0, 0.0, -9.81), fiber=1, fiber_radius=2.2e-4, dt=1e-5)
+
+
+def _sphere_faces(G, solid, c):
+    Ps = O._pad(G, solid)
+    fs = O.fshape(G, c)
+    return O._view(G, Ps, fs, {c: -1}) | O._view(G, Ps, fs, {c: 0})
+
+
+@pytest.mark.parametrize("geo", [FIBRE_2D, FIBRE_3D], ids=["axisym", "cart3d"])
+def test_fibre_is_a_closed_inert_sphere(geo):
+    """Table tableboundary, "sphere" row: no slip, zero gradient of alpha, T, omega and
+    p_rgh on the fibre.  Over a few steps of the full coupled step (evaporation, flow
+    under gravity, the centripetal force): the solid cells hold no liquid, their T and
+    omega stay at the values put there (a 600 K fibre inside a 300 K droplet, vapour
+    fraction 0.5: any flux across the sphere would change them), every face of the
+    sphere carries zero velocity, the pressure increment vanishes in the fibre, the
+    fibre's cells are never interface cells, and the liquid volume changes only by the
+    evaporated and clipped volumes (1e-13)."""
+    cfg = W.make(**geo)
+    G = Grid(cfg)
+    solid = O.solid_mask(cfg, G)
+    assert 8 <= int(solid.sum()) < 0.05 * G.ncell()
+    st = O.init_state(cfg)
+    assert st["alpha"][solid].max() == 0.0
+    st["T"] = np.where(solid, 600.0, st["T"])
+    st["omega"] = np.where(solid, 0.5, st["omega"])
+    for _ in range(4 if G.axisym else 2):
+        st1 = O.step(cfg, st, keep=True)
+        aux = st1["aux"]
+        assert st1["alpha"][solid].max() == 0.0
+        assert np.abs(st1["T"][solid] - 600.0).max() <= 1e-12 * 600.0
+        assert np.abs(st1["omega"][solid] - 0.5).max() <= 1e-12
+        for c in G.act:
+            assert np.abs(st1["u"][c][_sphere_faces(G, solid, c)]).max() == 0.0
+            assert np.abs(aux["ustar"][c][_sphere_faces(G, solid, c)]).max() == 0.0
+        assert np.abs(aux["dp"][solid]).max() == 0.0
+        assert np.abs(aux["mraw"][solid]).max() == 0.0
+        lhs = np.sum(st1["alpha"] * G.V) - np.sum(st["alpha"] * G.V)
+        rhs = -cfg["dt"] * np.sum(aux["mdot"] * G.V) / cfg["rho_l"] - (st1["clip_mass"] - st["clip_mass"])
+        assert lhs == pytest.approx(rhs, abs=1e-13 * np.sum(st["alpha"] * G.V))
+        st = st1
+    assert max(np.abs(st["u"][c]).max() for c in G.act) > 1e-4   # the flow around it is not trivial
+
+
+def test_fibre_energy_alone_conserves_the_enthalpy():
+    """Energy equation alone, no flow (every boundary then zero gradient): with the
+    fibre's cells at 600 K inside a 300 K droplet, sum rho c_p V T over the whole grid
+    is conserved by the backward-Euler step (1e-12), and the heat stays out of the
+    fibre, while without the fibre the same state cools the hot cells at once."""
+    cfg = W.make(**dict(FIBRE_2D, physics_mask=W.PHYS_ENERGY, g=(0.0, 0.0, 0.0)))
+    G = Grid(cfg)
+    solid = O.solid_mask(cfg, G)
+    st = O.init_state(cfg)
+    st["T"] = np.where(solid, 600.0, st["T"])
+    pr = O.props(cfg, st["alpha"], st["rhoG"], st["omega"], st["T"], solid)
+    H0 = float(np.sum(pr["rho"] * pr["cp"] * G.V * st["T"]))
+    st1 = O.step(cfg, st)
+    H1 = float(np.sum(pr["rho"] * pr["cp"] * G.V * st1["T"]))
+    assert H1 == pytest.approx(H0, rel=1e-12)
+    assert np.abs(st1["T"][solid] - 600.0).max() <= 1e-12 * 600.0
+    open_cfg = dict(cfg, fiber=0)
+    st2 = O.step(open_cfg, dict(st, T=st["T"].copy()))
+    assert st2["T"][solid].max() < 590.0
