@@ -804,19 +804,25 @@ __global__ void k_alpha_clip_only(Geo g, Phys p, const double* as, double* alpha
 __device__ __forceinline__ double gam(int mode, const double* kc, const double* rho, const double* D, long long q) {
   return mode == 0 ? kc[q] : rho[q] * D[q];
 }
-// (two zero values, the faces between two cells of the fibre, give 0: the sum is tested on
-// the integer pipe)
+// (FIB, with the fibre: two zero values, the faces between two of its cells, give 0; the sum
+// is tested on the integer pipe)
+template <bool FIB = false>
 __device__ __forceinline__ double harm(double x, double y) {
   const double t = x + y;
-  return (__double_as_longlong(t) << 1) == 0 ? 0.0 : 2.0 * x * y * rcp64(t);
+  if (FIB && (__double_as_longlong(t) << 1) == 0) return 0.0;
+  return 2.0 * x * y * rcp64(t);
 }
 // half the harmonic mean, x y / (x + y) (the 2 folded into a host constant)
+template <bool FIB = false>
 __device__ __forceinline__ double harm_half(double x, double y) {
   const double t = x + y;
-  return (__double_as_longlong(t) << 1) == 0 ? 0.0 : x * y * rcp64(t);
+  if (FIB && (__double_as_longlong(t) << 1) == 0) return 0.0;
+  return x * y * rcp64(t);
 }
 
-template <int NA>
+// FIB: with the fibre (zero k and rho D in its cells close the sphere; far upwind values inside
+// it replaced by the near ones)
+template <int NA, bool FIB>
 __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
                                   const double* kc, const double* D, const double* mdot, const double* u0,
                                   const double* u1, const double* u2, const double* alpha_new, const double* pinv,
@@ -864,7 +870,7 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
         double far = pos ? cellg(g, phi, LL[0], LL[1], LL[2], R_TO, amb, u0, u1, u2)
                          : cellg(g, phi, RR[0], RR[1], RR[2], R_TO, amb, u0, u1, u2);
         // a far upwind cell inside the fibre: the near one's value (zero gradient)
-        if (g.fib && (pos ? solid_nb(g, LL[0], LL[1], LL[2]) : solid_nb(g, RR[0], RR[1], RR[2]))) far = pos ? vL : vR;
+        if (FIB && (pos ? solid_nb(g, LL[0], LL[1], LL[2]) : solid_nb(g, RR[0], RR[1], RR[2]))) far = pos ? vL : vR;
         val = lim_up(far, pos ? vL : vR, pos ? vR : vL);
       }
       net = fma(side ? F : -F, val - phiP, net);
@@ -875,8 +881,8 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
       int Lc[3] = {i, j, k};
       Lc[a] -= 1;
       long long li = cidx(g, Lc[0], Lc[1], Lc[2]);
-      cl = NA == 3 ? harm_half(gam(mode, kc, rho, D, li), gP) * g.aih2[a]
-                   : harm(gam(mode, kc, rho, D, li), gP) * faceA(g, a, i) * g.ih[a];
+      cl = NA == 3 ? harm_half<FIB>(gam(mode, kc, rho, D, li), gP) * g.aih2[a]
+                   : harm<FIB>(gam(mode, kc, rho, D, li), gP) * faceA(g, a, i) * g.ih[a];
       if (mode == 1) {
         bool lp = ige64(alpha_new[li], 0.5);
         if (!pin && lp) { r += cl * pinv[li]; dP += cl; }
@@ -890,8 +896,8 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
       Hc[a] += 1;
       long long hi = cidx(g, Hc[0], Hc[1], Hc[2]);
       if (ige64(alpha_new[hi], 0.5)) {
-        double ch = NA == 3 ? harm_half(gP, gam(mode, kc, rho, D, hi)) * g.aih2[a]
-                            : harm(gP, gam(mode, kc, rho, D, hi)) * faceA(g, a, Hc[0]) * g.ih[a];
+        double ch = NA == 3 ? harm_half<FIB>(gP, gam(mode, kc, rho, D, hi)) * g.aih2[a]
+                            : harm<FIB>(gP, gam(mode, kc, rho, D, hi)) * faceA(g, a, Hc[0]) * g.ih[a];
         r += ch * pinv[hi];
         dP += ch;
       }
@@ -1515,8 +1521,10 @@ void L_geo_advect(cudaStream_t st, int grid, Geo g, Phys p, const double* astar,
 
 void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32*) {
   ++g_launches;
-  if (nact(g) == 3) k_scalar_assemble<3><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, kc, D, mdot, u0, u1, u2, alpha_new, pinv, amb, Dg, c0, c1, c2, rhs);
-  else k_scalar_assemble<2><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, kc, D, mdot, u0, u1, u2, alpha_new, pinv, amb, Dg, c0, c1, c2, rhs);
+#define DG_SCA(NN, FF) k_scalar_assemble<NN, FF><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, kc, D, mdot, u0, u1, u2, alpha_new, pinv, amb, Dg, c0, c1, c2, rhs)
+  if (nact(g) == 3) { if (g.fib) DG_SCA(3, true); else DG_SCA(3, false); }
+  else { if (g.fib) DG_SCA(2, true); else DG_SCA(2, false); }
+#undef DG_SCA
 }
 
 void L_mom_assemble(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0, const double* u1, const double* u2, const double* rho, const double* mu, const double* pr, const double* alpha, const double* xi, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32*) {
