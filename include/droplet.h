@@ -143,8 +143,8 @@ typedef struct droplet_config {
                            the momentum systems), no flux of alpha, T, omega or pressure, and
                            central differences reaching into them use the fluid cell's own
                            value; the solid cells hold alpha = 0, T = T_drop, omega = 0 and
-                           are never interface or adjacent gas cells.  Requires precision = 0,
-                           adv_scheme = 0 and drho_l_dT = 0; not available with
+                           are never interface or adjacent gas cells.  Either precision;
+                           requires adv_scheme = 0 and drho_l_dT = 0; not available with
                            droplet_adjoint. */
 } droplet_config;
 

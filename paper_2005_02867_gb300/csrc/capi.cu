@@ -104,9 +104,9 @@ static int check_cfg(const droplet_config& c) {
   if (c.wait_limit < 0 || (c.solver_select != 0 && c.solver_select != 1)) return DROPLET_ERR_ARG;
   if (!(c.co_max >= 0.0) || !std::isfinite(c.co_max)) return DROPLET_ERR_ARG;
   if (c.adv_scheme != 0 && c.adv_scheme != 1) return DROPLET_ERR_ARG;
-  // the fibre: FP64 throughout, the compressive advection, a constant liquid density
+  // the fibre: the compressive advection, a constant liquid density
   if (c.fiber != 0 && c.fiber != 1) return DROPLET_ERR_ARG;
-  if (c.fiber == 1 && (c.precision != 0 || c.adv_scheme != 0 || c.drho_l_dT != 0.0 || !(c.fiber_radius > 0.0)))
+  if (c.fiber == 1 && (c.adv_scheme != 0 || c.drho_l_dT != 0.0 || !(c.fiber_radius > 0.0)))
     return DROPLET_ERR_ARG;
   // a liquid density linear in T stays positive up to the ambient and boiling temperatures
   if (!std::isfinite(c.drho_l_dT) || !(c.rho_l + c.drho_l_dT * (c.T_amb - c.T_drop) > 0.0) ||

@@ -118,7 +118,9 @@ __device__ __forceinline__ float cellg_f(const Geo& g, const FT* f, int i, int j
   return vout < 0.0 ? 2.f * amb - vb : vb;
 }
 
-template <int C, int NA>
+// FIB: with the fibre (faces of its sphere pinned at u* = 0; a neighbour face's coupling to
+// one of them goes into the neighbour's diagonal), as in the FP64 kernel
+template <int C, int NA, bool FIB>
 __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const double* u0, const double* u1, const double* u2,
                                   const double* rho, const double* pr, const double* alpha, const double* xi,
                                   const float* muf, const float* uf0, const float* uf1, const float* uf2,
@@ -155,6 +157,13 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
   }
   const double u_f = uc[fidx(g, c, f[0], f[1], f[2])];
   const double d0 = rho_f * V_f * idt_of(p);
+  if (FIB && sphere_face(g, c, f[0], f[1], f[2])) {   // a face of the sphere: a decoupled row, u* = 0
+    Dg[id] = d0;
+    rhs[id] = 0.0;
+#pragma unroll
+    for (int a = 0; a < NA; ++a) Cc[a][id] = 0.0;
+    return;
+  }
   // the increments, FP32
   const float rho_ff = f32_rn(rho_f), V_ff = f32_rn(V_f), r_ff = f32_rn(r_f);
   const float A_ff = V_ff * q.ih[c];
@@ -214,6 +223,13 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
         d_visc += kR;
         t_bnd += kR * ucf[fidx(g, c, fb[0], fb[1], fb[2])];
       }
+      if (FIB) {   // neighbour faces along c on the sphere
+        if (b[c] > 0 && sphere_face(g, c, f[0] - (c == 0), f[1] - (c == 1), f[2] - (c == 2))) {
+          Cc[c][id] = 0.0;
+          d_visc += kL;
+        }
+        if (b[c] < m[c] - 1 && sphere_face(g, c, f[0] + (c == 0), f[1] + (c == 1), f[2] + (c == 2))) d_visc += kR;
+      }
     } else {
       float App, Apm;
       if (g.axisym && a == 0) {
@@ -236,6 +252,13 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
       Cc[a][id] = (b[a] > 0) ? f64_of(km) : 0.0;
       if (b[a] == 0 && (g.bc[a][0] == BC_WALL || g.bc[a][0] == BC_FORCED)) d_visc += 2.f * km;
       if (b[a] == m[a] - 1 && (g.bc[a][1] == BC_WALL || g.bc[a][1] == BC_FORCED)) d_visc += 2.f * kp;
+      if (FIB) {   // neighbour faces along a on the sphere
+        if (b[a] > 0 && sphere_face(g, c, f[0] - (a == 0), f[1] - (a == 1), f[2] - (a == 2))) {
+          Cc[a][id] = 0.0;
+          d_visc += km;
+        }
+        if (b[a] < m[a] - 1 && sphere_face(g, c, f[0] + (a == 0), f[1] + (a == 1), f[2] + (a == 2))) d_visc += kp;
+      }
     }
   }
   if (g.axisym && c == 0 && r_ff > 0.f) d_visc = d_visc + 2.f * mu_f * V_ff / (r_ff * r_ff);
@@ -253,7 +276,9 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
   rhs[id] = d0 * u_f + f64_of(((t_adv + t_vT) + t_force) + t_bnd);
 }
 
-template <int NA>
+// FIB: with the fibre (its cells carry gamma = 0; the harmonic mean of two zeros is 0, and a
+// far upwind value inside it is replaced by the near one)
+template <int NA, bool FIB>
 // phif, gf, uf*: binary32 copies of phi, of gamma (k, or rho D) and of the face velocities
 __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
                                      const double* mdot, const double* u0, const double* u1, const double* u2,
@@ -301,8 +326,13 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
         LL[a] -= 1;
         RR[a] += 1;
         float vL = phif[cidx(g, Lc[0], Lc[1], Lc[2])], vR = phif[cidx(g, f[0], f[1], f[2])];
-        if (F >= 0.f) val = lim_up_f(cellg_f(g, phif, LL[0], LL[1], LL[2], R_TO, ambf, u0, u1, u2), vL, vR);
-        else val = lim_up_f(cellg_f(g, phif, RR[0], RR[1], RR[2], R_TO, ambf, u0, u1, u2), vR, vL);
+        if (F >= 0.f) {
+          const float far = FIB && solid_nb(g, LL[0], LL[1], LL[2]) ? vL : cellg_f(g, phif, LL[0], LL[1], LL[2], R_TO, ambf, u0, u1, u2);
+          val = lim_up_f(far, vL, vR);
+        } else {
+          const float far = FIB && solid_nb(g, RR[0], RR[1], RR[2]) ? vR : cellg_f(g, phif, RR[0], RR[1], RR[2], R_TO, ambf, u0, u1, u2);
+          val = lim_up_f(far, vR, vL);
+        }
       }
       // advected value relative to the cell's own: the flux difference then carries
       // only the increment (net - phi Fsum of the FP64 form, without its cancellation)
@@ -319,7 +349,7 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
       const float gL = gf[li];
       const float Aa = a == 0 ? (g.axisym ? (i * q.h[0]) * q.h[1] : q.h[0] * q.h[1] * q.h[2] * q.ih[0])
                               : (g.axisym ? ((i + 0.5f) * q.h[0]) * q.h[0] : q.h[0] * q.h[1] * q.h[2] * q.ih[a]);
-      cl = 2.f * gL * gP / (gL + gP) * Aa * q.ih[a];
+      cl = (FIB && gL + gP == 0.f) ? 0.f : 2.f * gL * gP / (gL + gP) * Aa * q.ih[a];
       if (mode == 1) {
         bool lp = ige64(alpha_new[li], 0.5);
         if (!pin && lp) { r += f64_of(cl) * pinv[li]; dinc += cl; }
@@ -336,7 +366,7 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
         const float gH = gf[hi];
         const float Ah = a == 0 ? (g.axisym ? (Hc[0] * q.h[0]) * q.h[1] : q.h[0] * q.h[1] * q.h[2] * q.ih[0])
                                 : (g.axisym ? ((i + 0.5f) * q.h[0]) * q.h[0] : q.h[0] * q.h[1] * q.h[2] * q.ih[a]);
-        const float ch = 2.f * gP * gH / (gP + gH) * Ah * q.ih[a];
+        const float ch = (FIB && gP + gH == 0.f) ? 0.f : 2.f * gP * gH / (gP + gH) * Ah * q.ih[a];
         r += f64_of(ch) * pinv[hi];
         dinc += ch;
       }
@@ -394,8 +424,19 @@ __device__ __forceinline__ float alpha_gf(const Geo& g, const float* f, int i, i
 }
 
 // alpha gradient of a cell (central differences, the ghost rule of alpha), FP32
+// (a neighbour inside the fibre takes the cell's own value: zero gradient across the sphere)
+__device__ __forceinline__ float alpha_gf_m(const Geo& g, const float* f, int i, int j, int k, int ni, int nj, int nk) {
+  return solid_nb(g, ni, nj, nk) ? f[cidx(g, i, j, k)] : alpha_gf(g, f, ni, nj, nk);
+}
 __device__ __forceinline__ void grad_alpha_f(const Geo& g, const GeoF& q, const float* al, int i, int j, int k,
                                              float gr[3]) {
+  if (g.fib) {
+    gr[0] = (alpha_gf_m(g, al, i, j, k, i + 1, j, k) - alpha_gf_m(g, al, i, j, k, i - 1, j, k)) * (0.5f * q.ih[0]);
+    gr[1] = (alpha_gf_m(g, al, i, j, k, i, j + 1, k) - alpha_gf_m(g, al, i, j, k, i, j - 1, k)) * (0.5f * q.ih[1]);
+    gr[2] = g.act3 ? (alpha_gf_m(g, al, i, j, k, i, j, k + 1) - alpha_gf_m(g, al, i, j, k, i, j, k - 1)) * (0.5f * q.ih[2])
+                   : 0.f;
+    return;
+  }
   gr[0] = (alpha_gf(g, al, i + 1, j, k) - alpha_gf(g, al, i - 1, j, k)) * (0.5f * q.ih[0]);
   gr[1] = (alpha_gf(g, al, i, j + 1, k) - alpha_gf(g, al, i, j - 1, k)) * (0.5f * q.ih[1]);
   gr[2] = g.act3 ? (alpha_gf(g, al, i, j, k + 1) - alpha_gf(g, al, i, j, k - 1)) * (0.5f * q.ih[2]) : 0.f;
@@ -501,12 +542,11 @@ void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, co
   const float* gf = mode == 0 ? s32->k : s32->gD;
   const float* uf2 = s32->u[2] ? s32->u[2] : s32->u[0];
   ++g_launches;
-  if (nact(g) == 3)
-    k_scalar_assemble_mx<3><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, mdot, u0, u1, u2, alpha_new, pinv, amb,
-                                                  phif, gf, s32->u[0], s32->u[1], uf2, Dg, c0, c1, c2, rhs);
-  else
-    k_scalar_assemble_mx<2><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, mdot, u0, u1, u2, alpha_new, pinv, amb,
-                                                  phif, gf, s32->u[0], s32->u[1], uf2, Dg, c0, c1, c2, rhs);
+#define DG_SCA(NN, FF) k_scalar_assemble_mx<NN, FF><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, mdot, u0, u1, u2, \
+      alpha_new, pinv, amb, phif, gf, s32->u[0], s32->u[1], uf2, Dg, c0, c1, c2, rhs)
+  if (nact(g) == 3) { if (g.fib) DG_SCA(3, true); else DG_SCA(3, false); }
+  else { if (g.fib) DG_SCA(2, true); else DG_SCA(2, false); }
+#undef DG_SCA
 }
 
 void L_mom_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int c, const double* u0,
@@ -516,14 +556,22 @@ void L_mom_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int c, const do
   (void)mu;   // through its binary32 copy
   const float *m32 = s32->mu, *f0 = s32->u[0], *f1 = s32->u[1], *f2 = s32->u[2] ? s32->u[2] : s32->u[0];
   ++g_launches;
+#define DG_MOM(CC, NN, FF) k_mom_assemble_mx<CC, NN, FF><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, pr, alpha, xi, m32, \
+      f0, f1, f2, Dg, c0, c1, c2, rhs)
   if (nact(g) == 3) {
-    if (c == 0) k_mom_assemble_mx<0, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, pr, alpha, xi, m32, f0, f1, f2, Dg, c0, c1, c2, rhs);
-    else if (c == 1) k_mom_assemble_mx<1, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, pr, alpha, xi, m32, f0, f1, f2, Dg, c0, c1, c2, rhs);
-    else k_mom_assemble_mx<2, 3><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, pr, alpha, xi, m32, f0, f1, f2, Dg, c0, c1, c2, rhs);
+    if (g.fib) {
+      if (c == 0) DG_MOM(0, 3, true); else if (c == 1) DG_MOM(1, 3, true); else DG_MOM(2, 3, true);
+    } else {
+      if (c == 0) DG_MOM(0, 3, false); else if (c == 1) DG_MOM(1, 3, false); else DG_MOM(2, 3, false);
+    }
   } else {
-    if (c == 0) k_mom_assemble_mx<0, 2><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, pr, alpha, xi, m32, f0, f1, f2, Dg, c0, c1, c2, rhs);
-    else k_mom_assemble_mx<1, 2><<<grid, TPB, 0, st>>>(g, p, u0, u1, u2, rho, pr, alpha, xi, m32, f0, f1, f2, Dg, c0, c1, c2, rhs);
+    if (g.fib) {
+      if (c == 0) DG_MOM(0, 2, true); else DG_MOM(1, 2, true);
+    } else {
+      if (c == 0) DG_MOM(0, 2, false); else DG_MOM(1, 2, false);
+    }
   }
+#undef DG_MOM
 }
 
 // the conversions themselves, for checking them against IEEE 754 rounding

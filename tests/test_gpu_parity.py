@@ -241,6 +241,35 @@ def test_mixed_precision_matches_fp64(D):
     b.close()
 
 
+@pytest.mark.parametrize("name", ["axisym-gravity-fibre", "cart3d-pr-forced-16-fibre"])
+def test_fibre_in_mixed_precision(D, name):
+    """The fibre in mixed precision (binary32 assembly increments, FP32 solves): over ten
+    steps (2D; three in 3D) it follows the FP64 path of the same case (droplet volume 1e-5,
+    alpha and T 1e-5, solver tolerances 1e-10), and its sphere stays closed: no liquid in
+    the solid cells, their temperature kept (1e-9), zero velocity on every sphere face."""
+    cfg64 = dict(CASES[name][0], cg_rtol=1e-10, helm_rtol=1e-10)
+    cfg32 = dict(cfg64, precision=1)
+    G = Grid(cfg64)
+    solid = O.solid_mask(cfg64, G).ravel(order="F")
+    a, b = D.Droplet(cfg64), D.Droplet(cfg32)
+    T0 = b.get("T")[solid].copy()
+    for _ in range(10 if G.axisym else 3):
+        assert a.step(1) == 0 and b.step(1) == 0
+    da, db = a.diag(), b.diag()
+    assert abs(da["V_l"] - db["V_l"]) <= 1e-5 * da["V_l"]
+    assert rel(b.get("alpha"), a.get("alpha")) < 1e-5
+    assert rel(b.get("T"), a.get("T")) < 1e-5
+    assert b.get("alpha")[solid].max() == 0.0
+    assert np.abs(b.get("T")[solid] - T0).max() <= 1e-9 * T0.max()
+    Ps = O._pad(G, O.solid_mask(cfg64, G))
+    for c in G.act:
+        fs = O.fshape(G, c)
+        sph = (O._view(G, Ps, fs, {c: -1}) | O._view(G, Ps, fs, {c: 0})).ravel(order="F")
+        assert np.abs(b.get("u%d" % c)[sph]).max() == 0.0
+    a.close()
+    b.close()
+
+
 def test_not_converged_is_reported_and_state_advances(D):
     cfg = W.cfg1_axisym_64x128(**SMALL, cg_maxit=1, cg_rtol=1e-16)
     sim = D.Droplet(cfg)

@@ -61,7 +61,7 @@ def test_struct_layout_matches_header(tmp_path):
                                  dict(xc=(1e-3, 4e-3, 0.0)), dict(cp_v=1200.0), dict(eq_model=3),
                                  dict(cg_maxit=0), dict(wait_limit=-1), dict(solver_select=2), dict(co_max=-0.1),
                                  dict(co_max=float("nan")), dict(adv_scheme=2), dict(drho_l_dT=float("nan")),
-                                 dict(drho_l_dT=-2.0), dict(fiber=2), dict(fiber=1, precision=1),
+                                 dict(drho_l_dT=-2.0), dict(fiber=2),
                                  dict(fiber=1, adv_scheme=1), dict(fiber=1, drho_l_dT=-0.9),
                                  dict(fiber=1, fiber_radius=0.0)])
 def test_invalid_config_rejected_without_device(lib, bad):
