@@ -660,8 +660,10 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
       for (int id = id0; id < N; id += gs) {
         int i, j, kk;
         bdecomp(a.A.m, id, i, j, kk);
-        double ax, d;
-        box_row<double, double, true>(a.A.m, a.A.D, a.A.c, a.x, id, i, j, kk, ax, d);
+        // the total diagonal, then the defect in the diagonal form d x_P - sum c x_N (one
+        // multiply and one FMA per neighbour: fewer binary64 instructions than the difference form)
+        const double d = box_diag_total(a.A.m, a.A.D, a.A.c, id, i, j, kk);
+        const double ax = box_offdiag(a.A.m, a.A.c, a.x, id, i, j, kk, d * a.x[id]);
         const double bP = a.b[id], r0 = bP - ax;
         a.r[1][id] = (T)r0;                   // rounded once; r[1] is free until the first iteration
         const T dT = (T)d;
@@ -718,8 +720,8 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
       for (int id = id0; id < N; id += gs) {
         int i, j, kk;
         bdecomp(a.A.m, id, i, j, kk);
-        double ax, d;
-        box_row<double, double, true>(a.A.m, a.A.D, a.A.c, a.x, id, i, j, kk, ax, d);
+        const double d = box_diag_total(a.A.m, a.A.D, a.A.c, id, i, j, kk);
+        const double ax = box_offdiag(a.A.m, a.A.c, a.x, id, i, j, kk, d * a.x[id]);
         a.r[1][id] = (T)((a.b[id] - ax) * nu64);
       }
     }
@@ -1062,7 +1064,7 @@ __device__ __forceinline__ T mg_idg_cell(const LevV<T>& L, long long id) {
     if (q[a] > 0) dt += (double)L.c[a][id];
     if (q[a] < L.m[a] - 1) dt += (double)L.c[a][id + st[a]];
   }
-  return (T)(1.0 / dt);
+  return (T)rcp64(dt);   // (the reciprocal by rcp64: within an ulp, no division)
 }
 
 template <typename T>
@@ -1079,7 +1081,7 @@ __global__ void k_mg_idg(LevV<T> L, T* idg) {
     if (q[a] > 0) dt += (double)L.c[a][id];
     if (q[a] < L.m[a] - 1) dt += (double)L.c[a][id + st[a]];
   }
-  idg[id] = (T)(1.0 / dt);
+  idg[id] = (T)rcp64(dt);
 }
 
 // residual b - A x of one cell in the hierarchy precision

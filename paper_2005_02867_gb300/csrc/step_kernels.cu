@@ -1301,12 +1301,12 @@ __device__ __forceinline__ void correct_face(const Geo& g, const Phys& p, const 
   decomp(id, m0, m1, f[0], f[1], f[2]);
   double A = faceA(g, c, f[0]);
   double corr = 0.0;
-  if (A > 0.0) {
+  if (__double_as_longlong(A) > 0) {   // A > 0 (areas are never negative), on the integer pipe
     int L[3] = {f[0], f[1], f[2]};
     L[c] -= 1;
     if (f[c] > 0 && f[c] < g.n[c]) {
       long long li = cidx(g, L[0], L[1], L[2]), ri = cidx(g, f[0], f[1], f[2]);
-      corr = dt_of(p) * g.ih[c] * (2.0 * rcp64(rho[li] + rho[ri])) * (dp[ri] - dp[li]);
+      corr = (dt_of(p) * g.ih[c]) * (2.0 * rcp64(rho[li] + rho[ri])) * (dp[ri] - dp[li]);
       if (g.fib && (g.solid[li] || g.solid[ri])) corr = 0.0;   // the sphere's faces keep u* = 0
     } else {
       int side = f[c] == 0 ? 0 : 1;
