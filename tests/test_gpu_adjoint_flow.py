@@ -138,6 +138,38 @@ def test_one_step_rate_vjp_against_central_differences(D, make):
     assert not bad, errs
 
 
+@pytest.mark.parametrize("make", [small, small3d], ids=["axisym", "cart3d"])
+def test_one_step_dot_product(D, make):
+    """The dot-product test of one whole step s' = F(s) with flow: for a random cotangent
+    lam on every output field (alpha, T, omega, p_rgh, the face velocities; scaled by each
+    field's size) and a direction ds in the state, <(dF/ds)^T lam, ds> from the adjoint
+    equals <lam, (F(s + e ds) - F(s - e ds)) / 2e>.  The directions keep the flat parts of
+    the state flat (alpha (1 - alpha) in the interface band, T - T_amb, omega in the gas,
+    the velocities themselves), where the minmod- and upwind-limited stencils have one-sided
+    derivatives."""
+    sim, s0 = _state_after(D, make)
+    parts = unpack(sim, s0)
+    cfg = make()
+    rng = np.random.default_rng(11)
+    lam = {nm: rng.standard_normal(x.size) / max(np.abs(x).max(), 1e-30) for nm, x in parts.items()}
+    lam_v = np.concatenate([lam[nm] for nm in fields(sim)])
+    lam_prev, _ = D.droplet_adjoint_vjp(sim.h, lam_v, 0.0)
+    a = parts["alpha"]
+    d = {"alpha": a * (1.0 - a), "T": parts["T"] - cfg["T_amb"], "omega": parts["omega"] * (a < 0.5),
+         "p": parts["p"]}
+    for nm in fields(sim):
+        if nm.startswith("u"):
+            d[nm] = parts[nm]
+    dv = np.concatenate([d[k] for k in fields(sim)])
+    eps = 1e-6
+    sp, _ = step_from(sim, s0 + eps * dv)
+    sm, _ = step_from(sim, s0 - eps * dv)
+    fd = lam_v @ ((sp - sm) / (2 * eps))
+    ad = lam_prev @ dv
+    sim.close()
+    assert abs(ad - fd) <= 1e-5 * abs(fd), (ad, fd)
+
+
 def J_gpu(D, cfg, steps, dT0=None):
     sim = D.Droplet(cfg)
     if dT0 is not None:
