@@ -247,7 +247,8 @@ struct MGLevel {
   void* x;
   void* b;
   void* idg;        // 1 / (D + sum of adjacent couplings), used by the smoother
-  void* xp;         // post-smoothed iterate (tiled persistent V-cycle)
+  void* xp;         // post-smoothed iterate (tiled persistent V-cycle); b by colour (launched)
+  int split = 0;    // launched V-cycle, above its tail: idg and the copy of b by colour
 };
 
 class Solver {

@@ -1011,14 +1011,22 @@ struct LevV {
   const T* b;
   const T* idg;
   T* xp;        // post-smoothed iterate of the tiled persistent V-cycle
+  // launched V-cycle, levels above its one-block tail (split = 1): 1/diag stored by colour
+  // (index col n + t, n = ceil(m0 / 2) m1 m2 cells per colour, t the half sweep's thread of
+  // the cell), and bs, b copied into the same layout by each V-cycle's first half sweep, so
+  // that a half sweep reads only its own colour's b and 1/diag, whole sectors at a time
+  int split;
+  T* bs;
 };
 
 // one cell of a red-black Gauss-Seidel half sweep: x_P = (b_P + sum c x_nb) / diag_total
 // (first = 1: neighbours taken as 0).  Arithmetic in the hierarchy precision T.
-template <typename T>
-__device__ __forceinline__ void gs_cell(const LevV<T>& L, long long id, int i, int j, int k, int first) {
+// (SPLIT: b and 1/diag read from the colour-ordered copies at ts)
+template <typename T, bool SPLIT = false>
+__device__ __forceinline__ void gs_cell(const LevV<T>& L, long long id, int i, int j, int k, int first,
+                                        long long ts = 0) {
   long long st1 = L.m[0], st2 = (long long)L.m[0] * L.m[1];
-  T s = L.b[id];
+  T s = SPLIT ? L.bs[ts] : L.b[id];
   if (!first) {
     if (i > 0) s += L.c[0][id] * L.x[id - 1];
     if (i < L.m[0] - 1) s += L.c[0][id + 1] * L.x[id + 1];
@@ -1029,7 +1037,7 @@ __device__ __forceinline__ void gs_cell(const LevV<T>& L, long long id, int i, i
       if (k < L.m[2] - 1) s += L.c[2][id + st2] * L.x[id + st2];
     }
   }
-  L.x[id] = s * L.idg[id];
+  L.x[id] = s * L.idg[SPLIT ? ts : id];
 }
 
 // One half sweep of colour col over a whole level, one thread per updated cell: thread t
@@ -1038,13 +1046,13 @@ __device__ __forceinline__ void gs_cell(const LevV<T>& L, long long id, int i, i
 // same binary64 warp instructions for half the work: GB300's FP64 pipe, which retires a
 // warp instruction in a fixed number of cycles however many lanes are active, was 91 %
 // busy on such a sweep while DRAM ran at 61 %.)
-template <typename T>
+template <typename T, bool SPLIT = false>
 __device__ __forceinline__ void grid_half_sweep(const LevV<T>& L, int col, int first, int gid, int gs);
 
-template <typename T>
+template <typename T, bool SPLIT>
 __global__ void k_mg_smooth(LevV<T> L, int col, int first, const int* done) {
   if (*done) return;
-  grid_half_sweep<T>(L, col, first, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  grid_half_sweep<T, SPLIT>(L, col, first, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // threads of a launched half sweep (one per cell of one colour, rows padded to ceil(m0 / 2))
@@ -1081,7 +1089,12 @@ __global__ void k_mg_idg(LevV<T> L, T* idg) {
     if (q[a] > 0) dt += (double)L.c[a][id];
     if (q[a] < L.m[a] - 1) dt += (double)L.c[a][id + st[a]];
   }
-  idg[id] = (T)rcp64(dt);
+  long long o = id;
+  if (L.split) {   // the colour-ordered layout of the launched half sweeps
+    const int h = (L.m[0] + 1) >> 1;
+    o = (long long)((i + j + k) & 1) * h * L.m[1] * L.m[2] + (long long)(j + L.m[1] * k) * h + (i >> 1);
+  }
+  idg[o] = (T)rcp64(dt);
 }
 
 // residual b - A x of one cell in the hierarchy precision
@@ -1491,7 +1504,7 @@ __global__ void __launch_bounds__(TAIL_THREADS) k_mg_tail(TailLevels<T> TL, int 
 constexpr int PMG_TAIL_MAX_CELLS = 2048;
 
 // half sweep of colour `col` over a whole level, grid-strided
-template <typename T>
+template <typename T, bool SPLIT>
 __device__ __forceinline__ void grid_half_sweep(const LevV<T>& L, int col, int first, int gid, int gs) {
   const int m0 = L.m[0], m1 = L.m[1], h = (m0 + 1) >> 1;
   const int n = h * m1 * L.m[2];
@@ -1499,7 +1512,14 @@ __device__ __forceinline__ void grid_half_sweep(const LevV<T>& L, int col, int f
     const int row = t / h, q = t - row * h;
     const int k = row / m1, j = row - k * m1;
     const int i = 2 * q + ((j + k + col) & 1);
-    if (i < m0) gs_cell<T>(L, (long long)i + (long long)m0 * row, i, j, k, first);
+    if (SPLIT && first) {
+      // the V-cycle's first (red) half sweep of the level: both cells of this thread's pair
+      // copy their b into the colour-ordered layout (whole sectors read) for the later sweeps
+      const int ib = 2 * q + ((j + k + 1) & 1);
+      if (i < m0) L.bs[t] = L.b[(long long)i + (long long)m0 * row];
+      if (ib < m0) L.bs[(long long)n + t] = L.b[(long long)ib + (long long)m0 * row];
+    }
+    if (i < m0) gs_cell<T, SPLIT>(L, (long long)i + (long long)m0 * row, i, j, k, first, (long long)col * n + t);
   }
 }
 
@@ -2431,6 +2451,8 @@ static LevV<T> lv(const MGLevel& L) {
   v.b = (const T*)L.b;
   v.idg = (const T*)L.idg;
   v.xp = (T*)L.xp;
+  v.split = L.split;
+  v.bs = (T*)L.xp;   // (xp serves only the persistent V-cycle; the launched one keeps b there)
   return v;
 }
 
@@ -2526,6 +2548,11 @@ int Solver::prepare_mg(const int mm[3], int fp32) {
 int Solver::build_mg(const BoxSys& s, int fp32) {
   int rc = prepare_mg(s.m, fp32);
   if (rc) return rc;
+  {   // the launched V-cycle's levels above its tail use the colour-ordered b and 1/diag
+    int lt = nlev - 1;
+    while (lt > 0 && lev[lt - 1].N <= TAIL_MAX_CELLS) --lt;
+    for (int l = 0; l < nlev; ++l) lev[l].split = l < lt ? 1 : 0;
+  }
   // level 0 operator: the pressure box in the hierarchy precision
   MGLevel& L0 = lev[0];
   int g0 = lin_grid(L0.N);
@@ -2562,7 +2589,8 @@ static void smooth(Prof* prof, LevV<T> L, int col, int first, const int* done, c
   int d = L.c[2] ? 3 : 2;
   ProfScope ps(prof, KC_MG_SMOOTH, st, (2.5 + d) * L.N * (double)sizeof(T),
                sizeof(T) == 8 ? (2.0 * d + 1.0) * 0.5 * L.N : 0.0);
-  ++g_launches, k_mg_smooth<T><<<lin_grid(half_sweep_threads(L.m)), TPB, 0, st>>>(L, col, first, done);
+  if (L.split) ++g_launches, k_mg_smooth<T, true><<<lin_grid(half_sweep_threads(L.m)), TPB, 0, st>>>(L, col, first, done);
+  else ++g_launches, k_mg_smooth<T, false><<<lin_grid(half_sweep_threads(L.m)), TPB, 0, st>>>(L, col, first, done);
 }
 
 // (ad0: the total diagonal of level 0 when it is the FP64 box whose CG formed it, else null)
