@@ -1642,7 +1642,8 @@ extern "C" int droplet_adjoint_check(droplet_ctx* cc, double* rel, int nrel) {
 }
 
 // ---------------------------------------------------------------- checkpoint / resume
-static const char kMagic[8] = {'D', 'R', 'O', 'P', 'C', 'K', 'P', '4'};
+// (format 5: the configuration carries the fibre field)
+static const char kMagic[8] = {'D', 'R', 'O', 'P', 'C', 'K', 'P', '5'};
 
 // the checkpointed fields: the state, the history of the extrapolated guesses, and the
 // liquid's expansion term of the last step (a temperature-dependent liquid density only)
