@@ -47,6 +47,9 @@ WORKLOADS = {
     "cfg3_cart3d_128_fp64": lambda: W.cfg3_cart3d(nc=128, precision=0),
     "cfg3_cart3d_256_fp64_geometric": lambda: W.cfg3_cart3d(precision=0, adv_scheme=1),
     "cfg2_axisym_256x512_geometric": lambda: W.cfg2_axisym_256x512(adv_scheme=1),
+    # the droplet placed around the spherical fibre (fiber_radius 0.05 mm)
+    "cfg2_axisym_256x512_fibre": lambda: W.cfg2_axisym_256x512(fiber=1),
+    "cfg3_cart3d_256_fp64_fibre": lambda: W.cfg3_cart3d(precision=0, fiber=1),
     # the 3D launched path (more than 2^22 cells) at ~2.5 GB on the device: the size of
     # the full ncu captures of its kernels
     "cfg3_cart3d_176": lambda: W.cfg3_cart3d(nc=176),

@@ -1100,7 +1100,7 @@ def projection(cfg, G, st, ustar, pr, mdot, alpha, rhoG_old, rhoG_new, dt, rhoL_
         S = S - expand
     if solid is not None:
         S = np.where(solid, 0.0, S)      # the fibre holds no fluid: no continuity source
-    diag, coup, beta = pressure_system(G, rho, solid)
+    diag, coup, beta = pressure_system(G, rho, solid, cfg["rho_l"])
     div_star = divergence_sum(G, [ustar[a] * G.A[a] if a in G.act else None for a in range(3)])
     rhs = (S * G.V - div_star) / dt
     dp = solve_box(n, diag, coup, rhs)
@@ -1116,15 +1116,15 @@ def projection(cfg, G, st, ustar, pr, mdot, alpha, rhoG_old, rhoG_new, dt, rhoL_
     return unew, st["p"] + dp, dp, S, (diag, coup, rhs), expand
 
 
-def pressure_system(G, rho, solid=None):
+def pressure_system(G, rho, solid=None, rho_l=None):
     """Variable-density pressure operator of Eq. (pequation):
     (L x)_P = sum_f beta_f (x_P - x_N) + sum_open beta_b x_P,
     beta_f = A_f/(rho_f h) with rho_f the arithmetic face mean, beta_b =
     A_b/(rho_P h/2) on open (p_rgh = p_ext) faces, zero on walls, the axis and
     a forced inlet.  With a fibre (reading R32) beta vanishes on the faces of the
     sphere (zero normal gradient) and each solid cell's row is decoupled with the
-    diagonal 2 d V_P / (h_min^2 rho_P) (d the active axes), so that its increment is
-    0.  Returns (diag, couplings, beta per face)."""
+    diagonal 2 d V_P / (h_min^2 rho_L) (d the active axes; the value does not change the
+    solution), so that its increment is 0.  Returns (diag, couplings, beta per face)."""
     n = G.n
     Prho = pad_scalar(G, rho, "zg")
     diag = np.zeros(n)
@@ -1151,7 +1151,7 @@ def pressure_system(G, rho, solid=None):
         sl[a] = slice(1, n[a])
         coup[a] = b[tuple(sl)]
     if solid is not None:
-        diag = np.where(solid, 2.0 * len(G.act) * G.V / (G.hmin * G.hmin * rho), diag)
+        diag = np.where(solid, 2.0 * len(G.act) * G.V / (G.hmin * G.hmin * rho_l), diag)
     return diag, coup, beta
 
 

@@ -340,6 +340,24 @@ static int init_one(const droplet_config& cfg, cudaStream_t main_st, bool own_st
     }
     g.fib = 1;
     g.solid = c->solid;
+    // the box of the solid cells (an empty mask gives an empty box: lo > hi)
+    for (int a = 0; a < 3; ++a) { g.fib_lo[a] = g.n[a]; g.fib_hi[a] = -1; }
+    for (int k = 0; k < g.n[2]; ++k)
+      for (int j = 0; j < g.n[1]; ++j)
+        for (int i = 0; i < g.n[0]; ++i)
+          if (m[(size_t)i + (size_t)g.n[0] * ((size_t)j + (size_t)g.n[1] * k)]) {
+            const int q[3] = {i, j, k};
+            for (int a = 0; a < 3; ++a) {
+              g.fib_lo[a] = std::min(g.fib_lo[a], q[a]);
+              g.fib_hi[a] = std::max(g.fib_hi[a], q[a]);
+            }
+          }
+    // no cell centre inside the sphere (a fibre finer than the grid): nothing is solid, and the
+    // kernels run without the fibre's tests (whose box test needs a non-empty box)
+    if (g.fib_hi[0] < 0) {
+      g.fib = 0;
+      g.solid = nullptr;
+    }
   }
   c->solver.f32_helm = c->cfg.precision == 1;
   // latency-bound sizes: persistent solvers (in a batch each droplet is later given an

@@ -48,6 +48,7 @@ struct Geo {
   // per cell, 1 for the cells whose centre lies closer than D_f to the droplet centre
   int fib;
   const unsigned char* solid;
+  int fib_lo[3], fib_hi[3];   // the box of the solid cells (inclusive cell indices)
   long long N;       // number of cells (< 2^31)
 };
 
@@ -123,9 +124,11 @@ __device__ __forceinline__ double areaN(const Geo& g, int a, double rl) {
 // conditions on the sphere's faces).  All tests are false without a fibre (g.fib = 0).
 __device__ __forceinline__ bool solid_cell(const Geo& g, long long id) { return g.fib && g.solid[id]; }
 // cell (i, j, k), possibly outside the domain (then not solid)
+// (the box of the solid cells first: integer compares, and the mask read only inside it)
 __device__ __forceinline__ bool solid_nb(const Geo& g, int i, int j, int k) {
-  return g.fib && (unsigned)i < (unsigned)g.n[0] && (unsigned)j < (unsigned)g.n[1] && (unsigned)k < (unsigned)g.n[2] &&
-         g.solid[cidx(g, i, j, k)];
+  return g.fib && (unsigned)(i - g.fib_lo[0]) <= (unsigned)(g.fib_hi[0] - g.fib_lo[0]) &&
+         (unsigned)(j - g.fib_lo[1]) <= (unsigned)(g.fib_hi[1] - g.fib_lo[1]) &&
+         (unsigned)(k - g.fib_lo[2]) <= (unsigned)(g.fib_hi[2] - g.fib_lo[2]) && g.solid[cidx(g, i, j, k)];
 }
 // a face of the sphere: face (i, j, k) of direction a (cells i - e_a and i) with a fibre cell
 // on either side

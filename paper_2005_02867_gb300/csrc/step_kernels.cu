@@ -1283,9 +1283,10 @@ __global__ void k_poisson_assemble(Geo g, Phys p, const double* mdot, const doub
     if (ci[a] == 0 && g.bc[a][0] == BC_OPEN) dg += faceA(g, a, i) * (2.0 * g.ih[a]) / rP;
     if (ci[a] == g.n[a] - 1 && g.bc[a][1] == BC_OPEN) dg += faceA(g, a, hi[0]) * (2.0 * g.ih[a]) / rP;
   }
-  // a cell of the fibre: a decoupled row (its increment is 0), of the size of a Laplacian
-  // diagonal, 2 d V / (h_min^2 rho)
-  if (sol) dg = 2.0 * na * cellV(g, i) / (g.hmin * g.hmin * rP);
+  // a cell of the fibre: a decoupled row (its increment is 0), of the size of the surrounding
+  // liquid's Laplacian diagonal, 2 d V / (h_min^2 rho_L) (a larger one anchors the coarse cells
+  // of the multigrid that contain it and slows the pressure solve)
+  if (sol) dg = 2.0 * na * cellV(g, i) / (g.hmin * g.hmin * p.rho_l);
   Dg[id] = dg;
   rhs[id] = (s * cellV(g, i) - div) * idt_of(p);
 }

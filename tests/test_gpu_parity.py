@@ -270,6 +270,20 @@ def test_fibre_in_mixed_precision(D, name):
     b.close()
 
 
+def test_fibre_finer_than_the_grid_is_no_fibre(D):
+    """A fibre radius below every cell-centre distance leaves no solid cell: the run is the
+    run without a fibre (the same radius D_f of the potential xi), bit for bit (the fibre's
+    tests are then off altogether)."""
+    cfg = dict(CASES["axisym-gravity"][0], fiber_radius=1e-7)
+    a, b = D.Droplet(cfg), D.Droplet(dict(cfg, fiber=1))
+    for _ in range(2):
+        assert a.step(1) == 0 and b.step(1) == 0
+    for f in ("alpha", "T", "omega", "p", "u0", "u1"):
+        assert np.array_equal(a.get(f), b.get(f)), f
+    a.close()
+    b.close()
+
+
 def test_not_converged_is_reported_and_state_advances(D):
     cfg = W.cfg1_axisym_64x128(**SMALL, cg_maxit=1, cg_rtol=1e-16)
     sim = D.Droplet(cfg)
