@@ -262,8 +262,10 @@ int droplet_box_solve(const int m[3], const double* D, const double* c0, const d
  * current device (cudaGetSymbolAddress, which allocates nothing; no address is
  * kept between calls).  Under lazy module loading (the CUDA default) the array
  * is placed in device memory at the first call on a device: make that first
- * call before any stream capture, and early, if the caller's own pool is to
- * take the rest of the memory.  Every call reuses the same array and
+ * call early if the caller's own pool is to take the rest of the memory.  No
+ * call can be captured into a CUDA graph (each reads the solver's state back
+ * and synchronises the stream): on a stream under capture the call returns
+ * DROPLET_ERR_ARG before anything is enqueued.  Every call reuses the same array and
  * initialises what it needs, so calls must not overlap on the GPU: two solves
  * running at once on different streams would race on the array. */
 #define DROPLET_NOALLOC_MAX_UNKNOWNS 262144
@@ -273,7 +275,10 @@ int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0,
 
 /* Kernel classes timed by droplet_profile (algorithmic bytes per launch in brackets,
  * w = word size of the launch, d = 2 or 3 active axes, N = unknowns of the launch):
- *   0 MG_SMOOTH   red-black Gauss-Seidel half sweep    [(2.5 + d) N w; FP64: (2d + 1) N/2 instructions]
+ *   0 MG_SMOOTH   red-black Gauss-Seidel half sweep    [(2.5 + d) N w; FP64: (2d + 1) N/2 instructions;
+ *                                                        an FP32 level's first half sweep after
+ *                                                        the coarse correction also prolongs it:
+ *                                                        + N_coarse w, and no MG_PROLONG launch]
  *   1 SPMV        CG operator application + dot        [(3 + d) N w; FP64: (2d + 2) N instructions,
  *                                                        the diagonal form a_P x_P - sum c x_N]
  *   2 UPDATE      CG x/r update + dot                  [Jacobi 8 N w (x, r in and out, p, Ap,
@@ -281,7 +286,7 @@ int droplet_box_solve_noalloc(const int m[3], const double* D, const double* c0,
  *                                                        with an FP32 hierarchy); FP64: 5 N
  *                                                        (Jacobi), 3 N]
  *   3 MG_RESTRICT residual + restriction               [(3 + d) N w + N/2^d w; FP64: (4d + 3) N]
- *   4 MG_PROLONG  injection prolongation               [(2 + 1/2^d) N w; FP64: N]
+ *   4 MG_PROLONG  injection prolongation (FP64 levels) [(2 + 1/2^d) N w; FP64: N]
  *   5 MOM_ASSEMBLE momentum system assembly            [(12 + 2d) N 8]
  *   6 SCALAR_ASSEMBLE energy / species assembly        [(12 + 2d) N 8]
  *   7 PCG_PERSIST the whole Jacobi-preconditioned CG of one to three Helmholtz

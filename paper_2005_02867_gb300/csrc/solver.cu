@@ -837,17 +837,35 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
           T *r = a.r[0], *s = a.s[0];
           const T* w = a.w[0];
           T g = 0, q = 0;
-          for (int id = id0; id < N; id += gs) {
-            const T rP = r[id];
-            const T pP = rP + bt * a.p[id];       // p = r^ + beta p
-            const T sP = w[id] + bt * s[id];      // s = w + beta s
-            a.p[id] = pP;
-            a.dx[id] += al * pP;                  // x^ += alpha p
-            const T rN = rP - al * sP;            // r^ -= alpha s
-            r[id] = rN;
-            s[id] = sP;
-            g += rN * rN;
-            q += a.dg[id] * rN * rN;
+          // two cells a trip, id and id + gs (the cells and the order of the plain grid-stride
+          // loop, so the same sums): the twelve loads of the pair are issued before either
+          // cell's stores, twice the loads in flight of one cell per trip
+          for (int id = id0; id < N; id += 2 * gs) {
+            const int i1 = id + gs < N ? id + gs : id;
+            const T rP0 = r[id], p0 = a.p[id], w0 = w[id], s0 = s[id], x0 = a.dx[id], d0 = a.dg[id];
+            const T rP1 = r[i1], p1 = a.p[i1], w1 = w[i1], s1 = s[i1], x1 = a.dx[i1], d1 = a.dg[i1];
+            {
+              const T pP = rP0 + bt * p0;           // p = r^ + beta p
+              const T sP = w0 + bt * s0;            // s = w + beta s
+              const T rN = rP0 - al * sP;           // r^ -= alpha s
+              a.p[id] = pP;
+              a.dx[id] = x0 + al * pP;              // x^ += alpha p
+              r[id] = rN;
+              s[id] = sP;
+              g += rN * rN;
+              q += d0 * rN * rN;
+            }
+            if (i1 != id) {
+              const T pP = rP1 + bt * p1;
+              const T sP = w1 + bt * s1;
+              const T rN = rP1 - al * sP;
+              a.p[i1] = pP;
+              a.dx[i1] = x1 + al * pP;
+              r[i1] = rN;
+              s[i1] = sP;
+              g += rN * rN;
+              q += d1 * rN * rN;
+            }
           }
           v[3 * k] = g;
           v[3 * k + 2] = q;
@@ -864,10 +882,11 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
           const T* r = a.r[0];
           T* w = a.w[0];
           T dl = 0;
-          for (int id = id0; id < N; id += gs) {
+          // w = A^ r^ of one cell (loads only), with its r^
+          auto row = [&](int id, T& rN) -> T {
             int i, j, kk;
             bdecomp(a.A.m, id, i, j, kk);
-            const T rN = r[id];
+            rN = r[id];
             const int iw = i > 0 ? id - 1 : id, ie = i < m0 - 1 ? id + 1 : id;
             const int is = j > 0 ? id - st1 : id, in = j < m1 - 1 ? id + st1 : id;
             const T cw = a.ch[0][id], ce = i < m0 - 1 ? a.ch[0][ie] : (T)0;
@@ -878,8 +897,20 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
               const T cb = a.ch[2][id], ct = kk < m2 - 1 ? a.ch[2][it] : (T)0;
               y -= cb * r[ib] + ct * r[it];
             }
-            w[id] = y;
-            dl += y * rN;
+            return y;
+          };
+          // two cells a trip, as in the first pass: both rows are formed before either store
+          for (int id = id0; id < N; id += 2 * gs) {
+            const int i1 = id + gs < N ? id + gs : id;
+            T rN0, rN1;
+            const T y0 = row(id, rN0);
+            const T y1 = row(i1, rN1);
+            w[id] = y0;
+            dl += y0 * rN0;
+            if (i1 != id) {
+              w[i1] = y1;
+              dl += y1 * rN1;
+            }
           }
           v[3 * k + 1] = dl;
         }
@@ -1575,6 +1606,41 @@ __device__ __forceinline__ void grid_prolong_black(const LevV<T>& F, const LevV<
       if (k < m2 - 1) s += F.c[2][id + st2] * prolonged<T>(F, C, C.x, id + st2, i, j, k + 1);
     }
     F.x[id] = s * F.idg[id];
+  }
+}
+
+// The launched V-cycle's prolongation x_F += x_C fused with the first post-smoothing half
+// sweep (colour 1) of F, for binary32 levels.  A colour-1 cell's update reads only its
+// colour-0 neighbours, each taken as x_F + x_C of its parent (the prolonged value, rounded
+// as the separate prolongation rounds it), and overwrites the cell's own x; the colour-0
+// cells' prolonged values are read by nothing else, as the colour-0 half sweep that
+// follows overwrites them from their colour-1 neighbours.  So the level ends with the
+// values of the prolongation followed by the half sweep, with one pass over the level
+// fewer.  (A binary64 level keeps the separate pass: six additions per updated cell in
+// place of the prolongation's one per cell weigh on GB300's binary64 pipe.)
+template <typename T, bool SPLIT>
+__global__ void k_mg_prolong_smooth(LevV<T> F, LevV<T> C, const int* done) {
+  if (*done) return;
+  const int m0 = F.m[0], m1 = F.m[1], m2 = F.m[2], h = (m0 + 1) >> 1;
+  const int n = h * m1 * m2;
+  const long long st1 = m0, st2 = (long long)m0 * m1;
+  const int gs = gridDim.x * blockDim.x;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gs) {
+    const int row = t / h, q = t - row * h;
+    const int k = row / m1, j = row - k * m1;
+    const int i = 2 * q + ((j + k + 1) & 1);
+    if (i >= m0) continue;
+    const long long id = (long long)i + (long long)m0 * row, ts = (long long)n + t;
+    T s = SPLIT ? F.bs[ts] : F.b[id];
+    if (i > 0) s += F.c[0][id] * prolonged<T>(F, C, C.x, id - 1, i - 1, j, k);
+    if (i < m0 - 1) s += F.c[0][id + 1] * prolonged<T>(F, C, C.x, id + 1, i + 1, j, k);
+    if (j > 0) s += F.c[1][id] * prolonged<T>(F, C, C.x, id - st1, i, j - 1, k);
+    if (j < m1 - 1) s += F.c[1][id + st1] * prolonged<T>(F, C, C.x, id + st1, i, j + 1, k);
+    if (F.c[2]) {
+      if (k > 0) s += F.c[2][id] * prolonged<T>(F, C, C.x, id - st2, i, j, k - 1);
+      if (k < m2 - 1) s += F.c[2][id + st2] * prolonged<T>(F, C, C.x, id + st2, i, j, k + 1);
+    }
+    F.x[id] = s * F.idg[SPLIT ? ts : id];
   }
 }
 
@@ -2630,14 +2696,31 @@ static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaSt
   }
   for (int l = lt - 1; l >= 0; --l) {
     LevV<T> L = lv<T>(lev[l]), C = lv<T>(lev[l + 1]);
-    int g = lin_grid(L.N);
-    {
-      ProfScope ps(prof, KC_MG_PROLONG, st, (2.0 * L.N + C.N) * (double)sizeof(T), sizeof(T) == 8 ? 1.0 * L.N : 0.0);
-      ++g_launches, k_mg_prolong<T><<<g, TPB, 0, st>>>(L, C, done);
-    }
-    for (int s = 0; s < nu; ++s) {
-      smooth<T>(prof, L, 1, 0, done, st);
+    if constexpr (sizeof(T) == 4) {
+      {
+        // the prolongation inside the first colour-1 half sweep: the half sweep's bytes and
+        // the coarse level's x
+        const int d = L.c[2] ? 3 : 2;
+        ProfScope ps(prof, KC_MG_SMOOTH, st, ((2.5 + d) * L.N + C.N) * (double)sizeof(T));
+        const int g = lin_grid(half_sweep_threads(L.m));
+        if (L.split) ++g_launches, k_mg_prolong_smooth<T, true><<<g, TPB, 0, st>>>(L, C, done);
+        else ++g_launches, k_mg_prolong_smooth<T, false><<<g, TPB, 0, st>>>(L, C, done);
+      }
       smooth<T>(prof, L, 0, 0, done, st);
+      for (int s = 1; s < nu; ++s) {
+        smooth<T>(prof, L, 1, 0, done, st);
+        smooth<T>(prof, L, 0, 0, done, st);
+      }
+    } else {
+      int g = lin_grid(L.N);
+      {
+        ProfScope ps(prof, KC_MG_PROLONG, st, (2.0 * L.N + C.N) * (double)sizeof(T), 1.0 * L.N);
+        ++g_launches, k_mg_prolong<T><<<g, TPB, 0, st>>>(L, C, done);
+      }
+      for (int s = 0; s < nu; ++s) {
+        smooth<T>(prof, L, 1, 0, done, st);
+        smooth<T>(prof, L, 0, 0, done, st);
+      }
     }
   }
 }
@@ -2838,6 +2921,13 @@ extern "C" int droplet_box_solve_noalloc(const int m[3], const double* D, const 
   if (N > NA_MAX) {
     fprintf(stderr, "droplet_box_solve_noalloc: %lld unknowns exceed the static workspace (%lld)\n", N, NA_MAX);
     return DROPLET_ERR_SIZE;
+  }
+  // the call reads the solver's state back and synchronises its stream, which no stream
+  // capture allows: refused before anything is enqueued
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)cuda_stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    fprintf(stderr, "droplet_box_solve_noalloc: the stream is being captured\n");
+    return DROPLET_ERR_ARG;
   }
   double* ws = nullptr;
   int rc = noalloc_workspace(&ws);

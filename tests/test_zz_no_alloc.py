@@ -87,3 +87,21 @@ def test_noalloc_rejects_oversize_box(D):
     for m in ((big, 1, 1), (2, big, 1), (2**31 - 1, 2**31 - 1, 2**31 - 1)):
         rc, _, _ = D.droplet_box_solve_noalloc(m, p, p, p, p, p, p, 1e-10, 10, st)
         assert rc == -5, m
+
+
+def test_noalloc_refuses_a_capturing_stream(D):
+    """The call synchronises its stream, so inside a stream capture it must
+    refuse (DROPLET_ERR_ARG) before it enqueues anything; the (empty) capture
+    then ends cleanly and a plain call afterwards still solves."""
+    import torch
+    m = (16, 12, 1)
+    t = _system(m, 14)
+    x = torch.zeros_like(t[-1])
+    s = torch.cuda.Stream()
+    args = (m, t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr(), 0, t[4].data_ptr(), x.data_ptr(), 1e-12, 4000)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rc = D.droplet_box_solve_noalloc(*args, s.cuda_stream)[0]
+    assert rc == -1
+    torch.cuda.synchronize()
+    assert D.droplet_box_solve_noalloc(*args, torch.cuda.current_stream().cuda_stream)[0] == 0
