@@ -1054,8 +1054,8 @@ struct LevV {
 // (first = 1: neighbours taken as 0).  Arithmetic in the hierarchy precision T.
 // (SPLIT: b and 1/diag read from the colour-ordered copies at ts)
 template <typename T, bool SPLIT = false>
-__device__ __forceinline__ void gs_cell(const LevV<T>& L, long long id, int i, int j, int k, int first,
-                                        long long ts = 0) {
+__device__ __forceinline__ T gs_value(const LevV<T>& L, long long id, int i, int j, int k, int first,
+                                      long long ts = 0) {
   long long st1 = L.m[0], st2 = (long long)L.m[0] * L.m[1];
   T s = SPLIT ? L.bs[ts] : L.b[id];
   if (!first) {
@@ -1068,7 +1068,13 @@ __device__ __forceinline__ void gs_cell(const LevV<T>& L, long long id, int i, i
       if (k < L.m[2] - 1) s += L.c[2][id + st2] * L.x[id + st2];
     }
   }
-  L.x[id] = s * L.idg[SPLIT ? ts : id];
+  return s * L.idg[SPLIT ? ts : id];
+}
+
+template <typename T, bool SPLIT = false>
+__device__ __forceinline__ void gs_cell(const LevV<T>& L, long long id, int i, int j, int k, int first,
+                                        long long ts = 0) {
+  L.x[id] = gs_value<T, SPLIT>(L, id, i, j, k, first, ts);
 }
 
 // One half sweep of colour col over a whole level, one thread per updated cell: thread t
@@ -1080,11 +1086,18 @@ __device__ __forceinline__ void gs_cell(const LevV<T>& L, long long id, int i, i
 template <typename T, bool SPLIT = false>
 __device__ __forceinline__ void grid_half_sweep(const LevV<T>& L, int col, int first, int gid, int gs);
 
-template <typename T, bool SPLIT>
+template <typename T, bool SPLIT, int CC>
+__device__ __forceinline__ void grid_half_sweep_pair(const LevV<T>& L, int col, int first, int gid, int gs);
+
+// (launched with one thread per CC updated cells)
+template <typename T, bool SPLIT, int CC>
 __global__ void k_mg_smooth(LevV<T> L, int col, int first, const int* done) {
   if (*done) return;
-  grid_half_sweep<T, SPLIT>(L, col, first, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+  grid_half_sweep_pair<T, SPLIT, CC>(L, col, first, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
+
+// cells per thread of a launched half sweep: two from this many updated cells on
+constexpr long long SWEEP_PAIR_MIN = 1LL << 20;
 
 // threads of a launched half sweep (one per cell of one colour, rows padded to ceil(m0 / 2))
 inline long long half_sweep_threads(const int m[3]) { return (long long)((m[0] + 1) >> 1) * m[1] * m[2]; }
@@ -1554,6 +1567,45 @@ __device__ __forceinline__ void grid_half_sweep(const LevV<T>& L, int col, int f
   }
 }
 
+// The same half sweep with CC cells per thread and trip (t, t + gs, ...): all the cells'
+// loads are issued before any store (cells of one colour are never neighbours, so the values
+// are those of separate updates).  On a large level a launched half sweep at one cell per
+// thread keeps too few loads in flight per SM to cover the latency of its gathers; two cells
+// a thread run faster there (four were slower: fewer threads, more registers), while small
+// levels, with a wave of threads or less, lose more to the longer thread than they gain.
+template <typename T, bool SPLIT, int CC>
+__device__ __forceinline__ void grid_half_sweep_pair(const LevV<T>& L, int col, int first, int gid, int gs) {
+  constexpr int SWEEP_CELLS = CC;
+  const int m0 = L.m[0], m1 = L.m[1], h = (m0 + 1) >> 1;
+  const int n = h * m1 * L.m[2];
+  for (int t0 = gid; t0 < n; t0 += SWEEP_CELLS * gs) {
+    T v[SWEEP_CELLS];
+    long long at[SWEEP_CELLS];
+#pragma unroll
+    for (int u = 0; u < SWEEP_CELLS; ++u) at[u] = -1;
+#pragma unroll
+    for (int u = 0; u < SWEEP_CELLS; ++u) {
+      const int t = t0 + u * gs;
+      if (t >= n) break;
+      const int row = t / h, q = t - row * h;
+      const int k = row / m1, j = row - k * m1;
+      const int i = 2 * q + ((j + k + col) & 1);
+      if (SPLIT && first) {   // (as in grid_half_sweep)
+        const int ib = 2 * q + ((j + k + 1) & 1);
+        if (i < m0) L.bs[t] = L.b[(long long)i + (long long)m0 * row];
+        if (ib < m0) L.bs[(long long)n + t] = L.b[(long long)ib + (long long)m0 * row];
+      }
+      if (i < m0) {
+        at[u] = (long long)i + (long long)m0 * row;
+        v[u] = gs_value<T, SPLIT>(L, at[u], i, j, k, first, (long long)col * n + t);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SWEEP_CELLS; ++u)
+      if (at[u] >= 0) L.x[at[u]] = v[u];
+  }
+}
+
 // C.b = restricted residual of F; with `red`, also the first (red) half sweep on C
 template <typename T>
 __device__ __forceinline__ void grid_restrict(const LevV<T>& F, const LevV<T>& C, bool red, int gid, int gs) {
@@ -1618,29 +1670,44 @@ __device__ __forceinline__ void grid_prolong_black(const LevV<T>& F, const LevV<
 // values of the prolongation followed by the half sweep, with one pass over the level
 // fewer.  (A binary64 level keeps the separate pass: six additions per updated cell in
 // place of the prolongation's one per cell weigh on GB300's binary64 pipe.)
-template <typename T, bool SPLIT>
+// (CC cells a thread and trip, as the launched half sweeps)
+template <typename T, bool SPLIT, int CC>
 __global__ void k_mg_prolong_smooth(LevV<T> F, LevV<T> C, const int* done) {
+  constexpr int SWEEP_CELLS = CC;
   if (*done) return;
   const int m0 = F.m[0], m1 = F.m[1], m2 = F.m[2], h = (m0 + 1) >> 1;
   const int n = h * m1 * m2;
   const long long st1 = m0, st2 = (long long)m0 * m1;
   const int gs = gridDim.x * blockDim.x;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gs) {
-    const int row = t / h, q = t - row * h;
-    const int k = row / m1, j = row - k * m1;
-    const int i = 2 * q + ((j + k + 1) & 1);
-    if (i >= m0) continue;
-    const long long id = (long long)i + (long long)m0 * row, ts = (long long)n + t;
-    T s = SPLIT ? F.bs[ts] : F.b[id];
-    if (i > 0) s += F.c[0][id] * prolonged<T>(F, C, C.x, id - 1, i - 1, j, k);
-    if (i < m0 - 1) s += F.c[0][id + 1] * prolonged<T>(F, C, C.x, id + 1, i + 1, j, k);
-    if (j > 0) s += F.c[1][id] * prolonged<T>(F, C, C.x, id - st1, i, j - 1, k);
-    if (j < m1 - 1) s += F.c[1][id + st1] * prolonged<T>(F, C, C.x, id + st1, i, j + 1, k);
-    if (F.c[2]) {
-      if (k > 0) s += F.c[2][id] * prolonged<T>(F, C, C.x, id - st2, i, j, k - 1);
-      if (k < m2 - 1) s += F.c[2][id + st2] * prolonged<T>(F, C, C.x, id + st2, i, j, k + 1);
+  for (int t0 = blockIdx.x * blockDim.x + threadIdx.x; t0 < n; t0 += SWEEP_CELLS * gs) {
+    T v[SWEEP_CELLS];
+    long long at[SWEEP_CELLS];
+#pragma unroll
+    for (int u = 0; u < SWEEP_CELLS; ++u) at[u] = -1;
+#pragma unroll
+    for (int u = 0; u < SWEEP_CELLS; ++u) {
+      const int t = t0 + u * gs;
+      if (t >= n) break;
+      const int row = t / h, q = t - row * h;
+      const int k = row / m1, j = row - k * m1;
+      const int i = 2 * q + ((j + k + 1) & 1);
+      if (i >= m0) continue;
+      const long long id = (long long)i + (long long)m0 * row, ts = (long long)n + t;
+      T s = SPLIT ? F.bs[ts] : F.b[id];
+      if (i > 0) s += F.c[0][id] * prolonged<T>(F, C, C.x, id - 1, i - 1, j, k);
+      if (i < m0 - 1) s += F.c[0][id + 1] * prolonged<T>(F, C, C.x, id + 1, i + 1, j, k);
+      if (j > 0) s += F.c[1][id] * prolonged<T>(F, C, C.x, id - st1, i, j - 1, k);
+      if (j < m1 - 1) s += F.c[1][id + st1] * prolonged<T>(F, C, C.x, id + st1, i, j + 1, k);
+      if (F.c[2]) {
+        if (k > 0) s += F.c[2][id] * prolonged<T>(F, C, C.x, id - st2, i, j, k - 1);
+        if (k < m2 - 1) s += F.c[2][id + st2] * prolonged<T>(F, C, C.x, id + st2, i, j, k + 1);
+      }
+      at[u] = id;
+      v[u] = s * F.idg[SPLIT ? ts : id];
     }
-    F.x[id] = s * F.idg[SPLIT ? ts : id];
+#pragma unroll
+    for (int u = 0; u < SWEEP_CELLS; ++u)
+      if (at[u] >= 0) F.x[at[u]] = v[u];
   }
 }
 
@@ -2655,8 +2722,15 @@ static void smooth(Prof* prof, LevV<T> L, int col, int first, const int* done, c
   int d = L.c[2] ? 3 : 2;
   ProfScope ps(prof, KC_MG_SMOOTH, st, (2.5 + d) * L.N * (double)sizeof(T),
                sizeof(T) == 8 ? (2.0 * d + 1.0) * 0.5 * L.N : 0.0);
-  if (L.split) ++g_launches, k_mg_smooth<T, true><<<lin_grid(half_sweep_threads(L.m)), TPB, 0, st>>>(L, col, first, done);
-  else ++g_launches, k_mg_smooth<T, false><<<lin_grid(half_sweep_threads(L.m)), TPB, 0, st>>>(L, col, first, done);
+  const long long n = half_sweep_threads(L.m);
+  ++g_launches;
+  if (n >= SWEEP_PAIR_MIN) {
+    if (L.split) k_mg_smooth<T, true, 2><<<lin_grid((n + 1) / 2), TPB, 0, st>>>(L, col, first, done);
+    else k_mg_smooth<T, false, 2><<<lin_grid((n + 1) / 2), TPB, 0, st>>>(L, col, first, done);
+  } else {
+    if (L.split) k_mg_smooth<T, true, 1><<<lin_grid(n), TPB, 0, st>>>(L, col, first, done);
+    else k_mg_smooth<T, false, 1><<<lin_grid(n), TPB, 0, st>>>(L, col, first, done);
+  }
 }
 
 // (ad0: the total diagonal of level 0 when it is the FP64 box whose CG formed it, else null)
@@ -2702,9 +2776,15 @@ static void vcycle_t(Prof* prof, MGLevel* lev, int nlev, const int* done, cudaSt
         // the coarse level's x
         const int d = L.c[2] ? 3 : 2;
         ProfScope ps(prof, KC_MG_SMOOTH, st, ((2.5 + d) * L.N + C.N) * (double)sizeof(T));
-        const int g = lin_grid(half_sweep_threads(L.m));
-        if (L.split) ++g_launches, k_mg_prolong_smooth<T, true><<<g, TPB, 0, st>>>(L, C, done);
-        else ++g_launches, k_mg_prolong_smooth<T, false><<<g, TPB, 0, st>>>(L, C, done);
+        const long long n = half_sweep_threads(L.m);
+        ++g_launches;
+        if (n >= SWEEP_PAIR_MIN) {
+          if (L.split) k_mg_prolong_smooth<T, true, 2><<<lin_grid((n + 1) / 2), TPB, 0, st>>>(L, C, done);
+          else k_mg_prolong_smooth<T, false, 2><<<lin_grid((n + 1) / 2), TPB, 0, st>>>(L, C, done);
+        } else {
+          if (L.split) k_mg_prolong_smooth<T, true, 1><<<lin_grid(n), TPB, 0, st>>>(L, C, done);
+          else k_mg_prolong_smooth<T, false, 1><<<lin_grid(n), TPB, 0, st>>>(L, C, done);
+        }
       }
       smooth<T>(prof, L, 0, 0, done, st);
       for (int s = 1; s < nu; ++s) {
