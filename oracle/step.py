@@ -764,7 +764,8 @@ def alpha_advection_geometric(cfg, G, alpha_star, u, dt):
     return clipped, clip_vol, nclip, a
 
 
-def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=None, pin_val=None, solid=None):
+def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=None, pin_val=None, solid=None,
+                     src_int=None):
     """S5 / S6: backward-Euler diffusion, explicit limited-linear-upwind convection.
 
     coef_t V (phi - phi^n)/dt + coef_t [sum_f F_f phi_f - phi_P sum_f F_f]
@@ -777,7 +778,8 @@ def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=Non
     pin_val and eliminated symmetrically.  With a fibre (solid mask, reading R32) the
     solid cells carry gamma = 0, so the harmonic mean closes every face of the sphere
     (two zeros give 0), the faces of the sphere carry no velocity, and a far upwind
-    value inside the fibre is replaced by the near one (zero gradient).
+    value inside the fibre is replaced by the near one (zero gradient).  src_int, when
+    given, is a source already integrated over each cell, added to the right-hand side.
     """
     n = G.n
     P = pad_scalar(G, phi_n, "TO", u=u, amb=amb)
@@ -785,6 +787,8 @@ def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=Non
     coup = {}
     diag = coef_t * G.V / dt
     rhs = coef_t * G.V * phi_n / dt + src * G.V
+    if src_int is not None:
+        rhs = rhs + src_int
     Pg = pad_scalar(G, gamma, "zg")
     for a in G.act:
         fs = fshape(G, a)
@@ -861,6 +865,38 @@ def scalar_transport(cfg, G, phi_n, coef_t, gamma, src, u, dt, amb, pin_mask=Non
         diag = np.where(pin_mask, dpin, diag)
         rhs = np.where(pin_mask, dpin * pin_val, rhs)
     return solve_box(n, diag, coup, rhs)
+
+
+def enthalpy_diffusion(cfg, G, omega, T, gamma):
+    """The species-diffusion enthalpy term of Eq. (Teqn), -sum_i j_d,i C_p,i . grad T, for
+    the binary gas (vapour v, inert g): with Fick's fluxes j_v = -rho D grad(omega) and
+    j_g = -j_v it is (C_p,v - C_p,g) rho D grad(omega) . grad(T).  Reading R33: integrated
+    over each cell as half the sum, over the cell's interior faces f, of
+    gamma_f (A_f / h_f) (omega_N - omega_P)(T_N - T_P), gamma_f the harmonic face mean of
+    rho D of the species equation (S6); boundary faces carry none.  Each face's product is
+    shared equally by its two cells.  Evaluated at omega^n and T^n (explicit)."""
+    dcp = cfg["cp_v"] - cfg["cp_g"]
+    Q = np.zeros(G.n)
+    if dcp == 0.0:
+        return Q
+    for a in G.act:
+        if G.n[a] < 2:
+            continue
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[a] = slice(0, G.n[a] - 1)
+        hi[a] = slice(1, G.n[a])
+        lo, hi = tuple(lo), tuple(hi)
+        gL, gR = gamma[lo], gamma[hi]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            gf = np.where(gL + gR > 0.0, 2.0 * gL * gR / (gL + gR), 0.0)
+        sl = [slice(None)] * 3
+        sl[a] = slice(1, G.n[a])
+        Af = G.A[a][tuple(sl)]                  # the interior faces' areas
+        prod = gf * Af / G.h[a] * (omega[hi] - omega[lo]) * (T[hi] - T[lo])
+        Q[lo] += 0.5 * prod
+        Q[hi] += 0.5 * prod
+    return dcp * Q
 
 
 def momentum_predictor(cfg, G, st, pr, alpha, dt, parts=None):
@@ -1230,8 +1266,11 @@ def step(cfg, st, keep=False):
     pr = props(cfg, alpha_new, rhoG_old, omega, T, solid)
     # S5
     if (mask & PHYS_ENERGY) and not const:
+        hd = None
+        if cfg["cp_v"] != cfg["cp_g"]:
+            hd = enthalpy_diffusion(cfg, G, omega, T, pr["rho"] * pr["D"])
         T_new = scalar_transport(cfg, G, T, pr["rho"] * pr["cp"], pr["k"], -mdot * cfg["Lv"], u, dt, cfg["T_amb"],
-                                 solid=solid)
+                                 solid=solid, src_int=hd)
     else:
         T_new = T.copy()
     # S6

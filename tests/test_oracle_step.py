@@ -604,3 +604,60 @@ def test_fibre_energy_alone_conserves_the_enthalpy():
     open_cfg = dict(cfg, fiber=0)
     st2 = O.step(open_cfg, dict(st, T=st["T"].copy()))
     assert st2["T"][solid].max() < 590.0
+
+
+def _face_products(G, gamma, omega, T):
+    """S = sum over the interior faces of gamma_f (A_f / h_f) (omega_N - omega_P)(T_N - T_P),
+    gamma_f the harmonic mean of the two cells' gamma."""
+    S = 0.0
+    for a in G.act:
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[a] = slice(0, G.n[a] - 1)
+        hi[a] = slice(1, G.n[a])
+        lo, hi = tuple(lo), tuple(hi)
+        gf = 2.0 * gamma[lo] * gamma[hi] / (gamma[lo] + gamma[hi])
+        sl = [slice(None)] * 3
+        sl[a] = slice(1, G.n[a])
+        S += float(np.sum(gf * G.A[a][tuple(sl)] / G.h[a] * (omega[hi] - omega[lo]) * (T[hi] - T[lo])))
+    return S
+
+
+@pytest.mark.parametrize("geom", ["axisym", "cart3d"])
+def test_species_diffusion_carries_the_enthalpy(geom):
+    """The j_d,i C_p,i . grad T term of Eq. (Teqn) closes the mixture's enthalpy balance.
+    Pure gas (no liquid, no flow, closed box), vapour and inert of different heat
+    capacities, energy then species by backward Euler at the same rho: summing each
+    cell's energy row and, multiplied by T^{n+1}, its species row gives exactly
+      sum rho V [c_p(omega^{n+1}) T^{n+1} - c_p(omega^n) T^n] = dt (C_p,v - C_p,g) (S^n - S^{n+1})
+    (S the face sum of gamma (A/h) d_omega d_T, gamma = rho D): the conduction sums to zero,
+    the term contributes dt dC S^n and the species rows -dt dC S^{n+1} (summation by parts).
+    Without the term (or with its sign or weight wrong) the left side is about -dt dC S^n
+    instead, which the case makes many times larger than S^n - S^{n+1}."""
+    if geom == "axisym":
+        cfg = W.make(n=(16, 32, 1), L=(1e-3, 2e-3, 0.0), xc=(0.0, 1e-3, 0.0), D0=2e-4, dt=2e-6,
+                     physics_mask=W.PHYS_ENERGY | W.PHYS_SPECIES, cp_v=2400.0, cp_g=1100.0)
+    else:
+        cfg = W.make(geom=W.GEOM_CART3D, n=(10, 12, 14), L=(1e-3, 1.2e-3, 1.4e-3), xc=(5e-4, 6e-4, 7e-4),
+                     D0=1e-4, dt=2e-6, physics_mask=W.PHYS_ENERGY | W.PHYS_SPECIES, cp_v=2400.0, cp_g=1100.0)
+    G = Grid(cfg)
+    st = O.init_state(cfg)
+    X = np.meshgrid(*[G.xc[a] / cfg["L"][a] if a in G.act else np.zeros(1) for a in range(3)], indexing="ij")
+    st["alpha"] = np.zeros(G.n)
+    st["omega"] = 0.05 + 0.25 * np.exp(-8.0 * ((X[0] - 0.3) ** 2 + (X[1] - 0.6) ** 2 + (X[2] - 0.4) ** 2))
+    st["T"] = 350.0 + 150.0 * np.exp(-6.0 * ((X[0] - 0.5) ** 2 + (X[1] - 0.45) ** 2 + (X[2] - 0.55) ** 2))
+    st["rhoG"] = th.rho_gas(cfg, st["T"], st["omega"])
+    st1 = O.step(cfg, st)
+    rho = th.rho_gas(cfg, st["T"], st["omega"])          # the step's rho (S0, no liquid)
+    D = th.D_gas(cfg)
+    cp = lambda w: w * cfg["cp_v"] + (1.0 - w) * cfg["cp_g"]
+    lhs = float(np.sum(rho * G.V * (cp(st1["omega"]) * st1["T"] - cp(st["omega"]) * st["T"])))
+    dC = cfg["cp_v"] - cfg["cp_g"]
+    S0 = _face_products(G, rho * D, st["omega"], st["T"])
+    S1 = _face_products(G, rho * D, st1["omega"], st1["T"])
+    rhs = cfg["dt"] * dC * (S0 - S1)
+    scale = cfg["dt"] * abs(dC) * abs(S0)
+    assert abs(S0 - S1) < 0.2 * abs(S0)                  # a missing term would show as ~ -dt dC S0
+    assert abs(lhs - rhs) <= 1e-9 * scale, (lhs, rhs, scale)
+    # the term is not negligible against the whole enthalpy change of the step
+    assert abs(st1["T"] - st["T"]).max() > 0.0
