@@ -83,7 +83,12 @@ typedef struct droplet_config {
   int    bc_mode;       /* 0 natural convection (open inlet), 1 forced-convection inlet */
   int    eq_model;      /* 0 Raoult + Clausius-Clapeyron, 1 Peng-Robinson fugacities   */
   double Tb, Lv, M_l, rho_l, cp_l, k_l, mu_l, D_l;   /* liquid fuel                    */
-  double M_g, cp_g, cp_v, k_g, mu_g, D_g;            /* inert gas; D_g at 1 bar        */
+  double M_g, cp_g, cp_v, k_g, mu_g, D_g;            /* inert gas; D_g at 1 bar; cp_v:
+                                                        the vapour's heat capacity (the
+                                                        gas mixture's c_p, and with
+                                                        cp_v != cp_g the species-diffusion
+                                                        enthalpy term of Eq. Teqn; the
+                                                        adjoint needs cp_v = cp_g)     */
   double Tc, Pc, omega_ac, Tc_g, Pc_g, omega_g, kij; /* Peng-Robinson data            */
   double xi0;           /* centripetal potential intensity [m2/s2] (Eq. magneticpotential) */
   double fiber_radius;  /* D_f [m] (Eq. magneticpotential)                             */

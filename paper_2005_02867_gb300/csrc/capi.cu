@@ -96,7 +96,6 @@ static int check_cfg(const droplet_config& c) {
   if (c.geom == 0 && c.xc[0] != 0.0) return DROPLET_ERR_ARG;
   if (c.eq_model != 0 && c.eq_model != 1) return DROPLET_ERR_ARG;
   if (c.bc_mode != 0 && c.bc_mode != 1) return DROPLET_ERR_ARG;
-  if (c.cp_v != c.cp_g) return DROPLET_ERR_ARG;   // the j_d (cp_v - cp_g) . grad T term is not carried
   if (c.cg_maxit < 1 || c.helm_maxit < 1 || !(c.cg_rtol > 0.0) || !(c.helm_rtol > 0.0)) return DROPLET_ERR_ARG;
   if (c.precision != 0 && c.precision != 1) return DROPLET_ERR_ARG;
   for (int a = 0; a < 2; ++a)
@@ -588,7 +587,7 @@ static int one_step(dctx* c, int* nc_flag) {
     ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
     (c->cfg.precision == 1 ? L_scalar_assemble_mx : L_scalar_assemble)(
         st, gc, g, p, 0, c->T, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2, c->alpha, c->yq, p.T_amb,
-        c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs, &c->s32);
+        c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs, &c->s32, c->omega);
     }
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
@@ -607,7 +606,7 @@ static int one_step(dctx* c, int* nc_flag) {
     ProfScope ps(&c->prof, KC_SCALAR_ASSEMBLE, st, (12.0 + 2 * na) * N * 8.0);
     (c->cfg.precision == 1 ? L_scalar_assemble_mx : L_scalar_assemble)(
         st, gc, g, p, 1, c->omega, c->rho, c->cp, c->kc, c->Dm, c->mdot, c->u[0], c->u[1], u2, c->alpha, c->yq, 0.0,
-        c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs, &c->s32);
+        c->bD, c->bc[0], c->bc[1], na == 3 ? c->bc[2] : c->bc[0], c->brhs, &c->s32, nullptr);
     }
     for (int a = 0; a < 3; ++a) bs.m[a] = g.n[a];
     bs.N = N;
@@ -1080,7 +1079,7 @@ extern "C" int droplet_adjoint(droplet_ctx* cc, int n_steps, int ckpt_every, dou
   if (cf.physics_mask & DROPLET_PHYS_FLOW) return adjoint_flow(cc, n_steps, ckpt_every, J, dJ_dTamb, dJ_dDg, dJ_dT0, nT0);
   if (cf.physics_mask != (DROPLET_PHYS_EVAP | DROPLET_PHYS_ENERGY | DROPLET_PHYS_SPECIES) || cf.precision != 0 ||
       cf.eq_model != 0 || cf.const_props_check != 0 || cf.bc_mode != 0 || cf.co_max != 0.0 || cf.drho_l_dT != 0.0 ||
-      cf.fiber != 0 || x->step != 0)
+      cf.fiber != 0 || cf.cp_v != cf.cp_g || x->step != 0)
     return DROPLET_ERR_ARG;
   Geo& g = x->g;
   Phys& p = x->p;
@@ -1433,7 +1432,7 @@ static bool flow_adjoint_ok(const dctx* x) {
   const droplet_config& cf = x->cfg;
   return cf.physics_mask == (DROPLET_PHYS_EVAP | DROPLET_PHYS_ENERGY | DROPLET_PHYS_SPECIES | DROPLET_PHYS_FLOW) &&
          cf.precision == 0 && cf.eq_model == 0 && cf.const_props_check == 0 && cf.co_max == 0.0 &&
-         cf.drho_l_dT == 0.0 && cf.adv_scheme == 0 && cf.fiber == 0;
+         cf.drho_l_dT == 0.0 && cf.adv_scheme == 0 && cf.fiber == 0 && cf.cp_v == cf.cp_g;
 }
 
 static int adjoint_flow(droplet_ctx* cc, int n_steps, int ckpt_every, double* J, double* dJ_dTamb, double* dJ_dDg,

@@ -821,12 +821,16 @@ __device__ __forceinline__ double harm_half(double x, double y) {
 }
 
 // FIB: with the fibre (zero k and rho D in its cells close the sphere; far upwind values inside
-// it replaced by the near ones)
-template <int NA, bool FIB>
+// it replaced by the near ones).  HD (energy rows, c_p,v != c_p,g): the species-diffusion
+// enthalpy term of Eq. Teqn, (c_p,v - c_p,g) rho D grad(omega) . grad(T) integrated over the
+// cell as half the sum over its interior faces of the species equation's coupling
+// harm(rho D) A / h times (omega_N - omega_P)(T_N - T_P), at omega^n = wq and T^n = phi
+template <int NA, bool FIB, bool HD = false>
 __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
                                   const double* kc, const double* D, const double* mdot, const double* u0,
                                   const double* u1, const double* u2, const double* alpha_new, const double* pinv,
-                                  double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+                                  double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs,
+                                  const double* wq) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
   int i, j, k;
@@ -845,8 +849,31 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
   double gP = gam(mode, kc, rho, D, id);
   bool pin = (mode == 1) && ige64(alpha_new[id], 0.5);
   int ci[3] = {i, j, k};
+  double hq = 0.0, gdP = 0.0, wP = 0.0;   // HD: the face sum, rho D and omega of the cell
+  if (HD) {
+    gdP = rho[id] * D[id];
+    wP = wq[id];
+  }
   #pragma unroll
   for (int a = 0; a < na; ++a) {
+    if (HD) {
+      if (ci[a] > 0) {
+        int Lc[3] = {i, j, k};
+        Lc[a] -= 1;
+        const long long li = cidx(g, Lc[0], Lc[1], Lc[2]);
+        const double cf = NA == 3 ? harm_half<FIB>(rho[li] * D[li], gdP) * g.aih2[a]
+                                  : harm<FIB>(rho[li] * D[li], gdP) * faceA(g, a, i) * g.ih[a];
+        hq = fma(cf * (wq[li] - wP), phi[li] - phiP, hq);
+      }
+      if (ci[a] < g.n[a] - 1) {
+        int Hc[3] = {i, j, k};
+        Hc[a] += 1;
+        const long long hi = cidx(g, Hc[0], Hc[1], Hc[2]);
+        const double cf = NA == 3 ? harm_half<FIB>(gdP, rho[hi] * D[hi]) * g.aih2[a]
+                                  : harm<FIB>(gdP, rho[hi] * D[hi]) * faceA(g, a, Hc[0]) * g.ih[a];
+        hq = fma(cf * (wq[hi] - wP), phi[hi] - phiP, hq);
+      }
+    }
     #pragma unroll
     for (int side = 0; side < 2; ++side) {
       int f[3] = {i, j, k};
@@ -924,6 +951,7 @@ __global__ void k_scalar_assemble(Geo g, Phys p, int mode, const double* phi, co
     }
   }
   r -= coef * net;
+  if (HD) r = fma(0.5 * (p.cp_v - p.cp_g), hq, r);
   if (pin) {
     // pinned row, scaled like the other rows: (coef V/dt) x = (coef V/dt) Y_eq
     double dd = coef * V * idt_of(p);
@@ -1520,11 +1548,18 @@ void L_geo_advect(cudaStream_t st, int grid, Geo g, Phys p, const double* astar,
   }
 }
 
-void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32*) {
+void L_scalar_assemble(cudaStream_t st, int grid, Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp, const double* kc, const double* D, const double* mdot, const double* u0, const double* u1, const double* u2, const double* alpha_new, const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs, const Shadow32*, const double* wq) {
   ++g_launches;
-#define DG_SCA(NN, FF) k_scalar_assemble<NN, FF><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, kc, D, mdot, u0, u1, u2, alpha_new, pinv, amb, Dg, c0, c1, c2, rhs)
-  if (nact(g) == 3) { if (g.fib) DG_SCA(3, true); else DG_SCA(3, false); }
-  else { if (g.fib) DG_SCA(2, true); else DG_SCA(2, false); }
+  // the enthalpy term of the energy rows (wq: omega^n) when the heat capacities differ
+  const bool hd = mode == 0 && wq && p.cp_v != p.cp_g;
+#define DG_SCA(NN, FF, HH) k_scalar_assemble<NN, FF, HH><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, kc, D, mdot, u0, u1, u2, alpha_new, pinv, amb, Dg, c0, c1, c2, rhs, wq)
+  if (hd) {
+    if (nact(g) == 3) { if (g.fib) DG_SCA(3, true, true); else DG_SCA(3, false, true); }
+    else { if (g.fib) DG_SCA(2, true, true); else DG_SCA(2, false, true); }
+  } else {
+    if (nact(g) == 3) { if (g.fib) DG_SCA(3, true, false); else DG_SCA(3, false, false); }
+    else { if (g.fib) DG_SCA(2, true, false); else DG_SCA(2, false, false); }
+  }
 #undef DG_SCA
 }
 

@@ -277,14 +277,17 @@ __global__ void __launch_bounds__(TPB, 4) k_mom_assemble_mx(Geo g, Phys p, const
 }
 
 // FIB: with the fibre (its cells carry gamma = 0; the harmonic mean of two zeros is 0, and a
-// far upwind value inside it is replaced by the near one)
-template <int NA, bool FIB>
+// far upwind value inside it is replaced by the near one).  HD (energy rows, c_p,v != c_p,g):
+// the species-diffusion enthalpy term of Eq. Teqn as in the FP64 kernel, formed in binary32
+// from the copies of rho D (gdf) and omega^n (wf) as one more increment
+template <int NA, bool FIB, bool HD = false>
 // phif, gf, uf*: binary32 copies of phi, of gamma (k, or rho D) and of the face velocities
 __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi, const double* rho, const double* cp,
                                      const double* mdot, const double* u0, const double* u1, const double* u2,
                                      const double* alpha_new, const double* pinv, double amb, const float* phif,
                                      const float* gf, const float* uf0, const float* uf1, const float* uf2,
-                                     double* Dg, double* c0, double* c1, double* c2, double* rhs) {
+                                     double* Dg, double* c0, double* c1, double* c2, double* rhs,
+                                     const float* gdf, const float* wf) {
   long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (id >= g.N) return;
   int i, j, k;
@@ -305,8 +308,35 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
   const float gP = gf[id];
   float net = 0.f, Fsum = 0.f, dinc = 0.f, rinc = 0.f;
   int ci[3] = {i, j, k};
+  float hq = 0.f, gdP = 0.f, wP = 0.f;   // HD: the face sum, rho D and omega of the cell
+  if (HD) {
+    gdP = gdf[id];
+    wP = wf[id];
+  }
 #pragma unroll
   for (int a = 0; a < na; ++a) {
+    if (HD) {
+      if (ci[a] > 0) {
+        int Lc[3] = {i, j, k};
+        Lc[a] -= 1;
+        const long long li = cidx(g, Lc[0], Lc[1], Lc[2]);
+        const float gL = gdf[li];
+        const float Aa = a == 0 ? (g.axisym ? (i * q.h[0]) * q.h[1] : q.h[0] * q.h[1] * q.h[2] * q.ih[0])
+                                : (g.axisym ? ((i + 0.5f) * q.h[0]) * q.h[0] : q.h[0] * q.h[1] * q.h[2] * q.ih[a]);
+        const float cf = (FIB && gL + gdP == 0.f) ? 0.f : 2.f * gL * gdP / (gL + gdP) * Aa * q.ih[a];
+        hq += cf * (wf[li] - wP) * (phif[li] - phiP);
+      }
+      if (ci[a] < g.n[a] - 1) {
+        int Hc[3] = {i, j, k};
+        Hc[a] += 1;
+        const long long hi = cidx(g, Hc[0], Hc[1], Hc[2]);
+        const float gH = gdf[hi];
+        const float Ah = a == 0 ? (g.axisym ? (Hc[0] * q.h[0]) * q.h[1] : q.h[0] * q.h[1] * q.h[2] * q.ih[0])
+                                : (g.axisym ? ((i + 0.5f) * q.h[0]) * q.h[0] : q.h[0] * q.h[1] * q.h[2] * q.ih[a]);
+        const float cf = (FIB && gdP + gH == 0.f) ? 0.f : 2.f * gdP * gH / (gdP + gH) * Ah * q.ih[a];
+        hq += cf * (wf[hi] - wP) * (phif[hi] - phiP);
+      }
+    }
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
       int f[3] = {i, j, k};
@@ -395,6 +425,7 @@ __global__ void k_scalar_assemble_mx(Geo g, Phys p, int mode, const double* phi,
       }
     }
   }
+  if (HD) rinc += 0.5f * f32_rn(p.cp_v - p.cp_g) * hq;
   // - coef (net - phi Fsum): the FP32 sum above is already relative to phi
   r += f64_of(rinc) - coef * f64_of(net);
   dP += f64_of(dinc);
@@ -533,7 +564,7 @@ void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, co
                           const double* rho, const double* cp, const double* kc, const double* D, const double* mdot,
                           const double* u0, const double* u1, const double* u2, const double* alpha_new,
                           const double* pinv, double amb, double* Dg, double* c0, double* c1, double* c2, double* rhs,
-                          const Shadow32* s32) {
+                          const Shadow32* s32, const double* wq) {
   // kc and D enter through their binary32 copies (gamma = k or rho D, formed with the
   // properties); phi's copy is that of the step's old T or omega
   (void)kc;
@@ -541,11 +572,21 @@ void L_scalar_assemble_mx(cudaStream_t st, int grid, Geo g, Phys p, int mode, co
   const float* phif = mode == 0 ? s32->T : s32->w;
   const float* gf = mode == 0 ? s32->k : s32->gD;
   const float* uf2 = s32->u[2] ? s32->u[2] : s32->u[0];
+  // the enthalpy term of the energy rows (wq given: omega^n, whose binary32 copy enters) when
+  // the heat capacities differ
+  const bool hd = mode == 0 && wq && p.cp_v != p.cp_g;
+  const float* gdf = hd ? s32->gD : nullptr;
+  const float* wf = hd ? s32->w : nullptr;
   ++g_launches;
-#define DG_SCA(NN, FF) k_scalar_assemble_mx<NN, FF><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, mdot, u0, u1, u2, \
-      alpha_new, pinv, amb, phif, gf, s32->u[0], s32->u[1], uf2, Dg, c0, c1, c2, rhs)
-  if (nact(g) == 3) { if (g.fib) DG_SCA(3, true); else DG_SCA(3, false); }
-  else { if (g.fib) DG_SCA(2, true); else DG_SCA(2, false); }
+#define DG_SCA(NN, FF, HH) k_scalar_assemble_mx<NN, FF, HH><<<grid, TPB, 0, st>>>(g, p, mode, phi, rho, cp, mdot, u0, u1, \
+      u2, alpha_new, pinv, amb, phif, gf, s32->u[0], s32->u[1], uf2, Dg, c0, c1, c2, rhs, gdf, wf)
+  if (hd) {
+    if (nact(g) == 3) { if (g.fib) DG_SCA(3, true, true); else DG_SCA(3, false, true); }
+    else { if (g.fib) DG_SCA(2, true, true); else DG_SCA(2, false, true); }
+  } else {
+    if (nact(g) == 3) { if (g.fib) DG_SCA(3, true, false); else DG_SCA(3, false, false); }
+    else { if (g.fib) DG_SCA(2, true, false); else DG_SCA(2, false, false); }
+  }
 #undef DG_SCA
 }
 

@@ -302,7 +302,7 @@ def test_autograd_function_with_flow(D):
 
 
 def test_flow_adjoint_rejects_unsupported_forms(D):
-    for over in (dict(adv_scheme=1), dict(precision=1), dict(co_max=0.2)):
+    for over in (dict(adv_scheme=1), dict(precision=1), dict(co_max=0.2), dict(cp_v=2400.0)):
         sim = D.Droplet(small(**over))
         with pytest.raises(D.DropletError):
             D.droplet_adjoint(sim.h, 5, 5)

@@ -110,6 +110,14 @@ FIBRE = {name + "-fibre": (dict(cfg, fiber=1, fiber_radius=1.5e-4 if cfg["geom"]
          if name in ("axisym-gravity", "axisym-gravity-launched", "axisym-forced-inlet", "cart3d-natural-16",
                      "cart3d-natural-16-launched", "cart3d-pr-forced-16")}
 CASES.update(FIBRE)
+# Vapour and inert gas of different heat capacities (c_p,v = 2400 against c_p,g = 1100 J/kg/K):
+# the species-diffusion enthalpy term of Eq. Teqn in the energy rows (reading R33), on both
+# solver paths, with the fibre and on a ragged 3D grid
+HEATCAP = {name + "-heatcap": (dict(cfg, cp_v=2400.0), pre)
+           for name, (cfg, pre) in list(CASES.items())
+           if name in ("axisym-natural", "axisym-gravity-launched", "axisym-gravity-fibre", "cart3d-natural-16",
+                       "cart3d-pr-forced-16", "cart3d-ragged-12x10x14")}
+CASES.update(HEATCAP)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -268,6 +276,28 @@ def test_fibre_in_mixed_precision(D, name):
         assert np.abs(b.get("u%d" % c)[sph]).max() == 0.0
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("name", ["axisym-natural-heatcap", "cart3d-pr-forced-16-heatcap"])
+def test_heat_capacities_in_mixed_precision(D, name):
+    """The enthalpy term of different heat capacities in mixed precision (formed in binary32
+    from the copies of rho D, omega and T): over ten steps (2D; three in 3D) the run follows
+    the FP64 path of the same case (droplet volume 1e-5, alpha and T 1e-5, solver tolerances
+    1e-10), ten times closer than the FP64 run with equal heat capacities is."""
+    cfg64 = dict(CASES[name][0], cg_rtol=1e-10, helm_rtol=1e-10)
+    cfg32 = dict(cfg64, precision=1)
+    G = Grid(cfg64)
+    a, b, c = D.Droplet(cfg64), D.Droplet(cfg32), D.Droplet(dict(cfg64, cp_v=cfg64["cp_g"]))
+    for _ in range(10 if G.axisym else 3):
+        assert a.step(1) == 0 and b.step(1) == 0 and c.step(1) == 0
+    da, db = a.diag(), b.diag()
+    assert abs(da["V_l"] - db["V_l"]) <= 1e-5 * da["V_l"]
+    assert rel(b.get("alpha"), a.get("alpha")) < 1e-5
+    assert rel(b.get("T"), a.get("T")) < 1e-5
+    assert rel(c.get("T"), a.get("T")) > 10.0 * rel(b.get("T"), a.get("T"))
+    a.close()
+    b.close()
+    c.close()
 
 
 def test_fibre_finer_than_the_grid_is_no_fibre(D):

@@ -58,7 +58,7 @@ def test_struct_layout_matches_header(tmp_path):
 
 @pytest.mark.parametrize("bad", [dict(dt=0.0), dict(n=(2, 128, 1)), dict(D0=-1.0), dict(geom=5), dict(mg_tile=(4, 32)),
                                  dict(mg_tile=(32, 512)),
-                                 dict(xc=(1e-3, 4e-3, 0.0)), dict(cp_v=1200.0), dict(eq_model=3),
+                                 dict(xc=(1e-3, 4e-3, 0.0)), dict(eq_model=3),
                                  dict(cg_maxit=0), dict(wait_limit=-1), dict(solver_select=2), dict(co_max=-0.1),
                                  dict(co_max=float("nan")), dict(adv_scheme=2), dict(drho_l_dT=float("nan")),
                                  dict(drho_l_dT=-2.0), dict(fiber=2),
