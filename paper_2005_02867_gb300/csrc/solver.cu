@@ -756,45 +756,58 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
       const T* r0T = a.r[1];                    // the defect r0 in precision T (phase 0)
       T g = 0, dl = 0, q = 0;
 #define RH(o) (nu * a.sc[o] * r0T[o])
-      for (int id = id0; id < N; id += gs) {
+      // one cell's r^0, c^ on its low faces, w = A^ r^0 and diagonal (loads and arithmetic only)
+      struct SV { T rP, c0, c1, c2, y, d; };
+      auto cellv = [&](int id) -> SV {
         int i, j, kk;
         bdecomp(a.A.m, id, i, j, kk);
-        const T sP = a.sc[id], rP = RH(id);
-        a.r[0][id] = rP;
-        a.s[0][id] = 0;
-        a.p[id] = 0;
-        a.dx[id] = 0;
-        T y = rP;
+        SV o;
+        const T sP = a.sc[id];
+        o.rP = RH(id);
+        T y = o.rP;
+        o.c0 = 0;
         if (i > 0) {
-          const T c = (T)a.A.c[0][id] * sP * a.sc[id - 1];
-          a.ch[0][id] = c;
-          y -= c * RH(id - 1);
-        } else {
-          a.ch[0][id] = 0;
+          o.c0 = (T)a.A.c[0][id] * sP * a.sc[id - 1];
+          y -= o.c0 * RH(id - 1);
         }
         if (i < m0 - 1) y -= (T)a.A.c[0][id + 1] * sP * a.sc[id + 1] * RH(id + 1);
+        o.c1 = 0;
         if (j > 0) {
-          const T c = (T)a.A.c[1][id] * sP * a.sc[id - st1];
-          a.ch[1][id] = c;
-          y -= c * RH(id - st1);
-        } else {
-          a.ch[1][id] = 0;
+          o.c1 = (T)a.A.c[1][id] * sP * a.sc[id - st1];
+          y -= o.c1 * RH(id - st1);
         }
         if (j < m1 - 1) y -= (T)a.A.c[1][id + st1] * sP * a.sc[id + st1] * RH(id + st1);
+        o.c2 = 0;
         if (has2) {
           if (kk > 0) {
-            const T c = (T)a.A.c[2][id] * sP * a.sc[id - st2];
-            a.ch[2][id] = c;
-            y -= c * RH(id - st2);
-          } else {
-            a.ch[2][id] = 0;
+            o.c2 = (T)a.A.c[2][id] * sP * a.sc[id - st2];
+            y -= o.c2 * RH(id - st2);
           }
           if (kk < m2 - 1) y -= (T)a.A.c[2][id + st2] * sP * a.sc[id + st2] * RH(id + st2);
         }
-        a.w[0][id] = y;
-        g += rP * rP;
-        dl += y * rP;
-        q += a.dg[id] * rP * rP;
+        o.y = y;
+        o.d = a.dg[id];
+        return o;
+      };
+      auto store = [&](int id, const SV& o) {
+        a.r[0][id] = o.rP;
+        a.s[0][id] = 0;
+        a.p[id] = 0;
+        a.dx[id] = 0;
+        a.ch[0][id] = o.c0;
+        a.ch[1][id] = o.c1;
+        if (has2) a.ch[2][id] = o.c2;
+        a.w[0][id] = o.y;
+        g += o.rP * o.rP;
+        dl += o.y * o.rP;
+        q += o.d * o.rP * o.rP;
+      };
+      // two cells a trip (as the iterations' passes): both cells' loads before either's stores
+      for (int id = id0; id < N; id += 2 * gs) {
+        const int i1 = id + gs < N ? id + gs : id;
+        const SV v0 = cellv(id), v1 = cellv(i1);
+        store(id, v0);
+        if (i1 != id) store(i1, v1);
       }
 #undef RH
       v[3 * k] = g;
@@ -988,7 +1001,13 @@ __global__ void __launch_bounds__(PTPB, sizeof(T) == 4 ? 2 : 1) k_pcg_persist(Pe
       const PersistArgs<T>& a = M.s[k];
       const int N = (int)a.A.N;
       const double inv_nu = s_inv_nu[k];
-      for (int id = id0; id < N; id += gs) a.x[id] += (double)(a.sc[id] * a.dx[id]) * inv_nu;
+      for (int id = id0; id < N; id += 2 * gs) {   // two cells a trip
+        const int i1 = id + gs < N ? id + gs : id;
+        const double x0 = a.x[id], x1 = a.x[i1];
+        const T e0 = a.sc[id] * a.dx[id], e1 = a.sc[i1] * a.dx[i1];
+        a.x[id] = x0 + (double)e0 * inv_nu;
+        if (i1 != id) a.x[i1] = x1 + (double)e1 * inv_nu;
+      }
     }
   }
   // statistics of each system, then of the whole solve, then the barrier reset
