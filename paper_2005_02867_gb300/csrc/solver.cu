@@ -303,8 +303,13 @@ __global__ void k_fin_rz(const double* part, int nblk, double* sc, const int* do
 __global__ void k_p_update(long long N, double* p, const double* z, const double* sc, const int* done) {
   if (*done) return;
   double be = sc[S_BETA];
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N; id += (long long)gridDim.x * blockDim.x)
-    p[id] = z[id] + be * p[id];
+  const long long gs = (long long)gridDim.x * blockDim.x;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < N; id += 2 * gs) {   // two a trip
+    const long long i1 = id + gs < N ? id + gs : id;
+    const double z0 = z[id], p0 = p[id], z1 = z[i1], p1 = p[i1];
+    p[id] = z0 + be * p0;
+    if (i1 != id) p[i1] = z1 + be * p1;
+  }
 }
 
 // ---------------------------------------------------------------- FP32 defect-correction CG
