@@ -300,6 +300,34 @@ def test_heat_capacities_in_mixed_precision(D, name):
     c.close()
 
 
+@pytest.mark.parametrize("shape", [(25, 41, 1), (13, 11, 15), (176, 176, 176)])
+def test_launched_binary32_multigrid(D, shape):
+    """The launched V-cycle of a binary32 hierarchy (the path of the large mixed grids), on odd
+    dimensions (25 x 41, 13 x 11 x 15) and at 176^3: the prolongation folded into the first
+    post-smoothing half sweep, and on the levels of 2^20 or more updated cells (176^3) the half
+    sweeps at two cells a thread.  Over a few steps the mixed run follows the FP64 run of the same case (both on the
+    launched solvers): droplet volume 1e-5, alpha and T 1e-5."""
+    if shape[2] == 1:
+        cfg64 = W.cfg5_axisym_128x256(n=shape, L=(shape[0] * 6.25e-5, shape[1] * 6.25e-5, 0.0),
+                                      xc=(0.0, shape[1] * 3.125e-5, 0.0), D0=0.8e-3)
+    else:
+        h = 1.0e-4 if shape[0] < 64 else 2.0e-5
+        Lx = tuple(m * h for m in shape)
+        cfg64 = W.make(geom=1, n=shape, L=Lx, xc=tuple(0.5 * x for x in Lx), D0=0.5 * min(Lx),
+                       g=(0, 0, -9.81), dt=2e-6)
+    cfg64 = dict(cfg64, solver_select=1, cg_rtol=1e-10, helm_rtol=1e-10)
+    cfg32 = dict(cfg64, precision=1)
+    a, b = D.Droplet(cfg64), D.Droplet(cfg32)
+    for _ in range(4 if shape[0] < 64 else 2):
+        assert a.step(1) == 0 and b.step(1) == 0
+    da, db = a.diag(), b.diag()
+    assert abs(da["V_l"] - db["V_l"]) <= 1e-5 * da["V_l"]
+    assert rel(b.get("alpha"), a.get("alpha")) < 1e-5
+    assert rel(b.get("T"), a.get("T")) < 1e-5
+    a.close()
+    b.close()
+
+
 def test_fibre_finer_than_the_grid_is_no_fibre(D):
     """A fibre radius below every cell-centre distance leaves no solid cell: the run is the
     run without a fibre (the same radius D_f of the potential xi), bit for bit (the fibre's
