@@ -203,7 +203,10 @@ enum droplet_field {
  * reduction kernels (the state is restored afterwards) and keeps the fastest.
  * On success *out receives the context.  Errors: DROPLET_ERR_ARG (bad
  * dimensions, droplet not inside the domain, dt <= 0, unsupported option),
- * DROPLET_ERR_NOMEM, DROPLET_ERR_CUDA. */
+ * DROPLET_ERR_SIZE (the pressure multigrid halves the grid while every active
+ * dimension is even and above 2; when the level where that stops is too large
+ * for the one-block coarse solve's shared memory, e.g. a large grid with an odd
+ * dimension, the grid is refused), DROPLET_ERR_NOMEM, DROPLET_ERR_CUDA. */
 int droplet_init(const droplet_config* cfgs, int n_droplets, void* cuda_stream, droplet_ctx** out);
 
 /* Advance every droplet by n_steps time steps (the stage list of Sec. 3.1):
