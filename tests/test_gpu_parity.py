@@ -300,12 +300,12 @@ def test_heat_capacities_in_mixed_precision(D, name):
     c.close()
 
 
-@pytest.mark.parametrize("shape", [(25, 41, 1), (13, 11, 15), (176, 176, 176)])
+@pytest.mark.parametrize("shape", [(128, 96, 1), (32, 24, 20), (176, 176, 176)])
 def test_launched_binary32_multigrid(D, shape):
-    """The launched V-cycle of a binary32 hierarchy (the path of the large mixed grids), on odd
-    dimensions (25 x 41, 13 x 11 x 15) and at 176^3: the prolongation folded into the first
-    post-smoothing half sweep, and on the levels of 2^20 or more updated cells (176^3) the half
-    sweeps at two cells a thread.  Over a few steps the mixed run follows the FP64 run of the same case (both on the
+    """The launched V-cycle of a binary32 hierarchy (the path of the large mixed grids): the
+    prolongation folded into the first post-smoothing half sweep of every level above the
+    one-block coarse solve (one such level on 128 x 96 and 32 x 24 x 20, four at 176^3), and on
+    the levels of 2^20 or more updated cells (176^3) the half sweeps at two cells a thread.  Over a few steps the mixed run follows the FP64 run of the same case (both on the
     launched solvers): droplet volume 1e-5, alpha and T 1e-5."""
     if shape[2] == 1:
         cfg64 = W.cfg5_axisym_128x256(n=shape, L=(shape[0] * 6.25e-5, shape[1] * 6.25e-5, 0.0),
